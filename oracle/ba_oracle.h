@@ -1,0 +1,62 @@
+/*
+ * Plain FP64 CPU oracle for the local bundle-adjustment LM iteration.
+ * TEST INFRASTRUCTURE ONLY: used by tests/, the smoke check and the
+ * benchmark's CPU-baseline leg, never by the CUDA library.
+ *
+ * Arrays are row-major FP64 in caller-owned host memory:
+ *   intr     [n_cams][7]  f, cx, cy, k1, k2, p1, p2 (pixels; Brown terms on
+ *                         normalised coordinates)
+ *   R        [n_cams][9]  camera->world rotation (Eq. 5 uses R^T)
+ *   T        [n_cams][3]  camera centre, local ENU metres
+ *   X        [n_pts][3]   points, local ENU metres
+ *   R_prior, T_prior      IMU attitude / GNSS position per camera
+ *   fixed    [n_cams]     1 = pose held fixed (cluster overlap, Sec. 3.2)
+ *   obs_cam, obs_pt, obs_uv[n_obs][2]  observations in pixels
+ * sigma_gnss / sigma_imu of 0 switch that prior off.
+ */
+#ifndef BA_ORACLE_H
+#define BA_ORACLE_H
+
+#define ORC_MIN_DEPTH 1e-6
+#define ORC_DIAG_MIN 1e-6
+#define ORC_DIAG_MAX 1e32
+#define ORC_ERR_NOT_PD (-3)
+
+typedef struct {
+  int n_cams, n_pts, n_obs;
+  const double* intr;
+  const double* R_prior;
+  const double* T_prior;
+  const unsigned char* fixed;
+  const int* obs_cam;
+  const int* obs_pt;
+  const double* obs_uv;
+  double sigma_px, huber_delta, sigma_gnss, sigma_imu;
+} orc_problem;
+
+typedef struct {
+  int accepted, status;
+  double F, F_new, pred, gain, mu_used, mu, nu;
+} orc_step_info;
+
+void orc_so3_exp(const double w[3], double R[9]);
+void orc_so3_log(const double R[9], double w[3]);
+void orc_so3_jr_inv(const double w[3], double J[9]);
+int orc_project(const double intr[7], const double R[9], const double T[3], const double X[3], double uv[2]);
+double orc_huber_rho(double s, double delta);
+double orc_huber_weight(double s, double delta);
+int orc_linearize_obs(const orc_problem* P, const double* R, const double* T, const double* X, int i,
+                      double r[2], double Jc[12], double Jp[6], double* s_out);
+void orc_linearize_prior(const orc_problem* P, const double* R, const double* T, int k, double r[6],
+                         double J[36]);
+double orc_cost(const orc_problem* P, const double* R, const double* T, const double* X);
+int orc_solve_damped(const orc_problem* P, const double* R, const double* T, const double* X, double mu,
+                     double* dc, double* dp, double* gc_out, double* gp_out, double* Dc_out, double* Dp_out);
+void orc_apply_step(const orc_problem* P, const double* R, const double* T, const double* X, const double* dc,
+                    const double* dp, double* Rn, double* Tn, double* Xn);
+int orc_lm_step(const orc_problem* P, double* R, double* T, double* X, double* mu, double* nu,
+                orc_step_info* info);
+int orc_lm_run(const orc_problem* P, double* R, double* T, double* X, int iters, double mu0,
+               orc_step_info* trace);
+
+#endif
