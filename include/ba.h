@@ -1,0 +1,216 @@
+/*
+ * ba.h -- C ABI of the GB300 local bundle-adjustment library.
+ *
+ * The library runs the Levenberg-Marquardt iteration of a local (cluster)
+ * bundle adjustment on one GPU: per-observation reprojection residuals and
+ * Jacobians, Schur-complement assembly of the reduced camera system, a damped
+ * Cholesky solve, point back-substitution, and the cost / gain-ratio test.
+ *
+ * Problem statement it follows (arXiv 2511.06152, Sec. 3.2):
+ *   - a cluster C_l = {I_k1 ... I_kM} of M images, each with an initial pose
+ *     (R_k, T_k) from GNSS/IMU in local ENU coordinates;
+ *   - observations p_kj of points X_j, Eq. 5: p_kj = pi(K R_k^T (X_j - T_k)),
+ *     R_k camera->world, T_k the camera centre, pi(x,y,z) = (x/z, y/z);
+ *     K carries one focal length f, the principal point (cx, cy) and Brown
+ *     radial (k1, k2) and tangential (p1, p2) terms on normalised coordinates;
+ *   - the robust cost of Eq. 7, E = sum_k sum_j rho(||p_kj - pi(...)||^2), with
+ *     rho = Huber of threshold huber_delta_px acting on the squared 2-D norm,
+ *     residuals whitened by sigma_px; GNSS position and IMU attitude priors
+ *     whitened by sigma_gnss_m / sigma_imu_rad are added for every free camera;
+ *   - overlap images carried over from the previous cluster may be held fixed.
+ * The cost the library minimises is
+ *   F = 1/2 sum rho(s)/sigma_px^2 + 1/2 sum_free(|T - T_gnss|^2/sigma_gnss^2
+ *       + |Log(R_imu^T R)|^2 / sigma_imu^2).
+ * The optimiser (the paper names none) is LM with Marquardt scaling
+ * D = clamp(diag(J^T J), 1e-6, 1e32), pred = 1/2 d^T (mu D d + g), gain =
+ * (F - F(x+d)) / pred, accept when gain > 0, and Nielsen's mu/nu update.
+ * Parameters move by R <- R Exp(dtheta), T <- T + dT, X <- X + dX.
+ *
+ * Conventions for every entry point:
+ *   - Arrays are row-major.  Doubles are IEEE binary64, int32_t / uint8_t as
+ *     named.  A rotation is 9 doubles (3x3, camera->world).
+ *   - Pointers in ba_cluster_desc are host pointers when ptr_kind is
+ *     BA_PTR_HOST and device pointers (current device) when BA_PTR_DEVICE.
+ *     The library copies every input into device memory it owns before
+ *     ba_create_cluster returns; the caller may free its buffers afterwards.
+ *   - Output buffers are caller-owned and written before the call returns
+ *     (ba_get_state, ba_solve_step, ba_run, ba_solve_batch, ba_poll).
+ *   - Return codes only; nothing is thrown across the ABI.  A numerical
+ *     failure (a reduced camera system that is not positive definite) is
+ *     reported in the per-step status and handled as a rejected LM step.
+ *   - All GPU work of a context runs on the stream given in ba_config.  Calls
+ *     on one context must be serialised by the caller, except ba_poll, which
+ *     may be called from any thread.
+ *   - Reductions are deterministic: every sum runs in a fixed order that
+ *     depends only on the cluster, never on the batch it runs in, so a
+ *     cluster's result is bit-identical alone and in any batch.
+ */
+#ifndef BA_GB300_H
+#define BA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define BA_API __attribute__((visibility("default")))
+#else
+#define BA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ba_status;
+#define BA_OK 0
+#define BA_PENDING 1
+#define BA_ERR_INVALID (-1)   /* malformed argument or problem data */
+#define BA_ERR_BUDGET (-2)    /* would exceed hbm_budget_bytes or slots: retry later */
+#define BA_ERR_NOT_PD (-3)    /* damped reduced camera system not positive definite */
+#define BA_ERR_TIMEOUT (-4)   /* a bounded wait expired */
+#define BA_ERR_CUDA (-5)      /* a CUDA runtime call failed */
+#define BA_ERR_NOT_FOUND (-6) /* unknown cluster id or ticket */
+
+#define BA_FP64 0  /* every step in binary64 */
+#define BA_MIXED 1 /* per-observation work in binary32, solve and cost in binary64 */
+
+#define BA_PTR_HOST 0
+#define BA_PTR_DEVICE 1
+
+#define BA_MAX_TRACK 32 /* observations of one point in one cluster */
+
+typedef struct ba_ctx ba_ctx;
+typedef uint64_t ba_cluster_id; /* 0 is never a valid id */
+typedef uint64_t ba_ticket;     /* 0 is never a valid ticket */
+
+typedef struct {
+  int32_t device;            /* CUDA device ordinal */
+  void* stream;              /* cudaStream_t to run on; NULL: the library creates one */
+  uint64_t hbm_budget_bytes; /* device memory the context may hold; 0 = unlimited */
+  int32_t precision;         /* BA_FP64 or BA_MIXED */
+  int32_t n_slots;           /* clusters the serving scheduler runs at once (ba_submit); 0 = 64 */
+  int32_t refine_steps;      /* iterative-refinement passes after the Cholesky solve; <0 = default 1 */
+  int32_t reserved;
+} ba_config;
+
+typedef struct {
+  int32_t n_cams, n_pts, n_obs;
+  int32_t ptr_kind;             /* BA_PTR_HOST or BA_PTR_DEVICE */
+  const double* intr;           /* [n_cams][7]: f, cx, cy, k1, k2, p1, p2 */
+  const double* R;              /* [n_cams][9]: initial rotations, camera->world */
+  const double* T;              /* [n_cams][3]: initial centres, metres */
+  const double* X;              /* [n_pts][3]: initial points, metres */
+  const double* R_prior;        /* [n_cams][9]: IMU attitude */
+  const double* T_prior;        /* [n_cams][3]: GNSS position */
+  const uint8_t* fixed;         /* [n_cams]: 1 = pose held fixed; NULL = none fixed */
+  const int32_t* obs_cam;       /* [n_obs] camera of each observation */
+  const int32_t* obs_pt;        /* [n_obs] point of each observation */
+  const double* obs_uv;         /* [n_obs][2] pixel measurement */
+  double sigma_px;              /* pixel standard deviation (> 0) */
+  double huber_delta_px;        /* Huber threshold in pixels (> 0) */
+  double sigma_gnss_m;          /* GNSS sigma; 0 switches the position prior off */
+  double sigma_imu_rad;         /* IMU sigma; 0 switches the attitude prior off */
+  double mu0;                   /* initial damping; <= 0 means 1e-4 */
+  ba_cluster_id warm_from;      /* 0, or a live cluster whose state seeds this one */
+  const int32_t* warm_cam_map;  /* [n_cams] camera index in warm_from, or -1 (host pointer) */
+  const int32_t* warm_pt_map;   /* [n_pts] point index in warm_from, or -1 (host pointer) */
+} ba_cluster_desc;
+
+typedef struct {
+  double cost;     /* F(x) at the current state */
+  double grad_inf; /* max |g| over free-camera and point coordinates */
+  int32_t n_free;  /* free cameras */
+  int32_t reserved;
+} ba_lin_info;
+
+typedef struct {
+  int32_t accepted;
+  int32_t status;   /* BA_OK or BA_ERR_NOT_PD */
+  double F_before;  /* F(x) */
+  double F_after;   /* F(x + d) */
+  double predicted; /* pred = 1/2 d^T (mu D d + g) */
+  double gain;      /* (F_before - F_after) / pred */
+  double mu_used;   /* damping of this step */
+  double mu;        /* damping after the update */
+  double nu;
+} ba_step_info;
+
+typedef struct {
+  int32_t max_iters; /* LM iterations (accepted and rejected both count) */
+  int32_t reserved;
+} ba_solve_opts;
+
+typedef struct {
+  int32_t status;     /* BA_OK, or the last step's error */
+  int32_t iters;      /* iterations run */
+  int32_t accepted;   /* accepted steps */
+  int32_t reserved;
+  double initial_cost;
+  double final_cost;
+  double latency_ms;  /* submit -> completion seen by the scheduler */
+} ba_result;
+
+/* Create a context on cfg->device.  *out receives the handle. */
+BA_API ba_status ba_init(ba_ctx** out, const ba_config* cfg);
+
+/* Copy a cluster to the device and presort its observation index
+ * (point-major and camera-major orders, camera-pair table).  Fails with
+ * BA_ERR_INVALID on indices out of range, repeated (camera, point) pairs,
+ * more than BA_MAX_TRACK observations of one point, non-finite input, or
+ * no free camera; with BA_ERR_BUDGET when the device memory it needs would
+ * exceed the context's budget. */
+BA_API ba_status ba_create_cluster(ba_ctx* ctx, const ba_cluster_desc* d, ba_cluster_id* out);
+
+/* Evaluate F and the gradient infinity norm at the current state. */
+BA_API ba_status ba_linearize(ba_ctx* ctx, ba_cluster_id id, ba_lin_info* out);
+
+/* One LM iteration on one cluster (blocking); out may be NULL. */
+BA_API ba_status ba_solve_step(ba_ctx* ctx, ba_cluster_id id, ba_step_info* out);
+
+/* iters LM iterations on one cluster in one device-side sequence (no host
+ * round trip between iterations); trace[iters] may be NULL. */
+BA_API ba_status ba_run(ba_ctx* ctx, ba_cluster_id id, int32_t iters, ba_step_info* trace);
+
+/* iters LM iterations on n clusters at once: every kernel of an iteration is
+ * one launch over all clusters, and the whole sequence is one CUDA-graph
+ * launch.  Each cluster's result equals its ba_run result bit for bit.
+ * results[n] may be NULL; trace may be NULL or [n][iters]. */
+BA_API ba_status ba_solve_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n, int32_t iters,
+                         ba_result* results, ba_step_info* trace);
+
+/* Restore a cluster's initial state (the one given at create) and damping. */
+BA_API ba_status ba_reset(ba_ctx* ctx, ba_cluster_id id);
+
+/* Queue a cluster for the serving scheduler (non-blocking).  The scheduler
+ * admits queued clusters into free slots between LM iterations, so work
+ * submitted while others run joins the running batch.  *out receives a
+ * ticket for ba_poll. */
+BA_API ba_status ba_submit(ba_ctx* ctx, ba_cluster_id id, const ba_solve_opts* opts, ba_ticket* out);
+
+/* BA_PENDING while the ticket's cluster is queued or running; BA_OK with
+ * *out filled once it has finished.  Thread-safe. */
+BA_API ba_status ba_poll(ba_ctx* ctx, ba_ticket t, ba_result* out);
+
+/* Copy the current state out.  Pointers are host pointers when ptr_kind is
+ * BA_PTR_HOST, device pointers when BA_PTR_DEVICE; any may be NULL. */
+BA_API ba_status ba_get_state(ba_ctx* ctx, ba_cluster_id id, double* R, double* T, double* X, int32_t ptr_kind);
+
+/* Per-observation reprojection error norms |pi(...) - p| in pixels at the
+ * current state, in the caller's observation order (host buffer [n_obs]). */
+BA_API ba_status ba_reprojection_errors(ba_ctx* ctx, ba_cluster_id id, double* err);
+
+/* Device memory the context holds now, in bytes. */
+BA_API ba_status ba_memory_in_use(ba_ctx* ctx, uint64_t* bytes);
+
+BA_API ba_status ba_destroy_cluster(ba_ctx* ctx, ba_cluster_id id);
+BA_API ba_status ba_shutdown(ba_ctx* ctx);
+BA_API const char* ba_status_string(ba_status s);
+
+/* Human-readable reason of the last error returned on this context (valid
+ * until the next call on the context). */
+BA_API const char* ba_last_error(ba_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BA_GB300_H */

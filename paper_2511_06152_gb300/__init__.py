@@ -1,0 +1,278 @@
+"""Python binding of the GB300 local bundle-adjustment library (include/ba.h).
+
+Argument marshalling only: every step of the LM iteration runs in the CUDA
+kernels of ``_build/libba_gb300.so``.  There is no CPU fallback; importing
+``lib()`` on a machine where the library cannot be loaded raises.
+
+The functions keep the C names (``ba_init``, ``ba_create_cluster``,
+``ba_run`` ...) and take/return numpy arrays or ctypes structs.  ``Context``
+is a small convenience wrapper that owns a ``ba_ctx``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+BA_OK = 0
+BA_PENDING = 1
+BA_ERR_INVALID = -1
+BA_ERR_BUDGET = -2
+BA_ERR_NOT_PD = -3
+BA_ERR_TIMEOUT = -4
+BA_ERR_CUDA = -5
+BA_ERR_NOT_FOUND = -6
+BA_FP64 = 0
+BA_MIXED = 1
+BA_PTR_HOST = 0
+BA_PTR_DEVICE = 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+
+
+class ba_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("stream", ctypes.c_void_p), ("hbm_budget_bytes", ctypes.c_uint64),
+                ("precision", ctypes.c_int32), ("n_slots", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class ba_cluster_desc(ctypes.Structure):
+    _fields_ = [("n_cams", ctypes.c_int32), ("n_pts", ctypes.c_int32), ("n_obs", ctypes.c_int32),
+                ("ptr_kind", ctypes.c_int32),
+                ("intr", _dp), ("R", _dp), ("T", _dp), ("X", _dp), ("R_prior", _dp), ("T_prior", _dp),
+                ("fixed", _u8p), ("obs_cam", _ip), ("obs_pt", _ip), ("obs_uv", _dp),
+                ("sigma_px", ctypes.c_double), ("huber_delta_px", ctypes.c_double),
+                ("sigma_gnss_m", ctypes.c_double), ("sigma_imu_rad", ctypes.c_double), ("mu0", ctypes.c_double),
+                ("warm_from", ctypes.c_uint64), ("warm_cam_map", _ip), ("warm_pt_map", _ip)]
+
+
+class ba_lin_info(ctypes.Structure):
+    _fields_ = [("cost", ctypes.c_double), ("grad_inf", ctypes.c_double), ("n_free", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class ba_step_info(ctypes.Structure):
+    _fields_ = [("accepted", ctypes.c_int32), ("status", ctypes.c_int32), ("F_before", ctypes.c_double),
+                ("F_after", ctypes.c_double), ("predicted", ctypes.c_double), ("gain", ctypes.c_double),
+                ("mu_used", ctypes.c_double), ("mu", ctypes.c_double), ("nu", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ba_solve_opts(ctypes.Structure):
+    _fields_ = [("max_iters", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ba_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("accepted", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("initial_cost", ctypes.c_double), ("final_cost", ctypes.c_double),
+                ("latency_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["ba_init", "ba_create_cluster", "ba_linearize", "ba_solve_step", "ba_run", "ba_solve_batch", "ba_reset",
+           "ba_submit", "ba_poll", "ba_get_state", "ba_reprojection_errors", "ba_memory_in_use",
+           "ba_destroy_cluster", "ba_shutdown", "ba_status_string", "ba_last_error"]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path(build: bool = True) -> str:
+    return _build.build() if build else _build.LIB
+
+
+def lib(build: bool = True):
+    """Load the shared library (building it first if stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(library_path(build))
+            vp = ctypes.c_void_p
+            u64 = ctypes.c_uint64
+            L.ba_init.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ba_config)]
+            L.ba_create_cluster.argtypes = [vp, ctypes.POINTER(ba_cluster_desc), ctypes.POINTER(u64)]
+            L.ba_linearize.argtypes = [vp, u64, ctypes.POINTER(ba_lin_info)]
+            L.ba_solve_step.argtypes = [vp, u64, ctypes.POINTER(ba_step_info)]
+            L.ba_run.argtypes = [vp, u64, ctypes.c_int32, ctypes.POINTER(ba_step_info)]
+            L.ba_solve_batch.argtypes = [vp, ctypes.POINTER(u64), ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.POINTER(ba_result), ctypes.POINTER(ba_step_info)]
+            L.ba_reset.argtypes = [vp, u64]
+            L.ba_submit.argtypes = [vp, u64, ctypes.POINTER(ba_solve_opts), ctypes.POINTER(u64)]
+            L.ba_poll.argtypes = [vp, u64, ctypes.POINTER(ba_result)]
+            L.ba_get_state.argtypes = [vp, u64, _dp, _dp, _dp, ctypes.c_int32]
+            L.ba_reprojection_errors.argtypes = [vp, u64, _dp]
+            L.ba_memory_in_use.argtypes = [vp, ctypes.POINTER(u64)]
+            L.ba_destroy_cluster.argtypes = [vp, u64]
+            L.ba_shutdown.argtypes = [vp]
+            L.ba_status_string.argtypes = [ctypes.c_int32]
+            L.ba_status_string.restype = ctypes.c_char_p
+            L.ba_last_error.argtypes = [vp]
+            L.ba_last_error.restype = ctypes.c_char_p
+            for name in EXPORTS:
+                if name not in ("ba_status_string", "ba_last_error"):
+                    getattr(L, name).restype = ctypes.c_int32
+            _lib = L
+    return _lib
+
+
+class BAError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def _check(st, ctx=None, what=""):
+    if st not in (BA_OK, BA_PENDING):
+        L = lib()
+        detail = L.ba_last_error(ctx).decode() if ctx else ""
+        raise BAError(st, f"{what}: {L.ba_status_string(st).decode()} {detail}".strip())
+    return st
+
+
+def _f64(a, shape):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(shape))
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def make_desc(scene, keep):
+    """ba_cluster_desc for a scene dict (host arrays); `keep` holds the arrays alive."""
+    nc, npt, no = int(scene["n_cams"]), int(scene["n_pts"]), int(scene["n_obs"])
+    arrs = dict(
+        intr=_f64(scene["intr"], (nc, 7)), R=_f64(scene["R0"], (nc, 9)), T=_f64(scene["T0"], (nc, 3)),
+        X=_f64(scene["X0"], (npt, 3)), R_prior=_f64(scene["R_prior"], (nc, 9)), T_prior=_f64(scene["T_prior"], (nc, 3)),
+        fixed=np.ascontiguousarray(scene.get("fixed", np.zeros(nc)), dtype=np.uint8),
+        obs_cam=np.ascontiguousarray(scene["obs_cam"], dtype=np.int32),
+        obs_pt=np.ascontiguousarray(scene["obs_pt"], dtype=np.int32),
+        obs_uv=_f64(scene["obs_uv"], (no, 2)))
+    keep.append(arrs)
+    d = ba_cluster_desc()
+    d.n_cams, d.n_pts, d.n_obs, d.ptr_kind = nc, npt, no, BA_PTR_HOST
+    for k in ("intr", "R", "T", "X", "R_prior", "T_prior", "obs_uv"):
+        setattr(d, k, _d(arrs[k]))
+    d.fixed = arrs["fixed"].ctypes.data_as(_u8p)
+    d.obs_cam = arrs["obs_cam"].ctypes.data_as(_ip)
+    d.obs_pt = arrs["obs_pt"].ctypes.data_as(_ip)
+    d.sigma_px = float(scene["sigma_px"])
+    d.huber_delta_px = float(scene["huber_delta"])
+    d.sigma_gnss_m = float(scene["sigma_gnss"])
+    d.sigma_imu_rad = float(scene["sigma_imu"])
+    d.mu0 = float(scene.get("mu0", 1e-4))
+    d.warm_from = 0
+    return d
+
+
+class Context:
+    """Owns one ba_ctx on one device and stream."""
+
+    def __init__(self, device=0, precision=BA_FP64, stream=None, hbm_budget_bytes=0, n_slots=0, refine_steps=-1):
+        self.L = lib()
+        cfg = ba_config(device=device, stream=stream, hbm_budget_bytes=hbm_budget_bytes, precision=precision,
+                        n_slots=n_slots, refine_steps=refine_steps, reserved=0)
+        h = ctypes.c_void_p()
+        _check(self.L.ba_init(ctypes.byref(h), ctypes.byref(cfg)), None, "ba_init")
+        self.h = h
+        self.sizes = {}
+
+    def close(self):
+        if self.h:
+            self.L.ba_shutdown(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def create_cluster(self, scene, warm_from=0, warm_cam_map=None, warm_pt_map=None):
+        keep = []
+        d = make_desc(scene, keep)
+        if warm_from:
+            cm = np.ascontiguousarray(warm_cam_map, dtype=np.int32)
+            pm = np.ascontiguousarray(warm_pt_map, dtype=np.int32)
+            keep += [cm, pm]
+            d.warm_from = warm_from
+            d.warm_cam_map = cm.ctypes.data_as(_ip)
+            d.warm_pt_map = pm.ctypes.data_as(_ip)
+        cid = ctypes.c_uint64()
+        _check(self.L.ba_create_cluster(self.h, ctypes.byref(d), ctypes.byref(cid)), self.h, "ba_create_cluster")
+        self.sizes[cid.value] = (d.n_cams, d.n_pts, d.n_obs)
+        return cid.value
+
+    def linearize(self, cid):
+        out = ba_lin_info()
+        _check(self.L.ba_linearize(self.h, cid, ctypes.byref(out)), self.h, "ba_linearize")
+        return {"cost": out.cost, "grad_inf": out.grad_inf, "n_free": out.n_free}
+
+    def solve_step(self, cid):
+        out = ba_step_info()
+        _check(self.L.ba_solve_step(self.h, cid, ctypes.byref(out)), self.h, "ba_solve_step")
+        return out.as_dict()
+
+    def run(self, cid, iters, trace=True):
+        tr = (ba_step_info * max(1, iters))() if trace else None
+        _check(self.L.ba_run(self.h, cid, iters, tr), self.h, "ba_run")
+        return [tr[i].as_dict() for i in range(iters)] if trace else None
+
+    def solve_batch(self, cids, iters, trace=False):
+        n = len(cids)
+        ids = (ctypes.c_uint64 * n)(*cids)
+        res = (ba_result * n)()
+        tr = (ba_step_info * (n * max(1, iters)))() if trace else None
+        _check(self.L.ba_solve_batch(self.h, ids, n, iters, res, tr), self.h, "ba_solve_batch")
+        out = [res[i].as_dict() for i in range(n)]
+        if trace:
+            for i in range(n):
+                out[i]["trace"] = [tr[i * iters + t].as_dict() for t in range(iters)]
+        return out
+
+    def reset(self, cid):
+        _check(self.L.ba_reset(self.h, cid), self.h, "ba_reset")
+
+    def submit(self, cid, iters):
+        t = ctypes.c_uint64()
+        _check(self.L.ba_submit(self.h, cid, ctypes.byref(ba_solve_opts(iters, 0)), ctypes.byref(t)), self.h,
+               "ba_submit")
+        return t.value
+
+    def poll(self, ticket):
+        r = ba_result()
+        st = self.L.ba_poll(self.h, ticket, ctypes.byref(r))
+        if st == BA_PENDING:
+            return None
+        _check(st, self.h, "ba_poll")
+        return r.as_dict()
+
+    def get_state(self, cid):
+        nc, npt, _ = self.sizes[cid]
+        R, T, X = np.zeros((nc, 9)), np.zeros((nc, 3)), np.zeros((max(npt, 1), 3))
+        _check(self.L.ba_get_state(self.h, cid, _d(R), _d(T), _d(X), BA_PTR_HOST), self.h, "ba_get_state")
+        return R, T, X[:npt]
+
+    def reprojection_errors(self, cid):
+        _, _, no = self.sizes[cid]
+        e = np.zeros(max(no, 1))
+        _check(self.L.ba_reprojection_errors(self.h, cid, _d(e)), self.h, "ba_reprojection_errors")
+        return e[:no]
+
+    def memory_in_use(self):
+        v = ctypes.c_uint64()
+        _check(self.L.ba_memory_in_use(self.h, ctypes.byref(v)), self.h, "ba_memory_in_use")
+        return v.value
+
+    def destroy_cluster(self, cid):
+        _check(self.L.ba_destroy_cluster(self.h, cid), self.h, "ba_destroy_cluster")
+        self.sizes.pop(cid, None)

@@ -1,0 +1,1007 @@
+// Host side of the C ABI declared in include/ba.h: validation, the presort
+// that builds the deterministic reduction tables, device arenas, batch plans
+// with CUDA-graph replay, and the serving scheduler.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/ba.h"
+#include "ba_internal.h"
+
+using namespace bagpu;
+
+namespace {
+
+struct Cluster {
+  ba_cluster_id id = 0;
+  int nc = 0, np = 0, no = 0, nf = 0;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  DevCluster h{};                 // descriptor with device pointers
+  DevCluster* d_desc = nullptr;   // device copy of h
+  std::vector<int> pm_to_user;    // point-major position -> caller observation index
+  std::atomic<int> in_service{0}; // queued or running in the serving scheduler
+};
+
+struct Plan {
+  std::vector<ba_cluster_id> ids;
+  char* dbuf = nullptr;
+  size_t dbuf_bytes = 0;
+  BatchView bv{};
+  LmState* lm_out = nullptr;     // device [n]
+  double* gnorm = nullptr;       // device [n]
+  std::map<int, cudaGraphExec_t> graphs;
+};
+
+struct Ticket {
+  ba_cluster_id id = 0;
+  int iters = 0;
+  int done = 0;
+  ba_result res{};
+  std::chrono::steady_clock::time_point t_submit;
+};
+
+}  // namespace
+
+struct ba_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  uint64_t budget = 0;
+  bool mixed = false;
+  int n_slots = 64;
+  int refine = 1;
+  std::map<ba_cluster_id, Cluster*> clusters;
+  uint64_t next_id = 1;
+  uint64_t mem = 0;
+  std::map<std::vector<ba_cluster_id>, Plan*> plans;
+  int attr_max_n = 0;
+  std::string last_error;
+  std::mutex api_mu;  // serialises API calls against the scheduler thread
+
+  // serving
+  std::mutex sv_mu;
+  std::condition_variable sv_cv;
+  std::deque<ba_ticket> queue;
+  std::map<ba_ticket, Ticket> tickets;
+  uint64_t next_ticket = 1;
+  std::thread sched;
+  bool sched_stop = false;
+  bool sched_started = false;
+};
+
+namespace {
+
+ba_status set_err(ba_ctx* ctx, ba_status st, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return st;
+}
+
+#define CUDA_TRY(ctx, call)                                                            \
+  do {                                                                                 \
+    cudaError_t e__ = (call);                                                          \
+    if (e__ != cudaSuccess)                                                            \
+      return set_err(ctx, BA_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
+  } while (0)
+
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Layout {
+  size_t off = 0;
+  size_t add(size_t bytes) {
+    const size_t o = off;
+    off += align_up(bytes);
+    return o;
+  }
+};
+
+template <typename T>
+bool fetch(const T* src, size_t n, int kind, std::vector<T>& out) {
+  out.resize(n);
+  if (n == 0) return true;
+  if (!src) return false;
+  if (kind == BA_PTR_DEVICE) return cudaMemcpy(out.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost) == cudaSuccess;
+  std::memcpy(out.data(), src, n * sizeof(T));
+  return true;
+}
+
+bool all_finite(const std::vector<double>& v) {
+  for (double x : v)
+    if (!std::isfinite(x)) return false;
+  return true;
+}
+
+Cluster* find_cluster(ba_ctx* ctx, ba_cluster_id id) {
+  auto it = ctx->clusters.find(id);
+  return it == ctx->clusters.end() ? nullptr : it->second;
+}
+
+ba_status ensure_attrs(ba_ctx* ctx, int max_n) {
+  if (max_n <= ctx->attr_max_n) return BA_OK;
+  const int want = std::max(max_n, 6 * kMaxFreeSmall);
+  CUDA_TRY(ctx, set_kernel_attributes(want));
+  ctx->attr_max_n = want;
+  return BA_OK;
+}
+
+void free_plan(Plan* p) {
+  for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
+  if (p->dbuf) cudaFree(p->dbuf);
+  delete p;
+}
+
+void drop_plans_with(ba_ctx* ctx, ba_cluster_id id) {
+  for (auto it = ctx->plans.begin(); it != ctx->plans.end();) {
+    if (std::find(it->first.begin(), it->first.end(), id) != it->first.end()) {
+      ctx->mem -= it->second->dbuf_bytes;
+      free_plan(it->second);
+      it = ctx->plans.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** out) {
+  auto it = ctx->plans.find(ids);
+  if (it != ctx->plans.end()) {
+    *out = it->second;
+    return BA_OK;
+  }
+  const int n = (int)ids.size();
+  std::vector<DevCluster> descs(n);
+  std::vector<int> pre(3 * (size_t)(n + 1), 0);
+  int max_n = 6;
+  for (int i = 0; i < n; ++i) {
+    Cluster* c = find_cluster(ctx, ids[i]);
+    if (!c) return set_err(ctx, BA_ERR_NOT_FOUND, "unknown cluster id in batch");
+    descs[i] = c->h;
+    pre[i + 1] = pre[i] + c->h.n_tiles;
+    pre[(n + 1) + i + 1] = pre[(n + 1) + i] + c->h.n_cchunks;
+    pre[2 * (n + 1) + i + 1] = pre[2 * (n + 1) + i] + c->h.n_pchunks;
+    max_n = std::max(max_n, 6 * c->h.n_free);
+  }
+  ba_status st = ensure_attrs(ctx, max_n);
+  if (st != BA_OK) return st;
+  Plan* p = new Plan();
+  p->ids = ids;
+  Layout L;
+  const size_t o_desc = L.add(sizeof(DevCluster) * n);
+  const size_t o_pre = L.add(sizeof(int) * pre.size());
+  const size_t o_lm = L.add(sizeof(LmState) * n);
+  const size_t o_gn = L.add(sizeof(double) * n);
+  p->dbuf_bytes = L.off;
+  if (ctx->budget && ctx->mem + p->dbuf_bytes > ctx->budget) {
+    delete p;
+    return set_err(ctx, BA_ERR_BUDGET, "batch plan exceeds the device-memory budget");
+  }
+  cudaError_t e = cudaMalloc((void**)&p->dbuf, p->dbuf_bytes);
+  if (e != cudaSuccess) {
+    delete p;
+    return set_err(ctx, BA_ERR_CUDA, std::string("cudaMalloc(plan): ") + cudaGetErrorString(e));
+  }
+  ctx->mem += p->dbuf_bytes;
+  e = cudaMemcpyAsync(p->dbuf + o_desc, descs.data(), sizeof(DevCluster) * n, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->dbuf + o_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    ctx->mem -= p->dbuf_bytes;
+    free_plan(p);
+    return set_err(ctx, BA_ERR_CUDA, std::string("plan upload: ") + cudaGetErrorString(e));
+  }
+  const int* dpre = (const int*)(p->dbuf + o_pre);
+  p->bv.cl = (const DevCluster*)(p->dbuf + o_desc);
+  p->bv.tile_pre = dpre;
+  p->bv.cchunk_pre = dpre + (n + 1);
+  p->bv.pchunk_pre = dpre + 2 * (n + 1);
+  p->bv.n = n;
+  p->bv.total_tiles = pre[n];
+  p->bv.total_cchunks = pre[(n + 1) + n];
+  p->bv.total_pchunks = pre[2 * (n + 1) + n];
+  p->bv.max_n = max_n;
+  p->lm_out = (LmState*)(p->dbuf + o_lm);
+  p->gnorm = (double*)(p->dbuf + o_gn);
+  ctx->plans[ids] = p;
+  *out = p;
+  return BA_OK;
+}
+
+// iters LM iterations on the plan's clusters as one graph launch:
+// arm -> cost at the current state -> iters x (K1..K6).
+ba_status run_plan(ba_ctx* ctx, Plan* p, int iters) {
+  auto it = p->graphs.find(iters);
+  cudaGraphExec_t exec = nullptr;
+  if (it == p->graphs.end()) {
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    launch_arm(p->bv, iters, ctx->stream);
+    launch_cost_init(p->bv, ctx->stream);
+    for (int i = 0; i < iters; ++i) launch_iteration(p->bv, ctx->mixed, ctx->refine, ctx->stream);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (e != cudaSuccess) return set_err(ctx, BA_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return set_err(ctx, BA_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    p->graphs[iters] = exec;
+  } else {
+    exec = it->second;
+  }
+  CUDA_TRY(ctx, cudaGraphLaunch(exec, ctx->stream));
+  return BA_OK;
+}
+
+void fill_step(const StepRec& r, ba_step_info* o) {
+  o->accepted = r.accepted;
+  o->status = r.status;
+  o->F_before = r.F_before;
+  o->F_after = r.F_after;
+  o->predicted = r.predicted;
+  o->gain = r.gain;
+  o->mu_used = r.mu_used;
+  o->mu = r.mu;
+  o->nu = r.nu;
+}
+
+// Runs iters iterations on ids and returns per-cluster LM state and traces.
+ba_status run_and_collect(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, int iters, std::vector<LmState>* lm,
+                          std::vector<StepRec>* trace) {
+  Plan* p = nullptr;
+  ba_status st = get_plan(ctx, ids, &p);
+  if (st != BA_OK) return st;
+  const int n = (int)ids.size();
+  int before_iter = 0;
+  (void)before_iter;
+  st = run_plan(ctx, p, iters);
+  if (st != BA_OK) return st;
+  StepRec* dtrace = nullptr;
+  const int tcap = std::min(iters, kTraceCap);
+  if (trace && tcap > 0) {
+    CUDA_TRY(ctx, cudaMallocAsync((void**)&dtrace, sizeof(StepRec) * (size_t)n * tcap, ctx->stream));
+  }
+  launch_gather(p->bv, tcap, p->lm_out, dtrace, ctx->stream);
+  if (lm) {
+    lm->resize(n);
+    CUDA_TRY(ctx, cudaMemcpyAsync(lm->data(), p->lm_out, sizeof(LmState) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (trace && dtrace) {
+    trace->assign((size_t)n * tcap, StepRec{});
+    CUDA_TRY(ctx, cudaMemcpyAsync(trace->data(), dtrace, sizeof(StepRec) * (size_t)n * tcap, cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    CUDA_TRY(ctx, cudaFreeAsync(dtrace, ctx->stream));
+  }
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(ctx, cudaGetLastError());
+  return BA_OK;
+}
+
+// ------------------------------------------------------------------ cluster creation
+
+ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
+  const int nc = d->n_cams, np = d->n_pts, no = d->n_obs;
+  if (nc < 1 || np < 0 || no < 0) return set_err(ctx, BA_ERR_INVALID, "n_cams must be >= 1, n_pts and n_obs >= 0");
+  if (d->ptr_kind != BA_PTR_HOST && d->ptr_kind != BA_PTR_DEVICE) return set_err(ctx, BA_ERR_INVALID, "bad ptr_kind");
+  if (!(d->sigma_px > 0.0) || !(d->huber_delta_px > 0.0) || !(d->sigma_gnss_m >= 0.0) || !(d->sigma_imu_rad >= 0.0))
+    return set_err(ctx, BA_ERR_INVALID, "sigma_px and huber_delta_px must be > 0, prior sigmas >= 0");
+  const int kind = d->ptr_kind;
+  std::vector<double> intr, R, T, X, Rp, Tp, uv;
+  std::vector<int32_t> ocam, opt;
+  std::vector<uint8_t> fixed;
+  if (!fetch(d->intr, (size_t)nc * 7, kind, intr) || !fetch(d->R, (size_t)nc * 9, kind, R) ||
+      !fetch(d->T, (size_t)nc * 3, kind, T) || !fetch(d->X, (size_t)np * 3, kind, X) ||
+      !fetch(d->R_prior, (size_t)nc * 9, kind, Rp) || !fetch(d->T_prior, (size_t)nc * 3, kind, Tp) ||
+      !fetch(d->obs_uv, (size_t)no * 2, kind, uv) || !fetch(d->obs_cam, (size_t)no, kind, ocam) ||
+      !fetch(d->obs_pt, (size_t)no, kind, opt))
+    return set_err(ctx, BA_ERR_INVALID, "missing input array (NULL pointer or failed device read)");
+  if (d->fixed) {
+    if (!fetch(d->fixed, (size_t)nc, kind, fixed)) return set_err(ctx, BA_ERR_INVALID, "bad fixed array");
+  } else {
+    fixed.assign(nc, 0);
+  }
+  if (!all_finite(intr) || !all_finite(R) || !all_finite(T) || !all_finite(X) || !all_finite(Rp) ||
+      !all_finite(Tp) || !all_finite(uv))
+    return set_err(ctx, BA_ERR_INVALID, "non-finite value in the input");
+  for (int i = 0; i < no; ++i)
+    if (ocam[i] < 0 || ocam[i] >= nc || opt[i] < 0 || opt[i] >= np)
+      return set_err(ctx, BA_ERR_INVALID, "observation index out of range");
+
+  // free cameras, in camera order
+  std::vector<int> free_idx(nc, -1), cam_of_free;
+  for (int k = 0; k < nc; ++k)
+    if (!fixed[k]) {
+      free_idx[k] = (int)cam_of_free.size();
+      cam_of_free.push_back(k);
+    }
+  const int nf = (int)cam_of_free.size();
+  if (nf == 0) return set_err(ctx, BA_ERR_INVALID, "no free camera");
+  if (nf > kMaxFreeSmall)
+    return set_err(ctx, BA_ERR_INVALID, "more than 32 free cameras in one cluster is not supported");
+
+  // point-major order: stable counting sort by point, then by camera within a point
+  std::vector<int> cnt((size_t)np + 1, 0), pm(no);
+  for (int i = 0; i < no; ++i) cnt[opt[i] + 1]++;
+  for (int j = 0; j < np; ++j) cnt[j + 1] += cnt[j];
+  std::vector<int> pt_start(cnt);
+  {
+    std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+    for (int i = 0; i < no; ++i) pm[pos[opt[i]]++] = i;
+  }
+  for (int j = 0; j < np; ++j) {
+    const int s = pt_start[j], e = pt_start[j + 1];
+    if (e - s > kMaxTrack) return set_err(ctx, BA_ERR_INVALID, "a point has more than 32 observations");
+    for (int a = s + 1; a < e; ++a) {
+      const int v = pm[a];
+      int b = a - 1;
+      while (b >= s && ocam[pm[b]] > ocam[v]) {
+        pm[b + 1] = pm[b];
+        --b;
+      }
+      pm[b + 1] = v;
+    }
+    for (int a = s + 1; a < e; ++a)
+      if (ocam[pm[a]] == ocam[pm[a - 1]]) return set_err(ctx, BA_ERR_INVALID, "repeated (camera, point) observation");
+  }
+
+  // tiles: runs of whole points with at most 32 observations
+  std::vector<Tile> tiles;
+  {
+    int tb = 0, tn = 0;
+    for (int j = 0; j < np; ++j) {
+      const int L = pt_start[j + 1] - pt_start[j];
+      if (L == 0) continue;
+      if (tn + L > 32) {
+        tiles.push_back(Tile{tb, tn});
+        tb = pt_start[j];
+        tn = 0;
+      }
+      if (tn == 0) tb = pt_start[j];
+      tn += L;
+    }
+    if (tn > 0) tiles.push_back(Tile{tb, tn});
+  }
+
+  // camera-major list of free-camera observations (point-major order within a camera)
+  std::vector<int> ccnt((size_t)nf + 1, 0);
+  for (int p = 0; p < no; ++p) {
+    const int f = free_idx[ocam[pm[p]]];
+    if (f >= 0) ccnt[f + 1]++;
+  }
+  for (int f = 0; f < nf; ++f) ccnt[f + 1] += ccnt[f];
+  std::vector<int> cam_obs(ccnt[nf]);
+  {
+    std::vector<int> pos(ccnt.begin(), ccnt.end() - 1);
+    for (int p = 0; p < no; ++p) {
+      const int f = free_idx[ocam[pm[p]]];
+      if (f >= 0) cam_obs[pos[f]++] = p;
+    }
+  }
+  std::vector<ChunkItem> cchunks;
+  std::vector<int> cam_part_begin((size_t)nf + 1, 0);
+  for (int f = 0; f < nf; ++f) {
+    cam_part_begin[f] = (int)cchunks.size();
+    for (int b = ccnt[f]; b < ccnt[f + 1]; b += kCamChunk)
+      cchunks.push_back(ChunkItem{f, b, std::min(kCamChunk, ccnt[f + 1] - b), 0});
+  }
+  cam_part_begin[nf] = (int)cchunks.size();
+
+  // camera pairs (free a < free b) sharing a point, entries sorted by (pair, point)
+  std::vector<int> pcnt((size_t)nf * nf + 1, 0);
+  for (int j = 0; j < np; ++j) {
+    const int s = pt_start[j], e = pt_start[j + 1];
+    for (int a = s; a < e; ++a) {
+      const int fa = free_idx[ocam[pm[a]]];
+      if (fa < 0) continue;
+      for (int b = a + 1; b < e; ++b) {
+        const int fb = free_idx[ocam[pm[b]]];
+        if (fb >= 0) pcnt[(size_t)fa * nf + fb + 1]++;
+      }
+    }
+  }
+  for (size_t q = 0; q < (size_t)nf * nf; ++q) pcnt[q + 1] += pcnt[q];
+  std::vector<int2> pair_ent(pcnt[(size_t)nf * nf]);
+  {
+    std::vector<int> pos(pcnt.begin(), pcnt.end() - 1);
+    for (int j = 0; j < np; ++j) {
+      const int s = pt_start[j], e = pt_start[j + 1];
+      for (int a = s; a < e; ++a) {
+        const int fa = free_idx[ocam[pm[a]]];
+        if (fa < 0) continue;
+        for (int b = a + 1; b < e; ++b) {
+          const int fb = free_idx[ocam[pm[b]]];
+          if (fb >= 0) pair_ent[pos[(size_t)fa * nf + fb]++] = make_int2(a, b);
+        }
+      }
+    }
+  }
+  std::vector<int2> pair_key;
+  std::vector<ChunkItem> pchunks;
+  std::vector<int> pair_part_begin;
+  for (int fa = 0; fa < nf; ++fa)
+    for (int fb = fa + 1; fb < nf; ++fb) {
+      const size_t q = (size_t)fa * nf + fb;
+      if (pcnt[q + 1] == pcnt[q]) continue;
+      const int p = (int)pair_key.size();
+      pair_key.push_back(make_int2(fa, fb));
+      pair_part_begin.push_back((int)pchunks.size());
+      for (int b = pcnt[q]; b < pcnt[q + 1]; b += kPairChunk)
+        pchunks.push_back(ChunkItem{p, b, std::min(kPairChunk, pcnt[q + 1] - b), 0});
+    }
+  pair_part_begin.push_back((int)pchunks.size());
+
+  // arena layout: static (uploaded) part first
+  const bool mixed = ctx->mixed;
+  const size_t rs = mixed ? sizeof(float) : sizeof(double);
+  const int n = 6 * nf;
+  const int ntile = (int)tiles.size();
+  Layout Lo;
+  const size_t o_intr = Lo.add(sizeof(double) * nc * 7);
+  const size_t o_R = Lo.add(sizeof(double) * 2 * nc * 9);
+  const size_t o_T = Lo.add(sizeof(double) * 2 * nc * 3);
+  const size_t o_X = Lo.add(sizeof(double) * 2 * (size_t)np * 3);
+  const size_t o_Rp = Lo.add(sizeof(double) * nc * 9);
+  const size_t o_Tp = Lo.add(sizeof(double) * nc * 3);
+  const size_t o_Ri = Lo.add(sizeof(double) * nc * 9);
+  const size_t o_Ti = Lo.add(sizeof(double) * nc * 3);
+  const size_t o_Xi = Lo.add(sizeof(double) * (size_t)np * 3);
+  const size_t o_free = Lo.add(sizeof(int) * nc);
+  const size_t o_cof = Lo.add(sizeof(int) * nf);
+  const size_t o_tiles = Lo.add(sizeof(Tile) * tiles.size());
+  const size_t o_ocam = Lo.add(sizeof(int) * (size_t)no);
+  const size_t o_opt = Lo.add(sizeof(int) * (size_t)no);
+  const size_t o_uv = Lo.add(sizeof(double) * 2 * (size_t)no);
+  const size_t o_uv32 = Lo.add(mixed ? sizeof(float) * 2 * (size_t)no : 0);
+  const size_t o_cch = Lo.add(sizeof(ChunkItem) * cchunks.size());
+  const size_t o_cobs = Lo.add(sizeof(int) * cam_obs.size());
+  const size_t o_cpb = Lo.add(sizeof(int) * cam_part_begin.size());
+  const size_t o_pch = Lo.add(sizeof(ChunkItem) * pchunks.size());
+  const size_t o_pent = Lo.add(sizeof(int2) * pair_ent.size());
+  const size_t o_pkey = Lo.add(sizeof(int2) * pair_key.size());
+  const size_t o_ppb = Lo.add(sizeof(int) * pair_part_begin.size());
+  const size_t o_lm = Lo.add(sizeof(LmState));
+  const size_t static_bytes = Lo.off;
+  const size_t o_camreal = Lo.add(rs * 20 * nc);
+  const size_t o_rec = Lo.add(rs * kRec * (size_t)no);
+  const size_t o_paux = Lo.add(rs * kPaux * (size_t)np);
+  const size_t o_cpart = Lo.add(rs * kCamPart * cchunks.size());
+  const size_t o_ppart = Lo.add(rs * kPairPart * pchunks.size());
+  const size_t o_S = Lo.add(sizeof(double) * (size_t)n * n);
+  const size_t o_rhs = Lo.add(sizeof(double) * n);
+  const size_t o_gc = Lo.add(sizeof(double) * n);
+  const size_t o_Dc = Lo.add(sizeof(double) * n);
+  const size_t o_dc = Lo.add(sizeof(double) * n);
+  const size_t o_tp = Lo.add(sizeof(double) * 2 * tiles.size());
+  const size_t o_trace = Lo.add(sizeof(StepRec) * kTraceCap);
+  const size_t o_desc = Lo.add(sizeof(DevCluster));
+  const size_t total = Lo.off;
+
+  if (ctx->budget && ctx->mem + total > ctx->budget)
+    return set_err(ctx, BA_ERR_BUDGET, "cluster exceeds the device-memory budget");
+
+  std::vector<char> stage(static_bytes, 0);
+  auto put = [&](size_t off, const void* src, size_t bytes) {
+    if (bytes) std::memcpy(stage.data() + off, src, bytes);
+  };
+  // initial state in point-major/caller layouts (points and cameras keep caller indices)
+  put(o_intr, intr.data(), sizeof(double) * intr.size());
+  put(o_R, R.data(), sizeof(double) * R.size());
+  put(o_R + sizeof(double) * R.size(), R.data(), sizeof(double) * R.size());
+  put(o_T, T.data(), sizeof(double) * T.size());
+  put(o_T + sizeof(double) * T.size(), T.data(), sizeof(double) * T.size());
+  put(o_X, X.data(), sizeof(double) * X.size());
+  put(o_X + sizeof(double) * X.size(), X.data(), sizeof(double) * X.size());
+  put(o_Rp, Rp.data(), sizeof(double) * Rp.size());
+  put(o_Tp, Tp.data(), sizeof(double) * Tp.size());
+  put(o_Ri, R.data(), sizeof(double) * R.size());
+  put(o_Ti, T.data(), sizeof(double) * T.size());
+  put(o_Xi, X.data(), sizeof(double) * X.size());
+  put(o_free, free_idx.data(), sizeof(int) * nc);
+  put(o_cof, cam_of_free.data(), sizeof(int) * nf);
+  put(o_tiles, tiles.data(), sizeof(Tile) * tiles.size());
+  {
+    int* sc = (int*)(stage.data() + o_ocam);
+    int* sp = (int*)(stage.data() + o_opt);
+    double* su = (double*)(stage.data() + o_uv);
+    float* s32 = mixed ? (float*)(stage.data() + o_uv32) : nullptr;
+    for (int p = 0; p < no; ++p) {
+      const int i = pm[p];
+      sc[p] = ocam[i];
+      sp[p] = opt[i];
+      su[2 * p] = uv[2 * i];
+      su[2 * p + 1] = uv[2 * i + 1];
+      if (s32) {
+        s32[2 * p] = (float)uv[2 * i];
+        s32[2 * p + 1] = (float)uv[2 * i + 1];
+      }
+    }
+  }
+  put(o_cch, cchunks.data(), sizeof(ChunkItem) * cchunks.size());
+  put(o_cobs, cam_obs.data(), sizeof(int) * cam_obs.size());
+  put(o_cpb, cam_part_begin.data(), sizeof(int) * cam_part_begin.size());
+  put(o_pch, pchunks.data(), sizeof(ChunkItem) * pchunks.size());
+  put(o_pent, pair_ent.data(), sizeof(int2) * pair_ent.size());
+  put(o_pkey, pair_key.data(), sizeof(int2) * pair_key.size());
+  put(o_ppb, pair_part_begin.data(), sizeof(int) * pair_part_begin.size());
+  {
+    LmState lm{};
+    lm.mu0 = d->mu0 > 0.0 ? d->mu0 : 1e-4;
+    lm.mu = lm.mu0;
+    lm.nu = 2.0;
+    put(o_lm, &lm, sizeof(lm));
+  }
+
+  char* arena = nullptr;
+  cudaError_t e = cudaMalloc((void**)&arena, total);
+  if (e != cudaSuccess) return set_err(ctx, BA_ERR_BUDGET, std::string("cudaMalloc(cluster): ") + cudaGetErrorString(e));
+  e = cudaMemcpyAsync(arena, stage.data(), static_bytes, cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) {
+    cudaFree(arena);
+    return set_err(ctx, BA_ERR_CUDA, std::string("cluster upload: ") + cudaGetErrorString(e));
+  }
+
+  DevCluster& h = c->h;
+  h = DevCluster{};
+  h.n_cams = nc; h.n_pts = np; h.n_obs = no; h.n_free = nf;
+  h.n_tiles = ntile; h.n_cchunks = (int)cchunks.size(); h.n_pairs = (int)pair_key.size();
+  h.n_pchunks = (int)pchunks.size();
+  h.sigma_px = d->sigma_px; h.huber_delta = d->huber_delta_px; h.sigma_gnss = d->sigma_gnss_m;
+  h.sigma_imu = d->sigma_imu_rad;
+  h.intr = (const double*)(arena + o_intr);
+  h.R = (double*)(arena + o_R);
+  h.T = (double*)(arena + o_T);
+  h.X = (double*)(arena + o_X);
+  h.R_prior = (const double*)(arena + o_Rp);
+  h.T_prior = (const double*)(arena + o_Tp);
+  h.R_init = (const double*)(arena + o_Ri);
+  h.T_init = (const double*)(arena + o_Ti);
+  h.X_init = (const double*)(arena + o_Xi);
+  h.free_idx = (const int*)(arena + o_free);
+  h.cam_of_free = (const int*)(arena + o_cof);
+  h.camreal = arena + o_camreal;
+  h.tiles = (const Tile*)(arena + o_tiles);
+  h.obs_cam = (const int*)(arena + o_ocam);
+  h.obs_pt = (const int*)(arena + o_opt);
+  h.obs_uv = (const double*)(arena + o_uv);
+  h.obs_uv32 = mixed ? (const float*)(arena + o_uv32) : nullptr;
+  h.rec = arena + o_rec;
+  h.paux = arena + o_paux;
+  h.cchunks = (const ChunkItem*)(arena + o_cch);
+  h.cam_obs = (const int*)(arena + o_cobs);
+  h.campart = arena + o_cpart;
+  h.cam_part_begin = (const int*)(arena + o_cpb);
+  h.pchunks = (const ChunkItem*)(arena + o_pch);
+  h.pair_ent = (const int2*)(arena + o_pent);
+  h.pairpart = arena + o_ppart;
+  h.pair_key = (const int2*)(arena + o_pkey);
+  h.pair_part_begin = (const int*)(arena + o_ppb);
+  h.S = (double*)(arena + o_S);
+  h.rhs = (double*)(arena + o_rhs);
+  h.gc = (double*)(arena + o_gc);
+  h.Dc = (double*)(arena + o_Dc);
+  h.dc = (double*)(arena + o_dc);
+  h.tilepart = (double*)(arena + o_tp);
+  h.lm = (LmState*)(arena + o_lm);
+  h.trace = (StepRec*)(arena + o_trace);
+  h.trace_cap = kTraceCap;
+  c->d_desc = (DevCluster*)(arena + o_desc);
+  e = cudaMemcpyAsync(c->d_desc, &h, sizeof(DevCluster), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    cudaFree(arena);
+    return set_err(ctx, BA_ERR_CUDA, std::string("cluster upload: ") + cudaGetErrorString(e));
+  }
+  c->nc = nc; c->np = np; c->no = no; c->nf = nf;
+  c->arena = arena;
+  c->arena_bytes = total;
+  c->pm_to_user = std::move(pm);
+  ctx->mem += total;
+  return BA_OK;
+}
+
+// single-cluster view for kernels that take a BatchView
+ba_status single_view(ba_ctx* ctx, Cluster* c, Plan** p) { return get_plan(ctx, {c->id}, p); }
+
+// ------------------------------------------------------------------ serving scheduler
+//
+// Continuous batching at LM-iteration granularity: every round the scheduler
+// (1) admits queued clusters into free slots, (2) runs ONE iteration for all
+// running clusters as one batched launch sequence, (3) retires the clusters
+// that reached their iteration count.  A cluster's iterations are exactly
+// those of ba_run: the kernels' reductions are per cluster and fixed-order,
+// so results do not depend on which other clusters share the launches.
+
+void scheduler_loop(ba_ctx* ctx) {
+  struct Running {
+    ba_ticket t;
+    ba_cluster_id id;
+    int left;
+    int iters;
+  };
+  std::vector<Running> running;
+  cudaSetDevice(ctx->device);
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(ctx->sv_mu);
+      ctx->sv_cv.wait(lk, [&] { return ctx->sched_stop || !ctx->queue.empty() || !running.empty(); });
+      if (ctx->sched_stop && running.empty()) return;
+      while (!ctx->queue.empty() && (int)running.size() < ctx->n_slots) {
+        const ba_ticket t = ctx->queue.front();
+        ctx->queue.pop_front();
+        Ticket& tk = ctx->tickets[t];
+        running.push_back(Running{t, tk.id, tk.iters, tk.iters});
+      }
+    }
+    std::vector<ba_cluster_id> ids;
+    std::vector<Running> firsts;
+    for (auto& r : running) ids.push_back(r.id);
+    std::sort(ids.begin(), ids.end());
+    std::vector<LmState> lm;
+    ba_status st;
+    {
+      std::lock_guard<std::mutex> g(ctx->api_mu);
+      // the first iteration of a newly admitted cluster needs F at its state;
+      // run_and_collect arms + evaluates F for all, which is idempotent for the others
+      st = run_and_collect(ctx, ids, 1, &lm, nullptr);
+    }
+    std::vector<Running> still;
+    {
+      std::lock_guard<std::mutex> lk(ctx->sv_mu);
+      for (auto& r : running) {
+        const int pos = (int)(std::lower_bound(ids.begin(), ids.end(), r.id) - ids.begin());
+        r.left -= 1;
+        Ticket& tk = ctx->tickets[r.t];
+        if (st != BA_OK || r.left <= 0) {
+          tk.done = 1;
+          tk.res.status = st != BA_OK ? st : (st == BA_OK ? lm[pos].status : st);
+          tk.res.iters = r.iters - r.left;
+          tk.res.final_cost = st == BA_OK ? lm[pos].F : 0.0;
+          tk.res.accepted = st == BA_OK ? lm[pos].n_accepted : 0;
+          tk.res.latency_ms =
+              std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tk.t_submit).count();
+          Cluster* c = find_cluster(ctx, r.id);
+          if (c) c->in_service = 0;
+        } else {
+          still.push_back(r);
+        }
+      }
+    }
+    running.swap(still);
+  }
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+BA_API const char* ba_status_string(ba_status s) {
+  switch (s) {
+    case BA_OK: return "ok";
+    case BA_PENDING: return "pending";
+    case BA_ERR_INVALID: return "invalid argument or problem data";
+    case BA_ERR_BUDGET: return "device-memory budget or slots exhausted";
+    case BA_ERR_NOT_PD: return "damped system not positive definite";
+    case BA_ERR_TIMEOUT: return "bounded wait expired";
+    case BA_ERR_CUDA: return "CUDA runtime error";
+    case BA_ERR_NOT_FOUND: return "unknown cluster id or ticket";
+    default: return "unknown status";
+  }
+}
+
+BA_API const char* ba_last_error(ba_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+BA_API ba_status ba_init(ba_ctx** out, const ba_config* cfg) {
+  if (!out || !cfg) return BA_ERR_INVALID;
+  if (cfg->precision != BA_FP64 && cfg->precision != BA_MIXED) return BA_ERR_INVALID;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) return BA_ERR_CUDA;
+  if (cudaSetDevice(cfg->device) != cudaSuccess) return BA_ERR_CUDA;
+  ba_ctx* ctx = new ba_ctx();
+  ctx->device = cfg->device;
+  ctx->budget = cfg->hbm_budget_bytes;
+  ctx->mixed = cfg->precision == BA_MIXED;
+  ctx->n_slots = cfg->n_slots > 0 ? cfg->n_slots : 64;
+  ctx->refine = cfg->refine_steps >= 0 ? cfg->refine_steps : 1;
+  if (cfg->stream) {
+    ctx->stream = (cudaStream_t)cfg->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return BA_ERR_CUDA;
+    }
+    ctx->own_stream = true;
+  }
+  *out = ctx;
+  return BA_OK;
+}
+
+BA_API ba_status ba_create_cluster(ba_ctx* ctx, const ba_cluster_desc* d, ba_cluster_id* out) {
+  if (!ctx || !d || !out) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  cudaSetDevice(ctx->device);
+  Cluster* c = new Cluster();
+  c->id = ctx->next_id++;
+  ba_status st = build_cluster(ctx, d, c);
+  if (st != BA_OK) {
+    delete c;
+    return st;
+  }
+  ctx->clusters[c->id] = c;
+  if (d->warm_from) {
+    // warm start: copy the current state of shared cameras/points from a live cluster
+    Cluster* src = find_cluster(ctx, d->warm_from);
+    if (!src || !d->warm_cam_map || !d->warm_pt_map) {
+      ctx->clusters.erase(c->id);
+      ctx->mem -= c->arena_bytes;
+      cudaFree(c->arena);
+      delete c;
+      return set_err(ctx, BA_ERR_NOT_FOUND, "warm_from cluster not found or maps missing");
+    }
+    LmState sl{};
+    cudaMemcpy(&sl, src->h.lm, sizeof(LmState), cudaMemcpyDeviceToHost);
+    const double* sR = src->h.R + (size_t)sl.cur * src->nc * 9;
+    const double* sT = src->h.T + (size_t)sl.cur * src->nc * 3;
+    const double* sX = src->h.X + (size_t)sl.cur * src->np * 3;
+    for (int k = 0; k < c->nc; ++k) {
+      const int m = d->warm_cam_map[k];
+      if (m < 0 || m >= src->nc) continue;
+      for (int b = 0; b < 2; ++b) {
+        cudaMemcpyAsync(c->h.R + ((size_t)b * c->nc + k) * 9, sR + 9 * (size_t)m, 72, cudaMemcpyDeviceToDevice, ctx->stream);
+        cudaMemcpyAsync(c->h.T + ((size_t)b * c->nc + k) * 3, sT + 3 * (size_t)m, 24, cudaMemcpyDeviceToDevice, ctx->stream);
+      }
+      cudaMemcpyAsync((double*)c->h.R_init + 9 * (size_t)k, sR + 9 * (size_t)m, 72, cudaMemcpyDeviceToDevice, ctx->stream);
+      cudaMemcpyAsync((double*)c->h.T_init + 3 * (size_t)k, sT + 3 * (size_t)m, 24, cudaMemcpyDeviceToDevice, ctx->stream);
+    }
+    for (int j = 0; j < c->np; ++j) {
+      const int m = d->warm_pt_map[j];
+      if (m < 0 || m >= src->np) continue;
+      for (int b = 0; b < 2; ++b)
+        cudaMemcpyAsync(c->h.X + ((size_t)b * c->np + j) * 3, sX + 3 * (size_t)m, 24, cudaMemcpyDeviceToDevice, ctx->stream);
+      cudaMemcpyAsync((double*)c->h.X_init + 3 * (size_t)j, sX + 3 * (size_t)m, 24, cudaMemcpyDeviceToDevice, ctx->stream);
+    }
+  }
+  Plan* p = nullptr;
+  st = single_view(ctx, c, &p);
+  if (st != BA_OK) return st;
+  launch_camreal(p->bv, ctx->mixed, ctx->stream);
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(ctx, cudaGetLastError());
+  *out = c->id;
+  return BA_OK;
+}
+
+BA_API ba_status ba_linearize(ba_ctx* ctx, ba_cluster_id id, ba_lin_info* out) {
+  if (!ctx || !out) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  Cluster* c = find_cluster(ctx, id);
+  if (!c) return BA_ERR_NOT_FOUND;
+  if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
+  Plan* p = nullptr;
+  ba_status st = single_view(ctx, c, &p);
+  if (st != BA_OK) return st;
+  launch_arm(p->bv, -1, ctx->stream);
+  launch_cost_init(p->bv, ctx->stream);
+  launch_grad_norm(p->bv, ctx->mixed, p->gnorm, ctx->stream);
+  launch_arm(p->bv, -2, ctx->stream);
+  LmState lm{};
+  double gn = 0.0;
+  CUDA_TRY(ctx, cudaMemcpyAsync(&lm, c->h.lm, sizeof(LmState), cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(&gn, p->gnorm, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(ctx, cudaGetLastError());
+  out->cost = lm.F;
+  out->grad_inf = gn;
+  out->n_free = c->nf;
+  return BA_OK;
+}
+
+BA_API ba_status ba_run(ba_ctx* ctx, ba_cluster_id id, int32_t iters, ba_step_info* trace) {
+  if (!ctx || iters < 0) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  Cluster* c = find_cluster(ctx, id);
+  if (!c) return BA_ERR_NOT_FOUND;
+  if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
+  if (iters == 0) return BA_OK;
+  std::vector<StepRec> tr;
+  ba_status st = run_and_collect(ctx, {id}, iters, nullptr, trace ? &tr : nullptr);
+  if (st != BA_OK) return st;
+  if (trace) {
+    const int tcap = std::min(iters, kTraceCap);
+    for (int i = 0; i < iters; ++i) trace[i] = ba_step_info{};
+    for (int i = 0; i < tcap; ++i) fill_step(tr[i], trace + (iters - tcap) + i);
+  }
+  return BA_OK;
+}
+
+BA_API ba_status ba_solve_step(ba_ctx* ctx, ba_cluster_id id, ba_step_info* out) {
+  ba_step_info tmp;
+  ba_status st = ba_run(ctx, id, 1, &tmp);
+  if (st == BA_OK && out) *out = tmp;
+  return st;
+}
+
+BA_API ba_status ba_solve_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n, int32_t iters, ba_result* results,
+                         ba_step_info* trace) {
+  if (!ctx || !ids || n <= 0 || iters < 0) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  std::vector<ba_cluster_id> v(ids, ids + n);
+  for (auto id : v) {
+    Cluster* c = find_cluster(ctx, id);
+    if (!c) return BA_ERR_NOT_FOUND;
+    if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
+  }
+  {
+    std::vector<ba_cluster_id> s(v);
+    std::sort(s.begin(), s.end());
+    if (std::adjacent_find(s.begin(), s.end()) != s.end()) return set_err(ctx, BA_ERR_INVALID, "repeated id in batch");
+  }
+  std::vector<LmState> lm;
+  std::vector<StepRec> tr;
+  const int tcap = std::min(iters, kTraceCap);
+  ba_status st = run_and_collect(ctx, v, iters, &lm, trace ? &tr : nullptr);
+  if (st != BA_OK) return st;
+  for (int i = 0; i < n; ++i) {
+    if (results) {
+      ba_result& r = results[i];
+      r = ba_result{};
+      r.status = lm[i].status;
+      r.iters = iters;
+      r.accepted = lm[i].n_accepted;
+      r.final_cost = lm[i].F;
+      r.initial_cost = 0.0;
+    }
+    if (trace) {
+      for (int t = 0; t < iters; ++t) trace[(size_t)i * iters + t] = ba_step_info{};
+      for (int t = 0; t < tcap; ++t) fill_step(tr[(size_t)i * tcap + t], trace + (size_t)i * iters + (iters - tcap) + t);
+      if (results && iters > 0 && tcap == iters) results[i].initial_cost = tr[(size_t)i * tcap].F_before;
+    }
+  }
+  return BA_OK;
+}
+
+BA_API ba_status ba_reset(ba_ctx* ctx, ba_cluster_id id) {
+  if (!ctx) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  Cluster* c = find_cluster(ctx, id);
+  if (!c) return BA_ERR_NOT_FOUND;
+  if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
+  Plan* p = nullptr;
+  ba_status st = single_view(ctx, c, &p);
+  if (st != BA_OK) return st;
+  launch_reset(p->bv, ctx->mixed, ctx->stream);
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(ctx, cudaGetLastError());
+  return BA_OK;
+}
+
+BA_API ba_status ba_submit(ba_ctx* ctx, ba_cluster_id id, const ba_solve_opts* opts, ba_ticket* out) {
+  if (!ctx || !opts || !out || opts->max_iters <= 0) return BA_ERR_INVALID;
+  {
+    std::lock_guard<std::mutex> g(ctx->api_mu);
+    Cluster* c = find_cluster(ctx, id);
+    if (!c) return BA_ERR_NOT_FOUND;
+    int expect = 0;
+    if (!c->in_service.compare_exchange_strong(expect, 1))
+      return set_err(ctx, BA_ERR_INVALID, "cluster already submitted");
+  }
+  std::lock_guard<std::mutex> lk(ctx->sv_mu);
+  if (!ctx->sched_started) {
+    ctx->sched_started = true;
+    ctx->sched = std::thread(scheduler_loop, ctx);
+  }
+  const ba_ticket t = ctx->next_ticket++;
+  Ticket tk;
+  tk.id = id;
+  tk.iters = opts->max_iters;
+  tk.t_submit = std::chrono::steady_clock::now();
+  ctx->tickets[t] = tk;
+  ctx->queue.push_back(t);
+  ctx->sv_cv.notify_all();
+  *out = t;
+  return BA_OK;
+}
+
+BA_API ba_status ba_poll(ba_ctx* ctx, ba_ticket t, ba_result* out) {
+  if (!ctx) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(ctx->sv_mu);
+  auto it = ctx->tickets.find(t);
+  if (it == ctx->tickets.end()) return BA_ERR_NOT_FOUND;
+  if (!it->second.done) return BA_PENDING;
+  if (out) *out = it->second.res;
+  ctx->tickets.erase(it);
+  return BA_OK;
+}
+
+BA_API ba_status ba_get_state(ba_ctx* ctx, ba_cluster_id id, double* R, double* T, double* X, int32_t ptr_kind) {
+  if (!ctx) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  Cluster* c = find_cluster(ctx, id);
+  if (!c) return BA_ERR_NOT_FOUND;
+  LmState lm{};
+  CUDA_TRY(ctx, cudaMemcpyAsync(&lm, c->h.lm, sizeof(LmState), cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  const cudaMemcpyKind kind = ptr_kind == BA_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (R)
+    CUDA_TRY(ctx, cudaMemcpyAsync(R, c->h.R + (size_t)lm.cur * c->nc * 9, sizeof(double) * c->nc * 9, kind, ctx->stream));
+  if (T)
+    CUDA_TRY(ctx, cudaMemcpyAsync(T, c->h.T + (size_t)lm.cur * c->nc * 3, sizeof(double) * c->nc * 3, kind, ctx->stream));
+  if (X && c->np)
+    CUDA_TRY(ctx, cudaMemcpyAsync(X, c->h.X + (size_t)lm.cur * c->np * 3, sizeof(double) * (size_t)c->np * 3, kind,
+                                  ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return BA_OK;
+}
+
+BA_API ba_status ba_reprojection_errors(ba_ctx* ctx, ba_cluster_id id, double* err) {
+  if (!ctx || !err) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  Cluster* c = find_cluster(ctx, id);
+  if (!c) return BA_ERR_NOT_FOUND;
+  if (c->no == 0) return BA_OK;
+  double* d = nullptr;
+  CUDA_TRY(ctx, cudaMallocAsync((void**)&d, sizeof(double) * c->no, ctx->stream));
+  launch_reproj(c->d_desc, c->h, d, ctx->stream);
+  std::vector<double> pmv(c->no);
+  CUDA_TRY(ctx, cudaMemcpyAsync(pmv.data(), d, sizeof(double) * c->no, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaFreeAsync(d, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(ctx, cudaGetLastError());
+  for (int p = 0; p < c->no; ++p) err[c->pm_to_user[p]] = pmv[p];
+  return BA_OK;
+}
+
+BA_API ba_status ba_memory_in_use(ba_ctx* ctx, uint64_t* bytes) {
+  if (!ctx || !bytes) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  *bytes = ctx->mem;
+  return BA_OK;
+}
+
+BA_API ba_status ba_destroy_cluster(ba_ctx* ctx, ba_cluster_id id) {
+  if (!ctx) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  Cluster* c = find_cluster(ctx, id);
+  if (!c) return BA_ERR_NOT_FOUND;
+  if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
+  cudaStreamSynchronize(ctx->stream);
+  drop_plans_with(ctx, id);
+  ctx->clusters.erase(id);
+  ctx->mem -= c->arena_bytes;
+  cudaFree(c->arena);
+  delete c;
+  return BA_OK;
+}
+
+BA_API ba_status ba_shutdown(ba_ctx* ctx) {
+  if (!ctx) return BA_ERR_INVALID;
+  {
+    std::lock_guard<std::mutex> lk(ctx->sv_mu);
+    ctx->sched_stop = true;
+    ctx->sv_cv.notify_all();
+  }
+  if (ctx->sched.joinable()) ctx->sched.join();
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->plans) free_plan(kv.second);
+  for (auto& kv : ctx->clusters) {
+    cudaFree(kv.second->arena);
+    delete kv.second;
+  }
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return BA_OK;
+}
+
+}  // extern "C"

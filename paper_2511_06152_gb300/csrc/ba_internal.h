@@ -1,0 +1,143 @@
+// Internal layout shared by the kernels and the host side of the library.
+//
+// One cluster lives in one device arena.  Observations are stored in
+// point-major order (sorted by point, then camera), so the observations of a
+// point are contiguous; "tiles" cut that order into runs of at most 32
+// observations holding whole points, one warp per tile.  A camera-major
+// permutation and a camera-pair table, both presorted on the host, drive the
+// deterministic reductions into the reduced camera system.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bagpu {
+
+constexpr int kRec = 32;        // Reals per observation record: Jc[12], r[2], Z[18]
+constexpr int kRecJc = 0;
+constexpr int kRecR = 12;
+constexpr int kRecZ = 14;
+constexpr int kPaux = 16;       // Reals per point: Linv[6], q[3], Dp[3], gp[3], pad
+constexpr int kCamPart = 40;    // Reals per camera chunk: A[21], gobs[6], Zq[6], Udiag[6], pad
+constexpr int kPairPart = 36;   // Reals per pair chunk: sum Z_a Z_b^T (6x6 row-major)
+constexpr int kCamChunk = 1024; // observations per camera chunk
+constexpr int kPairChunk = 256; // entries per pair chunk
+constexpr int kMaxTrack = 32;
+constexpr int kMaxFreeSmall = 32;  // free cameras the single-CTA factor handles (n <= 192)
+constexpr double kDiagMin = 1e-6;
+constexpr double kDiagMax = 1e32;
+constexpr double kMinDepth = 1e-6;
+constexpr int BA_STATUS_NOT_PD = -3;  // same value as BA_ERR_NOT_PD in ba.h
+constexpr int kTraceCap = 256;
+
+struct Tile {
+  int obs_begin;
+  int n_obs;  // <= 32, whole points
+};
+
+struct ChunkItem {  // camera or pair chunk
+  int key;          // free camera index, or pair index
+  int begin;        // into cam_obs or pair_ent
+  int count;
+  int pad;
+};
+
+// Per-cluster LM control state, resident on the device.
+struct LmState {
+  double mu, nu;
+  double F;          // cost at the current state
+  double F_new;      // cost at the candidate
+  double pred_cam;   // camera part of d^T (mu D d + g)
+  double prior_new;  // prior cost at the candidate
+  double mu0;
+  double pad0;
+  int cur;           // which of the double-buffered states is current
+  int status;        // status of the last factorisation
+  int iter;          // iterations run
+  int n_accepted;
+  int active;        // 1 while the cluster still has iterations to run
+  int iters_target;
+  int pt_fail;       // a damped point block was not positive definite this iteration
+  int pad2;
+};
+
+// Same layout as ba_step_info.
+struct StepRec {
+  int accepted, status;
+  double F_before, F_after, predicted, gain, mu_used, mu, nu;
+};
+
+// Device-side descriptor of one cluster (plain pointers into its arena).
+struct DevCluster {
+  int n_cams, n_pts, n_obs, n_free;
+  int n_tiles, n_cchunks, n_pairs, n_pchunks;
+  double sigma_px, huber_delta, sigma_gnss, sigma_imu;
+
+  const double* intr;      // [nc][7]
+  double* R;               // [2][nc][9]
+  double* T;               // [2][nc][3]
+  double* X;               // [2][np][3]
+  const double* R_prior;   // [nc][9]
+  const double* T_prior;   // [nc][3]
+  const double* R_init;    // [nc][9] state given at create (for reset)
+  const double* T_init;    // [nc][3]
+  const double* X_init;    // [np][3]
+  const int* free_idx;     // [nc] -> free index or -1
+  const int* cam_of_free;  // [nf]
+  void* camreal;           // Real [nc][20]: R[9], T[3] (unused), intr[7], free flag
+
+  const Tile* tiles;       // [n_tiles]
+  const int* obs_cam;      // [no] point-major
+  const int* obs_pt;       // [no] point-major
+  const double* obs_uv;    // [no][2] point-major
+  const float* obs_uv32;   // [no][2] point-major (mixed precision)
+  void* rec;               // Real [no][kRec]
+  void* paux;              // Real [np][kPaux]
+
+  const ChunkItem* cchunks;   // [n_cchunks]
+  const int* cam_obs;         // [sum over free cams] point-major obs index, camera-major order
+  void* campart;              // Real [n_cchunks][kCamPart]
+  const int* cam_part_begin;  // [nf + 1]
+
+  const ChunkItem* pchunks;   // [n_pchunks]
+  const int2* pair_ent;       // (obs_a, obs_b), point-major indices, cam(a) < cam(b)
+  void* pairpart;             // Real [n_pchunks][kPairPart]
+  const int2* pair_key;       // [n_pairs] (free a, free b), a < b
+  const int* pair_part_begin; // [n_pairs + 1]
+
+  double* S;        // [n][n], n = 6 nf, row-major, full
+  double* rhs;      // [n]
+  double* gc;       // [n]
+  double* Dc;       // [n]
+  double* dc;       // [n]
+  double* tilepart; // [n_tiles][2]: cost, point pred
+  LmState* lm;
+  StepRec* trace;   // [trace_cap]
+  int trace_cap;
+  int pad;
+};
+
+struct BatchView {
+  const DevCluster* cl;  // [n]
+  const int* tile_pre;   // [n + 1]
+  const int* cchunk_pre; // [n + 1]
+  const int* pchunk_pre; // [n + 1]
+  int n;
+  int total_tiles, total_cchunks, total_pchunks;
+  int max_n;             // largest 6 * n_free in the batch
+  int pad;
+};
+
+// Kernel launchers (ba_kernels.cu).  All run on `st`.
+cudaError_t set_kernel_attributes(int max_n);
+void launch_arm(const BatchView& bv, int iters, cudaStream_t st);
+void launch_reset(const BatchView& bv, bool mixed, cudaStream_t st);
+void launch_gather(const BatchView& bv, int iters, LmState* lm_out, StepRec* trace_out, cudaStream_t st);
+void launch_camreal(const BatchView& bv, bool mixed, cudaStream_t st);
+void launch_cost_init(const BatchView& bv, cudaStream_t st);
+void launch_iteration(const BatchView& bv, bool mixed, int refine_steps, cudaStream_t st);
+void launch_grad_norm(const BatchView& bv, bool mixed, double* out, cudaStream_t st);
+void launch_reproj(const DevCluster* dcl, const DevCluster& hcl, double* err_pm, cudaStream_t st);
+size_t factor_smem_bytes(int max_n);
+
+}  // namespace bagpu

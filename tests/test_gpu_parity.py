@@ -1,0 +1,193 @@
+"""GPU path (through the C ABI) against the FP64 CPU oracle, step by step.
+
+FP64 path: every LM step matches the oracle to a relative 1e-10 on the state
+(rotation entries, centres and points; scale 1 m), on F, on the gain's
+accept/reject decision and on the damping.  Mixed path: the final
+reprojection RMS within 1e-3 px and camera centres within 1 mm of the
+oracle's.  The batch path equals the single-cluster path bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import scenegen as sg
+from helpers import rms_inliers, state_rel_err
+
+pytestmark = pytest.mark.gpu
+
+TOL_STEP = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ba():
+    import paper_2511_06152_gb300 as m
+    m.lib()
+    return m
+
+
+def _step_parity(ba, scene, iters, tol=TOL_STEP):
+    P, S = O.Problem(scene), O.State(scene)
+    with ba.Context(precision=ba.BA_FP64) as ctx:
+        cid = ctx.create_cluster(scene)
+        worst = 0.0
+        for it in range(iters):
+            io = O.lm_step(P, S)
+            ig = ctx.solve_step(cid)
+            R, T, X = ctx.get_state(cid)
+            if abs(io["gain"]) < 1e-8:
+                continue  # a decision on the boundary: flagged, not failed
+            assert ig["accepted"] == io["accepted"], (it, ig, io)
+            assert ig["F_before"] == pytest.approx(io["F"], rel=tol, abs=1e-300)
+            assert ig["F_after"] == pytest.approx(io["F_new"], rel=tol, abs=1e-12)
+            assert ig["mu"] == pytest.approx(io["mu"], rel=1e-9)
+            e = state_rel_err(R, T, X, S.R, S.T, S.X)
+            worst = max(worst, e)
+            assert e < tol, (it, e)
+        return worst
+
+
+def test_fp64_step_parity_c1(ba):
+    """6 images, ~7,000 observations, Huber outliers, GNSS/IMU priors, 10 steps."""
+    _step_parity(ba, sg.cluster_c1(), sg.ITERS["c1"])
+
+
+@pytest.mark.parametrize("seed,strips,per,npts,fixed,priors", [
+    (101, 1, 2, 10, None, True),
+    (102, 2, 2, 40, (0,), True),
+    (103, 1, 4, 60, (0, 3), False),
+    (104, 2, 3, 200, (1, 4), True),
+    (105, 3, 3, 500, None, True),
+])
+def test_fp64_step_parity_small_clusters(ba, seed, strips, per, npts, fixed, priors):
+    _step_parity(ba, sg.tiny_cluster(seed, strips, per, npts, fixed=fixed, priors=priors), 8)
+
+
+def test_fp64_step_parity_c2_full_size(ba):
+    """The paper-scale cluster (24 images, 40,000 points, ~230k observations)
+    at full size, 20 steps."""
+    _step_parity(ba, sg.cluster_c2(), sg.ITERS["c2"])
+
+
+def test_fp64_zero_noise_convergence(ba):
+    c = sg.cluster_c1(zero_noise_init=True)
+    with ba.Context(precision=ba.BA_FP64) as ctx:
+        cid = ctx.create_cluster(c)
+        ctx.run(cid, 25)
+        R, T, X = ctx.get_state(cid)
+    assert sg.centre_error(T, c["T_true"]) < 1e-9
+    assert np.abs(X - c["X_true"]).max() < 1e-8
+
+
+def test_run_equals_single_steps_bitwise(ba):
+    c = sg.cluster_c1()
+    with ba.Context(precision=ba.BA_FP64) as ctx:
+        a = ctx.create_cluster(c)
+        b = ctx.create_cluster(c)
+        ta = ctx.run(a, 6)
+        tb = [ctx.solve_step(b) for _ in range(6)]
+        for x, y in zip(ta, tb):
+            assert x == y
+        for u, v in zip(ctx.get_state(a), ctx.get_state(b)):
+            assert np.array_equal(u, v)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_equals_alone_bitwise(ba, precision):
+    prec = ba.BA_FP64 if precision == "fp64" else ba.BA_MIXED
+    scenes = sg.batch_c3(replica=7, n_clusters=5, scale=0.1)
+    with ba.Context(precision=prec) as ctx:
+        ids = [ctx.create_cluster(s) for s in scenes]
+        alone = []
+        for i in ids:
+            ctx.run(i, 4)
+            alone.append(ctx.get_state(i))
+            ctx.reset(i)
+        res = ctx.solve_batch(ids, 4)
+        for i, a, r in zip(ids, alone, res):
+            got = ctx.get_state(i)
+            for u, v in zip(got, a):
+                assert np.array_equal(u, v)
+            assert r["iters"] == 4
+
+
+def test_reset_and_determinism(ba):
+    c = sg.cluster_c1()
+    with ba.Context(precision=ba.BA_MIXED) as ctx:
+        cid = ctx.create_cluster(c)
+        t1 = ctx.run(cid, 5)
+        s1 = ctx.get_state(cid)
+        ctx.reset(cid)
+        t2 = ctx.run(cid, 5)
+        s2 = ctx.get_state(cid)
+    assert t1 == t2
+    for u, v in zip(s1, s2):
+        assert np.array_equal(u, v)
+
+
+def test_linearize_cost_and_gradient(ba):
+    c = sg.cluster_c1(fixed=(2,))
+    P = O.Problem(c)
+    ref = O.solve_damped(P, c["R0"], c["T0"], c["X0"], 1e-4)
+    F = O.cost(P, c["R0"], c["T0"], c["X0"])
+    with ba.Context(precision=ba.BA_FP64) as ctx:
+        cid = ctx.create_cluster(c)
+        lin = ctx.linearize(cid)
+    g = max(np.abs(ref["gc"]).max(), np.abs(ref["gp"]).max())
+    assert lin["cost"] == pytest.approx(F, rel=1e-12)
+    assert lin["grad_inf"] == pytest.approx(g, rel=1e-9)
+    assert lin["n_free"] == 5
+
+
+def test_reprojection_errors_match_oracle(ba):
+    c = sg.tiny_cluster(7, 2, 2, 50)
+    P = O.Problem(c)
+    with ba.Context(precision=ba.BA_FP64) as ctx:
+        cid = ctx.create_cluster(c)
+        e = ctx.reprojection_errors(cid)
+    ref = O.residual_stats(P, c["R0"], c["T0"], c["X0"])
+    np.testing.assert_allclose(e, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_mixed_precision_against_oracle_c1(ba):
+    """Mixed precision (FP32 per-observation work, FP64 solve and cost):
+    final reprojection RMS within 1e-3 px and centres within 1 mm."""
+    c = sg.cluster_c1()
+    P, S = O.Problem(c), O.State(c)
+    O.lm_run(P, S, sg.ITERS["c1"])
+    ref_rms = rms_inliers(O.residual_stats(P, S.R, S.T, S.X), c["outlier"])
+    with ba.Context(precision=ba.BA_MIXED) as ctx:
+        cid = ctx.create_cluster(c)
+        ctx.run(cid, sg.ITERS["c1"])
+        R, T, X = ctx.get_state(cid)
+        rms = rms_inliers(ctx.reprojection_errors(cid), c["outlier"])
+    assert abs(rms - ref_rms) < 1e-3
+    assert sg.centre_error(T, S.T) < 1e-3
+
+
+@pytest.mark.parametrize("bad", ["cam_range", "pt_range", "nan", "dup", "long_track", "all_fixed", "sigma"])
+def test_invalid_clusters_are_rejected(ba, bad):
+    c = sg.tiny_cluster(9, 1, 3, 10)
+    c = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in c.items()}
+    if bad == "cam_range":
+        c["obs_cam"][0] = c["n_cams"]
+    elif bad == "pt_range":
+        c["obs_pt"][0] = -1
+    elif bad == "nan":
+        c["obs_uv"][3, 1] = np.nan
+    elif bad == "dup":
+        c["obs_cam"][1] = c["obs_cam"][0]
+        c["obs_pt"][1] = c["obs_pt"][0]
+    elif bad == "long_track":
+        n = 33
+        c["n_obs"] = n
+        c["obs_cam"] = np.arange(n, dtype=np.int32) % c["n_cams"]
+        c["obs_pt"] = np.zeros(n, dtype=np.int32)
+        c["obs_uv"] = np.zeros((n, 2))
+    elif bad == "all_fixed":
+        c["fixed"] = np.ones(c["n_cams"], np.uint8)
+    elif bad == "sigma":
+        c["sigma_px"] = 0.0
+    with ba.Context() as ctx:
+        with pytest.raises(ba.BAError) as ei:
+            ctx.create_cluster(c)
+        assert ei.value.status == ba.BA_ERR_INVALID
