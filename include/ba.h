@@ -90,8 +90,22 @@ typedef struct {
   int32_t precision;         /* BA_FP64 or BA_MIXED */
   int32_t n_slots;           /* clusters the serving scheduler runs at once (ba_submit); 0 = 64 */
   int32_t refine_steps;      /* iterative-refinement passes after the Cholesky solve; <0 = default 1 */
-  int32_t reserved;
+  int32_t flags;             /* BA_FLAG_* */
 } ba_config;
+
+#define BA_FLAG_KERNEL_TIMING 1 /* bracket every kernel with CUDA events (also inside graphs) */
+
+/* Kernel kinds reported by ba_kernel_stats, in this order. */
+#define BA_KERNEL_LINEARIZE 0   /* residuals, Jacobians, point blocks, Z = W L^-T */
+#define BA_KERNEL_CAM_REDUCE 1  /* camera-major chunk sums */
+#define BA_KERNEL_PAIR_REDUCE 2 /* camera-pair chunk sums */
+#define BA_KERNEL_FACTOR 3      /* assembly, Cholesky, solve, refinement, candidate poses */
+#define BA_KERNEL_BACKSUB 4     /* point back-substitution and candidate cost */
+#define BA_KERNEL_LM_UPDATE 5   /* gain ratio, accept/reject, damping update */
+#define BA_KERNEL_COST_TILES 6  /* cost at the current state (per tile) */
+#define BA_KERNEL_COST_INIT 7   /* cost at the current state (per cluster) */
+#define BA_KERNEL_OTHER 8       /* arm, reset, gather, camera copies, diagnostics */
+#define BA_KERNEL_KINDS 9
 
 typedef struct {
   int32_t n_cams, n_pts, n_obs;
@@ -181,6 +195,10 @@ BA_API ba_status ba_solve_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n
 /* Restore a cluster's initial state (the one given at create) and damping. */
 BA_API ba_status ba_reset(ba_ctx* ctx, ba_cluster_id id);
 
+/* ba_reset on n clusters in one launch (enqueued on the context's stream;
+ * returns without waiting). */
+BA_API ba_status ba_reset_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n);
+
 /* Queue a cluster for the serving scheduler (non-blocking).  The scheduler
  * admits queued clusters into free slots between LM iterations, so work
  * submitted while others run joins the running batch.  *out receives a
@@ -201,6 +219,16 @@ BA_API ba_status ba_reprojection_errors(ba_ctx* ctx, ba_cluster_id id, double* e
 
 /* Device memory the context holds now, in bytes. */
 BA_API ba_status ba_memory_in_use(ba_ctx* ctx, uint64_t* bytes);
+
+/* Kernels this context has launched so far (kernel nodes of graph launches
+ * included). */
+BA_API ba_status ba_launch_count(ba_ctx* ctx, uint64_t* out);
+
+/* Per-kernel-kind device time (ms) and launch counts accumulated since the
+ * context was created or last reset (reset != 0 clears after reading).
+ * ms[n] and launches[n] are host arrays, n <= BA_KERNEL_KINDS; times are only
+ * collected when the context was created with BA_FLAG_KERNEL_TIMING. */
+BA_API ba_status ba_kernel_stats(ba_ctx* ctx, double* ms, uint64_t* launches, int32_t n, int32_t reset);
 
 BA_API ba_status ba_destroy_cluster(ba_ctx* ctx, ba_cluster_id id);
 BA_API ba_status ba_shutdown(ba_ctx* ctx);

@@ -30,6 +30,9 @@ BA_FP64 = 0
 BA_MIXED = 1
 BA_PTR_HOST = 0
 BA_PTR_DEVICE = 1
+BA_FLAG_KERNEL_TIMING = 1
+KERNEL_KINDS = ["linearize", "cam_reduce", "pair_reduce", "factor", "backsub_cost", "lm_update", "cost_tiles",
+                "cost_init", "other"]
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -39,7 +42,7 @@ _u8p = ctypes.POINTER(ctypes.c_uint8)
 class ba_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("stream", ctypes.c_void_p), ("hbm_budget_bytes", ctypes.c_uint64),
                 ("precision", ctypes.c_int32), ("n_slots", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("flags", ctypes.c_int32)]
 
 
 class ba_cluster_desc(ctypes.Structure):
@@ -80,8 +83,9 @@ class ba_result(ctypes.Structure):
 
 
 EXPORTS = ["ba_init", "ba_create_cluster", "ba_linearize", "ba_solve_step", "ba_run", "ba_solve_batch", "ba_reset",
-           "ba_submit", "ba_poll", "ba_get_state", "ba_reprojection_errors", "ba_memory_in_use",
-           "ba_destroy_cluster", "ba_shutdown", "ba_status_string", "ba_last_error"]
+           "ba_reset_batch", "ba_submit", "ba_poll", "ba_get_state", "ba_reprojection_errors", "ba_memory_in_use",
+           "ba_launch_count", "ba_kernel_stats", "ba_destroy_cluster", "ba_shutdown", "ba_status_string",
+           "ba_last_error"]
 
 _lib = None
 _lock = threading.Lock()
@@ -107,6 +111,9 @@ def lib(build: bool = True):
             L.ba_solve_batch.argtypes = [vp, ctypes.POINTER(u64), ctypes.c_int32, ctypes.c_int32,
                                          ctypes.POINTER(ba_result), ctypes.POINTER(ba_step_info)]
             L.ba_reset.argtypes = [vp, u64]
+            L.ba_reset_batch.argtypes = [vp, ctypes.POINTER(u64), ctypes.c_int32]
+            L.ba_launch_count.argtypes = [vp, ctypes.POINTER(u64)]
+            L.ba_kernel_stats.argtypes = [vp, _dp, ctypes.POINTER(u64), ctypes.c_int32, ctypes.c_int32]
             L.ba_submit.argtypes = [vp, u64, ctypes.POINTER(ba_solve_opts), ctypes.POINTER(u64)]
             L.ba_poll.argtypes = [vp, u64, ctypes.POINTER(ba_result)]
             L.ba_get_state.argtypes = [vp, u64, _dp, _dp, _dp, ctypes.c_int32]
@@ -177,10 +184,11 @@ def make_desc(scene, keep):
 class Context:
     """Owns one ba_ctx on one device and stream."""
 
-    def __init__(self, device=0, precision=BA_FP64, stream=None, hbm_budget_bytes=0, n_slots=0, refine_steps=-1):
+    def __init__(self, device=0, precision=BA_FP64, stream=None, hbm_budget_bytes=0, n_slots=0, refine_steps=-1,
+                 flags=0):
         self.L = lib()
         cfg = ba_config(device=device, stream=stream, hbm_budget_bytes=hbm_budget_bytes, precision=precision,
-                        n_slots=n_slots, refine_steps=refine_steps, reserved=0)
+                        n_slots=n_slots, refine_steps=refine_steps, flags=flags)
         h = ctypes.c_void_p()
         _check(self.L.ba_init(ctypes.byref(h), ctypes.byref(cfg)), None, "ba_init")
         self.h = h
@@ -241,6 +249,22 @@ class Context:
 
     def reset(self, cid):
         _check(self.L.ba_reset(self.h, cid), self.h, "ba_reset")
+
+    def reset_batch(self, cids):
+        ids = (ctypes.c_uint64 * len(cids))(*cids)
+        _check(self.L.ba_reset_batch(self.h, ids, len(cids)), self.h, "ba_reset_batch")
+
+    def launch_count(self):
+        v = ctypes.c_uint64()
+        _check(self.L.ba_launch_count(self.h, ctypes.byref(v)), self.h, "ba_launch_count")
+        return v.value
+
+    def kernel_stats(self, reset=False):
+        n = len(KERNEL_KINDS)
+        ms = np.zeros(n)
+        cnt = (ctypes.c_uint64 * n)()
+        _check(self.L.ba_kernel_stats(self.h, _d(ms), cnt, n, int(reset)), self.h, "ba_kernel_stats")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_KINDS)}
 
     def submit(self, cid, iters):
         t = ctypes.c_uint64()

@@ -36,6 +36,12 @@ struct Cluster {
   std::atomic<int> in_service{0}; // queued or running in the serving scheduler
 };
 
+struct GraphRec {
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long kernels = 0;  // kernel nodes in the graph
+  Probe* probe = nullptr;          // event pairs captured with the graph (timing mode)
+};
+
 struct Plan {
   std::vector<ba_cluster_id> ids;
   char* dbuf = nullptr;
@@ -43,7 +49,8 @@ struct Plan {
   BatchView bv{};
   LmState* lm_out = nullptr;     // device [n]
   double* gnorm = nullptr;       // device [n]
-  std::map<int, cudaGraphExec_t> graphs;
+  std::map<int, GraphRec> graphs;
+  GraphRec* last = nullptr;      // graph of the last launch (for timing readout)
 };
 
 struct Ticket {
@@ -69,6 +76,10 @@ struct ba_ctx {
   uint64_t mem = 0;
   std::map<std::vector<ba_cluster_id>, Plan*> plans;
   int attr_max_n = 0;
+  bool timing = false;
+  double kms[KK_COUNT] = {0};
+  uint64_t klaunch[KK_COUNT] = {0};
+  uint64_t launches = 0;
   std::string last_error;
   std::mutex api_mu;  // serialises API calls against the scheduler thread
 
@@ -137,8 +148,22 @@ ba_status ensure_attrs(ba_ctx* ctx, int max_n) {
   return BA_OK;
 }
 
+void free_probe(Probe* pr) {
+  if (!pr) return;
+  for (auto& r : pr->recs) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  delete pr;
+}
+
+void note_direct(ba_ctx* ctx) { ctx->launches += take_direct_launches(); }
+
 void free_plan(Plan* p) {
-  for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : p->graphs) {
+    cudaGraphExecDestroy(kv.second.exec);
+    free_probe(kv.second.probe);
+  }
   if (p->dbuf) cudaFree(p->dbuf);
   delete p;
 }
@@ -224,24 +249,49 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
 // arm -> cost at the current state -> iters x (K1..K6).
 ba_status run_plan(ba_ctx* ctx, Plan* p, int iters) {
   auto it = p->graphs.find(iters);
-  cudaGraphExec_t exec = nullptr;
   if (it == p->graphs.end()) {
+    GraphRec g;
     cudaGraph_t graph = nullptr;
+    note_direct(ctx);
+    take_captured_launches();
+    if (ctx->timing) {
+      g.probe = new Probe();
+      set_probe(g.probe);
+    }
     CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     launch_arm(p->bv, iters, ctx->stream);
     launch_cost_init(p->bv, ctx->stream);
     for (int i = 0; i < iters; ++i) launch_iteration(p->bv, ctx->mixed, ctx->refine, ctx->stream);
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
-    if (e != cudaSuccess) return set_err(ctx, BA_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&exec, graph, 0);
+    set_probe(nullptr);
+    g.kernels = take_captured_launches();
+    if (e != cudaSuccess) {
+      free_probe(g.probe);
+      return set_err(ctx, BA_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return set_err(ctx, BA_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-    p->graphs[iters] = exec;
-  } else {
-    exec = it->second;
+    if (e != cudaSuccess) {
+      free_probe(g.probe);
+      return set_err(ctx, BA_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    it = p->graphs.emplace(iters, g).first;
   }
-  CUDA_TRY(ctx, cudaGraphLaunch(exec, ctx->stream));
+  CUDA_TRY(ctx, cudaGraphLaunch(it->second.exec, ctx->stream));
+  ctx->launches += it->second.kernels;
+  p->last = &it->second;
   return BA_OK;
+}
+
+// After the stream has synchronised: fold the last graph's event times into
+// the per-kernel statistics.
+void collect_timing(ba_ctx* ctx, Plan* p) {
+  if (!ctx->timing || !p->last || !p->last->probe) return;
+  for (auto& r : p->last->probe->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) ctx->kms[r.kind] += ms;
+    ctx->klaunch[r.kind] += 1;
+  }
 }
 
 void fill_step(const StepRec& r, ba_step_info* o) {
@@ -285,6 +335,8 @@ ba_status run_and_collect(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, in
   }
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   CUDA_TRY(ctx, cudaGetLastError());
+  note_direct(ctx);
+  collect_timing(ctx, p);
   return BA_OK;
 }
 
@@ -715,6 +767,7 @@ BA_API ba_status ba_init(ba_ctx** out, const ba_config* cfg) {
   ctx->mixed = cfg->precision == BA_MIXED;
   ctx->n_slots = cfg->n_slots > 0 ? cfg->n_slots : 64;
   ctx->refine = cfg->refine_steps >= 0 ? cfg->refine_steps : 1;
+  ctx->timing = (cfg->flags & BA_FLAG_KERNEL_TIMING) != 0;
   if (cfg->stream) {
     ctx->stream = (cudaStream_t)cfg->stream;
   } else {
@@ -777,6 +830,7 @@ BA_API ba_status ba_create_cluster(ba_ctx* ctx, const ba_cluster_desc* d, ba_clu
   st = single_view(ctx, c, &p);
   if (st != BA_OK) return st;
   launch_camreal(p->bv, ctx->mixed, ctx->stream);
+  note_direct(ctx);
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   CUDA_TRY(ctx, cudaGetLastError());
   *out = c->id;
@@ -796,6 +850,7 @@ BA_API ba_status ba_linearize(ba_ctx* ctx, ba_cluster_id id, ba_lin_info* out) {
   launch_cost_init(p->bv, ctx->stream);
   launch_grad_norm(p->bv, ctx->mixed, p->gnorm, ctx->stream);
   launch_arm(p->bv, -2, ctx->stream);
+  note_direct(ctx);
   LmState lm{};
   double gn = 0.0;
   CUDA_TRY(ctx, cudaMemcpyAsync(&lm, c->h.lm, sizeof(LmState), cudaMemcpyDeviceToHost, ctx->stream));
@@ -882,8 +937,50 @@ BA_API ba_status ba_reset(ba_ctx* ctx, ba_cluster_id id) {
   ba_status st = single_view(ctx, c, &p);
   if (st != BA_OK) return st;
   launch_reset(p->bv, ctx->mixed, ctx->stream);
+  note_direct(ctx);
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   CUDA_TRY(ctx, cudaGetLastError());
+  return BA_OK;
+}
+
+BA_API ba_status ba_reset_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n) {
+  if (!ctx || !ids || n <= 0) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  std::vector<ba_cluster_id> v(ids, ids + n);
+  for (auto id : v) {
+    Cluster* c = find_cluster(ctx, id);
+    if (!c) return BA_ERR_NOT_FOUND;
+    if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
+  }
+  Plan* p = nullptr;
+  ba_status st = get_plan(ctx, v, &p);
+  if (st != BA_OK) return st;
+  launch_reset(p->bv, ctx->mixed, ctx->stream);
+  note_direct(ctx);
+  CUDA_TRY(ctx, cudaGetLastError());
+  return BA_OK;
+}
+
+BA_API ba_status ba_launch_count(ba_ctx* ctx, uint64_t* out) {
+  if (!ctx || !out) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  note_direct(ctx);
+  *out = ctx->launches;
+  return BA_OK;
+}
+
+BA_API ba_status ba_kernel_stats(ba_ctx* ctx, double* ms, uint64_t* launches, int32_t n, int32_t reset) {
+  if (!ctx || n < 0 || n > KK_COUNT) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  for (int i = 0; i < n; ++i) {
+    if (ms) ms[i] = ctx->kms[i];
+    if (launches) launches[i] = ctx->klaunch[i];
+  }
+  if (reset)
+    for (int i = 0; i < KK_COUNT; ++i) {
+      ctx->kms[i] = 0.0;
+      ctx->klaunch[i] = 0;
+    }
   return BA_OK;
 }
 
@@ -954,6 +1051,7 @@ BA_API ba_status ba_reprojection_errors(ba_ctx* ctx, ba_cluster_id id, double* e
   double* d = nullptr;
   CUDA_TRY(ctx, cudaMallocAsync((void**)&d, sizeof(double) * c->no, ctx->stream));
   launch_reproj(c->d_desc, c->h, d, ctx->stream);
+  note_direct(ctx);
   std::vector<double> pmv(c->no);
   CUDA_TRY(ctx, cudaMemcpyAsync(pmv.data(), d, sizeof(double) * c->no, cudaMemcpyDeviceToHost, ctx->stream));
   CUDA_TRY(ctx, cudaFreeAsync(d, ctx->stream));

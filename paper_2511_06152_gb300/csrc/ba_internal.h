@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace bagpu {
 
 constexpr int kRec = 32;        // Reals per observation record: Jc[12], r[2], Z[18]
@@ -127,6 +129,32 @@ struct BatchView {
   int max_n;             // largest 6 * n_free in the batch
   int pad;
 };
+
+// Kernel kinds, for launch counting and per-kernel timing.
+enum KernelKind {
+  KK_LINEARIZE = 0,
+  KK_CAM_REDUCE,
+  KK_PAIR_REDUCE,
+  KK_FACTOR,
+  KK_BACKSUB,
+  KK_LM_UPDATE,
+  KK_COST_TILES,
+  KK_COST_INIT,
+  KK_OTHER,
+  KK_COUNT
+};
+
+// CUDA events bracketing each launch while a probe is attached to the thread.
+struct ProbeRec {
+  int kind;
+  cudaEvent_t e0, e1;
+};
+struct Probe {
+  std::vector<ProbeRec> recs;
+};
+void set_probe(Probe* p);                       // attach to the calling thread (nullptr detaches)
+unsigned long long take_direct_launches();      // launches outside capture since the last call
+unsigned long long take_captured_launches();    // kernel nodes captured since the last call
 
 // Kernel launchers (ba_kernels.cu).  All run on `st`.
 cudaError_t set_kernel_attributes(int max_n);

@@ -809,20 +809,61 @@ __global__ void k_gather(BatchView bv, int iters, LmState* lm_out, StepRec* trac
 }
 
 // ------------------------------------------------------------------ launchers
+//
+// Every launch goes through LAUNCH(kind, ...): it counts the launch (as a
+// direct launch, or as a kernel node when the stream is being captured) and,
+// when a probe is attached to the calling thread, brackets the kernel with
+// CUDA events (captured as event-record nodes inside graphs).
 
-void launch_arm(const BatchView& bv, int iters, cudaStream_t st) {
-  k_arm<<<(bv.n + 127) / 128, 128, 0, st>>>(bv, iters);
+static thread_local Probe* t_probe = nullptr;
+static thread_local unsigned long long t_direct = 0, t_captured = 0;
+
+void set_probe(Probe* p) { t_probe = p; }
+unsigned long long take_direct_launches() {
+  const unsigned long long v = t_direct;
+  t_direct = 0;
+  return v;
+}
+unsigned long long take_captured_launches() {
+  const unsigned long long v = t_captured;
+  t_captured = 0;
+  return v;
 }
 
-void launch_reset(const BatchView& bv, bool mixed, cudaStream_t st) {
-  dim3 grid(64, bv.n < 65535 ? bv.n : 65535);
-  k_reset<<<grid, 256, 0, st>>>(bv);
-  launch_camreal(bv, mixed, st);
+static bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  return cs == cudaStreamCaptureStatusActive;
 }
 
-void launch_gather(const BatchView& bv, int iters, LmState* lm_out, StepRec* trace_out, cudaStream_t st) {
-  k_gather<<<bv.n < 65535 ? bv.n : 65535, 128, 0, st>>>(bv, iters, lm_out, trace_out);
+static void probe_mark(cudaStream_t st, cudaEvent_t* out) {
+  cudaEventCreate(out);
+  if (capturing(st)) cudaEventRecordWithFlags(*out, st, cudaEventRecordExternal);
+  else cudaEventRecord(*out, st);
 }
+
+struct LaunchScope {
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t e0 = nullptr;
+  LaunchScope(int k, cudaStream_t s) : kind(k), st(s) {
+    if (t_probe) probe_mark(st, &e0);
+  }
+  ~LaunchScope() {
+    if (capturing(st)) ++t_captured; else ++t_direct;
+    if (t_probe) {
+      cudaEvent_t e1;
+      probe_mark(st, &e1);
+      t_probe->recs.push_back(ProbeRec{kind, e0, e1});
+    }
+  }
+};
+
+#define LAUNCH(kind, st, ...) \
+  do {                          \
+    LaunchScope ls__(kind, st); \
+    __VA_ARGS__;                \
+  } while (0)
 
 static int grid_for(int items, int per_block, int cap) {
   int g = (items + per_block - 1) / per_block;
@@ -841,27 +882,42 @@ static int num_sms() {
   return g_num_sms;
 }
 
+void launch_arm(const BatchView& bv, int iters, cudaStream_t st) {
+  LAUNCH(KK_OTHER, st, k_arm<<<(bv.n + 127) / 128, 128, 0, st>>>(bv, iters));
+}
+
+void launch_reset(const BatchView& bv, bool mixed, cudaStream_t st) {
+  dim3 grid(64, bv.n < 65535 ? bv.n : 65535);
+  LAUNCH(KK_OTHER, st, k_reset<<<grid, 256, 0, st>>>(bv));
+  launch_camreal(bv, mixed, st);
+}
+
+void launch_gather(const BatchView& bv, int iters, LmState* lm_out, StepRec* trace_out, cudaStream_t st) {
+  LAUNCH(KK_OTHER, st, k_gather<<<bv.n < 65535 ? bv.n : 65535, 128, 0, st>>>(bv, iters, lm_out, trace_out));
+}
+
 void launch_camreal(const BatchView& bv, bool mixed, cudaStream_t st) {
-  if (mixed) k_camreal<float><<<grid_for(bv.n, 1, 65535), 64, 0, st>>>(bv);
-  else k_camreal<double><<<grid_for(bv.n, 1, 65535), 64, 0, st>>>(bv);
+  if (mixed) LAUNCH(KK_OTHER, st, k_camreal<float><<<grid_for(bv.n, 1, 65535), 64, 0, st>>>(bv));
+  else LAUNCH(KK_OTHER, st, k_camreal<double><<<grid_for(bv.n, 1, 65535), 64, 0, st>>>(bv));
 }
 
 void launch_cost_init(const BatchView& bv, cudaStream_t st) {
   const int sms = num_sms();
-  k_cost_tiles<<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv);
-  k_cost_init<<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv);
+  LAUNCH(KK_COST_TILES, st, k_cost_tiles<<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
+  LAUNCH(KK_COST_INIT, st, k_cost_init<<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv));
 }
 
 template <typename Real>
 static void launch_iteration_t(const BatchView& bv, int refine_steps, cudaStream_t st) {
   const int sms = num_sms();
-  k_linearize<Real><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv);
-  k_cam_reduce<Real><<<grid_for(bv.total_cchunks, 1, sms * 32), 128, 0, st>>>(bv);
-  if (bv.total_pchunks > 0) k_pair_reduce<Real><<<grid_for(bv.total_pchunks, 8, sms * 16), 256, 0, st>>>(bv);
+  LAUNCH(KK_LINEARIZE, st, k_linearize<Real><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
+  LAUNCH(KK_CAM_REDUCE, st, k_cam_reduce<Real><<<grid_for(bv.total_cchunks, 1, sms * 32), 128, 0, st>>>(bv));
+  if (bv.total_pchunks > 0)
+    LAUNCH(KK_PAIR_REDUCE, st, k_pair_reduce<Real><<<grid_for(bv.total_pchunks, 8, sms * 16), 256, 0, st>>>(bv));
   const size_t smem = factor_smem_bytes(bv.max_n);
-  k_factor_solve<Real><<<grid_for(bv.n, 1, 65535), 512, smem, st>>>(bv, refine_steps, 0);
-  k_backsub_cost<Real><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv);
-  k_lm_update<Real><<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv);
+  LAUNCH(KK_FACTOR, st, k_factor_solve<Real><<<grid_for(bv.n, 1, 65535), 512, smem, st>>>(bv, refine_steps, 0));
+  LAUNCH(KK_BACKSUB, st, k_backsub_cost<Real><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
+  LAUNCH(KK_LM_UPDATE, st, k_lm_update<Real><<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv));
 }
 
 void launch_iteration(const BatchView& bv, bool mixed, int refine_steps, cudaStream_t st) {
@@ -872,11 +928,13 @@ void launch_iteration(const BatchView& bv, bool mixed, int refine_steps, cudaStr
 template <typename Real>
 static void launch_grad_norm_t(const BatchView& bv, double* out, cudaStream_t st) {
   const int sms = num_sms();
-  k_linearize<Real><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv);
-  k_cam_reduce<Real><<<grid_for(bv.total_cchunks, 1, sms * 32), 128, 0, st>>>(bv);
-  if (bv.total_pchunks > 0) k_pair_reduce<Real><<<grid_for(bv.total_pchunks, 8, sms * 16), 256, 0, st>>>(bv);
-  k_factor_solve<Real><<<grid_for(bv.n, 1, 65535), 512, factor_smem_bytes(bv.max_n), st>>>(bv, 0, 1);
-  k_grad_norm<Real><<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv, out);
+  LAUNCH(KK_LINEARIZE, st, k_linearize<Real><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
+  LAUNCH(KK_CAM_REDUCE, st, k_cam_reduce<Real><<<grid_for(bv.total_cchunks, 1, sms * 32), 128, 0, st>>>(bv));
+  if (bv.total_pchunks > 0)
+    LAUNCH(KK_PAIR_REDUCE, st, k_pair_reduce<Real><<<grid_for(bv.total_pchunks, 8, sms * 16), 256, 0, st>>>(bv));
+  LAUNCH(KK_FACTOR, st,
+         k_factor_solve<Real><<<grid_for(bv.n, 1, 65535), 512, factor_smem_bytes(bv.max_n), st>>>(bv, 0, 1));
+  LAUNCH(KK_OTHER, st, k_grad_norm<Real><<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv, out));
 }
 
 void launch_grad_norm(const BatchView& bv, bool mixed, double* out, cudaStream_t st) {
@@ -885,7 +943,7 @@ void launch_grad_norm(const BatchView& bv, bool mixed, double* out, cudaStream_t
 }
 
 void launch_reproj(const DevCluster* dcl, const DevCluster& hcl, double* err_pm, cudaStream_t st) {
-  k_reproj<<<grid_for(hcl.n_obs, 256, num_sms() * 8), 256, 0, st>>>(dcl, err_pm);
+  LAUNCH(KK_OTHER, st, k_reproj<<<grid_for(hcl.n_obs, 256, num_sms() * 8), 256, 0, st>>>(dcl, err_pm));
 }
 
 cudaError_t set_kernel_attributes(int max_n) {

@@ -325,20 +325,33 @@ def cluster_c2(replica=0, **kw):
     return make_cluster(rng_for(2, replica), 3, 8, 40000, layout="patches", per_patch=30, **kw)
 
 
-def batch_c3(replica=0, n_clusters=256, scale=1.0):
-    """Batched workload: clusters with U{8..32} images in 2-3 strips,
-    U[5k, 60k] points (times `scale`), track length 2 + Geometric(0.5)
-    failures truncated at min(8, images containing the point)."""
+def batch_c3_specs(replica=0, n_clusters=256, scale=1.0):
+    """Per-cluster parameters of the batched workload: U{8..32} images in 2-3
+    strips, U[5k, 60k] points (times `scale`), and a sub-seed."""
     rng = rng_for(3, replica)
-    out = []
-    for i in range(n_clusters):
+    specs = []
+    for _ in range(n_clusters):
         nc = int(rng.integers(8, 33))
         ns = int(rng.integers(2, 4))
-        per = -(-nc // ns)
         npt = max(16, int(round(rng.uniform(5000, 60000) * scale)))
-        sub = np.random.Generator(np.random.PCG64(int(rng.integers(1 << 62))))
-        out.append(make_cluster(sub, ns, per, npt, track=(0.5, 8), n_cams=nc))
-    return out
+        specs.append((nc, ns, npt, int(rng.integers(1 << 62))))
+    return specs
+
+
+def cluster_from_spec(spec):
+    """One batched-workload cluster: track length 2 + Geometric(0.5) failures
+    truncated at min(8, images containing the point)."""
+    nc, ns, npt, seed = spec
+    sub = np.random.Generator(np.random.PCG64(seed))
+    return make_cluster(sub, ns, -(-nc // ns), npt, track=(0.5, 8), n_cams=nc)
+
+
+def batch_c3(replica=0, n_clusters=256, scale=1.0, pool=None):
+    """Batched workload of 256 uneven clusters (see batch_c3_specs)."""
+    specs = batch_c3_specs(replica, n_clusters, scale)
+    if pool is not None:
+        return list(pool.map(cluster_from_spec, specs))
+    return [cluster_from_spec(s) for s in specs]
 
 
 def cluster_c5(replica=0, n_points=2_000_000, **kw):
