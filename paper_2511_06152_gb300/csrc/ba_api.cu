@@ -260,7 +260,7 @@ ba_status run_plan(ba_ctx* ctx, Plan* p, int iters) {
     }
     CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     launch_arm(p->bv, iters, ctx->stream);
-    launch_cost_init(p->bv, ctx->stream);
+    launch_cost_init(p->bv, ctx->mixed, ctx->stream);
     for (int i = 0; i < iters; ++i) launch_iteration(p->bv, ctx->mixed, ctx->refine, ctx->stream);
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
     set_probe(nullptr);
@@ -514,7 +514,8 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const size_t o_ocam = Lo.add(sizeof(int) * (size_t)no);
   const size_t o_opt = Lo.add(sizeof(int) * (size_t)no);
   const size_t o_uv = Lo.add(sizeof(double) * 2 * (size_t)no);
-  const size_t o_uv32 = Lo.add(mixed ? sizeof(float) * 2 * (size_t)no : 0);
+  const size_t o_chi = Lo.add(mixed ? sizeof(float2) * (size_t)no : 0);
+  const size_t o_clo = Lo.add(mixed ? sizeof(float2) * (size_t)no : 0);
   const size_t o_cch = Lo.add(sizeof(ChunkItem) * cchunks.size());
   const size_t o_cobs = Lo.add(sizeof(int) * cam_obs.size());
   const size_t o_cpb = Lo.add(sizeof(int) * cam_part_begin.size());
@@ -524,7 +525,8 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const size_t o_ppb = Lo.add(sizeof(int) * pair_part_begin.size());
   const size_t o_lm = Lo.add(sizeof(LmState));
   const size_t static_bytes = Lo.off;
-  const size_t o_camreal = Lo.add(rs * 20 * nc);
+  const size_t o_camreal = Lo.add(mixed ? 0 : sizeof(double) * kCamReal * nc);
+  const size_t o_camdf = Lo.add(mixed ? sizeof(float) * 2 * kCamDf * nc : 0);
   const size_t o_rec = Lo.add(rs * kRec * (size_t)no);
   const size_t o_paux = Lo.add(rs * kPaux * (size_t)np);
   const size_t o_cpart = Lo.add(rs * kCamPart * cchunks.size());
@@ -534,6 +536,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const size_t o_gc = Lo.add(sizeof(double) * n);
   const size_t o_Dc = Lo.add(sizeof(double) * n);
   const size_t o_dc = Lo.add(sizeof(double) * n);
+  const size_t o_dc32 = Lo.add(sizeof(float) * n);
   const size_t o_tp = Lo.add(sizeof(double) * 2 * tiles.size());
   const size_t o_trace = Lo.add(sizeof(StepRec) * kTraceCap);
   const size_t o_desc = Lo.add(sizeof(DevCluster));
@@ -552,13 +555,24 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   put(o_R + sizeof(double) * R.size(), R.data(), sizeof(double) * R.size());
   put(o_T, T.data(), sizeof(double) * T.size());
   put(o_T + sizeof(double) * T.size(), T.data(), sizeof(double) * T.size());
-  put(o_X, X.data(), sizeof(double) * X.size());
-  put(o_X + sizeof(double) * X.size(), X.data(), sizeof(double) * X.size());
+  // points: binary64, or double-float (hi, lo) pairs in the mixed path
+  std::vector<double> Xrep(X);
+  if (mixed) {
+    float* xf = reinterpret_cast<float*>(Xrep.data());
+    for (size_t i = 0; i < X.size(); ++i) {
+      const float hi = (float)X[i];
+      const float lo = (float)(X[i] - (double)hi);
+      xf[2 * i] = hi;
+      xf[2 * i + 1] = lo;
+    }
+  }
+  put(o_X, Xrep.data(), sizeof(double) * Xrep.size());
+  put(o_X + sizeof(double) * Xrep.size(), Xrep.data(), sizeof(double) * Xrep.size());
   put(o_Rp, Rp.data(), sizeof(double) * Rp.size());
   put(o_Tp, Tp.data(), sizeof(double) * Tp.size());
   put(o_Ri, R.data(), sizeof(double) * R.size());
   put(o_Ti, T.data(), sizeof(double) * T.size());
-  put(o_Xi, X.data(), sizeof(double) * X.size());
+  put(o_Xi, Xrep.data(), sizeof(double) * Xrep.size());
   put(o_free, free_idx.data(), sizeof(int) * nc);
   put(o_cof, cam_of_free.data(), sizeof(int) * nf);
   put(o_tiles, tiles.data(), sizeof(Tile) * tiles.size());
@@ -566,16 +580,20 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
     int* sc = (int*)(stage.data() + o_ocam);
     int* sp = (int*)(stage.data() + o_opt);
     double* su = (double*)(stage.data() + o_uv);
-    float* s32 = mixed ? (float*)(stage.data() + o_uv32) : nullptr;
+    float2* chi = mixed ? (float2*)(stage.data() + o_chi) : nullptr;
+    float2* clo = mixed ? (float2*)(stage.data() + o_clo) : nullptr;
     for (int p = 0; p < no; ++p) {
       const int i = pm[p];
       sc[p] = ocam[i];
       sp[p] = opt[i];
       su[2 * p] = uv[2 * i];
       su[2 * p + 1] = uv[2 * i + 1];
-      if (s32) {
-        s32[2 * p] = (float)uv[2 * i];
-        s32[2 * p + 1] = (float)uv[2 * i + 1];
+      if (chi) {  // observation relative to the principal point, double-float
+        const double cu = uv[2 * i] - intr[7 * (size_t)ocam[i] + 1];
+        const double cv = uv[2 * i + 1] - intr[7 * (size_t)ocam[i] + 2];
+        const float hu = (float)cu, hv = (float)cv;
+        chi[p] = make_float2(hu, hv);
+        clo[p] = make_float2((float)(cu - (double)hu), (float)(cv - (double)hv));
       }
     }
   }
@@ -590,6 +608,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
     LmState lm{};
     lm.mu0 = d->mu0 > 0.0 ? d->mu0 : 1e-4;
     lm.mu = lm.mu0;
+    lm.mu_f = (float)lm.mu0;
     lm.nu = 2.0;
     put(o_lm, &lm, sizeof(lm));
   }
@@ -610,6 +629,9 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   h.n_pchunks = (int)pchunks.size();
   h.sigma_px = d->sigma_px; h.huber_delta = d->huber_delta_px; h.sigma_gnss = d->sigma_gnss_m;
   h.sigma_imu = d->sigma_imu_rad;
+  h.inv_sigma_f = (float)(1.0 / d->sigma_px);
+  h.delta_f = (float)d->huber_delta_px;
+  h.half_inv_s2_f = (float)(0.5 / (d->sigma_px * d->sigma_px));
   h.intr = (const double*)(arena + o_intr);
   h.R = (double*)(arena + o_R);
   h.T = (double*)(arena + o_T);
@@ -621,12 +643,14 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   h.X_init = (const double*)(arena + o_Xi);
   h.free_idx = (const int*)(arena + o_free);
   h.cam_of_free = (const int*)(arena + o_cof);
-  h.camreal = arena + o_camreal;
+  h.camreal = mixed ? nullptr : arena + o_camreal;
+  h.camdf = mixed ? (float*)(arena + o_camdf) : nullptr;
   h.tiles = (const Tile*)(arena + o_tiles);
   h.obs_cam = (const int*)(arena + o_ocam);
   h.obs_pt = (const int*)(arena + o_opt);
   h.obs_uv = (const double*)(arena + o_uv);
-  h.obs_uv32 = mixed ? (const float*)(arena + o_uv32) : nullptr;
+  h.obs_chi = mixed ? (const float2*)(arena + o_chi) : nullptr;
+  h.obs_clo = mixed ? (const float2*)(arena + o_clo) : nullptr;
   h.rec = arena + o_rec;
   h.paux = arena + o_paux;
   h.cchunks = (const ChunkItem*)(arena + o_cch);
@@ -643,6 +667,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   h.gc = (double*)(arena + o_gc);
   h.Dc = (double*)(arena + o_Dc);
   h.dc = (double*)(arena + o_dc);
+  h.dc32 = (float*)(arena + o_dc32);
   h.tilepart = (double*)(arena + o_tp);
   h.lm = (LmState*)(arena + o_lm);
   h.trace = (StepRec*)(arena + o_trace);
@@ -847,7 +872,7 @@ BA_API ba_status ba_linearize(ba_ctx* ctx, ba_cluster_id id, ba_lin_info* out) {
   ba_status st = single_view(ctx, c, &p);
   if (st != BA_OK) return st;
   launch_arm(p->bv, -1, ctx->stream);
-  launch_cost_init(p->bv, ctx->stream);
+  launch_cost_init(p->bv, ctx->mixed, ctx->stream);
   launch_grad_norm(p->bv, ctx->mixed, p->gnorm, ctx->stream);
   launch_arm(p->bv, -2, ctx->stream);
   note_direct(ctx);
@@ -1035,9 +1060,19 @@ BA_API ba_status ba_get_state(ba_ctx* ctx, ba_cluster_id id, double* R, double* 
     CUDA_TRY(ctx, cudaMemcpyAsync(R, c->h.R + (size_t)lm.cur * c->nc * 9, sizeof(double) * c->nc * 9, kind, ctx->stream));
   if (T)
     CUDA_TRY(ctx, cudaMemcpyAsync(T, c->h.T + (size_t)lm.cur * c->nc * 3, sizeof(double) * c->nc * 3, kind, ctx->stream));
-  if (X && c->np)
-    CUDA_TRY(ctx, cudaMemcpyAsync(X, c->h.X + (size_t)lm.cur * c->np * 3, sizeof(double) * (size_t)c->np * 3, kind,
-                                  ctx->stream));
+  if (X && c->np) {
+    if (ctx->mixed) {  // double-float points -> binary64
+      double* tmp = nullptr;
+      CUDA_TRY(ctx, cudaMallocAsync((void**)&tmp, sizeof(double) * (size_t)c->np * 3, ctx->stream));
+      launch_export_points(c->d_desc, c->h, true, tmp, ctx->stream);
+      note_direct(ctx);
+      CUDA_TRY(ctx, cudaMemcpyAsync(X, tmp, sizeof(double) * (size_t)c->np * 3, kind, ctx->stream));
+      CUDA_TRY(ctx, cudaFreeAsync(tmp, ctx->stream));
+    } else {
+      CUDA_TRY(ctx, cudaMemcpyAsync(X, c->h.X + (size_t)lm.cur * c->np * 3, sizeof(double) * (size_t)c->np * 3, kind,
+                                    ctx->stream));
+    }
+  }
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return BA_OK;
 }
@@ -1050,7 +1085,7 @@ BA_API ba_status ba_reprojection_errors(ba_ctx* ctx, ba_cluster_id id, double* e
   if (c->no == 0) return BA_OK;
   double* d = nullptr;
   CUDA_TRY(ctx, cudaMallocAsync((void**)&d, sizeof(double) * c->no, ctx->stream));
-  launch_reproj(c->d_desc, c->h, d, ctx->stream);
+  launch_reproj(c->d_desc, c->h, ctx->mixed, d, ctx->stream);
   note_direct(ctx);
   std::vector<double> pmv(c->no);
   CUDA_TRY(ctx, cudaMemcpyAsync(pmv.data(), d, sizeof(double) * c->no, cudaMemcpyDeviceToHost, ctx->stream));

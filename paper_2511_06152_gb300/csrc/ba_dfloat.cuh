@@ -1,0 +1,112 @@
+// Double-float ("double-word") arithmetic on binary32 pairs.
+//
+// A value is hi + lo with |lo| <= ulp(hi)/2, about 48 significant bits.  The
+// building blocks are the classical error-free transformations: Knuth's
+// TwoSum, Dekker's FastTwoSum, and the exact product through one fused
+// multiply-add; the double-word sum and product follow the algorithms
+// analysed by Joldes, Muller and Popescu (ACM TOMS 44(2), 2017, "Tight and
+// rigorous error bounds for basic building blocks of double-word
+// arithmetic").  Explicit _rn intrinsics keep the compiler from contracting
+// or reassociating the transformations.
+//
+// Used by the mixed-precision path for the point and camera state and for
+// the cost evaluation, which would otherwise need binary64 per observation
+// (GB300's binary64 rate is 1/59 of its binary32 rate).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace bagpu {
+
+struct dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfl df_make(float v) { return dfl{v, 0.0f}; }
+
+// exact a + b = s + e
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return dfl{s, e};
+}
+
+// exact a + b = s + e when |a| >= |b| (or a == 0)
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float e = __fsub_rn(b, __fsub_rn(s, a));
+  return dfl{s, e};
+}
+
+// exact a * b = p + e
+__device__ __forceinline__ dfl two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  return dfl{p, e};
+}
+
+// double-word + double-word (accurate version)
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  dfl s = two_sum(a.hi, b.hi);
+  const dfl t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ dfl df_neg(dfl a) { return dfl{-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+
+// double-word + float
+__device__ __forceinline__ dfl df_add_f(dfl a, float b) {
+  dfl s = two_sum(a.hi, b);
+  s.lo = __fadd_rn(s.lo, a.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+
+// double-word * double-word
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  dfl p = two_prod(a.hi, b.hi);
+  float t = __fmul_rn(a.lo, b.lo);
+  t = __fmaf_rn(a.hi, b.lo, t);
+  t = __fmaf_rn(a.lo, b.hi, t);
+  p.lo = __fadd_rn(p.lo, t);
+  return fast_two_sum(p.hi, p.lo);
+}
+
+// double-word * float
+__device__ __forceinline__ dfl df_mul_f(dfl a, float b) {
+  dfl p = two_prod(a.hi, b);
+  p.lo = __fmaf_rn(a.lo, b, p.lo);
+  return fast_two_sum(p.hi, p.lo);
+}
+
+// double-word / double-word: one correction step on the binary32 quotient
+__device__ __forceinline__ dfl df_div(dfl a, dfl b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const dfl r = df_sub(a, df_mul_f(b, q1));
+  const float q2 = __fdiv_rn(r.hi, b.hi);
+  return fast_two_sum(q1, q2);
+}
+
+// sqrt of a double-word (a > 0): one Newton correction
+__device__ __forceinline__ dfl df_sqrt(dfl a) {
+  const float s = __fsqrt_rn(a.hi);
+  const dfl r = df_sub(a, two_prod(s, s));
+  const float c = __fdiv_rn(r.hi, __fmul_rn(2.0f, s));
+  return fast_two_sum(s, c);
+}
+
+__device__ __forceinline__ float df_to_f(dfl a) { return __fadd_rn(a.hi, a.lo); }
+__device__ __forceinline__ double df_to_d(dfl a) { return (double)a.hi + (double)a.lo; }
+
+// binary64 -> double-word (hi = rounded value, lo = rounded remainder)
+__device__ __forceinline__ dfl df_from_d(double v) {
+  const float hi = __double2float_rn(v);
+  const float lo = __double2float_rn(v - (double)hi);
+  return dfl{hi, lo};
+}
+
+}  // namespace bagpu

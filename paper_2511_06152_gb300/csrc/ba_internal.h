@@ -31,6 +31,11 @@ constexpr double kDiagMax = 1e32;
 constexpr double kMinDepth = 1e-6;
 constexpr int BA_STATUS_NOT_PD = -3;  // same value as BA_ERR_NOT_PD in ba.h
 constexpr int kTraceCap = 256;
+// double-float camera record (floats): R as 9 (hi, lo) pairs [0..17], T as 3
+// pairs [18..23], f as a pair [24..25], k1 k2 p1 p2 as pairs [26..33], free
+// flag [34], padding to 40
+constexpr int kCamDf = 40;
+constexpr int kCamReal = 20;
 
 struct Tile {
   int obs_begin;
@@ -60,7 +65,7 @@ struct LmState {
   int active;        // 1 while the cluster still has iterations to run
   int iters_target;
   int pt_fail;       // a damped point block was not positive definite this iteration
-  int pad2;
+  float mu_f;        // mu rounded to binary32 (mixed-path kernels)
 };
 
 // Same layout as ba_step_info.
@@ -74,25 +79,30 @@ struct DevCluster {
   int n_cams, n_pts, n_obs, n_free;
   int n_tiles, n_cchunks, n_pairs, n_pchunks;
   double sigma_px, huber_delta, sigma_gnss, sigma_imu;
+  float inv_sigma_f, delta_f, half_inv_s2_f, pad_f;  // binary32 copies of 1/sigma_px, delta, 1/(2 sigma_px^2)
 
   const double* intr;      // [nc][7]
   double* R;               // [2][nc][9]
   double* T;               // [2][nc][3]
-  double* X;               // [2][np][3]
+  // Points, double-buffered.  FP64 path: binary64 [2][np][3].  Mixed path:
+  // double-float [2][np][3] of (hi, lo) binary32 pairs (same 24 bytes/point).
+  double* X;
   const double* R_prior;   // [nc][9]
   const double* T_prior;   // [nc][3]
   const double* R_init;    // [nc][9] state given at create (for reset)
   const double* T_init;    // [nc][3]
-  const double* X_init;    // [np][3]
+  const double* X_init;    // [np][3], same representation as X
   const int* free_idx;     // [nc] -> free index or -1
   const int* cam_of_free;  // [nf]
-  void* camreal;           // Real [nc][20]: R[9], T[3] (unused), intr[7], free flag
+  void* camreal;           // FP64 path: double [nc][20]: R[9], T[3], intr[7], free flag
+  float* camdf;            // mixed path: [2][nc][kCamDf] double-float cameras (layout below)
 
   const Tile* tiles;       // [n_tiles]
   const int* obs_cam;      // [no] point-major
   const int* obs_pt;       // [no] point-major
-  const double* obs_uv;    // [no][2] point-major
-  const float* obs_uv32;   // [no][2] point-major (mixed precision)
+  const double* obs_uv;    // [no][2] point-major, binary64 pixels
+  const float2* obs_chi;   // mixed path: [no] hi part of (u - cx, v - cy)
+  const float2* obs_clo;   // mixed path: [no] lo part of (u - cx, v - cy)
   void* rec;               // Real [no][kRec]
   void* paux;              // Real [np][kPaux]
 
@@ -112,6 +122,7 @@ struct DevCluster {
   double* gc;       // [n]
   double* Dc;       // [n]
   double* dc;       // [n]
+  float* dc32;      // [n] binary32 copy of dc (mixed path)
   double* tilepart; // [n_tiles][2]: cost, point pred
   LmState* lm;
   StepRec* trace;   // [trace_cap]
@@ -162,10 +173,11 @@ void launch_arm(const BatchView& bv, int iters, cudaStream_t st);
 void launch_reset(const BatchView& bv, bool mixed, cudaStream_t st);
 void launch_gather(const BatchView& bv, int iters, LmState* lm_out, StepRec* trace_out, cudaStream_t st);
 void launch_camreal(const BatchView& bv, bool mixed, cudaStream_t st);
-void launch_cost_init(const BatchView& bv, cudaStream_t st);
+void launch_cost_init(const BatchView& bv, bool mixed, cudaStream_t st);
 void launch_iteration(const BatchView& bv, bool mixed, int refine_steps, cudaStream_t st);
 void launch_grad_norm(const BatchView& bv, bool mixed, double* out, cudaStream_t st);
-void launch_reproj(const DevCluster* dcl, const DevCluster& hcl, double* err_pm, cudaStream_t st);
+void launch_reproj(const DevCluster* dcl, const DevCluster& hcl, bool mixed, double* err_pm, cudaStream_t st);
+void launch_export_points(const DevCluster* dcl, const DevCluster& hcl, bool mixed, double* out, cudaStream_t st);
 size_t factor_smem_bytes(int max_n);
 
 }  // namespace bagpu

@@ -13,8 +13,15 @@
 //                   rhs = g_c - W V*^-1 g_p with priors and damping, Cholesky,
 //                   solve, iterative refinement, candidate camera poses.
 //   k_backsub_cost  per observation: dX = Linv^T (q - sum_k Z_k^T dc_k),
-//                   candidate points, FP64 cost at the candidate, pred terms.
+//                   candidate points, cost at the candidate, pred terms.
 //   k_lm_update     per cluster: gain ratio, accept/reject, Nielsen update.
+//
+// Precision.  MIXED = false: every step in binary64.  MIXED = true: the
+// per-observation linearisation, the Schur reductions and the back-
+// substitution run in binary32; the state (points and cameras) is held in
+// double-float, and the cost F(x) that decides the gain ratio is evaluated
+// per observation in double-float and summed in binary64; the reduced
+// camera system is assembled, factored and refined in binary64.
 //
 // Every sum runs in an order fixed by the cluster's presorted tables; there
 // are no atomics.
@@ -22,40 +29,153 @@
 #include <stdio.h>
 
 #include "ba_device.cuh"
+#include "ba_dfloat.cuh"
 #include "ba_internal.h"
 
 namespace bagpu {
 
-constexpr int kCamReal = 20;
+template <bool MIXED> struct RealOf { using T = double; };
+template <> struct RealOf<true> { using T = float; };
 
 template <typename Real> struct Vec2;
 template <> struct Vec2<float> { using T = float2; };
 template <> struct Vec2<double> { using T = double2; };
 
+// ------------------------------------------------------------------ state access
+
+__device__ __forceinline__ const float2* xdf_ptr(const DevCluster& C, int buf, int j) {
+  return reinterpret_cast<const float2*>(C.X) + ((size_t)buf * C.n_pts + j) * 3;
+}
+__device__ __forceinline__ float2* xdf_wptr(const DevCluster& C, int buf, int j) {
+  return reinterpret_cast<float2*>(C.X) + ((size_t)buf * C.n_pts + j) * 3;
+}
+
+// double-float camera record
+struct CamDf {
+  dfl R[9], T[3], f, k1, k2, p1, p2;
+  float free_flag;
+};
+
+__device__ __forceinline__ CamDf load_camdf(const float* p) {
+  CamDf c;
+  float v[kCamDf];
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int i = 0; i < kCamDf / 4; ++i) {
+    const float4 w = q[i];
+    v[4 * i] = w.x; v[4 * i + 1] = w.y; v[4 * i + 2] = w.z; v[4 * i + 3] = w.w;
+  }
+#pragma unroll
+  for (int i = 0; i < 9; ++i) c.R[i] = dfl{v[2 * i], v[2 * i + 1]};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) c.T[i] = dfl{v[18 + 2 * i], v[19 + 2 * i]};
+  c.f = dfl{v[24], v[25]};
+  c.k1 = dfl{v[26], v[27]};
+  c.k2 = dfl{v[28], v[29]};
+  c.p1 = dfl{v[30], v[31]};
+  c.p2 = dfl{v[32], v[33]};
+  c.free_flag = v[34];
+  return c;
+}
+
+__device__ __forceinline__ const float* camdf_ptr(const DevCluster& C, int buf, int k) {
+  return C.camdf + ((size_t)buf * C.n_cams + k) * kCamDf;
+}
+
+// Eq. 5 with Brown distortion in double-float: residual (u - cx, v - cy) - c
+// for a double-float point, every term in double-float.
+__device__ __forceinline__ bool df_residual(const CamDf& c, dfl X0, dfl X1, dfl X2, dfl c0, dfl c1, dfl& e0,
+                                            dfl& e1) {
+  const dfl d0 = df_sub(X0, c.T[0]), d1 = df_sub(X1, c.T[1]), d2 = df_sub(X2, c.T[2]);
+  const dfl z = df_add(df_add(df_mul(c.R[2], d0), df_mul(c.R[5], d1)), df_mul(c.R[8], d2));
+  if (!(z.hi > (float)kMinDepth)) return false;
+  const dfl x = df_add(df_add(df_mul(c.R[0], d0), df_mul(c.R[3], d1)), df_mul(c.R[6], d2));
+  const dfl y = df_add(df_add(df_mul(c.R[1], d0), df_mul(c.R[4], d1)), df_mul(c.R[7], d2));
+  const dfl xn = df_div(x, z), yn = df_div(y, z);
+  const dfl xx = df_mul(xn, xn), yy = df_mul(yn, yn), xy2 = df_mul_f(df_mul(xn, yn), 2.0f);
+  const dfl r2 = df_add(xx, yy);
+  const dfl radm1 = df_mul(r2, df_add(c.k1, df_mul(c.k2, r2)));  // rad - 1
+  const dfl ddx = df_add(df_add(df_mul(xn, radm1), df_mul(c.p1, xy2)), df_mul(c.p2, df_add(r2, df_mul_f(xx, 2.0f))));
+  const dfl ddy = df_add(df_add(df_mul(yn, radm1), df_mul(c.p1, df_add(r2, df_mul_f(yy, 2.0f)))), df_mul(c.p2, xy2));
+  e0 = df_sub(df_mul(c.f, df_add(xn, ddx)), c0);
+  e1 = df_sub(df_mul(c.f, df_add(yn, ddy)), c1);
+  return true;
+}
+
+// 1/2 rho(s) / sigma^2 in double-float, s = e0^2 + e1^2 (Eq. 6: rho on the squared norm)
+__device__ __forceinline__ dfl df_robust_cost(dfl e0, dfl e1, float delta, float half_inv_s2) {
+  const dfl s = df_add(df_mul(e0, e0), df_mul(e1, e1));
+  const float d2 = delta * delta;
+  dfl rho;
+  if (s.hi <= d2) {
+    rho = s;
+  } else {
+    rho = df_add_f(df_mul_f(df_sqrt(s), 2.0f * delta), -d2);
+  }
+  return df_mul_f(rho, half_inv_s2);
+}
+
 // ------------------------------------------------------------------ camera copies
 
-template <typename Real>
+// FP64 path: camera records in binary64 for the per-observation kernels.
 __global__ void k_camreal(BatchView bv) {
   for (int s = blockIdx.x; s < bv.n; s += gridDim.x) {
     const DevCluster& C = bv.cl[s];
     const int cur = C.lm->cur;
-    Real* cr = (Real*)C.camreal;
+    double* cr = (double*)C.camreal;
     for (int k = threadIdx.x; k < C.n_cams; k += blockDim.x) {
       const double* R = C.R + ((size_t)cur * C.n_cams + k) * 9;
       const double* T = C.T + ((size_t)cur * C.n_cams + k) * 3;
-      Real* o = cr + (size_t)kCamReal * k;
-      for (int i = 0; i < 9; ++i) o[i] = (Real)R[i];
-      for (int i = 0; i < 3; ++i) o[9 + i] = (Real)T[i];
-      for (int i = 0; i < 7; ++i) o[12 + i] = (Real)C.intr[7 * k + i];
-      o[19] = C.free_idx[k] >= 0 ? Real(1) : Real(0);
+      double* o = cr + (size_t)kCamReal * k;
+      for (int i = 0; i < 9; ++i) o[i] = R[i];
+      for (int i = 0; i < 3; ++i) o[9 + i] = T[i];
+      for (int i = 0; i < 7; ++i) o[12 + i] = C.intr[7 * k + i];
+      o[19] = C.free_idx[k] >= 0 ? 1.0 : 0.0;
+    }
+  }
+}
+
+// mixed path: double-float record of camera k from (R, T) in binary64
+__device__ void write_camdf(const DevCluster& C, int buf, int k, const double* R, const double* T) {
+  float* o = C.camdf + ((size_t)buf * C.n_cams + k) * kCamDf;
+  for (int i = 0; i < 9; ++i) {
+    const dfl v = df_from_d(R[i]);
+    o[2 * i] = v.hi;
+    o[2 * i + 1] = v.lo;
+  }
+  for (int i = 0; i < 3; ++i) {
+    const dfl v = df_from_d(T[i]);
+    o[18 + 2 * i] = v.hi;
+    o[19 + 2 * i] = v.lo;
+  }
+  const dfl f = df_from_d(C.intr[7 * k]);
+  o[24] = f.hi;
+  o[25] = f.lo;
+  for (int i = 0; i < 4; ++i) {
+    const dfl v = df_from_d(C.intr[7 * k + 3 + i]);
+    o[26 + 2 * i] = v.hi;
+    o[27 + 2 * i] = v.lo;
+  }
+  o[34] = C.free_idx[k] >= 0 ? 1.0f : 0.0f;
+  for (int i = 35; i < kCamDf; ++i) o[i] = 0.0f;
+}
+
+// both buffers of the mixed camera records from the binary64 cameras
+__global__ void k_camdf_all(BatchView bv) {
+  for (int s = blockIdx.x; s < bv.n; s += gridDim.x) {
+    const DevCluster& C = bv.cl[s];
+    for (int idx = threadIdx.x; idx < 2 * C.n_cams; idx += blockDim.x) {
+      const int buf = idx / C.n_cams, k = idx - buf * C.n_cams;
+      write_camdf(C, buf, k, C.R + ((size_t)buf * C.n_cams + k) * 9, C.T + ((size_t)buf * C.n_cams + k) * 3);
     }
   }
 }
 
 // ------------------------------------------------------------------ K1
 
-template <typename Real>
+template <bool MIXED>
 __global__ void __launch_bounds__(256) k_linearize(BatchView bv) {
+  using Real = typename RealOf<MIXED>::T;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -72,7 +192,16 @@ __global__ void __launch_bounds__(256) k_linearize(BatchView bv) {
     int seg_start, seg_end;
     segments(j, lane, seg_start, seg_end);
     const int cur = lm->cur;
-    const Real mu = (Real)lm->mu;
+    Real mu, inv_sigma, delta;
+    if constexpr (MIXED) {
+      mu = lm->mu_f;
+      inv_sigma = C.inv_sigma_f;
+      delta = C.delta_f;
+    } else {
+      mu = lm->mu;
+      inv_sigma = 1.0 / C.sigma_px;
+      delta = C.huber_delta;
+    }
 
     Real r0 = 0, r1 = 0, Jc[12], Jp[6];
 #pragma unroll
@@ -80,25 +209,36 @@ __global__ void __launch_bounds__(256) k_linearize(BatchView bv) {
 #pragma unroll
     for (int i = 0; i < 6; ++i) Jp[i] = 0;
     if (act) {
-      const Real* cr = (const Real*)C.camreal + (size_t)kCamReal * k;
-      Real Rm[9], in[7];
+      Real Rm[9], in[7], dx, dy, dz, uo, vo;
+      bool is_free;
+      if constexpr (MIXED) {
+        const CamDf cd = load_camdf(camdf_ptr(C, cur, k));
+        const float2* xp = xdf_ptr(C, cur, j);
+        const float2 a = xp[0], b = xp[1], c = xp[2];
+        dx = df_to_f(df_sub(dfl{a.x, a.y}, cd.T[0]));
+        dy = df_to_f(df_sub(dfl{b.x, b.y}, cd.T[1]));
+        dz = df_to_f(df_sub(dfl{c.x, c.y}, cd.T[2]));
 #pragma unroll
-      for (int i = 0; i < 9; ++i) Rm[i] = cr[i];
-#pragma unroll
-      for (int i = 0; i < 7; ++i) in[i] = cr[12 + i];
-      const double* Xd = C.X + ((size_t)cur * C.n_pts + j) * 3;
-      const double* Td = C.T + ((size_t)cur * C.n_cams + k) * 3;
-      const Real dx = (Real)(Xd[0] - Td[0]), dy = (Real)(Xd[1] - Td[1]), dz = (Real)(Xd[2] - Td[2]);
-      Real uo, vo;
-      if (sizeof(Real) == 4) {
-        const float2 u = reinterpret_cast<const float2*>(C.obs_uv32)[o];
-        uo = (Real)u.x; vo = (Real)u.y;
+        for (int i = 0; i < 9; ++i) Rm[i] = cd.R[i].hi;
+        in[0] = cd.f.hi; in[1] = 0.f; in[2] = 0.f;
+        in[3] = cd.k1.hi; in[4] = cd.k2.hi; in[5] = cd.p1.hi; in[6] = cd.p2.hi;
+        const float2 ch = C.obs_chi[o];  // observation relative to the principal point
+        uo = ch.x; vo = ch.y;
+        is_free = cd.free_flag != 0.0f;
       } else {
+        const double* cr = (const double*)C.camreal + (size_t)kCamReal * k;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Rm[i] = cr[i];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) in[i] = cr[12 + i];
+        const double* Xd = C.X + ((size_t)cur * C.n_pts + j) * 3;
+        dx = Xd[0] - cr[9]; dy = Xd[1] - cr[10]; dz = Xd[2] - cr[11];
         const double2 u = reinterpret_cast<const double2*>(C.obs_uv)[o];
-        uo = (Real)u.x; vo = (Real)u.y;
+        uo = u.x; vo = u.y;
+        is_free = cr[19] != 0.0;
       }
-      obs_linearize<Real>(Rm, dx, dy, dz, in, uo, vo, (Real)(1.0 / C.sigma_px), (Real)C.huber_delta, r0, r1, Jc, Jp);
-      if (cr[19] == Real(0)) {
+      obs_linearize<Real>(Rm, dx, dy, dz, in, uo, vo, inv_sigma, delta, r0, r1, Jc, Jp);
+      if (!is_free) {
 #pragma unroll
         for (int i = 0; i < 12; ++i) Jc[i] = 0;
       }
@@ -124,7 +264,7 @@ __global__ void __launch_bounds__(256) k_linearize(BatchView bv) {
     g2 = seg_reduce(g2, lane, seg_start, seg_end);
 
     // head: damp, factor V* = L L^T, M = L^-1, q = M g_p
-    Real m00 = 0, m10 = 0, m11 = 0, m20 = 0, m21 = 0, m22 = 0, q0 = 0, q1 = 0, q2 = 0;
+    Real m00 = 0, m10 = 0, m11 = 0, m20 = 0, m21 = 0, m22 = 0;
     if (act && lane == seg_start) {
       const Real d0 = clamp_diag(v00), d1 = clamp_diag(v11), d2 = clamp_diag(v22);
       const Real a00 = v00 + mu * d0, a11 = v11 + mu * d1, a22 = v22 + mu * d2;
@@ -145,9 +285,9 @@ __global__ void __launch_bounds__(256) k_linearize(BatchView bv) {
       m10 = -l10 * m00 * m11;
       m21 = -l21 * m11 * m22;
       m20 = -(l20 * m00 + l21 * m10) * m22;
-      q0 = m00 * g0;
-      q1 = m10 * g0 + m11 * g1;
-      q2 = m20 * g0 + m21 * g1 + m22 * g2;
+      const Real q0 = m00 * g0;
+      const Real q1 = m10 * g0 + m11 * g1;
+      const Real q2 = m20 * g0 + m21 * g1 + m22 * g2;
       Real* pa = (Real*)C.paux + (size_t)kPaux * j;
       pa[0] = m00; pa[1] = m10; pa[2] = m11; pa[3] = m20; pa[4] = m21; pa[5] = m22;
       pa[6] = q0; pa[7] = q1; pa[8] = q2;
@@ -324,8 +464,9 @@ __device__ void chol_solve_warp(const double* A, double* b, int n, int lane) {
   }
 }
 
-template <typename Real>
+template <bool MIXED>
 __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_steps, int assemble_only) {
+  using Real = typename RealOf<MIXED>::T;
   extern __shared__ double sm[];
   __shared__ int fail;
   const int tid = threadIdx.x, bs = blockDim.x;
@@ -449,9 +590,16 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
         for (int idx = tid; idx < n; idx += bs) x[idx] += t[idx];
         __syncthreads();
       }
-      for (int idx = tid; idx < n; idx += bs) C.dc[idx] = x[idx];
+      for (int idx = tid; idx < n; idx += bs) {
+        C.dc[idx] = x[idx];
+        if (MIXED) C.dc32[idx] = (float)x[idx];
+      }
     } else {
-      for (int idx = tid; idx < n; idx += bs) { C.dc[idx] = 0.0; x[idx] = 0.0; }
+      for (int idx = tid; idx < n; idx += bs) {
+        C.dc[idx] = 0.0;
+        if (MIXED) C.dc32[idx] = 0.0f;
+        x[idx] = 0.0;
+      }
     }
     __syncthreads();
     // candidate cameras; per-camera prior cost and pred terms into t[]
@@ -463,21 +611,22 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
         for (int i = 0; i < 9; ++i) Rn[9 * k + i] = Rc[9 * k + i];
         for (int i = 0; i < 3; ++i) Tn[3 * k + i] = Tc[3 * k + i];
         if (f >= 0) { t[2 * f] = 0.0; t[2 * f + 1] = 0.0; }
-        continue;
+      } else {
+        const double* d = x + 6 * f;
+        double E[9];
+        so3_exp(d, E);
+        const double* R0 = Rc + 9 * k;
+        for (int r = 0; r < 3; ++r)
+          for (int c = 0; c < 3; ++c)
+            Rn[9 * k + 3 * r + c] = R0[3 * r] * E[c] + R0[3 * r + 1] * E[3 + c] + R0[3 * r + 2] * E[6 + c];
+        for (int i = 0; i < 3; ++i) Tn[3 * k + i] = Tc[3 * k + i] + d[3 + i];
+        double pc = 0.0;
+        for (int a = 0; a < 6; ++a) pc += d[a] * (mu * C.Dc[6 * f + a] * d[a] + C.gc[6 * f + a]);
+        t[2 * f] = pc;
+        t[2 * f + 1] = prior_terms(Rn + 9 * k, Tn + 3 * k, C.R_prior + 9 * k, C.T_prior + 3 * k, C.sigma_imu,
+                                   C.sigma_gnss, nullptr, nullptr);
       }
-      const double* d = x + 6 * f;
-      double E[9];
-      so3_exp(d, E);
-      const double* R0 = Rc + 9 * k;
-      for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c)
-          Rn[9 * k + 3 * r + c] = R0[3 * r] * E[c] + R0[3 * r + 1] * E[3 + c] + R0[3 * r + 2] * E[6 + c];
-      for (int i = 0; i < 3; ++i) Tn[3 * k + i] = Tc[3 * k + i] + d[3 + i];
-      double pc = 0.0;
-      for (int a = 0; a < 6; ++a) pc += d[a] * (mu * C.Dc[6 * f + a] * d[a] + C.gc[6 * f + a]);
-      t[2 * f] = pc;
-      t[2 * f + 1] = prior_terms(Rn + 9 * k, Tn + 3 * k, C.R_prior + 9 * k, C.T_prior + 3 * k, C.sigma_imu,
-                                 C.sigma_gnss, nullptr, nullptr);
+      if constexpr (MIXED) write_camdf(C, cur ^ 1, k, Rn + 9 * k, Tn + 3 * k);
     }
     __syncthreads();
     if (tid == 0) {
@@ -493,8 +642,9 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
 
 // ------------------------------------------------------------------ K5
 
-template <typename Real>
+template <bool MIXED>
 __global__ void __launch_bounds__(256) k_backsub_cost(BatchView bv) {
+  using Real = typename RealOf<MIXED>::T;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -513,7 +663,8 @@ __global__ void __launch_bounds__(256) k_backsub_cost(BatchView bv) {
     int seg_start, seg_end;
     segments(j, lane, seg_start, seg_end);
     const int cur = lm->cur;
-    const double mu = lm->mu;
+    Real mu_r;
+    if constexpr (MIXED) mu_r = lm->mu_f; else mu_r = lm->mu;
     // t = Z^T dc_k
     Real t0 = 0, t1 = 0, t2 = 0;
     const int f = act ? C.free_idx[k] : -1;
@@ -526,10 +677,18 @@ __global__ void __launch_bounds__(256) k_backsub_cost(BatchView bv) {
         Z[2 * i] = v.x;
         Z[2 * i + 1] = v.y;
       }
-      const double* d = C.dc + 6 * f;
+      Real d[6];
+      if constexpr (MIXED) {
+        const float2* d2 = reinterpret_cast<const float2*>(C.dc32 + 6 * f);
+        const float2 u0 = d2[0], u1 = d2[1], u2 = d2[2];
+        d[0] = u0.x; d[1] = u0.y; d[2] = u1.x; d[3] = u1.y; d[4] = u2.x; d[5] = u2.y;
+      } else {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) d[m] = C.dc[6 * f + m];
+      }
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
-        const Real dm = (Real)d[m];
+        const Real dm = d[m];
         t0 += Z[3 * m] * dm;
         t1 += Z[3 * m + 1] * dm;
         t2 += Z[3 * m + 2] * dm;
@@ -538,37 +697,79 @@ __global__ void __launch_bounds__(256) k_backsub_cost(BatchView bv) {
     t0 = seg_reduce(t0, lane, seg_start, seg_end);
     t1 = seg_reduce(t1, lane, seg_start, seg_end);
     t2 = seg_reduce(t2, lane, seg_start, seg_end);
-    double x0 = 0.0, x1 = 0.0, x2 = 0.0, ppred = 0.0;
+    // head: dX = M^T (q - t), candidate point, pred term
+    Real dX0 = 0, dX1 = 0, dX2 = 0;
+    Real pp = 0;  // dX^T (mu Dp dX + gp), summed below in FP64
     if (act && lane == seg_start) {
       const Real* pa = (const Real*)C.paux + (size_t)kPaux * j;
       const Real v0 = pa[6] - t0, v1 = pa[7] - t1, v2 = pa[8] - t2;
-      // dX = M^T v, M lower (m00, m10, m11, m20, m21, m22)
-      const Real dX0 = pa[0] * v0 + pa[1] * v1 + pa[3] * v2;
-      const Real dX1 = pa[2] * v1 + pa[4] * v2;
-      const Real dX2 = pa[5] * v2;
-      const double* X = C.X + ((size_t)cur * C.n_pts + j) * 3;
-      x0 = X[0] + (double)dX0;
-      x1 = X[1] + (double)dX1;
-      x2 = X[2] + (double)dX2;
-      double* Xn = C.X + ((size_t)(cur ^ 1) * C.n_pts + j) * 3;
-      Xn[0] = x0; Xn[1] = x1; Xn[2] = x2;
-      const double e0 = dX0, e1 = dX1, e2 = dX2;
-      ppred = e0 * (mu * (double)pa[9] * e0 + (double)pa[12]) + e1 * (mu * (double)pa[10] * e1 + (double)pa[13]) +
-              e2 * (mu * (double)pa[11] * e2 + (double)pa[14]);
+      dX0 = pa[0] * v0 + pa[1] * v1 + pa[3] * v2;
+      dX1 = pa[2] * v1 + pa[4] * v2;
+      dX2 = pa[5] * v2;
+      const Real m = mu_r;
+      pp = dX0 * (m * pa[9] * dX0 + pa[12]) + dX1 * (m * pa[10] * dX1 + pa[13]) + dX2 * (m * pa[11] * dX2 + pa[14]);
     }
-    x0 = __shfl_sync(BA_FULL_MASK, x0, seg_start);
-    x1 = __shfl_sync(BA_FULL_MASK, x1, seg_start);
-    x2 = __shfl_sync(BA_FULL_MASK, x2, seg_start);
     double cost = 0.0;
-    if (act) {
-      const double Xn[3] = {x0, x1, x2};
-      const double* Rn = C.R + ((size_t)(cur ^ 1) * C.n_cams + k) * 9;
-      const double* Tn = C.T + ((size_t)(cur ^ 1) * C.n_cams + k) * 3;
-      const double2 u = reinterpret_cast<const double2*>(C.obs_uv)[o];
-      cost = obs_cost(Rn, Tn, C.intr + 7 * k, Xn, u.x, u.y, 0.5 / (C.sigma_px * C.sigma_px), C.huber_delta);
+    if constexpr (MIXED) {
+      dfl x0{0.f, 0.f}, x1{0.f, 0.f}, x2{0.f, 0.f};
+      if (act && lane == seg_start) {
+        const float2* xp = xdf_ptr(C, cur, j);
+        const float2 a = xp[0], b = xp[1], c = xp[2];
+        x0 = df_add_f(dfl{a.x, a.y}, dX0);
+        x1 = df_add_f(dfl{b.x, b.y}, dX1);
+        x2 = df_add_f(dfl{c.x, c.y}, dX2);
+        float2* xn = xdf_wptr(C, cur ^ 1, j);
+        xn[0] = make_float2(x0.hi, x0.lo);
+        xn[1] = make_float2(x1.hi, x1.lo);
+        xn[2] = make_float2(x2.hi, x2.lo);
+      }
+      x0.hi = __shfl_sync(BA_FULL_MASK, x0.hi, seg_start); x0.lo = __shfl_sync(BA_FULL_MASK, x0.lo, seg_start);
+      x1.hi = __shfl_sync(BA_FULL_MASK, x1.hi, seg_start); x1.lo = __shfl_sync(BA_FULL_MASK, x1.lo, seg_start);
+      x2.hi = __shfl_sync(BA_FULL_MASK, x2.hi, seg_start); x2.lo = __shfl_sync(BA_FULL_MASK, x2.lo, seg_start);
+      dfl cst{0.f, 0.f};
+      if (act) {
+        const CamDf cdf = load_camdf(camdf_ptr(C, cur ^ 1, k));
+        const float2 ch = C.obs_chi[o], cl = C.obs_clo[o];
+        dfl e0, e1;
+        if (df_residual(cdf, x0, x1, x2, dfl{ch.x, cl.x}, dfl{ch.y, cl.y}, e0, e1))
+          cst = df_robust_cost(e0, e1, C.delta_f, C.half_inv_s2_f);
+      }
+      // fixed-order warp sum in double-float, one conversion per warp
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const dfl o2{__shfl_down_sync(BA_FULL_MASK, cst.hi, off), __shfl_down_sync(BA_FULL_MASK, cst.lo, off)};
+        cst = df_add(cst, o2);
+      }
+      if (lane == 0) cost = df_to_d(cst);
+    } else {
+      double x0 = 0.0, x1 = 0.0, x2 = 0.0;
+      if (act && lane == seg_start) {
+        const double* X = C.X + ((size_t)cur * C.n_pts + j) * 3;
+        x0 = X[0] + (double)dX0;
+        x1 = X[1] + (double)dX1;
+        x2 = X[2] + (double)dX2;
+        double* Xn = C.X + ((size_t)(cur ^ 1) * C.n_pts + j) * 3;
+        Xn[0] = x0; Xn[1] = x1; Xn[2] = x2;
+      }
+      x0 = __shfl_sync(BA_FULL_MASK, x0, seg_start);
+      x1 = __shfl_sync(BA_FULL_MASK, x1, seg_start);
+      x2 = __shfl_sync(BA_FULL_MASK, x2, seg_start);
+      if (act) {
+        const double Xn[3] = {x0, x1, x2};
+        const double* Rn = C.R + ((size_t)(cur ^ 1) * C.n_cams + k) * 9;
+        const double* Tn = C.T + ((size_t)(cur ^ 1) * C.n_cams + k) * 3;
+        const double2 u = reinterpret_cast<const double2*>(C.obs_uv)[o];
+        cost = obs_cost(Rn, Tn, C.intr + 7 * k, Xn, u.x, u.y, 0.5 / (C.sigma_px * C.sigma_px), C.huber_delta);
+      }
+      cost = warp_sum(cost);
     }
-    cost = warp_sum(cost);
-    ppred = warp_sum(ppred);
+    double ppred;
+    if constexpr (MIXED) {
+      const float ps = warp_sum(pp);  // binary32 warp sum, one conversion per warp
+      ppred = lane == 0 ? (double)ps : 0.0;
+    } else {
+      ppred = warp_sum((double)pp);
+    }
     if (lane == 0) {
       C.tilepart[2 * local] = cost;
       C.tilepart[2 * local + 1] = ppred;
@@ -578,6 +779,7 @@ __global__ void __launch_bounds__(256) k_backsub_cost(BatchView bv) {
 
 // ------------------------------------------------------------------ cost at the current state
 
+template <bool MIXED>
 __global__ void __launch_bounds__(256) k_cost_tiles(BatchView bv) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -590,15 +792,36 @@ __global__ void __launch_bounds__(256) k_cost_tiles(BatchView bv) {
     const Tile tl = C.tiles[local];
     const int cur = lm->cur;
     double cost = 0.0;
-    if (lane < tl.n_obs) {
-      const int o = tl.obs_begin + lane;
-      const int k = C.obs_cam[o], j = C.obs_pt[o];
-      const double2 u = reinterpret_cast<const double2*>(C.obs_uv)[o];
-      cost = obs_cost(C.R + ((size_t)cur * C.n_cams + k) * 9, C.T + ((size_t)cur * C.n_cams + k) * 3, C.intr + 7 * k,
-                      C.X + ((size_t)cur * C.n_pts + j) * 3, u.x, u.y, 0.5 / (C.sigma_px * C.sigma_px),
-                      C.huber_delta);
+    if constexpr (MIXED) {
+      dfl cst{0.f, 0.f};
+      if (lane < tl.n_obs) {
+        const int o = tl.obs_begin + lane;
+        const int k = C.obs_cam[o], j = C.obs_pt[o];
+        const CamDf cdf = load_camdf(camdf_ptr(C, cur, k));
+        const float2* xp = xdf_ptr(C, cur, j);
+        const float2 a = xp[0], b = xp[1], c = xp[2];
+        const float2 ch = C.obs_chi[o], cl = C.obs_clo[o];
+        dfl e0, e1;
+        if (df_residual(cdf, dfl{a.x, a.y}, dfl{b.x, b.y}, dfl{c.x, c.y}, dfl{ch.x, cl.x}, dfl{ch.y, cl.y}, e0, e1))
+          cst = df_robust_cost(e0, e1, C.delta_f, C.half_inv_s2_f);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const dfl o2{__shfl_down_sync(BA_FULL_MASK, cst.hi, off), __shfl_down_sync(BA_FULL_MASK, cst.lo, off)};
+        cst = df_add(cst, o2);
+      }
+      if (lane == 0) cost = df_to_d(cst);
+    } else {
+      if (lane < tl.n_obs) {
+        const int o = tl.obs_begin + lane;
+        const int k = C.obs_cam[o], j = C.obs_pt[o];
+        const double2 u = reinterpret_cast<const double2*>(C.obs_uv)[o];
+        cost = obs_cost(C.R + ((size_t)cur * C.n_cams + k) * 9, C.T + ((size_t)cur * C.n_cams + k) * 3,
+                        C.intr + 7 * k, C.X + ((size_t)cur * C.n_pts + j) * 3, u.x, u.y,
+                        0.5 / (C.sigma_px * C.sigma_px), C.huber_delta);
+      }
+      cost = warp_sum(cost);
     }
-    cost = warp_sum(cost);
     if (lane == 0) C.tilepart[2 * local] = cost;
   }
 }
@@ -641,7 +864,7 @@ __global__ void __launch_bounds__(256) k_cost_init(BatchView bv) {
 
 // ------------------------------------------------------------------ K6
 
-template <typename Real>
+template <bool MIXED>
 __global__ void __launch_bounds__(256) k_lm_update(BatchView bv) {
   __shared__ double red[8];
   __shared__ int s_cur, s_act;
@@ -689,18 +912,19 @@ __global__ void __launch_bounds__(256) k_lm_update(BatchView bv) {
       lm->iter += 1;
       if (lm->iter >= lm->iters_target) lm->active = 0;
       lm->pt_fail = 0;
+      lm->mu_f = (float)lm->mu;
       s_cur = lm->cur;
       s_act = accepted;
     }
     __syncthreads();
-    if (s_act) {  // refresh the working-precision camera copies for the new state
-      Real* cr = (Real*)C.camreal;
+    if (!MIXED && s_act) {  // refresh the binary64 camera records for the new state
+      double* cr = (double*)C.camreal;
       for (int k = threadIdx.x; k < C.n_cams; k += blockDim.x) {
         const double* R = C.R + ((size_t)s_cur * C.n_cams + k) * 9;
         const double* T = C.T + ((size_t)s_cur * C.n_cams + k) * 3;
-        Real* o = cr + (size_t)kCamReal * k;
-        for (int i = 0; i < 9; ++i) o[i] = (Real)R[i];
-        for (int i = 0; i < 3; ++i) o[9 + i] = (Real)T[i];
+        double* o = cr + (size_t)kCamReal * k;
+        for (int i = 0; i < 9; ++i) o[i] = R[i];
+        for (int i = 0; i < 3; ++i) o[9 + i] = T[i];
       }
     }
     __syncthreads();
@@ -733,14 +957,38 @@ __global__ void k_grad_norm(BatchView bv, double* out) {
   }
 }
 
-__global__ void k_reproj(const DevCluster* dcl, double* err) {
+__device__ __forceinline__ void point_f64(const DevCluster& C, bool mixed, int buf, int j, double X[3]) {
+  if (mixed) {
+    const float2* p = xdf_ptr(C, buf, j);
+    for (int i = 0; i < 3; ++i) X[i] = (double)p[i].x + (double)p[i].y;
+  } else {
+    const double* p = C.X + ((size_t)buf * C.n_pts + j) * 3;
+    for (int i = 0; i < 3; ++i) X[i] = p[i];
+  }
+}
+
+__global__ void k_reproj(const DevCluster* dcl, int mixed, double* err) {
   const DevCluster& C = *dcl;
   const int cur = C.lm->cur;
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < C.n_obs; o += gridDim.x * blockDim.x) {
     const int k = C.obs_cam[o], j = C.obs_pt[o];
     const double2 u = reinterpret_cast<const double2*>(C.obs_uv)[o];
+    double X[3];
+    point_f64(C, mixed, cur, j, X);
     err[o] = obs_error_norm(C.R + ((size_t)cur * C.n_cams + k) * 9, C.T + ((size_t)cur * C.n_cams + k) * 3,
-                            C.intr + 7 * k, C.X + ((size_t)cur * C.n_pts + j) * 3, u.x, u.y);
+                            C.intr + 7 * k, X, u.x, u.y);
+  }
+}
+
+__global__ void k_export_points(const DevCluster* dcl, int mixed, double* out) {
+  const DevCluster& C = *dcl;
+  const int cur = C.lm->cur;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < C.n_pts; j += gridDim.x * blockDim.x) {
+    double X[3];
+    point_f64(C, mixed, cur, j, X);
+    out[3 * j] = X[0];
+    out[3 * j + 1] = X[1];
+    out[3 * j + 2] = X[2];
   }
 }
 
@@ -761,7 +1009,8 @@ __global__ void k_arm(BatchView bv, int iters) {
   }
 }
 
-// Restore the state given at create into both state buffers and reset LM control.
+// Restore the state given at create into both state buffers and reset LM
+// control.  The copy is representation-agnostic (8-byte words).
 __global__ void k_reset(BatchView bv) {
   for (int s = blockIdx.y; s < bv.n; s += gridDim.y) {
     const DevCluster& C = bv.cl[s];
@@ -777,6 +1026,7 @@ __global__ void k_reset(BatchView bv) {
       if (threadIdx.x == 0) {
         LmState* lm = C.lm;
         lm->mu = lm->mu0;
+        lm->mu_f = (float)lm->mu0;
         lm->nu = 2.0;
         lm->F = 0.0;
         lm->F_new = 0.0;
@@ -886,6 +1136,11 @@ void launch_arm(const BatchView& bv, int iters, cudaStream_t st) {
   LAUNCH(KK_OTHER, st, k_arm<<<(bv.n + 127) / 128, 128, 0, st>>>(bv, iters));
 }
 
+void launch_camreal(const BatchView& bv, bool mixed, cudaStream_t st) {
+  if (mixed) LAUNCH(KK_OTHER, st, k_camdf_all<<<grid_for(bv.n, 1, 65535), 64, 0, st>>>(bv));
+  else LAUNCH(KK_OTHER, st, k_camreal<<<grid_for(bv.n, 1, 65535), 64, 0, st>>>(bv));
+}
+
 void launch_reset(const BatchView& bv, bool mixed, cudaStream_t st) {
   dim3 grid(64, bv.n < 65535 ? bv.n : 65535);
   LAUNCH(KK_OTHER, st, k_reset<<<grid, 256, 0, st>>>(bv));
@@ -896,61 +1151,68 @@ void launch_gather(const BatchView& bv, int iters, LmState* lm_out, StepRec* tra
   LAUNCH(KK_OTHER, st, k_gather<<<bv.n < 65535 ? bv.n : 65535, 128, 0, st>>>(bv, iters, lm_out, trace_out));
 }
 
-void launch_camreal(const BatchView& bv, bool mixed, cudaStream_t st) {
-  if (mixed) LAUNCH(KK_OTHER, st, k_camreal<float><<<grid_for(bv.n, 1, 65535), 64, 0, st>>>(bv));
-  else LAUNCH(KK_OTHER, st, k_camreal<double><<<grid_for(bv.n, 1, 65535), 64, 0, st>>>(bv));
-}
-
-void launch_cost_init(const BatchView& bv, cudaStream_t st) {
+template <bool MIXED>
+static void launch_cost_init_t(const BatchView& bv, cudaStream_t st) {
   const int sms = num_sms();
-  LAUNCH(KK_COST_TILES, st, k_cost_tiles<<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
+  LAUNCH(KK_COST_TILES, st, k_cost_tiles<MIXED><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
   LAUNCH(KK_COST_INIT, st, k_cost_init<<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv));
 }
 
-template <typename Real>
+void launch_cost_init(const BatchView& bv, bool mixed, cudaStream_t st) {
+  if (mixed) launch_cost_init_t<true>(bv, st);
+  else launch_cost_init_t<false>(bv, st);
+}
+
+template <bool MIXED>
 static void launch_iteration_t(const BatchView& bv, int refine_steps, cudaStream_t st) {
+  using Real = typename RealOf<MIXED>::T;
   const int sms = num_sms();
-  LAUNCH(KK_LINEARIZE, st, k_linearize<Real><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
+  LAUNCH(KK_LINEARIZE, st, k_linearize<MIXED><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
   LAUNCH(KK_CAM_REDUCE, st, k_cam_reduce<Real><<<grid_for(bv.total_cchunks, 1, sms * 32), 128, 0, st>>>(bv));
   if (bv.total_pchunks > 0)
     LAUNCH(KK_PAIR_REDUCE, st, k_pair_reduce<Real><<<grid_for(bv.total_pchunks, 8, sms * 16), 256, 0, st>>>(bv));
   const size_t smem = factor_smem_bytes(bv.max_n);
-  LAUNCH(KK_FACTOR, st, k_factor_solve<Real><<<grid_for(bv.n, 1, 65535), 512, smem, st>>>(bv, refine_steps, 0));
-  LAUNCH(KK_BACKSUB, st, k_backsub_cost<Real><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
-  LAUNCH(KK_LM_UPDATE, st, k_lm_update<Real><<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv));
+  LAUNCH(KK_FACTOR, st, k_factor_solve<MIXED><<<grid_for(bv.n, 1, 65535), 512, smem, st>>>(bv, refine_steps, 0));
+  LAUNCH(KK_BACKSUB, st, k_backsub_cost<MIXED><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
+  LAUNCH(KK_LM_UPDATE, st, k_lm_update<MIXED><<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv));
 }
 
 void launch_iteration(const BatchView& bv, bool mixed, int refine_steps, cudaStream_t st) {
-  if (mixed) launch_iteration_t<float>(bv, refine_steps, st);
-  else launch_iteration_t<double>(bv, refine_steps, st);
+  if (mixed) launch_iteration_t<true>(bv, refine_steps, st);
+  else launch_iteration_t<false>(bv, refine_steps, st);
 }
 
-template <typename Real>
+template <bool MIXED>
 static void launch_grad_norm_t(const BatchView& bv, double* out, cudaStream_t st) {
+  using Real = typename RealOf<MIXED>::T;
   const int sms = num_sms();
-  LAUNCH(KK_LINEARIZE, st, k_linearize<Real><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
+  LAUNCH(KK_LINEARIZE, st, k_linearize<MIXED><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
   LAUNCH(KK_CAM_REDUCE, st, k_cam_reduce<Real><<<grid_for(bv.total_cchunks, 1, sms * 32), 128, 0, st>>>(bv));
   if (bv.total_pchunks > 0)
     LAUNCH(KK_PAIR_REDUCE, st, k_pair_reduce<Real><<<grid_for(bv.total_pchunks, 8, sms * 16), 256, 0, st>>>(bv));
   LAUNCH(KK_FACTOR, st,
-         k_factor_solve<Real><<<grid_for(bv.n, 1, 65535), 512, factor_smem_bytes(bv.max_n), st>>>(bv, 0, 1));
+         k_factor_solve<MIXED><<<grid_for(bv.n, 1, 65535), 512, factor_smem_bytes(bv.max_n), st>>>(bv, 0, 1));
   LAUNCH(KK_OTHER, st, k_grad_norm<Real><<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv, out));
 }
 
 void launch_grad_norm(const BatchView& bv, bool mixed, double* out, cudaStream_t st) {
-  if (mixed) launch_grad_norm_t<float>(bv, out, st);
-  else launch_grad_norm_t<double>(bv, out, st);
+  if (mixed) launch_grad_norm_t<true>(bv, out, st);
+  else launch_grad_norm_t<false>(bv, out, st);
 }
 
-void launch_reproj(const DevCluster* dcl, const DevCluster& hcl, double* err_pm, cudaStream_t st) {
-  LAUNCH(KK_OTHER, st, k_reproj<<<grid_for(hcl.n_obs, 256, num_sms() * 8), 256, 0, st>>>(dcl, err_pm));
+void launch_reproj(const DevCluster* dcl, const DevCluster& hcl, bool mixed, double* err_pm, cudaStream_t st) {
+  LAUNCH(KK_OTHER, st, k_reproj<<<grid_for(hcl.n_obs, 256, num_sms() * 8), 256, 0, st>>>(dcl, mixed, err_pm));
+}
+
+void launch_export_points(const DevCluster* dcl, const DevCluster& hcl, bool mixed, double* out, cudaStream_t st) {
+  LAUNCH(KK_OTHER, st, k_export_points<<<grid_for(hcl.n_pts, 256, num_sms() * 8), 256, 0, st>>>(dcl, mixed, out));
 }
 
 cudaError_t set_kernel_attributes(int max_n) {
   const size_t smem = factor_smem_bytes(max_n);
-  cudaError_t e = cudaFuncSetAttribute(k_factor_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_factor_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_factor_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaFuncSetAttribute(k_factor_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 }  // namespace bagpu

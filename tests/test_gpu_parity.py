@@ -138,6 +138,35 @@ def test_linearize_cost_and_gradient(ba):
     assert lin["n_free"] == 5
 
 
+@pytest.mark.parametrize("fixed", [None, (1,)])
+def test_mixed_cost_evaluation_matches_fp64(ba, fixed):
+    """The mixed path evaluates F in double-float per observation and sums in
+    binary64: it must agree with the oracle's binary64 F to ~1e-12."""
+    c = sg.cluster_c1(fixed=fixed)
+    P = O.Problem(c)
+    F = O.cost(P, c["R0"], c["T0"], c["X0"])
+    with ba.Context(precision=ba.BA_MIXED) as ctx:
+        cid = ctx.create_cluster(c)
+        lin = ctx.linearize(cid)
+        R, T, X = ctx.get_state(cid)
+    assert lin["cost"] == pytest.approx(F, rel=1e-11)
+    # the initial state round-trips exactly through the double-float representation
+    assert np.array_equal(T, c["T0"]) and np.array_equal(R, c["R0"].reshape(-1, 9))
+    assert np.abs(X - c["X0"]).max() <= 1e-12
+
+
+def test_mixed_step_decisions_follow_fp64(ba):
+    """Mixed and FP64 paths take the same accept/reject decisions on c1 and
+    reach costs within 1e-6 relative after every step."""
+    c = sg.cluster_c1()
+    with ba.Context(precision=ba.BA_MIXED) as cm, ba.Context(precision=ba.BA_FP64) as cd:
+        a, b = cm.create_cluster(c), cd.create_cluster(c)
+        tm, td = cm.run(a, 10), cd.run(b, 10)
+    for x, y in zip(tm, td):
+        assert x["accepted"] == y["accepted"]
+        assert x["F_after"] == pytest.approx(y["F_after"], rel=1e-6)
+
+
 def test_reprojection_errors_match_oracle(ba):
     c = sg.tiny_cluster(7, 2, 2, 50)
     P = O.Problem(c)
