@@ -230,6 +230,28 @@ BA_API ba_status ba_launch_count(ba_ctx* ctx, uint64_t* out);
  * collected when the context was created with BA_FLAG_KERNEL_TIMING. */
 BA_API ba_status ba_kernel_stats(ba_ctx* ctx, double* ms, uint64_t* launches, int32_t n, int32_t reset);
 
+/* Robust cost F(x) of a cluster given entirely in caller-owned device memory,
+ * computed without allocating anything.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate once running, such as
+ * onboard flight software that reserves all its memory at start-up, or a
+ * process whose device memory belongs to another allocator.
+ *   d       every pointer a device pointer (d->ptr_kind must be
+ *           BA_PTR_DEVICE); R, T, X are the state at which F is evaluated;
+ *           fixed may be NULL; mu0, warm_* are ignored.  Observations may be
+ *           in any order.  Indices are not checked on the host: an
+ *           out-of-range index makes *F_out NaN (never a fault).
+ *   stream  cudaStream_t to run on (NULL = the legacy default stream); the
+ *           call enqueues two kernels and returns without waiting.
+ *   F_out   device pointer to one double, written when the kernels finish.
+ * Scratch is a 512 KiB file-scope device array that every GPU loading the
+ * library holds until exit, so n_obs may be at most 67,108,864; larger
+ * problems are rejected with BA_ERR_INVALID.  The array is shared by all
+ * calls: calls that overlap on the GPU race, and must be ordered (one
+ * stream, or events).  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  No
+ * cudaMalloc, cudaFree or other allocating routine is called. */
+BA_API ba_status ba_cost_noalloc(const ba_cluster_desc* d, void* stream, double* F_out);
+
 BA_API ba_status ba_destroy_cluster(ba_ctx* ctx, ba_cluster_id id);
 BA_API ba_status ba_shutdown(ba_ctx* ctx);
 BA_API const char* ba_status_string(ba_status s);

@@ -84,8 +84,8 @@ class ba_result(ctypes.Structure):
 
 EXPORTS = ["ba_init", "ba_create_cluster", "ba_linearize", "ba_solve_step", "ba_run", "ba_solve_batch", "ba_reset",
            "ba_reset_batch", "ba_submit", "ba_poll", "ba_get_state", "ba_reprojection_errors", "ba_memory_in_use",
-           "ba_launch_count", "ba_kernel_stats", "ba_destroy_cluster", "ba_shutdown", "ba_status_string",
-           "ba_last_error"]
+           "ba_launch_count", "ba_kernel_stats", "ba_cost_noalloc", "ba_destroy_cluster", "ba_shutdown",
+           "ba_status_string", "ba_last_error"]
 
 _lib = None
 _lock = threading.Lock()
@@ -114,6 +114,7 @@ def lib(build: bool = True):
             L.ba_reset_batch.argtypes = [vp, ctypes.POINTER(u64), ctypes.c_int32]
             L.ba_launch_count.argtypes = [vp, ctypes.POINTER(u64)]
             L.ba_kernel_stats.argtypes = [vp, _dp, ctypes.POINTER(u64), ctypes.c_int32, ctypes.c_int32]
+            L.ba_cost_noalloc.argtypes = [ctypes.POINTER(ba_cluster_desc), vp, _dp]
             L.ba_submit.argtypes = [vp, u64, ctypes.POINTER(ba_solve_opts), ctypes.POINTER(u64)]
             L.ba_poll.argtypes = [vp, u64, ctypes.POINTER(ba_result)]
             L.ba_get_state.argtypes = [vp, u64, _dp, _dp, _dp, ctypes.c_int32]
