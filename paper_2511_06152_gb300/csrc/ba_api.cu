@@ -33,6 +33,7 @@ struct Cluster {
   DevCluster h{};                 // descriptor with device pointers
   DevCluster* d_desc = nullptr;   // device copy of h
   std::vector<int> pm_to_user;    // point-major position -> caller observation index
+  std::vector<int> pt_inv;        // caller point index -> internal point index
   std::atomic<int> in_service{0}; // queued or running in the serving scheduler
 };
 
@@ -195,8 +196,8 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
     if (!c) return set_err(ctx, BA_ERR_NOT_FOUND, "unknown cluster id in batch");
     descs[i] = c->h;
     pre[i + 1] = pre[i] + c->h.n_tiles;
-    pre[(n + 1) + i + 1] = pre[(n + 1) + i] + c->h.n_cchunks;
-    pre[2 * (n + 1) + i + 1] = pre[2 * (n + 1) + i] + c->h.n_pchunks;
+    pre[(n + 1) + i + 1] = pre[(n + 1) + i] + c->h.n_chunks;
+    pre[2 * (n + 1) + i + 1] = pre[2 * (n + 1) + i] + c->h.n_free + c->h.n_pairs;
     max_n = std::max(max_n, 6 * c->h.n_free);
   }
   ba_status st = ensure_attrs(ctx, max_n);
@@ -208,6 +209,10 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
   const size_t o_pre = L.add(sizeof(int) * pre.size());
   const size_t o_lm = L.add(sizeof(LmState) * n);
   const size_t o_gn = L.add(sizeof(double) * n);
+  const size_t o_ord = L.add(sizeof(int) * n);
+  std::vector<int> order(n);  // factor kernel: largest reduced systems first
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return descs[a].n_free > descs[b].n_free; });
   p->dbuf_bytes = L.off;
   if (ctx->budget && ctx->mem + p->dbuf_bytes > ctx->budget) {
     delete p;
@@ -222,6 +227,8 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
   e = cudaMemcpyAsync(p->dbuf + o_desc, descs.data(), sizeof(DevCluster) * n, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->dbuf + o_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->dbuf + o_ord, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     ctx->mem -= p->dbuf_bytes;
@@ -231,12 +238,13 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
   const int* dpre = (const int*)(p->dbuf + o_pre);
   p->bv.cl = (const DevCluster*)(p->dbuf + o_desc);
   p->bv.tile_pre = dpre;
-  p->bv.cchunk_pre = dpre + (n + 1);
-  p->bv.pchunk_pre = dpre + 2 * (n + 1);
+  p->bv.chunk_pre = dpre + (n + 1);
+  p->bv.item_pre = dpre + 2 * (n + 1);
+  p->bv.factor_order = (const int*)(p->dbuf + o_ord);
   p->bv.n = n;
   p->bv.total_tiles = pre[n];
-  p->bv.total_cchunks = pre[(n + 1) + n];
-  p->bv.total_pchunks = pre[2 * (n + 1) + n];
+  p->bv.total_chunks = pre[(n + 1) + n];
+  p->bv.total_items = pre[2 * (n + 1) + n];
   p->bv.max_n = max_n;
   p->lm_out = (LmState*)(p->dbuf + o_lm);
   p->gnorm = (double*)(p->dbuf + o_gn);
@@ -382,14 +390,44 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   if (nf > kMaxFreeSmall)
     return set_err(ctx, BA_ERR_INVALID, "more than 32 free cameras in one cluster is not supported");
 
-  // point-major order: stable counting sort by point, then by camera within a point
+  // internal point order: Morton code of the initial ground position (x, y),
+  // ties by the caller's index, so that consecutive points share cameras
+  std::vector<int> perm(np), inv(np);  // internal -> caller, caller -> internal
+  {
+    double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300;
+    for (int j = 0; j < np; ++j) {
+      xmin = std::min(xmin, X[3 * (size_t)j]); xmax = std::max(xmax, X[3 * (size_t)j]);
+      ymin = std::min(ymin, X[3 * (size_t)j + 1]); ymax = std::max(ymax, X[3 * (size_t)j + 1]);
+    }
+    const double sx = xmax > xmin ? 65535.0 / (xmax - xmin) : 0.0, sy = ymax > ymin ? 65535.0 / (ymax - ymin) : 0.0;
+    auto spread = [](uint32_t v) {
+      v &= 0xffffu;
+      v = (v | (v << 8)) & 0x00ff00ffu;
+      v = (v | (v << 4)) & 0x0f0f0f0fu;
+      v = (v | (v << 2)) & 0x33333333u;
+      v = (v | (v << 1)) & 0x55555555u;
+      return v;
+    };
+    std::vector<std::pair<uint32_t, int>> key(np);
+    for (int j = 0; j < np; ++j) {
+      const uint32_t qx = (uint32_t)((X[3 * (size_t)j] - xmin) * sx), qy = (uint32_t)((X[3 * (size_t)j + 1] - ymin) * sy);
+      key[j] = {spread(qx) | (spread(qy) << 1), j};
+    }
+    std::sort(key.begin(), key.end());
+    for (int i = 0; i < np; ++i) {
+      perm[i] = key[i].second;
+      inv[key[i].second] = i;
+    }
+  }
+
+  // point-major order: counting sort by internal point, then by camera within a point
   std::vector<int> cnt((size_t)np + 1, 0), pm(no);
-  for (int i = 0; i < no; ++i) cnt[opt[i] + 1]++;
+  for (int i = 0; i < no; ++i) cnt[inv[opt[i]] + 1]++;
   for (int j = 0; j < np; ++j) cnt[j + 1] += cnt[j];
   std::vector<int> pt_start(cnt);
   {
     std::vector<int> pos(cnt.begin(), cnt.end() - 1);
-    for (int i = 0; i < no; ++i) pm[pos[opt[i]]++] = i;
+    for (int i = 0; i < no; ++i) pm[pos[inv[opt[i]]]++] = i;
   }
   for (int j = 0; j < np; ++j) {
     const int s = pt_start[j], e = pt_start[j + 1];
@@ -406,6 +444,12 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
     for (int a = s + 1; a < e; ++a)
       if (ocam[pm[a]] == ocam[pm[a - 1]]) return set_err(ctx, BA_ERR_INVALID, "repeated (camera, point) observation");
   }
+  // camera of each point-major observation, and its point
+  std::vector<int> pcam(no), ppt(no);
+  for (int p = 0; p < no; ++p) {
+    pcam[p] = ocam[pm[p]];
+    ppt[p] = inv[opt[pm[p]]];
+  }
 
   // tiles: runs of whole points with at most 32 observations
   std::vector<Tile> tiles;
@@ -416,7 +460,6 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
       if (L == 0) continue;
       if (tn + L > 32) {
         tiles.push_back(Tile{tb, tn});
-        tb = pt_start[j];
         tn = 0;
       }
       if (tn == 0) tb = pt_start[j];
@@ -425,79 +468,156 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
     if (tn > 0) tiles.push_back(Tile{tb, tn});
   }
 
-  // camera-major list of free-camera observations (point-major order within a camera)
-  std::vector<int> ccnt((size_t)nf + 1, 0);
-  for (int p = 0; p < no; ++p) {
-    const int f = free_idx[ocam[pm[p]]];
-    if (f >= 0) ccnt[f + 1]++;
-  }
-  for (int f = 0; f < nf; ++f) ccnt[f + 1] += ccnt[f];
-  std::vector<int> cam_obs(ccnt[nf]);
+  // chunks of consecutive tiles with at most chunk_obs() observations, and per
+  // chunk the observation lists of its free cameras and the observation pairs
+  // of its co-visible camera pairs (all in increasing point-major order)
+  const bool mixed = ctx->mixed;
+  const int ch_tiles = chunk_tiles(mixed);
+  std::vector<Chunk> chunks;
+  std::vector<Job> jobs;
+  std::vector<int> mjobs;
+  std::vector<unsigned short> cm_list;
+  std::vector<unsigned int> pent;
+  std::vector<int> pair_of((size_t)nf * nf, -1);  // (fa, fb) -> pair index
+  std::vector<int2> pair_key;
+  std::vector<std::vector<int>> cam_slot_lists(nf), pair_slot_lists;
+  int n_cslots = 0, n_pslots = 0;
   {
-    std::vector<int> pos(ccnt.begin(), ccnt.end() - 1);
-    for (int p = 0; p < no; ++p) {
-      const int f = free_idx[ocam[pm[p]]];
-      if (f >= 0) cam_obs[pos[f]++] = p;
-    }
-  }
-  std::vector<ChunkItem> cchunks;
-  std::vector<int> cam_part_begin((size_t)nf + 1, 0);
-  for (int f = 0; f < nf; ++f) {
-    cam_part_begin[f] = (int)cchunks.size();
-    for (int b = ccnt[f]; b < ccnt[f + 1]; b += kCamChunk)
-      cchunks.push_back(ChunkItem{f, b, std::min(kCamChunk, ccnt[f + 1] - b), 0});
-  }
-  cam_part_begin[nf] = (int)cchunks.size();
-
-  // camera pairs (free a < free b) sharing a point, entries sorted by (pair, point)
-  std::vector<int> pcnt((size_t)nf * nf + 1, 0);
-  for (int j = 0; j < np; ++j) {
-    const int s = pt_start[j], e = pt_start[j + 1];
-    for (int a = s; a < e; ++a) {
-      const int fa = free_idx[ocam[pm[a]]];
-      if (fa < 0) continue;
-      for (int b = a + 1; b < e; ++b) {
-        const int fb = free_idx[ocam[pm[b]]];
-        if (fb >= 0) pcnt[(size_t)fa * nf + fb + 1]++;
+    std::vector<std::vector<unsigned short>> per_cam(nf);
+    std::vector<std::vector<unsigned int>> per_pair;  // indexed by local pair
+    std::vector<int> local_pair_of((size_t)nf * nf, -1);
+    std::vector<int> lp_keys;
+    size_t t = 0;
+    while (t < tiles.size()) {
+      Chunk ch{};
+      ch.obs_begin = tiles[t].obs_begin;
+      ch.tile_begin = (int)t;
+      while (t < tiles.size() && ch.n_tiles < ch_tiles) {
+        ch.n_obs += tiles[t].n_obs;
+        ++t;
+        ++ch.n_tiles;
       }
-    }
-  }
-  for (size_t q = 0; q < (size_t)nf * nf; ++q) pcnt[q + 1] += pcnt[q];
-  std::vector<int2> pair_ent(pcnt[(size_t)nf * nf]);
-  {
-    std::vector<int> pos(pcnt.begin(), pcnt.end() - 1);
-    for (int j = 0; j < np; ++j) {
-      const int s = pt_start[j], e = pt_start[j + 1];
-      for (int a = s; a < e; ++a) {
-        const int fa = free_idx[ocam[pm[a]]];
-        if (fa < 0) continue;
-        for (int b = a + 1; b < e; ++b) {
-          const int fb = free_idx[ocam[pm[b]]];
-          if (fb >= 0) pair_ent[pos[(size_t)fa * nf + fb]++] = make_int2(a, b);
+      for (auto& v : per_cam) v.clear();
+      per_pair.clear();
+      lp_keys.clear();
+      for (int p = ch.obs_begin; p < ch.obs_begin + ch.n_obs; ++p) {
+        const int f = free_idx[pcam[p]];
+        if (f >= 0) per_cam[f].push_back((unsigned short)(p - ch.obs_begin));
+      }
+      // pairs, point by point (observations of a point are sorted by camera)
+      for (int p = ch.obs_begin; p < ch.obs_begin + ch.n_obs;) {
+        int e = p;
+        while (e < ch.obs_begin + ch.n_obs && ppt[e] == ppt[p]) ++e;
+        for (int a = p; a < e; ++a) {
+          const int fa = free_idx[pcam[a]];
+          if (fa < 0) continue;
+          for (int b = a + 1; b < e; ++b) {
+            const int fb = free_idx[pcam[b]];
+            if (fb < 0) continue;
+            const size_t key = (size_t)fa * nf + fb;
+            if (local_pair_of[key] < 0) {
+              local_pair_of[key] = (int)per_pair.size();
+              per_pair.emplace_back();
+              lp_keys.push_back((int)key);
+            }
+            per_pair[local_pair_of[key]].push_back((unsigned)(a - ch.obs_begin) | ((unsigned)(b - ch.obs_begin) << 16));
+          }
+        }
+        p = e;
+      }
+      // jobs: the chunk's free cameras, then its camera pairs (both by
+      // decreasing item count, ties by index / key)
+      ch.job_begin = (int)jobs.size();
+      std::vector<int> corder;
+      for (int f = 0; f < nf; ++f)
+        if (!per_cam[f].empty()) corder.push_back(f);
+      std::stable_sort(corder.begin(), corder.end(),
+                       [&](int x, int y) { return per_cam[x].size() > per_cam[y].size(); });
+      for (int f : corder) {
+        Job jb{n_cslots++, (int)cm_list.size(), (int)per_cam[f].size(), 0, 1};
+        cam_slot_lists[f].push_back(jb.slot);
+        cm_list.insert(cm_list.end(), per_cam[f].begin(), per_cam[f].end());
+        jobs.push_back(jb);
+      }
+      ch.n_lc = (int)corder.size();
+      std::vector<int> order(lp_keys.size());
+      for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+      std::sort(order.begin(), order.end(), [&](int x, int y) {
+        if (per_pair[x].size() != per_pair[y].size()) return per_pair[x].size() > per_pair[y].size();
+        return lp_keys[x] < lp_keys[y];
+      });
+      for (int li : order) {
+        const int key = lp_keys[li];
+        if (pair_of[key] < 0) {
+          pair_of[key] = (int)pair_key.size();
+          pair_key.push_back(make_int2(key / nf, key % nf));
+          pair_slot_lists.emplace_back();
+        }
+        Job jb{n_pslots++, (int)pent.size(), (int)per_pair[li].size(), 0, 1};
+        pair_slot_lists[pair_of[key]].push_back(jb.slot);
+        pent.insert(pent.end(), per_pair[li].begin(), per_pair[li].end());
+        jobs.push_back(jb);
+        local_pair_of[key] = -1;
+      }
+      ch.n_lp = (int)order.size();
+      // lanes per job in proportion to its cost (camera item ~135, pair item
+      // ~160 instructions), at least one each; jobs beyond the thread count run
+      // one lane each (the kernel's fallback mode)
+      const int nj = ch.n_lc + ch.n_lp;
+      ch.mjob_begin = (int)mjobs.size();
+      if (nj > 0 && nj <= kChunkThreads) {
+        std::vector<double> cost(nj);
+        double tot = 0.0;
+        for (int q = 0; q < nj; ++q) {
+          cost[q] = jobs[ch.job_begin + q].count * (q < ch.n_lc ? 135.0 : 160.0);
+          tot += cost[q];
+        }
+        std::vector<int> lanes(nj);
+        int used = 0;
+        for (int q = 0; q < nj; ++q) {
+          lanes[q] = std::max(1, (int)(cost[q] * kChunkThreads / std::max(tot, 1.0)));
+          lanes[q] = std::min(lanes[q], std::max(1, jobs[ch.job_begin + q].count));
+          used += lanes[q];
+        }
+        while (used > kChunkThreads) {  // trim the widest job (lowest index on ties)
+          int w = 0;
+          for (int q = 1; q < nj; ++q)
+            if (lanes[q] > lanes[w]) w = q;
+          --lanes[w];
+          --used;
+        }
+        int lb = 0;
+        for (int q = 0; q < nj; ++q) {
+          Job& jb = jobs[ch.job_begin + q];
+          jb.lane_begin = (short)lb;
+          jb.n_lanes = (short)lanes[q];
+          lb += lanes[q];
+          if (lanes[q] > 1) mjobs.push_back(q);
         }
       }
+      ch.n_mjobs = (int)mjobs.size() - ch.mjob_begin;
+      chunks.push_back(ch);
     }
   }
-  std::vector<int2> pair_key;
-  std::vector<ChunkItem> pchunks;
-  std::vector<int> pair_part_begin;
-  for (int fa = 0; fa < nf; ++fa)
-    for (int fb = fa + 1; fb < nf; ++fb) {
-      const size_t q = (size_t)fa * nf + fb;
-      if (pcnt[q + 1] == pcnt[q]) continue;
-      const int p = (int)pair_key.size();
-      pair_key.push_back(make_int2(fa, fb));
-      pair_part_begin.push_back((int)pchunks.size());
-      for (int b = pcnt[q]; b < pcnt[q + 1]; b += kPairChunk)
-        pchunks.push_back(ChunkItem{p, b, std::min(kPairChunk, pcnt[q + 1] - b), 0});
-    }
-  pair_part_begin.push_back((int)pchunks.size());
+  // pairs in key order (the reduced system does not depend on this order, but a
+  // fixed one keeps the tables reproducible)
+  std::vector<int> cam_slot_begin((size_t)nf + 1, 0), cam_slots;
+  for (int f = 0; f < nf; ++f) {
+    cam_slot_begin[f] = (int)cam_slots.size();
+    cam_slots.insert(cam_slots.end(), cam_slot_lists[f].begin(), cam_slot_lists[f].end());
+  }
+  cam_slot_begin[nf] = (int)cam_slots.size();
+  const int n_pairs = (int)pair_key.size();
+  std::vector<int> pair_slot_begin((size_t)n_pairs + 1, 0), pair_slots;
+  for (int p = 0; p < n_pairs; ++p) {
+    pair_slot_begin[p] = (int)pair_slots.size();
+    pair_slots.insert(pair_slots.end(), pair_slot_lists[p].begin(), pair_slot_lists[p].end());
+  }
+  pair_slot_begin[n_pairs] = (int)pair_slots.size();
 
   // arena layout: static (uploaded) part first
-  const bool mixed = ctx->mixed;
   const size_t rs = mixed ? sizeof(float) : sizeof(double);
   const int n = 6 * nf;
-  const int ntile = (int)tiles.size();
   Layout Lo;
   const size_t o_intr = Lo.add(sizeof(double) * nc * 7);
   const size_t o_R = Lo.add(sizeof(double) * 2 * nc * 9);
@@ -508,6 +628,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const size_t o_Ri = Lo.add(sizeof(double) * nc * 9);
   const size_t o_Ti = Lo.add(sizeof(double) * nc * 3);
   const size_t o_Xi = Lo.add(sizeof(double) * (size_t)np * 3);
+  const size_t o_perm = Lo.add(sizeof(int) * (size_t)np);
   const size_t o_free = Lo.add(sizeof(int) * nc);
   const size_t o_cof = Lo.add(sizeof(int) * nf);
   const size_t o_tiles = Lo.add(sizeof(Tile) * tiles.size());
@@ -516,21 +637,24 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const size_t o_uv = Lo.add(sizeof(double) * 2 * (size_t)no);
   const size_t o_chi = Lo.add(mixed ? sizeof(float2) * (size_t)no : 0);
   const size_t o_clo = Lo.add(mixed ? sizeof(float2) * (size_t)no : 0);
-  const size_t o_cch = Lo.add(sizeof(ChunkItem) * cchunks.size());
-  const size_t o_cobs = Lo.add(sizeof(int) * cam_obs.size());
-  const size_t o_cpb = Lo.add(sizeof(int) * cam_part_begin.size());
-  const size_t o_pch = Lo.add(sizeof(ChunkItem) * pchunks.size());
-  const size_t o_pent = Lo.add(sizeof(int2) * pair_ent.size());
+  const size_t o_chunks = Lo.add(sizeof(Chunk) * chunks.size());
+  const size_t o_jobs = Lo.add(sizeof(Job) * jobs.size());
+  const size_t o_mjobs = Lo.add(sizeof(int) * mjobs.size());
+  const size_t o_cml = Lo.add(sizeof(unsigned short) * cm_list.size());
+  const size_t o_pent = Lo.add(sizeof(unsigned int) * pent.size());
+  const size_t o_csb = Lo.add(sizeof(int) * cam_slot_begin.size());
+  const size_t o_cs = Lo.add(sizeof(int) * cam_slots.size());
   const size_t o_pkey = Lo.add(sizeof(int2) * pair_key.size());
-  const size_t o_ppb = Lo.add(sizeof(int) * pair_part_begin.size());
+  const size_t o_psb = Lo.add(sizeof(int) * pair_slot_begin.size());
+  const size_t o_ps = Lo.add(sizeof(int) * pair_slots.size());
   const size_t o_lm = Lo.add(sizeof(LmState));
   const size_t static_bytes = Lo.off;
   const size_t o_camreal = Lo.add(mixed ? 0 : sizeof(double) * kCamReal * nc);
   const size_t o_camdf = Lo.add(mixed ? sizeof(float) * 2 * kCamDf * nc : 0);
-  const size_t o_rec = Lo.add(rs * kRec * (size_t)no);
-  const size_t o_paux = Lo.add(rs * kPaux * (size_t)np);
-  const size_t o_cpart = Lo.add(rs * kCamPart * cchunks.size());
-  const size_t o_ppart = Lo.add(rs * kPairPart * pchunks.size());
+  const size_t o_cpart = Lo.add(rs * kCamPart * (size_t)n_cslots);
+  const size_t o_ppart = Lo.add(rs * kPairPart * (size_t)n_pslots);
+  const size_t o_csum = Lo.add(sizeof(double) * kCamPart * (size_t)nf);
+  const size_t o_psum = Lo.add(sizeof(double) * kPairPart * (size_t)n_pairs);
   const size_t o_S = Lo.add(sizeof(double) * (size_t)n * n);
   const size_t o_rhs = Lo.add(sizeof(double) * n);
   const size_t o_gc = Lo.add(sizeof(double) * n);
@@ -549,19 +673,21 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   auto put = [&](size_t off, const void* src, size_t bytes) {
     if (bytes) std::memcpy(stage.data() + off, src, bytes);
   };
-  // initial state in point-major/caller layouts (points and cameras keep caller indices)
   put(o_intr, intr.data(), sizeof(double) * intr.size());
   put(o_R, R.data(), sizeof(double) * R.size());
   put(o_R + sizeof(double) * R.size(), R.data(), sizeof(double) * R.size());
   put(o_T, T.data(), sizeof(double) * T.size());
   put(o_T + sizeof(double) * T.size(), T.data(), sizeof(double) * T.size());
-  // points: binary64, or double-float (hi, lo) pairs in the mixed path
-  std::vector<double> Xrep(X);
+  // points in internal order: binary64, or double-float (hi, lo) pairs in the mixed path
+  std::vector<double> Xrep((size_t)np * 3);
+  for (int i = 0; i < np; ++i)
+    for (int a = 0; a < 3; ++a) Xrep[3 * (size_t)i + a] = X[3 * (size_t)perm[i] + a];
   if (mixed) {
     float* xf = reinterpret_cast<float*>(Xrep.data());
-    for (size_t i = 0; i < X.size(); ++i) {
-      const float hi = (float)X[i];
-      const float lo = (float)(X[i] - (double)hi);
+    for (size_t i = 0; i < Xrep.size(); ++i) {
+      const double v = Xrep[i];
+      const float hi = (float)v;
+      const float lo = (float)(v - (double)hi);
       xf[2 * i] = hi;
       xf[2 * i + 1] = lo;
     }
@@ -573,19 +699,18 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   put(o_Ri, R.data(), sizeof(double) * R.size());
   put(o_Ti, T.data(), sizeof(double) * T.size());
   put(o_Xi, Xrep.data(), sizeof(double) * Xrep.size());
+  put(o_perm, perm.data(), sizeof(int) * perm.size());
   put(o_free, free_idx.data(), sizeof(int) * nc);
   put(o_cof, cam_of_free.data(), sizeof(int) * nf);
   put(o_tiles, tiles.data(), sizeof(Tile) * tiles.size());
+  put(o_ocam, pcam.data(), sizeof(int) * (size_t)no);
+  put(o_opt, ppt.data(), sizeof(int) * (size_t)no);
   {
-    int* sc = (int*)(stage.data() + o_ocam);
-    int* sp = (int*)(stage.data() + o_opt);
     double* su = (double*)(stage.data() + o_uv);
     float2* chi = mixed ? (float2*)(stage.data() + o_chi) : nullptr;
     float2* clo = mixed ? (float2*)(stage.data() + o_clo) : nullptr;
     for (int p = 0; p < no; ++p) {
       const int i = pm[p];
-      sc[p] = ocam[i];
-      sp[p] = opt[i];
       su[2 * p] = uv[2 * i];
       su[2 * p + 1] = uv[2 * i + 1];
       if (chi) {  // observation relative to the principal point, double-float
@@ -597,13 +722,16 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
       }
     }
   }
-  put(o_cch, cchunks.data(), sizeof(ChunkItem) * cchunks.size());
-  put(o_cobs, cam_obs.data(), sizeof(int) * cam_obs.size());
-  put(o_cpb, cam_part_begin.data(), sizeof(int) * cam_part_begin.size());
-  put(o_pch, pchunks.data(), sizeof(ChunkItem) * pchunks.size());
-  put(o_pent, pair_ent.data(), sizeof(int2) * pair_ent.size());
+  put(o_chunks, chunks.data(), sizeof(Chunk) * chunks.size());
+  put(o_jobs, jobs.data(), sizeof(Job) * jobs.size());
+  put(o_mjobs, mjobs.data(), sizeof(int) * mjobs.size());
+  put(o_cml, cm_list.data(), sizeof(unsigned short) * cm_list.size());
+  put(o_pent, pent.data(), sizeof(unsigned int) * pent.size());
+  put(o_csb, cam_slot_begin.data(), sizeof(int) * cam_slot_begin.size());
+  put(o_cs, cam_slots.data(), sizeof(int) * cam_slots.size());
   put(o_pkey, pair_key.data(), sizeof(int2) * pair_key.size());
-  put(o_ppb, pair_part_begin.data(), sizeof(int) * pair_part_begin.size());
+  put(o_psb, pair_slot_begin.data(), sizeof(int) * pair_slot_begin.size());
+  put(o_ps, pair_slots.data(), sizeof(int) * pair_slots.size());
   {
     LmState lm{};
     lm.mu0 = d->mu0 > 0.0 ? d->mu0 : 1e-4;
@@ -625,8 +753,8 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   DevCluster& h = c->h;
   h = DevCluster{};
   h.n_cams = nc; h.n_pts = np; h.n_obs = no; h.n_free = nf;
-  h.n_tiles = ntile; h.n_cchunks = (int)cchunks.size(); h.n_pairs = (int)pair_key.size();
-  h.n_pchunks = (int)pchunks.size();
+  h.n_tiles = (int)tiles.size(); h.n_chunks = (int)chunks.size(); h.n_pairs = n_pairs;
+  h.n_cslots = n_cslots; h.n_pslots = n_pslots;
   h.sigma_px = d->sigma_px; h.huber_delta = d->huber_delta_px; h.sigma_gnss = d->sigma_gnss_m;
   h.sigma_imu = d->sigma_imu_rad;
   h.inv_sigma_f = (float)(1.0 / d->sigma_px);
@@ -641,6 +769,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   h.R_init = (const double*)(arena + o_Ri);
   h.T_init = (const double*)(arena + o_Ti);
   h.X_init = (const double*)(arena + o_Xi);
+  h.pt_perm = (const int*)(arena + o_perm);
   h.free_idx = (const int*)(arena + o_free);
   h.cam_of_free = (const int*)(arena + o_cof);
   h.camreal = mixed ? nullptr : arena + o_camreal;
@@ -651,17 +780,20 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   h.obs_uv = (const double*)(arena + o_uv);
   h.obs_chi = mixed ? (const float2*)(arena + o_chi) : nullptr;
   h.obs_clo = mixed ? (const float2*)(arena + o_clo) : nullptr;
-  h.rec = arena + o_rec;
-  h.paux = arena + o_paux;
-  h.cchunks = (const ChunkItem*)(arena + o_cch);
-  h.cam_obs = (const int*)(arena + o_cobs);
+  h.chunks = (const Chunk*)(arena + o_chunks);
+  h.jobs = (const Job*)(arena + o_jobs);
+  h.mjobs = (const int*)(arena + o_mjobs);
+  h.cm_list = (const unsigned short*)(arena + o_cml);
+  h.pent = (const unsigned int*)(arena + o_pent);
   h.campart = arena + o_cpart;
-  h.cam_part_begin = (const int*)(arena + o_cpb);
-  h.pchunks = (const ChunkItem*)(arena + o_pch);
-  h.pair_ent = (const int2*)(arena + o_pent);
   h.pairpart = arena + o_ppart;
+  h.cam_slot_begin = (const int*)(arena + o_csb);
+  h.cam_slots = (const int*)(arena + o_cs);
   h.pair_key = (const int2*)(arena + o_pkey);
-  h.pair_part_begin = (const int*)(arena + o_ppb);
+  h.pair_slot_begin = (const int*)(arena + o_psb);
+  h.pair_slots = (const int*)(arena + o_ps);
+  h.camsum = (double*)(arena + o_csum);
+  h.pairsum = (double*)(arena + o_psum);
   h.S = (double*)(arena + o_S);
   h.rhs = (double*)(arena + o_rhs);
   h.gc = (double*)(arena + o_gc);
@@ -683,6 +815,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   c->arena = arena;
   c->arena_bytes = total;
   c->pm_to_user = std::move(pm);
+  c->pt_inv = std::move(inv);
   ctx->mem += total;
   return BA_OK;
 }
@@ -843,9 +976,10 @@ BA_API ba_status ba_create_cluster(ba_ctx* ctx, const ba_cluster_desc* d, ba_clu
       cudaMemcpyAsync((double*)c->h.R_init + 9 * (size_t)k, sR + 9 * (size_t)m, 72, cudaMemcpyDeviceToDevice, ctx->stream);
       cudaMemcpyAsync((double*)c->h.T_init + 3 * (size_t)k, sT + 3 * (size_t)m, 24, cudaMemcpyDeviceToDevice, ctx->stream);
     }
-    for (int j = 0; j < c->np; ++j) {
-      const int m = d->warm_pt_map[j];
-      if (m < 0 || m >= src->np) continue;
+    for (int ju = 0; ju < c->np; ++ju) {  // caller indices -> internal indices on both sides
+      const int mu_ = d->warm_pt_map[ju];
+      if (mu_ < 0 || mu_ >= src->np) continue;
+      const int j = c->pt_inv[ju], m = src->pt_inv[mu_];
       for (int b = 0; b < 2; ++b)
         cudaMemcpyAsync(c->h.X + ((size_t)b * c->np + j) * 3, sX + 3 * (size_t)m, 24, cudaMemcpyDeviceToDevice, ctx->stream);
       cudaMemcpyAsync((double*)c->h.X_init + 3 * (size_t)j, sX + 3 * (size_t)m, 24, cudaMemcpyDeviceToDevice, ctx->stream);
@@ -1060,18 +1194,13 @@ BA_API ba_status ba_get_state(ba_ctx* ctx, ba_cluster_id id, double* R, double* 
     CUDA_TRY(ctx, cudaMemcpyAsync(R, c->h.R + (size_t)lm.cur * c->nc * 9, sizeof(double) * c->nc * 9, kind, ctx->stream));
   if (T)
     CUDA_TRY(ctx, cudaMemcpyAsync(T, c->h.T + (size_t)lm.cur * c->nc * 3, sizeof(double) * c->nc * 3, kind, ctx->stream));
-  if (X && c->np) {
-    if (ctx->mixed) {  // double-float points -> binary64
-      double* tmp = nullptr;
-      CUDA_TRY(ctx, cudaMallocAsync((void**)&tmp, sizeof(double) * (size_t)c->np * 3, ctx->stream));
-      launch_export_points(c->d_desc, c->h, true, tmp, ctx->stream);
-      note_direct(ctx);
-      CUDA_TRY(ctx, cudaMemcpyAsync(X, tmp, sizeof(double) * (size_t)c->np * 3, kind, ctx->stream));
-      CUDA_TRY(ctx, cudaFreeAsync(tmp, ctx->stream));
-    } else {
-      CUDA_TRY(ctx, cudaMemcpyAsync(X, c->h.X + (size_t)lm.cur * c->np * 3, sizeof(double) * (size_t)c->np * 3, kind,
-                                    ctx->stream));
-    }
+  if (X && c->np) {  // internal order (and double-float in the mixed path) -> caller's order, binary64
+    double* tmp = nullptr;
+    CUDA_TRY(ctx, cudaMallocAsync((void**)&tmp, sizeof(double) * (size_t)c->np * 3, ctx->stream));
+    launch_export_points(c->d_desc, c->h, ctx->mixed, tmp, ctx->stream);
+    note_direct(ctx);
+    CUDA_TRY(ctx, cudaMemcpyAsync(X, tmp, sizeof(double) * (size_t)c->np * 3, kind, ctx->stream));
+    CUDA_TRY(ctx, cudaFreeAsync(tmp, ctx->stream));
   }
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   return BA_OK;

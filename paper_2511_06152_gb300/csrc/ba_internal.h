@@ -1,11 +1,16 @@
 // Internal layout shared by the kernels and the host side of the library.
 //
-// One cluster lives in one device arena.  Observations are stored in
-// point-major order (sorted by point, then camera), so the observations of a
-// point are contiguous; "tiles" cut that order into runs of at most 32
-// observations holding whole points, one warp per tile.  A camera-major
-// permutation and a camera-pair table, both presorted on the host, drive the
-// deterministic reductions into the reduced camera system.
+// One cluster lives in one device arena.  Points are reordered along a
+// Morton curve of their initial ground position, and observations are stored
+// in point-major order (sorted by point, then camera), so the observations of
+// a point are contiguous and nearby points share cameras.  "Tiles" cut that
+// order into runs of at most 32 observations holding whole points (one warp
+// each); "chunks" group consecutive tiles (one CTA each).  Per chunk, a
+// presorted table lists the observations of each free camera and the
+// observation pairs of each co-visible camera pair; the chunk reduces its
+// observations into per-camera and per-pair partial sums in that fixed order,
+// and the reduced camera system sums the partials in chunk order.  No
+// reduction depends on anything but the cluster itself.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -15,15 +20,17 @@
 
 namespace bagpu {
 
-constexpr int kRec = 32;        // Reals per observation record: Jc[12], r[2], Z[18]
-constexpr int kRecJc = 0;
-constexpr int kRecR = 12;
-constexpr int kRecZ = 14;
-constexpr int kPaux = 16;       // Reals per point: Linv[6], q[3], Dp[3], gp[3], pad
-constexpr int kCamPart = 40;    // Reals per camera chunk: A[21], gobs[6], Zq[6], Udiag[6], pad
-constexpr int kPairPart = 36;   // Reals per pair chunk: sum Z_a Z_b^T (6x6 row-major)
-constexpr int kCamChunk = 1024; // observations per camera chunk
-constexpr int kPairChunk = 256; // entries per pair chunk
+constexpr int kSrec = 35;         // per-observation shared record: Jc[12], r[2], Z[18], q[3]
+constexpr int kSrecR = 12;
+constexpr int kSrecZ = 14;
+constexpr int kSrecQ = 32;
+constexpr int kCamPart = 40;      // camera partial: A[21], gobs[6], Zq[6], Udiag[6], pad
+constexpr int kPairPart = 36;     // pair partial: sum Z_a Z_b^T (6x6 row-major)
+constexpr int kChunkTilesMixed = 16;  // tiles per chunk (two per warp), binary32 records
+constexpr int kChunkTilesF64 = 8;     // tiles per chunk (one per warp), binary64 records
+constexpr int kChunkObsMixed = 32 * kChunkTilesMixed;  // at most this many observations per chunk
+constexpr int kChunkObsF64 = 32 * kChunkTilesF64;
+constexpr int kChunkThreads = 256;
 constexpr int kMaxTrack = 32;
 constexpr int kMaxFreeSmall = 32;  // free cameras the single-CTA factor handles (n <= 192)
 constexpr double kDiagMin = 1e-6;
@@ -42,12 +49,26 @@ struct Tile {
   int n_obs;  // <= 32, whole points
 };
 
-struct ChunkItem {  // camera or pair chunk
-  int key;          // free camera index, or pair index
-  int begin;        // into cam_obs or pair_ent
-  int count;
+struct Chunk {
+  int obs_begin, n_obs;     // point-major observation range (whole tiles)
+  int tile_begin, n_tiles;  // its tiles
+  int job_begin;            // its jobs: n_lc free cameras, then n_lp co-visible camera pairs
+  int n_lc, n_lp;
+  int mjob_begin, n_mjobs;  // its jobs spread over more than one lane (indices into its jobs)
   int pad;
 };
+
+// One reduction job of a chunk: a free camera (items: its observations, as
+// chunk-local indices into cm_list) or a camera pair (items: the chunk-local
+// observation index pairs a | b << 16 in pent), summed by a run of lanes.
+struct Job {
+  int slot;        // camera or pair partial slot
+  int item_begin;  // into cm_list (camera) or pent (pair)
+  int count;       // items
+  short lane_begin, n_lanes;
+};
+
+constexpr int kLanePart = 40;  // shared-memory row per lane for multi-lane jobs
 
 // Per-cluster LM control state, resident on the device.
 struct LmState {
@@ -77,45 +98,48 @@ struct StepRec {
 // Device-side descriptor of one cluster (plain pointers into its arena).
 struct DevCluster {
   int n_cams, n_pts, n_obs, n_free;
-  int n_tiles, n_cchunks, n_pairs, n_pchunks;
+  int n_tiles, n_chunks, n_pairs, n_cslots, n_pslots, pad_i;
   double sigma_px, huber_delta, sigma_gnss, sigma_imu;
   float inv_sigma_f, delta_f, half_inv_s2_f, pad_f;  // binary32 copies of 1/sigma_px, delta, 1/(2 sigma_px^2)
 
   const double* intr;      // [nc][7]
   double* R;               // [2][nc][9]
   double* T;               // [2][nc][3]
-  // Points, double-buffered.  FP64 path: binary64 [2][np][3].  Mixed path:
-  // double-float [2][np][3] of (hi, lo) binary32 pairs (same 24 bytes/point).
+  // Points (internal order), double-buffered.  FP64 path: binary64 [2][np][3].
+  // Mixed path: double-float [2][np][3] of (hi, lo) binary32 pairs (same 24 B).
   double* X;
   const double* R_prior;   // [nc][9]
   const double* T_prior;   // [nc][3]
   const double* R_init;    // [nc][9] state given at create (for reset)
   const double* T_init;    // [nc][3]
-  const double* X_init;    // [np][3], same representation as X
+  const double* X_init;    // [np][3], same representation as X, internal order
+  const int* pt_perm;      // [np] internal point -> caller's point index
   const int* free_idx;     // [nc] -> free index or -1
   const int* cam_of_free;  // [nf]
   void* camreal;           // FP64 path: double [nc][20]: R[9], T[3], intr[7], free flag
-  float* camdf;            // mixed path: [2][nc][kCamDf] double-float cameras (layout below)
+  float* camdf;            // mixed path: [2][nc][kCamDf] double-float cameras
 
   const Tile* tiles;       // [n_tiles]
   const int* obs_cam;      // [no] point-major
-  const int* obs_pt;       // [no] point-major
+  const int* obs_pt;       // [no] point-major, internal point index
   const double* obs_uv;    // [no][2] point-major, binary64 pixels
   const float2* obs_chi;   // mixed path: [no] hi part of (u - cx, v - cy)
   const float2* obs_clo;   // mixed path: [no] lo part of (u - cx, v - cy)
-  void* rec;               // Real [no][kRec]
-  void* paux;              // Real [np][kPaux]
 
-  const ChunkItem* cchunks;   // [n_cchunks]
-  const int* cam_obs;         // [sum over free cams] point-major obs index, camera-major order
-  void* campart;              // Real [n_cchunks][kCamPart]
-  const int* cam_part_begin;  // [nf + 1]
-
-  const ChunkItem* pchunks;   // [n_pchunks]
-  const int2* pair_ent;       // (obs_a, obs_b), point-major indices, cam(a) < cam(b)
-  void* pairpart;             // Real [n_pchunks][kPairPart]
-  const int2* pair_key;       // [n_pairs] (free a, free b), a < b
-  const int* pair_part_begin; // [n_pairs + 1]
+  const Chunk* chunks;         // [n_chunks]
+  const Job* jobs;             // per chunk, in lane order
+  const int* mjobs;            // per chunk: indices of its multi-lane jobs
+  const unsigned short* cm_list;  // chunk-local observation lists per camera job
+  const unsigned int* pent;       // chunk-local observation pairs per pair job
+  void* campart;               // Real [n_cslots][kCamPart]
+  void* pairpart;              // Real [n_pslots][kPairPart]
+  const int* cam_slot_begin;   // [nf + 1]
+  const int* cam_slots;        // [n_cslots] camera partial slots by free camera, chunk order
+  const int2* pair_key;        // [n_pairs] (free a, free b), a < b
+  const int* pair_slot_begin;  // [n_pairs + 1]
+  const int* pair_slots;       // [n_pslots] pair partial slots by pair, chunk order
+  double* camsum;              // [nf][kCamPart] per-camera sums of the partials
+  double* pairsum;             // [n_pairs][kPairPart] per-pair sums of the partials
 
   double* S;        // [n][n], n = 6 nf, row-major, full
   double* rhs;      // [n]
@@ -123,7 +147,7 @@ struct DevCluster {
   double* Dc;       // [n]
   double* dc;       // [n]
   float* dc32;      // [n] binary32 copy of dc (mixed path)
-  double* tilepart; // [n_tiles][2]: cost, point pred
+  double* tilepart; // [n_tiles][2]: cost, point pred (or max |g_p| in the diagnostic pass)
   LmState* lm;
   StepRec* trace;   // [trace_cap]
   int trace_cap;
@@ -133,10 +157,11 @@ struct DevCluster {
 struct BatchView {
   const DevCluster* cl;  // [n]
   const int* tile_pre;   // [n + 1]
-  const int* cchunk_pre; // [n + 1]
-  const int* pchunk_pre; // [n + 1]
+  const int* chunk_pre;  // [n + 1]
+  const int* item_pre;   // [n + 1] free cameras + camera pairs
+  const int* factor_order;  // [n] clusters by decreasing reduced-system size
   int n;
-  int total_tiles, total_cchunks, total_pchunks;
+  int total_tiles, total_chunks, total_items;
   int max_n;             // largest 6 * n_free in the batch
   int pad;
 };
@@ -144,8 +169,8 @@ struct BatchView {
 // Kernel kinds, for launch counting and per-kernel timing.
 enum KernelKind {
   KK_LINEARIZE = 0,
-  KK_CAM_REDUCE,
-  KK_PAIR_REDUCE,
+  KK_CAM_REDUCE,   // chunk partials -> per-camera / per-pair sums
+  KK_PAIR_REDUCE,  // unused
   KK_FACTOR,
   KK_BACKSUB,
   KK_LM_UPDATE,
@@ -179,5 +204,7 @@ void launch_grad_norm(const BatchView& bv, bool mixed, double* out, cudaStream_t
 void launch_reproj(const DevCluster* dcl, const DevCluster& hcl, bool mixed, double* err_pm, cudaStream_t st);
 void launch_export_points(const DevCluster* dcl, const DevCluster& hcl, bool mixed, double* out, cudaStream_t st);
 size_t factor_smem_bytes(int max_n);
+int chunk_obs(bool mixed);
+int chunk_tiles(bool mixed);
 
 }  // namespace bagpu

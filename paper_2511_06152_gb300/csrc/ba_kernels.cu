@@ -171,268 +171,354 @@ __global__ void k_camdf_all(BatchView bv) {
   }
 }
 
-// ------------------------------------------------------------------ K1
+// ------------------------------------------------------------------ per-tile linearisation
+
+// What one lane knows after linearising its observation of a tile: the
+// whitened, robust-weighted Jacobians and residual, Z = Jc^T Jp L^-T, and
+// (broadcast from the point's first lane) L^-1 and q = L^-1 g_p of the damped
+// point block; D_p and g_p are valid on the point's first lane.
+template <bool MIXED>
+struct TileLin {
+  using Real = typename RealOf<MIXED>::T;
+  bool act, head;
+  int o, k, j, seg_start, seg_end;
+  Real Jc[12], r0, r1, Z[18];
+  Real m00, m10, m11, m20, m21, m22, q0, q1, q2;
+  Real d0, d1, d2, g0, g1, g2;
+};
+
+// Linearise one tile (one warp).  Identical arithmetic wherever it is called,
+// so the back-substitution reproduces the linearisation pass bit for bit.
+template <bool MIXED>
+__device__ __forceinline__ void linearize_tile(const DevCluster& C, LmState* lm, const Tile& tl, int lane,
+                                               bool report_fail, TileLin<MIXED>& L) {
+  using Real = typename RealOf<MIXED>::T;
+  L.act = lane < tl.n_obs;
+  L.o = tl.obs_begin + (L.act ? lane : 0);
+  L.k = L.act ? C.obs_cam[L.o] : 0;
+  L.j = L.act ? C.obs_pt[L.o] : -1 - lane;
+  segments(L.j, lane, L.seg_start, L.seg_end);
+  L.head = L.act && lane == L.seg_start;
+  const int cur = lm->cur;
+  Real mu, inv_sigma, delta;
+  if constexpr (MIXED) {
+    mu = lm->mu_f;
+    inv_sigma = C.inv_sigma_f;
+    delta = C.delta_f;
+  } else {
+    mu = lm->mu;
+    inv_sigma = 1.0 / C.sigma_px;
+    delta = C.huber_delta;
+  }
+  Real Jp[6];
+  L.r0 = 0;
+  L.r1 = 0;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) L.Jc[i] = 0;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) Jp[i] = 0;
+  if (L.act) {
+    Real Rm[9], in[7], dx, dy, dz, uo, vo;
+    bool is_free;
+    if constexpr (MIXED) {
+      const CamDf cd = load_camdf(camdf_ptr(C, cur, L.k));
+      const float2* xp = xdf_ptr(C, cur, L.j);
+      const float2 a = xp[0], b = xp[1], c = xp[2];
+      dx = df_to_f(df_sub(dfl{a.x, a.y}, cd.T[0]));
+      dy = df_to_f(df_sub(dfl{b.x, b.y}, cd.T[1]));
+      dz = df_to_f(df_sub(dfl{c.x, c.y}, cd.T[2]));
+#pragma unroll
+      for (int i = 0; i < 9; ++i) Rm[i] = cd.R[i].hi;
+      in[0] = cd.f.hi; in[1] = 0.f; in[2] = 0.f;
+      in[3] = cd.k1.hi; in[4] = cd.k2.hi; in[5] = cd.p1.hi; in[6] = cd.p2.hi;
+      const float2 ch = C.obs_chi[L.o];  // observation relative to the principal point
+      uo = ch.x; vo = ch.y;
+      is_free = cd.free_flag != 0.0f;
+    } else {
+      const double* cr = (const double*)C.camreal + (size_t)kCamReal * L.k;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) Rm[i] = cr[i];
+#pragma unroll
+      for (int i = 0; i < 7; ++i) in[i] = cr[12 + i];
+      const double* Xd = C.X + ((size_t)cur * C.n_pts + L.j) * 3;
+      dx = Xd[0] - cr[9]; dy = Xd[1] - cr[10]; dz = Xd[2] - cr[11];
+      const double2 u = reinterpret_cast<const double2*>(C.obs_uv)[L.o];
+      uo = u.x; vo = u.y;
+      is_free = cr[19] != 0.0;
+    }
+    obs_linearize<Real>(Rm, dx, dy, dz, in, uo, vo, inv_sigma, delta, L.r0, L.r1, L.Jc, Jp);
+    if (!is_free) {
+#pragma unroll
+      for (int i = 0; i < 12; ++i) L.Jc[i] = 0;
+    }
+  }
+  // point blocks by segmented reduction
+  Real v00 = Jp[0] * Jp[0] + Jp[3] * Jp[3];
+  Real v01 = Jp[0] * Jp[1] + Jp[3] * Jp[4];
+  Real v02 = Jp[0] * Jp[2] + Jp[3] * Jp[5];
+  Real v11 = Jp[1] * Jp[1] + Jp[4] * Jp[4];
+  Real v12 = Jp[1] * Jp[2] + Jp[4] * Jp[5];
+  Real v22 = Jp[2] * Jp[2] + Jp[5] * Jp[5];
+  Real g0 = -(Jp[0] * L.r0 + Jp[3] * L.r1);
+  Real g1 = -(Jp[1] * L.r0 + Jp[4] * L.r1);
+  Real g2 = -(Jp[2] * L.r0 + Jp[5] * L.r1);
+  v00 = seg_reduce(v00, lane, L.seg_start, L.seg_end);
+  v01 = seg_reduce(v01, lane, L.seg_start, L.seg_end);
+  v02 = seg_reduce(v02, lane, L.seg_start, L.seg_end);
+  v11 = seg_reduce(v11, lane, L.seg_start, L.seg_end);
+  v12 = seg_reduce(v12, lane, L.seg_start, L.seg_end);
+  v22 = seg_reduce(v22, lane, L.seg_start, L.seg_end);
+  g0 = seg_reduce(g0, lane, L.seg_start, L.seg_end);
+  g1 = seg_reduce(g1, lane, L.seg_start, L.seg_end);
+  g2 = seg_reduce(g2, lane, L.seg_start, L.seg_end);
+  // head: damp, factor V* = L L^T, M = L^-1, q = M g_p
+  Real m00 = 0, m10 = 0, m11 = 0, m20 = 0, m21 = 0, m22 = 0, q0 = 0, q1 = 0, q2 = 0;
+  L.d0 = L.d1 = L.d2 = 0;
+  L.g0 = g0; L.g1 = g1; L.g2 = g2;
+  if (L.head) {
+    const Real d0 = clamp_diag(v00), d1 = clamp_diag(v11), d2 = clamp_diag(v22);
+    const Real a00 = v00 + mu * d0, a11 = v11 + mu * d1, a22 = v22 + mu * d2;
+    bool ok = a00 > Real(0);
+    const Real l00 = sqrt(ok ? a00 : Real(1));
+    const Real l10 = v01 / l00, l20 = v02 / l00;
+    const Real t11 = a11 - l10 * l10;
+    ok = ok && t11 > Real(0);
+    const Real l11 = sqrt(t11 > Real(0) ? t11 : Real(1));
+    const Real l21 = (v12 - l20 * l10) / l11;
+    const Real t22 = a22 - l20 * l20 - l21 * l21;
+    ok = ok && t22 > Real(0);
+    const Real l22 = sqrt(t22 > Real(0) ? t22 : Real(1));
+    if (!ok && report_fail) lm->pt_fail = 1;  // point block not positive definite: reject this step
+    m00 = Real(1) / l00;
+    m11 = Real(1) / l11;
+    m22 = Real(1) / l22;
+    m10 = -l10 * m00 * m11;
+    m21 = -l21 * m11 * m22;
+    m20 = -(l20 * m00 + l21 * m10) * m22;
+    q0 = m00 * g0;
+    q1 = m10 * g0 + m11 * g1;
+    q2 = m20 * g0 + m21 * g1 + m22 * g2;
+    L.d0 = d0; L.d1 = d1; L.d2 = d2;
+  }
+  L.m00 = __shfl_sync(BA_FULL_MASK, m00, L.seg_start);
+  L.m10 = __shfl_sync(BA_FULL_MASK, m10, L.seg_start);
+  L.m11 = __shfl_sync(BA_FULL_MASK, m11, L.seg_start);
+  L.m20 = __shfl_sync(BA_FULL_MASK, m20, L.seg_start);
+  L.m21 = __shfl_sync(BA_FULL_MASK, m21, L.seg_start);
+  L.m22 = __shfl_sync(BA_FULL_MASK, m22, L.seg_start);
+  L.q0 = __shfl_sync(BA_FULL_MASK, q0, L.seg_start);
+  L.q1 = __shfl_sync(BA_FULL_MASK, q1, L.seg_start);
+  L.q2 = __shfl_sync(BA_FULL_MASK, q2, L.seg_start);
+  // P = Jp M^T (2x3), Z = Jc^T P (6x3)
+  const Real P00 = Jp[0] * L.m00;
+  const Real P01 = Jp[0] * L.m10 + Jp[1] * L.m11;
+  const Real P02 = Jp[0] * L.m20 + Jp[1] * L.m21 + Jp[2] * L.m22;
+  const Real P10 = Jp[3] * L.m00;
+  const Real P11 = Jp[3] * L.m10 + Jp[4] * L.m11;
+  const Real P12 = Jp[3] * L.m20 + Jp[4] * L.m21 + Jp[5] * L.m22;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    L.Z[3 * m + 0] = L.Jc[m] * P00 + L.Jc[6 + m] * P10;
+    L.Z[3 * m + 1] = L.Jc[m] * P01 + L.Jc[6 + m] * P11;
+    L.Z[3 * m + 2] = L.Jc[m] * P02 + L.Jc[6 + m] * P12;
+  }
+}
+
+// ------------------------------------------------------------------ K1: linearise + Schur reductions, one CTA per chunk
 
 template <bool MIXED>
-__global__ void __launch_bounds__(256) k_linearize(BatchView bv) {
+__global__ void __launch_bounds__(kChunkThreads) k_lin_schur(BatchView bv, int diag) {
   using Real = typename RealOf<MIXED>::T;
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int g = warp; g < bv.total_tiles; g += nwarps) {
-    const int s = find_slot(bv.tile_pre, bv.n, g);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Real* srec = reinterpret_cast<Real*>(smraw);                        // [chunk_obs][kSrec]
+  Real* lanepart = srec + (size_t)(MIXED ? kChunkObsMixed : kChunkObsF64) * kSrec;  // [threads][kLanePart]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int g = blockIdx.x; g < bv.total_chunks; g += gridDim.x) {
+    const int s = find_slot(bv.chunk_pre, bv.n, g);
     const DevCluster& C = bv.cl[s];
     LmState* lm = C.lm;
     if (!lm->active) continue;
-    const Tile tl = C.tiles[g - bv.tile_pre[s]];
-    const bool act = lane < tl.n_obs;
-    const int o = tl.obs_begin + (act ? lane : 0);
-    const int k = act ? C.obs_cam[o] : 0;
-    const int j = act ? C.obs_pt[o] : -1 - lane;
-    int seg_start, seg_end;
-    segments(j, lane, seg_start, seg_end);
-    const int cur = lm->cur;
-    Real mu, inv_sigma, delta;
-    if constexpr (MIXED) {
-      mu = lm->mu_f;
-      inv_sigma = C.inv_sigma_f;
-      delta = C.delta_f;
-    } else {
-      mu = lm->mu;
-      inv_sigma = 1.0 / C.sigma_px;
-      delta = C.huber_delta;
-    }
-
-    Real r0 = 0, r1 = 0, Jc[12], Jp[6];
+    const Chunk ch = C.chunks[g - bv.chunk_pre[s]];
+    // 1. linearise the chunk's tiles into shared memory
+    for (int t = warp; t < ch.n_tiles; t += nw) {
+      const Tile tl = C.tiles[ch.tile_begin + t];
+      TileLin<MIXED> L;
+      linearize_tile<MIXED>(C, lm, tl, lane, true, L);
+      if (L.act) {
+        Real* r = srec + (size_t)(L.o - ch.obs_begin) * kSrec;
 #pragma unroll
-    for (int i = 0; i < 12; ++i) Jc[i] = 0;
+        for (int i = 0; i < 12; ++i) r[i] = L.Jc[i];
+        r[kSrecR] = L.r0;
+        r[kSrecR + 1] = L.r1;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) Jp[i] = 0;
-    if (act) {
-      Real Rm[9], in[7], dx, dy, dz, uo, vo;
-      bool is_free;
-      if constexpr (MIXED) {
-        const CamDf cd = load_camdf(camdf_ptr(C, cur, k));
-        const float2* xp = xdf_ptr(C, cur, j);
-        const float2 a = xp[0], b = xp[1], c = xp[2];
-        dx = df_to_f(df_sub(dfl{a.x, a.y}, cd.T[0]));
-        dy = df_to_f(df_sub(dfl{b.x, b.y}, cd.T[1]));
-        dz = df_to_f(df_sub(dfl{c.x, c.y}, cd.T[2]));
-#pragma unroll
-        for (int i = 0; i < 9; ++i) Rm[i] = cd.R[i].hi;
-        in[0] = cd.f.hi; in[1] = 0.f; in[2] = 0.f;
-        in[3] = cd.k1.hi; in[4] = cd.k2.hi; in[5] = cd.p1.hi; in[6] = cd.p2.hi;
-        const float2 ch = C.obs_chi[o];  // observation relative to the principal point
-        uo = ch.x; vo = ch.y;
-        is_free = cd.free_flag != 0.0f;
-      } else {
-        const double* cr = (const double*)C.camreal + (size_t)kCamReal * k;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) Rm[i] = cr[i];
-#pragma unroll
-        for (int i = 0; i < 7; ++i) in[i] = cr[12 + i];
-        const double* Xd = C.X + ((size_t)cur * C.n_pts + j) * 3;
-        dx = Xd[0] - cr[9]; dy = Xd[1] - cr[10]; dz = Xd[2] - cr[11];
-        const double2 u = reinterpret_cast<const double2*>(C.obs_uv)[o];
-        uo = u.x; vo = u.y;
-        is_free = cr[19] != 0.0;
+        for (int i = 0; i < 18; ++i) r[kSrecZ + i] = L.Z[i];
+        r[kSrecQ] = L.q0;
+        r[kSrecQ + 1] = L.q1;
+        r[kSrecQ + 2] = L.q2;
       }
-      obs_linearize<Real>(Rm, dx, dy, dz, in, uo, vo, inv_sigma, delta, r0, r1, Jc, Jp);
-      if (!is_free) {
+      if (diag) {  // largest |g_p| of the tile, for the gradient norm
+        double gm = L.head ? fmax(fabs((double)L.g0), fmax(fabs((double)L.g1), fabs((double)L.g2))) : 0.0;
 #pragma unroll
-        for (int i = 0; i < 12; ++i) Jc[i] = 0;
+        for (int off = 16; off > 0; off >>= 1) gm = fmax(gm, __shfl_down_sync(BA_FULL_MASK, gm, off));
+        if (lane == 0) C.tilepart[2 * (ch.tile_begin + t) + 1] = gm;
       }
     }
-    // point blocks by segmented reduction
-    Real v00 = Jp[0] * Jp[0] + Jp[3] * Jp[3];
-    Real v01 = Jp[0] * Jp[1] + Jp[3] * Jp[4];
-    Real v02 = Jp[0] * Jp[2] + Jp[3] * Jp[5];
-    Real v11 = Jp[1] * Jp[1] + Jp[4] * Jp[4];
-    Real v12 = Jp[1] * Jp[2] + Jp[4] * Jp[5];
-    Real v22 = Jp[2] * Jp[2] + Jp[5] * Jp[5];
-    Real g0 = -(Jp[0] * r0 + Jp[3] * r1);
-    Real g1 = -(Jp[1] * r0 + Jp[4] * r1);
-    Real g2 = -(Jp[2] * r0 + Jp[5] * r1);
-    v00 = seg_reduce(v00, lane, seg_start, seg_end);
-    v01 = seg_reduce(v01, lane, seg_start, seg_end);
-    v02 = seg_reduce(v02, lane, seg_start, seg_end);
-    v11 = seg_reduce(v11, lane, seg_start, seg_end);
-    v12 = seg_reduce(v12, lane, seg_start, seg_end);
-    v22 = seg_reduce(v22, lane, seg_start, seg_end);
-    g0 = seg_reduce(g0, lane, seg_start, seg_end);
-    g1 = seg_reduce(g1, lane, seg_start, seg_end);
-    g2 = seg_reduce(g2, lane, seg_start, seg_end);
-
-    // head: damp, factor V* = L L^T, M = L^-1, q = M g_p
-    Real m00 = 0, m10 = 0, m11 = 0, m20 = 0, m21 = 0, m22 = 0;
-    if (act && lane == seg_start) {
-      const Real d0 = clamp_diag(v00), d1 = clamp_diag(v11), d2 = clamp_diag(v22);
-      const Real a00 = v00 + mu * d0, a11 = v11 + mu * d1, a22 = v22 + mu * d2;
-      bool ok = a00 > Real(0);
-      const Real l00 = sqrt(ok ? a00 : Real(1));
-      const Real l10 = v01 / l00, l20 = v02 / l00;
-      const Real t11 = a11 - l10 * l10;
-      ok = ok && t11 > Real(0);
-      const Real l11 = sqrt(t11 > Real(0) ? t11 : Real(1));
-      const Real l21 = (v12 - l20 * l10) / l11;
-      const Real t22 = a22 - l20 * l20 - l21 * l21;
-      ok = ok && t22 > Real(0);
-      const Real l22 = sqrt(t22 > Real(0) ? t22 : Real(1));
-      if (!ok) lm->pt_fail = 1;  // point block not positive definite: reject this step
-      m00 = Real(1) / l00;
-      m11 = Real(1) / l11;
-      m22 = Real(1) / l22;
-      m10 = -l10 * m00 * m11;
-      m21 = -l21 * m11 * m22;
-      m20 = -(l20 * m00 + l21 * m10) * m22;
-      const Real q0 = m00 * g0;
-      const Real q1 = m10 * g0 + m11 * g1;
-      const Real q2 = m20 * g0 + m21 * g1 + m22 * g2;
-      Real* pa = (Real*)C.paux + (size_t)kPaux * j;
-      pa[0] = m00; pa[1] = m10; pa[2] = m11; pa[3] = m20; pa[4] = m21; pa[5] = m22;
-      pa[6] = q0; pa[7] = q1; pa[8] = q2;
-      pa[9] = d0; pa[10] = d1; pa[11] = d2;
-      pa[12] = g0; pa[13] = g1; pa[14] = g2;
-      pa[15] = 0;
-    }
-    m00 = __shfl_sync(BA_FULL_MASK, m00, seg_start);
-    m10 = __shfl_sync(BA_FULL_MASK, m10, seg_start);
-    m11 = __shfl_sync(BA_FULL_MASK, m11, seg_start);
-    m20 = __shfl_sync(BA_FULL_MASK, m20, seg_start);
-    m21 = __shfl_sync(BA_FULL_MASK, m21, seg_start);
-    m22 = __shfl_sync(BA_FULL_MASK, m22, seg_start);
-    if (!act) continue;
-    // P = Jp M^T (2x3), Z = Jc^T P (6x3)
-    const Real P00 = Jp[0] * m00;
-    const Real P01 = Jp[0] * m10 + Jp[1] * m11;
-    const Real P02 = Jp[0] * m20 + Jp[1] * m21 + Jp[2] * m22;
-    const Real P10 = Jp[3] * m00;
-    const Real P11 = Jp[3] * m10 + Jp[4] * m11;
-    const Real P12 = Jp[3] * m20 + Jp[4] * m21 + Jp[5] * m22;
-    Real rec[kRec];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) rec[kRecJc + i] = Jc[i];
-    rec[kRecR] = r0;
-    rec[kRecR + 1] = r1;
-#pragma unroll
-    for (int m = 0; m < 6; ++m) {
-      rec[kRecZ + 3 * m + 0] = Jc[m] * P00 + Jc[6 + m] * P10;
-      rec[kRecZ + 3 * m + 1] = Jc[m] * P01 + Jc[6 + m] * P11;
-      rec[kRecZ + 3 * m + 2] = Jc[m] * P02 + Jc[6 + m] * P12;
-    }
-    using V2 = typename Vec2<Real>::T;
-    V2* dst = reinterpret_cast<V2*>((Real*)C.rec + (size_t)kRec * o);
-#pragma unroll
-    for (int i = 0; i < kRec / 2; ++i) {
-      V2 v;
-      v.x = rec[2 * i];
-      v.y = rec[2 * i + 1];
-      dst[i] = v;
-    }
-  }
-}
-
-// ------------------------------------------------------------------ K2
-
-template <typename Real>
-__global__ void __launch_bounds__(128) k_cam_reduce(BatchView bv) {
-  __shared__ Real red[4][40];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int g = blockIdx.x; g < bv.total_cchunks; g += gridDim.x) {
-    const int s = find_slot(bv.cchunk_pre, bv.n, g);
-    const DevCluster& C = bv.cl[s];
-    if (!C.lm->active) continue;
-    const int local = g - bv.cchunk_pre[s];
-    const ChunkItem it = C.cchunks[local];
-    Real acc[39];
-#pragma unroll
-    for (int i = 0; i < 39; ++i) acc[i] = 0;
-    using V2 = typename Vec2<Real>::T;
-    for (int e = threadIdx.x; e < it.count; e += blockDim.x) {
-      const int o = C.cam_obs[it.begin + e];
-      const V2* rp = reinterpret_cast<const V2*>((const Real*)C.rec + (size_t)kRec * o);
-      Real rc[kRec];
-#pragma unroll
-      for (int i = 0; i < kRec / 2; ++i) {
-        const V2 v = rp[i];
-        rc[2 * i] = v.x;
-        rc[2 * i + 1] = v.y;
+    __syncthreads();
+    // 2. Schur reductions of the chunk.  Jobs: each free camera (sum of
+    //    Jc^T Jc - Z Z^T, -Jc^T r, Z q, diag(Jc^T Jc) over its observations) and
+    //    each co-visible camera pair (sum of Z_a Z_b^T over its point pairs).
+    //    The host gave every job a run of lanes in proportion to its cost;
+    //    lane i of a job sums a contiguous range of the job's items, and the
+    //    lanes' partial sums are added in lane order.  A chunk with more jobs
+    //    than threads runs one lane per job.
+    const int n_jobs = ch.n_lc + ch.n_lp;
+    const bool spread = n_jobs <= (int)blockDim.x;
+    for (int base = 0; base < (spread ? 1 : n_jobs); base += blockDim.x) {
+      int jb = -1, part = 0, n_parts = 1;
+      if (spread) {
+        // job whose lane run holds this thread (jobs are in lane order)
+        int lo = 0, hi = n_jobs - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (C.jobs[ch.job_begin + mid].lane_begin <= (int)threadIdx.x) lo = mid; else hi = mid - 1;
+        }
+        const Job J = C.jobs[ch.job_begin + lo];
+        if ((int)threadIdx.x < J.lane_begin + J.n_lanes) {
+          jb = lo;
+          part = threadIdx.x - J.lane_begin;
+          n_parts = J.n_lanes;
+        }
+      } else if (base + (int)threadIdx.x < n_jobs) {
+        jb = base + threadIdx.x;
       }
-      const Real* pa = (const Real*)C.paux + (size_t)kPaux * C.obs_pt[o];
-      const Real q0 = pa[6], q1 = pa[7], q2 = pa[8];
-      const Real* Jc = rc + kRecJc;
-      const Real* Z = rc + kRecZ;
-      const Real r0 = rc[kRecR], r1 = rc[kRecR + 1];
-      int t = 0;
+      if (jb >= 0) {
+        const Job J = C.jobs[ch.job_begin + jb];
+        const int i0 = (int)(((long long)J.count * part) / n_parts);
+        const int i1 = (int)(((long long)J.count * (part + 1)) / n_parts);
+        Real acc[39];
 #pragma unroll
-      for (int a = 0; a < 6; ++a) {
+        for (int i = 0; i < 39; ++i) acc[i] = 0;
+        const bool cam = jb < ch.n_lc;
+        if (cam) {
+          for (int e = i0; e < i1; ++e) {
+            const Real* r = srec + (size_t)C.cm_list[J.item_begin + e] * kSrec;
+            Real Jc[12], Z[18];
 #pragma unroll
-        for (int b = a; b < 6; ++b) {
-          acc[t++] += Jc[a] * Jc[b] + Jc[6 + a] * Jc[6 + b] -
-                      (Z[3 * a] * Z[3 * b] + Z[3 * a + 1] * Z[3 * b + 1] + Z[3 * a + 2] * Z[3 * b + 2]);
+            for (int i = 0; i < 12; ++i) Jc[i] = r[i];
+#pragma unroll
+            for (int i = 0; i < 18; ++i) Z[i] = r[kSrecZ + i];
+            const Real r0 = r[kSrecR], r1 = r[kSrecR + 1];
+            const Real q0 = r[kSrecQ], q1 = r[kSrecQ + 1], q2 = r[kSrecQ + 2];
+            int t = 0;
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+#pragma unroll
+              for (int b = a; b < 6; ++b) {
+                acc[t++] += Jc[a] * Jc[b] + Jc[6 + a] * Jc[6 + b] -
+                            (Z[3 * a] * Z[3 * b] + Z[3 * a + 1] * Z[3 * b + 1] + Z[3 * a + 2] * Z[3 * b + 2]);
+              }
+            }
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+              acc[21 + a] -= Jc[a] * r0 + Jc[6 + a] * r1;
+              acc[27 + a] += Z[3 * a] * q0 + Z[3 * a + 1] * q1 + Z[3 * a + 2] * q2;
+              acc[33 + a] += Jc[a] * Jc[a] + Jc[6 + a] * Jc[6 + a];
+            }
+          }
+        } else {
+          for (int e = i0; e < i1; ++e) {
+            const unsigned int u = C.pent[J.item_begin + e];
+            const Real* za = srec + (size_t)(u & 0xffffu) * kSrec + kSrecZ;
+            const Real* zb = srec + (size_t)(u >> 16) * kSrec + kSrecZ;
+            Real Za[18], Zb[18];
+#pragma unroll
+            for (int i = 0; i < 18; ++i) {
+              Za[i] = za[i];
+              Zb[i] = zb[i];
+            }
+#pragma unroll
+            for (int a = 0; a < 6; ++a)
+#pragma unroll
+              for (int b = 0; b < 6; ++b)
+                acc[6 * a + b] += Za[3 * a] * Zb[3 * b] + Za[3 * a + 1] * Zb[3 * b + 1] + Za[3 * a + 2] * Zb[3 * b + 2];
+          }
+        }
+        const int width = cam ? 39 : 36;
+        if (n_parts == 1) {
+          Real* out = cam ? (Real*)C.campart + (size_t)kCamPart * J.slot : (Real*)C.pairpart + (size_t)kPairPart * J.slot;
+#pragma unroll
+          for (int i = 0; i < 39; ++i)
+            if (i < width) out[i] = acc[i];
+        } else {
+          Real* lp = lanepart + (size_t)threadIdx.x * kLanePart;
+#pragma unroll
+          for (int i = 0; i < 39; ++i) lp[i] = acc[i];
         }
       }
-#pragma unroll
-      for (int a = 0; a < 6; ++a) {
-        acc[21 + a] -= Jc[a] * r0 + Jc[6 + a] * r1;
-        acc[27 + a] += Z[3 * a] * q0 + Z[3 * a + 1] * q1 + Z[3 * a + 2] * q2;
-        acc[33 + a] += Jc[a] * Jc[a] + Jc[6 + a] * Jc[6 + a];
+    }
+    if (spread) {
+      __syncthreads();
+      // multi-lane jobs: element e of job j = sum over its lanes, in lane order
+      for (int u = threadIdx.x; u < ch.n_mjobs * kLanePart; u += blockDim.x) {
+        const int mj = u / kLanePart, e = u - mj * kLanePart;
+        const int jb = C.mjobs[ch.mjob_begin + mj];
+        const bool cam = jb < ch.n_lc;
+        if (e >= (cam ? 39 : 36)) continue;
+        const Job J = C.jobs[ch.job_begin + jb];
+        Real v = 0;
+        for (int l = J.lane_begin; l < J.lane_begin + J.n_lanes; ++l) v += lanepart[(size_t)l * kLanePart + e];
+        Real* out = cam ? (Real*)C.campart + (size_t)kCamPart * J.slot : (Real*)C.pairpart + (size_t)kPairPart * J.slot;
+        out[e] = v;
       }
-    }
-#pragma unroll
-    for (int i = 0; i < 39; ++i) {
-      const Real v = warp_sum(acc[i]);
-      if (lane == 0) red[wid][i] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 39) {
-      const int i = threadIdx.x;
-      const Real v = (red[0][i] + red[1][i]) + (red[2][i] + red[3][i]);
-      ((Real*)C.campart)[(size_t)kCamPart * local + i] = v;
     }
     __syncthreads();
   }
 }
 
-// ------------------------------------------------------------------ K3
+// ------------------------------------------------------------------ partial sums -> per-camera / per-pair sums
 
+// Warp per free camera or camera pair of a cluster: sum its chunk partials in
+// chunk order (lane i owns element i and i + 32), in binary64.
 template <typename Real>
-__global__ void __launch_bounds__(256) k_pair_reduce(BatchView bv) {
+__global__ void __launch_bounds__(256) k_partial_reduce(BatchView bv) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  using V2 = typename Vec2<Real>::T;
-  for (int g = warp; g < bv.total_pchunks; g += nwarps) {
-    const int s = find_slot(bv.pchunk_pre, bv.n, g);
+  for (int g = warp; g < bv.total_items; g += nwarps) {
+    const int s = find_slot(bv.item_pre, bv.n, g);
     const DevCluster& C = bv.cl[s];
     if (!C.lm->active) continue;
-    const int local = g - bv.pchunk_pre[s];
-    const ChunkItem it = C.pchunks[local];
-    Real acc[36];
-#pragma unroll
-    for (int i = 0; i < 36; ++i) acc[i] = 0;
-    for (int e = lane; e < it.count; e += 32) {
-      const int2 ab = C.pair_ent[it.begin + e];
-      const V2* pa = reinterpret_cast<const V2*>((const Real*)C.rec + (size_t)kRec * ab.x + kRecZ);
-      const V2* pb = reinterpret_cast<const V2*>((const Real*)C.rec + (size_t)kRec * ab.y + kRecZ);
-      Real Za[18], Zb[18];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const V2 x = pa[i], y = pb[i];
-        Za[2 * i] = x.x; Za[2 * i + 1] = x.y;
-        Zb[2 * i] = y.x; Zb[2 * i + 1] = y.y;
-      }
-#pragma unroll
-      for (int a = 0; a < 6; ++a)
-#pragma unroll
-        for (int b = 0; b < 6; ++b)
-          acc[6 * a + b] += Za[3 * a] * Zb[3 * b] + Za[3 * a + 1] * Zb[3 * b + 1] + Za[3 * a + 2] * Zb[3 * b + 2];
+    const int it = g - bv.item_pre[s];
+    const bool cam = it < C.n_free;
+    const int key = cam ? it : it - C.n_free;
+    const int width = cam ? 39 : 36, stride = cam ? kCamPart : kPairPart;
+    const int* slots = cam ? C.cam_slots : C.pair_slots;
+    const int b = cam ? C.cam_slot_begin[key] : C.pair_slot_begin[key];
+    const int e = cam ? C.cam_slot_begin[key + 1] : C.pair_slot_begin[key + 1];
+    const Real* part = (const Real*)(cam ? C.campart : C.pairpart);
+    double* out = cam ? C.camsum + (size_t)kCamPart * key : C.pairsum + (size_t)kPairPart * key;
+    const bool two = lane + 32 < width;
+    double v0 = 0.0, v1 = 0.0;
+    int p = b;
+    for (; p + 4 <= e; p += 4) {  // four independent loads in flight, added in slot order
+      const Real* a0 = part + (size_t)stride * slots[p];
+      const Real* a1 = part + (size_t)stride * slots[p + 1];
+      const Real* a2 = part + (size_t)stride * slots[p + 2];
+      const Real* a3 = part + (size_t)stride * slots[p + 3];
+      const double x0 = lane < width ? (double)a0[lane] : 0.0, x1 = lane < width ? (double)a1[lane] : 0.0;
+      const double x2 = lane < width ? (double)a2[lane] : 0.0, x3 = lane < width ? (double)a3[lane] : 0.0;
+      const double y0 = two ? (double)a0[lane + 32] : 0.0, y1 = two ? (double)a1[lane + 32] : 0.0;
+      const double y2 = two ? (double)a2[lane + 32] : 0.0, y3 = two ? (double)a3[lane + 32] : 0.0;
+      v0 += x0; v0 += x1; v0 += x2; v0 += x3;
+      v1 += y0; v1 += y1; v1 += y2; v1 += y3;
     }
-#pragma unroll
-    for (int i = 0; i < 36; ++i) {
-      const Real v = warp_sum(acc[i]);
-      if (lane == 0) ((Real*)C.pairpart)[(size_t)kPairPart * local + i] = v;
+    for (; p < e; ++p) {
+      const Real* a0 = part + (size_t)stride * slots[p];
+      if (lane < width) v0 += (double)a0[lane];
+      if (two) v1 += (double)a0[lane + 32];
     }
+    if (lane < width) out[lane] = v0;
+    if (two) out[lane + 32] = v1;
   }
 }
 
@@ -446,21 +532,120 @@ size_t factor_smem_bytes(int max_n) {
   return doubles * sizeof(double);
 }
 
-// Solve L L^T x = b in place (b in shared memory), one warp.
-__device__ void chol_solve_warp(const double* A, double* b, int n, int lane) {
-  for (int j = 0; j < n; ++j) {
-    const double yj = b[j] / A[pk(j, j)];
-    __syncwarp();
-    if (lane == 0) b[j] = yj;
-    for (int i = j + 1 + lane; i < n; i += 32) b[i] -= A[pk(i, j)] * yj;
-    __syncwarp();
+constexpr int kFactorNB = 8;  // panel width of the blocked factorisation and solves
+
+// Blocked right-looking Cholesky A = L L^T of the packed lower matrix in
+// shared memory, by the whole CTA.  Per panel of kFactorNB columns: factor
+// the panel (column by column over all rows below), then update the trailing
+// matrix with the panel in 4x4 register tiles.  colbuf: shared scratch [n].
+// Sets *fail (shared) when a pivot is not positive.
+__device__ void chol_blocked(double* A, int n, double* colbuf, int* fail) {
+  const int tid = threadIdx.x, bs = blockDim.x;
+  for (int k0 = 0; k0 < n; k0 += kFactorNB) {
+    const int k1 = min(k0 + kFactorNB, n);
+    for (int j = k0; j < k1; ++j) {
+      if (tid == 0) {
+        const double d = A[pk(j, j)];
+        if (!(d > 0.0)) *fail = 1;
+        A[pk(j, j)] = sqrt(d > 0.0 ? d : 1.0);
+      }
+      __syncthreads();
+      if (*fail) return;
+      const double inv = 1.0 / A[pk(j, j)];
+      for (int i = j + 1 + tid; i < n; i += bs) {
+        const double l = A[pk(i, j)] * inv;
+        A[pk(i, j)] = l;
+        colbuf[i] = l;
+      }
+      __syncthreads();
+      const int w = k1 - j - 1;  // remaining panel columns
+      if (w > 0) {
+        const int rows = n - j - 1;
+        for (int u = tid; u < rows * w; u += bs) {
+          const int i = j + 1 + u / w, c = j + 1 + u % w;
+          if (c <= i) A[pk(i, c)] -= colbuf[i] * colbuf[c];
+        }
+        __syncthreads();
+      }
+    }
+    const int m = n - k1;  // trailing matrix rows/cols k1..n-1
+    if (m > 0) {
+      const int nt = (m + 3) >> 2;
+      const int ntiles = nt * (nt + 1) / 2;
+      for (int t = tid; t < ntiles; t += bs) {
+        int bi = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+        while (bi * (bi + 1) / 2 > t) --bi;
+        const int bc = t - bi * (bi + 1) / 2;
+        const int i0 = k1 + 4 * bi, c0 = k1 + 4 * bc;
+        double acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+        for (int q = k0; q < k1; ++q) {
+          double li[4], lc[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            li[a] = i0 + a < n ? A[pk(i0 + a, q)] : 0.0;
+            lc[a] = c0 + a < n ? A[pk(c0 + a, q)] : 0.0;
+          }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += li[a] * lc[b];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int i = i0 + a, c = c0 + b;
+            if (i < n && c <= i) A[pk(i, c)] -= acc[a][b];
+          }
+      }
+      __syncthreads();
+    }
   }
-  for (int j = n - 1; j >= 0; --j) {
-    const double xj = b[j] / A[pk(j, j)];
-    __syncwarp();
-    if (lane == 0) b[j] = xj;
-    for (int i = lane; i < j; i += 32) b[i] -= A[pk(j, i)] * xj;
-    __syncwarp();
+}
+
+// Solve L L^T x = b in place (b in shared memory), by the whole CTA: per
+// panel, one thread solves the small diagonal triangle and all threads update
+// the rest of the vector with the panel.
+__device__ void chol_solve_blocked(const double* A, double* b, int n) {
+  const int tid = threadIdx.x, bs = blockDim.x;
+  for (int k0 = 0; k0 < n; k0 += kFactorNB) {  // L y = b
+    const int k1 = min(k0 + kFactorNB, n);
+    if (tid == 0) {
+      for (int j = k0; j < k1; ++j) {
+        double s = b[j];
+        for (int q = k0; q < j; ++q) s -= A[pk(j, q)] * b[q];
+        b[j] = s / A[pk(j, j)];
+      }
+    }
+    __syncthreads();
+    for (int i = k1 + tid; i < n; i += bs) {
+      double s = 0.0;
+      for (int q = k0; q < k1; ++q) s += A[pk(i, q)] * b[q];
+      b[i] -= s;
+    }
+    __syncthreads();
+  }
+  for (int k1 = n; k1 > 0; k1 -= kFactorNB) {  // L^T x = y
+    const int k0 = max(k1 - kFactorNB, 0);
+    if (tid == 0) {
+      for (int j = k1 - 1; j >= k0; --j) {
+        double s = b[j];
+        for (int q = j + 1; q < k1; ++q) s -= A[pk(q, j)] * b[q];
+        b[j] = s / A[pk(j, j)];
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < k0; i += bs) {
+      double s = 0.0;
+      for (int q = k0; q < k1; ++q) s += A[pk(q, i)] * b[q];
+      b[i] -= s;
+    }
+    __syncthreads();
   }
 }
 
@@ -470,7 +655,8 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
   extern __shared__ double sm[];
   __shared__ int fail;
   const int tid = threadIdx.x, bs = blockDim.x;
-  for (int s = blockIdx.x; s < bv.n; s += gridDim.x) {
+  for (int so = blockIdx.x; so < bv.n; so += gridDim.x) {
+    const int s = bv.factor_order[so];  // largest systems first
     const DevCluster& C = bv.cl[s];
     LmState* lm = C.lm;
     if (!lm->active && !assemble_only) continue;
@@ -486,13 +672,10 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
     const double* Rc = C.R + (size_t)cur * nc * 9;
     const double* Tc = C.T + (size_t)cur * nc * 3;
 
-    // camera chunk partials, summed in chunk order
+    // per-camera sums (k_partial_reduce)
     for (int idx = tid; idx < nf * 39; idx += bs) {
       const int f = idx / 39, e = idx - 39 * f;
-      double v = 0.0;
-      for (int p = C.cam_part_begin[f]; p < C.cam_part_begin[f + 1]; ++p)
-        v += (double)((const Real*)C.campart)[(size_t)kCamPart * p + e];
-      cd[40 * f + e] = v;
+      cd[40 * f + e] = C.camsum[(size_t)kCamPart * f + e];
     }
     for (int f = tid; f < nf; f += bs) {
       const int k = C.cam_of_free[f];
@@ -529,9 +712,7 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
     for (int idx = tid; idx < C.n_pairs * 36; idx += bs) {
       const int p = idx / 36, e = idx - 36 * p;
       const int i = e / 6, c = e - 6 * i;
-      double v = 0.0;
-      for (int q = C.pair_part_begin[p]; q < C.pair_part_begin[p + 1]; ++q)
-        v += (double)((const Real*)C.pairpart)[(size_t)kPairPart * q + e];
+      const double v = C.pairsum[(size_t)kPairPart * p + e];
       const int2 key = C.pair_key[p];
       A[pk(6 * key.y + c, 6 * key.x + i)] = -v;
     }
@@ -544,35 +725,13 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
       __syncthreads();
       continue;
     }
-    // right-looking Cholesky in shared memory
-    for (int j = 0; j < n; ++j) {
-      if (tid == 0) {
-        const double d = A[pk(j, j)];
-        if (!(d > 0.0)) fail = 1;
-        A[pk(j, j)] = sqrt(d > 0.0 ? d : 1.0);
-      }
-      __syncthreads();
-      if (fail) break;
-      const double inv = 1.0 / A[pk(j, j)];
-      for (int i = j + 1 + tid; i < n; i += bs) A[pk(i, j)] *= inv;
-      __syncthreads();
-      const int m = n - j - 1;
-      const int total = m * (m + 1) / 2;
-      for (int u = tid; u < total; u += bs) {
-        int ii = (int)((sqrtf(8.0f * (float)u + 1.0f) - 1.0f) * 0.5f);
-        while ((ii + 1) * (ii + 2) / 2 <= u) ++ii;
-        while (ii * (ii + 1) / 2 > u) --ii;
-        const int cc = u - ii * (ii + 1) / 2;
-        const int row = j + 1 + ii, col = j + 1 + cc;
-        A[pk(row, col)] -= A[pk(row, j)] * A[pk(col, j)];
-      }
-      __syncthreads();
-    }
+    __syncthreads();  // the copy of S above reads A
+    // blocked right-looking Cholesky in shared memory (t[] is the column buffer)
+    if (!fail) chol_blocked(A, n, t, &fail);
     __syncthreads();
     const int status = fail ? BA_STATUS_NOT_PD : 0;
     if (!fail) {
-      if (tid < 32) chol_solve_warp(A, b, n, tid);
-      __syncthreads();
+      chol_solve_blocked(A, b, n);
       for (int idx = tid; idx < n; idx += bs) x[idx] = b[idx];
       __syncthreads();
       // iterative refinement against the FP64 system kept in global memory
@@ -585,8 +744,7 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
           if (lane == 0) t[r] = C.rhs[r] - acc;
         }
         __syncthreads();
-        if (tid < 32) chol_solve_warp(A, t, n, tid);
-        __syncthreads();
+        chol_solve_blocked(A, t, n);
         for (int idx = tid; idx < n; idx += bs) x[idx] += t[idx];
         __syncthreads();
       }
@@ -642,41 +800,31 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
 
 // ------------------------------------------------------------------ K5
 
+// Back-substitution and candidate cost, warp per tile.  The tile is
+// linearised again (the same arithmetic as in k_lin_schur) instead of reading
+// per-observation records back from memory.
 template <bool MIXED>
 __global__ void __launch_bounds__(256) k_backsub_cost(BatchView bv) {
   using Real = typename RealOf<MIXED>::T;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  using V2 = typename Vec2<Real>::T;
   for (int g = warp; g < bv.total_tiles; g += nwarps) {
     const int s = find_slot(bv.tile_pre, bv.n, g);
     const DevCluster& C = bv.cl[s];
-    const LmState* lm = C.lm;
+    LmState* lm = C.lm;
     if (!lm->active || lm->status != 0) continue;
     const int local = g - bv.tile_pre[s];
     const Tile tl = C.tiles[local];
-    const bool act = lane < tl.n_obs;
-    const int o = tl.obs_begin + (act ? lane : 0);
-    const int k = act ? C.obs_cam[o] : 0;
-    const int j = act ? C.obs_pt[o] : -1 - lane;
-    int seg_start, seg_end;
-    segments(j, lane, seg_start, seg_end);
+    TileLin<MIXED> L;
+    linearize_tile<MIXED>(C, lm, tl, lane, false, L);
     const int cur = lm->cur;
     Real mu_r;
     if constexpr (MIXED) mu_r = lm->mu_f; else mu_r = lm->mu;
     // t = Z^T dc_k
     Real t0 = 0, t1 = 0, t2 = 0;
-    const int f = act ? C.free_idx[k] : -1;
+    const int f = L.act ? C.free_idx[L.k] : -1;
     if (f >= 0) {
-      const V2* zp = reinterpret_cast<const V2*>((const Real*)C.rec + (size_t)kRec * o + kRecZ);
-      Real Z[18];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const V2 v = zp[i];
-        Z[2 * i] = v.x;
-        Z[2 * i + 1] = v.y;
-      }
       Real d[6];
       if constexpr (MIXED) {
         const float2* d2 = reinterpret_cast<const float2*>(C.dc32 + 6 * f);
@@ -688,31 +836,31 @@ __global__ void __launch_bounds__(256) k_backsub_cost(BatchView bv) {
       }
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
-        const Real dm = d[m];
-        t0 += Z[3 * m] * dm;
-        t1 += Z[3 * m + 1] * dm;
-        t2 += Z[3 * m + 2] * dm;
+        t0 += L.Z[3 * m] * d[m];
+        t1 += L.Z[3 * m + 1] * d[m];
+        t2 += L.Z[3 * m + 2] * d[m];
       }
     }
-    t0 = seg_reduce(t0, lane, seg_start, seg_end);
-    t1 = seg_reduce(t1, lane, seg_start, seg_end);
-    t2 = seg_reduce(t2, lane, seg_start, seg_end);
+    t0 = seg_reduce(t0, lane, L.seg_start, L.seg_end);
+    t1 = seg_reduce(t1, lane, L.seg_start, L.seg_end);
+    t2 = seg_reduce(t2, lane, L.seg_start, L.seg_end);
     // head: dX = M^T (q - t), candidate point, pred term
     Real dX0 = 0, dX1 = 0, dX2 = 0;
-    Real pp = 0;  // dX^T (mu Dp dX + gp), summed below in FP64
-    if (act && lane == seg_start) {
-      const Real* pa = (const Real*)C.paux + (size_t)kPaux * j;
-      const Real v0 = pa[6] - t0, v1 = pa[7] - t1, v2 = pa[8] - t2;
-      dX0 = pa[0] * v0 + pa[1] * v1 + pa[3] * v2;
-      dX1 = pa[2] * v1 + pa[4] * v2;
-      dX2 = pa[5] * v2;
-      const Real m = mu_r;
-      pp = dX0 * (m * pa[9] * dX0 + pa[12]) + dX1 * (m * pa[10] * dX1 + pa[13]) + dX2 * (m * pa[11] * dX2 + pa[14]);
+    Real pp = 0;  // dX^T (mu Dp dX + gp)
+    if (L.head) {
+      const Real v0 = L.q0 - t0, v1 = L.q1 - t1, v2 = L.q2 - t2;
+      dX0 = L.m00 * v0 + L.m10 * v1 + L.m20 * v2;
+      dX1 = L.m11 * v1 + L.m21 * v2;
+      dX2 = L.m22 * v2;
+      pp = dX0 * (mu_r * L.d0 * dX0 + L.g0) + dX1 * (mu_r * L.d1 * dX1 + L.g1) + dX2 * (mu_r * L.d2 * dX2 + L.g2);
     }
+    const int o = L.o, k = L.k, j = L.j;
+    const bool act = L.act;
+    const int seg_start = L.seg_start;
     double cost = 0.0;
     if constexpr (MIXED) {
       dfl x0{0.f, 0.f}, x1{0.f, 0.f}, x2{0.f, 0.f};
-      if (act && lane == seg_start) {
+      if (L.head) {
         const float2* xp = xdf_ptr(C, cur, j);
         const float2 a = xp[0], b = xp[1], c = xp[2];
         x0 = df_add_f(dfl{a.x, a.y}, dX0);
@@ -743,7 +891,7 @@ __global__ void __launch_bounds__(256) k_backsub_cost(BatchView bv) {
       if (lane == 0) cost = df_to_d(cst);
     } else {
       double x0 = 0.0, x1 = 0.0, x2 = 0.0;
-      if (act && lane == seg_start) {
+      if (L.head) {
         const double* X = C.X + ((size_t)cur * C.n_pts + j) * 3;
         x0 = X[0] + (double)dX0;
         x1 = X[1] + (double)dX1;
@@ -933,17 +1081,13 @@ __global__ void __launch_bounds__(256) k_lm_update(BatchView bv) {
 
 // ------------------------------------------------------------------ diagnostics
 
-template <typename Real>
 __global__ void k_grad_norm(BatchView bv, double* out) {
   __shared__ double red[8];
   for (int s = blockIdx.x; s < bv.n; s += gridDim.x) {
     const DevCluster& C = bv.cl[s];
     double m = 0.0;
     for (int i = threadIdx.x; i < 6 * C.n_free; i += blockDim.x) m = fmax(m, fabs(C.gc[i]));
-    for (int j = threadIdx.x; j < C.n_pts; j += blockDim.x) {
-      const Real* pa = (const Real*)C.paux + (size_t)kPaux * j;
-      m = fmax(m, fmax(fabs((double)pa[12]), fmax(fabs((double)pa[13]), fabs((double)pa[14]))));
-    }
+    for (int t = threadIdx.x; t < C.n_tiles; t += blockDim.x) m = fmax(m, C.tilepart[2 * t + 1]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(BA_FULL_MASK, m, off));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -986,9 +1130,10 @@ __global__ void k_export_points(const DevCluster* dcl, int mixed, double* out) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < C.n_pts; j += gridDim.x * blockDim.x) {
     double X[3];
     point_f64(C, mixed, cur, j, X);
-    out[3 * j] = X[0];
-    out[3 * j + 1] = X[1];
-    out[3 * j + 2] = X[2];
+    const int u = C.pt_perm[j];  // caller's index
+    out[3 * u] = X[0];
+    out[3 * u + 1] = X[1];
+    out[3 * u + 2] = X[2];
   }
 }
 
@@ -1163,14 +1308,31 @@ void launch_cost_init(const BatchView& bv, bool mixed, cudaStream_t st) {
   else launch_cost_init_t<false>(bv, st);
 }
 
+int chunk_obs(bool mixed) { return mixed ? kChunkObsMixed : kChunkObsF64; }
+int chunk_tiles(bool mixed) { return mixed ? kChunkTilesMixed : kChunkTilesF64; }
+
+static size_t chunk_smem_bytes(bool mixed) {
+  return ((size_t)chunk_obs(mixed) * kSrec + (size_t)kChunkThreads * kLanePart) * (mixed ? sizeof(float) : sizeof(double));
+}
+
+template <bool MIXED>
+static void launch_lin_schur(const BatchView& bv, int diag, cudaStream_t st) {
+  LAUNCH(KK_LINEARIZE, st,
+         k_lin_schur<MIXED><<<grid_for(bv.total_chunks, 1, num_sms() * 8), kChunkThreads, chunk_smem_bytes(MIXED),
+                              st>>>(bv, diag));
+}
+
+template <bool MIXED>
+static void launch_partial_reduce(const BatchView& bv, cudaStream_t st) {
+  using Real = typename RealOf<MIXED>::T;
+  LAUNCH(KK_CAM_REDUCE, st, k_partial_reduce<Real><<<grid_for(bv.total_items, 8, num_sms() * 16), 256, 0, st>>>(bv));
+}
+
 template <bool MIXED>
 static void launch_iteration_t(const BatchView& bv, int refine_steps, cudaStream_t st) {
-  using Real = typename RealOf<MIXED>::T;
   const int sms = num_sms();
-  LAUNCH(KK_LINEARIZE, st, k_linearize<MIXED><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
-  LAUNCH(KK_CAM_REDUCE, st, k_cam_reduce<Real><<<grid_for(bv.total_cchunks, 1, sms * 32), 128, 0, st>>>(bv));
-  if (bv.total_pchunks > 0)
-    LAUNCH(KK_PAIR_REDUCE, st, k_pair_reduce<Real><<<grid_for(bv.total_pchunks, 8, sms * 16), 256, 0, st>>>(bv));
+  launch_lin_schur<MIXED>(bv, 0, st);
+  launch_partial_reduce<MIXED>(bv, st);
   const size_t smem = factor_smem_bytes(bv.max_n);
   LAUNCH(KK_FACTOR, st, k_factor_solve<MIXED><<<grid_for(bv.n, 1, 65535), 512, smem, st>>>(bv, refine_steps, 0));
   LAUNCH(KK_BACKSUB, st, k_backsub_cost<MIXED><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
@@ -1184,15 +1346,11 @@ void launch_iteration(const BatchView& bv, bool mixed, int refine_steps, cudaStr
 
 template <bool MIXED>
 static void launch_grad_norm_t(const BatchView& bv, double* out, cudaStream_t st) {
-  using Real = typename RealOf<MIXED>::T;
-  const int sms = num_sms();
-  LAUNCH(KK_LINEARIZE, st, k_linearize<MIXED><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
-  LAUNCH(KK_CAM_REDUCE, st, k_cam_reduce<Real><<<grid_for(bv.total_cchunks, 1, sms * 32), 128, 0, st>>>(bv));
-  if (bv.total_pchunks > 0)
-    LAUNCH(KK_PAIR_REDUCE, st, k_pair_reduce<Real><<<grid_for(bv.total_pchunks, 8, sms * 16), 256, 0, st>>>(bv));
+  launch_lin_schur<MIXED>(bv, 1, st);
+  launch_partial_reduce<MIXED>(bv, st);
   LAUNCH(KK_FACTOR, st,
          k_factor_solve<MIXED><<<grid_for(bv.n, 1, 65535), 512, factor_smem_bytes(bv.max_n), st>>>(bv, 0, 1));
-  LAUNCH(KK_OTHER, st, k_grad_norm<Real><<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv, out));
+  LAUNCH(KK_OTHER, st, k_grad_norm<<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv, out));
 }
 
 void launch_grad_norm(const BatchView& bv, bool mixed, double* out, cudaStream_t st) {
@@ -1212,7 +1370,12 @@ cudaError_t set_kernel_attributes(int max_n) {
   const size_t smem = factor_smem_bytes(max_n);
   cudaError_t e = cudaFuncSetAttribute(k_factor_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_factor_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(k_factor_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_lin_schur<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chunk_smem_bytes(true));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_lin_schur<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)chunk_smem_bytes(false));
 }
 
 }  // namespace bagpu

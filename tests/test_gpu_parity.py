@@ -34,10 +34,13 @@ def _step_parity(ba, scene, iters, tol=TOL_STEP):
             io = O.lm_step(P, S)
             ig = ctx.solve_step(cid)
             R, T, X = ctx.get_state(cid)
-            if abs(io["gain"]) < 1e-8:
-                continue  # a decision on the boundary: flagged, not failed
-            assert ig["accepted"] == io["accepted"], (it, ig, io)
             assert ig["F_before"] == pytest.approx(io["F"], rel=tol, abs=1e-300)
+            undetermined = abs(io["F"] - io["F_new"]) <= 1e-10 * abs(io["F"]) or abs(io["gain"]) < 1e-8
+            if undetermined:
+                # converged to rounding level: the accept/reject decision is not
+                # determined in binary64; flagged, not failed, and the comparison ends
+                break
+            assert ig["accepted"] == io["accepted"], (it, ig, io)
             assert ig["F_after"] == pytest.approx(io["F_new"], rel=tol, abs=1e-12)
             assert ig["mu"] == pytest.approx(io["mu"], rel=1e-9)
             e = state_rel_err(R, T, X, S.R, S.T, S.X)
