@@ -52,7 +52,10 @@ def parse():
     ap.add_argument("--fp64-sample", type=int, default=16, help="clusters timed on the plain FP64 path")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU oracle baseline")
     ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--no-extras", action="store_true", help="skip FP64 / CPU / e2e legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip FP64 / CPU / e2e / serving legs")
+    ap.add_argument("--serving-flights", type=int, default=16)
+    ap.add_argument("--serving-rate", type=float, default=200.0, help="requests/s, Poisson, all flights")
+    ap.add_argument("--serving-iters", type=int, default=10)
     return ap.parse_args()
 
 
@@ -63,13 +66,108 @@ def dist_env():
     return rank, world, local
 
 
-def make_workload(replica, n_clusters):
-    """Generate the batch in a spawn pool (before any CUDA call)."""
+def make_workload(replica, n_clusters, n_flights=0):
+    """Generate the batch (and the serving flights) in a spawn pool, before
+    any CUDA call."""
     import multiprocessing as mp
     n = min(16, os.cpu_count() or 1)
     ctx = mp.get_context("spawn")
     with ctx.Pool(n) as pool:
-        return sg.batch_c3(replica=replica, n_clusters=n_clusters, pool=pool)
+        scenes = sg.batch_c3(replica=replica, n_clusters=n_clusters, pool=pool)
+        flights = pool.map(serving_flight, [4000 + 100 * replica + f for f in range(n_flights)]) if n_flights else []
+    return scenes, flights
+
+
+def serving_flight(seed):
+    """One simulated flight (3 strips x 40 images, c2 point density) cut into
+    sliding windows of 12-32 images: [(cluster, cams, pts, warm maps)]."""
+    fl = sg.flight(seed)
+    out = []
+    prev = None
+    for (s, e, nf) in sg.window_plan(seed, fl["n_cams"]):
+        c, cams, pts = sg.window_cluster(fl, s, e, nf)
+        maps = sg.warm_maps(prev[0], prev[1], cams, pts) if prev is not None else None
+        out.append((c, maps))
+        prev = (cams, pts)
+    return out
+
+
+def torch_device():
+    import torch
+    return torch.cuda.current_device()
+
+
+def serving_leg(args, ba, stream, flights):
+    """Poisson arrivals of sliding-window requests from several flights; each
+    window warm-starts on the device from the flight's previous window and is
+    submitted to the continuous-batching scheduler.  Latency = completion -
+    arrival (host clock)."""
+    import time as _t
+    from concurrent.futures import ThreadPoolExecutor
+    rng = np.random.Generator(np.random.PCG64(7))
+    rate_f = args.serving_rate / max(1, len(flights))
+    arrivals = [np.cumsum(rng.exponential(1.0 / rate_f, len(w))) for w in flights]
+    ctx = ba.Context(device=torch_device(), precision=ba.BA_MIXED,
+                     stream=stream.cuda_stream, n_slots=64, hbm_budget_bytes=16 << 30)
+    iters = args.serving_iters
+
+    def create_and_submit(f, w, prev_id):
+        c, maps = flights[f][w]
+        while True:
+            try:
+                if maps is None:
+                    cid = ctx.create_cluster(c)
+                else:
+                    cid = ctx.create_cluster(c, warm_from=prev_id, warm_cam_map=maps[0], warm_pt_map=maps[1])
+                break
+            except ba.BAError as e:  # HBM budget: wait for completions to free memory
+                if e.status != ba.BA_ERR_BUDGET:
+                    raise
+                _t.sleep(0.001)
+        return cid, ctx.submit(cid, iters)
+
+    nxt = [0] * len(flights)
+    prev = [None] * len(flights)
+    old = [None] * len(flights)
+    pending, inflight = {}, {}
+    lat, obs_done = [], 0
+    max_inflight = 0
+    with ThreadPoolExecutor(8) as ex:
+        t0 = _t.perf_counter()
+        while any(nxt[f] < len(flights[f]) for f in range(len(flights))) or pending or inflight:
+            now = _t.perf_counter() - t0
+            for f in range(len(flights)):
+                if (nxt[f] < len(flights[f]) and f not in pending and f not in inflight
+                        and arrivals[f][nxt[f]] <= now):
+                    pending[f] = ex.submit(create_and_submit, f, nxt[f], prev[f])
+            for f in list(pending):
+                if pending[f].done():
+                    cid, t = pending.pop(f).result()
+                    inflight[f] = (cid, t)
+            max_inflight = max(max_inflight, len(inflight))
+            for f in list(inflight):
+                cid, t = inflight[f]
+                r = ctx.poll(t)
+                if r is None:
+                    continue
+                inflight.pop(f)
+                done = _t.perf_counter() - t0
+                lat.append(1e3 * (done - arrivals[f][nxt[f]]))
+                obs_done += flights[f][nxt[f]][0]["n_obs"] * iters
+                if old[f] is not None:
+                    ctx.destroy_cluster(old[f])
+                old[f], prev[f] = prev[f], cid
+                nxt[f] += 1
+            _t.sleep(0.0002)
+        span = _t.perf_counter() - t0
+    ctx.close()
+    lat = np.array(lat)
+    return {"requests": int(len(lat)), "flights": len(flights), "arrival_rate_req_s": args.serving_rate,
+            "iters_per_request": iters, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+            "throughput_req_s": len(lat) / span, "obs_per_s": obs_done / span, "max_in_flight": max_inflight,
+            "window_images": "12-32, last 25 % reused, first half of the overlap fixed, device warm start",
+            "note": "latency = completion - arrival, host clock; includes cluster creation (presort + upload)"}
 
 
 def pair_entries(scene):
@@ -239,7 +337,8 @@ def main():
         run_reference(args)
         return
     rank, world, local = dist_env()
-    scenes = make_workload(rank, args.clusters)  # spawn pool before the first CUDA call
+    n_fl = 0 if (args.no_extras or rank != 0 or world != 1) else args.serving_flights
+    scenes, flights = make_workload(rank, args.clusters, n_fl)  # spawn pool before the first CUDA call
     total_obs = sum(s["n_obs"] for s in scenes)
     iters = args.iters
 
@@ -318,7 +417,7 @@ def main():
             "kernels": kernels}
 
     if not args.no_extras and rank == 0 and world == 1:
-        line.update(extras(args, ba, torch, scenes, ids, ctx, stream, iters, value))
+        line.update(extras(args, ba, torch, scenes, ids, ctx, stream, iters, value, flights))
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -326,7 +425,7 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed):
+def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flights):
     out = {}
     # accuracy of the mixed path on a few clusters against the FP64 path
     sample = list(range(min(args.fp64_sample, len(scenes))))
@@ -385,6 +484,8 @@ def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed):
                               "ba_get_state to host"}
     out["cpu_baseline"] = oracle_obs_per_s(scenes, iters, args.cpu_seconds)
     out["paper_context"] = "paper: full BA per cluster in < 2 s, MATLAB on an i7 13th-gen 20-core laptop, no GPU"
+    if flights:
+        out["serving"] = serving_leg(args, ba, stream, flights)
     return out
 
 

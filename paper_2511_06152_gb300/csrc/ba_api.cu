@@ -62,6 +62,27 @@ struct Ticket {
   std::chrono::steady_clock::time_point t_submit;
 };
 
+// Serving slots (see scheduler_loop).
+struct SlotTable {
+  int n = 0;
+  char* dbuf = nullptr;
+  size_t bytes = 0;
+  BatchView bv{};
+  DevCluster* d_desc = nullptr;
+  int* d_pre = nullptr;
+  int* d_order = nullptr;
+  int* d_arm = nullptr;
+  LmState* d_lm = nullptr;
+  DevCluster empty{};
+  std::vector<DevCluster> descs;
+  std::vector<int> arm;
+  std::vector<ba_cluster_id> occ;
+  std::vector<ba_ticket> occ_ticket;
+  std::vector<LmState> lm;
+  GraphRec graph;
+  bool dirty = true;
+};
+
 }  // namespace
 
 struct ba_ctx {
@@ -93,6 +114,7 @@ struct ba_ctx {
   std::thread sched;
   bool sched_stop = false;
   bool sched_started = false;
+  SlotTable slots;
 };
 
 namespace {
@@ -204,6 +226,9 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
   if (st != BA_OK) return st;
   Plan* p = new Plan();
   p->ids = ids;
+  pre.push_back(pre[n]);  // totals, read by the kernels
+  pre.push_back(pre[(n + 1) + n]);
+  pre.push_back(pre[2 * (n + 1) + n]);
   Layout L;
   const size_t o_desc = L.add(sizeof(DevCluster) * n);
   const size_t o_pre = L.add(sizeof(int) * pre.size());
@@ -241,6 +266,7 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
   p->bv.chunk_pre = dpre + (n + 1);
   p->bv.item_pre = dpre + 2 * (n + 1);
   p->bv.factor_order = (const int*)(p->dbuf + o_ord);
+  p->bv.tot = dpre + 3 * (n + 1);
   p->bv.n = n;
   p->bv.total_tiles = pre[n];
   p->bv.total_chunks = pre[(n + 1) + n];
@@ -666,9 +692,6 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const size_t o_desc = Lo.add(sizeof(DevCluster));
   const size_t total = Lo.off;
 
-  if (ctx->budget && ctx->mem + total > ctx->budget)
-    return set_err(ctx, BA_ERR_BUDGET, "cluster exceeds the device-memory budget");
-
   std::vector<char> stage(static_bytes, 0);
   auto put = [&](size_t off, const void* src, size_t bytes) {
     if (bytes) std::memcpy(stage.data() + off, src, bytes);
@@ -741,6 +764,10 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
     put(o_lm, &lm, sizeof(lm));
   }
 
+  // everything above is host work; the device part runs under the API lock
+  std::unique_lock<std::mutex> lk(ctx->api_mu);
+  if (ctx->budget && ctx->mem + total > ctx->budget)
+    return set_err(ctx, BA_ERR_BUDGET, "cluster exceeds the device-memory budget");
   char* arena = nullptr;
   cudaError_t e = cudaMalloc((void**)&arena, total);
   if (e != cudaSuccess) return set_err(ctx, BA_ERR_BUDGET, std::string("cudaMalloc(cluster): ") + cudaGetErrorString(e));
@@ -825,69 +852,196 @@ ba_status single_view(ba_ctx* ctx, Cluster* c, Plan** p) { return get_plan(ctx, 
 
 // ------------------------------------------------------------------ serving scheduler
 //
-// Continuous batching at LM-iteration granularity: every round the scheduler
-// (1) admits queued clusters into free slots, (2) runs ONE iteration for all
-// running clusters as one batched launch sequence, (3) retires the clusters
-// that reached their iteration count.  A cluster's iterations are exactly
-// those of ba_run: the kernels' reductions are per cluster and fixed-order,
-// so results do not depend on which other clusters share the launches.
+// Continuous batching at LM-iteration granularity.  The running clusters sit
+// in a fixed table of n_slots slots in device memory (descriptors, prefix
+// sums, totals, factor order, arm counts); one CUDA graph, captured once,
+// runs one LM iteration for every slot, reading the table as data.  Every
+// round the scheduler (1) admits queued clusters into free slots and uploads
+// the table if it changed, (2) launches the graph, (3) reads back the slots'
+// LM state and retires the clusters that reached their iteration count.
+// Requests that arrive while others run join at the next round.  A cluster's
+// iterations are exactly those of ba_run: every reduction is per cluster and
+// fixed-order, so results do not depend on which clusters share a round.
+
+ba_status slots_setup(ba_ctx* ctx) {
+  SlotTable& T = ctx->slots;
+  if (T.dbuf) return BA_OK;
+  const int n = ctx->n_slots;
+  ba_status st = ensure_attrs(ctx, 6 * kMaxFreeSmall);
+  if (st != BA_OK) return st;
+  Layout L;
+  const size_t o_desc = L.add(sizeof(DevCluster) * n);
+  const size_t o_pre = L.add(sizeof(int) * (3 * (size_t)(n + 1) + 3));
+  const size_t o_ord = L.add(sizeof(int) * n);
+  const size_t o_arm = L.add(sizeof(int) * n);
+  const size_t o_lm = L.add(sizeof(LmState) * n);
+  const size_t o_dummy = L.add(sizeof(LmState));
+  T.bytes = L.off;
+  CUDA_TRY(ctx, cudaMalloc((void**)&T.dbuf, T.bytes));
+  CUDA_TRY(ctx, cudaMemset(T.dbuf, 0, T.bytes));
+  ctx->mem += T.bytes;
+  T.n = n;
+  T.d_desc = (DevCluster*)(T.dbuf + o_desc);
+  T.d_pre = (int*)(T.dbuf + o_pre);
+  T.d_order = (int*)(T.dbuf + o_ord);
+  T.d_arm = (int*)(T.dbuf + o_arm);
+  T.d_lm = (LmState*)(T.dbuf + o_lm);
+  T.empty = DevCluster{};
+  T.empty.lm = (LmState*)(T.dbuf + o_dummy);  // zeroed: inactive, nothing to evaluate
+  T.descs.assign(n, T.empty);
+  T.arm.assign(n, 0);
+  T.occ.assign(n, 0);
+  T.occ_ticket.assign(n, 0);
+  T.lm.assign(n, LmState{});
+  BatchView& bv = T.bv;
+  bv.cl = T.d_desc;
+  bv.tile_pre = T.d_pre;
+  bv.chunk_pre = T.d_pre + (n + 1);
+  bv.item_pre = T.d_pre + 2 * (n + 1);
+  bv.tot = T.d_pre + 3 * (n + 1);
+  bv.factor_order = T.d_order;
+  bv.n = n;
+  bv.total_tiles = bv.total_chunks = bv.total_items = 1 << 30;  // the graph uses the largest grids
+  bv.max_n = 6 * kMaxFreeSmall;
+  T.dirty = true;
+  return BA_OK;
+}
+
+ba_status slots_upload(ba_ctx* ctx) {
+  SlotTable& T = ctx->slots;
+  const int n = T.n;
+  std::vector<int> pre(3 * (size_t)(n + 1) + 3, 0), order(n);
+  for (int i = 0; i < n; ++i) {
+    const DevCluster& h = T.descs[i];
+    pre[i + 1] = pre[i] + h.n_tiles;
+    pre[(n + 1) + i + 1] = pre[(n + 1) + i] + h.n_chunks;
+    pre[2 * (n + 1) + i + 1] = pre[2 * (n + 1) + i] + h.n_free + h.n_pairs;
+    order[i] = i;
+  }
+  pre[3 * (n + 1)] = pre[n];
+  pre[3 * (n + 1) + 1] = pre[(n + 1) + n];
+  pre[3 * (n + 1) + 2] = pre[2 * (n + 1) + n];
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return T.descs[a].n_free > T.descs[b].n_free; });
+  CUDA_TRY(ctx, cudaMemcpyAsync(T.d_desc, T.descs.data(), sizeof(DevCluster) * n, cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(T.d_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(T.d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(T.d_arm, T.arm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
+  T.dirty = false;
+  return BA_OK;
+}
+
+// one round: arm -> F for newly armed slots -> one LM iteration -> gather
+ba_status slots_round(ba_ctx* ctx) {
+  SlotTable& T = ctx->slots;
+  if (!T.graph.exec) {
+    cudaGraph_t graph = nullptr;
+    note_direct(ctx);
+    take_captured_launches();
+    if (ctx->timing) {
+      T.graph.probe = new Probe();
+      set_probe(T.graph.probe);
+    }
+    CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    launch_arm_slots(T.bv, T.d_arm, ctx->stream);
+    launch_cost_init(T.bv, ctx->mixed, ctx->stream);
+    launch_iteration(T.bv, ctx->mixed, ctx->refine, ctx->stream);
+    launch_gather(T.bv, 0, T.d_lm, nullptr, ctx->stream);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    set_probe(nullptr);
+    T.graph.kernels = take_captured_launches();
+    if (e != cudaSuccess) return set_err(ctx, BA_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&T.graph.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return set_err(ctx, BA_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  if (T.dirty) {
+    ba_status st = slots_upload(ctx);
+    if (st != BA_OK) return st;
+  }
+  CUDA_TRY(ctx, cudaGraphLaunch(T.graph.exec, ctx->stream));
+  ctx->launches += T.graph.kernels;
+  CUDA_TRY(ctx, cudaMemcpyAsync(T.lm.data(), T.d_lm, sizeof(LmState) * T.n, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(ctx, cudaGetLastError());
+  if (ctx->timing && T.graph.probe)
+    for (auto& r : T.graph.probe->recs) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) ctx->kms[r.kind] += ms;
+      ctx->klaunch[r.kind] += 1;
+    }
+  bool armed = false;
+  for (int s = 0; s < T.n; ++s)
+    if (T.arm[s]) {
+      T.arm[s] = 0;
+      armed = true;
+    }
+  if (armed) T.dirty = true;
+  return BA_OK;
+}
 
 void scheduler_loop(ba_ctx* ctx) {
-  struct Running {
-    ba_ticket t;
-    ba_cluster_id id;
-    int left;
-    int iters;
-  };
-  std::vector<Running> running;
+  SlotTable& T = ctx->slots;
   cudaSetDevice(ctx->device);
+  int running = 0;
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(ctx->sv_mu);
-      ctx->sv_cv.wait(lk, [&] { return ctx->sched_stop || !ctx->queue.empty() || !running.empty(); });
-      if (ctx->sched_stop && running.empty()) return;
-      while (!ctx->queue.empty() && (int)running.size() < ctx->n_slots) {
+      ctx->sv_cv.wait(lk, [&] { return ctx->sched_stop || !ctx->queue.empty() || running > 0; });
+      if (ctx->sched_stop && running == 0) return;
+      for (int s = 0; s < T.n && !ctx->queue.empty(); ++s) {
+        if (T.occ[s]) continue;
         const ba_ticket t = ctx->queue.front();
         ctx->queue.pop_front();
         Ticket& tk = ctx->tickets[t];
-        running.push_back(Running{t, tk.id, tk.iters, tk.iters});
+        Cluster* c = nullptr;
+        {
+          std::lock_guard<std::mutex> g(ctx->api_mu);
+          c = find_cluster(ctx, tk.id);
+        }
+        if (!c) {  // destroyed while queued
+          tk.done = 1;
+          tk.res.status = BA_ERR_NOT_FOUND;
+          continue;
+        }
+        T.occ[s] = tk.id;
+        T.occ_ticket[s] = t;
+        T.descs[s] = c->h;
+        T.arm[s] = tk.iters;
+        T.dirty = true;
+        ++running;
       }
     }
-    std::vector<ba_cluster_id> ids;
-    std::vector<Running> firsts;
-    for (auto& r : running) ids.push_back(r.id);
-    std::sort(ids.begin(), ids.end());
-    std::vector<LmState> lm;
     ba_status st;
     {
       std::lock_guard<std::mutex> g(ctx->api_mu);
-      // the first iteration of a newly admitted cluster needs F at its state;
-      // run_and_collect arms + evaluates F for all, which is idempotent for the others
-      st = run_and_collect(ctx, ids, 1, &lm, nullptr);
+      st = slots_round(ctx);
     }
-    std::vector<Running> still;
     {
       std::lock_guard<std::mutex> lk(ctx->sv_mu);
-      for (auto& r : running) {
-        const int pos = (int)(std::lower_bound(ids.begin(), ids.end(), r.id) - ids.begin());
-        r.left -= 1;
-        Ticket& tk = ctx->tickets[r.t];
-        if (st != BA_OK || r.left <= 0) {
-          tk.done = 1;
-          tk.res.status = st != BA_OK ? st : (st == BA_OK ? lm[pos].status : st);
-          tk.res.iters = r.iters - r.left;
-          tk.res.final_cost = st == BA_OK ? lm[pos].F : 0.0;
-          tk.res.accepted = st == BA_OK ? lm[pos].n_accepted : 0;
-          tk.res.latency_ms =
-              std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tk.t_submit).count();
-          Cluster* c = find_cluster(ctx, r.id);
+      const auto now = std::chrono::steady_clock::now();
+      for (int s = 0; s < T.n; ++s) {
+        if (!T.occ[s]) continue;
+        if (st == BA_OK && T.lm[s].active) continue;
+        Ticket& tk = ctx->tickets[T.occ_ticket[s]];
+        tk.done = 1;
+        tk.res.status = st != BA_OK ? st : T.lm[s].status;
+        tk.res.iters = tk.iters;
+        tk.res.final_cost = T.lm[s].F;
+        tk.res.accepted = T.lm[s].n_accepted;
+        tk.res.latency_ms = std::chrono::duration<double, std::milli>(now - tk.t_submit).count();
+        {
+          std::lock_guard<std::mutex> g(ctx->api_mu);
+          Cluster* c = find_cluster(ctx, T.occ[s]);
           if (c) c->in_service = 0;
-        } else {
-          still.push_back(r);
         }
+        T.occ[s] = 0;
+        T.descs[s] = T.empty;
+        T.dirty = true;
+        --running;
       }
+      ctx->sv_cv.notify_all();
     }
-    running.swap(still);
   }
 }
 
@@ -941,48 +1095,44 @@ BA_API ba_status ba_init(ba_ctx** out, const ba_config* cfg) {
 
 BA_API ba_status ba_create_cluster(ba_ctx* ctx, const ba_cluster_desc* d, ba_cluster_id* out) {
   if (!ctx || !d || !out) return BA_ERR_INVALID;
-  std::lock_guard<std::mutex> g(ctx->api_mu);
   cudaSetDevice(ctx->device);
   Cluster* c = new Cluster();
-  c->id = ctx->next_id++;
-  ba_status st = build_cluster(ctx, d, c);
+  ba_status st = build_cluster(ctx, d, c);  // host presort unlocked; device upload under the lock
   if (st != BA_OK) {
     delete c;
     return st;
   }
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  c->id = ctx->next_id++;
   ctx->clusters[c->id] = c;
   if (d->warm_from) {
-    // warm start: copy the current state of shared cameras/points from a live cluster
+    // warm start: the current state of the shared cameras and points of a live
+    // cluster, copied on the device (caller indices -> internal indices)
     Cluster* src = find_cluster(ctx, d->warm_from);
-    if (!src || !d->warm_cam_map || !d->warm_pt_map) {
+    if (!src || !d->warm_cam_map || !d->warm_pt_map || src->in_service) {
       ctx->clusters.erase(c->id);
       ctx->mem -= c->arena_bytes;
       cudaFree(c->arena);
       delete c;
-      return set_err(ctx, BA_ERR_NOT_FOUND, "warm_from cluster not found or maps missing");
+      return set_err(ctx, BA_ERR_NOT_FOUND, "warm_from cluster not found, in service, or maps missing");
     }
-    LmState sl{};
-    cudaMemcpy(&sl, src->h.lm, sizeof(LmState), cudaMemcpyDeviceToHost);
-    const double* sR = src->h.R + (size_t)sl.cur * src->nc * 9;
-    const double* sT = src->h.T + (size_t)sl.cur * src->nc * 3;
-    const double* sX = src->h.X + (size_t)sl.cur * src->np * 3;
+    std::vector<int2> pairs;
     for (int k = 0; k < c->nc; ++k) {
       const int m = d->warm_cam_map[k];
-      if (m < 0 || m >= src->nc) continue;
-      for (int b = 0; b < 2; ++b) {
-        cudaMemcpyAsync(c->h.R + ((size_t)b * c->nc + k) * 9, sR + 9 * (size_t)m, 72, cudaMemcpyDeviceToDevice, ctx->stream);
-        cudaMemcpyAsync(c->h.T + ((size_t)b * c->nc + k) * 3, sT + 3 * (size_t)m, 24, cudaMemcpyDeviceToDevice, ctx->stream);
-      }
-      cudaMemcpyAsync((double*)c->h.R_init + 9 * (size_t)k, sR + 9 * (size_t)m, 72, cudaMemcpyDeviceToDevice, ctx->stream);
-      cudaMemcpyAsync((double*)c->h.T_init + 3 * (size_t)k, sT + 3 * (size_t)m, 24, cudaMemcpyDeviceToDevice, ctx->stream);
+      if (m >= 0 && m < src->nc) pairs.push_back(make_int2(k, m));
     }
-    for (int ju = 0; ju < c->np; ++ju) {  // caller indices -> internal indices on both sides
+    const int n_cam_pairs = (int)pairs.size();
+    for (int ju = 0; ju < c->np; ++ju) {
       const int mu_ = d->warm_pt_map[ju];
-      if (mu_ < 0 || mu_ >= src->np) continue;
-      const int j = c->pt_inv[ju], m = src->pt_inv[mu_];
-      for (int b = 0; b < 2; ++b)
-        cudaMemcpyAsync(c->h.X + ((size_t)b * c->np + j) * 3, sX + 3 * (size_t)m, 24, cudaMemcpyDeviceToDevice, ctx->stream);
-      cudaMemcpyAsync((double*)c->h.X_init + 3 * (size_t)j, sX + 3 * (size_t)m, 24, cudaMemcpyDeviceToDevice, ctx->stream);
+      if (mu_ >= 0 && mu_ < src->np) pairs.push_back(make_int2(c->pt_inv[ju], src->pt_inv[mu_]));
+    }
+    if (!pairs.empty()) {
+      int2* dp = nullptr;
+      CUDA_TRY(ctx, cudaMallocAsync((void**)&dp, sizeof(int2) * pairs.size(), ctx->stream));
+      CUDA_TRY(ctx, cudaMemcpyAsync(dp, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice, ctx->stream));
+      launch_warm_copy(c->d_desc, src->d_desc, dp, n_cam_pairs, dp + n_cam_pairs, (int)pairs.size() - n_cam_pairs,
+                       ctx->stream);
+      CUDA_TRY(ctx, cudaFreeAsync(dp, ctx->stream));
     }
   }
   Plan* p = nullptr;
@@ -1149,6 +1299,9 @@ BA_API ba_status ba_submit(ba_ctx* ctx, ba_cluster_id id, const ba_solve_opts* o
     std::lock_guard<std::mutex> g(ctx->api_mu);
     Cluster* c = find_cluster(ctx, id);
     if (!c) return BA_ERR_NOT_FOUND;
+    if (6 * c->nf > 6 * kMaxFreeSmall) return set_err(ctx, BA_ERR_INVALID, "cluster too large for a serving slot");
+    ba_status st = slots_setup(ctx);
+    if (st != BA_OK) return st;
     int expect = 0;
     if (!c->in_service.compare_exchange_strong(expect, 1))
       return set_err(ctx, BA_ERR_INVALID, "cluster already submitted");
@@ -1256,6 +1409,9 @@ BA_API ba_status ba_shutdown(ba_ctx* ctx) {
   }
   if (ctx->sched.joinable()) ctx->sched.join();
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->slots.graph.exec) cudaGraphExecDestroy(ctx->slots.graph.exec);
+  free_probe(ctx->slots.graph.probe);
+  if (ctx->slots.dbuf) cudaFree(ctx->slots.dbuf);
   for (auto& kv : ctx->plans) free_plan(kv.second);
   for (auto& kv : ctx->clusters) {
     cudaFree(kv.second->arena);

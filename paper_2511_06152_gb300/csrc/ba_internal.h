@@ -87,6 +87,8 @@ struct LmState {
   int iters_target;
   int pt_fail;       // a damped point block was not positive definite this iteration
   float mu_f;        // mu rounded to binary32 (mixed-path kernels)
+  int needs_init;    // F must be evaluated at the current state before the next iteration
+  int pad3;
 };
 
 // Same layout as ba_step_info.
@@ -160,6 +162,7 @@ struct BatchView {
   const int* chunk_pre;  // [n + 1]
   const int* item_pre;   // [n + 1] free cameras + camera pairs
   const int* factor_order;  // [n] clusters by decreasing reduced-system size
+  const int* tot;        // device [3]: total tiles, chunks, reduction items (kernels read these)
   int n;
   int total_tiles, total_chunks, total_items;
   int max_n;             // largest 6 * n_free in the batch
@@ -195,6 +198,9 @@ unsigned long long take_captured_launches();    // kernel nodes captured since t
 // Kernel launchers (ba_kernels.cu).  All run on `st`.
 cudaError_t set_kernel_attributes(int max_n);
 void launch_arm(const BatchView& bv, int iters, cudaStream_t st);
+void launch_arm_slots(const BatchView& bv, const int* arm, cudaStream_t st);
+void launch_warm_copy(const DevCluster* dst, const DevCluster* src, const int2* cams, int n_cams, const int2* pts,
+                      int n_pts, cudaStream_t st);
 void launch_reset(const BatchView& bv, bool mixed, cudaStream_t st);
 void launch_gather(const BatchView& bv, int iters, LmState* lm_out, StepRec* trace_out, cudaStream_t st);
 void launch_camreal(const BatchView& bv, bool mixed, cudaStream_t st);

@@ -333,7 +333,8 @@ __global__ void __launch_bounds__(kChunkThreads) k_lin_schur(BatchView bv, int d
   Real* srec = reinterpret_cast<Real*>(smraw);                        // [chunk_obs][kSrec]
   Real* lanepart = srec + (size_t)(MIXED ? kChunkObsMixed : kChunkObsF64) * kSrec;  // [threads][kLanePart]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int g = blockIdx.x; g < bv.total_chunks; g += gridDim.x) {
+  const int total = bv.tot[1];
+  for (int g = blockIdx.x; g < total; g += gridDim.x) {
     const int s = find_slot(bv.chunk_pre, bv.n, g);
     const DevCluster& C = bv.cl[s];
     LmState* lm = C.lm;
@@ -484,7 +485,8 @@ __global__ void __launch_bounds__(256) k_partial_reduce(BatchView bv) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int g = warp; g < bv.total_items; g += nwarps) {
+  const int total = bv.tot[2];
+  for (int g = warp; g < total; g += nwarps) {
     const int s = find_slot(bv.item_pre, bv.n, g);
     const DevCluster& C = bv.cl[s];
     if (!C.lm->active) continue;
@@ -809,7 +811,8 @@ __global__ void __launch_bounds__(256) k_backsub_cost(BatchView bv) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int g = warp; g < bv.total_tiles; g += nwarps) {
+  const int total = bv.tot[0];
+  for (int g = warp; g < total; g += nwarps) {
     const int s = find_slot(bv.tile_pre, bv.n, g);
     const DevCluster& C = bv.cl[s];
     LmState* lm = C.lm;
@@ -932,10 +935,12 @@ __global__ void __launch_bounds__(256) k_cost_tiles(BatchView bv) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int g = warp; g < bv.total_tiles; g += nwarps) {
+  const int total = bv.tot[0];
+  for (int g = warp; g < total; g += nwarps) {
     const int s = find_slot(bv.tile_pre, bv.n, g);
     const DevCluster& C = bv.cl[s];
     const LmState* lm = C.lm;
+    if (!lm->needs_init) continue;
     const int local = g - bv.tile_pre[s];
     const Tile tl = C.tiles[local];
     const int cur = lm->cur;
@@ -994,8 +999,10 @@ __global__ void __launch_bounds__(256) k_cost_init(BatchView bv) {
   for (int s = blockIdx.x; s < bv.n; s += gridDim.x) {
     const DevCluster& C = bv.cl[s];
     LmState* lm = C.lm;
+    if (!lm->needs_init) continue;
     const double F = block_sum_tiles(C, 0, red);
     if (threadIdx.x == 0) {
+      lm->needs_init = 0;
       const int cur = lm->cur;
       double pc = 0.0;
       for (int k = 0; k < C.n_cams; ++k) {
@@ -1150,7 +1157,54 @@ __global__ void k_arm(BatchView bv, int iters) {
     } else {
       lm->active = iters == -1;
     }
+    lm->needs_init = 1;
     lm->pt_fail = 0;
+  }
+}
+
+// Serving slots: arm[s] > 0 starts arm[s] more iterations for slot s (and asks
+// for F at its state first); 0 leaves the slot as it is.
+__global__ void k_arm_slots(BatchView bv, const int* arm) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < bv.n; s += gridDim.x * blockDim.x) {
+    const int a = arm[s];
+    if (a <= 0) continue;
+    LmState* lm = bv.cl[s].lm;
+    lm->iters_target = lm->iter + a;
+    lm->active = 1;
+    lm->needs_init = 1;
+    lm->pt_fail = 0;
+  }
+}
+
+// Warm start: copy the current state of shared cameras and points from a live
+// cluster (src) into a new one (dst): both state buffers and the reset state.
+// cams / pts hold (dst index, src index) pairs in internal order.  The copy is
+// representation-agnostic (8-byte words), so both clusters must use the same
+// precision.
+__global__ void k_warm_copy(const DevCluster* dst, const DevCluster* src, const int2* cams, int n_cams,
+                            const int2* pts, int n_pts) {
+  const int scur = src->lm->cur;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pts; i += stride) {
+    const int2 p = pts[i];
+    const double* sx = src->X + ((size_t)scur * src->n_pts + p.y) * 3;
+    for (int a = 0; a < 3; ++a) {
+      const double v = sx[a];
+      dst->X[(size_t)p.x * 3 + a] = v;
+      dst->X[((size_t)dst->n_pts + p.x) * 3 + a] = v;
+      const_cast<double*>(dst->X_init)[(size_t)p.x * 3 + a] = v;
+    }
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_cams; i += stride) {
+    const int2 p = cams[i];
+    const double* sr = src->R + ((size_t)scur * src->n_cams + p.y) * 9;
+    const double* st = src->T + ((size_t)scur * src->n_cams + p.y) * 3;
+    for (int b = 0; b < 2; ++b) {
+      for (int a = 0; a < 9; ++a) dst->R[((size_t)b * dst->n_cams + p.x) * 9 + a] = sr[a];
+      for (int a = 0; a < 3; ++a) dst->T[((size_t)b * dst->n_cams + p.x) * 3 + a] = st[a];
+    }
+    for (int a = 0; a < 9; ++a) const_cast<double*>(dst->R_init)[(size_t)p.x * 9 + a] = sr[a];
+    for (int a = 0; a < 3; ++a) const_cast<double*>(dst->T_init)[(size_t)p.x * 3 + a] = st[a];
   }
 }
 
@@ -1279,6 +1333,17 @@ static int num_sms() {
 
 void launch_arm(const BatchView& bv, int iters, cudaStream_t st) {
   LAUNCH(KK_OTHER, st, k_arm<<<(bv.n + 127) / 128, 128, 0, st>>>(bv, iters));
+}
+
+void launch_arm_slots(const BatchView& bv, const int* arm, cudaStream_t st) {
+  LAUNCH(KK_OTHER, st, k_arm_slots<<<(bv.n + 127) / 128, 128, 0, st>>>(bv, arm));
+}
+
+void launch_warm_copy(const DevCluster* dst, const DevCluster* src, const int2* cams, int n_cams, const int2* pts,
+                      int n_pts, cudaStream_t st) {
+  const int n = n_pts > n_cams ? n_pts : n_cams;
+  LAUNCH(KK_OTHER, st,
+         k_warm_copy<<<grid_for(n, 256, num_sms() * 4), 256, 0, st>>>(dst, src, cams, n_cams, pts, n_pts));
 }
 
 void launch_camreal(const BatchView& bv, bool mixed, cudaStream_t st) {

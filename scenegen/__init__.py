@@ -379,3 +379,77 @@ def centre_error(T_est, T_ref):
 def image_interval_s(footprint_along_m, overlap_pct, velocity_mps):
     """t = h_im (1 - beta/100) / v  (Eq. 1)."""
     return footprint_along_m * (1.0 - overlap_pct / 100.0) / velocity_mps
+
+
+# --------------------------------------------------------------------------
+# serving workload: long flights cut into sliding windows (Sec. 3.2, cluster
+# transition: the last 25 % of a window is reused by the next one, the first
+# half of that overlap held fixed)
+# --------------------------------------------------------------------------
+def flight(seed, n_strips=3, per_strip=40, pts_per_cam=1667):
+    """One flight: serpentine strips of images over terrain, points at the
+    c2 density (1,667 per image), every image containing a point observes it."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = n_strips * per_strip
+    return make_cluster(rng, n_strips, per_strip, pts_per_cam * n)
+
+
+def window_plan(seed, n_images, m_lo=12, m_hi=32, overlap=0.25):
+    """Window boundaries over a flight's images in time order: sizes
+    M ~ U{m_lo..m_hi}; each window after the first starts with the last
+    ceil(overlap * M_prev) images of the previous one, and the first half of
+    those (ceil) are held fixed."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out, start, prev = [], 0, None
+    while True:
+        m = int(rng.integers(m_lo, m_hi + 1))
+        if prev is not None:
+            n_ov = int(math.ceil(overlap * (prev[1] - prev[0])))
+            start = prev[1] - n_ov
+            n_fix = int(math.ceil(n_ov / 2))
+        else:
+            n_fix = 0
+        end = min(start + m, n_images)
+        if end - start < 4 or (prev is not None and end <= prev[1]):
+            break
+        out.append((start, end, n_fix))
+        prev = (start, end)
+        if end == n_images:
+            break
+    return out
+
+
+def window_cluster(fl, start, end, n_fix):
+    """The local-BA cluster of images [start, end) of a flight, with its first
+    n_fix images fixed; points seen by >= 2 of its images.  Returns the cluster
+    and the flight indices of its cameras and points."""
+    cams = np.arange(start, end)
+    obs_sel = (fl["obs_cam"] >= start) & (fl["obs_cam"] < end)
+    pc = np.bincount(fl["obs_pt"][obs_sel], minlength=fl["n_pts"])
+    pts = np.nonzero(pc >= 2)[0]
+    pmap = -np.ones(fl["n_pts"], dtype=np.int64)
+    pmap[pts] = np.arange(len(pts))
+    keep = obs_sel & (pmap[fl["obs_pt"]] >= 0)
+    nc = end - start
+    c = dict(
+        n_cams=nc, n_pts=len(pts), n_obs=int(keep.sum()),
+        intr=fl["intr"][cams], R0=fl["R0"][cams].copy(), T0=fl["T0"][cams].copy(), X0=fl["X0"][pts].copy(),
+        R_prior=fl["R_prior"][cams], T_prior=fl["T_prior"][cams],
+        R_true=fl["R_true"][cams], T_true=fl["T_true"][cams], X_true=fl["X_true"][pts],
+        fixed=np.zeros(nc, dtype=np.uint8),
+        obs_cam=(fl["obs_cam"][keep] - start).astype(np.int32), obs_pt=pmap[fl["obs_pt"][keep]].astype(np.int32),
+        obs_uv=fl["obs_uv"][keep], outlier=fl["outlier"][keep],
+        sigma_px=fl["sigma_px"], huber_delta=fl["huber_delta"], sigma_gnss=fl["sigma_gnss"],
+        sigma_imu=fl["sigma_imu"], origin=fl["origin"])
+    c["fixed"][:n_fix] = 1
+    return c, cams, pts
+
+
+def warm_maps(prev_cams, prev_pts, cams, pts):
+    """Index of each camera / point of a window in the previous window, or -1."""
+    pc = {int(v): i for i, v in enumerate(prev_cams)}
+    pp = np.full(int(max(prev_pts.max() if len(prev_pts) else 0, pts.max() if len(pts) else 0)) + 1, -1, np.int64)
+    pp[prev_pts] = np.arange(len(prev_pts))
+    cam_map = np.array([pc.get(int(v), -1) for v in cams], dtype=np.int32)
+    pt_map = pp[pts].astype(np.int32)
+    return cam_map, pt_map

@@ -1,0 +1,104 @@
+"""Serving (continuous batching, ba_submit / ba_poll): a cluster's result is
+the same alone and in the mix.
+
+Two flights are cut into sliding windows (the last 25 % of a window reused
+by the next, the first half of that overlap fixed, warm start on the device
+from the previous window).  Each flight is solved once window by window with
+ba_run, and once through the serving scheduler with both flights' windows in
+flight at the same time.  Every window's final state must agree bit for bit.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import scenegen as sg
+
+pytestmark = pytest.mark.gpu
+
+ITERS = 6
+
+
+def _flight(seed):
+    fl = sg.flight(seed, n_strips=2, per_strip=12, pts_per_cam=120)
+    plan = sg.window_plan(seed, fl["n_cams"], m_lo=8, m_hi=12)
+    wins = [sg.window_cluster(fl, s, e, nf) for (s, e, nf) in plan]
+    return wins
+
+
+def _create(ctx, wins, w, prev_id):
+    c, cams, pts = wins[w]
+    if w == 0:
+        return ctx.create_cluster(c)
+    _, pc, pp = wins[w - 1]
+    cm, pm = sg.warm_maps(pc, pp, cams, pts)
+    return ctx.create_cluster(c, warm_from=prev_id, warm_cam_map=cm, warm_pt_map=pm)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_serving_results_equal_alone(precision):
+    import paper_2511_06152_gb300 as ba
+    prec = ba.BA_MIXED if precision == "mixed" else ba.BA_FP64
+    flights = [_flight(9101), _flight(9102)]
+    assert all(len(w) >= 2 for w in flights)
+
+    alone = []
+    with ba.Context(precision=prec) as ctx:
+        for wins in flights:
+            prev, states = None, []
+            for w in range(len(wins)):
+                cid = _create(ctx, wins, w, prev)
+                ctx.run(cid, ITERS, trace=False)
+                states.append(ctx.get_state(cid))
+                prev = cid
+            alone.append(states)
+
+    mixed = [[None] * len(w) for w in flights]
+    with ba.Context(precision=prec, n_slots=8) as ctx:
+        nxt = [0, 0]
+        prev = [None, None]
+        tickets = {}
+        deadline = time.time() + 120
+        while any(nxt[f] < len(flights[f]) for f in range(2)) or tickets:
+            assert time.time() < deadline, "serving did not finish"
+            for f in range(2):
+                if nxt[f] < len(flights[f]) and not any(v[0] == f for v in tickets.values()):
+                    cid = _create(ctx, flights[f], nxt[f], prev[f])
+                    tickets[ctx.submit(cid, ITERS)] = (f, nxt[f], cid)
+            for t in list(tickets):
+                r = ctx.poll(t)
+                if r is None:
+                    continue
+                f, w, cid = tickets.pop(t)
+                assert r["status"] == 0 and r["iters"] == ITERS
+                mixed[f][w] = ctx.get_state(cid)
+                prev[f] = cid
+                nxt[f] += 1
+            time.sleep(0.001)
+
+    for f in range(2):
+        for w in range(len(flights[f])):
+            for a, b in zip(alone[f][w], mixed[f][w]):
+                assert np.array_equal(a, b), (f, w)
+
+
+def test_serving_rejects_double_submit_and_reports_latency():
+    import paper_2511_06152_gb300 as ba
+    wins = _flight(9103)
+    with ba.Context(precision=ba.BA_MIXED) as ctx:
+        cid = _create(ctx, wins, 0, None)
+        t = ctx.submit(cid, 1000)  # long enough to still be running at the second submit
+        try:
+            t2 = ctx.submit(cid, 3)
+        except ba.BAError:
+            t2 = None
+        assert t2 is None, ("second submit accepted", ctx.poll(t), ctx.L.ba_last_error(ctx.h))
+        r = None
+        for _ in range(10000):
+            r = ctx.poll(t)
+            if r is not None:
+                break
+            time.sleep(0.001)
+        assert r is not None and r["iters"] == 1000 and r["latency_ms"] > 0
+        with pytest.raises(ba.BAError):
+            ctx.poll(t)  # a ticket is consumed by the poll that returns it
