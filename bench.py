@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--serving-flights", type=int, default=16)
     ap.add_argument("--serving-rate", type=float, default=200.0, help="requests/s, Poisson, all flights")
     ap.add_argument("--serving-iters", type=int, default=10)
+    ap.add_argument("--serving-timeout", type=float, default=120.0, help="seconds before the serving leg gives up")
     return ap.parse_args()
 
 
@@ -92,6 +93,11 @@ def serving_flight(seed):
     return out
 
 
+def log(msg):
+    """Progress of the legs on stderr (stdout carries only the JSON line)."""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def torch_device():
     import torch
     return torch.cuda.current_device()
@@ -110,56 +116,72 @@ def serving_leg(args, ba, stream, flights):
     ctx = ba.Context(device=torch_device(), precision=ba.BA_MIXED,
                      stream=stream.cuda_stream, n_slots=64, hbm_budget_bytes=16 << 30)
     iters = args.serving_iters
+    deadline = _t.perf_counter() + args.serving_timeout
+    stop = threading.Event()
 
-    def create_and_submit(f, w, prev_id):
-        c, maps = flights[f][w]
-        while True:
+    def create(f, w):
+        """Presort and upload a window as soon as it arrives (in parallel with
+        the flight's previous window still being solved)."""
+        c, _ = flights[f][w]
+        while not stop.is_set():
             try:
-                if maps is None:
-                    cid = ctx.create_cluster(c)
-                else:
-                    cid = ctx.create_cluster(c, warm_from=prev_id, warm_cam_map=maps[0], warm_pt_map=maps[1])
-                break
+                return ctx.create_cluster(c)
             except ba.BAError as e:  # HBM budget: wait for completions to free memory
-                if e.status != ba.BA_ERR_BUDGET:
+                if e.status != ba.BA_ERR_BUDGET or _t.perf_counter() > deadline:
                     raise
                 _t.sleep(0.001)
-        return cid, ctx.submit(cid, iters)
+        raise RuntimeError("serving leg stopped")
 
-    nxt = [0] * len(flights)
-    prev = [None] * len(flights)
-    old = [None] * len(flights)
-    pending, inflight = {}, {}
+    n_fl = len(flights)
+    ncreate = [0] * n_fl        # next window to create (when it has arrived)
+    ndone = [0] * n_fl          # windows completed
+    prev = [None] * n_fl        # cluster of the last completed window (warm-start source)
+    old = [None] * n_fl         # the one before (destroyed once prev has been used)
+    pending, inflight = {}, {}  # f -> (w, future) / (w, cid, ticket)
     lat, obs_done = [], 0
     max_inflight = 0
-    with ThreadPoolExecutor(8) as ex:
+    ex = ThreadPoolExecutor(8)
+    try:
         t0 = _t.perf_counter()
-        while any(nxt[f] < len(flights[f]) for f in range(len(flights))) or pending or inflight:
+        while any(ndone[f] < len(flights[f]) for f in range(n_fl)):
+            if _t.perf_counter() > deadline:
+                raise RuntimeError(f"serving leg exceeded {args.serving_timeout} s ({sum(ndone)} requests done)")
             now = _t.perf_counter() - t0
-            for f in range(len(flights)):
-                if (nxt[f] < len(flights[f]) and f not in pending and f not in inflight
-                        and arrivals[f][nxt[f]] <= now):
-                    pending[f] = ex.submit(create_and_submit, f, nxt[f], prev[f])
-            for f in list(pending):
-                if pending[f].done():
-                    cid, t = pending.pop(f).result()
-                    inflight[f] = (cid, t)
+            for f in range(n_fl):
+                w = ncreate[f]
+                if w < len(flights[f]) and f not in pending and arrivals[f][w] <= now:
+                    pending[f] = (w, ex.submit(create, f, w))
+                    ncreate[f] += 1
+            for f in list(pending):  # warm start + submit once the previous window is done
+                w, fut = pending[f]
+                if f not in inflight and ndone[f] == w and fut.done():
+                    pending.pop(f)
+                    cid = fut.result()
+                    maps = flights[f][w][1]
+                    if maps is not None:
+                        ctx.warm_start(cid, prev[f], maps[0], maps[1])
+                    inflight[f] = (w, cid, ctx.submit(cid, iters))
             max_inflight = max(max_inflight, len(inflight))
             for f in list(inflight):
-                cid, t = inflight[f]
+                w, cid, t = inflight[f]
                 r = ctx.poll(t)
                 if r is None:
                     continue
                 inflight.pop(f)
+                if r["status"] != 0:
+                    raise RuntimeError(f"serving request failed: flight {f} window {w} status {r['status']}")
                 done = _t.perf_counter() - t0
-                lat.append(1e3 * (done - arrivals[f][nxt[f]]))
-                obs_done += flights[f][nxt[f]][0]["n_obs"] * iters
+                lat.append(1e3 * (done - arrivals[f][w]))
+                obs_done += flights[f][w][0]["n_obs"] * iters
                 if old[f] is not None:
                     ctx.destroy_cluster(old[f])
                 old[f], prev[f] = prev[f], cid
-                nxt[f] += 1
+                ndone[f] += 1
             _t.sleep(0.0002)
         span = _t.perf_counter() - t0
+    finally:
+        stop.set()
+        ex.shutdown(wait=True, cancel_futures=True)
     ctx.close()
     lat = np.array(lat)
     return {"requests": int(len(lat)), "flights": len(flights), "arrival_rate_req_s": args.serving_rate,
@@ -338,6 +360,7 @@ def main():
         return
     rank, world, local = dist_env()
     n_fl = 0 if (args.no_extras or rank != 0 or world != 1) else args.serving_flights
+    log(f"generating {args.clusters} clusters and {n_fl} serving flights")
     scenes, flights = make_workload(rank, args.clusters, n_fl)  # spawn pool before the first CUDA call
     total_obs = sum(s["n_obs"] for s in scenes)
     iters = args.iters
@@ -351,6 +374,7 @@ def main():
     stream = torch.cuda.Stream()
     ctx = ba.Context(device=local, precision=ba.BA_MIXED, stream=stream.cuda_stream, flags=ba.BA_FLAG_KERNEL_TIMING)
     ids = [ctx.create_cluster(s) for s in scenes]
+    log(f"created {len(ids)} clusters, {total_obs} observations; warm-up")
 
     def barrier():
         torch.cuda.synchronize()
@@ -365,6 +389,7 @@ def main():
     for _ in range(args.warmup):
         res = step()
     ctx.kernel_stats(reset=True)
+    log(f"timing {args.steps} steps")
     launches0 = ctx.launch_count()
     clocks = ClockSampler(local)
     barrier()
@@ -416,6 +441,7 @@ def main():
             "lm_iters_per_s": lm_iters_per_s, "clocks": ck, "gpu_launches": launches, "roofline": roof,
             "kernels": kernels}
 
+    log(f"timed: {ms_per_step:.2f} ms/step")
     if not args.no_extras and rank == 0 and world == 1:
         line.update(extras(args, ba, torch, scenes, ids, ctx, stream, iters, value, flights))
     ctx.close()
@@ -434,6 +460,7 @@ def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flight
         e = ctx.reprojection_errors(ids[i])
         rms_mixed.append(float(np.sqrt(np.mean(e[~scenes[i]["outlier"]] ** 2))))
     # plain per-cluster FP64 GPU path: one cluster at a time
+    log("fp64 plain leg")
     c64 = ba.Context(device=torch.cuda.current_device(), precision=ba.BA_FP64, stream=stream.cuda_stream)
     ids64 = [c64.create_cluster(scenes[i]) for i in sample]
     c64.run(ids64[0], iters, trace=False)  # warm-up (graph capture)
@@ -460,6 +487,7 @@ def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flight
                          "max_rms_diff_px": float(np.max(np.abs(np.array(rms_mixed) - np.array(rms64)))),
                          "max_centre_diff_m": float(np.max(dcen))}
     # end to end through the public API with host buffers
+    log("e2e leg")
     h2d = sum(s["intr"].nbytes + 2 * s["R0"].nbytes + 2 * s["T0"].nbytes + s["X0"].nbytes + s["fixed"].nbytes +
               s["obs_cam"].nbytes + s["obs_pt"].nbytes + s["obs_uv"].nbytes for s in scenes)
     d2h = sum(s["R0"].nbytes + s["T0"].nbytes + s["X0"].nbytes for s in scenes)
@@ -482,9 +510,11 @@ def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flight
                   "d2h_bytes_per_step": int(d2h), "seconds_per_step": statistics.median(times),
                   "includes": "ba_create_cluster from host arrays (validation, presort, H2D), batched solve, "
                               "ba_get_state to host"}
+    log("cpu baseline leg")
     out["cpu_baseline"] = oracle_obs_per_s(scenes, iters, args.cpu_seconds)
     out["paper_context"] = "paper: full BA per cluster in < 2 s, MATLAB on an i7 13th-gen 20-core laptop, no GPU"
     if flights:
+        log("serving leg")
         out["serving"] = serving_leg(args, ba, stream, flights)
     return out
 

@@ -175,6 +175,18 @@ BA_API ba_status ba_init(ba_ctx** out, const ba_config* cfg);
  * exceed the context's budget. */
 BA_API ba_status ba_create_cluster(ba_ctx* ctx, const ba_cluster_desc* d, ba_cluster_id* out);
 
+/* Warm start an existing cluster from a live one (the cluster transition of
+ * Sec. 3.2: a new window reuses the optimised overlap images and their
+ * points).  cam_map[dst n_cams] / pt_map[dst n_pts] (host arrays) give, for
+ * each camera / point of dst, its index in src or -1.  The current state of
+ * the mapped cameras and points of src is copied on the device into dst
+ * (also into the state ba_reset restores).  Neither cluster may be queued or
+ * running in the serving scheduler.  Enqueued on the context's stream; this
+ * split from ba_create_cluster lets a caller presort a window while the
+ * previous one is still being solved. */
+BA_API ba_status ba_warm_start(ba_ctx* ctx, ba_cluster_id dst, ba_cluster_id src, const int32_t* cam_map,
+                               const int32_t* pt_map);
+
 /* Evaluate F and the gradient infinity norm at the current state. */
 BA_API ba_status ba_linearize(ba_ctx* ctx, ba_cluster_id id, ba_lin_info* out);
 

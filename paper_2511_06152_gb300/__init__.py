@@ -84,7 +84,7 @@ class ba_result(ctypes.Structure):
 
 EXPORTS = ["ba_init", "ba_create_cluster", "ba_linearize", "ba_solve_step", "ba_run", "ba_solve_batch", "ba_reset",
            "ba_reset_batch", "ba_submit", "ba_poll", "ba_get_state", "ba_reprojection_errors", "ba_memory_in_use",
-           "ba_launch_count", "ba_kernel_stats", "ba_cost_noalloc", "ba_destroy_cluster", "ba_shutdown",
+           "ba_launch_count", "ba_kernel_stats", "ba_cost_noalloc", "ba_warm_start", "ba_destroy_cluster", "ba_shutdown",
            "ba_status_string", "ba_last_error"]
 
 _lib = None
@@ -115,6 +115,7 @@ def lib(build: bool = True):
             L.ba_launch_count.argtypes = [vp, ctypes.POINTER(u64)]
             L.ba_kernel_stats.argtypes = [vp, _dp, ctypes.POINTER(u64), ctypes.c_int32, ctypes.c_int32]
             L.ba_cost_noalloc.argtypes = [ctypes.POINTER(ba_cluster_desc), vp, _dp]
+            L.ba_warm_start.argtypes = [vp, u64, u64, _ip, _ip]
             L.ba_submit.argtypes = [vp, u64, ctypes.POINTER(ba_solve_opts), ctypes.POINTER(u64)]
             L.ba_poll.argtypes = [vp, u64, ctypes.POINTER(ba_result)]
             L.ba_get_state.argtypes = [vp, u64, _dp, _dp, _dp, ctypes.c_int32]
@@ -220,6 +221,12 @@ class Context:
         _check(self.L.ba_create_cluster(self.h, ctypes.byref(d), ctypes.byref(cid)), self.h, "ba_create_cluster")
         self.sizes[cid.value] = (d.n_cams, d.n_pts, d.n_obs)
         return cid.value
+
+    def warm_start(self, dst, src, cam_map, pt_map):
+        cm = np.ascontiguousarray(cam_map, dtype=np.int32)
+        pm = np.ascontiguousarray(pt_map, dtype=np.int32)
+        _check(self.L.ba_warm_start(self.h, dst, src, cm.ctypes.data_as(_ip), pm.ctypes.data_as(_ip)), self.h,
+               "ba_warm_start")
 
     def linearize(self, cid):
         out = ba_lin_info()

@@ -510,7 +510,8 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   int n_cslots = 0, n_pslots = 0;
   {
     std::vector<std::vector<unsigned short>> per_cam(nf);
-    std::vector<std::vector<unsigned int>> per_pair;  // indexed by local pair
+    std::vector<std::vector<unsigned int>> per_pair;  // indexed by local pair; inner vectors are reused
+    int n_lp_used = 0;
     std::vector<int> local_pair_of((size_t)nf * nf, -1);
     std::vector<int> lp_keys;
     size_t t = 0;
@@ -524,7 +525,8 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
         ++ch.n_tiles;
       }
       for (auto& v : per_cam) v.clear();
-      per_pair.clear();
+      for (int i = 0; i < n_lp_used; ++i) per_pair[i].clear();
+      n_lp_used = 0;
       lp_keys.clear();
       for (int p = ch.obs_begin; p < ch.obs_begin + ch.n_obs; ++p) {
         const int f = free_idx[pcam[p]];
@@ -542,8 +544,8 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
             if (fb < 0) continue;
             const size_t key = (size_t)fa * nf + fb;
             if (local_pair_of[key] < 0) {
-              local_pair_of[key] = (int)per_pair.size();
-              per_pair.emplace_back();
+              if (n_lp_used == (int)per_pair.size()) per_pair.emplace_back();
+              local_pair_of[key] = n_lp_used++;
               lp_keys.push_back((int)key);
             }
             per_pair[local_pair_of[key]].push_back((unsigned)(a - ch.obs_begin) | ((unsigned)(b - ch.obs_begin) << 16));
@@ -692,9 +694,10 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const size_t o_desc = Lo.add(sizeof(DevCluster));
   const size_t total = Lo.off;
 
-  std::vector<char> stage(static_bytes, 0);
+  std::unique_ptr<char[]> stage_buf(new char[static_bytes]);  // every byte used below is written
+  char* const stage_ptr = stage_buf.get();
   auto put = [&](size_t off, const void* src, size_t bytes) {
-    if (bytes) std::memcpy(stage.data() + off, src, bytes);
+    if (bytes) std::memcpy(stage_ptr + off, src, bytes);
   };
   put(o_intr, intr.data(), sizeof(double) * intr.size());
   put(o_R, R.data(), sizeof(double) * R.size());
@@ -729,9 +732,9 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   put(o_ocam, pcam.data(), sizeof(int) * (size_t)no);
   put(o_opt, ppt.data(), sizeof(int) * (size_t)no);
   {
-    double* su = (double*)(stage.data() + o_uv);
-    float2* chi = mixed ? (float2*)(stage.data() + o_chi) : nullptr;
-    float2* clo = mixed ? (float2*)(stage.data() + o_clo) : nullptr;
+    double* su = (double*)(stage_ptr + o_uv);
+    float2* chi = mixed ? (float2*)(stage_ptr + o_chi) : nullptr;
+    float2* clo = mixed ? (float2*)(stage_ptr + o_clo) : nullptr;
     for (int p = 0; p < no; ++p) {
       const int i = pm[p];
       su[2 * p] = uv[2 * i];
@@ -771,7 +774,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   char* arena = nullptr;
   cudaError_t e = cudaMalloc((void**)&arena, total);
   if (e != cudaSuccess) return set_err(ctx, BA_ERR_BUDGET, std::string("cudaMalloc(cluster): ") + cudaGetErrorString(e));
-  e = cudaMemcpyAsync(arena, stage.data(), static_bytes, cudaMemcpyHostToDevice, ctx->stream);
+  e = cudaMemcpyAsync(arena, stage_ptr, static_bytes, cudaMemcpyHostToDevice, ctx->stream);
   if (e != cudaSuccess) {
     cudaFree(arena);
     return set_err(ctx, BA_ERR_CUDA, std::string("cluster upload: ") + cudaGetErrorString(e));
@@ -849,6 +852,31 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
 
 // single-cluster view for kernels that take a BatchView
 ba_status single_view(ba_ctx* ctx, Cluster* c, Plan** p) { return get_plan(ctx, {c->id}, p); }
+
+// Warm start: the current state of the cameras and points that c shares with
+// src, copied on the device (caller indices -> internal indices), into both
+// state buffers and the reset state of c.  Enqueued on the context's stream.
+ba_status warm_copy(ba_ctx* ctx, Cluster* c, Cluster* src, const int32_t* cam_map, const int32_t* pt_map) {
+  std::vector<int2> pairs;
+  for (int k = 0; k < c->nc; ++k) {
+    const int m = cam_map[k];
+    if (m >= 0 && m < src->nc) pairs.push_back(make_int2(k, m));
+  }
+  const int n_cam_pairs = (int)pairs.size();
+  for (int ju = 0; ju < c->np; ++ju) {
+    const int mu_ = pt_map[ju];
+    if (mu_ >= 0 && mu_ < src->np) pairs.push_back(make_int2(c->pt_inv[ju], src->pt_inv[mu_]));
+  }
+  if (pairs.empty()) return BA_OK;
+  int2* dp = nullptr;
+  CUDA_TRY(ctx, cudaMallocAsync((void**)&dp, sizeof(int2) * pairs.size(), ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(dp, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice, ctx->stream));
+  launch_warm_copy(c->d_desc, src->d_desc, dp, n_cam_pairs, dp + n_cam_pairs, (int)pairs.size() - n_cam_pairs,
+                   ctx->stream);
+  note_direct(ctx);
+  CUDA_TRY(ctx, cudaFreeAsync(dp, ctx->stream));
+  return BA_OK;
+}
 
 // ------------------------------------------------------------------ serving scheduler
 //
@@ -1106,33 +1134,17 @@ BA_API ba_status ba_create_cluster(ba_ctx* ctx, const ba_cluster_desc* d, ba_clu
   c->id = ctx->next_id++;
   ctx->clusters[c->id] = c;
   if (d->warm_from) {
-    // warm start: the current state of the shared cameras and points of a live
-    // cluster, copied on the device (caller indices -> internal indices)
     Cluster* src = find_cluster(ctx, d->warm_from);
-    if (!src || !d->warm_cam_map || !d->warm_pt_map || src->in_service) {
+    st = (src && d->warm_cam_map && d->warm_pt_map && !src->in_service)
+             ? warm_copy(ctx, c, src, d->warm_cam_map, d->warm_pt_map)
+             : set_err(ctx, BA_ERR_NOT_FOUND, "warm_from cluster not found, in service, or maps missing");
+    if (st != BA_OK) {
       ctx->clusters.erase(c->id);
+      drop_plans_with(ctx, c->id);
       ctx->mem -= c->arena_bytes;
       cudaFree(c->arena);
       delete c;
-      return set_err(ctx, BA_ERR_NOT_FOUND, "warm_from cluster not found, in service, or maps missing");
-    }
-    std::vector<int2> pairs;
-    for (int k = 0; k < c->nc; ++k) {
-      const int m = d->warm_cam_map[k];
-      if (m >= 0 && m < src->nc) pairs.push_back(make_int2(k, m));
-    }
-    const int n_cam_pairs = (int)pairs.size();
-    for (int ju = 0; ju < c->np; ++ju) {
-      const int mu_ = d->warm_pt_map[ju];
-      if (mu_ >= 0 && mu_ < src->np) pairs.push_back(make_int2(c->pt_inv[ju], src->pt_inv[mu_]));
-    }
-    if (!pairs.empty()) {
-      int2* dp = nullptr;
-      CUDA_TRY(ctx, cudaMallocAsync((void**)&dp, sizeof(int2) * pairs.size(), ctx->stream));
-      CUDA_TRY(ctx, cudaMemcpyAsync(dp, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice, ctx->stream));
-      launch_warm_copy(c->d_desc, src->d_desc, dp, n_cam_pairs, dp + n_cam_pairs, (int)pairs.size() - n_cam_pairs,
-                       ctx->stream);
-      CUDA_TRY(ctx, cudaFreeAsync(dp, ctx->stream));
+      return st;
     }
   }
   Plan* p = nullptr;
@@ -1143,6 +1155,25 @@ BA_API ba_status ba_create_cluster(ba_ctx* ctx, const ba_cluster_desc* d, ba_clu
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   CUDA_TRY(ctx, cudaGetLastError());
   *out = c->id;
+  return BA_OK;
+}
+
+BA_API ba_status ba_warm_start(ba_ctx* ctx, ba_cluster_id dst, ba_cluster_id src, const int32_t* cam_map,
+                               const int32_t* pt_map) {
+  if (!ctx || !cam_map || !pt_map) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  Cluster* c = find_cluster(ctx, dst);
+  Cluster* s = find_cluster(ctx, src);
+  if (!c || !s) return BA_ERR_NOT_FOUND;
+  if (c->in_service || s->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
+  ba_status st = warm_copy(ctx, c, s, cam_map, pt_map);
+  if (st != BA_OK) return st;
+  Plan* p = nullptr;
+  st = single_view(ctx, c, &p);
+  if (st != BA_OK) return st;
+  launch_camreal(p->bv, ctx->mixed, ctx->stream);
+  note_direct(ctx);
+  CUDA_TRY(ctx, cudaGetLastError());
   return BA_OK;
 }
 

@@ -372,8 +372,8 @@ __global__ void __launch_bounds__(kChunkThreads) k_lin_schur(BatchView bv, int d
     //    lane i of a job sums a contiguous range of the job's items, and the
     //    lanes' partial sums are added in lane order.  A chunk with more jobs
     //    than threads runs one lane per job.
-    const int n_jobs = ch.n_lc + ch.n_lp;
-    const bool spread = n_jobs <= (int)blockDim.x;
+    const int n_jobs = ch.n_lc + ch.n_lp;  // 0 when every observation of the chunk is of a fixed camera
+    const bool spread = n_jobs > 0 && n_jobs <= (int)blockDim.x;
     for (int base = 0; base < (spread ? 1 : n_jobs); base += blockDim.x) {
       int jb = -1, part = 0, n_parts = 1;
       if (spread) {

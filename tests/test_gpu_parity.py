@@ -223,3 +223,26 @@ def test_invalid_clusters_are_rejected(ba, bad):
         with pytest.raises(ba.BAError) as ei:
             ctx.create_cluster(c)
         assert ei.value.status == ba.BA_ERR_INVALID
+
+
+def test_chunks_with_only_fixed_camera_observations(ba):
+    """Points seen only by fixed cameras fill whole chunks that have no
+    camera or pair to reduce; the step must still match the oracle."""
+    c = sg.tiny_cluster(4242, 1, 8, 6000, fixed=(0, 1, 2, 3))
+    seen = np.zeros(c["n_pts"], dtype=int)
+    np.add.at(seen, c["obs_pt"], c["fixed"][c["obs_cam"]] == 0)
+    # ~1800 points seen by fixed cameras only; in Morton order they fill
+    # several whole chunks at both chunk sizes
+    assert (seen == 0).sum() > 1500
+    _step_parity(ba, c, 5)
+    P, S = O.Problem(c), O.State(c)
+    O.lm_run(P, S, 5)
+    ref_rms = rms_inliers(O.residual_stats(P, S.R, S.T, S.X), c["outlier"])
+    with ba.Context(precision=ba.BA_MIXED) as ctx:
+        cid = ctx.create_cluster(c)
+        tr = ctx.run(cid, 5)
+        assert all(t["status"] == 0 for t in tr)
+        R, T, X = ctx.get_state(cid)
+        rms = rms_inliers(ctx.reprojection_errors(cid), c["outlier"])
+    assert abs(rms - ref_rms) < 1e-3
+    assert sg.centre_error(T, S.T) < 1e-3

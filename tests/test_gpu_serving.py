@@ -19,8 +19,8 @@ pytestmark = pytest.mark.gpu
 ITERS = 6
 
 
-def _flight(seed):
-    fl = sg.flight(seed, n_strips=2, per_strip=12, pts_per_cam=120)
+def _flight(seed, pts_per_cam=120):
+    fl = sg.flight(seed, n_strips=2, per_strip=12, pts_per_cam=pts_per_cam)
     plan = sg.window_plan(seed, fl["n_cams"], m_lo=8, m_hi=12)
     wins = [sg.window_cluster(fl, s, e, nf) for (s, e, nf) in plan]
     return wins
@@ -35,11 +35,13 @@ def _create(ctx, wins, w, prev_id):
     return ctx.create_cluster(c, warm_from=prev_id, warm_cam_map=cm, warm_pt_map=pm)
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_serving_results_equal_alone(precision):
+@pytest.mark.parametrize("precision,pts_per_cam", [("mixed", 120), ("fp64", 120), ("mixed", 800), ("fp64", 800)])
+def test_serving_results_equal_alone(precision, pts_per_cam):
+    """At 800 points per image the last windows hold points seen only by
+    their fixed images, whole chunks of them (chunks with nothing to reduce)."""
     import paper_2511_06152_gb300 as ba
     prec = ba.BA_MIXED if precision == "mixed" else ba.BA_FP64
-    flights = [_flight(9101), _flight(9102)]
+    flights = [_flight(9101, pts_per_cam), _flight(9102, pts_per_cam)]
     assert all(len(w) >= 2 for w in flights)
 
     alone = []
@@ -102,3 +104,24 @@ def test_serving_rejects_double_submit_and_reports_latency():
         assert r is not None and r["iters"] == 1000 and r["latency_ms"] > 0
         with pytest.raises(ba.BAError):
             ctx.poll(t)  # a ticket is consumed by the poll that returns it
+
+
+def test_warm_start_after_create_equals_warm_create():
+    """ba_warm_start on an existing cluster gives the same state and result as
+    creating the cluster with warm_from."""
+    import paper_2511_06152_gb300 as ba
+    wins = _flight(9104)
+    (c0, _, _), (c1, cams1, pts1) = wins[0], wins[1]
+    cm, pm = sg.warm_maps(wins[0][1], wins[0][2], cams1, pts1)
+    with ba.Context(precision=ba.BA_MIXED) as ctx:
+        a0 = ctx.create_cluster(c0)
+        ctx.run(a0, ITERS, trace=False)
+        a = ctx.create_cluster(c1, warm_from=a0, warm_cam_map=cm, warm_pt_map=pm)
+        b = ctx.create_cluster(c1)
+        ctx.warm_start(b, a0, cm, pm)
+        for u, v in zip(ctx.get_state(a), ctx.get_state(b)):
+            assert np.array_equal(u, v)
+        ta, tb = ctx.run(a, ITERS), ctx.run(b, ITERS)
+        assert ta == tb
+        for u, v in zip(ctx.get_state(a), ctx.get_state(b)):
+            assert np.array_equal(u, v)
