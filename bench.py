@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--serving-flights", type=int, default=16)
     ap.add_argument("--serving-rate", type=float, default=200.0, help="requests/s, Poisson, all flights")
     ap.add_argument("--serving-iters", type=int, default=10)
+    ap.add_argument("--serving-only", action="store_true", help="run only the serving leg")
     ap.add_argument("--serving-timeout", type=float, default=120.0, help="seconds before the serving leg gives up")
     return ap.parse_args()
 
@@ -114,7 +115,8 @@ def serving_leg(args, ba, stream, flights):
     rate_f = args.serving_rate / max(1, len(flights))
     arrivals = [np.cumsum(rng.exponential(1.0 / rate_f, len(w))) for w in flights]
     ctx = ba.Context(device=torch_device(), precision=ba.BA_MIXED,
-                     stream=stream.cuda_stream, n_slots=64, hbm_budget_bytes=16 << 30)
+                     stream=stream.cuda_stream, n_slots=64, hbm_budget_bytes=16 << 30,
+                     flags=ba.BA_FLAG_KERNEL_TIMING)
     iters = args.serving_iters
     deadline = _t.perf_counter() + args.serving_timeout
     stop = threading.Event()
@@ -123,9 +125,11 @@ def serving_leg(args, ba, stream, flights):
         """Presort and upload a window as soon as it arrives (in parallel with
         the flight's previous window still being solved)."""
         c, _ = flights[f][w]
+        ts = _t.perf_counter()
         while not stop.is_set():
             try:
-                return ctx.create_cluster(c)
+                cid = ctx.create_cluster(c)
+                return cid, ts, _t.perf_counter()
             except ba.BAError as e:  # HBM budget: wait for completions to free memory
                 if e.status != ba.BA_ERR_BUDGET or _t.perf_counter() > deadline:
                     raise
@@ -139,6 +143,8 @@ def serving_leg(args, ba, stream, flights):
     old = [None] * n_fl         # the one before (destroyed once prev has been used)
     pending, inflight = {}, {}  # f -> (w, future) / (w, cid, ticket)
     lat, obs_done = [], 0
+    parts = {"create_ms": [], "wait_prev_ms": [], "service_ms": [], "sched_ms": []}
+    t_sub = {}
     max_inflight = 0
     ex = ThreadPoolExecutor(8)
     try:
@@ -156,11 +162,15 @@ def serving_leg(args, ba, stream, flights):
                 w, fut = pending[f]
                 if f not in inflight and ndone[f] == w and fut.done():
                     pending.pop(f)
-                    cid = fut.result()
+                    cid, cs, ce = fut.result()
                     maps = flights[f][w][1]
                     if maps is not None:
                         ctx.warm_start(cid, prev[f], maps[0], maps[1])
                     inflight[f] = (w, cid, ctx.submit(cid, iters))
+                    ts = _t.perf_counter()
+                    t_sub[f] = ts
+                    parts["create_ms"].append(1e3 * (ce - cs))
+                    parts["wait_prev_ms"].append(1e3 * (ts - max(ce, t0 + arrivals[f][w])))
             max_inflight = max(max_inflight, len(inflight))
             for f in list(inflight):
                 w, cid, t = inflight[f]
@@ -172,6 +182,8 @@ def serving_leg(args, ba, stream, flights):
                     raise RuntimeError(f"serving request failed: flight {f} window {w} status {r['status']}")
                 done = _t.perf_counter() - t0
                 lat.append(1e3 * (done - arrivals[f][w]))
+                parts["service_ms"].append(1e3 * (done + t0 - t_sub[f]))
+                parts["sched_ms"].append(r["latency_ms"])
                 obs_done += flights[f][w][0]["n_obs"] * iters
                 if old[f] is not None:
                     ctx.destroy_cluster(old[f])
@@ -182,21 +194,24 @@ def serving_leg(args, ba, stream, flights):
     finally:
         stop.set()
         ex.shutdown(wait=True, cancel_futures=True)
+    kst = ctx.kernel_stats(reset=True)
     ctx.close()
+    rounds = max(1, kst["lm_update"][1])
+    round_kernels = {k: v[0] / rounds for k, v in kst.items() if v[1]}
     lat = np.array(lat)
+    pct = {k: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))} for k, v in parts.items() if v}
     return {"requests": int(len(lat)), "flights": len(flights), "arrival_rate_req_s": args.serving_rate,
             "iters_per_request": iters, "p50_ms": float(np.percentile(lat, 50)),
             "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
             "throughput_req_s": len(lat) / span, "obs_per_s": obs_done / span, "max_in_flight": max_inflight,
             "window_images": "12-32, last 25 % reused, first half of the overlap fixed, device warm start",
-            "note": "latency = completion - arrival, host clock; includes cluster creation (presort + upload)"}
-
-
-def pair_entries(scene):
-    """Co-visible (camera, camera) pairs per point, summed: the units of the
-    pair reduction."""
-    L = np.bincount(scene["obs_pt"], minlength=scene["n_pts"])
-    return int(np.sum(L * (L - 1) // 2))
+            "obs_per_request_mean": float(np.mean([w[0]["n_obs"] for fl in flights for w in fl])),
+            "breakdown": pct, "rounds": rounds, "kernel_ms_per_round": round_kernels,
+            "span_s": span,
+            "note": "latency = completion - arrival, host clock; includes cluster creation (presort + upload); "
+                    "breakdown: create = ba_create_cluster, wait_prev = submit - max(created, arrival) (the "
+                    "flight's previous window still running), service = completion seen by the client - submit, "
+                    "sched = submit -> completion inside the library"}
 
 
 # ---------------------------------------------------------------- clocks
@@ -311,33 +326,62 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- roofline helpers
 
-def algorithmic_bytes(kind, scenes):
-    """Minimum DRAM bytes one launch of a kernel kind must move for the whole
-    batch in mixed precision (FP32 records), from the per-unit figures."""
-    no = sum(s["n_obs"] for s in scenes)
-    npt = sum(s["n_pts"] for s in scenes)
-    nfree_obs = sum(int(np.sum(s["fixed"][s["obs_cam"]] == 0)) for s in scenes)
-    if kind == "linearize":
-        # obs: cam+pt idx 8 B, uv 8 B; point read 24 B; record write 128 B; point aux write 64 B
-        return no * (8 + 8 + 128) + npt * (24 + 64)
-    if kind == "cam_reduce":
-        # per free-camera observation: index 4 B, record 128 B, point idx 4 B, q 12 B
-        return nfree_obs * (4 + 128 + 4 + 12)
-    if kind == "pair_reduce":
-        # Z (72 B) of every observation once + 8 B per pair entry
-        return no * 72 + 8 * sum(pair_entries(s) for s in scenes)
+# Algorithmic work per unit of one LM iteration (binary64-equivalent operation
+# counts of the method's arithmetic; double-float and recomputation overheads
+# are not counted).  Units come from ba_get_cluster_info.
+#   lin_schur   258 flop / observation (projection + Brown distortion 54, Huber
+#               weight and whitening 4, Jacobians 91, point-block terms 36,
+#               P = Jp M^T and Z = Jc^T P 72) + 294 / observation of a free
+#               image (21 entries of Jc^T Jc - Z Z^T at 10, -Jc^T r 24, Z q 36,
+#               diag 24) + 216 / pair entry (36 entries of Z_a Z_b^T at 6)
+#               + 45 / point (damping, 3x3 Cholesky, inverse, q)
+#   backsub     258 / observation (relinearisation) + 36 / free observation
+#               (Z^T dc) + 63 / observation (candidate residual and Huber cost)
+#               + 60 / point (linearisation head, M^T (q - s), update)
+#   bytes (lin_schur): per observation image index 4 + point index 4 +
+#               observation 8 B; per point state 24 B; per free observation
+#               2 B (list); per pair entry 4 B; per chunk partial 156 / 144 B written
+FLOP_LIN = dict(obs=258, free_obs=294, pair=216, pt=45)
+FLOP_BACK = dict(obs=258 + 63, free_obs=36, pair=0, pt=60)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+FP64_PEAK_TFLOPS = 1.25                               # nominal dense FP64
+
+
+def units(infos):
+    u = dict(obs=0, free_obs=0, pair=0, pt=0, cslots=0, pslots=0, free=0, pairs=0, tiles=0)
+    for v in infos:
+        u["obs"] += v["n_obs"]; u["free_obs"] += v["n_free_obs"]; u["pair"] += v["n_pair_entries"]
+        u["pt"] += v["n_pts"]; u["cslots"] += v["n_cam_slots"]; u["pslots"] += v["n_pair_slots"]
+        u["free"] += v["n_free"]; u["pairs"] += v["n_pairs"]; u["tiles"] += v["n_tiles"]
+    return u
+
+
+def kernel_work(kind, u, infos, refine):
+    """(bound, amount, unit) of one launch of a kernel kind over the batch."""
+    if kind == "lin_schur":
+        return "alu", sum(FLOP_LIN[k] * u[k] for k in FLOP_LIN), "flop"
     if kind == "backsub_cost":
-        # obs: idx 8 B, Z 72 B, uv 16 B; point read 24 B + aux 64 B, candidate write 24 B; partials
-        return no * (8 + 72 + 16) + npt * (24 + 64 + 24)
+        return "alu", sum(FLOP_BACK[k] * u[k] for k in FLOP_BACK), "flop"
+    if kind == "factor":
+        return "alu64", factor_flops(infos, refine), "flop"
+    if kind == "partial_reduce":
+        # FP32 chunk partials read, FP64 per-camera / per-pair sums written, slot lists read
+        b = (u["cslots"] * 39 + u["pslots"] * 36) * 4 + (u["free"] * 39 + u["pairs"] * 36) * 8 + \
+            4 * (u["cslots"] + u["pslots"])
+        return "hbm", b, "byte"
     if kind == "cost_tiles":
-        return no * (8 + 16) + npt * 24
+        return "hbm", u["obs"] * 16 + u["pt"] * 24, "byte"
     return None
 
 
-def factor_flops(scenes, refine):
+def lin_schur_bytes(u):
+    return u["obs"] * 16 + u["pt"] * 24 + u["free_obs"] * 2 + u["pair"] * 4 + u["cslots"] * 156 + u["pslots"] * 144
+
+
+def factor_flops(infos, refine):
     tot = 0.0
-    for s in scenes:
-        n = 6 * int(np.sum(s["fixed"] == 0))
+    for v in infos:
+        n = 6 * v["n_free"]
         tot += n ** 3 / 3.0 + (2 + 2 * refine) * 2.0 * n * n + refine * 2.0 * n * n
     return tot
 
@@ -359,6 +403,17 @@ def main():
         run_reference(args)
         return
     rank, world, local = dist_env()
+    if args.serving_only:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+            flights = pool.map(serving_flight, [4000 + f for f in range(args.serving_flights)])
+        import torch
+        import paper_2511_06152_gb300 as ba
+        torch.cuda.set_device(local)
+        stream = torch.cuda.Stream()
+        log("serving leg")
+        print(json.dumps({"serving": serving_leg(args, ba, stream, flights)}), flush=True)
+        return
     n_fl = 0 if (args.no_extras or rank != 0 or world != 1) else args.serving_flights
     log(f"generating {args.clusters} clusters and {n_fl} serving flights")
     scenes, flights = make_workload(rank, args.clusters, n_fl)  # spawn pool before the first CUDA call
@@ -415,20 +470,28 @@ def main():
     lm_iters_per_s = world * len(ids) * iters * args.steps / (t_max * 1e-3)
 
     # dominant kernel and its roofline
+    infos = [ctx.cluster_info(c) for c in ids]
+    u = units(infos)
     dom = max((k for k in kst if k != "other"), key=lambda k: kst[k][0])
     dom_ms, dom_n = kst[dom]
     pk, src = peaks()
-    if dom == "factor":
-        flops = factor_flops(scenes, 1)
-        achieved = flops / (dom_ms / dom_n * 1e-3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": 1.25, "unit": "TFLOP/s",
-                "frac": achieved / 1.25, "traffic": None,
-                "peak_source": "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak in MEASURED_PEAKS.json)"}
-    else:
-        b = algorithmic_bytes(dom, scenes)
-        achieved = b / (dom_ms / dom_n * 1e-3) / 1e9
+    bound, amount, _ = kernel_work(dom, u, infos, 1)
+    sec = dom_ms / dom_n * 1e-3
+    if bound == "hbm":
+        achieved = amount / sec / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": f"hbm_gbs of {src}"}
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": f"hbm_gbs of {src}",
+                "algorithmic_bytes_per_launch": amount}
+    else:
+        peak = FP32_PEAK_TFLOPS if bound == "alu" else FP64_PEAK_TFLOPS
+        achieved = amount / sec / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": ("FP32: 152 SMs x 128 lanes x 2 flop x 2.070 GHz (derived)" if bound == "alu"
+                                else "FP64 nominal dense 1.25 TFLOP/s"),
+                "algorithmic_flop_per_launch": amount}
+        if dom == "lin_schur":
+            roof["hbm_gbs_algorithmic"] = lin_schur_bytes(u) / sec / 1e9
     kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / max(1e-9, sum(
         x[0] for x in kst.values()))} for k, v in kst.items() if v[1]}
 

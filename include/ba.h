@@ -96,16 +96,15 @@ typedef struct {
 #define BA_FLAG_KERNEL_TIMING 1 /* bracket every kernel with CUDA events (also inside graphs) */
 
 /* Kernel kinds reported by ba_kernel_stats, in this order. */
-#define BA_KERNEL_LINEARIZE 0   /* residuals, Jacobians, point blocks, Z = W L^-T */
-#define BA_KERNEL_CAM_REDUCE 1  /* camera-major chunk sums */
-#define BA_KERNEL_PAIR_REDUCE 2 /* camera-pair chunk sums */
-#define BA_KERNEL_FACTOR 3      /* assembly, Cholesky, solve, refinement, candidate poses */
-#define BA_KERNEL_BACKSUB 4     /* point back-substitution and candidate cost */
-#define BA_KERNEL_LM_UPDATE 5   /* gain ratio, accept/reject, damping update */
-#define BA_KERNEL_COST_TILES 6  /* cost at the current state (per tile) */
-#define BA_KERNEL_COST_INIT 7   /* cost at the current state (per cluster) */
-#define BA_KERNEL_OTHER 8       /* arm, reset, gather, camera copies, diagnostics */
-#define BA_KERNEL_KINDS 9
+#define BA_KERNEL_LIN_SCHUR 0      /* per chunk: residuals, Jacobians, point blocks, Schur partial sums */
+#define BA_KERNEL_PARTIAL_REDUCE 1 /* chunk partial sums -> per-camera / per-pair sums */
+#define BA_KERNEL_FACTOR 2         /* assembly, Cholesky, solve, refinement, candidate poses */
+#define BA_KERNEL_BACKSUB 3        /* point back-substitution and candidate cost */
+#define BA_KERNEL_LM_UPDATE 4      /* gain ratio, accept/reject, damping update */
+#define BA_KERNEL_COST_TILES 5     /* cost at the current state (per tile) */
+#define BA_KERNEL_COST_INIT 6      /* cost at the current state (per cluster) */
+#define BA_KERNEL_OTHER 7          /* arm, reset, gather, camera copies, diagnostics */
+#define BA_KERNEL_KINDS 8
 
 typedef struct {
   int32_t n_cams, n_pts, n_obs;
@@ -228,6 +227,28 @@ BA_API ba_status ba_get_state(ba_ctx* ctx, ba_cluster_id id, double* R, double* 
 /* Per-observation reprojection error norms |pi(...) - p| in pixels at the
  * current state, in the caller's observation order (host buffer [n_obs]). */
 BA_API ba_status ba_reprojection_errors(ba_ctx* ctx, ba_cluster_id id, double* err);
+
+/* Sizes of a cluster's presorted tables: the units the kernels of one LM
+ * iteration process (used to state work per launch, and to plan capacity).
+ * Observations and points count as after validation; pair entries are the
+ * (observation, observation) pairs of one point whose two images are both
+ * free, i.e. the terms of sum_j Z_kj Z_lj^T in the Schur complement. */
+typedef struct ba_cluster_info {
+  int32_t n_cams, n_free, n_pts, n_obs;
+  int32_t n_tiles;       /* warp tiles of whole points, at most 32 observations each */
+  int32_t n_chunks;      /* CTA chunks of consecutive tiles */
+  int32_t n_cam_slots;   /* per-chunk partial sums of free cameras */
+  int32_t n_pair_slots;  /* per-chunk partial sums of co-visible free-camera pairs */
+  int32_t n_pairs;       /* co-visible free-camera pairs (off-diagonal blocks of S) */
+  int32_t reserved;
+  int64_t n_free_obs;    /* observations by free cameras */
+  int64_t n_pair_entries;
+  int64_t arena_bytes;   /* device memory held by the cluster */
+} ba_cluster_info;
+
+/* Fill *out for cluster id (host pointer).  BA_ERR_NOT_FOUND for an unknown
+ * id.  Reads host-side records only: no device work. */
+BA_API ba_status ba_get_cluster_info(ba_ctx* ctx, ba_cluster_id id, ba_cluster_info* out);
 
 /* Device memory the context holds now, in bytes. */
 BA_API ba_status ba_memory_in_use(ba_ctx* ctx, uint64_t* bytes);

@@ -31,8 +31,8 @@ BA_MIXED = 1
 BA_PTR_HOST = 0
 BA_PTR_DEVICE = 1
 BA_FLAG_KERNEL_TIMING = 1
-KERNEL_KINDS = ["linearize", "cam_reduce", "pair_reduce", "factor", "backsub_cost", "lm_update", "cost_tiles",
-                "cost_init", "other"]
+KERNEL_KINDS = ["lin_schur", "partial_reduce", "factor", "backsub_cost", "lm_update", "cost_tiles", "cost_init",
+                "other"]
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int32)
@@ -82,9 +82,18 @@ class ba_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ba_cluster_info(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in ("n_cams", "n_free", "n_pts", "n_obs", "n_tiles", "n_chunks",
+                                             "n_cam_slots", "n_pair_slots", "n_pairs", "reserved")] + \
+               [(k, ctypes.c_int64) for k in ("n_free_obs", "n_pair_entries", "arena_bytes")]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 EXPORTS = ["ba_init", "ba_create_cluster", "ba_linearize", "ba_solve_step", "ba_run", "ba_solve_batch", "ba_reset",
            "ba_reset_batch", "ba_submit", "ba_poll", "ba_get_state", "ba_reprojection_errors", "ba_memory_in_use",
-           "ba_launch_count", "ba_kernel_stats", "ba_cost_noalloc", "ba_warm_start", "ba_destroy_cluster", "ba_shutdown",
+           "ba_launch_count", "ba_kernel_stats", "ba_cost_noalloc", "ba_warm_start", "ba_get_cluster_info", "ba_destroy_cluster", "ba_shutdown",
            "ba_status_string", "ba_last_error"]
 
 _lib = None
@@ -121,6 +130,7 @@ def lib(build: bool = True):
             L.ba_get_state.argtypes = [vp, u64, _dp, _dp, _dp, ctypes.c_int32]
             L.ba_reprojection_errors.argtypes = [vp, u64, _dp]
             L.ba_memory_in_use.argtypes = [vp, ctypes.POINTER(u64)]
+            L.ba_get_cluster_info.argtypes = [vp, u64, ctypes.POINTER(ba_cluster_info)]
             L.ba_destroy_cluster.argtypes = [vp, u64]
             L.ba_shutdown.argtypes = [vp]
             L.ba_status_string.argtypes = [ctypes.c_int32]
@@ -304,6 +314,12 @@ class Context:
         v = ctypes.c_uint64()
         _check(self.L.ba_memory_in_use(self.h, ctypes.byref(v)), self.h, "ba_memory_in_use")
         return v.value
+
+    def cluster_info(self, cid):
+        """Table sizes of a cluster (units of work per LM iteration)."""
+        v = ba_cluster_info()
+        _check(self.L.ba_get_cluster_info(self.h, cid, ctypes.byref(v)), self.h, "ba_get_cluster_info")
+        return v.as_dict()
 
     def destroy_cluster(self, cid):
         _check(self.L.ba_destroy_cluster(self.h, cid), self.h, "ba_destroy_cluster")

@@ -35,6 +35,7 @@ struct Cluster {
   std::vector<int> pm_to_user;    // point-major position -> caller observation index
   std::vector<int> pt_inv;        // caller point index -> internal point index
   std::atomic<int> in_service{0}; // queued or running in the serving scheduler
+  ba_cluster_info info{};         // table sizes, filled at creation
 };
 
 struct GraphRec {
@@ -844,6 +845,15 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   c->nc = nc; c->np = np; c->no = no; c->nf = nf;
   c->arena = arena;
   c->arena_bytes = total;
+  c->info.n_cams = nc; c->info.n_free = nf; c->info.n_pts = np; c->info.n_obs = no;
+  c->info.n_tiles = (int)tiles.size();
+  c->info.n_chunks = (int)chunks.size();
+  c->info.n_cam_slots = n_cslots;
+  c->info.n_pair_slots = n_pslots;
+  c->info.n_pairs = n_pairs;
+  c->info.n_free_obs = (int64_t)cm_list.size();
+  c->info.n_pair_entries = (int64_t)pent.size();
+  c->info.arena_bytes = (int64_t)total;
   c->pm_to_user = std::move(pm);
   c->pt_inv = std::move(inv);
   ctx->mem += total;
@@ -1413,6 +1423,15 @@ BA_API ba_status ba_memory_in_use(ba_ctx* ctx, uint64_t* bytes) {
   if (!ctx || !bytes) return BA_ERR_INVALID;
   std::lock_guard<std::mutex> g(ctx->api_mu);
   *bytes = ctx->mem;
+  return BA_OK;
+}
+
+BA_API ba_status ba_get_cluster_info(ba_ctx* ctx, ba_cluster_id id, ba_cluster_info* out) {
+  if (!ctx || !out) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  Cluster* c = find_cluster(ctx, id);
+  if (!c) return BA_ERR_NOT_FOUND;
+  *out = c->info;
   return BA_OK;
 }
 

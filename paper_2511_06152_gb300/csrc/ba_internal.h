@@ -171,9 +171,8 @@ struct BatchView {
 
 // Kernel kinds, for launch counting and per-kernel timing.
 enum KernelKind {
-  KK_LINEARIZE = 0,
-  KK_CAM_REDUCE,   // chunk partials -> per-camera / per-pair sums
-  KK_PAIR_REDUCE,  // unused
+  KK_LIN_SCHUR = 0,
+  KK_PARTIAL_REDUCE,  // chunk partials -> per-camera / per-pair sums
   KK_FACTOR,
   KK_BACKSUB,
   KK_LM_UPDATE,

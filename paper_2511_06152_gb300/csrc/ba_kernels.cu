@@ -1,20 +1,27 @@
 // Kernels of one LM iteration, batched over many clusters.
 //
-//   k_linearize     per observation (warp per tile of whole points): residual,
-//                   Jacobians, point blocks V = sum Jp^T Jp, g_p = -sum Jp^T r
-//                   by deterministic segmented warp reductions, the damped
-//                   point block V* = V + mu Dp, its Cholesky factor L and
-//                   Linv = L^-1, q = Linv g_p, and Z = W Linv^T = Jc^T (Jp Linv^T),
-//                   so that W V*^-1 W^T = Z Z^T and W V*^-1 g_p = Z q.
-//   k_cam_reduce    camera-major chunks: sum (Jc^T Jc - Z Z^T), -Jc^T r, Z q,
-//                   diag(Jc^T Jc) of every observation of a free camera.
-//   k_pair_reduce   camera-pair chunks: sum Z_a Z_b^T over co-visible points.
-//   k_factor_solve  per cluster (FP64): assemble S = U* - W V*^-1 W^T and
-//                   rhs = g_c - W V*^-1 g_p with priors and damping, Cholesky,
-//                   solve, iterative refinement, candidate camera poses.
-//   k_backsub_cost  per observation: dX = Linv^T (q - sum_k Z_k^T dc_k),
-//                   candidate points, cost at the candidate, pred terms.
-//   k_lm_update     per cluster: gain ratio, accept/reject, Nielsen update.
+//   k_lin_schur      one CTA per chunk of consecutive tiles (a tile is up to 32
+//                    observations of whole points, one warp).  Each warp
+//                    linearises its tiles: residual, Jacobians (Eq. 5-7),
+//                    point blocks V = sum Jp^T Jp and g_p = -sum Jp^T r by
+//                    segmented warp reductions, V* = V + mu D_p = L L^T,
+//                    M = L^-1, q = M g_p and Z = Jc^T Jp M^T, so that
+//                    W V*^-1 W^T = Z Z^T and W V*^-1 g_p = Z q; one record per
+//                    observation goes to shared memory.  The CTA then runs the
+//                    chunk's reduction jobs: per free image the sums of
+//                    Jc^T Jc - Z Z^T, -Jc^T r, Z q, diag(Jc^T Jc), and per
+//                    co-visible image pair the sum of Z_a Z_b^T, each job on a
+//                    run of lanes sized by its cost.  One partial sum per job.
+//   k_partial_reduce the chunks' partial sums of each image and each pair,
+//                    added in chunk order (FP64).
+//   k_factor_solve   per cluster (FP64): assemble S = U* - W V*^-1 W^T and
+//                    rhs = g_c - W V*^-1 g_p with priors and damping, blocked
+//                    Cholesky in shared memory, solve, iterative refinement,
+//                    candidate camera poses.
+//   k_backsub_cost   per tile: linearise again (same arithmetic, same values),
+//                    dX = M^T (q - sum_k Z_k^T dc_k), candidate points, cost
+//                    at the candidate and the predicted reduction.
+//   k_lm_update      per cluster: gain ratio, accept/reject, Nielsen update.
 //
 // Precision.  MIXED = false: every step in binary64.  MIXED = true: the
 // per-observation linearisation, the Schur reductions and the back-
@@ -1382,7 +1389,7 @@ static size_t chunk_smem_bytes(bool mixed) {
 
 template <bool MIXED>
 static void launch_lin_schur(const BatchView& bv, int diag, cudaStream_t st) {
-  LAUNCH(KK_LINEARIZE, st,
+  LAUNCH(KK_LIN_SCHUR, st,
          k_lin_schur<MIXED><<<grid_for(bv.total_chunks, 1, num_sms() * 8), kChunkThreads, chunk_smem_bytes(MIXED),
                               st>>>(bv, diag));
 }
@@ -1390,7 +1397,7 @@ static void launch_lin_schur(const BatchView& bv, int diag, cudaStream_t st) {
 template <bool MIXED>
 static void launch_partial_reduce(const BatchView& bv, cudaStream_t st) {
   using Real = typename RealOf<MIXED>::T;
-  LAUNCH(KK_CAM_REDUCE, st, k_partial_reduce<Real><<<grid_for(bv.total_items, 8, num_sms() * 16), 256, 0, st>>>(bv));
+  LAUNCH(KK_PARTIAL_REDUCE, st, k_partial_reduce<Real><<<grid_for(bv.total_items, 8, num_sms() * 16), 256, 0, st>>>(bv));
 }
 
 template <bool MIXED>

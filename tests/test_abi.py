@@ -44,10 +44,34 @@ def test_status_strings_and_init_without_gpu():
     assert st == ba.BA_ERR_CUDA  # fails loudly: no CPU fallback
 
 
-def test_struct_layouts_match_header():
-    """ctypes mirrors of the ABI structs have the C sizes (x86-64 / aarch64 LP64)."""
+STRUCTS = ["ba_config", "ba_cluster_desc", "ba_lin_info", "ba_step_info", "ba_solve_opts", "ba_result",
+           "ba_cluster_info"]
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """ctypes mirrors of the ABI structs have the size and field offsets that
+    the C compiler gives the declarations in include/ba.h."""
+    import shutil
+    import subprocess
     import paper_2511_06152_gb300 as ba
-    assert ctypes.sizeof(ba.ba_config) == 4 + 4 + 8 + 8 + 4 * 4
-    assert ctypes.sizeof(ba.ba_step_info) == 8 + 7 * 8
-    assert ctypes.sizeof(ba.ba_result) == 16 + 3 * 8
-    assert ctypes.sizeof(ba.ba_lin_info) == 24
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "ba.h"', "int main(void) {"]
+    for name in STRUCTS:
+        st = getattr(ba, name)
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                              text=True).stdout.splitlines())
+    for name in STRUCTS:
+        st = getattr(ba, name)
+        assert int(out[name]) == ctypes.sizeof(st), name
+        for f, _ in st._fields_:
+            assert int(out[f"{name}.{f}"]) == getattr(st, f).offset, (name, f)
