@@ -61,6 +61,7 @@ struct Ticket {
   int done = 0;
   ba_result res{};
   std::chrono::steady_clock::time_point t_submit;
+  cudaEvent_t ready = nullptr;  // recorded on the context's stream at submit
 };
 
 // Serving slots (see scheduler_loop).
@@ -100,11 +101,12 @@ struct ba_ctx {
   std::map<std::vector<ba_cluster_id>, Plan*> plans;
   int attr_max_n = 0;
   bool timing = false;
+  std::mutex stats_mu;  // kernel statistics (API threads and the scheduler)
   double kms[KK_COUNT] = {0};
   uint64_t klaunch[KK_COUNT] = {0};
-  uint64_t launches = 0;
-  std::string last_error;
-  std::mutex api_mu;  // serialises API calls against the scheduler thread
+  std::atomic<uint64_t> launches{0};
+  std::mutex api_mu;  // cluster table, plans, budget; never held across a serving round
+  cudaMemPool_t pool = nullptr;  // device memory of clusters and plans (stream-ordered)
 
   // serving
   std::mutex sv_mu;
@@ -115,13 +117,19 @@ struct ba_ctx {
   std::thread sched;
   bool sched_stop = false;
   bool sched_started = false;
+  cudaStream_t sched_stream = nullptr;  // the scheduler's rounds
   SlotTable slots;
 };
 
 namespace {
 
+// message of the calling thread's last failing call (like errno: the API is
+// called from several threads, the scheduler among them)
+thread_local std::string t_last_error;
+
 ba_status set_err(ba_ctx* ctx, ba_status st, const std::string& msg) {
-  if (ctx) ctx->last_error = msg;
+  (void)ctx;
+  t_last_error = msg;
   return st;
 }
 
@@ -183,12 +191,20 @@ void free_probe(Probe* pr) {
 
 void note_direct(ba_ctx* ctx) { ctx->launches += take_direct_launches(); }
 
-void free_plan(Plan* p) {
+// Device memory of clusters and plans comes from the context's own pool,
+// stream-ordered: a free is queued behind the work already on its stream and
+// never waits for the device, so retiring a cluster does not stall a serving
+// round.  The pool keeps what it has reserved (no release threshold).
+cudaError_t pool_alloc(ba_ctx* ctx, void** p, size_t bytes, cudaStream_t st) {
+  return cudaMallocFromPoolAsync(p, bytes, ctx->pool, st);
+}
+
+void free_plan(ba_ctx* ctx, Plan* p) {
   for (auto& kv : p->graphs) {
-    cudaGraphExecDestroy(kv.second.exec);
+    cudaGraphExecDestroy(kv.second.exec);  // an executing graph is freed when it completes
     free_probe(kv.second.probe);
   }
-  if (p->dbuf) cudaFree(p->dbuf);
+  if (p->dbuf) cudaFreeAsync(p->dbuf, ctx->stream);
   delete p;
 }
 
@@ -196,7 +212,7 @@ void drop_plans_with(ba_ctx* ctx, ba_cluster_id id) {
   for (auto it = ctx->plans.begin(); it != ctx->plans.end();) {
     if (std::find(it->first.begin(), it->first.end(), id) != it->first.end()) {
       ctx->mem -= it->second->dbuf_bytes;
-      free_plan(it->second);
+      free_plan(ctx, it->second);
       it = ctx->plans.erase(it);
     } else {
       ++it;
@@ -244,10 +260,10 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
     delete p;
     return set_err(ctx, BA_ERR_BUDGET, "batch plan exceeds the device-memory budget");
   }
-  cudaError_t e = cudaMalloc((void**)&p->dbuf, p->dbuf_bytes);
+  cudaError_t e = pool_alloc(ctx, (void**)&p->dbuf, p->dbuf_bytes, ctx->stream);
   if (e != cudaSuccess) {
     delete p;
-    return set_err(ctx, BA_ERR_CUDA, std::string("cudaMalloc(plan): ") + cudaGetErrorString(e));
+    return set_err(ctx, BA_ERR_CUDA, std::string("plan allocation: ") + cudaGetErrorString(e));
   }
   ctx->mem += p->dbuf_bytes;
   e = cudaMemcpyAsync(p->dbuf + o_desc, descs.data(), sizeof(DevCluster) * n, cudaMemcpyHostToDevice, ctx->stream);
@@ -258,7 +274,7 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     ctx->mem -= p->dbuf_bytes;
-    free_plan(p);
+    free_plan(ctx, p);
     return set_err(ctx, BA_ERR_CUDA, std::string("plan upload: ") + cudaGetErrorString(e));
   }
   const int* dpre = (const int*)(p->dbuf + o_pre);
@@ -320,13 +336,18 @@ ba_status run_plan(ba_ctx* ctx, Plan* p, int iters) {
 
 // After the stream has synchronised: fold the last graph's event times into
 // the per-kernel statistics.
-void collect_timing(ba_ctx* ctx, Plan* p) {
-  if (!ctx->timing || !p->last || !p->last->probe) return;
-  for (auto& r : p->last->probe->recs) {
+void fold_probe(ba_ctx* ctx, const Probe* pr) {
+  std::lock_guard<std::mutex> g(ctx->stats_mu);
+  for (auto& r : pr->recs) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) ctx->kms[r.kind] += ms;
     ctx->klaunch[r.kind] += 1;
   }
+}
+
+void collect_timing(ba_ctx* ctx, Plan* p) {
+  if (!ctx->timing || !p->last || !p->last->probe) return;
+  fold_probe(ctx, p->last->probe);
 }
 
 void fill_step(const StepRec& r, ba_step_info* o) {
@@ -376,6 +397,16 @@ ba_status run_and_collect(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, in
 }
 
 // ------------------------------------------------------------------ cluster creation
+
+// A one-cluster view for the kernels that only walk the descriptor table
+// (camera records, warm start): no prefix sums, no device allocation.
+BatchView one_view(const DevCluster* d_desc, int n_free) {
+  BatchView bv{};
+  bv.cl = d_desc;
+  bv.n = 1;
+  bv.max_n = 6 * n_free;
+  return bv;
+}
 
 ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const int nc = d->n_cams, np = d->n_pts, no = d->n_obs;
@@ -768,18 +799,41 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
     put(o_lm, &lm, sizeof(lm));
   }
 
-  // everything above is host work; the device part runs under the API lock
-  std::unique_lock<std::mutex> lk(ctx->api_mu);
-  if (ctx->budget && ctx->mem + total > ctx->budget)
-    return set_err(ctx, BA_ERR_BUDGET, "cluster exceeds the device-memory budget");
-  char* arena = nullptr;
-  cudaError_t e = cudaMalloc((void**)&arena, total);
-  if (e != cudaSuccess) return set_err(ctx, BA_ERR_BUDGET, std::string("cudaMalloc(cluster): ") + cudaGetErrorString(e));
-  e = cudaMemcpyAsync(arena, stage_ptr, static_bytes, cudaMemcpyHostToDevice, ctx->stream);
-  if (e != cudaSuccess) {
-    cudaFree(arena);
-    return set_err(ctx, BA_ERR_CUDA, std::string("cluster upload: ") + cudaGetErrorString(e));
+  // Everything above is host work.  The budget is reserved under the API
+  // lock; allocation, upload and the camera records run on a stream of this
+  // call without the lock, so creation overlaps other calls and serving.
+  {
+    std::lock_guard<std::mutex> g(ctx->api_mu);
+    if (ctx->budget && ctx->mem + total > ctx->budget)
+      return set_err(ctx, BA_ERR_BUDGET, "cluster exceeds the device-memory budget");
+    ctx->mem += total;
   }
+  auto unreserve = [&]() {
+    std::lock_guard<std::mutex> g(ctx->api_mu);
+    ctx->mem -= total;
+  };
+  cudaStream_t up = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    unreserve();
+    return set_err(ctx, BA_ERR_CUDA, std::string("upload stream: ") + cudaGetErrorString(e));
+  }
+  char* arena = nullptr;
+  e = pool_alloc(ctx, (void**)&arena, total, up);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(up);
+    unreserve();
+    return set_err(ctx, BA_ERR_BUDGET, std::string("cluster allocation: ") + cudaGetErrorString(e));
+  }
+  auto fail = [&](const char* what, cudaError_t err) {
+    cudaFreeAsync(arena, up);
+    cudaStreamSynchronize(up);
+    cudaStreamDestroy(up);
+    unreserve();
+    return set_err(ctx, BA_ERR_CUDA, std::string(what) + cudaGetErrorString(err));
+  };
+  e = cudaMemcpyAsync(arena, stage_ptr, static_bytes, cudaMemcpyHostToDevice, up);
+  if (e != cudaSuccess) return fail("cluster upload: ", e);
 
   DevCluster& h = c->h;
   h = DevCluster{};
@@ -836,12 +890,15 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   h.trace = (StepRec*)(arena + o_trace);
   h.trace_cap = kTraceCap;
   c->d_desc = (DevCluster*)(arena + o_desc);
-  e = cudaMemcpyAsync(c->d_desc, &h, sizeof(DevCluster), cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-  if (e != cudaSuccess) {
-    cudaFree(arena);
-    return set_err(ctx, BA_ERR_CUDA, std::string("cluster upload: ") + cudaGetErrorString(e));
+  e = cudaMemcpyAsync(c->d_desc, &h, sizeof(DevCluster), cudaMemcpyHostToDevice, up);
+  if (e == cudaSuccess) {
+    launch_camreal(one_view(c->d_desc, nf), mixed, up);
+    note_direct(ctx);
+    e = cudaGetLastError();
   }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(up);
+  if (e != cudaSuccess) return fail("cluster upload: ", e);
+  cudaStreamDestroy(up);
   c->nc = nc; c->np = np; c->no = no; c->nf = nf;
   c->arena = arena;
   c->arena_bytes = total;
@@ -856,7 +913,6 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   c->info.arena_bytes = (int64_t)total;
   c->pm_to_user = std::move(pm);
   c->pt_inv = std::move(inv);
-  ctx->mem += total;
   return BA_OK;
 }
 
@@ -961,10 +1017,10 @@ ba_status slots_upload(ba_ctx* ctx) {
   pre[3 * (n + 1) + 2] = pre[2 * (n + 1) + n];
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int b) { return T.descs[a].n_free > T.descs[b].n_free; });
-  CUDA_TRY(ctx, cudaMemcpyAsync(T.d_desc, T.descs.data(), sizeof(DevCluster) * n, cudaMemcpyHostToDevice, ctx->stream));
-  CUDA_TRY(ctx, cudaMemcpyAsync(T.d_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, ctx->stream));
-  CUDA_TRY(ctx, cudaMemcpyAsync(T.d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
-  CUDA_TRY(ctx, cudaMemcpyAsync(T.d_arm, T.arm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(T.d_desc, T.descs.data(), sizeof(DevCluster) * n, cudaMemcpyHostToDevice, ctx->sched_stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(T.d_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, ctx->sched_stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(T.d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->sched_stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(T.d_arm, T.arm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->sched_stream));
   T.dirty = false;
   return BA_OK;
 }
@@ -980,12 +1036,12 @@ ba_status slots_round(ba_ctx* ctx) {
       T.graph.probe = new Probe();
       set_probe(T.graph.probe);
     }
-    CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    launch_arm_slots(T.bv, T.d_arm, ctx->stream);
-    launch_cost_init(T.bv, ctx->mixed, ctx->stream);
-    launch_iteration(T.bv, ctx->mixed, ctx->refine, ctx->stream);
-    launch_gather(T.bv, 0, T.d_lm, nullptr, ctx->stream);
-    cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->sched_stream, cudaStreamCaptureModeThreadLocal));
+    launch_arm_slots(T.bv, T.d_arm, ctx->sched_stream);
+    launch_cost_init(T.bv, ctx->mixed, ctx->sched_stream);
+    launch_iteration(T.bv, ctx->mixed, ctx->refine, ctx->sched_stream);
+    launch_gather(T.bv, 0, T.d_lm, nullptr, ctx->sched_stream);
+    cudaError_t e = cudaStreamEndCapture(ctx->sched_stream, &graph);
     set_probe(nullptr);
     T.graph.kernels = take_captured_launches();
     if (e != cudaSuccess) return set_err(ctx, BA_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -997,17 +1053,12 @@ ba_status slots_round(ba_ctx* ctx) {
     ba_status st = slots_upload(ctx);
     if (st != BA_OK) return st;
   }
-  CUDA_TRY(ctx, cudaGraphLaunch(T.graph.exec, ctx->stream));
+  CUDA_TRY(ctx, cudaGraphLaunch(T.graph.exec, ctx->sched_stream));
   ctx->launches += T.graph.kernels;
-  CUDA_TRY(ctx, cudaMemcpyAsync(T.lm.data(), T.d_lm, sizeof(LmState) * T.n, cudaMemcpyDeviceToHost, ctx->stream));
-  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(T.lm.data(), T.d_lm, sizeof(LmState) * T.n, cudaMemcpyDeviceToHost, ctx->sched_stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->sched_stream));
   CUDA_TRY(ctx, cudaGetLastError());
-  if (ctx->timing && T.graph.probe)
-    for (auto& r : T.graph.probe->recs) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) ctx->kms[r.kind] += ms;
-      ctx->klaunch[r.kind] += 1;
-    }
+  if (ctx->timing && T.graph.probe) fold_probe(ctx, T.graph.probe);
   bool armed = false;
   for (int s = 0; s < T.n; ++s)
     if (T.arm[s]) {
@@ -1022,7 +1073,9 @@ void scheduler_loop(ba_ctx* ctx) {
   SlotTable& T = ctx->slots;
   cudaSetDevice(ctx->device);
   int running = 0;
+  std::vector<cudaEvent_t> admitted;
   for (;;) {
+    admitted.clear();
     {
       std::unique_lock<std::mutex> lk(ctx->sv_mu);
       ctx->sv_cv.wait(lk, [&] { return ctx->sched_stop || !ctx->queue.empty() || running > 0; });
@@ -1048,13 +1101,20 @@ void scheduler_loop(ba_ctx* ctx) {
         T.arm[s] = tk.iters;
         T.dirty = true;
         ++running;
+        admitted.push_back(tk.ready);
+        tk.ready = nullptr;
       }
     }
-    ba_status st;
-    {
-      std::lock_guard<std::mutex> g(ctx->api_mu);
-      st = slots_round(ctx);
+    // The round runs without the API lock: the clusters in the slots are
+    // marked in service, which every call that writes or frees a cluster
+    // refuses.  Work the caller queued on the context's stream before
+    // submitting (creation, warm start, reset) is ordered before the round.
+    ba_status st = BA_OK;
+    for (cudaEvent_t ev : admitted) {
+      if (cudaStreamWaitEvent(ctx->sched_stream, ev, 0) != cudaSuccess) st = BA_ERR_CUDA;
+      cudaEventDestroy(ev);
     }
+    if (st == BA_OK) st = slots_round(ctx);
     {
       std::lock_guard<std::mutex> lk(ctx->sv_mu);
       const auto now = std::chrono::steady_clock::now();
@@ -1103,7 +1163,7 @@ BA_API const char* ba_status_string(ba_status s) {
   }
 }
 
-BA_API const char* ba_last_error(ba_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+BA_API const char* ba_last_error(ba_ctx* ctx) { return ctx ? t_last_error.c_str() : "null context"; }
 
 BA_API ba_status ba_init(ba_ctx** out, const ba_config* cfg) {
   if (!out || !cfg) return BA_ERR_INVALID;
@@ -1127,6 +1187,20 @@ BA_API ba_status ba_init(ba_ctx** out, const ba_config* cfg) {
     }
     ctx->own_stream = true;
   }
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = cfg->device;
+  const uint64_t keep = UINT64_MAX;
+  if (cudaStreamCreateWithFlags(&ctx->sched_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess ||
+      cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, (void*)&keep) != cudaSuccess) {
+    if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    if (ctx->sched_stream) cudaStreamDestroy(ctx->sched_stream);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return BA_ERR_CUDA;
+  }
   *out = ctx;
   return BA_OK;
 }
@@ -1135,35 +1209,31 @@ BA_API ba_status ba_create_cluster(ba_ctx* ctx, const ba_cluster_desc* d, ba_clu
   if (!ctx || !d || !out) return BA_ERR_INVALID;
   cudaSetDevice(ctx->device);
   Cluster* c = new Cluster();
-  ba_status st = build_cluster(ctx, d, c);  // host presort unlocked; device upload under the lock
+  ba_status st = build_cluster(ctx, d, c);  // presort, upload and camera records, without the API lock
   if (st != BA_OK) {
     delete c;
     return st;
   }
   std::lock_guard<std::mutex> g(ctx->api_mu);
-  c->id = ctx->next_id++;
-  ctx->clusters[c->id] = c;
   if (d->warm_from) {
     Cluster* src = find_cluster(ctx, d->warm_from);
     st = (src && d->warm_cam_map && d->warm_pt_map && !src->in_service)
              ? warm_copy(ctx, c, src, d->warm_cam_map, d->warm_pt_map)
              : set_err(ctx, BA_ERR_NOT_FOUND, "warm_from cluster not found, in service, or maps missing");
+    if (st == BA_OK) {
+      launch_camreal(one_view(c->d_desc, c->nf), ctx->mixed, ctx->stream);
+      note_direct(ctx);
+      if (cudaGetLastError() != cudaSuccess) st = set_err(ctx, BA_ERR_CUDA, "warm start launch failed");
+    }
     if (st != BA_OK) {
-      ctx->clusters.erase(c->id);
-      drop_plans_with(ctx, c->id);
       ctx->mem -= c->arena_bytes;
-      cudaFree(c->arena);
+      cudaFreeAsync(c->arena, ctx->stream);
       delete c;
       return st;
     }
   }
-  Plan* p = nullptr;
-  st = single_view(ctx, c, &p);
-  if (st != BA_OK) return st;
-  launch_camreal(p->bv, ctx->mixed, ctx->stream);
-  note_direct(ctx);
-  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  CUDA_TRY(ctx, cudaGetLastError());
+  c->id = ctx->next_id++;
+  ctx->clusters[c->id] = c;
   *out = c->id;
   return BA_OK;
 }
@@ -1178,10 +1248,7 @@ BA_API ba_status ba_warm_start(ba_ctx* ctx, ba_cluster_id dst, ba_cluster_id src
   if (c->in_service || s->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
   ba_status st = warm_copy(ctx, c, s, cam_map, pt_map);
   if (st != BA_OK) return st;
-  Plan* p = nullptr;
-  st = single_view(ctx, c, &p);
-  if (st != BA_OK) return st;
-  launch_camreal(p->bv, ctx->mixed, ctx->stream);
+  launch_camreal(one_view(c->d_desc, c->nf), ctx->mixed, ctx->stream);
   note_direct(ctx);
   CUDA_TRY(ctx, cudaGetLastError());
   return BA_OK;
@@ -1321,7 +1388,7 @@ BA_API ba_status ba_launch_count(ba_ctx* ctx, uint64_t* out) {
 
 BA_API ba_status ba_kernel_stats(ba_ctx* ctx, double* ms, uint64_t* launches, int32_t n, int32_t reset) {
   if (!ctx || n < 0 || n > KK_COUNT) return BA_ERR_INVALID;
-  std::lock_guard<std::mutex> g(ctx->api_mu);
+  std::lock_guard<std::mutex> g(ctx->stats_mu);
   for (int i = 0; i < n; ++i) {
     if (ms) ms[i] = ctx->kms[i];
     if (launches) launches[i] = ctx->klaunch[i];
@@ -1336,6 +1403,7 @@ BA_API ba_status ba_kernel_stats(ba_ctx* ctx, double* ms, uint64_t* launches, in
 
 BA_API ba_status ba_submit(ba_ctx* ctx, ba_cluster_id id, const ba_solve_opts* opts, ba_ticket* out) {
   if (!ctx || !opts || !out || opts->max_iters <= 0) return BA_ERR_INVALID;
+  cudaEvent_t ready = nullptr;
   {
     std::lock_guard<std::mutex> g(ctx->api_mu);
     Cluster* c = find_cluster(ctx, id);
@@ -1343,9 +1411,16 @@ BA_API ba_status ba_submit(ba_ctx* ctx, ba_cluster_id id, const ba_solve_opts* o
     if (6 * c->nf > 6 * kMaxFreeSmall) return set_err(ctx, BA_ERR_INVALID, "cluster too large for a serving slot");
     ba_status st = slots_setup(ctx);
     if (st != BA_OK) return st;
+    CUDA_TRY(ctx, cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    if (cudaEventRecord(ready, ctx->stream) != cudaSuccess) {
+      cudaEventDestroy(ready);
+      return set_err(ctx, BA_ERR_CUDA, "ba_submit: event record failed");
+    }
     int expect = 0;
-    if (!c->in_service.compare_exchange_strong(expect, 1))
+    if (!c->in_service.compare_exchange_strong(expect, 1)) {
+      cudaEventDestroy(ready);
       return set_err(ctx, BA_ERR_INVALID, "cluster already submitted");
+    }
   }
   std::lock_guard<std::mutex> lk(ctx->sv_mu);
   if (!ctx->sched_started) {
@@ -1357,6 +1432,7 @@ BA_API ba_status ba_submit(ba_ctx* ctx, ba_cluster_id id, const ba_solve_opts* o
   tk.id = id;
   tk.iters = opts->max_iters;
   tk.t_submit = std::chrono::steady_clock::now();
+  tk.ready = ready;
   ctx->tickets[t] = tk;
   ctx->queue.push_back(t);
   ctx->sv_cv.notify_all();
@@ -1441,11 +1517,12 @@ BA_API ba_status ba_destroy_cluster(ba_ctx* ctx, ba_cluster_id id) {
   Cluster* c = find_cluster(ctx, id);
   if (!c) return BA_ERR_NOT_FOUND;
   if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
-  cudaStreamSynchronize(ctx->stream);
+  // stream-ordered: the arena is released after the work already queued on
+  // the context's stream; serving rounds that used it have completed
   drop_plans_with(ctx, id);
   ctx->clusters.erase(id);
   ctx->mem -= c->arena_bytes;
-  cudaFree(c->arena);
+  CUDA_TRY(ctx, cudaFreeAsync(c->arena, ctx->stream));
   delete c;
   return BA_OK;
 }
@@ -1458,15 +1535,21 @@ BA_API ba_status ba_shutdown(ba_ctx* ctx) {
     ctx->sv_cv.notify_all();
   }
   if (ctx->sched.joinable()) ctx->sched.join();
+  for (auto& kv : ctx->tickets)
+    if (kv.second.ready) cudaEventDestroy(kv.second.ready);
+  cudaStreamSynchronize(ctx->sched_stream);
   cudaStreamSynchronize(ctx->stream);
   if (ctx->slots.graph.exec) cudaGraphExecDestroy(ctx->slots.graph.exec);
   free_probe(ctx->slots.graph.probe);
   if (ctx->slots.dbuf) cudaFree(ctx->slots.dbuf);
-  for (auto& kv : ctx->plans) free_plan(kv.second);
+  for (auto& kv : ctx->plans) free_plan(ctx, kv.second);
   for (auto& kv : ctx->clusters) {
-    cudaFree(kv.second->arena);
+    cudaFreeAsync(kv.second->arena, ctx->stream);
     delete kv.second;
   }
+  cudaStreamSynchronize(ctx->stream);
+  cudaMemPoolDestroy(ctx->pool);
+  cudaStreamDestroy(ctx->sched_stream);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return BA_OK;

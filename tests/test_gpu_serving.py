@@ -125,3 +125,65 @@ def test_warm_start_after_create_equals_warm_create():
         assert ta == tb
         for u, v in zip(ctx.get_state(a), ctx.get_state(b)):
             assert np.array_equal(u, v)
+
+
+def test_creation_in_threads_while_serving_equals_alone():
+    """Windows are created on worker threads while other windows are being
+    solved (creation uploads on its own stream, the scheduler's rounds run
+    without the API lock); warm start and submit follow each flight's
+    previous window.  Every window's final state equals the one of the same
+    sequence run alone."""
+    from concurrent.futures import ThreadPoolExecutor
+    import paper_2511_06152_gb300 as ba
+    flights = [_flight(9111 + f) for f in range(4)]
+
+    def maps(f, w):
+        _, pc, pp = flights[f][w - 1]
+        _, cams, pts = flights[f][w]
+        return sg.warm_maps(pc, pp, cams, pts)
+
+    alone = []
+    with ba.Context(precision=ba.BA_MIXED) as ctx:
+        for f, wins in enumerate(flights):
+            prev, states = None, []
+            for w in range(len(wins)):
+                cid = ctx.create_cluster(wins[w][0])
+                if w:
+                    ctx.warm_start(cid, prev, *maps(f, w))
+                ctx.run(cid, ITERS, trace=False)
+                states.append(ctx.get_state(cid))
+                prev = cid
+            alone.append(states)
+
+    got = [[None] * len(w) for w in flights]
+    with ba.Context(precision=ba.BA_MIXED, n_slots=8) as ctx, ThreadPoolExecutor(4) as ex:
+        futs = [[ex.submit(ctx.create_cluster, wins[w][0]) for w in range(len(wins))] for wins in flights]
+        nxt, prev, live = [0] * len(flights), [None] * len(flights), {}
+        deadline = time.time() + 120
+        while any(nxt[f] < len(flights[f]) for f in range(len(flights))) or live:
+            assert time.time() < deadline, "serving did not finish"
+            for f in range(len(flights)):
+                w = nxt[f]
+                if f in live or w >= len(flights[f]) or not futs[f][w].done():
+                    continue
+                cid = futs[f][w].result()
+                if w:
+                    ctx.warm_start(cid, prev[f], *maps(f, w))
+                live[f] = (w, cid, ctx.submit(cid, ITERS))
+            for f in list(live):
+                w, cid, t = live[f]
+                r = ctx.poll(t)
+                if r is None:
+                    continue
+                assert r["status"] == 0 and r["iters"] == ITERS
+                del live[f]
+                got[f][w] = ctx.get_state(cid)
+                if prev[f] is not None:
+                    ctx.destroy_cluster(prev[f])
+                prev[f] = cid
+                nxt[f] += 1
+            time.sleep(0.0005)
+    for f in range(len(flights)):
+        for w in range(len(flights[f])):
+            for a, b in zip(alone[f][w], got[f][w]):
+                assert np.array_equal(a, b), (f, w)
