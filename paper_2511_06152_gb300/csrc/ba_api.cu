@@ -21,6 +21,8 @@
 #include "../../include/ba.h"
 #include "ba_internal.h"
 
+static_assert(bagpu::kDevErrTimeout == BA_ERR_TIMEOUT, "device and ABI timeout codes differ");
+
 using namespace bagpu;
 
 namespace {
@@ -556,6 +558,8 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
         ++t;
         ++ch.n_tiles;
       }
+      ch.pt_begin = ppt[ch.obs_begin];  // observations are sorted by internal point
+      ch.n_pts = ppt[ch.obs_begin + ch.n_obs - 1] - ch.pt_begin + 1;
       for (auto& v : per_cam) v.clear();
       for (int i = 0; i < n_lp_used; ++i) per_pair[i].clear();
       n_lp_used = 0;

@@ -26,10 +26,13 @@ __device__ __forceinline__ int find_slot(const int* __restrict__ pre, int n, int
 
 // Reduce v over lanes [seg_start, seg_end) of a warp to lane seg_start by a
 // binary tree whose shape depends only on the segment: deterministic.
+// span = the warp's longest segment (warp-uniform): the levels at or above
+// it add nothing and are skipped, which leaves every sum unchanged.
 template <typename T>
-__device__ __forceinline__ T seg_reduce(T v, int lane, int seg_start, int seg_end) {
+__device__ __forceinline__ T seg_reduce(T v, int lane, int seg_start, int seg_end, int span = 32) {
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
+    if (off >= span) break;
     const T o = __shfl_down_sync(BA_FULL_MASK, v, off);
     if (((lane - seg_start) & (2 * off - 1)) == 0 && lane + off < seg_end) v += o;
   }
@@ -54,6 +57,11 @@ __device__ __forceinline__ void segments(int key, int lane, int& seg_start, int&
   seg_start = 31 - __clz(heads & upto);
   const unsigned after = heads & ~upto;
   seg_end = after ? __ffs(after) - 1 : 32;
+}
+
+// longest segment of the warp
+__device__ __forceinline__ int segment_span(int seg_start, int seg_end) {
+  return (int)__reduce_max_sync(BA_FULL_MASK, (unsigned)(seg_end - seg_start));
 }
 
 template <typename Real>

@@ -20,10 +20,14 @@
 
 namespace bagpu {
 
-constexpr int kSrec = 35;         // per-observation shared record: Jc[12], r[2], Z[18], q[3]
-constexpr int kSrecR = 12;
-constexpr int kSrecZ = 14;
+constexpr int kSrec = 36;         // per-observation shared record: Jc[12], Z[18], r[2], q[3], pad
+constexpr int kSrecZ = 12;
+constexpr int kSrecR = 30;
 constexpr int kSrecQ = 32;
+#ifndef BA_LIN_SCHUR_MIN_BLOCKS
+#define BA_LIN_SCHUR_MIN_BLOCKS 2
+#endif
+constexpr int kLinSchurMinBlocksMixed = BA_LIN_SCHUR_MIN_BLOCKS;  // CTAs per SM the mixed linearise+Schur kernel is compiled for
 constexpr int kCamPart = 40;      // camera partial: A[21], gobs[6], Zq[6], Udiag[6], pad
 constexpr int kPairPart = 36;     // pair partial: sum Z_a Z_b^T (6x6 row-major)
 constexpr int kChunkTilesMixed = 16;  // tiles per chunk (two per warp), binary32 records
@@ -55,7 +59,7 @@ struct Chunk {
   int job_begin;            // its jobs: n_lc free cameras, then n_lp co-visible camera pairs
   int n_lc, n_lp;
   int mjob_begin, n_mjobs;  // its jobs spread over more than one lane (indices into its jobs)
-  int pad;
+  int pt_begin, n_pts;      // internal point range spanned by its observations
 };
 
 // One reduction job of a chunk: a free camera (items: its observations, as
@@ -88,8 +92,10 @@ struct LmState {
   int pt_fail;       // a damped point block was not positive definite this iteration
   float mu_f;        // mu rounded to binary32 (mixed-path kernels)
   int needs_init;    // F must be evaluated at the current state before the next iteration
-  int pad3;
+  int dev_error;     // a kernel gave up on a bounded wait this iteration (kDevErrTimeout); rejects the step
 };
+
+constexpr int kDevErrTimeout = -4;  // = BA_ERR_TIMEOUT
 
 // Same layout as ba_step_info.
 struct StepRec {

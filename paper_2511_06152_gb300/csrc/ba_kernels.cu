@@ -35,7 +35,10 @@
 #include <cuda_runtime.h>
 #include <stdio.h>
 
+#include <algorithm>
+
 #include "ba_device.cuh"
+#include "ba_bulk.cuh"
 #include "ba_dfloat.cuh"
 #include "ba_internal.h"
 
@@ -188,23 +191,46 @@ template <bool MIXED>
 struct TileLin {
   using Real = typename RealOf<MIXED>::T;
   bool act, head;
-  int o, k, j, seg_start, seg_end;
+  int o, k, j, seg_start, seg_end, span;
   Real Jc[12], r0, r1, Z[18];
   Real m00, m10, m11, m20, m21, m22, q0, q1, q2;
   Real d0, d1, d2, g0, g1, g2;
 };
 
-// Linearise one tile (one warp).  Identical arithmetic wherever it is called,
-// so the back-substitution reproduces the linearisation pass bit for bit.
+// Where the mixed linearisation reads a chunk's observations (camera, point,
+// observation relative to the principal point) and the current points:
+// the cluster's arrays in global memory, or a shared-memory copy of the
+// chunk's ranges (index o - o0, point j - j0).
+struct ObsView {
+  const int* cam;
+  const int* pt;
+  const float2* chi;
+  const float2* x;  // 3 float2 (hi, lo) per point
+  int o0, j0;
+};
+
+__device__ __forceinline__ ObsView global_view(const DevCluster& C, int cur) {
+  return ObsView{C.obs_cam, C.obs_pt, C.obs_chi, reinterpret_cast<const float2*>(C.X) + (size_t)cur * C.n_pts * 3,
+                 0, 0};
+}
+
+// Linearise one tile (one warp).  The same arithmetic wherever it is called
+// (the back-substitution linearises again rather than storing the result).
 template <bool MIXED>
 __device__ __forceinline__ void linearize_tile(const DevCluster& C, LmState* lm, const Tile& tl, int lane,
-                                               bool report_fail, TileLin<MIXED>& L) {
+                                               bool report_fail, TileLin<MIXED>& L, const ObsView& V) {
   using Real = typename RealOf<MIXED>::T;
   L.act = lane < tl.n_obs;
   L.o = tl.obs_begin + (L.act ? lane : 0);
-  L.k = L.act ? C.obs_cam[L.o] : 0;
-  L.j = L.act ? C.obs_pt[L.o] : -1 - lane;
+  if constexpr (MIXED) {
+    L.k = L.act ? V.cam[L.o - V.o0] : 0;
+    L.j = L.act ? V.pt[L.o - V.o0] : -1 - lane;
+  } else {
+    L.k = L.act ? C.obs_cam[L.o] : 0;
+    L.j = L.act ? C.obs_pt[L.o] : -1 - lane;
+  }
   segments(L.j, lane, L.seg_start, L.seg_end);
+  L.span = segment_span(L.seg_start, L.seg_end);
   L.head = L.act && lane == L.seg_start;
   const int cur = lm->cur;
   Real mu, inv_sigma, delta;
@@ -229,7 +255,7 @@ __device__ __forceinline__ void linearize_tile(const DevCluster& C, LmState* lm,
     bool is_free;
     if constexpr (MIXED) {
       const CamDf cd = load_camdf(camdf_ptr(C, cur, L.k));
-      const float2* xp = xdf_ptr(C, cur, L.j);
+      const float2* xp = V.x + (size_t)(L.j - V.j0) * 3;
       const float2 a = xp[0], b = xp[1], c = xp[2];
       dx = df_to_f(df_sub(dfl{a.x, a.y}, cd.T[0]));
       dy = df_to_f(df_sub(dfl{b.x, b.y}, cd.T[1]));
@@ -238,7 +264,7 @@ __device__ __forceinline__ void linearize_tile(const DevCluster& C, LmState* lm,
       for (int i = 0; i < 9; ++i) Rm[i] = cd.R[i].hi;
       in[0] = cd.f.hi; in[1] = 0.f; in[2] = 0.f;
       in[3] = cd.k1.hi; in[4] = cd.k2.hi; in[5] = cd.p1.hi; in[6] = cd.p2.hi;
-      const float2 ch = C.obs_chi[L.o];  // observation relative to the principal point
+      const float2 ch = V.chi[L.o - V.o0];  // observation relative to the principal point
       uo = ch.x; vo = ch.y;
       is_free = cd.free_flag != 0.0f;
     } else {
@@ -269,15 +295,15 @@ __device__ __forceinline__ void linearize_tile(const DevCluster& C, LmState* lm,
   Real g0 = -(Jp[0] * L.r0 + Jp[3] * L.r1);
   Real g1 = -(Jp[1] * L.r0 + Jp[4] * L.r1);
   Real g2 = -(Jp[2] * L.r0 + Jp[5] * L.r1);
-  v00 = seg_reduce(v00, lane, L.seg_start, L.seg_end);
-  v01 = seg_reduce(v01, lane, L.seg_start, L.seg_end);
-  v02 = seg_reduce(v02, lane, L.seg_start, L.seg_end);
-  v11 = seg_reduce(v11, lane, L.seg_start, L.seg_end);
-  v12 = seg_reduce(v12, lane, L.seg_start, L.seg_end);
-  v22 = seg_reduce(v22, lane, L.seg_start, L.seg_end);
-  g0 = seg_reduce(g0, lane, L.seg_start, L.seg_end);
-  g1 = seg_reduce(g1, lane, L.seg_start, L.seg_end);
-  g2 = seg_reduce(g2, lane, L.seg_start, L.seg_end);
+  v00 = seg_reduce(v00, lane, L.seg_start, L.seg_end, L.span);
+  v01 = seg_reduce(v01, lane, L.seg_start, L.seg_end, L.span);
+  v02 = seg_reduce(v02, lane, L.seg_start, L.seg_end, L.span);
+  v11 = seg_reduce(v11, lane, L.seg_start, L.seg_end, L.span);
+  v12 = seg_reduce(v12, lane, L.seg_start, L.seg_end, L.span);
+  v22 = seg_reduce(v22, lane, L.seg_start, L.seg_end, L.span);
+  g0 = seg_reduce(g0, lane, L.seg_start, L.seg_end, L.span);
+  g1 = seg_reduce(g1, lane, L.seg_start, L.seg_end, L.span);
+  g2 = seg_reduce(g2, lane, L.seg_start, L.seg_end, L.span);
   // head: damp, factor V* = L L^T, M = L^-1, q = M g_p
   Real m00 = 0, m10 = 0, m11 = 0, m20 = 0, m21 = 0, m22 = 0, q0 = 0, q1 = 0, q2 = 0;
   L.d0 = L.d1 = L.d2 = 0;
@@ -333,45 +359,273 @@ __device__ __forceinline__ void linearize_tile(const DevCluster& C, LmState* lm,
 
 // ------------------------------------------------------------------ K1: linearise + Schur reductions, one CTA per chunk
 
+// Shared record of one observation, kSrec = 36 Real, 16-byte aligned:
+// Jc [0, 12), Z [12, 30), r [30, 32), q [32, 35), one pad.
+__device__ __forceinline__ void ld_rec_jc(const float* r, float Jc[12]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float4 v = reinterpret_cast<const float4*>(r)[i];
+    Jc[4 * i] = v.x; Jc[4 * i + 1] = v.y; Jc[4 * i + 2] = v.z; Jc[4 * i + 3] = v.w;
+  }
+}
+__device__ __forceinline__ void ld_rec_jc(const double* r, double Jc[12]) {
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const double2 v = reinterpret_cast<const double2*>(r)[i];
+    Jc[2 * i] = v.x; Jc[2 * i + 1] = v.y;
+  }
+}
+// Z (18 values from offset kSrecZ = 12)
+__device__ __forceinline__ void ld_rec_z(const float* r, float Z[18]) {
+  const float4* q = reinterpret_cast<const float4*>(r + kSrecZ);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float4 v = q[i];
+    Z[4 * i] = v.x; Z[4 * i + 1] = v.y; Z[4 * i + 2] = v.z; Z[4 * i + 3] = v.w;
+  }
+  const float2 t = reinterpret_cast<const float2*>(r + kSrecZ + 16)[0];
+  Z[16] = t.x; Z[17] = t.y;
+}
+__device__ __forceinline__ void ld_rec_z(const double* r, double Z[18]) {
+  const double2* q = reinterpret_cast<const double2*>(r + kSrecZ);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const double2 v = q[i];
+    Z[2 * i] = v.x; Z[2 * i + 1] = v.y;
+  }
+}
+// r (2) and q (3)
+__device__ __forceinline__ void ld_rec_rq(const float* r, float& r0, float& r1, float& q0, float& q1, float& q2) {
+  const float2 a = reinterpret_cast<const float2*>(r + kSrecR)[0];
+  const float4 b = reinterpret_cast<const float4*>(r + kSrecQ)[0];
+  r0 = a.x; r1 = a.y; q0 = b.x; q1 = b.y; q2 = b.z;
+}
+__device__ __forceinline__ void ld_rec_rq(const double* r, double& r0, double& r1, double& q0, double& q1,
+                                          double& q2) {
+  const double2 a = reinterpret_cast<const double2*>(r + kSrecR)[0];
+  const double2 b = reinterpret_cast<const double2*>(r + kSrecQ)[0];
+  r0 = a.x; r1 = a.y; q0 = b.x; q1 = b.y; q2 = r[kSrecQ + 2];
+}
+
+// One job's sums over its items [i0, i1).  Image job: the upper triangle of
+// sum (Jc^T Jc - Z Z^T) (21), -sum Jc^T r (6), sum Z q (6), diag sum Jc^T Jc
+// (6).  Pair job: sum Z_a Z_b^T (36, row-major).
+template <typename Real>
+__device__ __forceinline__ void job_sums(const DevCluster& C, const Job& J, bool cam, int i0, int i1,
+                                         const Real* srec, Real acc[39]) {
+#pragma unroll
+  for (int i = 0; i < 39; ++i) acc[i] = 0;
+  if (cam) {
+    for (int e = i0; e < i1; ++e) {
+      const Real* r = srec + (size_t)C.cm_list[J.item_begin + e] * kSrec;
+      Real r0, r1, q0, q1, q2;
+      ld_rec_rq(r, r0, r1, q0, q1, q2);
+      {  // terms of Jc (fewer live registers than both blocks at once)
+        Real Jc[12];
+        ld_rec_jc(r, Jc);
+        int t = 0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+          for (int b = a; b < 6; ++b) acc[t++] += Jc[a] * Jc[b] + Jc[6 + a] * Jc[6 + b];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+          acc[21 + a] -= Jc[a] * r0 + Jc[6 + a] * r1;
+          acc[33 + a] += Jc[a] * Jc[a] + Jc[6 + a] * Jc[6 + a];
+        }
+      }
+      {  // terms of Z
+        Real Z[18];
+        ld_rec_z(r, Z);
+        int t = 0;
+#pragma unroll
+        for (int a = 0; a < 6; ++a)
+#pragma unroll
+          for (int b = a; b < 6; ++b)
+            acc[t++] -= Z[3 * a] * Z[3 * b] + Z[3 * a + 1] * Z[3 * b + 1] + Z[3 * a + 2] * Z[3 * b + 2];
+#pragma unroll
+        for (int a = 0; a < 6; ++a) acc[27 + a] += Z[3 * a] * q0 + Z[3 * a + 1] * q1 + Z[3 * a + 2] * q2;
+      }
+    }
+  } else {
+    for (int e = i0; e < i1; ++e) {
+      const unsigned int u = C.pent[J.item_begin + e];
+      Real Za[18], Zb[18];
+      ld_rec_z(srec + (size_t)(u & 0xffffu) * kSrec, Za);
+      ld_rec_z(srec + (size_t)(u >> 16) * kSrec, Zb);
+#pragma unroll
+      for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int b = 0; b < 6; ++b)
+          acc[6 * a + b] += Za[3 * a] * Zb[3 * b] + Za[3 * a + 1] * Zb[3 * b + 1] + Za[3 * a + 2] * Zb[3 * b + 2];
+    }
+  }
+}
+
+template <typename Real>
+__device__ __forceinline__ void store_job(const DevCluster& C, const Job& J, bool cam, const Real acc[39]) {
+  Real* out = cam ? (Real*)C.campart + (size_t)kCamPart * J.slot : (Real*)C.pairpart + (size_t)kPairPart * J.slot;
+  const int width = cam ? 39 : 36;
+#pragma unroll
+  for (int i = 0; i < 39; ++i)
+    if (i < width) out[i] = acc[i];
+}
+
+// bytes of the per-observation records (and, overlaid, the lane partials)
+__host__ __device__ constexpr size_t chunk_records_bytes(bool mixed) {
+  return (mixed ? sizeof(float) : sizeof(double)) *
+         ((size_t)(mixed ? kChunkObsMixed : kChunkObsF64) * kSrec > (size_t)kChunkThreads * kLanePart
+              ? (size_t)(mixed ? kChunkObsMixed : kChunkObsF64) * kSrec
+              : (size_t)kChunkThreads * kLanePart);
+}
+
+// Shared-memory staging of one chunk's observations and points (mixed path):
+// camera and point indices (int), observations relative to the principal
+// point (float2 hi), points (3 float2 each), each range rounded outward to
+// 16 bytes.  A chunk spanning more than kStagePts points reads its points
+// from global memory instead.
+constexpr int kStagePts = 512;
+constexpr uint32_t kStageIdxBytes = kChunkObsMixed * 4 + 32;
+constexpr uint32_t kStageChiBytes = kChunkObsMixed * 8 + 32;
+constexpr uint32_t kStageXBytes = kStagePts * 24 + 32;
+constexpr uint32_t kStageBytes = 2 * kStageIdxBytes + kStageChiBytes + kStageXBytes;
+constexpr uint64_t kCopyWaitNs = 200000000ull;  // give up on a staged copy after 200 ms
+
+struct Stage {
+  char* idx_cam;
+  char* idx_pt;
+  char* chi;
+  char* x;
+  uint64_t* bar;
+  int* ok;
+};
+
+// Issue the copies of chunk g (one thread).  Returns nothing; the barrier's
+// transaction count covers exactly the bytes issued.
+__device__ __forceinline__ void stage_issue(const BatchView& bv, int g, const Stage& S) {
+  const int s = find_slot(bv.chunk_pre, bv.n, g);
+  const DevCluster& C = bv.cl[s];
+  const Chunk ch = C.chunks[g - bv.chunk_pre[s]];
+  const BulkRange rc = bulk_range(C.obs_cam + ch.obs_begin, (size_t)ch.n_obs * 4);
+  const BulkRange rp = bulk_range(C.obs_pt + ch.obs_begin, (size_t)ch.n_obs * 4);
+  const BulkRange rh = bulk_range(C.obs_chi + ch.obs_begin, (size_t)ch.n_obs * 8);
+  const bool stage_x = ch.n_pts <= kStagePts;
+  const float2* xb = reinterpret_cast<const float2*>(C.X) + ((size_t)C.lm->cur * C.n_pts + ch.pt_begin) * 3;
+  const BulkRange rx = bulk_range(xb, stage_x ? (size_t)ch.n_pts * 24 : 0);
+  fence_proxy_async_smem();
+  mbar_arrive_expect_tx(S.bar, rc.bytes + rp.bytes + rh.bytes + (stage_x ? rx.bytes : 0u));
+  bulk_copy_g2s(S.idx_cam, rc.src, rc.bytes, S.bar);
+  bulk_copy_g2s(S.idx_pt, rp.src, rp.bytes, S.bar);
+  bulk_copy_g2s(S.chi, rh.src, rh.bytes, S.bar);
+  if (stage_x && rx.bytes) bulk_copy_g2s(S.x, rx.src, rx.bytes, S.bar);
+}
+
+// The view of the staged chunk (same rounding as stage_issue).
+__device__ __forceinline__ ObsView stage_view(const DevCluster& C, const Chunk& ch, int cur, const Stage& S) {
+  ObsView V;
+  V.cam = reinterpret_cast<const int*>(S.idx_cam + bulk_range(C.obs_cam + ch.obs_begin, 4).lead);
+  V.pt = reinterpret_cast<const int*>(S.idx_pt + bulk_range(C.obs_pt + ch.obs_begin, 4).lead);
+  V.chi = reinterpret_cast<const float2*>(S.chi + bulk_range(C.obs_chi + ch.obs_begin, 8).lead);
+  V.o0 = ch.obs_begin;
+  const float2* xb = reinterpret_cast<const float2*>(C.X) + ((size_t)cur * C.n_pts + ch.pt_begin) * 3;
+  if (ch.n_pts <= kStagePts) {
+    V.x = reinterpret_cast<const float2*>(S.x + bulk_range(xb, 24).lead);
+    V.j0 = ch.pt_begin;
+  } else {
+    V.x = reinterpret_cast<const float2*>(C.X) + (size_t)cur * C.n_pts * 3;
+    V.j0 = 0;
+  }
+  return V;
+}
+
 template <bool MIXED>
-__global__ void __launch_bounds__(kChunkThreads) k_lin_schur(BatchView bv, int diag) {
+__global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed : 1)
+    k_lin_schur(BatchView bv, int diag) {
   using Real = typename RealOf<MIXED>::T;
   extern __shared__ __align__(16) unsigned char smraw[];
-  Real* srec = reinterpret_cast<Real*>(smraw);                        // [chunk_obs][kSrec]
-  Real* lanepart = srec + (size_t)(MIXED ? kChunkObsMixed : kChunkObsF64) * kSrec;  // [threads][kLanePart]
+  // [chunk_obs][kSrec] records; once every job has read them, the same
+  // memory holds the lane partials of multi-lane jobs ([threads][kLanePart])
+  Real* srec = reinterpret_cast<Real*>(smraw);
+  Real* lanepart = srec;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int total = bv.tot[1];
+  // mixed path: the next chunk's observations and points are copied into
+  // shared memory by the copy engine while this chunk is reduced
+  Stage S{};
+  uint32_t phase = 0;
+  if constexpr (MIXED) {
+    char* st = reinterpret_cast<char*>(smraw) + chunk_records_bytes(true);
+    S.idx_cam = st;
+    S.idx_pt = st + kStageIdxBytes;
+    S.chi = st + 2 * kStageIdxBytes;
+    S.x = st + 2 * kStageIdxBytes + kStageChiBytes;
+    S.bar = reinterpret_cast<uint64_t*>(st + kStageBytes);
+    S.ok = reinterpret_cast<int*>(st + kStageBytes + 8);
+    if (threadIdx.x == 0) {
+      mbar_init(S.bar, 1);
+      fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && (int)blockIdx.x < total) stage_issue(bv, blockIdx.x, S);
+  }
   for (int g = blockIdx.x; g < total; g += gridDim.x) {
     const int s = find_slot(bv.chunk_pre, bv.n, g);
     const DevCluster& C = bv.cl[s];
     LmState* lm = C.lm;
-    if (!lm->active) continue;
     const Chunk ch = C.chunks[g - bv.chunk_pre[s]];
-    // 1. linearise the chunk's tiles into shared memory
-    for (int t = warp; t < ch.n_tiles; t += nw) {
-      const Tile tl = C.tiles[ch.tile_begin + t];
-      TileLin<MIXED> L;
-      linearize_tile<MIXED>(C, lm, tl, lane, true, L);
-      if (L.act) {
-        Real* r = srec + (size_t)(L.o - ch.obs_begin) * kSrec;
-#pragma unroll
-        for (int i = 0; i < 12; ++i) r[i] = L.Jc[i];
-        r[kSrecR] = L.r0;
-        r[kSrecR + 1] = L.r1;
-#pragma unroll
-        for (int i = 0; i < 18; ++i) r[kSrecZ + i] = L.Z[i];
-        r[kSrecQ] = L.q0;
-        r[kSrecQ + 1] = L.q1;
-        r[kSrecQ + 2] = L.q2;
+    ObsView V{};
+    if constexpr (MIXED) {
+      if (threadIdx.x == 0) *S.ok = mbar_wait_bounded(S.bar, phase, kCopyWaitNs) ? 1 : 0;
+      __syncthreads();
+      phase ^= 1u;
+      if (!*S.ok) {
+        // the copy did not complete in time: flag every cluster whose chunks
+        // this CTA has still to process (their steps are rejected), wait once
+        // more for the copies in flight, and stop
+        if (threadIdx.x == 0) {
+          for (int h = g; h < total; h += gridDim.x) {
+            LmState* hl = bv.cl[find_slot(bv.chunk_pre, bv.n, h)].lm;
+            hl->dev_error = kDevErrTimeout;
+            hl->pt_fail = 1;
+          }
+          mbar_wait_bounded(S.bar, phase ^ 1u, kCopyWaitNs);
+        }
+        return;
       }
-      if (diag) {  // largest |g_p| of the tile, for the gradient norm
-        double gm = L.head ? fmax(fabs((double)L.g0), fmax(fabs((double)L.g1), fabs((double)L.g2))) : 0.0;
+      V = stage_view(C, ch, lm->cur, S);
+    }
+    const bool active = lm->active != 0;
+    // 1. linearise the chunk's tiles into shared memory
+    if (active) {
+      for (int t = warp; t < ch.n_tiles; t += nw) {
+        const Tile tl = C.tiles[ch.tile_begin + t];
+        TileLin<MIXED> L;
+        linearize_tile<MIXED>(C, lm, tl, lane, true, L, V);
+        if (L.act) {
+          Real* r = srec + (size_t)(L.o - ch.obs_begin) * kSrec;
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) gm = fmax(gm, __shfl_down_sync(BA_FULL_MASK, gm, off));
-        if (lane == 0) C.tilepart[2 * (ch.tile_begin + t) + 1] = gm;
+          for (int i = 0; i < 12; ++i) r[i] = L.Jc[i];
+#pragma unroll
+          for (int i = 0; i < 18; ++i) r[kSrecZ + i] = L.Z[i];
+          r[kSrecR] = L.r0;
+          r[kSrecR + 1] = L.r1;
+          r[kSrecQ] = L.q0;
+          r[kSrecQ + 1] = L.q1;
+          r[kSrecQ + 2] = L.q2;
+        }
+        if (diag) {  // largest |g_p| of the tile, for the gradient norm
+          double gm = L.head ? fmax(fabs((double)L.g0), fmax(fabs((double)L.g1), fabs((double)L.g2))) : 0.0;
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) gm = fmax(gm, __shfl_down_sync(BA_FULL_MASK, gm, off));
+          if (lane == 0) C.tilepart[2 * (ch.tile_begin + t) + 1] = gm;
+        }
       }
     }
     __syncthreads();
+    if constexpr (MIXED) {  // staging is free: start the copies of this CTA's next chunk
+      if (threadIdx.x == 0 && g + (int)gridDim.x < total) stage_issue(bv, g + gridDim.x, S);
+    }
+    if (!active) continue;
     // 2. Schur reductions of the chunk.  Jobs: each free camera (sum of
     //    Jc^T Jc - Z Z^T, -Jc^T r, Z q, diag(Jc^T Jc) over its observations) and
     //    each co-visible camera pair (sum of Z_a Z_b^T over its point pairs).
@@ -380,103 +634,50 @@ __global__ void __launch_bounds__(kChunkThreads) k_lin_schur(BatchView bv, int d
     //    lanes' partial sums are added in lane order.  A chunk with more jobs
     //    than threads runs one lane per job.
     const int n_jobs = ch.n_lc + ch.n_lp;  // 0 when every observation of the chunk is of a fixed camera
-    const bool spread = n_jobs > 0 && n_jobs <= (int)blockDim.x;
-    for (int base = 0; base < (spread ? 1 : n_jobs); base += blockDim.x) {
-      int jb = -1, part = 0, n_parts = 1;
-      if (spread) {
-        // job whose lane run holds this thread (jobs are in lane order)
-        int lo = 0, hi = n_jobs - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (C.jobs[ch.job_begin + mid].lane_begin <= (int)threadIdx.x) lo = mid; else hi = mid - 1;
-        }
-        const Job J = C.jobs[ch.job_begin + lo];
-        if ((int)threadIdx.x < J.lane_begin + J.n_lanes) {
-          jb = lo;
-          part = threadIdx.x - J.lane_begin;
-          n_parts = J.n_lanes;
-        }
-      } else if (base + (int)threadIdx.x < n_jobs) {
-        jb = base + threadIdx.x;
+    if (n_jobs > 0 && n_jobs <= (int)blockDim.x) {
+      // job whose lane run holds this thread (jobs are in lane order)
+      int lo = 0, hi = n_jobs - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (C.jobs[ch.job_begin + mid].lane_begin <= (int)threadIdx.x) lo = mid; else hi = mid - 1;
       }
-      if (jb >= 0) {
-        const Job J = C.jobs[ch.job_begin + jb];
-        const int i0 = (int)(((long long)J.count * part) / n_parts);
-        const int i1 = (int)(((long long)J.count * (part + 1)) / n_parts);
-        Real acc[39];
-#pragma unroll
-        for (int i = 0; i < 39; ++i) acc[i] = 0;
-        const bool cam = jb < ch.n_lc;
-        if (cam) {
-          for (int e = i0; e < i1; ++e) {
-            const Real* r = srec + (size_t)C.cm_list[J.item_begin + e] * kSrec;
-            Real Jc[12], Z[18];
-#pragma unroll
-            for (int i = 0; i < 12; ++i) Jc[i] = r[i];
-#pragma unroll
-            for (int i = 0; i < 18; ++i) Z[i] = r[kSrecZ + i];
-            const Real r0 = r[kSrecR], r1 = r[kSrecR + 1];
-            const Real q0 = r[kSrecQ], q1 = r[kSrecQ + 1], q2 = r[kSrecQ + 2];
-            int t = 0;
-#pragma unroll
-            for (int a = 0; a < 6; ++a) {
-#pragma unroll
-              for (int b = a; b < 6; ++b) {
-                acc[t++] += Jc[a] * Jc[b] + Jc[6 + a] * Jc[6 + b] -
-                            (Z[3 * a] * Z[3 * b] + Z[3 * a + 1] * Z[3 * b + 1] + Z[3 * a + 2] * Z[3 * b + 2]);
-              }
-            }
-#pragma unroll
-            for (int a = 0; a < 6; ++a) {
-              acc[21 + a] -= Jc[a] * r0 + Jc[6 + a] * r1;
-              acc[27 + a] += Z[3 * a] * q0 + Z[3 * a + 1] * q1 + Z[3 * a + 2] * q2;
-              acc[33 + a] += Jc[a] * Jc[a] + Jc[6 + a] * Jc[6 + a];
-            }
-          }
-        } else {
-          for (int e = i0; e < i1; ++e) {
-            const unsigned int u = C.pent[J.item_begin + e];
-            const Real* za = srec + (size_t)(u & 0xffffu) * kSrec + kSrecZ;
-            const Real* zb = srec + (size_t)(u >> 16) * kSrec + kSrecZ;
-            Real Za[18], Zb[18];
-#pragma unroll
-            for (int i = 0; i < 18; ++i) {
-              Za[i] = za[i];
-              Zb[i] = zb[i];
-            }
-#pragma unroll
-            for (int a = 0; a < 6; ++a)
-#pragma unroll
-              for (int b = 0; b < 6; ++b)
-                acc[6 * a + b] += Za[3 * a] * Zb[3 * b] + Za[3 * a + 1] * Zb[3 * b + 1] + Za[3 * a + 2] * Zb[3 * b + 2];
-          }
-        }
-        const int width = cam ? 39 : 36;
-        if (n_parts == 1) {
-          Real* out = cam ? (Real*)C.campart + (size_t)kCamPart * J.slot : (Real*)C.pairpart + (size_t)kPairPart * J.slot;
-#pragma unroll
-          for (int i = 0; i < 39; ++i)
-            if (i < width) out[i] = acc[i];
-        } else {
-          Real* lp = lanepart + (size_t)threadIdx.x * kLanePart;
-#pragma unroll
-          for (int i = 0; i < 39; ++i) lp[i] = acc[i];
-        }
+      const Job J = C.jobs[ch.job_begin + lo];
+      const bool mine = (int)threadIdx.x < J.lane_begin + J.n_lanes;
+      const int part = threadIdx.x - J.lane_begin;
+      const bool cam = lo < ch.n_lc;
+      Real acc[39];
+      if (mine) {
+        const int i0 = (int)(((long long)J.count * part) / J.n_lanes);
+        const int i1 = (int)(((long long)J.count * (part + 1)) / J.n_lanes);
+        job_sums<Real>(C, J, cam, i0, i1, srec, acc);
+        if (J.n_lanes == 1) store_job<Real>(C, J, cam, acc);
       }
-    }
-    if (spread) {
+      __syncthreads();  // every record has been read: the lane partials may overwrite them
+      if (mine && J.n_lanes > 1) {
+        Real* lp = lanepart + (size_t)threadIdx.x * kLanePart;
+#pragma unroll
+        for (int i = 0; i < 39; ++i) lp[i] = acc[i];
+      }
       __syncthreads();
       // multi-lane jobs: element e of job j = sum over its lanes, in lane order
       for (int u = threadIdx.x; u < ch.n_mjobs * kLanePart; u += blockDim.x) {
         const int mj = u / kLanePart, e = u - mj * kLanePart;
         const int jb = C.mjobs[ch.mjob_begin + mj];
-        const bool cam = jb < ch.n_lc;
-        if (e >= (cam ? 39 : 36)) continue;
-        const Job J = C.jobs[ch.job_begin + jb];
+        const bool mcam = jb < ch.n_lc;
+        if (e >= (mcam ? 39 : 36)) continue;
+        const Job M = C.jobs[ch.job_begin + jb];
         Real v = 0;
-        for (int l = J.lane_begin; l < J.lane_begin + J.n_lanes; ++l) v += lanepart[(size_t)l * kLanePart + e];
-        Real* out = cam ? (Real*)C.campart + (size_t)kCamPart * J.slot : (Real*)C.pairpart + (size_t)kPairPart * J.slot;
+        for (int l = M.lane_begin; l < M.lane_begin + M.n_lanes; ++l) v += lanepart[(size_t)l * kLanePart + e];
+        Real* out = mcam ? (Real*)C.campart + (size_t)kCamPart * M.slot : (Real*)C.pairpart + (size_t)kPairPart * M.slot;
         out[e] = v;
+      }
+    } else {
+      for (int jb = threadIdx.x; jb < n_jobs; jb += blockDim.x) {
+        const Job J = C.jobs[ch.job_begin + jb];
+        const bool cam = jb < ch.n_lc;
+        Real acc[39];
+        job_sums<Real>(C, J, cam, 0, J.count, srec, acc);
+        store_job<Real>(C, J, cam, acc);
       }
     }
     __syncthreads();
@@ -801,7 +1002,8 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
       for (int f = 0; f < nf; ++f) { pc += t[2 * f]; pn += t[2 * f + 1]; }
       lm->pred_cam = pc;
       lm->prior_new = pn;
-      lm->status = status;
+      lm->status = lm->dev_error ? lm->dev_error : status;
+      lm->dev_error = 0;
     }
     __syncthreads();
   }
@@ -827,7 +1029,7 @@ __global__ void __launch_bounds__(256) k_backsub_cost(BatchView bv) {
     const int local = g - bv.tile_pre[s];
     const Tile tl = C.tiles[local];
     TileLin<MIXED> L;
-    linearize_tile<MIXED>(C, lm, tl, lane, false, L);
+    linearize_tile<MIXED>(C, lm, tl, lane, false, L, global_view(C, lm->cur));
     const int cur = lm->cur;
     Real mu_r;
     if constexpr (MIXED) mu_r = lm->mu_f; else mu_r = lm->mu;
@@ -851,9 +1053,9 @@ __global__ void __launch_bounds__(256) k_backsub_cost(BatchView bv) {
         t2 += L.Z[3 * m + 2] * d[m];
       }
     }
-    t0 = seg_reduce(t0, lane, L.seg_start, L.seg_end);
-    t1 = seg_reduce(t1, lane, L.seg_start, L.seg_end);
-    t2 = seg_reduce(t2, lane, L.seg_start, L.seg_end);
+    t0 = seg_reduce(t0, lane, L.seg_start, L.seg_end, L.span);
+    t1 = seg_reduce(t1, lane, L.seg_start, L.seg_end, L.span);
+    t2 = seg_reduce(t2, lane, L.seg_start, L.seg_end, L.span);
     // head: dX = M^T (q - t), candidate point, pred term
     Real dX0 = 0, dX1 = 0, dX2 = 0;
     Real pp = 0;  // dX^T (mu Dp dX + gp)
@@ -1243,6 +1445,7 @@ __global__ void k_reset(BatchView bv) {
         lm->active = 0;
         lm->iters_target = 0;
         lm->pt_fail = 0;
+        lm->dev_error = 0;
       }
     }
   }
@@ -1384,7 +1587,9 @@ int chunk_obs(bool mixed) { return mixed ? kChunkObsMixed : kChunkObsF64; }
 int chunk_tiles(bool mixed) { return mixed ? kChunkTilesMixed : kChunkTilesF64; }
 
 static size_t chunk_smem_bytes(bool mixed) {
-  return ((size_t)chunk_obs(mixed) * kSrec + (size_t)kChunkThreads * kLanePart) * (mixed ? sizeof(float) : sizeof(double));
+  // records (later overlaid by the lane partials); mixed path: the chunk
+  // staging, its barrier and a flag
+  return chunk_records_bytes(mixed) + (mixed ? (size_t)kStageBytes + 16 : 0);
 }
 
 template <bool MIXED>
