@@ -738,46 +738,46 @@ __device__ __forceinline__ int pk(int i, int j) { return (i * (i + 1)) / 2 + j; 
 
 size_t factor_smem_bytes(int max_n) {
   const int nf = max_n / 6;
-  const size_t doubles = (size_t)max_n * (max_n + 1) / 2 + (size_t)nf * 40 + (size_t)nf * 42 + 3 * (size_t)max_n + 64;
+  const size_t doubles = (size_t)max_n * (max_n + 1) / 2 + (size_t)nf * 40 + (size_t)nf * 42 + 4 * (size_t)max_n + 64;
   return doubles * sizeof(double);
 }
 
-constexpr int kFactorNB = 8;  // panel width of the blocked factorisation and solves
+constexpr int kFactorNB = 8;  // panel width of the blocked factorisation
 
 // Blocked right-looking Cholesky A = L L^T of the packed lower matrix in
-// shared memory, by the whole CTA.  Per panel of kFactorNB columns: factor
-// the panel (column by column over all rows below), then update the trailing
-// matrix with the panel in 4x4 register tiles.  colbuf: shared scratch [n].
-// Sets *fail (shared) when a pivot is not positive.
-__device__ void chol_blocked(double* A, int n, double* colbuf, int* fail) {
-  const int tid = threadIdx.x, bs = blockDim.x;
+// shared memory.  Per panel of kFactorNB columns: warp 0 factors the panel
+// (every row below it, column by column, synchronising only the warp), then
+// the whole CTA updates the trailing matrix with the panel in 4x4 register
+// tiles.  inv_diag[j] = 1 / L(j, j) (shared, [n]) is computed once per pivot
+// and reused by the solves.  Sets *fail (shared) when a pivot is not
+// positive.  Two CTA barriers per panel.
+__device__ void chol_blocked(double* A, int n, double* inv_diag, int* fail) {
+  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31;
   for (int k0 = 0; k0 < n; k0 += kFactorNB) {
     const int k1 = min(k0 + kFactorNB, n);
-    for (int j = k0; j < k1; ++j) {
-      if (tid == 0) {
-        const double d = A[pk(j, j)];
-        if (!(d > 0.0)) *fail = 1;
-        A[pk(j, j)] = sqrt(d > 0.0 ? d : 1.0);
-      }
-      __syncthreads();
-      if (*fail) return;
-      const double inv = 1.0 / A[pk(j, j)];
-      for (int i = j + 1 + tid; i < n; i += bs) {
-        const double l = A[pk(i, j)] * inv;
-        A[pk(i, j)] = l;
-        colbuf[i] = l;
-      }
-      __syncthreads();
-      const int w = k1 - j - 1;  // remaining panel columns
-      if (w > 0) {
-        const int rows = n - j - 1;
-        for (int u = tid; u < rows * w; u += bs) {
-          const int i = j + 1 + u / w, c = j + 1 + u % w;
-          if (c <= i) A[pk(i, c)] -= colbuf[i] * colbuf[c];
+    if (tid < 32) {
+      for (int j = k0; j < k1; ++j) {
+        if (lane == 0) {
+          const double d = A[pk(j, j)];
+          if (!(d > 0.0)) *fail = 1;
+          const double r = sqrt(d > 0.0 ? d : 1.0);
+          A[pk(j, j)] = r;
+          inv_diag[j] = 1.0 / r;
         }
-        __syncthreads();
+        __syncwarp();
+        const double inv = inv_diag[j];
+        for (int i = j + 1 + lane; i < n; i += 32) A[pk(i, j)] *= inv;
+        __syncwarp();
+        // the panel's remaining columns c in (j, k1), rows i >= c
+        for (int c = j + 1; c < k1; ++c) {
+          const double lc = A[pk(c, j)];
+          for (int i = c + lane; i < n; i += 32) A[pk(i, c)] -= A[pk(i, j)] * lc;
+        }
+        __syncwarp();
       }
     }
+    __syncthreads();
+    if (*fail) return;
     const int m = n - k1;  // trailing matrix rows/cols k1..n-1
     if (m > 0) {
       const int nt = (m + 3) >> 2;
@@ -818,44 +818,23 @@ __device__ void chol_blocked(double* A, int n, double* colbuf, int* fail) {
   }
 }
 
-// Solve L L^T x = b in place (b in shared memory), by the whole CTA: per
-// panel, one thread solves the small diagonal triangle and all threads update
-// the rest of the vector with the panel.
-__device__ void chol_solve_blocked(const double* A, double* b, int n) {
-  const int tid = threadIdx.x, bs = blockDim.x;
-  for (int k0 = 0; k0 < n; k0 += kFactorNB) {  // L y = b
-    const int k1 = min(k0 + kFactorNB, n);
-    if (tid == 0) {
-      for (int j = k0; j < k1; ++j) {
-        double s = b[j];
-        for (int q = k0; q < j; ++q) s -= A[pk(j, q)] * b[q];
-        b[j] = s / A[pk(j, j)];
-      }
-    }
-    __syncthreads();
-    for (int i = k1 + tid; i < n; i += bs) {
-      double s = 0.0;
-      for (int q = k0; q < k1; ++q) s += A[pk(i, q)] * b[q];
-      b[i] -= s;
-    }
-    __syncthreads();
+// Solve L L^T x = b in place (b in shared memory) by one warp (call from
+// all lanes of warp 0 only): column sweeps, lane l owning rows l, l+32, ...
+__device__ void chol_solve_warp(const double* A, const double* inv_diag, double* b, int n) {
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < n; ++j) {  // L y = b
+    if (lane == (j & 31)) b[j] *= inv_diag[j];
+    __syncwarp();
+    const double y = b[j];
+    for (int i = j + 1 + lane; i < n; i += 32) b[i] -= A[pk(i, j)] * y;
+    __syncwarp();
   }
-  for (int k1 = n; k1 > 0; k1 -= kFactorNB) {  // L^T x = y
-    const int k0 = max(k1 - kFactorNB, 0);
-    if (tid == 0) {
-      for (int j = k1 - 1; j >= k0; --j) {
-        double s = b[j];
-        for (int q = j + 1; q < k1; ++q) s -= A[pk(q, j)] * b[q];
-        b[j] = s / A[pk(j, j)];
-      }
-    }
-    __syncthreads();
-    for (int i = tid; i < k0; i += bs) {
-      double s = 0.0;
-      for (int q = k0; q < k1; ++q) s += A[pk(q, i)] * b[q];
-      b[i] -= s;
-    }
-    __syncthreads();
+  for (int j = n - 1; j >= 0; --j) {  // L^T x = y
+    if (lane == (j & 31)) b[j] *= inv_diag[j];
+    __syncwarp();
+    const double xj = b[j];
+    for (int i = lane; i < j; i += 32) b[i] -= A[pk(j, i)] * xj;
+    __syncwarp();
   }
 }
 
@@ -879,6 +858,7 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
     double* x = pr + (size_t)nf * 42;          // [n]
     double* b = x + n;                         // [n]
     double* t = b + n;                         // [n]
+    double* inv_diag = t + n;                  // [n]
     const double* Rc = C.R + (size_t)cur * nc * 9;
     const double* Tc = C.T + (size_t)cur * nc * 3;
 
@@ -937,11 +917,12 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
     }
     __syncthreads();  // the copy of S above reads A
     // blocked right-looking Cholesky in shared memory (t[] is the column buffer)
-    if (!fail) chol_blocked(A, n, t, &fail);
+    if (!fail) chol_blocked(A, n, inv_diag, &fail);
     __syncthreads();
     const int status = fail ? BA_STATUS_NOT_PD : 0;
     if (!fail) {
-      chol_solve_blocked(A, b, n);
+      if (tid < 32) chol_solve_warp(A, inv_diag, b, n);
+      __syncthreads();
       for (int idx = tid; idx < n; idx += bs) x[idx] = b[idx];
       __syncthreads();
       // iterative refinement against the FP64 system kept in global memory
@@ -954,7 +935,8 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
           if (lane == 0) t[r] = C.rhs[r] - acc;
         }
         __syncthreads();
-        chol_solve_blocked(A, t, n);
+        if (tid < 32) chol_solve_warp(A, inv_diag, t, n);
+        __syncthreads();
         for (int idx = tid; idx < n; idx += bs) x[idx] += t[idx];
         __syncthreads();
       }
