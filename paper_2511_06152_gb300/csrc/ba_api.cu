@@ -679,6 +679,48 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   }
   pair_slot_begin[n_pairs] = (int)pair_slots.size();
 
+  // Elimination order of the reduced camera system: reverse Cuthill-McKee
+  // (Cuthill & McKee 1969; George 1971) on the co-visibility graph of the
+  // free images, which keeps the envelope of S, and with it the fill of its
+  // Cholesky factor, narrow for images along strips.  The envelope of each
+  // block row starts at its first co-visible block in that order.
+  std::vector<int> fpos(nf), env_first(nf);
+  {
+    std::vector<std::vector<int>> adj(nf);
+    for (const int2& k : pair_key) {
+      adj[k.x].push_back(k.y);
+      adj[k.y].push_back(k.x);
+    }
+    for (auto& v : adj) std::sort(v.begin(), v.end(), [&](int a, int b) {
+      return adj[a].size() != adj[b].size() ? adj[a].size() < adj[b].size() : a < b;
+    });
+    std::vector<int> order;
+    std::vector<char> seen(nf, 0);
+    while ((int)order.size() < nf) {  // one BFS per connected component, from a least-connected image
+      int start = -1;
+      for (int f = 0; f < nf; ++f)
+        if (!seen[f] && (start < 0 || adj[f].size() < adj[start].size())) start = f;
+      seen[start] = 1;
+      size_t head = order.size();
+      order.push_back(start);
+      while (head < order.size()) {
+        const int u = order[head++];
+        for (int v : adj[u])
+          if (!seen[v]) {
+            seen[v] = 1;
+            order.push_back(v);
+          }
+      }
+    }
+    std::reverse(order.begin(), order.end());
+    for (int p = 0; p < nf; ++p) fpos[order[p]] = p;
+    for (int f = 0; f < nf; ++f) {
+      int first = fpos[f];
+      for (int g : adj[f]) first = std::min(first, fpos[g]);
+      env_first[fpos[f]] = first;
+    }
+  }
+
   // arena layout: static (uploaded) part first
   const size_t rs = mixed ? sizeof(float) : sizeof(double);
   const int n = 6 * nf;
@@ -695,6 +737,8 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const size_t o_perm = Lo.add(sizeof(int) * (size_t)np);
   const size_t o_free = Lo.add(sizeof(int) * nc);
   const size_t o_cof = Lo.add(sizeof(int) * nf);
+  const size_t o_fpos = Lo.add(sizeof(int) * nf);
+  const size_t o_envf = Lo.add(sizeof(int) * nf);
   const size_t o_tiles = Lo.add(sizeof(Tile) * tiles.size());
   const size_t o_ocam = Lo.add(sizeof(int) * (size_t)no);
   const size_t o_opt = Lo.add(sizeof(int) * (size_t)no);
@@ -764,6 +808,8 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   put(o_perm, perm.data(), sizeof(int) * perm.size());
   put(o_free, free_idx.data(), sizeof(int) * nc);
   put(o_cof, cam_of_free.data(), sizeof(int) * nf);
+  put(o_fpos, fpos.data(), sizeof(int) * nf);
+  put(o_envf, env_first.data(), sizeof(int) * nf);
   put(o_tiles, tiles.data(), sizeof(Tile) * tiles.size());
   put(o_ocam, pcam.data(), sizeof(int) * (size_t)no);
   put(o_opt, ppt.data(), sizeof(int) * (size_t)no);
@@ -861,6 +907,8 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   h.pt_perm = (const int*)(arena + o_perm);
   h.free_idx = (const int*)(arena + o_free);
   h.cam_of_free = (const int*)(arena + o_cof);
+  h.fpos = (const int*)(arena + o_fpos);
+  h.env_first = (const int*)(arena + o_envf);
   h.camreal = mixed ? nullptr : arena + o_camreal;
   h.camdf = mixed ? (float*)(arena + o_camdf) : nullptr;
   h.tiles = (const Tile*)(arena + o_tiles);

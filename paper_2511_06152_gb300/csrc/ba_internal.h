@@ -124,6 +124,11 @@ struct DevCluster {
   const int* pt_perm;      // [np] internal point -> caller's point index
   const int* free_idx;     // [nc] -> free index or -1
   const int* cam_of_free;  // [nf]
+  // elimination order of the reduced camera system: free image f sits at
+  // block position fpos[f]; env_first[p] = first block column of block row
+  // p inside the envelope of S (and of its Cholesky factor)
+  const int* fpos;         // [nf]
+  const int* env_first;    // [nf]
   void* camreal;           // FP64 path: double [nc][20]: R[9], T[3], intr[7], free flag
   float* camdf;            // mixed path: [2][nc][kCamDf] double-float cameras
 

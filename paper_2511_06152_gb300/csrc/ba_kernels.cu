@@ -738,45 +738,59 @@ __device__ __forceinline__ int pk(int i, int j) { return (i * (i + 1)) / 2 + j; 
 
 size_t factor_smem_bytes(int max_n) {
   const int nf = max_n / 6;
-  const size_t doubles = (size_t)max_n * (max_n + 1) / 2 + (size_t)nf * 40 + (size_t)nf * 42 + 4 * (size_t)max_n + 64;
+  const size_t doubles = (size_t)max_n * (max_n + 1) / 2 + (size_t)nf * 40 + (size_t)nf * 42 + 5 * (size_t)max_n + 64;
   return doubles * sizeof(double);
 }
 
-constexpr int kFactorNB = 8;  // panel width of the blocked factorisation
+#ifndef BA_FACTOR_NB
+#define BA_FACTOR_NB 8
+#endif
+constexpr int kFactorNB = BA_FACTOR_NB;  // panel width of the blocked factorisation
+constexpr int kSolveNB = 32;   // diagonal block of the triangular solves (one warp)
 
 // Blocked right-looking Cholesky A = L L^T of the packed lower matrix in
-// shared memory.  Per panel of kFactorNB columns: warp 0 factors the panel
-// (every row below it, column by column, synchronising only the warp), then
-// the whole CTA updates the trailing matrix with the panel in 4x4 register
-// tiles.  inv_diag[j] = 1 / L(j, j) (shared, [n]) is computed once per pivot
-// and reused by the solves.  Sets *fail (shared) when a pivot is not
-// positive.  Two CTA barriers per panel.
-__device__ void chol_blocked(double* A, int n, double* inv_diag, int* fail) {
-  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31;
+// shared memory, by the whole CTA.  Per column j of a panel of kFactorNB
+// columns: warp 0 takes the pivot (square root and its reciprocal, once) and
+// the scaled entries of the panel's own rows; then every thread scales its
+// rows of column j and updates the panel's remaining columns.  After the
+// panel the trailing matrix is updated with it in 4x4 register tiles.
+// inv_diag[j] = 1 / L(j, j) is kept for the solves; colbuf: shared [n].
+// efirst[i]: first column of row i inside the envelope of A.  The factor has
+// no fill outside the envelope, so every product with an entry left of it
+// is zero and is skipped (the sums are unchanged).
+// Sets *fail (shared) when a pivot is not positive.
+__device__ void chol_blocked(double* A, int n, double* inv_diag, double* colbuf, const int* efirst, int* fail) {
+  const int tid = threadIdx.x, bs = blockDim.x;
   for (int k0 = 0; k0 < n; k0 += kFactorNB) {
     const int k1 = min(k0 + kFactorNB, n);
-    if (tid < 32) {
-      for (int j = k0; j < k1; ++j) {
+    for (int j = k0; j < k1; ++j) {
+      if (tid < 32) {
+        const int lane = tid;
+        double inv = 0.0;
         if (lane == 0) {
           const double d = A[pk(j, j)];
           if (!(d > 0.0)) *fail = 1;
-          const double r = sqrt(d > 0.0 ? d : 1.0);
+          inv = rsqrt(d > 0.0 ? d : 1.0);  // one reciprocal square root per pivot
+          const double r = (d > 0.0 ? d : 1.0) * inv;
           A[pk(j, j)] = r;
-          inv_diag[j] = 1.0 / r;
+          inv_diag[j] = inv;
         }
-        __syncwarp();
-        const double inv = inv_diag[j];
-        for (int i = j + 1 + lane; i < n; i += 32) A[pk(i, j)] *= inv;
-        __syncwarp();
-        // the panel's remaining columns c in (j, k1), rows i >= c
-        for (int c = j + 1; c < k1; ++c) {
-          const double lc = A[pk(c, j)];
-          for (int i = c + lane; i < n; i += 32) A[pk(i, c)] -= A[pk(i, j)] * lc;
-        }
-        __syncwarp();
+        inv = __shfl_sync(BA_FULL_MASK, inv, 0);
+        if (j + 1 + lane < k1) colbuf[j + 1 + lane] = A[pk(j + 1 + lane, j)] * inv;
       }
+      __syncthreads();
+      const double inv = inv_diag[j];
+      const int w = k1 - j - 1;  // the panel's remaining columns j+1 .. k1-1
+      for (int i = j + 1 + tid; i < n; i += bs) {
+        if (efirst[i] > j) continue;  // L(i, j) = 0
+        const double l = A[pk(i, j)] * inv;
+        A[pk(i, j)] = l;
+        const int cmax = min(i, k1 - 1);
+        for (int c = j + 1; c <= cmax; ++c) A[pk(i, c)] -= l * colbuf[c];
+      }
+      (void)w;
+      __syncthreads();
     }
-    __syncthreads();
     if (*fail) return;
     const int m = n - k1;  // trailing matrix rows/cols k1..n-1
     if (m > 0) {
@@ -788,12 +802,21 @@ __device__ void chol_blocked(double* A, int n, double* inv_diag, int* fail) {
         while (bi * (bi + 1) / 2 > t) --bi;
         const int bc = t - bi * (bi + 1) / 2;
         const int i0 = k1 + 4 * bi, c0 = k1 + 4 * bc;
+        // columns of the panel that can be nonzero in both row groups
+        int fi = n, fc = n;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          if (i0 + a < n) fi = min(fi, efirst[i0 + a]);
+          if (c0 + a < n) fc = min(fc, efirst[c0 + a]);
+        }
+        const int qlo = max(k0, max(fi, fc));
+        if (qlo >= k1) continue;
         double acc[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
           for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
-        for (int q = k0; q < k1; ++q) {
+        for (int q = qlo; q < k1; ++q) {
           double li[4], lc[4];
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
@@ -818,23 +841,72 @@ __device__ void chol_blocked(double* A, int n, double* inv_diag, int* fail) {
   }
 }
 
-// Solve L L^T x = b in place (b in shared memory) by one warp (call from
-// all lanes of warp 0 only): column sweeps, lane l owning rows l, l+32, ...
-__device__ void chol_solve_warp(const double* A, const double* inv_diag, double* b, int n) {
-  const int lane = threadIdx.x & 31;
-  for (int j = 0; j < n; ++j) {  // L y = b
-    if (lane == (j & 31)) b[j] *= inv_diag[j];
-    __syncwarp();
-    const double y = b[j];
-    for (int i = j + 1 + lane; i < n; i += 32) b[i] -= A[pk(i, j)] * y;
-    __syncwarp();
+// After the factorisation: L = Lu D with D = diag(L) and Lu unit lower
+// triangular; the strictly lower part of A is scaled to Lu in place (the
+// diagonal keeps L(j, j)), so that S = Lu D^2 Lu^T and the sweeps need no
+// division.
+__device__ void chol_unit_scale(double* A, const double* inv_diag, const int* efirst, int n) {
+  const int total = n * (n + 1) / 2;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    int i = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);  // row of packed entry idx
+    while ((i + 1) * (i + 2) / 2 <= idx) ++i;
+    while (i * (i + 1) / 2 > idx) --i;
+    const int j = idx - i * (i + 1) / 2;
+    if (j < i && j >= efirst[i]) A[idx] *= inv_diag[j];
   }
-  for (int j = n - 1; j >= 0; --j) {  // L^T x = y
-    if (lane == (j & 31)) b[j] *= inv_diag[j];
-    __syncwarp();
-    const double xj = b[j];
-    for (int i = lane; i < j; i += 32) b[i] -= A[pk(j, i)] * xj;
-    __syncwarp();
+}
+
+// Solve S x = b in place (b in shared memory) with S = Lu D^2 Lu^T, by the
+// whole CTA.  Per diagonal block of kSolveNB rows, warp 0 sweeps the unit
+// triangle (lane = row of the block); then one thread per row updates the
+// rest of the vector with the block's columns.  Entries left of a row's
+// envelope are zero and skipped.
+__device__ void chol_solve_blocked(const double* A, const double* inv_diag, const int* efirst, double* b, int n) {
+  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  for (int k0 = 0; k0 < n; k0 += kSolveNB) {  // Lu z = b
+    const int k1 = min(k0 + kSolveNB, n);
+    if (wid == 0) {
+      const int i = k0 + lane;
+      double v = i < k1 ? b[i] : 0.0;
+      for (int j = k0; j < k1 - 1; ++j) {
+        const double z = __shfl_sync(BA_FULL_MASK, v, j - k0);
+        if (i > j && i < k1 && efirst[i] <= j) v -= A[pk(i, j)] * z;
+      }
+      if (i < k1) b[i] = v;
+    }
+    __syncthreads();
+    for (int i = k1 + tid; i < n; i += bs) {  // b_i -= sum_{q in block} Lu(i, q) z_q
+      const int q0 = max(k0, efirst[i]);
+      double s = 0.0;
+      for (int q = q0; q < k1; ++q) s += A[pk(i, q)] * b[q];
+      b[i] -= s;
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += bs) b[i] *= inv_diag[i] * inv_diag[i];  // w = D^-2 z
+  __syncthreads();
+  const int nb = (n + kSolveNB - 1) / kSolveNB;
+  for (int blk = nb - 1; blk >= 0; --blk) {  // Lu^T x = w
+    const int k0 = blk * kSolveNB, k1 = min(k0 + kSolveNB, n);
+    if (wid == 0) {
+      const int i = k0 + lane;
+      double v = i < k1 ? b[i] : 0.0;
+      for (int j = k1 - 1; j > k0; --j) {
+        const double xj = __shfl_sync(BA_FULL_MASK, v, j - k0);
+        if (i < j && i >= k0 && efirst[j] <= i) v -= A[pk(j, i)] * xj;
+      }
+      if (i < k1) b[i] = v;
+    }
+    __syncthreads();
+    int lo = k0;  // the block's rows have no entry left of their envelopes
+    for (int q = k0; q < k1; ++q) lo = min(lo, efirst[q]);
+    for (int i = lo + tid; i < k0; i += bs) {  // b_i -= sum_{q in block} Lu(q, i) x_q
+      double s = 0.0;
+      for (int q = k0; q < k1; ++q)
+        if (efirst[q] <= i) s += A[pk(q, i)] * b[q];
+      b[i] -= s;
+    }
+    __syncthreads();
   }
 }
 
@@ -888,15 +960,17 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
         v += mu * D;
         C.Dc[6 * f + a] = D;
       }
-      A[pk(6 * f + bb, 6 * f + a)] = v;  // row bb >= col a
+      const int p = C.fpos[f];
+      A[pk(6 * p + bb, 6 * p + a)] = v;  // row bb >= col a
     }
     for (int idx = tid; idx < n; idx += bs) {
       const int f = idx / 6, a = idx - 6 * f;
       const double g = cd[40 * f + 21 + a] - pr[42 * f + 36 + a];
       C.gc[idx] = g;
       const double r = g - cd[40 * f + 27 + a];
-      C.rhs[idx] = r;
-      b[idx] = r;
+      const int pi = 6 * C.fpos[f] + a;  // elimination order
+      C.rhs[pi] = r;
+      b[pi] = r;
     }
     // off-diagonal blocks: S(fb, fa) = -(sum Z_a Z_b^T)^T
     for (int idx = tid; idx < C.n_pairs * 36; idx += bs) {
@@ -904,7 +978,9 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
       const int i = e / 6, c = e - 6 * i;
       const double v = C.pairsum[(size_t)kPairPart * p + e];
       const int2 key = C.pair_key[p];
-      A[pk(6 * key.y + c, 6 * key.x + i)] = -v;
+      const int pa = C.fpos[key.x], pb = C.fpos[key.y];
+      if (pb > pa) A[pk(6 * pb + c, 6 * pa + i)] = -v;
+      else A[pk(6 * pa + i, 6 * pb + c)] = -v;
     }
     __syncthreads();
     for (int idx = tid; idx < n * n; idx += bs) {
@@ -917,12 +993,16 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
     }
     __syncthreads();  // the copy of S above reads A
     // blocked right-looking Cholesky in shared memory (t[] is the column buffer)
-    if (!fail) chol_blocked(A, n, inv_diag, &fail);
+    int* efirst = reinterpret_cast<int*>(inv_diag + n);  // [n]: first column of each row's envelope
+    for (int idx = tid; idx < n; idx += bs) efirst[idx] = 6 * C.env_first[idx / 6];
+    __syncthreads();
+    if (!fail) chol_blocked(A, n, inv_diag, t, efirst, &fail);
     __syncthreads();
     const int status = fail ? BA_STATUS_NOT_PD : 0;
     if (!fail) {
-      if (tid < 32) chol_solve_warp(A, inv_diag, b, n);
+      chol_unit_scale(A, inv_diag, efirst, n);
       __syncthreads();
+      chol_solve_blocked(A, inv_diag, efirst, b, n);
       for (int idx = tid; idx < n; idx += bs) x[idx] = b[idx];
       __syncthreads();
       // iterative refinement against the FP64 system kept in global memory
@@ -930,19 +1010,20 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
         const int lane = tid & 31, wid = tid >> 5, nw = bs >> 5;
         for (int r = wid; r < n; r += nw) {
           double acc = 0.0;
-          for (int c = lane; c < n; c += 32) acc += C.S[(size_t)r * n + c] * x[c];
+          for (int c = efirst[r] + lane; c < n; c += 32)  // zero blocks outside the envelope skipped
+            if (c <= r || efirst[c] <= r) acc += C.S[(size_t)r * n + c] * x[c];
           acc = warp_sum(acc);
           if (lane == 0) t[r] = C.rhs[r] - acc;
         }
         __syncthreads();
-        if (tid < 32) chol_solve_warp(A, inv_diag, t, n);
-        __syncthreads();
+        chol_solve_blocked(A, inv_diag, efirst, t, n);
         for (int idx = tid; idx < n; idx += bs) x[idx] += t[idx];
         __syncthreads();
       }
-      for (int idx = tid; idx < n; idx += bs) {
-        C.dc[idx] = x[idx];
-        if (MIXED) C.dc32[idx] = (float)x[idx];
+      for (int idx = tid; idx < n; idx += bs) {  // back to free-image order
+        const double v = x[6 * C.fpos[idx / 6] + idx % 6];
+        C.dc[idx] = v;
+        if (MIXED) C.dc32[idx] = (float)v;
       }
     } else {
       for (int idx = tid; idx < n; idx += bs) {
@@ -962,7 +1043,7 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
         for (int i = 0; i < 3; ++i) Tn[3 * k + i] = Tc[3 * k + i];
         if (f >= 0) { t[2 * f] = 0.0; t[2 * f + 1] = 0.0; }
       } else {
-        const double* d = x + 6 * f;
+        const double* d = x + 6 * C.fpos[f];
         double E[9];
         so3_exp(d, E);
         const double* R0 = Rc + 9 * k;
