@@ -13,6 +13,8 @@ namespace bagpu {
 
 __device__ __forceinline__ float rsqrt_any(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_any(double x) { return rsqrt(x); }
+__device__ __forceinline__ float recip_any(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip_any(double x) { return 1.0 / x; }
 
 // largest s in [0, n) with pre[s] <= g (pre is non-decreasing)
 __device__ __forceinline__ int find_slot(const int* __restrict__ pre, int n, int g) {
@@ -245,7 +247,7 @@ __device__ __forceinline__ bool obs_linearize(const Real* Rm, Real dx, Real dy, 
     return false;
   }
   const Real f = in[0], k1 = in[3], k2 = in[4], p1 = in[5], p2 = in[6];
-  const Real iz = Real(1) / z;
+  const Real iz = recip_any(z);
   const Real xn = x * iz, yn = y * iz;
   const Real r2 = xn * xn + yn * yn;
   const Real rad = Real(1) + r2 * (k1 + k2 * r2);

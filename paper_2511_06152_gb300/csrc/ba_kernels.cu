@@ -311,20 +311,18 @@ __device__ __forceinline__ void linearize_tile(const DevCluster& C, LmState* lm,
   if (L.head) {
     const Real d0 = clamp_diag(v00), d1 = clamp_diag(v11), d2 = clamp_diag(v22);
     const Real a00 = v00 + mu * d0, a11 = v11 + mu * d1, a22 = v22 + mu * d2;
+    // V* = L L^T with M = L^-1 from reciprocal square roots of the pivots
     bool ok = a00 > Real(0);
-    const Real l00 = sqrt(ok ? a00 : Real(1));
-    const Real l10 = v01 / l00, l20 = v02 / l00;
+    m00 = rsqrt_any(ok ? a00 : Real(1));
+    const Real l10 = v01 * m00, l20 = v02 * m00;
     const Real t11 = a11 - l10 * l10;
     ok = ok && t11 > Real(0);
-    const Real l11 = sqrt(t11 > Real(0) ? t11 : Real(1));
-    const Real l21 = (v12 - l20 * l10) / l11;
+    m11 = rsqrt_any(t11 > Real(0) ? t11 : Real(1));
+    const Real l21 = (v12 - l20 * l10) * m11;
     const Real t22 = a22 - l20 * l20 - l21 * l21;
     ok = ok && t22 > Real(0);
-    const Real l22 = sqrt(t22 > Real(0) ? t22 : Real(1));
+    m22 = rsqrt_any(t22 > Real(0) ? t22 : Real(1));
     if (!ok && report_fail) lm->pt_fail = 1;  // point block not positive definite: reject this step
-    m00 = Real(1) / l00;
-    m11 = Real(1) / l11;
-    m22 = Real(1) / l22;
     m10 = -l10 * m00 * m11;
     m21 = -l21 * m11 * m22;
     m20 = -(l20 * m00 + l21 * m10) * m22;
@@ -405,6 +403,30 @@ __device__ __forceinline__ void ld_rec_rq(const double* r, double& r0, double& r
   const double2 a = reinterpret_cast<const double2*>(r + kSrecR)[0];
   const double2 b = reinterpret_cast<const double2*>(r + kSrecQ)[0];
   r0 = a.x; r1 = a.y; q0 = b.x; q1 = b.y; q2 = r[kSrecQ + 2];
+}
+
+// Store one observation's record (vector stores).
+__device__ __forceinline__ void st_rec(float* r, const TileLin<true>& L) {
+  float4* v = reinterpret_cast<float4*>(r);
+  v[0] = make_float4(L.Jc[0], L.Jc[1], L.Jc[2], L.Jc[3]);
+  v[1] = make_float4(L.Jc[4], L.Jc[5], L.Jc[6], L.Jc[7]);
+  v[2] = make_float4(L.Jc[8], L.Jc[9], L.Jc[10], L.Jc[11]);
+  v[3] = make_float4(L.Z[0], L.Z[1], L.Z[2], L.Z[3]);
+  v[4] = make_float4(L.Z[4], L.Z[5], L.Z[6], L.Z[7]);
+  v[5] = make_float4(L.Z[8], L.Z[9], L.Z[10], L.Z[11]);
+  v[6] = make_float4(L.Z[12], L.Z[13], L.Z[14], L.Z[15]);
+  v[7] = make_float4(L.Z[16], L.Z[17], L.r0, L.r1);
+  v[8] = make_float4(L.q0, L.q1, L.q2, 0.f);
+}
+__device__ __forceinline__ void st_rec(double* r, const TileLin<false>& L) {
+  double2* v = reinterpret_cast<double2*>(r);
+#pragma unroll
+  for (int i = 0; i < 6; ++i) v[i] = make_double2(L.Jc[2 * i], L.Jc[2 * i + 1]);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) v[6 + i] = make_double2(L.Z[2 * i], L.Z[2 * i + 1]);
+  v[15] = make_double2(L.r0, L.r1);
+  v[16] = make_double2(L.q0, L.q1);
+  v[17] = make_double2(L.q2, 0.0);
 }
 
 // One job's sums over its items [i0, i1).  Image job: the upper triangle of
@@ -601,18 +623,7 @@ __global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed
         const Tile tl = C.tiles[ch.tile_begin + t];
         TileLin<MIXED> L;
         linearize_tile<MIXED>(C, lm, tl, lane, true, L, V);
-        if (L.act) {
-          Real* r = srec + (size_t)(L.o - ch.obs_begin) * kSrec;
-#pragma unroll
-          for (int i = 0; i < 12; ++i) r[i] = L.Jc[i];
-#pragma unroll
-          for (int i = 0; i < 18; ++i) r[kSrecZ + i] = L.Z[i];
-          r[kSrecR] = L.r0;
-          r[kSrecR + 1] = L.r1;
-          r[kSrecQ] = L.q0;
-          r[kSrecQ + 1] = L.q1;
-          r[kSrecQ + 2] = L.q2;
-        }
+        if (L.act) st_rec(srec + (size_t)(L.o - ch.obs_begin) * kSrec, L);
         if (diag) {  // largest |g_p| of the tile, for the gradient norm
           double gm = L.head ? fmax(fabs((double)L.g0), fmax(fabs((double)L.g1), fabs((double)L.g2))) : 0.0;
 #pragma unroll
