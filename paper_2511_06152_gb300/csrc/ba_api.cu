@@ -38,6 +38,7 @@ struct Cluster {
   std::vector<int> pt_inv;        // caller point index -> internal point index
   std::atomic<int> in_service{0}; // queued or running in the serving scheduler
   ba_cluster_info info{};         // table sizes, filled at creation
+  std::vector<int> big_below;     // global-memory solver: row blocks below each block column (else empty)
 };
 
 struct GraphRec {
@@ -55,6 +56,7 @@ struct Plan {
   double* gnorm = nullptr;       // device [n]
   std::map<int, GraphRec> graphs;
   GraphRec* last = nullptr;      // graph of the last launch (for timing readout)
+  std::vector<BigRef> big;       // clusters whose reduced systems are solved in global memory
 };
 
 struct Ticket {
@@ -177,7 +179,8 @@ Cluster* find_cluster(ba_ctx* ctx, ba_cluster_id id) {
 ba_status ensure_attrs(ba_ctx* ctx, int max_n) {
   if (max_n <= ctx->attr_max_n) return BA_OK;
   const int want = std::max(max_n, 6 * kMaxFreeSmall);
-  CUDA_TRY(ctx, set_kernel_attributes(want));
+  CUDA_TRY(ctx, set_kernel_attributes(std::min(want, 6 * kMaxFreeSmall)));
+  if (want > 6 * kMaxFreeSmall) CUDA_TRY(ctx, set_big_attributes(want));
   ctx->attr_max_n = want;
   return BA_OK;
 }
@@ -231,7 +234,7 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
   const int n = (int)ids.size();
   std::vector<DevCluster> descs(n);
   std::vector<int> pre(3 * (size_t)(n + 1), 0);
-  int max_n = 6;
+  int max_n = 6, big_max = 0;
   for (int i = 0; i < n; ++i) {
     Cluster* c = find_cluster(ctx, ids[i]);
     if (!c) return set_err(ctx, BA_ERR_NOT_FOUND, "unknown cluster id in batch");
@@ -239,12 +242,18 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
     pre[i + 1] = pre[i] + c->h.n_tiles;
     pre[(n + 1) + i + 1] = pre[(n + 1) + i] + c->h.n_chunks;
     pre[2 * (n + 1) + i + 1] = pre[2 * (n + 1) + i] + c->h.n_free + c->h.n_pairs;
-    max_n = std::max(max_n, 6 * c->h.n_free);
+    if (c->nf <= kMaxFreeSmall) max_n = std::max(max_n, 6 * c->h.n_free);
+    else big_max = std::max(big_max, 6 * c->nf);
   }
-  ba_status st = ensure_attrs(ctx, max_n);
+  ba_status st = ensure_attrs(ctx, std::max(max_n, big_max));
   if (st != BA_OK) return st;
   Plan* p = new Plan();
   p->ids = ids;
+  for (int i = 0; i < n; ++i) {
+    Cluster* c = find_cluster(ctx, ids[i]);
+    if (c->nf > kMaxFreeSmall)
+      p->big.push_back(BigRef{c->d_desc, 6 * c->nf, c->nf, c->h.n_pairs, c->h.S, c->h.F, c->big_below});
+  }
   pre.push_back(pre[n]);  // totals, read by the kernels
   pre.push_back(pre[(n + 1) + n]);
   pre.push_back(pre[2 * (n + 1) + n]);
@@ -314,7 +323,7 @@ ba_status run_plan(ba_ctx* ctx, Plan* p, int iters) {
     CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     launch_arm(p->bv, iters, ctx->stream);
     launch_cost_init(p->bv, ctx->mixed, ctx->stream);
-    for (int i = 0; i < iters; ++i) launch_iteration(p->bv, ctx->mixed, ctx->refine, ctx->stream);
+    for (int i = 0; i < iters; ++i) launch_iteration(p->bv, ctx->mixed, ctx->refine, ctx->stream, &p->big);
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
     set_probe(nullptr);
     g.kernels = take_captured_launches();
@@ -447,8 +456,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
     }
   const int nf = (int)cam_of_free.size();
   if (nf == 0) return set_err(ctx, BA_ERR_INVALID, "no free camera");
-  if (nf > kMaxFreeSmall)
-    return set_err(ctx, BA_ERR_INVALID, "more than 32 free cameras in one cluster is not supported");
+  if (nf > kMaxFree) return set_err(ctx, BA_ERR_INVALID, "more than 1024 free cameras in one cluster");
 
   // internal point order: Morton code of the initial ground position (x, y),
   // ties by the caller's index, so that consecutive points share cameras
@@ -719,6 +727,22 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
       for (int g : adj[f]) first = std::min(first, fpos[g]);
       env_first[fpos[f]] = first;
     }
+    // widen to a non-decreasing envelope (a superset: still no fill outside)
+    for (int p = nf - 2; p >= 0; --p) env_first[p] = std::min(env_first[p], env_first[p + 1]);
+  }
+  // global-memory solver: per block column of kBigNB, the row blocks below it
+  // whose first row reaches into it (contiguous, as the envelope is monotone)
+  std::vector<int> big_below;
+  const bool big = nf > kMaxFreeSmall;
+  if (big) {
+    const int n = 6 * nf, nblk = (n + kBigNB - 1) / kBigNB;
+    big_below.assign(nblk, 0);
+    for (int k = 0; k < nblk; ++k) {
+      const int last_col = std::min(n, kBigNB * (k + 1)) - 1;
+      int i = k + 1;
+      while (i < nblk && 6 * env_first[(kBigNB * i) / 6] <= last_col) ++i;
+      big_below[k] = i - (k + 1);
+    }
   }
 
   // arena layout: static (uploaded) part first
@@ -756,6 +780,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const size_t o_psb = Lo.add(sizeof(int) * pair_slot_begin.size());
   const size_t o_ps = Lo.add(sizeof(int) * pair_slots.size());
   const size_t o_lm = Lo.add(sizeof(LmState));
+  const size_t o_bflag = Lo.add(big ? sizeof(int) : 0);  // zero from the staging
   const size_t static_bytes = Lo.off;
   const size_t o_camreal = Lo.add(mixed ? 0 : sizeof(double) * kCamReal * nc);
   const size_t o_camdf = Lo.add(mixed ? sizeof(float) * 2 * kCamDf * nc : 0);
@@ -772,6 +797,8 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const size_t o_tp = Lo.add(sizeof(double) * 2 * tiles.size());
   const size_t o_trace = Lo.add(sizeof(StepRec) * kTraceCap);
   const size_t o_desc = Lo.add(sizeof(DevCluster));
+  const size_t o_F = Lo.add(big ? sizeof(double) * (size_t)n * n : 0);
+  const size_t o_bx = Lo.add(big ? sizeof(double) * 4 * (size_t)n : 0);
   const size_t total = Lo.off;
 
   std::unique_ptr<char[]> stage_buf(new char[static_bytes]);  // every byte used below is written
@@ -848,6 +875,10 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
     lm.nu = 2.0;
     put(o_lm, &lm, sizeof(lm));
   }
+  if (big) {
+    const int zero = 0;
+    put(o_bflag, &zero, sizeof(int));
+  }
 
   // Everything above is host work.  The budget is reserved under the API
   // lock; allocation, upload and the camera records run on a stream of this
@@ -909,6 +940,9 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   h.cam_of_free = (const int*)(arena + o_cof);
   h.fpos = (const int*)(arena + o_fpos);
   h.env_first = (const int*)(arena + o_envf);
+  h.F = big ? (double*)(arena + o_F) : nullptr;
+  h.bx = big ? (double*)(arena + o_bx) : nullptr;
+  h.bflag = big ? (int*)(arena + o_bflag) : nullptr;
   h.camreal = mixed ? nullptr : arena + o_camreal;
   h.camdf = mixed ? (float*)(arena + o_camdf) : nullptr;
   h.tiles = (const Tile*)(arena + o_tiles);
@@ -965,6 +999,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   c->info.arena_bytes = (int64_t)total;
   c->pm_to_user = std::move(pm);
   c->pt_inv = std::move(inv);
+  c->big_below = std::move(big_below);
   return BA_OK;
 }
 
@@ -1317,7 +1352,7 @@ BA_API ba_status ba_linearize(ba_ctx* ctx, ba_cluster_id id, ba_lin_info* out) {
   if (st != BA_OK) return st;
   launch_arm(p->bv, -1, ctx->stream);
   launch_cost_init(p->bv, ctx->mixed, ctx->stream);
-  launch_grad_norm(p->bv, ctx->mixed, p->gnorm, ctx->stream);
+  launch_grad_norm(p->bv, ctx->mixed, p->gnorm, ctx->stream, &p->big);
   launch_arm(p->bv, -2, ctx->stream);
   note_direct(ctx);
   LmState lm{};

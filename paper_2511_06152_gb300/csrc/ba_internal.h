@@ -37,6 +37,8 @@ constexpr int kChunkObsF64 = 32 * kChunkTilesF64;
 constexpr int kChunkThreads = 256;
 constexpr int kMaxTrack = 32;
 constexpr int kMaxFreeSmall = 32;  // free cameras the single-CTA factor handles (n <= 192)
+constexpr int kMaxFree = 1024;     // free cameras of one cluster (larger systems: the global-memory solver)
+constexpr int kBigNB = 32;         // block size of the global-memory factorisation
 constexpr double kDiagMin = 1e-6;
 constexpr double kDiagMax = 1e32;
 constexpr double kMinDepth = 1e-6;
@@ -128,7 +130,11 @@ struct DevCluster {
   // block position fpos[f]; env_first[p] = first block column of block row
   // p inside the envelope of S (and of its Cholesky factor)
   const int* fpos;         // [nf]
-  const int* env_first;    // [nf]
+  const int* env_first;    // [nf], non-decreasing
+  // global-memory solver (more than kMaxFreeSmall free images), else null:
+  double* F;               // [n][n] Cholesky factor (lower), elimination order
+  double* bx;              // [4][n]: right-hand side / work, solution, correction, 1 / L(j, j)
+  int* bflag;              // nonzero: a pivot was not positive
   void* camreal;           // FP64 path: double [nc][20]: R[9], T[3], intr[7], free flag
   float* camdf;            // mixed path: [2][nc][kCamDf] double-float cameras
 
@@ -205,6 +211,36 @@ void set_probe(Probe* p);                       // attach to the calling thread 
 unsigned long long take_direct_launches();      // launches outside capture since the last call
 unsigned long long take_captured_launches();    // kernel nodes captured since the last call
 
+// Every kernel launch goes through LAUNCH(kind, stream, launch): it counts the
+// launch (direct, or as a captured graph node) and, with a probe attached to
+// the calling thread, brackets it with events for per-kind timing.
+struct LaunchScope {
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t e0 = nullptr;
+  LaunchScope(int k, cudaStream_t s);
+  ~LaunchScope();
+};
+#define LAUNCH(kind, st, ...)   \
+  do {                          \
+    LaunchScope ls__(kind, st); \
+    __VA_ARGS__;                \
+  } while (0)
+
+int num_sms();
+
+// A cluster whose reduced system is solved in global memory (more than
+// kMaxFreeSmall free images): what the host needs to emit its launches.
+struct BigRef {
+  const DevCluster* d;     // device descriptor
+  int n, nf, n_pairs;
+  double* S;               // device [n][n]
+  double* F;               // device [n][n]
+  std::vector<int> below;  // per block column of kBigNB: row blocks below it inside the envelope
+};
+void launch_big_solve(const BigRef& b, bool mixed, int refine_steps, int assemble_only, cudaStream_t st);
+cudaError_t set_big_attributes(int max_n);
+
 // Kernel launchers (ba_kernels.cu).  All run on `st`.
 cudaError_t set_kernel_attributes(int max_n);
 void launch_arm(const BatchView& bv, int iters, cudaStream_t st);
@@ -215,8 +251,12 @@ void launch_reset(const BatchView& bv, bool mixed, cudaStream_t st);
 void launch_gather(const BatchView& bv, int iters, LmState* lm_out, StepRec* trace_out, cudaStream_t st);
 void launch_camreal(const BatchView& bv, bool mixed, cudaStream_t st);
 void launch_cost_init(const BatchView& bv, bool mixed, cudaStream_t st);
-void launch_iteration(const BatchView& bv, bool mixed, int refine_steps, cudaStream_t st);
-void launch_grad_norm(const BatchView& bv, bool mixed, double* out, cudaStream_t st);
+// big: the batch's clusters with more than kMaxFreeSmall free images (their
+// reduced systems are solved by launch_big_solve), or null
+void launch_iteration(const BatchView& bv, bool mixed, int refine_steps, cudaStream_t st,
+                      const std::vector<BigRef>* big = nullptr);
+void launch_grad_norm(const BatchView& bv, bool mixed, double* out, cudaStream_t st,
+                      const std::vector<BigRef>* big = nullptr);
 void launch_reproj(const DevCluster* dcl, const DevCluster& hcl, bool mixed, double* err_pm, cudaStream_t st);
 void launch_export_points(const DevCluster* dcl, const DevCluster& hcl, bool mixed, double* out, cudaStream_t st);
 size_t factor_smem_bytes(int max_n);

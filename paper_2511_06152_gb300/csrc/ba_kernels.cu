@@ -39,6 +39,7 @@
 
 #include "ba_device.cuh"
 #include "ba_bulk.cuh"
+#include "ba_camera.cuh"
 #include "ba_dfloat.cuh"
 #include "ba_internal.h"
 
@@ -143,31 +144,6 @@ __global__ void k_camreal(BatchView bv) {
       o[19] = C.free_idx[k] >= 0 ? 1.0 : 0.0;
     }
   }
-}
-
-// mixed path: double-float record of camera k from (R, T) in binary64
-__device__ void write_camdf(const DevCluster& C, int buf, int k, const double* R, const double* T) {
-  float* o = C.camdf + ((size_t)buf * C.n_cams + k) * kCamDf;
-  for (int i = 0; i < 9; ++i) {
-    const dfl v = df_from_d(R[i]);
-    o[2 * i] = v.hi;
-    o[2 * i + 1] = v.lo;
-  }
-  for (int i = 0; i < 3; ++i) {
-    const dfl v = df_from_d(T[i]);
-    o[18 + 2 * i] = v.hi;
-    o[19 + 2 * i] = v.lo;
-  }
-  const dfl f = df_from_d(C.intr[7 * k]);
-  o[24] = f.hi;
-  o[25] = f.lo;
-  for (int i = 0; i < 4; ++i) {
-    const dfl v = df_from_d(C.intr[7 * k + 3 + i]);
-    o[26 + 2 * i] = v.hi;
-    o[27 + 2 * i] = v.lo;
-  }
-  o[34] = C.free_idx[k] >= 0 ? 1.0f : 0.0f;
-  for (int i = 35; i < kCamDf; ++i) o[i] = 0.0f;
 }
 
 // both buffers of the mixed camera records from the binary64 cameras
@@ -932,6 +908,7 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
     const DevCluster& C = bv.cl[s];
     LmState* lm = C.lm;
     if (!lm->active && !assemble_only) continue;
+    if (C.n_free > kMaxFreeSmall) continue;  // the global-memory solver takes larger systems
     const int nf = C.n_free, n = 6 * nf, nc = C.n_cams;
     const double mu = lm->mu;
     const int cur = lm->cur;
@@ -1045,30 +1022,14 @@ __global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_s
     }
     __syncthreads();
     // candidate cameras; per-camera prior cost and pred terms into t[]
-    double* Rn = C.R + (size_t)(cur ^ 1) * nc * 9;
-    double* Tn = C.T + (size_t)(cur ^ 1) * nc * 3;
     for (int k = tid; k < nc; k += bs) {
       const int f = C.free_idx[k];
-      if (f < 0 || fail) {
-        for (int i = 0; i < 9; ++i) Rn[9 * k + i] = Rc[9 * k + i];
-        for (int i = 0; i < 3; ++i) Tn[3 * k + i] = Tc[3 * k + i];
-        if (f >= 0) { t[2 * f] = 0.0; t[2 * f + 1] = 0.0; }
-      } else {
-        const double* d = x + 6 * C.fpos[f];
-        double E[9];
-        so3_exp(d, E);
-        const double* R0 = Rc + 9 * k;
-        for (int r = 0; r < 3; ++r)
-          for (int c = 0; c < 3; ++c)
-            Rn[9 * k + 3 * r + c] = R0[3 * r] * E[c] + R0[3 * r + 1] * E[3 + c] + R0[3 * r + 2] * E[6 + c];
-        for (int i = 0; i < 3; ++i) Tn[3 * k + i] = Tc[3 * k + i] + d[3 + i];
-        double pc = 0.0;
-        for (int a = 0; a < 6; ++a) pc += d[a] * (mu * C.Dc[6 * f + a] * d[a] + C.gc[6 * f + a]);
+      double pc, pn;
+      candidate_camera<MIXED>(C, k, x, mu, cur, fail != 0, &pc, &pn);
+      if (f >= 0) {
         t[2 * f] = pc;
-        t[2 * f + 1] = prior_terms(Rn + 9 * k, Tn + 3 * k, C.R_prior + 9 * k, C.T_prior + 3 * k, C.sigma_imu,
-                                   C.sigma_gnss, nullptr, nullptr);
+        t[2 * f + 1] = pn;
       }
-      if constexpr (MIXED) write_camdf(C, cur ^ 1, k, Rn + 9 * k, Tn + 3 * k);
     }
     __syncthreads();
     if (tid == 0) {
@@ -1575,28 +1536,18 @@ static void probe_mark(cudaStream_t st, cudaEvent_t* out) {
   else cudaEventRecord(*out, st);
 }
 
-struct LaunchScope {
-  int kind;
-  cudaStream_t st;
-  cudaEvent_t e0 = nullptr;
-  LaunchScope(int k, cudaStream_t s) : kind(k), st(s) {
-    if (t_probe) probe_mark(st, &e0);
-  }
-  ~LaunchScope() {
-    if (capturing(st)) ++t_captured; else ++t_direct;
-    if (t_probe) {
-      cudaEvent_t e1;
-      probe_mark(st, &e1);
-      t_probe->recs.push_back(ProbeRec{kind, e0, e1});
-    }
-  }
-};
+LaunchScope::LaunchScope(int k, cudaStream_t s) : kind(k), st(s) {
+  if (t_probe) probe_mark(st, &e0);
+}
 
-#define LAUNCH(kind, st, ...) \
-  do {                          \
-    LaunchScope ls__(kind, st); \
-    __VA_ARGS__;                \
-  } while (0)
+LaunchScope::~LaunchScope() {
+  if (capturing(st)) ++t_captured; else ++t_direct;
+  if (t_probe) {
+    cudaEvent_t e1;
+    probe_mark(st, &e1);
+    t_probe->recs.push_back(ProbeRec{kind, e0, e1});
+  }
+}
 
 static int grid_for(int items, int per_block, int cap) {
   int g = (items + per_block - 1) / per_block;
@@ -1605,7 +1556,7 @@ static int grid_for(int items, int per_block, int cap) {
 }
 
 static int g_num_sms = 0;
-static int num_sms() {
+int num_sms() {
   if (!g_num_sms) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1680,33 +1631,38 @@ static void launch_partial_reduce(const BatchView& bv, cudaStream_t st) {
 }
 
 template <bool MIXED>
-static void launch_iteration_t(const BatchView& bv, int refine_steps, cudaStream_t st) {
+static void launch_iteration_t(const BatchView& bv, int refine_steps, cudaStream_t st, const std::vector<BigRef>* big) {
   const int sms = num_sms();
   launch_lin_schur<MIXED>(bv, 0, st);
   launch_partial_reduce<MIXED>(bv, st);
   const size_t smem = factor_smem_bytes(bv.max_n);
   LAUNCH(KK_FACTOR, st, k_factor_solve<MIXED><<<grid_for(bv.n, 1, 65535), 512, smem, st>>>(bv, refine_steps, 0));
+  if (big)
+    for (const BigRef& b : *big) launch_big_solve(b, MIXED, refine_steps, 0, st);
   LAUNCH(KK_BACKSUB, st, k_backsub_cost<MIXED><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
   LAUNCH(KK_LM_UPDATE, st, k_lm_update<MIXED><<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv));
 }
 
-void launch_iteration(const BatchView& bv, bool mixed, int refine_steps, cudaStream_t st) {
-  if (mixed) launch_iteration_t<true>(bv, refine_steps, st);
-  else launch_iteration_t<false>(bv, refine_steps, st);
+void launch_iteration(const BatchView& bv, bool mixed, int refine_steps, cudaStream_t st,
+                      const std::vector<BigRef>* big) {
+  if (mixed) launch_iteration_t<true>(bv, refine_steps, st, big);
+  else launch_iteration_t<false>(bv, refine_steps, st, big);
 }
 
 template <bool MIXED>
-static void launch_grad_norm_t(const BatchView& bv, double* out, cudaStream_t st) {
+static void launch_grad_norm_t(const BatchView& bv, double* out, cudaStream_t st, const std::vector<BigRef>* big) {
   launch_lin_schur<MIXED>(bv, 1, st);
   launch_partial_reduce<MIXED>(bv, st);
   LAUNCH(KK_FACTOR, st,
          k_factor_solve<MIXED><<<grid_for(bv.n, 1, 65535), 512, factor_smem_bytes(bv.max_n), st>>>(bv, 0, 1));
+  if (big)
+    for (const BigRef& b : *big) launch_big_solve(b, MIXED, 0, 1, st);
   LAUNCH(KK_OTHER, st, k_grad_norm<<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv, out));
 }
 
-void launch_grad_norm(const BatchView& bv, bool mixed, double* out, cudaStream_t st) {
-  if (mixed) launch_grad_norm_t<true>(bv, out, st);
-  else launch_grad_norm_t<false>(bv, out, st);
+void launch_grad_norm(const BatchView& bv, bool mixed, double* out, cudaStream_t st, const std::vector<BigRef>* big) {
+  if (mixed) launch_grad_norm_t<true>(bv, out, st, big);
+  else launch_grad_norm_t<false>(bv, out, st, big);
 }
 
 void launch_reproj(const DevCluster* dcl, const DevCluster& hcl, bool mixed, double* err_pm, cudaStream_t st) {
