@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--serving-rate", type=float, default=200.0, help="requests/s, Poisson, all flights")
     ap.add_argument("--serving-iters", type=int, default=10)
     ap.add_argument("--serving-only", action="store_true", help="run only the serving leg")
+    ap.add_argument("--no-large", action="store_true", help="skip the 400-image large-block leg")
     ap.add_argument("--serving-timeout", type=float, default=120.0, help="seconds before the serving leg gives up")
     return ap.parse_args()
 
@@ -68,16 +69,18 @@ def dist_env():
     return rank, world, local
 
 
-def make_workload(replica, n_clusters, n_flights=0):
-    """Generate the batch (and the serving flights) in a spawn pool, before
-    any CUDA call."""
+def make_workload(replica, n_clusters, n_flights=0, large=False):
+    """Generate the batch (and the serving flights and the large block) in a
+    spawn pool, before any CUDA call."""
     import multiprocessing as mp
     n = min(16, os.cpu_count() or 1)
     ctx = mp.get_context("spawn")
     with ctx.Pool(n) as pool:
+        big = pool.apply_async(sg.cluster_c5, (replica,)) if large else None  # ~1 min, alongside the rest
         scenes = sg.batch_c3(replica=replica, n_clusters=n_clusters, pool=pool)
         flights = pool.map(serving_flight, [4000 + 100 * replica + f for f in range(n_flights)]) if n_flights else []
-    return scenes, flights
+        big = big.get() if big is not None else None
+    return scenes, flights, big
 
 
 def serving_flight(seed):
@@ -416,7 +419,7 @@ def main():
         return
     n_fl = 0 if (args.no_extras or rank != 0 or world != 1) else args.serving_flights
     log(f"generating {args.clusters} clusters and {n_fl} serving flights")
-    scenes, flights = make_workload(rank, args.clusters, n_fl)  # spawn pool before the first CUDA call
+    scenes, flights, large = make_workload(rank, args.clusters, n_fl, large=n_fl > 0 and not args.no_large)
     total_obs = sum(s["n_obs"] for s in scenes)
     iters = args.iters
 
@@ -506,7 +509,7 @@ def main():
 
     log(f"timed: {ms_per_step:.2f} ms/step")
     if not args.no_extras and rank == 0 and world == 1:
-        line.update(extras(args, ba, torch, scenes, ids, ctx, stream, iters, value, flights))
+        line.update(extras(args, ba, torch, scenes, ids, ctx, stream, iters, value, flights, large))
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -514,7 +517,38 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flights):
+def large_block_leg(ba, torch, stream, c):
+    """The 400-image large block (10 strips x 40 images, 2 M points, n = 2400
+    reduced system, global-memory solver): 15 LM iterations, mixed and FP64."""
+    out = {"workload": "10 strips x 40 images, 2,000,000 points, track 2+Geom(1/4) <= 16, 15 LM iterations",
+           "observations": int(c["n_obs"])}
+    T = {}
+    for prec in ("mixed", "fp64"):
+        cx = ba.Context(device=torch.cuda.current_device(), precision=ba.BA_MIXED if prec == "mixed" else ba.BA_FP64,
+                        stream=stream.cuda_stream, flags=ba.BA_FLAG_KERNEL_TIMING)
+        cid = cx.create_cluster(c)
+        cx.run(cid, 1, trace=False)  # graph capture
+        cx.reset(cid)
+        cx.kernel_stats(reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tr = cx.run(cid, sg.ITERS["c5"])
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        k = cx.kernel_stats(reset=True)
+        err = cx.reprojection_errors(cid)
+        _, T[prec], _ = cx.get_state(cid)
+        out[prec] = {"ms_per_iter": ms / sg.ITERS["c5"], "obs_per_s": c["n_obs"] * sg.ITERS["c5"] / (ms * 1e-3),
+                     "rms_px": float(np.sqrt(np.mean(err[~c["outlier"]] ** 2))),
+                     "accepted": int(sum(x["accepted"] for x in tr)),
+                     "kernel_ms_per_iter": {a: v[0] / sg.ITERS["c5"] for a, v in k.items() if v[1]}}
+        cx.close()
+    out["max_centre_diff_m"] = float(sg.centre_error(T["mixed"], T["fp64"]))
+    return out
+
+
+def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flights, large=None):
     out = {}
     # accuracy of the mixed path on a few clusters against the FP64 path
     sample = list(range(min(args.fp64_sample, len(scenes))))
@@ -576,6 +610,9 @@ def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flight
     log("cpu baseline leg")
     out["cpu_baseline"] = oracle_obs_per_s(scenes, iters, args.cpu_seconds)
     out["paper_context"] = "paper: full BA per cluster in < 2 s, MATLAB on an i7 13th-gen 20-core laptop, no GPU"
+    if large is not None:
+        log("large block leg")
+        out["large_block"] = large_block_leg(ba, torch, stream, large)
     if flights:
         log("serving leg")
         out["serving"] = serving_leg(args, ba, stream, flights)

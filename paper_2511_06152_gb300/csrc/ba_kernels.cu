@@ -1224,6 +1224,35 @@ __global__ void __launch_bounds__(256) k_cost_tiles(BatchView bv) {
 }
 
 // fixed-order block sum of tilepart[:, which]
+// Both per-tile sums (cost at the candidate, pred) over the cluster's tiles,
+// in a fixed order: each thread a strided run of tiles, then a warp tree and
+// the warps in order.  red: shared [2][blockDim / 32].  Valid in thread 0.
+__device__ double2 block_sum_tiles2(const DevCluster& C, double* red) {
+  double a = 0.0, b = 0.0;
+  const double2* tp = reinterpret_cast<const double2*>(C.tilepart);
+  for (int i = threadIdx.x; i < C.n_tiles; i += blockDim.x) {
+    const double2 v = tp[i];
+    a += v.x;
+    b += v.y;
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    red[wid] = a;
+    red[nw + wid] = b;
+  }
+  __syncthreads();
+  double2 tot = make_double2(0.0, 0.0);
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nw; ++w) {
+      tot.x += red[w];
+      tot.y += red[nw + w];
+    }
+  __syncthreads();
+  return tot;
+}
+
 __device__ double block_sum_tiles(const DevCluster& C, int which, double* red) {
   double v = 0.0;
   for (int i = threadIdx.x; i < C.n_tiles; i += blockDim.x) v += C.tilepart[2 * i + which];
@@ -1264,8 +1293,8 @@ __global__ void __launch_bounds__(256) k_cost_init(BatchView bv) {
 // ------------------------------------------------------------------ K6
 
 template <bool MIXED>
-__global__ void __launch_bounds__(256) k_lm_update(BatchView bv) {
-  __shared__ double red[8];
+__global__ void __launch_bounds__(1024) k_lm_update(BatchView bv) {
+  __shared__ double red[64];
   __shared__ int s_cur, s_act;
   for (int s = blockIdx.x; s < bv.n; s += gridDim.x) {
     const DevCluster& C = bv.cl[s];
@@ -1274,8 +1303,9 @@ __global__ void __launch_bounds__(256) k_lm_update(BatchView bv) {
     const bool ok = lm->status == 0;
     double Fo = 0.0, pp = 0.0;
     if (ok) {
-      Fo = block_sum_tiles(C, 0, red);
-      pp = block_sum_tiles(C, 1, red);
+      const double2 t = block_sum_tiles2(C, red);
+      Fo = t.x;
+      pp = t.y;
     }
     if (threadIdx.x == 0) {
       const double F = lm->F;
@@ -1640,7 +1670,7 @@ static void launch_iteration_t(const BatchView& bv, int refine_steps, cudaStream
   if (big)
     for (const BigRef& b : *big) launch_big_solve(b, MIXED, refine_steps, 0, st);
   LAUNCH(KK_BACKSUB, st, k_backsub_cost<MIXED><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
-  LAUNCH(KK_LM_UPDATE, st, k_lm_update<MIXED><<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv));
+  LAUNCH(KK_LM_UPDATE, st, k_lm_update<MIXED><<<grid_for(bv.n, 1, 65535), 1024, 0, st>>>(bv));
 }
 
 void launch_iteration(const BatchView& bv, bool mixed, int refine_steps, cudaStream_t st,
