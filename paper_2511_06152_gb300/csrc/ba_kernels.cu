@@ -673,10 +673,27 @@ __global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed
 
 // ------------------------------------------------------------------ partial sums -> per-camera / per-pair sums
 
+// Running sum of binary32 partials kept in double-float (TwoSum, error-free
+// to ~2^-48 of the total; binary64 adds run at 1/59 of the binary32 rate),
+// or of binary64 partials in binary64.
+struct AccF {
+  dfl v{0.f, 0.f};
+  __device__ __forceinline__ void add(float x) { v = df_add_f(v, x); }
+  __device__ __forceinline__ double get() const { return (double)v.hi + (double)v.lo; }
+};
+struct AccD {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ double get() const { return v; }
+};
+template <typename Real> struct AccOf { using T = AccD; };
+template <> struct AccOf<float> { using T = AccF; };
+
 // Warp per free camera or camera pair of a cluster: sum its chunk partials in
-// chunk order (lane i owns element i and i + 32), in binary64.
+// chunk order (lane i owns element i and i + 32).
 template <typename Real>
 __global__ void __launch_bounds__(256) k_partial_reduce(BatchView bv) {
+  using Acc = typename AccOf<Real>::T;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -695,27 +712,27 @@ __global__ void __launch_bounds__(256) k_partial_reduce(BatchView bv) {
     const Real* part = (const Real*)(cam ? C.campart : C.pairpart);
     double* out = cam ? C.camsum + (size_t)kCamPart * key : C.pairsum + (size_t)kPairPart * key;
     const bool two = lane + 32 < width;
-    double v0 = 0.0, v1 = 0.0;
+    Acc v0, v1;
     int p = b;
     for (; p + 4 <= e; p += 4) {  // four independent loads in flight, added in slot order
       const Real* a0 = part + (size_t)stride * slots[p];
       const Real* a1 = part + (size_t)stride * slots[p + 1];
       const Real* a2 = part + (size_t)stride * slots[p + 2];
       const Real* a3 = part + (size_t)stride * slots[p + 3];
-      const double x0 = lane < width ? (double)a0[lane] : 0.0, x1 = lane < width ? (double)a1[lane] : 0.0;
-      const double x2 = lane < width ? (double)a2[lane] : 0.0, x3 = lane < width ? (double)a3[lane] : 0.0;
-      const double y0 = two ? (double)a0[lane + 32] : 0.0, y1 = two ? (double)a1[lane + 32] : 0.0;
-      const double y2 = two ? (double)a2[lane + 32] : 0.0, y3 = two ? (double)a3[lane + 32] : 0.0;
-      v0 += x0; v0 += x1; v0 += x2; v0 += x3;
-      v1 += y0; v1 += y1; v1 += y2; v1 += y3;
+      const Real x0 = lane < width ? a0[lane] : Real(0), x1 = lane < width ? a1[lane] : Real(0);
+      const Real x2 = lane < width ? a2[lane] : Real(0), x3 = lane < width ? a3[lane] : Real(0);
+      const Real y0 = two ? a0[lane + 32] : Real(0), y1 = two ? a1[lane + 32] : Real(0);
+      const Real y2 = two ? a2[lane + 32] : Real(0), y3 = two ? a3[lane + 32] : Real(0);
+      v0.add(x0); v0.add(x1); v0.add(x2); v0.add(x3);
+      v1.add(y0); v1.add(y1); v1.add(y2); v1.add(y3);
     }
     for (; p < e; ++p) {
       const Real* a0 = part + (size_t)stride * slots[p];
-      if (lane < width) v0 += (double)a0[lane];
-      if (two) v1 += (double)a0[lane + 32];
+      if (lane < width) v0.add(a0[lane]);
+      if (two) v1.add(a0[lane + 32]);
     }
-    if (lane < width) out[lane] = v0;
-    if (two) out[lane + 32] = v1;
+    if (lane < width) out[lane] = v0.get();
+    if (two) out[lane + 32] = v1.get();
   }
 }
 
