@@ -136,6 +136,15 @@ def so3_jr_inv(w):
     return J.reshape(3, 3)
 
 
+def transition(R_old, T_old, w_old, R_new, T_new, w_new):
+    """Eq. 8: weighted average of an overlap image's poses from the previous
+    and the new cluster (weights = its observations in each)."""
+    R, T = np.zeros(9), np.zeros(3)
+    lib().orc_transition(_d(_f64(R_old, (9,))), _d(_f64(T_old, (3,))), ctypes.c_double(w_old),
+                         _d(_f64(R_new, (9,))), _d(_f64(T_new, (3,))), ctypes.c_double(w_new), _d(R), _d(T))
+    return R.reshape(3, 3), T
+
+
 def project(intr, R, T, X):
     uv = np.zeros(2)
     ok = lib().orc_project(_d(_f64(intr)), _d(_f64(R, (9,))), _d(_f64(T)), _d(_f64(X)), _d(uv))

@@ -616,3 +616,26 @@ int orc_lm_run(const orc_problem* P, double* R, double* T, double* X, int iters,
   for (int it = 0; it < iters; ++it) last = orc_lm_step(P, R, T, X, &mu, &nu, trace ? trace + it : NULL);
   return last;
 }
+
+/* Cluster transition, Sec. 3.2 Eq. 8: an overlap image adjusted in both the
+ * previous and the new cluster takes the weighted average of its two poses,
+ * weights in proportion to its feature matches (observations) in each.
+ * Position: the weighted arithmetic mean.  Orientation: the weighted mean on
+ * SO(3), which for two rotations is the point at fraction
+ * t = w_new / (w_old + w_new) along the geodesic from R_old to R_new:
+ * R_old Exp(t Log(R_old^T R_new)). */
+void orc_transition(const double R_old[9], const double T_old[3], double w_old, const double R_new[9],
+                    const double T_new[3], double w_new, double R_out[9], double T_out[3]) {
+  const double t = w_new / (w_old + w_new);
+  double E[9], phi[3], D[9];
+  for (int i = 0; i < 3; ++i)  /* E = R_old^T R_new */
+    for (int j = 0; j < 3; ++j)
+      E[3 * i + j] = R_old[i] * R_new[j] + R_old[3 + i] * R_new[3 + j] + R_old[6 + i] * R_new[6 + j];
+  orc_so3_log(E, phi);
+  for (int i = 0; i < 3; ++i) phi[i] *= t;
+  orc_so3_exp(phi, D);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      R_out[3 * i + j] = R_old[3 * i] * D[j] + R_old[3 * i + 1] * D[3 + j] + R_old[3 * i + 2] * D[6 + j];
+  for (int i = 0; i < 3; ++i) T_out[i] = (w_old * T_old[i] + w_new * T_new[i]) / (w_old + w_new);
+}

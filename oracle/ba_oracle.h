@@ -58,5 +58,8 @@ int orc_lm_step(const orc_problem* P, double* R, double* T, double* X, double* m
                 orc_step_info* info);
 int orc_lm_run(const orc_problem* P, double* R, double* T, double* X, int iters, double mu0,
                orc_step_info* trace);
+/* Eq. 8: weighted pose average of an overlap image (weights w_old, w_new > 0). */
+void orc_transition(const double R_old[9], const double T_old[3], double w_old, const double R_new[9],
+                    const double T_new[3], double w_new, double R_out[9], double T_out[3]);
 
 #endif
