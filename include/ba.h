@@ -186,6 +186,20 @@ BA_API ba_status ba_create_cluster(ba_ctx* ctx, const ba_cluster_desc* d, ba_clu
 BA_API ba_status ba_warm_start(ba_ctx* ctx, ba_cluster_id dst, ba_cluster_id src, const int32_t* cam_map,
                                const int32_t* pt_map);
 
+/* Cluster transition (Sec. 3.2, Eq. 8).  For every image of cluster dst that
+ * is free in dst and mapped to an image of src (cam_map[dst n_cams], host
+ * array: its index in src or -1), its current pose in dst is replaced by the
+ * weighted average of its current poses in src and in dst, the weights being
+ * its numbers of observations in src and in dst: the position is the weighted
+ * mean; the orientation is the point at fraction w_dst / (w_src + w_dst) on
+ * the geodesic from the src orientation to the dst orientation (the weighted
+ * mean on SO(3) of two rotations).  Images fixed in dst keep their pose (they
+ * hold the optimised pose of src already).  Typically called once dst has
+ * been solved.  Neither cluster may be queued or running in the serving
+ * scheduler.  Enqueued on the context's stream.  BA_ERR_NOT_FOUND for an
+ * unknown id, BA_ERR_INVALID for a null map or an index out of range. */
+BA_API ba_status ba_transition(ba_ctx* ctx, ba_cluster_id dst, ba_cluster_id src, const int32_t* cam_map);
+
 /* Evaluate F and the gradient infinity norm at the current state. */
 BA_API ba_status ba_linearize(ba_ctx* ctx, ba_cluster_id id, ba_lin_info* out);
 

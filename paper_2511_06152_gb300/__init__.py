@@ -93,7 +93,7 @@ class ba_cluster_info(ctypes.Structure):
 
 EXPORTS = ["ba_init", "ba_create_cluster", "ba_linearize", "ba_solve_step", "ba_run", "ba_solve_batch", "ba_reset",
            "ba_reset_batch", "ba_submit", "ba_poll", "ba_get_state", "ba_reprojection_errors", "ba_memory_in_use",
-           "ba_launch_count", "ba_kernel_stats", "ba_cost_noalloc", "ba_warm_start", "ba_get_cluster_info", "ba_destroy_cluster", "ba_shutdown",
+           "ba_launch_count", "ba_kernel_stats", "ba_cost_noalloc", "ba_warm_start", "ba_transition", "ba_get_cluster_info", "ba_destroy_cluster", "ba_shutdown",
            "ba_status_string", "ba_last_error"]
 
 _lib = None
@@ -125,6 +125,7 @@ def lib(build: bool = True):
             L.ba_kernel_stats.argtypes = [vp, _dp, ctypes.POINTER(u64), ctypes.c_int32, ctypes.c_int32]
             L.ba_cost_noalloc.argtypes = [ctypes.POINTER(ba_cluster_desc), vp, _dp]
             L.ba_warm_start.argtypes = [vp, u64, u64, _ip, _ip]
+            L.ba_transition.argtypes = [vp, u64, u64, _ip]
             L.ba_submit.argtypes = [vp, u64, ctypes.POINTER(ba_solve_opts), ctypes.POINTER(u64)]
             L.ba_poll.argtypes = [vp, u64, ctypes.POINTER(ba_result)]
             L.ba_get_state.argtypes = [vp, u64, _dp, _dp, _dp, ctypes.c_int32]
@@ -314,6 +315,12 @@ class Context:
         v = ctypes.c_uint64()
         _check(self.L.ba_memory_in_use(self.h, ctypes.byref(v)), self.h, "ba_memory_in_use")
         return v.value
+
+    def transition(self, dst, src, cam_map):
+        """Eq. 8: blend the poses of the images of dst shared with src (free in
+        dst) by their observation counts in both clusters."""
+        m = np.ascontiguousarray(cam_map, dtype=np.int32)
+        _check(self.L.ba_transition(self.h, dst, src, m.ctypes.data_as(_ip)), self.h, "ba_transition")
 
     def cluster_info(self, cid):
         """Table sizes of a cluster (units of work per LM iteration)."""

@@ -762,6 +762,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const size_t o_free = Lo.add(sizeof(int) * nc);
   const size_t o_cof = Lo.add(sizeof(int) * nf);
   const size_t o_fpos = Lo.add(sizeof(int) * nf);
+  const size_t o_cnobs = Lo.add(sizeof(int) * nc);
   const size_t o_envf = Lo.add(sizeof(int) * nf);
   const size_t o_tiles = Lo.add(sizeof(Tile) * tiles.size());
   const size_t o_ocam = Lo.add(sizeof(int) * (size_t)no);
@@ -836,6 +837,11 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   put(o_free, free_idx.data(), sizeof(int) * nc);
   put(o_cof, cam_of_free.data(), sizeof(int) * nf);
   put(o_fpos, fpos.data(), sizeof(int) * nf);
+  {
+    std::vector<int> cnobs(nc, 0);
+    for (int i = 0; i < no; ++i) ++cnobs[ocam[i]];
+    put(o_cnobs, cnobs.data(), sizeof(int) * nc);
+  }
   put(o_envf, env_first.data(), sizeof(int) * nf);
   put(o_tiles, tiles.data(), sizeof(Tile) * tiles.size());
   put(o_ocam, pcam.data(), sizeof(int) * (size_t)no);
@@ -939,6 +945,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   h.free_idx = (const int*)(arena + o_free);
   h.cam_of_free = (const int*)(arena + o_cof);
   h.fpos = (const int*)(arena + o_fpos);
+  h.cam_nobs = (const int*)(arena + o_cnobs);
   h.env_first = (const int*)(arena + o_envf);
   h.F = big ? (double*)(arena + o_F) : nullptr;
   h.bx = big ? (double*)(arena + o_bx) : nullptr;
@@ -1337,6 +1344,31 @@ BA_API ba_status ba_warm_start(ba_ctx* ctx, ba_cluster_id dst, ba_cluster_id src
   if (st != BA_OK) return st;
   launch_camreal(one_view(c->d_desc, c->nf), ctx->mixed, ctx->stream);
   note_direct(ctx);
+  CUDA_TRY(ctx, cudaGetLastError());
+  return BA_OK;
+}
+
+BA_API ba_status ba_transition(ba_ctx* ctx, ba_cluster_id dst, ba_cluster_id src, const int32_t* cam_map) {
+  if (!ctx || !cam_map) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  Cluster* c = find_cluster(ctx, dst);
+  Cluster* s = find_cluster(ctx, src);
+  if (!c || !s) return BA_ERR_NOT_FOUND;
+  if (c->in_service || s->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
+  std::vector<int2> pairs;
+  for (int k = 0; k < c->nc; ++k) {
+    const int m = cam_map[k];
+    if (m < -1 || m >= s->nc) return set_err(ctx, BA_ERR_INVALID, "cam_map index out of range");
+    if (m >= 0) pairs.push_back(make_int2(k, m));
+  }
+  if (pairs.empty()) return BA_OK;
+  int2* dp = nullptr;
+  CUDA_TRY(ctx, cudaMallocAsync((void**)&dp, sizeof(int2) * pairs.size(), ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(dp, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice, ctx->stream));
+  launch_transition(c->d_desc, s->d_desc, dp, (int)pairs.size(), ctx->stream);
+  launch_camreal(one_view(c->d_desc, c->nf), ctx->mixed, ctx->stream);  // camera records of the new poses
+  note_direct(ctx);
+  CUDA_TRY(ctx, cudaFreeAsync(dp, ctx->stream));
   CUDA_TRY(ctx, cudaGetLastError());
   return BA_OK;
 }

@@ -126,6 +126,7 @@ struct DevCluster {
   const int* pt_perm;      // [np] internal point -> caller's point index
   const int* free_idx;     // [nc] -> free index or -1
   const int* cam_of_free;  // [nf]
+  const int* cam_nobs;     // [nc] observations of each camera
   // elimination order of the reduced camera system: free image f sits at
   // block position fpos[f]; env_first[p] = first block column of block row
   // p inside the envelope of S (and of its Cholesky factor)
@@ -245,6 +246,8 @@ cudaError_t set_big_attributes(int max_n);
 cudaError_t set_kernel_attributes(int max_n);
 void launch_arm(const BatchView& bv, int iters, cudaStream_t st);
 void launch_arm_slots(const BatchView& bv, const int* arm, cudaStream_t st);
+// Eq. 8 on the (dst camera, src camera) pairs of pairs[n]
+void launch_transition(const DevCluster* dst, const DevCluster* src, const int2* pairs, int n, cudaStream_t st);
 void launch_warm_copy(const DevCluster* dst, const DevCluster* src, const int2* cams, int n_cams, const int2* pts,
                       int n_pts, cudaStream_t st);
 void launch_reset(const BatchView& bv, bool mixed, cudaStream_t st);

@@ -1472,6 +1472,38 @@ __global__ void k_arm_slots(BatchView bv, const int* arm) {
 // cams / pts hold (dst index, src index) pairs in internal order.  The copy is
 // representation-agnostic (8-byte words), so both clusters must use the same
 // precision.
+// Cluster transition (Sec. 3.2, Eq. 8): an image free in dst and shared with
+// src takes the weighted average of its two current poses, weights = its
+// observations in each cluster; orientation at fraction w_dst / (w_src +
+// w_dst) along the geodesic from the src orientation, position the weighted
+// mean.  Binary64.  pairs[i] = (camera in dst, camera in src).
+__global__ void k_transition(const DevCluster* dst, const DevCluster* src, const int2* pairs, int n) {
+  const DevCluster& D = *dst;
+  const DevCluster& S = *src;
+  const int dcur = D.lm->cur, scur = S.lm->cur;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int kd = pairs[i].x, ks = pairs[i].y;
+    if (D.free_idx[kd] < 0) continue;  // fixed in dst: already the src pose
+    const double wo = (double)S.cam_nobs[ks], wn = (double)D.cam_nobs[kd];
+    if (!(wo + wn > 0.0)) continue;
+    const double t = wn / (wo + wn);
+    const double* Ro = S.R + ((size_t)scur * S.n_cams + ks) * 9;
+    const double* To = S.T + ((size_t)scur * S.n_cams + ks) * 3;
+    double* Rn = D.R + ((size_t)dcur * D.n_cams + kd) * 9;
+    double* Tn = D.T + ((size_t)dcur * D.n_cams + kd) * 3;
+    double E[9], phi[3], Q[9], Rm[9];
+    for (int a = 0; a < 3; ++a)  // E = Ro^T Rn
+      for (int b = 0; b < 3; ++b) E[3 * a + b] = Ro[a] * Rn[b] + Ro[3 + a] * Rn[3 + b] + Ro[6 + a] * Rn[6 + b];
+    so3_log(E, phi);
+    for (int a = 0; a < 3; ++a) phi[a] *= t;
+    so3_exp(phi, Q);
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) Rm[3 * a + b] = Ro[3 * a] * Q[b] + Ro[3 * a + 1] * Q[3 + b] + Ro[3 * a + 2] * Q[6 + b];
+    for (int a = 0; a < 9; ++a) Rn[a] = Rm[a];
+    for (int a = 0; a < 3; ++a) Tn[a] = (wo * To[a] + wn * Tn[a]) / (wo + wn);
+  }
+}
+
 __global__ void k_warm_copy(const DevCluster* dst, const DevCluster* src, const int2* cams, int n_cams,
                             const int2* pts, int n_pts) {
   const int scur = src->lm->cur;
@@ -1626,6 +1658,10 @@ void launch_warm_copy(const DevCluster* dst, const DevCluster* src, const int2* 
   const int n = n_pts > n_cams ? n_pts : n_cams;
   LAUNCH(KK_OTHER, st,
          k_warm_copy<<<grid_for(n, 256, num_sms() * 4), 256, 0, st>>>(dst, src, cams, n_cams, pts, n_pts));
+}
+
+void launch_transition(const DevCluster* dst, const DevCluster* src, const int2* pairs, int n, cudaStream_t st) {
+  LAUNCH(KK_OTHER, st, k_transition<<<grid_for(n, 128, 1024), 128, 0, st>>>(dst, src, pairs, n));
 }
 
 void launch_camreal(const BatchView& bv, bool mixed, cudaStream_t st) {

@@ -187,3 +187,36 @@ def test_creation_in_threads_while_serving_equals_alone():
         for w in range(len(flights[f])):
             for a, b in zip(alone[f][w], got[f][w]):
                 assert np.array_equal(a, b), (f, w)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_transition_matches_oracle(precision):
+    """Eq. 8 on the device equals the oracle's weighted pose average for every
+    free overlap image; every other image keeps its pose."""
+    import oracle as O
+    import paper_2511_06152_gb300 as ba
+    wins = _flight(9121)
+    (c0, cams0, pts0), (c1, cams1, pts1) = wins[0], wins[1]
+    cm, pm = sg.warm_maps(cams0, pts0, cams1, pts1)
+    with ba.Context(precision=ba.BA_MIXED if precision == "mixed" else ba.BA_FP64) as ctx:
+        a = ctx.create_cluster(c0)
+        ctx.run(a, ITERS, trace=False)
+        b = ctx.create_cluster(c1, warm_from=a, warm_cam_map=cm, warm_pt_map=pm)
+        ctx.run(b, ITERS, trace=False)
+        Ra, Ta, _ = ctx.get_state(a)
+        Rb, Tb, _ = ctx.get_state(b)
+        ctx.transition(b, a, cm)
+        R2, T2, _ = ctx.get_state(b)
+    wa = np.bincount(c0["obs_cam"], minlength=c0["n_cams"])
+    wb = np.bincount(c1["obs_cam"], minlength=c1["n_cams"])
+    blended = 0
+    for k in range(c1["n_cams"]):
+        m = cm[k]
+        if m < 0 or c1["fixed"][k]:
+            assert np.array_equal(R2[k], Rb[k]) and np.array_equal(T2[k], Tb[k])
+            continue
+        R, T = O.transition(Ra[m], Ta[m], float(wa[m]), Rb[k], Tb[k], float(wb[k]))
+        np.testing.assert_allclose(R2[k].reshape(3, 3), R, atol=1e-13)
+        np.testing.assert_allclose(T2[k], T, rtol=0, atol=1e-9)
+        blended += 1
+    assert blended >= 1
