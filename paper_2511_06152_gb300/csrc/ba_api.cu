@@ -632,34 +632,40 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
         local_pair_of[key] = -1;
       }
       ch.n_lp = (int)order.size();
-      // lanes per job in proportion to its cost (camera item ~135, pair item
-      // ~160 instructions), at least one each; jobs beyond the thread count run
-      // one lane each (the kernel's fallback mode)
+      // Lanes per job: every lane of every job gets about the same work, a
+      // quantum Q of instructions (camera item ~165, pair item ~123), the
+      // smallest Q whose lanes fit the CTA; the pair jobs start on a warp
+      // boundary so that no warp runs both loop bodies.  A job has at least
+      // one lane and at most one per item; chunks with more jobs than threads
+      // run one lane per job (the kernel's fallback mode).
       const int nj = ch.n_lc + ch.n_lp;
       ch.mjob_begin = (int)mjobs.size();
       if (nj > 0 && nj <= kChunkThreads) {
         std::vector<double> cost(nj);
-        double tot = 0.0;
-        for (int q = 0; q < nj; ++q) {
-          cost[q] = jobs[ch.job_begin + q].count * (q < ch.n_lc ? 135.0 : 160.0);
-          tot += cost[q];
-        }
+        for (int q = 0; q < nj; ++q) cost[q] = jobs[ch.job_begin + q].count * (q < ch.n_lc ? 165.0 : 123.0);
         std::vector<int> lanes(nj);
-        int used = 0;
-        for (int q = 0; q < nj; ++q) {
-          lanes[q] = std::max(1, (int)(cost[q] * kChunkThreads / std::max(tot, 1.0)));
-          lanes[q] = std::min(lanes[q], std::max(1, jobs[ch.job_begin + q].count));
-          used += lanes[q];
+        auto alloc = [&](double Q, bool align) {
+          int nc = 0, np_ = 0;
+          for (int q = 0; q < nj; ++q) {
+            const int cnt = jobs[ch.job_begin + q].count;
+            int l = (int)std::ceil(cost[q] / Q);
+            l = std::max(1, std::min(l, std::max(1, cnt)));
+            lanes[q] = l;
+            (q < ch.n_lc ? nc : np_) += l;
+          }
+          return (align && ch.n_lp > 0 ? (nc + 31) / 32 * 32 : nc) + np_;
+        };
+        bool align = alloc(1e300, true) <= kChunkThreads;  // one lane each must fit
+        double lo = 0.0, hi = 1.0;
+        for (int q = 0; q < nj; ++q) hi = std::max(hi, cost[q]);
+        for (int it = 0; it < 60; ++it) {  // smallest quantum that fits
+          const double mid = 0.5 * (lo + hi);
+          if (mid > 0.0 && alloc(mid, align) <= kChunkThreads) hi = mid; else lo = mid;
         }
-        while (used > kChunkThreads) {  // trim the widest job (lowest index on ties)
-          int w = 0;
-          for (int q = 1; q < nj; ++q)
-            if (lanes[q] > lanes[w]) w = q;
-          --lanes[w];
-          --used;
-        }
+        alloc(hi, align);
         int lb = 0;
         for (int q = 0; q < nj; ++q) {
+          if (align && q == ch.n_lc && q > 0) lb = (lb + 31) / 32 * 32;
           Job& jb = jobs[ch.job_begin + q];
           jb.lane_begin = (short)lb;
           jb.n_lanes = (short)lanes[q];
