@@ -20,10 +20,7 @@
 
 namespace bagpu {
 
-constexpr int kSrec = 36;         // per-observation shared record: Jc[12], Z[18], r[2], q[3], pad
-constexpr int kSrecZ = 12;
-constexpr int kSrecR = 30;
-constexpr int kSrecQ = 32;
+constexpr int kSrec = 28;         // per-observation shared record: Jc[12], P[6], r[2], u[2], W[3], pad
 #ifndef BA_LIN_SCHUR_MIN_BLOCKS
 #define BA_LIN_SCHUR_MIN_BLOCKS 2
 #endif

@@ -169,6 +169,7 @@ struct TileLin {
   bool act, head;
   int o, k, j, seg_start, seg_end, span;
   Real Jc[12], r0, r1, Z[18];
+  Real P[6];  // P = Jp M^T (2x3, row-major), so that Z = Jc^T P
   Real m00, m10, m11, m20, m21, m22, q0, q1, q2;
   Real d0, d1, d2, g0, g1, g2;
 };
@@ -192,7 +193,7 @@ __device__ __forceinline__ ObsView global_view(const DevCluster& C, int cur) {
 
 // Linearise one tile (one warp).  The same arithmetic wherever it is called
 // (the back-substitution linearises again rather than storing the result).
-template <bool MIXED>
+template <bool MIXED, bool WANT_Z = true>
 __device__ __forceinline__ void linearize_tile(const DevCluster& C, LmState* lm, const Tile& tl, int lane,
                                                bool report_fail, TileLin<MIXED>& L, const ObsView& V) {
   using Real = typename RealOf<MIXED>::T;
@@ -323,91 +324,91 @@ __device__ __forceinline__ void linearize_tile(const DevCluster& C, LmState* lm,
   const Real P10 = Jp[3] * L.m00;
   const Real P11 = Jp[3] * L.m10 + Jp[4] * L.m11;
   const Real P12 = Jp[3] * L.m20 + Jp[4] * L.m21 + Jp[5] * L.m22;
+  L.P[0] = P00; L.P[1] = P01; L.P[2] = P02;
+  L.P[3] = P10; L.P[4] = P11; L.P[5] = P12;
+  if constexpr (WANT_Z) {
 #pragma unroll
-  for (int m = 0; m < 6; ++m) {
-    L.Z[3 * m + 0] = L.Jc[m] * P00 + L.Jc[6 + m] * P10;
-    L.Z[3 * m + 1] = L.Jc[m] * P01 + L.Jc[6 + m] * P11;
-    L.Z[3 * m + 2] = L.Jc[m] * P02 + L.Jc[6 + m] * P12;
+    for (int m = 0; m < 6; ++m) {
+      L.Z[3 * m + 0] = L.Jc[m] * P00 + L.Jc[6 + m] * P10;
+      L.Z[3 * m + 1] = L.Jc[m] * P01 + L.Jc[6 + m] * P11;
+      L.Z[3 * m + 2] = L.Jc[m] * P02 + L.Jc[6 + m] * P12;
+    }
   }
 }
 
 // ------------------------------------------------------------------ K1: linearise + Schur reductions, one CTA per chunk
 
-// Shared record of one observation, kSrec = 36 Real, 16-byte aligned:
-// Jc [0, 12), Z [12, 30), r [30, 32), q [32, 35), one pad.
-__device__ __forceinline__ void ld_rec_jc(const float* r, float Jc[12]) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const float4 v = reinterpret_cast<const float4*>(r)[i];
-    Jc[4 * i] = v.x; Jc[4 * i + 1] = v.y; Jc[4 * i + 2] = v.z; Jc[4 * i + 3] = v.w;
-  }
+// Shared record of one observation, kSrec = 28 Real, 16-byte aligned:
+// Jc [0, 12), P [12, 18) (P = Jp M^T, 2x3), r [18, 20), u = P q [20, 22),
+// W = I - P P^T as (w00, w01, w11) [22, 25), pad.  Since Z = Jc^T P, the
+// observation's share of the image block is Jc^T Jc - Z Z^T = Jc^T W Jc, of
+// the right-hand side Z q = Jc^T u, and of a pair block
+// Z_a Z_b^T = Jc_a^T (P_a P_b^T) Jc_b.
+__device__ __forceinline__ void ld4(const float* r, int at, float* o) {
+  const float4 v = *reinterpret_cast<const float4*>(r + at);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
 }
-__device__ __forceinline__ void ld_rec_jc(const double* r, double Jc[12]) {
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    const double2 v = reinterpret_cast<const double2*>(r)[i];
-    Jc[2 * i] = v.x; Jc[2 * i + 1] = v.y;
-  }
-}
-// Z (18 values from offset kSrecZ = 12)
-__device__ __forceinline__ void ld_rec_z(const float* r, float Z[18]) {
-  const float4* q = reinterpret_cast<const float4*>(r + kSrecZ);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float4 v = q[i];
-    Z[4 * i] = v.x; Z[4 * i + 1] = v.y; Z[4 * i + 2] = v.z; Z[4 * i + 3] = v.w;
-  }
-  const float2 t = reinterpret_cast<const float2*>(r + kSrecZ + 16)[0];
-  Z[16] = t.x; Z[17] = t.y;
-}
-__device__ __forceinline__ void ld_rec_z(const double* r, double Z[18]) {
-  const double2* q = reinterpret_cast<const double2*>(r + kSrecZ);
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const double2 v = q[i];
-    Z[2 * i] = v.x; Z[2 * i + 1] = v.y;
-  }
-}
-// r (2) and q (3)
-__device__ __forceinline__ void ld_rec_rq(const float* r, float& r0, float& r1, float& q0, float& q1, float& q2) {
-  const float2 a = reinterpret_cast<const float2*>(r + kSrecR)[0];
-  const float4 b = reinterpret_cast<const float4*>(r + kSrecQ)[0];
-  r0 = a.x; r1 = a.y; q0 = b.x; q1 = b.y; q2 = b.z;
-}
-__device__ __forceinline__ void ld_rec_rq(const double* r, double& r0, double& r1, double& q0, double& q1,
-                                          double& q2) {
-  const double2 a = reinterpret_cast<const double2*>(r + kSrecR)[0];
-  const double2 b = reinterpret_cast<const double2*>(r + kSrecQ)[0];
-  r0 = a.x; r1 = a.y; q0 = b.x; q1 = b.y; q2 = r[kSrecQ + 2];
+__device__ __forceinline__ void ld4(const double* r, int at, double* o) {
+  const double2 a = *reinterpret_cast<const double2*>(r + at);
+  const double2 b = *reinterpret_cast<const double2*>(r + at + 2);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
 }
 
-// Store one observation's record (vector stores).
-__device__ __forceinline__ void st_rec(float* r, const TileLin<true>& L) {
-  float4* v = reinterpret_cast<float4*>(r);
-  v[0] = make_float4(L.Jc[0], L.Jc[1], L.Jc[2], L.Jc[3]);
-  v[1] = make_float4(L.Jc[4], L.Jc[5], L.Jc[6], L.Jc[7]);
-  v[2] = make_float4(L.Jc[8], L.Jc[9], L.Jc[10], L.Jc[11]);
-  v[3] = make_float4(L.Z[0], L.Z[1], L.Z[2], L.Z[3]);
-  v[4] = make_float4(L.Z[4], L.Z[5], L.Z[6], L.Z[7]);
-  v[5] = make_float4(L.Z[8], L.Z[9], L.Z[10], L.Z[11]);
-  v[6] = make_float4(L.Z[12], L.Z[13], L.Z[14], L.Z[15]);
-  v[7] = make_float4(L.Z[16], L.Z[17], L.r0, L.r1);
-  v[8] = make_float4(L.q0, L.q1, L.q2, 0.f);
+// Jc (12) and P (6)
+template <typename Real>
+__device__ __forceinline__ void ld_rec_jcp(const Real* r, Real Jc[12], Real P[6]) {
+  ld4(r, 0, Jc);
+  ld4(r, 4, Jc + 4);
+  ld4(r, 8, Jc + 8);
+  Real t[4];
+  ld4(r, 12, P);
+  ld4(r, 16, t);
+  P[4] = t[0];
+  P[5] = t[1];
 }
-__device__ __forceinline__ void st_rec(double* r, const TileLin<false>& L) {
-  double2* v = reinterpret_cast<double2*>(r);
+// Jc (12), r (2), u (2), W (3)
+template <typename Real>
+__device__ __forceinline__ void ld_rec_cam(const Real* r, Real Jc[12], Real rr[2], Real u[2], Real w[3]) {
+  ld4(r, 0, Jc);
+  ld4(r, 4, Jc + 4);
+  ld4(r, 8, Jc + 8);
+  Real a[4], b[4], c[4];
+  ld4(r, 16, a);
+  ld4(r, 20, b);
+  ld4(r, 24, c);
+  rr[0] = a[2]; rr[1] = a[3];
+  u[0] = b[0]; u[1] = b[1];
+  w[0] = b[2]; w[1] = b[3]; w[2] = c[0];
+}
+
+// Store one observation's record (vector stores): Jc, P, r, u = P q and
+// W = I - P P^T.
+template <bool MIXED>
+__device__ __forceinline__ void st_rec(typename RealOf<MIXED>::T* r, const TileLin<MIXED>& L) {
+  using Real = typename RealOf<MIXED>::T;
+  const Real* P = L.P;
+  const Real u0 = P[0] * L.q0 + P[1] * L.q1 + P[2] * L.q2;
+  const Real u1 = P[3] * L.q0 + P[4] * L.q1 + P[5] * L.q2;
+  const Real w00 = Real(1) - (P[0] * P[0] + P[1] * P[1] + P[2] * P[2]);
+  const Real w01 = -(P[0] * P[3] + P[1] * P[4] + P[2] * P[5]);
+  const Real w11 = Real(1) - (P[3] * P[3] + P[4] * P[4] + P[5] * P[5]);
+  const Real v[28] = {L.Jc[0], L.Jc[1], L.Jc[2], L.Jc[3], L.Jc[4], L.Jc[5], L.Jc[6], L.Jc[7], L.Jc[8], L.Jc[9],
+                      L.Jc[10], L.Jc[11], P[0], P[1], P[2], P[3], P[4], P[5], L.r0, L.r1, u0, u1, w00, w01,
+                      w11, Real(0), Real(0), Real(0)};
+  if constexpr (MIXED) {
+    float4* o = reinterpret_cast<float4*>(r);
 #pragma unroll
-  for (int i = 0; i < 6; ++i) v[i] = make_double2(L.Jc[2 * i], L.Jc[2 * i + 1]);
+    for (int i = 0; i < 7; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  } else {
+    double2* o = reinterpret_cast<double2*>(r);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) v[6 + i] = make_double2(L.Z[2 * i], L.Z[2 * i + 1]);
-  v[15] = make_double2(L.r0, L.r1);
-  v[16] = make_double2(L.q0, L.q1);
-  v[17] = make_double2(L.q2, 0.0);
+    for (int i = 0; i < 14; ++i) o[i] = make_double2(v[2 * i], v[2 * i + 1]);
+  }
 }
 
 // One job's sums over its items [i0, i1).  Image job: the upper triangle of
-// sum (Jc^T Jc - Z Z^T) (21), -sum Jc^T r (6), sum Z q (6), diag sum Jc^T Jc
-// (6).  Pair job: sum Z_a Z_b^T (36, row-major).
+// sum Jc^T W Jc (21), -sum Jc^T r (6), sum Jc^T u (6), diag sum Jc^T Jc (6).
+// Pair job: sum Jc_a^T (P_a P_b^T) Jc_b (36, row-major).
 template <typename Real>
 __device__ __forceinline__ void job_sums(const DevCluster& C, const Job& J, bool cam, int i0, int i1,
                                          const Real* srec, Real acc[39]) {
@@ -416,46 +417,47 @@ __device__ __forceinline__ void job_sums(const DevCluster& C, const Job& J, bool
   if (cam) {
     for (int e = i0; e < i1; ++e) {
       const Real* r = srec + (size_t)C.cm_list[J.item_begin + e] * kSrec;
-      Real r0, r1, q0, q1, q2;
-      ld_rec_rq(r, r0, r1, q0, q1, q2);
-      {  // terms of Jc (fewer live registers than both blocks at once)
-        Real Jc[12];
-        ld_rec_jc(r, Jc);
-        int t = 0;
+      Real Jc[12], rr[2], u[2], w[3];
+      ld_rec_cam(r, Jc, rr, u, w);
+      Real WJ0[6], WJ1[6];
 #pragma unroll
-        for (int a = 0; a < 6; ++a)
-#pragma unroll
-          for (int b = a; b < 6; ++b) acc[t++] += Jc[a] * Jc[b] + Jc[6 + a] * Jc[6 + b];
-#pragma unroll
-        for (int a = 0; a < 6; ++a) {
-          acc[21 + a] -= Jc[a] * r0 + Jc[6 + a] * r1;
-          acc[33 + a] += Jc[a] * Jc[a] + Jc[6 + a] * Jc[6 + a];
-        }
+      for (int m = 0; m < 6; ++m) {
+        WJ0[m] = w[0] * Jc[m] + w[1] * Jc[6 + m];
+        WJ1[m] = w[1] * Jc[m] + w[2] * Jc[6 + m];
       }
-      {  // terms of Z
-        Real Z[18];
-        ld_rec_z(r, Z);
-        int t = 0;
+      int t = 0;
 #pragma unroll
-        for (int a = 0; a < 6; ++a)
+      for (int a = 0; a < 6; ++a)
 #pragma unroll
-          for (int b = a; b < 6; ++b)
-            acc[t++] -= Z[3 * a] * Z[3 * b] + Z[3 * a + 1] * Z[3 * b + 1] + Z[3 * a + 2] * Z[3 * b + 2];
+        for (int b = a; b < 6; ++b) acc[t++] += Jc[a] * WJ0[b] + Jc[6 + a] * WJ1[b];
 #pragma unroll
-        for (int a = 0; a < 6; ++a) acc[27 + a] += Z[3 * a] * q0 + Z[3 * a + 1] * q1 + Z[3 * a + 2] * q2;
+      for (int a = 0; a < 6; ++a) {
+        acc[21 + a] -= Jc[a] * rr[0] + Jc[6 + a] * rr[1];
+        acc[27 + a] += Jc[a] * u[0] + Jc[6 + a] * u[1];
+        acc[33 + a] += Jc[a] * Jc[a] + Jc[6 + a] * Jc[6 + a];
       }
     }
   } else {
     for (int e = i0; e < i1; ++e) {
-      const unsigned int u = C.pent[J.item_begin + e];
-      Real Za[18], Zb[18];
-      ld_rec_z(srec + (size_t)(u & 0xffffu) * kSrec, Za);
-      ld_rec_z(srec + (size_t)(u >> 16) * kSrec, Zb);
+      const unsigned int it = C.pent[J.item_begin + e];
+      Real Ja[12], Pa[6], Jb[12], Pb[6];
+      ld_rec_jcp(srec + (size_t)(it & 0xffffu) * kSrec, Ja, Pa);
+      ld_rec_jcp(srec + (size_t)(it >> 16) * kSrec, Jb, Pb);
+      // G = P_a P_b^T (2x2), H = G Jc_b (2x6)
+      const Real g00 = Pa[0] * Pb[0] + Pa[1] * Pb[1] + Pa[2] * Pb[2];
+      const Real g01 = Pa[0] * Pb[3] + Pa[1] * Pb[4] + Pa[2] * Pb[5];
+      const Real g10 = Pa[3] * Pb[0] + Pa[4] * Pb[1] + Pa[5] * Pb[2];
+      const Real g11 = Pa[3] * Pb[3] + Pa[4] * Pb[4] + Pa[5] * Pb[5];
+      Real H0[6], H1[6];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        H0[m] = g00 * Jb[m] + g01 * Jb[6 + m];
+        H1[m] = g10 * Jb[m] + g11 * Jb[6 + m];
+      }
 #pragma unroll
       for (int a = 0; a < 6; ++a)
 #pragma unroll
-        for (int b = 0; b < 6; ++b)
-          acc[6 * a + b] += Za[3 * a] * Zb[3 * b] + Za[3 * a + 1] * Zb[3 * b + 1] + Za[3 * a + 2] * Zb[3 * b + 2];
+        for (int b = 0; b < 6; ++b) acc[6 * a + b] += Ja[a] * H0[b] + Ja[6 + a] * H1[b];
     }
   }
 }
@@ -598,8 +600,8 @@ __global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed
       for (int t = warp; t < ch.n_tiles; t += nw) {
         const Tile tl = C.tiles[ch.tile_begin + t];
         TileLin<MIXED> L;
-        linearize_tile<MIXED>(C, lm, tl, lane, true, L, V);
-        if (L.act) st_rec(srec + (size_t)(L.o - ch.obs_begin) * kSrec, L);
+        linearize_tile<MIXED, false>(C, lm, tl, lane, true, L, V);
+        if (L.act) st_rec<MIXED>(srec + (size_t)(L.o - ch.obs_begin) * kSrec, L);
         if (diag) {  // largest |g_p| of the tile, for the gradient norm
           double gm = L.head ? fmax(fabs((double)L.g0), fmax(fabs((double)L.g1), fabs((double)L.g2))) : 0.0;
 #pragma unroll
@@ -1081,11 +1083,11 @@ __global__ void __launch_bounds__(256) k_backsub_cost(BatchView bv) {
     const int local = g - bv.tile_pre[s];
     const Tile tl = C.tiles[local];
     TileLin<MIXED> L;
-    linearize_tile<MIXED>(C, lm, tl, lane, false, L, global_view(C, lm->cur));
+    linearize_tile<MIXED, false>(C, lm, tl, lane, false, L, global_view(C, lm->cur));
     const int cur = lm->cur;
     Real mu_r;
     if constexpr (MIXED) mu_r = lm->mu_f; else mu_r = lm->mu;
-    // t = Z^T dc_k
+    // t = Z^T dc_k = P^T (Jc dc_k)
     Real t0 = 0, t1 = 0, t2 = 0;
     const int f = L.act ? C.free_idx[L.k] : -1;
     if (f >= 0) {
@@ -1098,12 +1100,15 @@ __global__ void __launch_bounds__(256) k_backsub_cost(BatchView bv) {
 #pragma unroll
         for (int m = 0; m < 6; ++m) d[m] = C.dc[6 * f + m];
       }
+      Real u0 = 0, u1 = 0;
 #pragma unroll
       for (int m = 0; m < 6; ++m) {
-        t0 += L.Z[3 * m] * d[m];
-        t1 += L.Z[3 * m + 1] * d[m];
-        t2 += L.Z[3 * m + 2] * d[m];
+        u0 += L.Jc[m] * d[m];
+        u1 += L.Jc[6 + m] * d[m];
       }
+      t0 = L.P[0] * u0 + L.P[3] * u1;
+      t1 = L.P[1] * u0 + L.P[4] * u1;
+      t2 = L.P[2] * u0 + L.P[5] * u1;
     }
     t0 = seg_reduce(t0, lane, L.seg_start, L.seg_end, L.span);
     t1 = seg_reduce(t1, lane, L.seg_start, L.seg_end, L.span);
