@@ -56,6 +56,15 @@ __device__ __forceinline__ dfl df_add(dfl a, dfl b) {
   return fast_two_sum(s.hi, s.lo);
 }
 
+// double-word + double-word, "sloppy" version (Dekker): the low words are
+// added without their own TwoSum.  Relative to max(|a|, |b|) the error stays
+// near 2^-44, but it is not relative to the result: only for sums without
+// heavy cancellation against the needed absolute accuracy.
+__device__ __forceinline__ dfl df_add_fast(dfl a, dfl b) {
+  const dfl s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
 __device__ __forceinline__ dfl df_neg(dfl a) { return dfl{-a.hi, -a.lo}; }
 __device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
 
@@ -89,6 +98,15 @@ __device__ __forceinline__ dfl df_div(dfl a, dfl b) {
   const dfl r = df_sub(a, df_mul_f(b, q1));
   const float q2 = __fdiv_rn(r.hi, b.hi);
   return fast_two_sum(q1, q2);
+}
+
+// 1 / b (b != 0): the binary32 reciprocal r and one Newton correction
+// r + r (1 - b r), with 1 - b.hi r exact (TwoProduct, then Sterbenz).
+__device__ __forceinline__ dfl df_recip(dfl b) {
+  const float r = __frcp_rn(b.hi);
+  const dfl p = two_prod(b.hi, r);
+  const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, p.hi), p.lo), __fmul_rn(b.lo, r));
+  return fast_two_sum(r, __fmul_rn(r, e));
 }
 
 // sqrt of a double-word (a > 0): one Newton correction

@@ -94,28 +94,35 @@ __device__ __forceinline__ const float* camdf_ptr(const DevCluster& C, int buf, 
 }
 
 // Eq. 5 with Brown distortion in double-float: residual (u - cx, v - cy) - c
-// for a double-float point, every term in double-float.
+// for a double-float point, every term in double-float.  X - T and the final
+// difference with the observation, where the result is much smaller than the
+// operands, use the accurate sum; the other sums (the rotation, the
+// distortion terms, all far below the pixel accuracy the cost needs in their
+// cancellation) the sloppy one; one reciprocal of the depth.
 __device__ __forceinline__ bool df_residual(const CamDf& c, dfl X0, dfl X1, dfl X2, dfl c0, dfl c1, dfl& e0,
                                             dfl& e1) {
   const dfl d0 = df_sub(X0, c.T[0]), d1 = df_sub(X1, c.T[1]), d2 = df_sub(X2, c.T[2]);
-  const dfl z = df_add(df_add(df_mul(c.R[2], d0), df_mul(c.R[5], d1)), df_mul(c.R[8], d2));
+  const dfl z = df_add_fast(df_add_fast(df_mul(c.R[2], d0), df_mul(c.R[5], d1)), df_mul(c.R[8], d2));
   if (!(z.hi > (float)kMinDepth)) return false;
-  const dfl x = df_add(df_add(df_mul(c.R[0], d0), df_mul(c.R[3], d1)), df_mul(c.R[6], d2));
-  const dfl y = df_add(df_add(df_mul(c.R[1], d0), df_mul(c.R[4], d1)), df_mul(c.R[7], d2));
-  const dfl xn = df_div(x, z), yn = df_div(y, z);
+  const dfl x = df_add_fast(df_add_fast(df_mul(c.R[0], d0), df_mul(c.R[3], d1)), df_mul(c.R[6], d2));
+  const dfl y = df_add_fast(df_add_fast(df_mul(c.R[1], d0), df_mul(c.R[4], d1)), df_mul(c.R[7], d2));
+  const dfl iz = df_recip(z);
+  const dfl xn = df_mul(x, iz), yn = df_mul(y, iz);
   const dfl xx = df_mul(xn, xn), yy = df_mul(yn, yn), xy2 = df_mul_f(df_mul(xn, yn), 2.0f);
-  const dfl r2 = df_add(xx, yy);
-  const dfl radm1 = df_mul(r2, df_add(c.k1, df_mul(c.k2, r2)));  // rad - 1
-  const dfl ddx = df_add(df_add(df_mul(xn, radm1), df_mul(c.p1, xy2)), df_mul(c.p2, df_add(r2, df_mul_f(xx, 2.0f))));
-  const dfl ddy = df_add(df_add(df_mul(yn, radm1), df_mul(c.p1, df_add(r2, df_mul_f(yy, 2.0f)))), df_mul(c.p2, xy2));
-  e0 = df_sub(df_mul(c.f, df_add(xn, ddx)), c0);
-  e1 = df_sub(df_mul(c.f, df_add(yn, ddy)), c1);
+  const dfl r2 = df_add_fast(xx, yy);
+  const dfl radm1 = df_mul(r2, df_add_fast(c.k1, df_mul(c.k2, r2)));  // rad - 1
+  const dfl ddx = df_add_fast(df_add_fast(df_mul(xn, radm1), df_mul(c.p1, xy2)),
+                              df_mul(c.p2, df_add_fast(r2, df_mul_f(xx, 2.0f))));
+  const dfl ddy = df_add_fast(df_add_fast(df_mul(yn, radm1), df_mul(c.p1, df_add_fast(r2, df_mul_f(yy, 2.0f)))),
+                              df_mul(c.p2, xy2));
+  e0 = df_sub(df_mul(c.f, df_add_fast(xn, ddx)), c0);
+  e1 = df_sub(df_mul(c.f, df_add_fast(yn, ddy)), c1);
   return true;
 }
 
 // 1/2 rho(s) / sigma^2 in double-float, s = e0^2 + e1^2 (Eq. 6: rho on the squared norm)
 __device__ __forceinline__ dfl df_robust_cost(dfl e0, dfl e1, float delta, float half_inv_s2) {
-  const dfl s = df_add(df_mul(e0, e0), df_mul(e1, e1));
+  const dfl s = df_add_fast(df_mul(e0, e0), df_mul(e1, e1));
   const float d2 = delta * delta;
   dfl rho;
   if (s.hi <= d2) {
