@@ -347,6 +347,11 @@ def run_reference(args):
 FLOP_LIN = dict(obs=258, free_obs=294, pair=216, pt=45)
 FLOP_BACK = dict(obs=258 + 63, free_obs=36, pair=0, pt=60)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+# DRAM bytes (read + write) per observation of one k_lin_schur launch, from an
+# ncu capture of the current kernel on 32 clusters of the same mix (87.2 MB for
+# 2,452,644 observations); scaled to a launch by its observations.  Set to
+# None whenever the kernel changes until it is captured again.
+LIN_SCHUR_DRAM_BYTES_PER_OBS = 87.183616e6 / 2452644
 FP64_PEAK_TFLOPS = 1.25                               # nominal dense FP64
 
 
@@ -495,6 +500,10 @@ def main():
                 "algorithmic_flop_per_launch": amount}
         if dom == "lin_schur":
             roof["hbm_gbs_algorithmic"] = lin_schur_bytes(u) / sec / 1e9
+            if LIN_SCHUR_DRAM_BYTES_PER_OBS is not None:
+                roof["traffic"] = LIN_SCHUR_DRAM_BYTES_PER_OBS * u["obs"]
+                roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of a 32-cluster launch, "
+                                          "scaled by observations")
     kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / max(1e-9, sum(
         x[0] for x in kst.values()))} for k, v in kst.items() if v[1]}
 
