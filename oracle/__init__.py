@@ -81,6 +81,9 @@ def lib():
             L.orc_huber_rho.restype = ctypes.c_double
             L.orc_huber_weight.restype = ctypes.c_double
             L.orc_cost.restype = ctypes.c_double
+            L.orc_dsm_height.restype = ctypes.c_double
+            L.orc_quad_overlap.restype = ctypes.c_double
+            L.orc_quad_area.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -134,6 +137,46 @@ def so3_jr_inv(w):
     J = np.zeros(9)
     lib().orc_so3_jr_inv(_d(_f64(w)), _d(J))
     return J.reshape(3, 3)
+
+
+class _Dsm(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("h", _dp)]
+
+
+class Dsm:
+    """A DSM raster (dict h[ny, nx], x0, y0, dx, dy) held for the ctypes struct."""
+
+    def __init__(self, d):
+        self.h = _f64(d["h"])
+        ny, nx = self.h.shape
+        self.s = _Dsm(nx, ny, float(d["x0"]), float(d["y0"]), float(d["dx"]), float(d["dy"]), _d(self.h))
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def dsm_height(dsm: Dsm, x, y):
+    return lib().orc_dsm_height(dsm.ref, ctypes.c_double(x), ctypes.c_double(y))
+
+
+def footprint(intr, width, height, R, T, dsm: Dsm):
+    """Ground points of an image's four corners on the DSM, (4, 3); None for
+    a ray that does not point down."""
+    out = np.zeros(12)
+    st = lib().orc_footprint(_d(_f64(intr, (7,))), ctypes.c_double(width), ctypes.c_double(height),
+                             _d(_f64(R, (9,))), _d(_f64(T, (3,))), dsm.ref, _d(out))
+    return None if st != 0 else out.reshape(4, 3)
+
+
+def quad_overlap(qa, qb):
+    """Area of the intersection of two convex footprints (ground plane)."""
+    return lib().orc_quad_overlap(_d(_f64(qa, (12,))), _d(_f64(qb, (12,))))
+
+
+def quad_area(q):
+    return lib().orc_quad_area(_d(_f64(q, (12,))))
 
 
 def transition(R_old, T_old, w_old, R_new, T_new, w_new):

@@ -639,3 +639,132 @@ void orc_transition(const double R_old[9], const double T_old[3], double w_old, 
       R_out[3 * i + j] = R_old[3 * i] * D[j] + R_old[3 * i + 1] * D[3 + j] + R_old[3 * i + 2] * D[6 + j];
   for (int i = 0; i < 3; ++i) T_out[i] = (w_old * T_old[i] + w_new * T_new[i]) / (w_old + w_new);
 }
+
+/* ---- Image footprints on a DSM (Sec. 3.1) and their overlap (Sec. 3.1 cross-strip
+ * detection, Sec. 3.2 cluster formation). ---- */
+
+/* Height of the DSM at (x, y): bilinear interpolation of the raster, the
+ * position clamped to the raster. */
+double orc_dsm_height(const orc_dsm* D, double x, double y) {
+  double fx = (x - D->x0) / D->dx, fy = (y - D->y0) / D->dy;
+  if (fx < 0.0) fx = 0.0;
+  if (fy < 0.0) fy = 0.0;
+  if (fx > D->nx - 1) fx = D->nx - 1;
+  if (fy > D->ny - 1) fy = D->ny - 1;
+  int ix = (int)fx, iy = (int)fy;
+  if (ix > D->nx - 2) ix = D->nx - 2;
+  if (iy > D->ny - 2) iy = D->ny - 2;
+  const double ax = fx - ix, ay = fy - iy;
+  const double* h = D->h + (size_t)iy * D->nx + ix;
+  const double h0 = h[0] * (1.0 - ax) + h[1] * ax;
+  const double h1 = h[D->nx] * (1.0 - ax) + h[D->nx + 1] * ax;
+  return h0 * (1.0 - ay) + h1 * ay;
+}
+
+/* Ground point of pixel (u, v): the ray from the camera centre T along
+ * R [(u - cx)/f, (v - cy)/f, 1] (lens distortion not applied) meets the DSM
+ * surface.  The ray is sampled from where it enters the raster's height range
+ * to where it leaves it, in steps of at most half a raster cell horizontally
+ * (ORC_DSM_MAX_STEPS at most); the first sample at or below the surface
+ * brackets the crossing, which ORC_DSM_BISECT bisections refine.  Returns 0,
+ * or -1 for a ray that does not point down. */
+int orc_ray_dsm(const double intr[7], const double R[9], const double T[3], double u, double v, const orc_dsm* D,
+                double hmin, double hmax, double P[3]) {
+  const double a = (u - intr[1]) / intr[0], b = (v - intr[2]) / intr[0];
+  double d[3];
+  for (int i = 0; i < 3; ++i) d[i] = R[3 * i] * a + R[3 * i + 1] * b + R[3 * i + 2];
+  if (!(d[2] < 0.0)) return -1;
+  double t0 = (T[2] - hmax) / (-d[2]), t1 = (T[2] - hmin) / (-d[2]);
+  if (t0 < 0.0) t0 = 0.0;
+  const double dxy = sqrt(d[0] * d[0] + d[1] * d[1]);
+  const double cell = D->dx < D->dy ? D->dx : D->dy;
+  int n = 1;
+  if (dxy > 0.0) {
+    const double steps = ceil((t1 - t0) * dxy / (0.5 * cell));
+    n = steps < 1.0 ? 1 : (steps > ORC_DSM_MAX_STEPS ? ORC_DSM_MAX_STEPS : (int)steps);
+  }
+  double lo = t0, hi = t1;
+  for (int i = 1; i <= n; ++i) {
+    const double t = t0 + (t1 - t0) * i / n;
+    const double g = T[2] + t * d[2] - orc_dsm_height(D, T[0] + t * d[0], T[1] + t * d[1]);
+    if (g <= 0.0) {
+      hi = t;
+      lo = t0 + (t1 - t0) * (i - 1) / n;
+      break;
+    }
+  }
+  for (int it = 0; it < ORC_DSM_BISECT; ++it) {
+    const double t = 0.5 * (lo + hi);
+    const double g = T[2] + t * d[2] - orc_dsm_height(D, T[0] + t * d[0], T[1] + t * d[1]);
+    if (g <= 0.0) hi = t; else lo = t;
+  }
+  for (int i = 0; i < 3; ++i) P[i] = T[i] + hi * d[i];
+  return 0;
+}
+
+/* Footprint of an image of width x height pixels: the ground points of its
+ * four corners (0,0), (w,0), (w,h), (0,h), as corners[4][3]. */
+int orc_footprint(const double intr[7], double width, double height, const double R[9], const double T[3],
+                  const orc_dsm* D, double corners[12]) {
+  double hmin = D->h[0], hmax = D->h[0];
+  for (size_t i = 0; i < (size_t)D->nx * D->ny; ++i) {
+    if (D->h[i] < hmin) hmin = D->h[i];
+    if (D->h[i] > hmax) hmax = D->h[i];
+  }
+  const double uv[4][2] = {{0.0, 0.0}, {width, 0.0}, {width, height}, {0.0, height}};
+  for (int c = 0; c < 4; ++c)
+    if (orc_ray_dsm(intr, R, T, uv[c][0], uv[c][1], D, hmin, hmax, corners + 3 * c) != 0) return -1;
+  return 0;
+}
+
+/* signed area of a polygon (x, y pairs) */
+static double poly_area(const double* p, int n) {
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const int j = (i + 1) % n;
+    s += p[2 * i] * p[2 * j + 1] - p[2 * j] * p[2 * i + 1];
+  }
+  return 0.5 * s;
+}
+
+/* Area of the intersection of two convex quadrilaterals in the ground plane
+ * (x, y of the footprint corners, any orientation): Sutherland-Hodgman
+ * clipping of one by the other, then the shoelace formula. */
+double orc_quad_overlap(const double qa[12], const double qb[12]) {
+  double A[8], B[8];
+  for (int i = 0; i < 4; ++i) {
+    A[2 * i] = qa[3 * i]; A[2 * i + 1] = qa[3 * i + 1];
+    B[2 * i] = qb[3 * i]; B[2 * i + 1] = qb[3 * i + 1];
+  }
+  const double sb = poly_area(B, 4) >= 0.0 ? 1.0 : -1.0;  /* orientation of the clipper */
+  double P[32], Q[32];
+  int np = 4;
+  for (int i = 0; i < 8; ++i) P[i] = A[i];
+  for (int e = 0; e < 4 && np > 0; ++e) {
+    const double ex = B[2 * e], ey = B[2 * e + 1];
+    const double fx = B[2 * ((e + 1) % 4)], fy = B[2 * ((e + 1) % 4) + 1];
+    int nq = 0;
+    for (int i = 0; i < np; ++i) {
+      const double* s = P + 2 * i;
+      const double* t = P + 2 * ((i + 1) % np);
+      const double ds = sb * ((fx - ex) * (s[1] - ey) - (fy - ey) * (s[0] - ex));
+      const double dt = sb * ((fx - ex) * (t[1] - ey) - (fy - ey) * (t[0] - ex));
+      if (ds >= 0.0) { Q[2 * nq] = s[0]; Q[2 * nq + 1] = s[1]; ++nq; }
+      if ((ds >= 0.0) != (dt >= 0.0)) {
+        const double w = ds / (ds - dt);
+        Q[2 * nq] = s[0] + w * (t[0] - s[0]);
+        Q[2 * nq + 1] = s[1] + w * (t[1] - s[1]);
+        ++nq;
+      }
+    }
+    np = nq;
+    for (int i = 0; i < 2 * np; ++i) P[i] = Q[i];
+  }
+  return np >= 3 ? fabs(poly_area(P, np)) : 0.0;
+}
+
+double orc_quad_area(const double q[12]) {
+  double A[8];
+  for (int i = 0; i < 4; ++i) { A[2 * i] = q[3 * i]; A[2 * i + 1] = q[3 * i + 1]; }
+  return fabs(poly_area(A, 4));
+}

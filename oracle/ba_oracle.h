@@ -58,6 +58,24 @@ int orc_lm_step(const orc_problem* P, double* R, double* T, double* X, double* m
                 orc_step_info* info);
 int orc_lm_run(const orc_problem* P, double* R, double* T, double* X, int iters, double mu0,
                orc_step_info* trace);
+/* DSM raster: heights h[iy * nx + ix] at (x0 + ix dx, y0 + iy dy), bilinear between nodes. */
+typedef struct {
+  int nx, ny;
+  double x0, y0, dx, dy;
+  const double* h;
+} orc_dsm;
+
+#define ORC_DSM_MAX_STEPS 100000
+#define ORC_DSM_BISECT 60
+
+double orc_dsm_height(const orc_dsm* D, double x, double y);
+int orc_ray_dsm(const double intr[7], const double R[9], const double T[3], double u, double v, const orc_dsm* D,
+                double hmin, double hmax, double P[3]);
+int orc_footprint(const double intr[7], double width, double height, const double R[9], const double T[3],
+                  const orc_dsm* D, double corners[12]);
+double orc_quad_overlap(const double qa[12], const double qb[12]);
+double orc_quad_area(const double q[12]);
+
 /* Eq. 8: weighted pose average of an overlap image (weights w_old, w_new > 0). */
 void orc_transition(const double R_old[9], const double T_old[3], double w_old, const double R_new[9],
                     const double T_new[3], double w_new, double R_out[9], double T_out[3]);

@@ -755,6 +755,11 @@ size_t factor_smem_bytes(int max_n) {
   return doubles * sizeof(double);
 }
 
+#ifndef BA_FACTOR_THREADS
+#define BA_FACTOR_THREADS 512
+#endif
+constexpr int kFactorThreads = BA_FACTOR_THREADS;  // threads of the shared-memory factor CTA
+
 #ifndef BA_FACTOR_NB
 #define BA_FACTOR_NB 8
 #endif
@@ -924,7 +929,7 @@ __device__ void chol_solve_blocked(const double* A, const double* inv_diag, cons
 }
 
 template <bool MIXED>
-__global__ void __launch_bounds__(512) k_factor_solve(BatchView bv, int refine_steps, int assemble_only) {
+__global__ void __launch_bounds__(kFactorThreads) k_factor_solve(BatchView bv, int refine_steps, int assemble_only) {
   using Real = typename RealOf<MIXED>::T;
   extern __shared__ double sm[];
   __shared__ int fail;
@@ -1731,7 +1736,7 @@ static void launch_iteration_t(const BatchView& bv, int refine_steps, cudaStream
   launch_lin_schur<MIXED>(bv, 0, st);
   launch_partial_reduce<MIXED>(bv, st);
   const size_t smem = factor_smem_bytes(bv.max_n);
-  LAUNCH(KK_FACTOR, st, k_factor_solve<MIXED><<<grid_for(bv.n, 1, 65535), 512, smem, st>>>(bv, refine_steps, 0));
+  LAUNCH(KK_FACTOR, st, k_factor_solve<MIXED><<<grid_for(bv.n, 1, 65535), kFactorThreads, smem, st>>>(bv, refine_steps, 0));
   if (big)
     for (const BigRef& b : *big) launch_big_solve(b, MIXED, refine_steps, 0, st);
   LAUNCH(KK_BACKSUB, st, k_backsub_cost<MIXED><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
@@ -1749,7 +1754,7 @@ static void launch_grad_norm_t(const BatchView& bv, double* out, cudaStream_t st
   launch_lin_schur<MIXED>(bv, 1, st);
   launch_partial_reduce<MIXED>(bv, st);
   LAUNCH(KK_FACTOR, st,
-         k_factor_solve<MIXED><<<grid_for(bv.n, 1, 65535), 512, factor_smem_bytes(bv.max_n), st>>>(bv, 0, 1));
+         k_factor_solve<MIXED><<<grid_for(bv.n, 1, 65535), kFactorThreads, factor_smem_bytes(bv.max_n), st>>>(bv, 0, 1));
   if (big)
     for (const BigRef& b : *big) launch_big_solve(b, MIXED, 0, 1, st);
   LAUNCH(KK_OTHER, st, k_grad_norm<<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv, out));

@@ -303,7 +303,7 @@ def make_cluster(rng, n_strips, cams_per_strip, n_points, *, layout="uniform",
         fixed=fixed_mask, obs_cam=obs_cam, obs_pt=obs_pt, obs_uv=obs_uv, outlier=outlier,
         sigma_px=SIGMA_PX, huber_delta=HUBER_DELTA_PX,
         sigma_gnss=SIGMA_GNSS_M if priors else 0.0, sigma_imu=SIGMA_IMU_RAD if priors else 0.0,
-        strip=strip, origin=np.zeros(3),
+        strip=strip, origin=np.zeros(3), buildings=buildings, bbox=np.array(bbox, dtype=np.float64),
     )
 
 
@@ -392,6 +392,21 @@ def flight(seed, n_strips=3, per_strip=40, pts_per_cam=1667):
     rng = np.random.Generator(np.random.PCG64(seed))
     n = n_strips * per_strip
     return make_cluster(rng, n_strips, per_strip, pts_per_cam * n)
+
+
+def dsm_raster(scene, spacing=2.0):
+    """The scene's surface model (terrain plus buildings) sampled on a regular
+    grid over its bounding box, as a DSM raster: heights h[iy, ix] at
+    (x0 + ix * dx, y0 + iy * dy).  Scene data only (no method arithmetic)."""
+    xmin, xmax, ymin, ymax = scene["bbox"]
+    nx = int(math.ceil((xmax - xmin) / spacing)) + 1
+    ny = int(math.ceil((ymax - ymin) / spacing)) + 1
+    xs = xmin + spacing * np.arange(nx)
+    ys = ymin + spacing * np.arange(ny)
+    X, Y = np.meshgrid(xs, ys)
+    h = terrain_height(X.ravel(), Y.ravel(), scene["buildings"]).reshape(ny, nx)
+    return dict(h=np.ascontiguousarray(h, dtype=np.float64), x0=float(xmin), y0=float(ymin), dx=float(spacing),
+                dy=float(spacing))
 
 
 def window_plan(seed, n_images, m_lo=12, m_hi=32, overlap=0.25):
