@@ -200,6 +200,39 @@ BA_API ba_status ba_warm_start(ba_ctx* ctx, ba_cluster_id dst, ba_cluster_id src
  * unknown id, BA_ERR_INVALID for a null map or an index out of range. */
 BA_API ba_status ba_transition(ba_ctx* ctx, ba_cluster_id dst, ba_cluster_id src, const int32_t* cam_map);
 
+/* ---- Cluster formation: image footprints and their overlaps ----
+ *
+ * Sec. 3.1 projects each image's four corners onto a digital surface model
+ * (the image's footprint, a ground quadrilateral) and detects the overlap
+ * between new images and images of neighbouring strips by comparing
+ * footprints; Sec. 3.2 brings those adjacent-strip images into the cluster. */
+
+/* DSM raster, host memory: heights h[iy * nx + ix] (metres, same frame as
+ * the poses) at (x0 + ix * dx, y0 + iy * dy); nx, ny >= 2; bilinear between
+ * nodes, positions outside clamped to the raster. */
+typedef struct ba_dsm {
+  int32_t nx, ny;
+  double x0, y0, dx, dy;
+  const double* h;
+} ba_dsm;
+
+/* Footprints of n images (host arrays): intr[n][7], R[n][9] (camera->world),
+ * T[n][3]; images of width x height pixels.  corners[n][4][3] (host, output):
+ * the first surface point of the rays through pixels (0,0), (w,0), (w,h),
+ * (0,h) (lens distortion not applied; the ray is sampled at most half a
+ * raster cell apart from where it enters the DSM's height range, then the
+ * bracketed hit is bisected 60 times).  A corner whose ray does not point
+ * down is NaN.  BA_ERR_INVALID for bad sizes or null pointers. */
+BA_API ba_status ba_footprints(ba_ctx* ctx, int32_t n, const double* intr, double width, double height,
+                               const double* R, const double* T, const ba_dsm* dsm, double* corners);
+
+/* Areas of intersection, in the ground plane, of every footprint of qa[na]
+ * with every footprint of qb[nb] (host arrays of [4][3] corners as written by
+ * ba_footprints; convex quadrilaterals, either orientation): area[na][nb]
+ * (host, output).  Sutherland-Hodgman clipping; binary64. */
+BA_API ba_status ba_footprint_overlaps(ba_ctx* ctx, int32_t na, const double* qa, int32_t nb, const double* qb,
+                                       double* area);
+
 /* Evaluate F and the gradient infinity norm at the current state. */
 BA_API ba_status ba_linearize(ba_ctx* ctx, ba_cluster_id id, ba_lin_info* out);
 

@@ -91,9 +91,14 @@ class ba_cluster_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class ba_dsm(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("h", ctypes.POINTER(ctypes.c_double))]
+
+
 EXPORTS = ["ba_init", "ba_create_cluster", "ba_linearize", "ba_solve_step", "ba_run", "ba_solve_batch", "ba_reset",
            "ba_reset_batch", "ba_submit", "ba_poll", "ba_get_state", "ba_reprojection_errors", "ba_memory_in_use",
-           "ba_launch_count", "ba_kernel_stats", "ba_cost_noalloc", "ba_warm_start", "ba_transition", "ba_get_cluster_info", "ba_destroy_cluster", "ba_shutdown",
+           "ba_launch_count", "ba_kernel_stats", "ba_cost_noalloc", "ba_warm_start", "ba_transition", "ba_footprints", "ba_footprint_overlaps", "ba_get_cluster_info", "ba_destroy_cluster", "ba_shutdown",
            "ba_status_string", "ba_last_error"]
 
 _lib = None
@@ -126,6 +131,9 @@ def lib(build: bool = True):
             L.ba_cost_noalloc.argtypes = [ctypes.POINTER(ba_cluster_desc), vp, _dp]
             L.ba_warm_start.argtypes = [vp, u64, u64, _ip, _ip]
             L.ba_transition.argtypes = [vp, u64, u64, _ip]
+            L.ba_footprints.argtypes = [vp, ctypes.c_int32, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp,
+                                        ctypes.POINTER(ba_dsm), _dp]
+            L.ba_footprint_overlaps.argtypes = [vp, ctypes.c_int32, _dp, ctypes.c_int32, _dp, _dp]
             L.ba_submit.argtypes = [vp, u64, ctypes.POINTER(ba_solve_opts), ctypes.POINTER(u64)]
             L.ba_poll.argtypes = [vp, u64, ctypes.POINTER(ba_result)]
             L.ba_get_state.argtypes = [vp, u64, _dp, _dp, _dp, ctypes.c_int32]
@@ -321,6 +329,27 @@ class Context:
         dst) by their observation counts in both clusters."""
         m = np.ascontiguousarray(cam_map, dtype=np.int32)
         _check(self.L.ba_transition(self.h, dst, src, m.ctypes.data_as(_ip)), self.h, "ba_transition")
+
+    def footprints(self, intr, width, height, R, T, dsm):
+        """Ground quadrilaterals (n, 4, 3) of the images' corners on a DSM
+        raster (dict h[ny, nx], x0, y0, dx, dy)."""
+        intr, R, T = _f64(intr, (-1, 7)), _f64(R, (-1, 9)), _f64(T, (-1, 3))
+        n = intr.shape[0]
+        h = _f64(dsm["h"], (-1,))
+        ny, nx = np.shape(dsm["h"])
+        d = ba_dsm(nx, ny, float(dsm["x0"]), float(dsm["y0"]), float(dsm["dx"]), float(dsm["dy"]), _d(h))
+        out = np.zeros((n, 4, 3))
+        _check(self.L.ba_footprints(self.h, n, _d(intr), float(width), float(height), _d(R), _d(T), ctypes.byref(d),
+                                    _d(out)), self.h, "ba_footprints")
+        return out
+
+    def footprint_overlaps(self, qa, qb):
+        """Intersection areas (na, nb) of two sets of footprints."""
+        qa, qb = _f64(qa, (-1, 12)), _f64(qb, (-1, 12))
+        out = np.zeros((qa.shape[0], qb.shape[0]))
+        _check(self.L.ba_footprint_overlaps(self.h, qa.shape[0], _d(qa), qb.shape[0], _d(qb), _d(out)), self.h,
+               "ba_footprint_overlaps")
+        return out
 
     def cluster_info(self, cid):
         """Table sizes of a cluster (units of work per LM iteration)."""

@@ -1379,6 +1379,68 @@ BA_API ba_status ba_transition(ba_ctx* ctx, ba_cluster_id dst, ba_cluster_id src
   return BA_OK;
 }
 
+BA_API ba_status ba_footprints(ba_ctx* ctx, int32_t n, const double* intr, double width, double height,
+                               const double* R, const double* T, const ba_dsm* dsm, double* corners) {
+  if (!ctx || n < 0 || !dsm || (n > 0 && (!intr || !R || !T || !corners))) return BA_ERR_INVALID;
+  if (dsm->nx < 2 || dsm->ny < 2 || !dsm->h || !(dsm->dx > 0.0) || !(dsm->dy > 0.0) || !(width > 0.0) ||
+      !(height > 0.0))
+    return set_err(ctx, BA_ERR_INVALID, "ba_footprints: bad DSM or image size");
+  if (n == 0) return BA_OK;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  const size_t nh = (size_t)dsm->nx * dsm->ny;
+  DsmView D{dsm->nx, dsm->ny, dsm->x0, dsm->y0, dsm->dx, dsm->dy, dsm->h[0], dsm->h[0], nullptr};
+  for (size_t i = 0; i < nh; ++i) {
+    if (!std::isfinite(dsm->h[i])) return set_err(ctx, BA_ERR_INVALID, "ba_footprints: non-finite DSM height");
+    D.hmin = std::min(D.hmin, dsm->h[i]);
+    D.hmax = std::max(D.hmax, dsm->h[i]);
+  }
+  const size_t b_in = sizeof(double) * (size_t)n * (7 + 9 + 3), b_h = sizeof(double) * nh,
+               b_out = sizeof(double) * (size_t)n * 12;
+  char* buf = nullptr;
+  CUDA_TRY(ctx, cudaMallocAsync((void**)&buf, b_in + b_h + b_out, ctx->stream));
+  double* d_intr = (double*)buf;
+  double* d_R = d_intr + 7 * (size_t)n;
+  double* d_T = d_R + 9 * (size_t)n;
+  double* d_h = d_T + 3 * (size_t)n;
+  double* d_out = d_h + nh;
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_intr, intr, sizeof(double) * 7 * n, cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_R, R, sizeof(double) * 9 * n, cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_T, T, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_h, dsm->h, b_h, cudaMemcpyHostToDevice, ctx->stream));
+  D.h = d_h;
+  launch_footprints(n, d_intr, width, height, d_R, d_T, D, d_out, ctx->stream);
+  note_direct(ctx);
+  CUDA_TRY(ctx, cudaMemcpyAsync(corners, d_out, b_out, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaFreeAsync(buf, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(ctx, cudaGetLastError());
+  return BA_OK;
+}
+
+BA_API ba_status ba_footprint_overlaps(ba_ctx* ctx, int32_t na, const double* qa, int32_t nb, const double* qb,
+                                       double* area) {
+  if (!ctx || na < 0 || nb < 0 || (na > 0 && nb > 0 && (!qa || !qb || !area))) return BA_ERR_INVALID;
+  if ((int64_t)na * nb > (int64_t)1 << 30) return set_err(ctx, BA_ERR_INVALID, "ba_footprint_overlaps: too many pairs");
+  if (na == 0 || nb == 0) return BA_OK;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  const size_t ba_ = sizeof(double) * 12 * (size_t)na, bb = sizeof(double) * 12 * (size_t)nb,
+               bo = sizeof(double) * (size_t)na * nb;
+  char* buf = nullptr;
+  CUDA_TRY(ctx, cudaMallocAsync((void**)&buf, ba_ + bb + bo, ctx->stream));
+  double* d_a = (double*)buf;
+  double* d_b = d_a + 12 * (size_t)na;
+  double* d_o = d_b + 12 * (size_t)nb;
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_a, qa, ba_, cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_b, qb, bb, cudaMemcpyHostToDevice, ctx->stream));
+  launch_overlaps(na, d_a, nb, d_b, d_o, ctx->stream);
+  note_direct(ctx);
+  CUDA_TRY(ctx, cudaMemcpyAsync(area, d_o, bo, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaFreeAsync(buf, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(ctx, cudaGetLastError());
+  return BA_OK;
+}
+
 BA_API ba_status ba_linearize(ba_ctx* ctx, ba_cluster_id id, ba_lin_info* out) {
   if (!ctx || !out) return BA_ERR_INVALID;
   std::lock_guard<std::mutex> g(ctx->api_mu);

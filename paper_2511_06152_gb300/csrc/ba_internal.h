@@ -243,6 +243,19 @@ cudaError_t set_big_attributes(int max_n);
 cudaError_t set_kernel_attributes(int max_n);
 void launch_arm(const BatchView& bv, int iters, cudaStream_t st);
 void launch_arm_slots(const BatchView& bv, const int* arm, cudaStream_t st);
+// DSM raster on the device (heights h[iy * nx + ix] at (x0 + ix dx, y0 + iy dy)),
+// with its height range
+struct DsmView {
+  int nx, ny;
+  double x0, y0, dx, dy, hmin, hmax;
+  const double* h;
+};
+constexpr int kDsmMaxSteps = 100000;  // ray samples before the bisection, at most
+constexpr int kDsmBisect = 60;        // bisections of the bracketed first hit
+void launch_footprints(int n, const double* intr, double width, double height, const double* R, const double* T,
+                       const DsmView& D, double* corners, cudaStream_t st);
+void launch_overlaps(int na, const double* qa, int nb, const double* qb, double* area, cudaStream_t st);
+
 // Eq. 8 on the (dst camera, src camera) pairs of pairs[n]
 void launch_transition(const DevCluster* dst, const DevCluster* src, const int2* pairs, int n, cudaStream_t st);
 void launch_warm_copy(const DevCluster* dst, const DevCluster* src, const int2* cams, int n_cams, const int2* pts,
