@@ -77,10 +77,50 @@ def make_workload(replica, n_clusters, n_flights=0, large=False):
     ctx = mp.get_context("spawn")
     with ctx.Pool(n) as pool:
         big = pool.apply_async(sg.cluster_c5, (replica,)) if large else None  # ~1 min, alongside the rest
+        form = pool.apply_async(formation_scene, (4000 + 100 * replica,)) if large else None
         scenes = sg.batch_c3(replica=replica, n_clusters=n_clusters, pool=pool)
         flights = pool.map(serving_flight, [4000 + 100 * replica + f for f in range(n_flights)]) if n_flights else []
         big = big.get() if big is not None else None
-    return scenes, flights, big
+        form = form.get() if form is not None else None
+    return scenes, flights, (big, form)
+
+
+def formation_scene(seed):
+    """A serving flight (3 strips x 40 images) and its DSM raster at 2 m."""
+    fl = sg.flight(seed, pts_per_cam=50)
+    return fl, sg.dsm_raster(fl, 2.0)
+
+
+def formation_leg(ba, torch, stream, form):
+    """Cluster formation inputs of one flight: the footprints of its 120 images
+    on the DSM and the overlap areas of every pair, through the C ABI (host
+    arrays in and out, copies included), median of 5 calls each; and the
+    adjacent-strip images a 30 % overlap ratio brings into each window."""
+    fl, dsm = form
+    ctx = ba.Context(device=torch.cuda.current_device(), stream=stream.cuda_stream)
+    tf, to = [], []
+    for _ in range(6):
+        t0 = time.perf_counter()
+        q = ctx.footprints(fl["intr"], sg.SENSOR_W, sg.SENSOR_H, fl["R_prior"], fl["T_prior"], dsm)
+        t1 = time.perf_counter()
+        A = ctx.footprint_overlaps(q, q)
+        t2 = time.perf_counter()
+        tf.append(t1 - t0)
+        to.append(t2 - t1)
+    ctx.close()
+    n = fl["n_cams"]
+    strip = fl["strip"]
+    adds = []
+    for (s, e, _) in sg.window_plan(4000, n):
+        win = np.arange(s, e)
+        other = np.nonzero(strip < strip[win].min())[0]
+        if len(other) == 0:
+            continue
+        ratio = A[np.ix_(win, other)] / np.diag(A)[win][:, None]
+        adds.append(int((ratio >= 0.3).any(axis=0).sum()))
+    return {"images": int(n), "dsm_nodes": int(dsm["h"].size), "footprints_ms": 1e3 * statistics.median(tf[1:]),
+            "overlap_pairs": int(n * n), "overlaps_ms": 1e3 * statistics.median(to[1:]),
+            "adjacent_strip_images_per_window": adds, "poses": "GNSS/IMU priors (the initial values)"}
 
 
 def serving_flight(seed):
@@ -424,7 +464,7 @@ def main():
         return
     n_fl = 0 if (args.no_extras or rank != 0 or world != 1) else args.serving_flights
     log(f"generating {args.clusters} clusters and {n_fl} serving flights")
-    scenes, flights, large = make_workload(rank, args.clusters, n_fl, large=n_fl > 0 and not args.no_large)
+    scenes, flights, (large, form) = make_workload(rank, args.clusters, n_fl, large=n_fl > 0 and not args.no_large)
     total_obs = sum(s["n_obs"] for s in scenes)
     iters = args.iters
 
@@ -518,7 +558,7 @@ def main():
 
     log(f"timed: {ms_per_step:.2f} ms/step")
     if not args.no_extras and rank == 0 and world == 1:
-        line.update(extras(args, ba, torch, scenes, ids, ctx, stream, iters, value, flights, large))
+        line.update(extras(args, ba, torch, scenes, ids, ctx, stream, iters, value, flights, large, form))
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -557,7 +597,7 @@ def large_block_leg(ba, torch, stream, c):
     return out
 
 
-def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flights, large=None):
+def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flights, large=None, form=None):
     out = {}
     # accuracy of the mixed path on a few clusters against the FP64 path
     sample = list(range(min(args.fp64_sample, len(scenes))))
@@ -619,6 +659,9 @@ def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flight
     log("cpu baseline leg")
     out["cpu_baseline"] = oracle_obs_per_s(scenes, iters, args.cpu_seconds)
     out["paper_context"] = "paper: full BA per cluster in < 2 s, MATLAB on an i7 13th-gen 20-core laptop, no GPU"
+    if form is not None:
+        log("cluster formation leg")
+        out["cluster_formation"] = formation_leg(ba, torch, stream, form)
     if large is not None:
         log("large block leg")
         out["large_block"] = large_block_leg(ba, torch, stream, large)

@@ -31,10 +31,10 @@ def test_footprints_match_oracle(scene, pose):
 
 
 def test_overlaps_match_oracle_and_select_adjacent_strip_images(scene):
-    """Every footprint against every other: the GPU areas equal the oracle's;
-    the images of the other strips overlapping a window of the third strip by
-    at least 20 % of its area are found, and they all lie on the neighbouring
-    strip."""
+    """Every footprint against every other: the GPU areas equal the oracle's.
+    With 60 % side overlap, neighbouring strips share ~60 % of a footprint's
+    width and strips two apart ~20 %: a 30 % threshold on the overlap ratio
+    selects images of the neighbouring strip only."""
     import paper_2511_06152_gb300 as ba
     fl, dsm = scene
     with ba.Context() as ctx:
@@ -50,7 +50,6 @@ def test_overlaps_match_oracle_and_select_adjacent_strip_images(scene):
     window = np.nonzero(strip == 2)[0][:6]
     earlier = np.nonzero(strip < 2)[0]
     ratio = A[np.ix_(window, earlier)] / np.diag(A)[window][:, None]
-    sel = earlier[(ratio >= 0.2).any(axis=0)]
+    sel = earlier[(ratio >= 0.3).any(axis=0)]
     assert len(sel) > 0 and np.all(strip[sel] == 1)
-    far = earlier[strip[earlier] == 0]
-    assert np.all(A[np.ix_(window, far)] == 0.0)
+    assert ratio[:, strip[earlier] == 0].max() < 0.3
