@@ -391,7 +391,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x ma
 # ncu capture of the current kernel on 32 clusters of the same mix (87.2 MB for
 # 2,452,644 observations); scaled to a launch by its observations.  Set to
 # None whenever the kernel changes until it is captured again.
-LIN_SCHUR_DRAM_BYTES_PER_OBS = 87.183616e6 / 2452644
+LIN_SCHUR_DRAM_BYTES_PER_OBS = None  # kernel changed since the last capture (87.2 MB / 2,452,644 obs)
 FP64_PEAK_TFLOPS = 1.25                               # nominal dense FP64
 
 

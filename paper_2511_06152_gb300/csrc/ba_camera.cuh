@@ -6,29 +6,31 @@
 
 namespace bagpu {
 
-// mixed path: double-float record of camera k from (R, T) in binary64
+// mixed path: double-float record of camera k from (R, T) in binary64, in the
+// layout the kernels read (high words of the linearisation's inputs first)
 __device__ inline void write_camdf(const DevCluster& C, int buf, int k, const double* R, const double* T) {
   float* o = C.camdf + ((size_t)buf * C.n_cams + k) * kCamDf;
   for (int i = 0; i < 9; ++i) {
     const dfl v = df_from_d(R[i]);
-    o[2 * i] = v.hi;
-    o[2 * i + 1] = v.lo;
+    o[i] = v.hi;
+    o[24 + i] = v.lo;
   }
   for (int i = 0; i < 3; ++i) {
     const dfl v = df_from_d(T[i]);
-    o[18 + 2 * i] = v.hi;
-    o[19 + 2 * i] = v.lo;
+    o[9 + i] = v.hi;
+    o[12 + i] = v.lo;
   }
   const dfl f = df_from_d(C.intr[7 * k]);
-  o[24] = f.hi;
-  o[25] = f.lo;
+  o[15] = f.hi;
+  o[33] = f.lo;
   for (int i = 0; i < 4; ++i) {
     const dfl v = df_from_d(C.intr[7 * k + 3 + i]);
-    o[26 + 2 * i] = v.hi;
-    o[27 + 2 * i] = v.lo;
+    o[16 + i] = v.hi;
+    o[34 + i] = v.lo;
   }
-  o[34] = C.free_idx[k] >= 0 ? 1.0f : 0.0f;
-  for (int i = 35; i < kCamDf; ++i) o[i] = 0.0f;
+  o[20] = C.free_idx[k] >= 0 ? 1.0f : 0.0f;
+  for (int i = 21; i < 24; ++i) o[i] = 0.0f;
+  for (int i = 38; i < kCamDf; ++i) o[i] = 0.0f;
 }
 
 // Candidate pose of camera k for the step x (in the elimination order,

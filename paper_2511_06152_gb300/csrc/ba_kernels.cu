@@ -67,25 +67,52 @@ struct CamDf {
   float free_flag;
 };
 
-__device__ __forceinline__ CamDf load_camdf(const float* p) {
-  CamDf c;
-  float v[kCamDf];
+// Camera record layout (kCamDf = 40 floats): the part the binary32
+// linearisation reads first, in six float4: R.hi [0, 9), T.hi [9, 12),
+// T.lo [12, 15), f.hi 15, k1 k2 p1 p2 .hi [16, 20), free flag 20, pad; then
+// R.lo [24, 33), f.lo 33, k1 k2 p1 p2 .lo [34, 38), pad.
+__device__ __forceinline__ void load_f4(const float* p, int n4, float* v) {
   const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
-  for (int i = 0; i < kCamDf / 4; ++i) {
+  for (int i = 0; i < n4; ++i) {
     const float4 w = q[i];
     v[4 * i] = w.x; v[4 * i + 1] = w.y; v[4 * i + 2] = w.z; v[4 * i + 3] = w.w;
   }
+}
+
+// the linearisation's part: high words of R, f and the distortion, T in full
+__device__ __forceinline__ CamDf load_camdf_lin(const float* p) {
+  CamDf c;
+  float v[24];
+  load_f4(p, 6, v);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) c.R[i] = dfl{v[2 * i], v[2 * i + 1]};
+  for (int i = 0; i < 9; ++i) c.R[i] = dfl{v[i], 0.f};
 #pragma unroll
-  for (int i = 0; i < 3; ++i) c.T[i] = dfl{v[18 + 2 * i], v[19 + 2 * i]};
-  c.f = dfl{v[24], v[25]};
-  c.k1 = dfl{v[26], v[27]};
-  c.k2 = dfl{v[28], v[29]};
-  c.p1 = dfl{v[30], v[31]};
-  c.p2 = dfl{v[32], v[33]};
-  c.free_flag = v[34];
+  for (int i = 0; i < 3; ++i) c.T[i] = dfl{v[9 + i], v[12 + i]};
+  c.f = dfl{v[15], 0.f};
+  c.k1 = dfl{v[16], 0.f};
+  c.k2 = dfl{v[17], 0.f};
+  c.p1 = dfl{v[18], 0.f};
+  c.p2 = dfl{v[19], 0.f};
+  c.free_flag = v[20];
+  return c;
+}
+
+// the whole double-float record
+__device__ __forceinline__ CamDf load_camdf(const float* p) {
+  CamDf c;
+  float v[kCamDf];
+  load_f4(p, kCamDf / 4, v);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) c.R[i] = dfl{v[i], v[24 + i]};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) c.T[i] = dfl{v[9 + i], v[12 + i]};
+  c.f = dfl{v[15], v[33]};
+  c.k1 = dfl{v[16], v[34]};
+  c.k2 = dfl{v[17], v[35]};
+  c.p1 = dfl{v[18], v[36]};
+  c.p2 = dfl{v[19], v[37]};
+  c.free_flag = v[20];
   return c;
 }
 
@@ -238,7 +265,7 @@ __device__ __forceinline__ void linearize_tile(const DevCluster& C, LmState* lm,
     Real Rm[9], in[7], dx, dy, dz, uo, vo;
     bool is_free;
     if constexpr (MIXED) {
-      const CamDf cd = load_camdf(camdf_ptr(C, cur, L.k));
+      const CamDf cd = load_camdf_lin(camdf_ptr(C, cur, L.k));
       const float2* xp = V.x + (size_t)(L.j - V.j0) * 3;
       const float2 a = xp[0], b = xp[1], c = xp[2];
       dx = df_to_f(df_sub(dfl{a.x, a.y}, cd.T[0]));
