@@ -886,6 +886,120 @@ __device__ void chol_blocked(double* A, int n, double* inv_diag, double* colbuf,
   }
 }
 
+// Cholesky with one panel of look-ahead.  Warps 0-3 (group P) factor the
+// next panel while warps 4.. (group T) update the rest of the trailing matrix
+// with the current panel, so that the panel's sequential pivot chain runs
+// behind the trailing update.  Per panel p (columns [k0, k1), already
+// factored) and next panel [k1, k2): group P first updates the next panel's
+// columns with panel p, then factors them column by column, synchronising on
+// a named barrier of its 128 threads; group T updates columns >= k2.  The
+// writes of the two groups are disjoint and both only read panel p.  Same
+// envelope skipping as chol_blocked.  Requires blockDim.x > 128.
+__device__ __forceinline__ void bar_group_p() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// factor columns [k1, k2) (already updated by every earlier panel), group P only
+__device__ void chol_panel_p(double* A, int n, int k1, int k2, double* inv_diag, double* colbuf, const int* efirst,
+                             int* fail) {
+  const int tid = threadIdx.x;
+  for (int j = k1; j < k2; ++j) {
+    if (tid < 32) {
+      double inv = 0.0;
+      if (tid == 0) {
+        const double d = A[pk(j, j)];
+        if (!(d > 0.0)) *fail = 1;
+        inv = rsqrt(d > 0.0 ? d : 1.0);
+        A[pk(j, j)] = (d > 0.0 ? d : 1.0) * inv;
+        inv_diag[j] = inv;
+      }
+      inv = __shfl_sync(BA_FULL_MASK, inv, 0);
+      if (j + 1 + tid < k2) colbuf[j + 1 + tid] = A[pk(j + 1 + tid, j)] * inv;
+    }
+    bar_group_p();
+    const double inv = inv_diag[j];
+    for (int i = j + 1 + tid; i < n; i += 128) {
+      if (efirst[i] > j) continue;  // L(i, j) = 0
+      const double l = A[pk(i, j)] * inv;
+      A[pk(i, j)] = l;
+      const int cmax = min(i, k2 - 1);
+      for (int c = j + 1; c <= cmax; ++c) A[pk(i, c)] -= l * colbuf[c];
+    }
+    bar_group_p();
+  }
+}
+
+__device__ void chol_lookahead(double* A, int n, double* inv_diag, double* colbuf, const int* efirst, int* fail) {
+  const int tid = threadIdx.x;
+  const bool gp = tid < 128;
+  if (gp) chol_panel_p(A, n, 0, min(kFactorNB, n), inv_diag, colbuf, efirst, fail);
+  __syncthreads();
+  for (int k0 = 0; k0 < n; k0 += kFactorNB) {
+    if (*fail) return;
+    const int k1 = min(k0 + kFactorNB, n), k2 = min(k1 + kFactorNB, n);
+    if (gp) {
+      if (k1 < n) {
+        // the next panel's columns c in [k1, k2), rows i >= c, with panel p
+        const int w = k2 - k1;
+        for (int u = tid; u < (n - k1) * w; u += 128) {
+          const int i = k1 + u / w, c = k1 + u % w;
+          if (c > i) continue;
+          const int qlo = max(k0, max(efirst[i], efirst[c]));
+          double s = 0.0;
+          for (int q = qlo; q < k1; ++q) s += A[pk(i, q)] * A[pk(c, q)];
+          A[pk(i, c)] -= s;
+        }
+        bar_group_p();
+        chol_panel_p(A, n, k1, k2, inv_diag, colbuf, efirst, fail);
+      }
+    } else if (k2 < n) {
+      // trailing columns >= k2 with panel p, by the other warps
+      const int tt = tid - 128, nt_thr = blockDim.x - 128;
+      const int m = n - k2;
+      const int nt = (m + 3) >> 2;
+      const int ntiles = nt * (nt + 1) / 2;
+      for (int t = tt; t < ntiles; t += nt_thr) {
+        int bi = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+        while (bi * (bi + 1) / 2 > t) --bi;
+        const int bc = t - bi * (bi + 1) / 2;
+        const int i0 = k2 + 4 * bi, c0 = k2 + 4 * bc;
+        int fi = n, fc = n;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          if (i0 + a < n) fi = min(fi, efirst[i0 + a]);
+          if (c0 + a < n) fc = min(fc, efirst[c0 + a]);
+        }
+        const int qlo = max(k0, max(fi, fc));
+        if (qlo >= k1) continue;
+        double acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+        for (int q = qlo; q < k1; ++q) {
+          double li[4], lc[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            li[a] = i0 + a < n ? A[pk(i0 + a, q)] : 0.0;
+            lc[a] = c0 + a < n ? A[pk(c0 + a, q)] : 0.0;
+          }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] += li[a] * lc[b];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int i = i0 + a, c = c0 + b;
+            if (i < n && c <= i) A[pk(i, c)] -= acc[a][b];
+          }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // After the factorisation: L = Lu D with D = diag(L) and Lu unit lower
 // triangular; the strictly lower part of A is scaled to Lu in place (the
 // diagonal keeps L(j, j)), so that S = Lu D^2 Lu^T and the sweeps need no
@@ -1042,7 +1156,11 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_solve(BatchView bv, i
     int* efirst = reinterpret_cast<int*>(inv_diag + n);  // [n]: first column of each row's envelope
     for (int idx = tid; idx < n; idx += bs) efirst[idx] = 6 * C.env_first[idx / 6];
     __syncthreads();
+#ifdef BA_FACTOR_NO_LOOKAHEAD
     if (!fail) chol_blocked(A, n, inv_diag, t, efirst, &fail);
+#else
+    if (!fail) chol_lookahead(A, n, inv_diag, t, efirst, &fail);
+#endif
     __syncthreads();
     const int status = fail ? BA_STATUS_NOT_PD : 0;
     if (!fail) {
