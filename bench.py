@@ -651,6 +651,9 @@ def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flight
             ce.get_state(c)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
+        infos = [ce.cluster_info(c) for c in cids]
+        presort_ms = sum(v["presort_ms"] for v in infos)
+        upload_ms = sum(v["upload_ms"] for v in infos)
         for c in cids:
             ce.destroy_cluster(c)
     ce.close()
@@ -659,7 +662,8 @@ def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flight
                   "d2h_bytes_per_step": int(d2h), "seconds_per_step": statistics.median(times),
                   "includes": "ba_create_cluster from host arrays (validation, presort, H2D) on "
                               f"{n_thr} host threads, batched solve, ba_get_state to host",
-                  "steps": args.e2e_steps, "all_seconds": times}
+                  "steps": args.e2e_steps, "all_seconds": times,
+                  "host_presort_ms_summed_over_clusters": presort_ms, "upload_ms_summed_over_clusters": upload_ms}
     log("cpu baseline leg")
     out["cpu_baseline"] = oracle_obs_per_s(scenes, iters, args.cpu_seconds)
     out["paper_context"] = "paper: full BA per cluster in < 2 s, MATLAB on an i7 13th-gen 20-core laptop, no GPU"

@@ -291,6 +291,8 @@ typedef struct ba_cluster_info {
   int64_t n_free_obs;    /* observations by free cameras */
   int64_t n_pair_entries;
   int64_t arena_bytes;   /* device memory held by the cluster */
+  double presort_ms;     /* ba_create_cluster: host validation, presort and staging (wall clock) */
+  double upload_ms;      /* ba_create_cluster: device allocation, upload and camera records */
 } ba_cluster_info;
 
 /* Fill *out for cluster id (host pointer).  BA_ERR_NOT_FOUND for an unknown

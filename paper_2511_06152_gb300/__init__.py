@@ -85,7 +85,8 @@ class ba_result(ctypes.Structure):
 class ba_cluster_info(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in ("n_cams", "n_free", "n_pts", "n_obs", "n_tiles", "n_chunks",
                                              "n_cam_slots", "n_pair_slots", "n_pairs", "reserved")] + \
-               [(k, ctypes.c_int64) for k in ("n_free_obs", "n_pair_entries", "arena_bytes")]
+               [(k, ctypes.c_int64) for k in ("n_free_obs", "n_pair_entries", "arena_bytes")] + \
+               [(k, ctypes.c_double) for k in ("presort_ms", "upload_ms")]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

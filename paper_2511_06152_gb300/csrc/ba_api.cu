@@ -420,6 +420,7 @@ BatchView one_view(const DevCluster* d_desc, int n_free) {
 }
 
 ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
+  const auto t_start = std::chrono::steady_clock::now();
   const int nc = d->n_cams, np = d->n_pts, no = d->n_obs;
   if (nc < 1 || np < 0 || no < 0) return set_err(ctx, BA_ERR_INVALID, "n_cams must be >= 1, n_pts and n_obs >= 0");
   if (d->ptr_kind != BA_PTR_HOST && d->ptr_kind != BA_PTR_DEVICE) return set_err(ctx, BA_ERR_INVALID, "bad ptr_kind");
@@ -892,6 +893,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
     put(o_bflag, &zero, sizeof(int));
   }
 
+  const auto t_staged = std::chrono::steady_clock::now();
   // Everything above is host work.  The budget is reserved under the API
   // lock; allocation, upload and the camera records run on a stream of this
   // call without the lock, so creation overlaps other calls and serving.
@@ -1010,6 +1012,9 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   c->info.n_free_obs = (int64_t)cm_list.size();
   c->info.n_pair_entries = (int64_t)pent.size();
   c->info.arena_bytes = (int64_t)total;
+  const auto t_end = std::chrono::steady_clock::now();
+  c->info.presort_ms = std::chrono::duration<double, std::milli>(t_staged - t_start).count();
+  c->info.upload_ms = std::chrono::duration<double, std::milli>(t_end - t_staged).count();
   c->pm_to_user = std::move(pm);
   c->pt_inv = std::move(inv);
   c->big_below = std::move(big_below);
