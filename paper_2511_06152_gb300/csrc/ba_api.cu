@@ -477,15 +477,30 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
       v = (v | (v << 1)) & 0x55555555u;
       return v;
     };
-    std::vector<std::pair<uint32_t, int>> key(np);
+    // stable LSD radix sort of the codes, 8 bits per pass, starting from the
+    // caller's order (so ties stay in caller order)
+    std::vector<uint32_t> code(np), code2(np);
+    std::vector<int> idx(np), idx2(np);
     for (int j = 0; j < np; ++j) {
       const uint32_t qx = (uint32_t)((X[3 * (size_t)j] - xmin) * sx), qy = (uint32_t)((X[3 * (size_t)j + 1] - ymin) * sy);
-      key[j] = {spread(qx) | (spread(qy) << 1), j};
+      code[j] = spread(qx) | (spread(qy) << 1);
+      idx[j] = j;
     }
-    std::sort(key.begin(), key.end());
+    for (int shift = 0; shift < 32; shift += 8) {
+      int cnt[257] = {0};
+      for (int j = 0; j < np; ++j) ++cnt[((code[j] >> shift) & 255u) + 1];
+      for (int b = 0; b < 256; ++b) cnt[b + 1] += cnt[b];
+      for (int j = 0; j < np; ++j) {
+        const int dst = cnt[(code[j] >> shift) & 255u]++;
+        code2[dst] = code[j];
+        idx2[dst] = idx[j];
+      }
+      code.swap(code2);
+      idx.swap(idx2);
+    }
     for (int i = 0; i < np; ++i) {
-      perm[i] = key[i].second;
-      inv[key[i].second] = i;
+      perm[i] = idx[i];
+      inv[idx[i]] = i;
     }
   }
 
@@ -659,7 +674,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
         bool align = alloc(1e300, true) <= kChunkThreads;  // one lane each must fit
         double lo = 0.0, hi = 1.0;
         for (int q = 0; q < nj; ++q) hi = std::max(hi, cost[q]);
-        for (int it = 0; it < 60; ++it) {  // smallest quantum that fits
+        for (int it = 0; it < 24; ++it) {  // smallest quantum that fits (to 2^-24 of the largest cost)
           const double mid = 0.5 * (lo + hi);
           if (mid > 0.0 && alloc(mid, align) <= kChunkThreads) hi = mid; else lo = mid;
         }
