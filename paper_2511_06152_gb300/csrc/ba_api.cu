@@ -559,8 +559,8 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const int ch_tiles = chunk_tiles(mixed);
   std::vector<Chunk> chunks;
   std::vector<Job> jobs;
-  std::vector<int> mjobs;
   std::vector<unsigned short> cm_list;
+  std::vector<unsigned char> lane_job;  // per chunk: the job of each lane (kChunkThreads bytes)
   std::vector<unsigned int> pent;
   std::vector<int> pair_of((size_t)nf * nf, -1);  // (fa, fb) -> pair index
   std::vector<int2> pair_key;
@@ -655,7 +655,6 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
       // one lane and at most one per item; chunks with more jobs than threads
       // run one lane per job (the kernel's fallback mode).
       const int nj = ch.n_lc + ch.n_lp;
-      ch.mjob_begin = (int)mjobs.size();
       if (nj > 0 && nj <= kChunkThreads) {
         std::vector<double> cost(nj);
         for (int q = 0; q < nj; ++q) cost[q] = jobs[ch.job_begin + q].count * (q < ch.n_lc ? 165.0 : 123.0);
@@ -686,10 +685,19 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
           jb.lane_begin = (short)lb;
           jb.n_lanes = (short)lanes[q];
           lb += lanes[q];
-          if (lanes[q] > 1) mjobs.push_back(q);
         }
       }
-      ch.n_mjobs = (int)mjobs.size() - ch.mjob_begin;
+      {  // lane t runs the last job whose lane run starts at or before t
+        const size_t base = lane_job.size();
+        lane_job.resize(base + kChunkThreads, 0);
+        if (nj > 0 && nj <= kChunkThreads) {
+          int q = 0;
+          for (int t2 = 0; t2 < kChunkThreads; ++t2) {
+            while (q + 1 < nj && jobs[ch.job_begin + q + 1].lane_begin <= t2) ++q;
+            lane_job[base + t2] = (unsigned char)q;
+          }
+        }
+      }
       chunks.push_back(ch);
     }
   }
@@ -794,7 +802,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const size_t o_clo = Lo.add(mixed ? sizeof(float2) * (size_t)no : 0);
   const size_t o_chunks = Lo.add(sizeof(Chunk) * chunks.size());
   const size_t o_jobs = Lo.add(sizeof(Job) * jobs.size());
-  const size_t o_mjobs = Lo.add(sizeof(int) * mjobs.size());
+  const size_t o_ljob = Lo.add(lane_job.size());
   const size_t o_cml = Lo.add(sizeof(unsigned short) * cm_list.size());
   const size_t o_pent = Lo.add(sizeof(unsigned int) * pent.size());
   const size_t o_csb = Lo.add(sizeof(int) * cam_slot_begin.size());
@@ -887,7 +895,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   }
   put(o_chunks, chunks.data(), sizeof(Chunk) * chunks.size());
   put(o_jobs, jobs.data(), sizeof(Job) * jobs.size());
-  put(o_mjobs, mjobs.data(), sizeof(int) * mjobs.size());
+  put(o_ljob, lane_job.data(), lane_job.size());
   put(o_cml, cm_list.data(), sizeof(unsigned short) * cm_list.size());
   put(o_pent, pent.data(), sizeof(unsigned int) * pent.size());
   put(o_csb, cam_slot_begin.data(), sizeof(int) * cam_slot_begin.size());
@@ -983,7 +991,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   h.obs_clo = mixed ? (const float2*)(arena + o_clo) : nullptr;
   h.chunks = (const Chunk*)(arena + o_chunks);
   h.jobs = (const Job*)(arena + o_jobs);
-  h.mjobs = (const int*)(arena + o_mjobs);
+  h.lane_job = (const unsigned char*)(arena + o_ljob);
   h.cm_list = (const unsigned short*)(arena + o_cml);
   h.pent = (const unsigned int*)(arena + o_pent);
   h.campart = arena + o_cpart;

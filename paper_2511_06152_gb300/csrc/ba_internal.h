@@ -41,9 +41,9 @@ constexpr double kDiagMax = 1e32;
 constexpr double kMinDepth = 1e-6;
 constexpr int BA_STATUS_NOT_PD = -3;  // same value as BA_ERR_NOT_PD in ba.h
 constexpr int kTraceCap = 256;
-// double-float camera record (floats): R as 9 (hi, lo) pairs [0..17], T as 3
-// pairs [18..23], f as a pair [24..25], k1 k2 p1 p2 as pairs [26..33], free
-// flag [34], padding to 40
+// double-float camera record (floats): high words of R [0, 9), T.hi [9, 12),
+// T.lo [12, 15), f.hi 15, k1 k2 p1 p2 .hi [16, 20), free flag 20, pad; then
+// the low words of R [24, 33), f.lo 33, k1 k2 p1 p2 .lo [34, 38), pad to 40
 constexpr int kCamDf = 40;
 constexpr int kCamReal = 20;
 
@@ -57,7 +57,6 @@ struct Chunk {
   int tile_begin, n_tiles;  // its tiles
   int job_begin;            // its jobs: n_lc free cameras, then n_lp co-visible camera pairs
   int n_lc, n_lp;
-  int mjob_begin, n_mjobs;  // its jobs spread over more than one lane (indices into its jobs)
   int pt_begin, n_pts;      // internal point range spanned by its observations
 };
 
@@ -70,8 +69,11 @@ struct Job {
   int count;       // items
   short lane_begin, n_lanes;
 };
+static_assert(sizeof(Job) == 16, "jobs are staged as 16-byte records");
 
-constexpr int kLanePart = 40;  // shared-memory row per lane for multi-lane jobs
+// shared-memory row per lane for multi-lane jobs: 44 words, so that the
+// 16-byte stores of the eight lanes of a quarter-warp fall on distinct banks
+constexpr int kLanePart = 44;
 
 // Per-cluster LM control state, resident on the device.
 struct LmState {
@@ -145,7 +147,7 @@ struct DevCluster {
 
   const Chunk* chunks;         // [n_chunks]
   const Job* jobs;             // per chunk, in lane order
-  const int* mjobs;            // per chunk: indices of its multi-lane jobs
+  const unsigned char* lane_job;  // [n_chunks][kChunkThreads] job of each lane (chunks of at most kChunkThreads jobs)
   const unsigned short* cm_list;  // chunk-local observation lists per camera job
   const unsigned int* pent;       // chunk-local observation pairs per pair job
   void* campart;               // Real [n_cslots][kCamPart]

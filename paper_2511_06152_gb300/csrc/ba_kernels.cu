@@ -36,6 +36,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "ba_device.cuh"
 #include "ba_bulk.cuh"
@@ -512,46 +513,92 @@ __host__ __device__ constexpr size_t chunk_records_bytes(bool mixed) {
               ? (size_t)(mixed ? kChunkObsMixed : kChunkObsF64) * kSrec
               : (size_t)kChunkThreads * kLanePart);
 }
+__device__ __forceinline__ float4 vadd(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
 // Shared-memory staging of one chunk's observations and points (mixed path):
 // camera and point indices (int), observations relative to the principal
 // point (float2 hi), points (3 float2 each), each range rounded outward to
 // 16 bytes.  A chunk spanning more than kStagePts points reads its points
-// from global memory instead.
+// from global memory instead.  Double-buffered beside them, so that the next
+// chunk's copies land while this chunk's jobs still read its own: the chunk's
+// head (cluster slot, state buffer, chunk record; written by the issuing
+// thread), its tile headers, its job records and the job of each lane (the
+// last two for chunks of at most kChunkThreads jobs).
 constexpr int kStagePts = 512;
 constexpr uint32_t kStageIdxBytes = kChunkObsMixed * 4 + 32;
 constexpr uint32_t kStageChiBytes = kChunkObsMixed * 8 + 32;
 constexpr uint32_t kStageXBytes = kStagePts * 24 + 32;
-constexpr uint32_t kStageBytes = 2 * kStageIdxBytes + kStageChiBytes + kStageXBytes;
+struct ChunkHead {
+  int s, cur, pad0, pad1;
+  Chunk ch;
+};
+constexpr uint32_t kHeadBytes = (sizeof(ChunkHead) + 15) / 16 * 16;
+constexpr uint32_t kStageTileBytes = kChunkTilesMixed * sizeof(Tile) + 32;
+constexpr uint32_t kStageJobBytes = kChunkThreads * sizeof(Job) + 32;
+constexpr uint32_t kStageLaneBytes = kChunkThreads;  // one byte per lane
+constexpr uint32_t kTableBytes = kHeadBytes + kStageTileBytes + kStageJobBytes + kStageLaneBytes;
+constexpr uint32_t kStageBytes = 2 * kStageIdxBytes + kStageChiBytes + kStageXBytes + 2 * kTableBytes;
 constexpr uint64_t kCopyWaitNs = 200000000ull;  // give up on a staged copy after 200 ms
+static_assert(kTableBytes % 16 == 0 && kStageTileBytes % 16 == 0 && kStageJobBytes % 16 == 0, "16-byte staging");
 
 struct Stage {
   char* idx_cam;
   char* idx_pt;
   char* chi;
   char* x;
+  char* tab;  // two table buffers of kTableBytes
   uint64_t* bar;
   int* ok;
+  __device__ ChunkHead* head(int b) const { return reinterpret_cast<ChunkHead*>(tab + b * kTableBytes); }
+  __device__ char* tiles(int b) const { return tab + b * kTableBytes + kHeadBytes; }
+  __device__ char* jobs(int b) const { return tab + b * kTableBytes + kHeadBytes + kStageTileBytes; }
+  __device__ unsigned char* lanes(int b) const {
+    return reinterpret_cast<unsigned char*>(tab + b * kTableBytes + kHeadBytes + kStageTileBytes + kStageJobBytes);
+  }
 };
 
-// Issue the copies of chunk g (one thread).  Returns nothing; the barrier's
-// transaction count covers exactly the bytes issued.
-__device__ __forceinline__ void stage_issue(const BatchView& bv, int g, const Stage& S) {
+__device__ __forceinline__ bool job_table_mode(const Chunk& ch) {
+  const int nj = ch.n_lc + ch.n_lp;
+  return nj > 0 && nj <= kChunkThreads;
+}
+
+// Issue the copies of chunk g into table buffer b (one thread) and write its
+// head.  The barrier's transaction count covers exactly the bytes issued.
+__device__ __forceinline__ void stage_issue(const BatchView& bv, int g, const Stage& S, int b) {
   const int s = find_slot(bv.chunk_pre, bv.n, g);
   const DevCluster& C = bv.cl[s];
-  const Chunk ch = C.chunks[g - bv.chunk_pre[s]];
+  const int local = g - bv.chunk_pre[s];
+  const Chunk ch = C.chunks[local];
+  const int cur = C.lm->cur;
+  ChunkHead* hd = S.head(b);
+  hd->s = s;
+  hd->cur = cur;
+  hd->ch = ch;
   const BulkRange rc = bulk_range(C.obs_cam + ch.obs_begin, (size_t)ch.n_obs * 4);
   const BulkRange rp = bulk_range(C.obs_pt + ch.obs_begin, (size_t)ch.n_obs * 4);
   const BulkRange rh = bulk_range(C.obs_chi + ch.obs_begin, (size_t)ch.n_obs * 8);
   const bool stage_x = ch.n_pts <= kStagePts;
-  const float2* xb = reinterpret_cast<const float2*>(C.X) + ((size_t)C.lm->cur * C.n_pts + ch.pt_begin) * 3;
+  const float2* xb = reinterpret_cast<const float2*>(C.X) + ((size_t)cur * C.n_pts + ch.pt_begin) * 3;
   const BulkRange rx = bulk_range(xb, stage_x ? (size_t)ch.n_pts * 24 : 0);
+  const BulkRange rt = bulk_range(C.tiles + ch.tile_begin, (size_t)ch.n_tiles * sizeof(Tile));
+  const bool tab = job_table_mode(ch);
+  const BulkRange rj = bulk_range(C.jobs + ch.job_begin, tab ? (size_t)(ch.n_lc + ch.n_lp) * sizeof(Job) : 0);
+  const unsigned char* lj = C.lane_job + (size_t)local * kChunkThreads;
   fence_proxy_async_smem();
-  mbar_arrive_expect_tx(S.bar, rc.bytes + rp.bytes + rh.bytes + (stage_x ? rx.bytes : 0u));
+  mbar_arrive_expect_tx(S.bar, rc.bytes + rp.bytes + rh.bytes + (stage_x ? rx.bytes : 0u) + rt.bytes +
+                                   (tab ? rj.bytes + kStageLaneBytes : 0u));
   bulk_copy_g2s(S.idx_cam, rc.src, rc.bytes, S.bar);
   bulk_copy_g2s(S.idx_pt, rp.src, rp.bytes, S.bar);
   bulk_copy_g2s(S.chi, rh.src, rh.bytes, S.bar);
   if (stage_x && rx.bytes) bulk_copy_g2s(S.x, rx.src, rx.bytes, S.bar);
+  bulk_copy_g2s(S.tiles(b), rt.src, rt.bytes, S.bar);
+  if (tab) {
+    bulk_copy_g2s(S.jobs(b), rj.src, rj.bytes, S.bar);
+    bulk_copy_g2s(S.lanes(b), lj, kStageLaneBytes, S.bar);
+  }
 }
 
 // The view of the staged chunk (same rounding as stage_issue).
@@ -593,6 +640,7 @@ __global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed
     S.idx_pt = st + kStageIdxBytes;
     S.chi = st + 2 * kStageIdxBytes;
     S.x = st + 2 * kStageIdxBytes + kStageChiBytes;
+    S.tab = st + 2 * kStageIdxBytes + kStageChiBytes + kStageXBytes;
     S.bar = reinterpret_cast<uint64_t*>(st + kStageBytes);
     S.ok = reinterpret_cast<int*>(st + kStageBytes + 8);
     if (threadIdx.x == 0) {
@@ -600,13 +648,16 @@ __global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed
       fence_barrier_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0 && (int)blockIdx.x < total) stage_issue(bv, blockIdx.x, S);
+    if (threadIdx.x == 0 && (int)blockIdx.x < total) stage_issue(bv, blockIdx.x, S, 0);
   }
-  for (int g = blockIdx.x; g < total; g += gridDim.x) {
-    const int s = find_slot(bv.chunk_pre, bv.n, g);
-    const DevCluster& C = bv.cl[s];
-    LmState* lm = C.lm;
-    const Chunk ch = C.chunks[g - bv.chunk_pre[s]];
+  int b = 0;  // table buffer of the current chunk (mixed path)
+  for (int g = blockIdx.x; g < total; g += gridDim.x, b ^= 1) {
+    int s;
+    Chunk ch;
+    if constexpr (!MIXED) {
+      s = find_slot(bv.chunk_pre, bv.n, g);
+      ch = bv.cl[s].chunks[g - bv.chunk_pre[s]];
+    }
     ObsView V{};
     if constexpr (MIXED) {
       if (threadIdx.x == 0) *S.ok = mbar_wait_bounded(S.bar, phase, kCopyWaitNs) ? 1 : 0;
@@ -626,13 +677,23 @@ __global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed
         }
         return;
       }
-      V = stage_view(C, ch, lm->cur, S);
+      const ChunkHead* hd = S.head(b);
+      s = hd->s;
+      ch = hd->ch;
+      V = stage_view(bv.cl[s], ch, hd->cur, S);
     }
+    const DevCluster& C = bv.cl[s];
+    LmState* lm = C.lm;
     const bool active = lm->active != 0;
     // 1. linearise the chunk's tiles into shared memory
     if (active) {
       for (int t = warp; t < ch.n_tiles; t += nw) {
-        const Tile tl = C.tiles[ch.tile_begin + t];
+        Tile tl;
+        if constexpr (MIXED) {
+          tl = reinterpret_cast<const Tile*>(S.tiles(b) + bulk_range(C.tiles + ch.tile_begin, 8).lead)[t];
+        } else {
+          tl = C.tiles[ch.tile_begin + t];
+        }
         TileLin<MIXED> L;
         linearize_tile<MIXED, false>(C, lm, tl, lane, true, L, V);
         if (L.act) st_rec<MIXED>(srec + (size_t)(L.o - ch.obs_begin) * kSrec, L);
@@ -646,7 +707,7 @@ __global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed
     }
     __syncthreads();
     if constexpr (MIXED) {  // staging is free: start the copies of this CTA's next chunk
-      if (threadIdx.x == 0 && g + (int)gridDim.x < total) stage_issue(bv, g + gridDim.x, S);
+      if (threadIdx.x == 0 && g + (int)gridDim.x < total) stage_issue(bv, g + gridDim.x, S, b ^ 1);
     }
     if (!active) continue;
     // 2. Schur reductions of the chunk.  Jobs: each free camera (sum of
@@ -658,13 +719,23 @@ __global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed
     //    than threads runs one lane per job.
     const int n_jobs = ch.n_lc + ch.n_lp;  // 0 when every observation of the chunk is of a fixed camera
     if (n_jobs > 0 && n_jobs <= (int)blockDim.x) {
-      // job whose lane run holds this thread (jobs are in lane order)
-      int lo = 0, hi = n_jobs - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (C.jobs[ch.job_begin + mid].lane_begin <= (int)threadIdx.x) lo = mid; else hi = mid - 1;
+      // job whose lane run holds this thread: the last job starting at or
+      // before it (jobs are in lane order); staged by the host's table on the
+      // mixed path, a binary search on the other
+      int lo;
+      Job J;
+      if constexpr (MIXED) {
+        lo = S.lanes(b)[threadIdx.x];
+        J = reinterpret_cast<const Job*>(S.jobs(b) + bulk_range(C.jobs + ch.job_begin, 16).lead)[lo];
+      } else {
+        lo = 0;
+        int hi = n_jobs - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (C.jobs[ch.job_begin + mid].lane_begin <= (int)threadIdx.x) lo = mid; else hi = mid - 1;
+        }
+        J = C.jobs[ch.job_begin + lo];
       }
-      const Job J = C.jobs[ch.job_begin + lo];
       const bool mine = (int)threadIdx.x < J.lane_begin + J.n_lanes;
       const int part = threadIdx.x - J.lane_begin;
       const bool cam = lo < ch.n_lc;
@@ -678,21 +749,34 @@ __global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed
       __syncthreads();  // every record has been read: the lane partials may overwrite them
       if (mine && J.n_lanes > 1) {
         Real* lp = lanepart + (size_t)threadIdx.x * kLanePart;
+        if constexpr (MIXED) {
+          float4* o = reinterpret_cast<float4*>(lp);
 #pragma unroll
-        for (int i = 0; i < 39; ++i) lp[i] = acc[i];
+          for (int i = 0; i < 9; ++i) o[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+          o[9] = make_float4(acc[36], acc[37], acc[38], 0.f);
+        } else {
+          double2* o = reinterpret_cast<double2*>(lp);
+#pragma unroll
+          for (int i = 0; i < 19; ++i) o[i] = make_double2(acc[2 * i], acc[2 * i + 1]);
+          o[19] = make_double2(acc[38], 0.0);
+        }
       }
       __syncthreads();
-      // multi-lane jobs: element e of job j = sum over its lanes, in lane order
-      for (int u = threadIdx.x; u < ch.n_mjobs * kLanePart; u += blockDim.x) {
-        const int mj = u / kLanePart, e = u - mj * kLanePart;
-        const int jb = C.mjobs[ch.mjob_begin + mj];
-        const bool mcam = jb < ch.n_lc;
-        if (e >= (mcam ? 39 : 36)) continue;
-        const Job M = C.jobs[ch.job_begin + jb];
-        Real v = 0;
-        for (int l = M.lane_begin; l < M.lane_begin + M.n_lanes; ++l) v += lanepart[(size_t)l * kLanePart + e];
-        Real* out = mcam ? (Real*)C.campart + (size_t)kCamPart * M.slot : (Real*)C.pairpart + (size_t)kPairPart * M.slot;
-        out[e] = v;
+      // multi-lane jobs: the job's own lanes add its lane partials, each lane
+      // a share of the 16-byte groups of the row, every element summed over
+      // the job's lanes in lane order
+      if (mine && J.n_lanes > 1) {
+        using Vec = typename std::conditional<MIXED, float4, double2>::type;
+        constexpr int kPer = 16 / sizeof(Real);  // elements of a group
+        const int groups = (cam ? kCamPart : kPairPart) / kPer;
+        const Vec* rows = reinterpret_cast<const Vec*>(lanepart);
+        Vec* out = reinterpret_cast<Vec*>(cam ? (Real*)C.campart + (size_t)kCamPart * J.slot
+                                              : (Real*)C.pairpart + (size_t)kPairPart * J.slot);
+        for (int q = part; q < groups; q += J.n_lanes) {
+          Vec v = rows[(size_t)J.lane_begin * (kLanePart / kPer) + q];
+          for (int l = J.lane_begin + 1; l < J.lane_begin + J.n_lanes; ++l) v = vadd(v, rows[(size_t)l * (kLanePart / kPer) + q]);
+          out[q] = v;
+        }
       }
     } else {
       for (int jb = threadIdx.x; jb < n_jobs; jb += blockDim.x) {
