@@ -388,10 +388,10 @@ FLOP_LIN = dict(obs=258, free_obs=294, pair=216, pt=45)
 FLOP_BACK = dict(obs=258 + 63, free_obs=36, pair=0, pt=60)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes (read + write) per observation of one k_lin_schur launch, from an
-# ncu capture of the current kernel on 32 clusters of the same mix (87.16 MB for
+# ncu capture of the current kernel on 32 clusters of the same mix (87.95 MB for
 # 2,452,644 observations); scaled to a launch by its observations.  Set to
 # None whenever the kernel changes until it is captured again.
-LIN_SCHUR_DRAM_BYTES_PER_OBS = (80.977152e6 + 6.1824e6) / 2452644
+LIN_SCHUR_DRAM_BYTES_PER_OBS = (81.45792e6 + 6.495488e6) / 2452644
 FP64_PEAK_TFLOPS = 1.25                               # nominal dense FP64
 
 
