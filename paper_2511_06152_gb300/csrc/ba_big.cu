@@ -145,8 +145,9 @@ __global__ void __launch_bounds__(256) k_big_trsm(const DevCluster* dcl, int k) 
     Lk[r][c] = (r < nb && c <= r) ? C.F[(size_t)(c0 + r) * n + c0 + c] : 0.0;
     X[r][c] = (r < nr && c < nb) ? C.F[(size_t)(r0 + r) * n + c0 + c] : 0.0;
   }
+  __shared__ double inv[kBigNB];
+  for (int c = tid; c < nb; c += blockDim.x) inv[c] = C.bx[3 * n + c0 + c];
   __syncthreads();
-  const double* inv = C.bx + 3 * n + c0;
   for (int c = 0; c < nb; ++c) {
     for (int r = tid; r < nr; r += blockDim.x) X[r][c] *= inv[c];
     __syncthreads();
@@ -163,58 +164,79 @@ __global__ void __launch_bounds__(256) k_big_trsm(const DevCluster* dcl, int k) 
   }
 }
 
-// Tiles (i, j), k < j <= i < k + 1 + m: A_ij -= L_ik L_jk^T.  Each thread
-// computes four entries of a row of the tile.
+// Tiles (i, j), k < j <= i < k + 1 + m: A_ij -= L_ik L_jk^T, each tile as two
+// CTAs of 16 rows (twice the CTAs of the step over twice the SMs).  Each
+// thread computes two entries of a row.
+constexpr int kHalf = kBigNB / 2;
 __global__ void __launch_bounds__(256) k_big_update(const DevCluster* dcl, int k) {
   const DevCluster& C = *dcl;
   const int n = 6 * C.n_free, c0 = kBigNB * k, nb = min(kBigNB, n - c0);
-  const int t = blockIdx.x;
+  const int t = blockIdx.x >> 1, half = blockIdx.x & 1;
   int ii = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
   while ((ii + 1) * (ii + 2) / 2 <= t) ++ii;
   while (ii * (ii + 1) / 2 > t) --ii;
   const int jj = t - ii * (ii + 1) / 2;
-  const int ri = kBigNB * (k + 1 + ii), rj = kBigNB * (k + 1 + jj);
-  const int ni = min(kBigNB, n - ri), nj = min(kBigNB, n - rj);
+  const int ri = kBigNB * (k + 1 + ii) + kHalf * half, rj = kBigNB * (k + 1 + jj);
+  const int ni = min(kHalf, n - ri), nj = min(kBigNB, n - rj);
   if (ni <= 0 || nj <= 0) return;
-  __shared__ double Li[kBigNB][kBigNB + 1];
+  __shared__ double Li[kHalf][kBigNB + 1];
   __shared__ double Lj[kBigNB][kBigNB + 1];
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < kBigNB * kBigNB; idx += blockDim.x) {
+  for (int idx = tid; idx < kHalf * kBigNB; idx += blockDim.x) {
     const int r = idx / kBigNB, q = idx - r * kBigNB;
     Li[r][q] = (r < ni && q < nb) ? C.F[(size_t)(ri + r) * n + c0 + q] : 0.0;
+  }
+  for (int idx = tid; idx < kBigNB * kBigNB; idx += blockDim.x) {
+    const int r = idx / kBigNB, q = idx - r * kBigNB;
     Lj[r][q] = (r < nj && q < nb) ? C.F[(size_t)(rj + r) * n + c0 + q] : 0.0;
   }
   __syncthreads();
-  const int r = tid >> 3, cb = (tid & 7) * 4;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int r = tid >> 4, cb = (tid & 15) * 2;
+  double acc[2] = {0.0, 0.0};
   for (int q = 0; q < nb; ++q) {
     const double a = Li[r][q];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc[u] += a * Lj[cb + u][q];
+    for (int u = 0; u < 2; ++u) acc[u] += a * Lj[cb + u][q];
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < 2; ++u) {
     const int c = cb + u;
-    if (r < ni && c < nj && (ri != rj || c <= r)) C.F[(size_t)(ri + r) * n + rj + c] -= acc[u];
+    if (r < ni && c < nj && (ri - kHalf * half != rj || c <= r + kHalf * half))
+      C.F[(size_t)(ri + r) * n + rj + c] -= acc[u];
+  }
+}
+
+// Shared memory of the solve: v (n), the pivots' reciprocals (n), and the
+// strictly lower triangle of the current diagonal block.
+constexpr int kBlkLd = kBigNB + 1;
+size_t big_solve_smem(int n) { return sizeof(double) * (2 * (size_t)n + (size_t)kBigNB * kBlkLd); }
+
+// the strictly lower triangle of diagonal block r0 (nb rows) into blk (all threads)
+__device__ __forceinline__ void stage_diag_block(const DevCluster& C, int n, int r0, int nb, double* blk) {
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+    const int r = idx / nb, c = idx - r * nb;
+    blk[r * kBlkLd + c] = c < r ? C.F[(size_t)(r0 + r) * n + r0 + c] : 0.0;
   }
 }
 
 // Solve S y = v with the factor (one CTA; v and y in shared memory, y
-// overwrites v).  Per block of kBigNB rows: warp 0 sweeps the diagonal
-// triangle (lane = row), then one thread per row updates the rows inside the
-// envelope with the block's columns.
-__device__ void big_solve_cta(const DevCluster& C, double* v) {
+// overwrites v).  Per block of kBigNB rows: the block's triangle is staged in
+// shared memory and warp 0 sweeps it (lane = row), then one thread per row
+// updates the rows inside the envelope with the block's columns.
+__device__ void big_solve_cta(const DevCluster& C, double* v, double* inv, double* blk) {
   const int n = 6 * C.n_free, tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, wid = tid >> 5;
-  const double* inv = C.bx + 3 * n;
+  for (int i = tid; i < n; i += bs) inv[i] = C.bx[3 * n + i];
   const int nblk = (n + kBigNB - 1) / kBigNB;
   for (int k = 0; k < nblk; ++k) {  // L y = v
     const int r0 = kBigNB * k, nb = min(kBigNB, n - r0);
+    stage_diag_block(C, n, r0, nb, blk);
+    __syncthreads();
     if (wid == 0) {
       double y = lane < nb ? v[r0 + lane] : 0.0;
       for (int j = 0; j < nb; ++j) {
         const double yj = __shfl_sync(BA_FULL_MASK, y * inv[r0 + j], j);
         if (lane == j) y = yj;
-        else if (lane > j && lane < nb) y -= C.F[(size_t)(r0 + lane) * n + r0 + j] * yj;
+        else if (lane > j && lane < nb) y -= blk[lane * kBlkLd + j] * yj;
       }
       if (lane < nb) v[r0 + lane] = y;
     }
@@ -229,12 +251,14 @@ __device__ void big_solve_cta(const DevCluster& C, double* v) {
   }
   for (int k = nblk - 1; k >= 0; --k) {  // L^T x = y
     const int r0 = kBigNB * k, nb = min(kBigNB, n - r0);
+    stage_diag_block(C, n, r0, nb, blk);
+    __syncthreads();
     if (wid == 0) {
       double x = lane < nb ? v[r0 + lane] : 0.0;
       for (int j = nb - 1; j >= 0; --j) {
         const double xj = __shfl_sync(BA_FULL_MASK, x * inv[r0 + j], j);
         if (lane == j) x = xj;
-        else if (lane < j) x -= C.F[(size_t)(r0 + j) * n + r0 + lane] * xj;
+        else if (lane < j) x -= blk[j * kBlkLd + lane] * xj;
       }
       if (lane < nb) v[r0 + lane] = x;
     }
@@ -256,8 +280,7 @@ __global__ void __launch_bounds__(1024) k_big_solve(const DevCluster* dcl, int m
   const int n = 6 * C.n_free;
   const double* src = mode == 0 ? C.rhs : C.bx + 2 * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = src[i];
-  __syncthreads();
-  big_solve_cta(C, v);
+  big_solve_cta(C, v, v + n, v + 2 * n);
   double* x = C.bx + n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = mode == 0 ? v[i] : x[i] + v[i];
 }
@@ -342,10 +365,10 @@ void launch_big_solve(const BigRef& b, bool mixed, int refine_steps, int assembl
     const int m = b.below[k];
     if (m > 0) {
       LAUNCH(KK_FACTOR, st, k_big_trsm<<<m, 256, 0, st>>>(b.d, k));
-      LAUNCH(KK_FACTOR, st, k_big_update<<<m * (m + 1) / 2, 256, 0, st>>>(b.d, k));
+      LAUNCH(KK_FACTOR, st, k_big_update<<<m * (m + 1), 256, 0, st>>>(b.d, k));
     }
   }
-  const size_t sm = (size_t)n * sizeof(double);
+  const size_t sm = big_solve_smem(n);
   LAUNCH(KK_FACTOR, st, k_big_solve<<<1, 1024, sm, st>>>(b.d, 0));
   for (int it = 0; it < refine_steps; ++it) {
     LAUNCH(KK_FACTOR, st, k_big_resid<<<grid_for_big(n * 32, 256), 256, 0, st>>>(b.d));
@@ -356,7 +379,7 @@ void launch_big_solve(const BigRef& b, bool mixed, int refine_steps, int assembl
 }
 
 cudaError_t set_big_attributes(int max_n) {
-  const int smem = max_n * (int)sizeof(double);
+  const int smem = (int)big_solve_smem(max_n);
   return cudaFuncSetAttribute(k_big_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem > 48 * 1024 ? smem : 48 * 1024);
 }
 

@@ -1530,6 +1530,20 @@ __device__ double block_sum_tiles(const DevCluster& C, int which, double* red) {
   return tot;  // valid in thread 0
 }
 
+// Fixed-order sum over the block (warp trees, then the warps in order);
+// valid in thread 0.
+__device__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+  __syncthreads();
+  return tot;
+}
+
 __global__ void __launch_bounds__(256) k_cost_init(BatchView bv) {
   __shared__ double red[8];
   for (int s = blockIdx.x; s < bv.n; s += gridDim.x) {
@@ -1537,15 +1551,18 @@ __global__ void __launch_bounds__(256) k_cost_init(BatchView bv) {
     LmState* lm = C.lm;
     if (!lm->needs_init) continue;
     const double F = block_sum_tiles(C, 0, red);
+    // prior terms of the free images at the current state: thread t takes
+    // images t, t + blockDim.x, ... in order
+    const int cur = lm->cur;
+    double pc = 0.0;
+    for (int k = threadIdx.x; k < C.n_cams; k += blockDim.x) {
+      if (C.free_idx[k] < 0) continue;
+      pc += prior_terms(C.R + ((size_t)cur * C.n_cams + k) * 9, C.T + ((size_t)cur * C.n_cams + k) * 3,
+                        C.R_prior + 9 * k, C.T_prior + 3 * k, C.sigma_imu, C.sigma_gnss, nullptr, nullptr);
+    }
+    pc = block_sum(pc, red);
     if (threadIdx.x == 0) {
       lm->needs_init = 0;
-      const int cur = lm->cur;
-      double pc = 0.0;
-      for (int k = 0; k < C.n_cams; ++k) {
-        if (C.free_idx[k] < 0) continue;
-        pc += prior_terms(C.R + ((size_t)cur * C.n_cams + k) * 9, C.T + ((size_t)cur * C.n_cams + k) * 3,
-                          C.R_prior + 9 * k, C.T_prior + 3 * k, C.sigma_imu, C.sigma_gnss, nullptr, nullptr);
-      }
       lm->F = F + pc;
       lm->pt_fail = 0;
     }
