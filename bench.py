@@ -641,16 +641,20 @@ def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flight
     ce = ba.Context(device=torch.cuda.current_device(), precision=ba.BA_MIXED, stream=stream.cuda_stream)
     n_thr = min(16, os.cpu_count() or 1)
     times = []
+    phases = []
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with ThreadPoolExecutor(n_thr) as ex:  # ba_create_cluster is thread-safe: presort on the caller's threads
             cids = list(ex.map(ce.create_cluster, scenes))
+        t1 = time.perf_counter()
         ce.solve_batch(cids, iters)
+        t2 = time.perf_counter()
         for c in cids:
             ce.get_state(c)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
+        phases.append({"create_s": t1 - t0, "solve_batch_s": t2 - t1, "get_state_s": time.perf_counter() - t2})
         infos = [ce.cluster_info(c) for c in cids]
         presort_ms = sum(v["presort_ms"] for v in infos)
         upload_ms = sum(v["upload_ms"] for v in infos)
@@ -663,7 +667,8 @@ def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flight
                   "includes": "ba_create_cluster from host arrays (validation, presort, H2D) on "
                               f"{n_thr} host threads, batched solve, ba_get_state to host",
                   "steps": args.e2e_steps, "all_seconds": times,
-                  "host_presort_ms_summed_over_clusters": presort_ms, "upload_ms_summed_over_clusters": upload_ms}
+                  "host_presort_ms_summed_over_clusters": presort_ms, "upload_ms_summed_over_clusters": upload_ms,
+                  "phases_of_median_step": phases[sorted(range(len(times)), key=times.__getitem__)[len(times) // 2]]}
     log("cpu baseline leg")
     out["cpu_baseline"] = oracle_obs_per_s(scenes, iters, args.cpu_seconds)
     out["paper_context"] = "paper: full BA per cluster in < 2 s, MATLAB on an i7 13th-gen 20-core laptop, no GPU"

@@ -38,9 +38,11 @@
  *   - Return codes only; nothing is thrown across the ABI.  A numerical
  *     failure (a reduced camera system that is not positive definite) is
  *     reported in the per-step status and handled as a rejected LM step.
- *   - All GPU work of a context runs on the stream given in ba_config.  Calls
- *     on one context must be serialised by the caller, except ba_poll, which
- *     may be called from any thread.
+ *   - Solves run on the stream given in ba_config; ba_create_cluster uploads
+ *     on a stream of its own and the serving scheduler runs on its own.  Any
+ *     entry point may be called from any thread: the context serialises its
+ *     bookkeeping with one lock, which is not held during a cluster's host
+ *     presort, a serving round or the device run of ba_solve_batch.
  *   - Reductions are deterministic: every sum runs in a fixed order that
  *     depends only on the cluster, never on the batch it runs in, so a
  *     cluster's result is bit-identical alone and in any batch.
@@ -246,7 +248,13 @@ BA_API ba_status ba_run(ba_ctx* ctx, ba_cluster_id id, int32_t iters, ba_step_in
 /* iters LM iterations on n clusters at once: every kernel of an iteration is
  * one launch over all clusters, and the whole sequence is one CUDA-graph
  * launch.  Each cluster's result equals its ba_run result bit for bit.
- * results[n] may be NULL; trace may be NULL or [n][iters]. */
+ * results[n] may be NULL; trace may be NULL or [n][iters].  While the device
+ * runs the batch the context stays open to other threads (creating, reading
+ * or solving other clusters); the batch's own clusters are in service until
+ * the call returns: calls that write or free them fail with BA_ERR_INVALID
+ * ("cluster is in service"), and reads (ba_get_state,
+ * ba_reprojection_errors) are queued behind the batch on the context's
+ * stream, so they return its final state. */
 BA_API ba_status ba_solve_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n, int32_t iters,
                          ba_result* results, ba_step_info* trace);
 

@@ -56,6 +56,7 @@ struct Plan {
   double* gnorm = nullptr;       // device [n]
   std::map<int, GraphRec> graphs;
   GraphRec* last = nullptr;      // graph of the last launch (for timing readout)
+  cudaEvent_t done = nullptr;    // recorded behind a batch's result copies
   std::vector<BigRef> big;       // clusters whose reduced systems are solved in global memory
 };
 
@@ -122,6 +123,9 @@ struct ba_ctx {
   bool sched_stop = false;
   bool sched_started = false;
   cudaStream_t sched_stream = nullptr;  // the scheduler's rounds
+  cudaStream_t plan_stream = nullptr;   // plan tables (allocated and uploaded without waiting for the solves)
+  double* hstage = nullptr;             // pinned host staging of ba_get_state (grown on demand)
+  size_t hstage_bytes = 0;
   SlotTable slots;
 };
 
@@ -210,6 +214,7 @@ void free_plan(ba_ctx* ctx, Plan* p) {
     free_probe(kv.second.probe);
   }
   if (p->dbuf) cudaFreeAsync(p->dbuf, ctx->stream);
+  if (p->done) cudaEventDestroy(p->done);
   delete p;
 }
 
@@ -271,18 +276,22 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
     delete p;
     return set_err(ctx, BA_ERR_BUDGET, "batch plan exceeds the device-memory budget");
   }
-  cudaError_t e = pool_alloc(ctx, (void**)&p->dbuf, p->dbuf_bytes, ctx->stream);
+  // allocated and filled on the plan stream and waited for there: the
+  // solves already queued on the context's stream (another batch still on
+  // the device) are not waited for
+  cudaError_t e = pool_alloc(ctx, (void**)&p->dbuf, p->dbuf_bytes, ctx->plan_stream);
   if (e != cudaSuccess) {
     delete p;
     return set_err(ctx, BA_ERR_CUDA, std::string("plan allocation: ") + cudaGetErrorString(e));
   }
   ctx->mem += p->dbuf_bytes;
-  e = cudaMemcpyAsync(p->dbuf + o_desc, descs.data(), sizeof(DevCluster) * n, cudaMemcpyHostToDevice, ctx->stream);
+  const cudaStream_t ps = ctx->plan_stream;
+  e = cudaMemcpyAsync(p->dbuf + o_desc, descs.data(), sizeof(DevCluster) * n, cudaMemcpyHostToDevice, ps);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(p->dbuf + o_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, ctx->stream);
+    e = cudaMemcpyAsync(p->dbuf + o_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, ps);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(p->dbuf + o_ord, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    e = cudaMemcpyAsync(p->dbuf + o_ord, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ps);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
   if (e != cudaSuccess) {
     ctx->mem -= p->dbuf_bytes;
     free_plan(ctx, p);
@@ -374,8 +383,11 @@ void fill_step(const StepRec& r, ba_step_info* o) {
 }
 
 // Runs iters iterations on ids and returns per-cluster LM state and traces.
+// With lk (holding the context's lock), the lock is released while the host
+// waits for the device and taken again before returning; the caller keeps
+// the batch's clusters out of every other call meanwhile (in_service).
 ba_status run_and_collect(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, int iters, std::vector<LmState>* lm,
-                          std::vector<StepRec>* trace) {
+                          std::vector<StepRec>* trace, std::unique_lock<std::mutex>* lk = nullptr) {
   Plan* p = nullptr;
   ba_status st = get_plan(ctx, ids, &p);
   if (st != BA_OK) return st;
@@ -400,7 +412,16 @@ ba_status run_and_collect(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, in
                                   ctx->stream));
     CUDA_TRY(ctx, cudaFreeAsync(dtrace, ctx->stream));
   }
-  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (lk) {
+    if (!p->done) CUDA_TRY(ctx, cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
+    CUDA_TRY(ctx, cudaEventRecord(p->done, ctx->stream));
+    lk->unlock();
+    const cudaError_t e = cudaEventSynchronize(p->done);
+    lk->lock();
+    CUDA_TRY(ctx, e);
+  } else {
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  }
   CUDA_TRY(ctx, cudaGetLastError());
   note_direct(ctx);
   collect_timing(ctx, p);
@@ -826,6 +847,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const size_t o_dc = Lo.add(sizeof(double) * n);
   const size_t o_dc32 = Lo.add(sizeof(float) * n);
   const size_t o_tp = Lo.add(sizeof(double) * 2 * tiles.size());
+  const size_t o_ptblk = Lo.add(rs * 16 * (size_t)np);
   const size_t o_trace = Lo.add(sizeof(StepRec) * kTraceCap);
   const size_t o_desc = Lo.add(sizeof(DevCluster));
   const size_t o_F = Lo.add(big ? sizeof(double) * (size_t)n * n : 0);
@@ -984,6 +1006,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   h.camreal = mixed ? nullptr : arena + o_camreal;
   h.camdf = mixed ? (float*)(arena + o_camdf) : nullptr;
   h.tiles = (const Tile*)(arena + o_tiles);
+  h.ptblk = arena + o_ptblk;
   h.obs_cam = (const int*)(arena + o_ocam);
   h.obs_pt = (const int*)(arena + o_opt);
   h.obs_uv = (const double*)(arena + o_uv);
@@ -1321,10 +1344,12 @@ BA_API ba_status ba_init(ba_ctx** out, const ba_config* cfg) {
   props.location.id = cfg->device;
   const uint64_t keep = UINT64_MAX;
   if (cudaStreamCreateWithFlags(&ctx->sched_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->plan_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess ||
       cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, (void*)&keep) != cudaSuccess) {
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->sched_stream) cudaStreamDestroy(ctx->sched_stream);
+    if (ctx->plan_stream) cudaStreamDestroy(ctx->plan_stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return BA_ERR_CUDA;
@@ -1373,7 +1398,7 @@ BA_API ba_status ba_warm_start(ba_ctx* ctx, ba_cluster_id dst, ba_cluster_id src
   Cluster* c = find_cluster(ctx, dst);
   Cluster* s = find_cluster(ctx, src);
   if (!c || !s) return BA_ERR_NOT_FOUND;
-  if (c->in_service || s->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
+  if (c->in_service || s->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in service");
   ba_status st = warm_copy(ctx, c, s, cam_map, pt_map);
   if (st != BA_OK) return st;
   launch_camreal(one_view(c->d_desc, c->nf), ctx->mixed, ctx->stream);
@@ -1388,7 +1413,7 @@ BA_API ba_status ba_transition(ba_ctx* ctx, ba_cluster_id dst, ba_cluster_id src
   Cluster* c = find_cluster(ctx, dst);
   Cluster* s = find_cluster(ctx, src);
   if (!c || !s) return BA_ERR_NOT_FOUND;
-  if (c->in_service || s->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
+  if (c->in_service || s->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in service");
   std::vector<int2> pairs;
   for (int k = 0; k < c->nc; ++k) {
     const int m = cam_map[k];
@@ -1474,7 +1499,7 @@ BA_API ba_status ba_linearize(ba_ctx* ctx, ba_cluster_id id, ba_lin_info* out) {
   std::lock_guard<std::mutex> g(ctx->api_mu);
   Cluster* c = find_cluster(ctx, id);
   if (!c) return BA_ERR_NOT_FOUND;
-  if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
+  if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in service");
   Plan* p = nullptr;
   ba_status st = single_view(ctx, c, &p);
   if (st != BA_OK) return st;
@@ -1500,7 +1525,7 @@ BA_API ba_status ba_run(ba_ctx* ctx, ba_cluster_id id, int32_t iters, ba_step_in
   std::lock_guard<std::mutex> g(ctx->api_mu);
   Cluster* c = find_cluster(ctx, id);
   if (!c) return BA_ERR_NOT_FOUND;
-  if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
+  if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in service");
   if (iters == 0) return BA_OK;
   std::vector<StepRec> tr;
   ba_status st = run_and_collect(ctx, {id}, iters, nullptr, trace ? &tr : nullptr);
@@ -1523,12 +1548,12 @@ BA_API ba_status ba_solve_step(ba_ctx* ctx, ba_cluster_id id, ba_step_info* out)
 BA_API ba_status ba_solve_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n, int32_t iters, ba_result* results,
                          ba_step_info* trace) {
   if (!ctx || !ids || n <= 0 || iters < 0) return BA_ERR_INVALID;
-  std::lock_guard<std::mutex> g(ctx->api_mu);
+  std::unique_lock<std::mutex> g(ctx->api_mu);
   std::vector<ba_cluster_id> v(ids, ids + n);
   for (auto id : v) {
     Cluster* c = find_cluster(ctx, id);
     if (!c) return BA_ERR_NOT_FOUND;
-    if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
+    if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in service");
   }
   {
     std::vector<ba_cluster_id> s(v);
@@ -1538,7 +1563,12 @@ BA_API ba_status ba_solve_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n
   std::vector<LmState> lm;
   std::vector<StepRec> tr;
   const int tcap = std::min(iters, kTraceCap);
-  ba_status st = run_and_collect(ctx, v, iters, &lm, trace ? &tr : nullptr);
+  // The device runs the batch without the lock (other threads may create,
+  // read or solve other clusters meanwhile); the batch's own clusters are in
+  // service until it returns.
+  for (auto id : v) find_cluster(ctx, id)->in_service = 1;
+  ba_status st = run_and_collect(ctx, v, iters, &lm, trace ? &tr : nullptr, &g);
+  for (auto id : v) find_cluster(ctx, id)->in_service = 0;
   if (st != BA_OK) return st;
   for (int i = 0; i < n; ++i) {
     if (results) {
@@ -1564,7 +1594,7 @@ BA_API ba_status ba_reset(ba_ctx* ctx, ba_cluster_id id) {
   std::lock_guard<std::mutex> g(ctx->api_mu);
   Cluster* c = find_cluster(ctx, id);
   if (!c) return BA_ERR_NOT_FOUND;
-  if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
+  if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in service");
   Plan* p = nullptr;
   ba_status st = single_view(ctx, c, &p);
   if (st != BA_OK) return st;
@@ -1582,7 +1612,7 @@ BA_API ba_status ba_reset_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n
   for (auto id : v) {
     Cluster* c = find_cluster(ctx, id);
     if (!c) return BA_ERR_NOT_FOUND;
-    if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
+    if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in service");
   }
   Plan* p = nullptr;
   ba_status st = get_plan(ctx, v, &p);
@@ -1671,23 +1701,39 @@ BA_API ba_status ba_get_state(ba_ctx* ctx, ba_cluster_id id, double* R, double* 
   std::lock_guard<std::mutex> g(ctx->api_mu);
   Cluster* c = find_cluster(ctx, id);
   if (!c) return BA_ERR_NOT_FOUND;
-  LmState lm{};
-  CUDA_TRY(ctx, cudaMemcpyAsync(&lm, c->h.lm, sizeof(LmState), cudaMemcpyDeviceToHost, ctx->stream));
-  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  const cudaMemcpyKind kind = ptr_kind == BA_PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (R)
-    CUDA_TRY(ctx, cudaMemcpyAsync(R, c->h.R + (size_t)lm.cur * c->nc * 9, sizeof(double) * c->nc * 9, kind, ctx->stream));
-  if (T)
-    CUDA_TRY(ctx, cudaMemcpyAsync(T, c->h.T + (size_t)lm.cur * c->nc * 3, sizeof(double) * c->nc * 3, kind, ctx->stream));
-  if (X && c->np) {  // internal order (and double-float in the mixed path) -> caller's order, binary64
-    double* tmp = nullptr;
-    CUDA_TRY(ctx, cudaMallocAsync((void**)&tmp, sizeof(double) * (size_t)c->np * 3, ctx->stream));
-    launch_export_points(c->d_desc, c->h, ctx->mixed, tmp, ctx->stream);
-    note_direct(ctx);
-    CUDA_TRY(ctx, cudaMemcpyAsync(X, tmp, sizeof(double) * (size_t)c->np * 3, kind, ctx->stream));
+  // one kernel writes the requested parts of the current state into one
+  // device block (it reads the current buffer's index itself); host
+  // destinations get it through one copy into pinned staging
+  const size_t nr = (size_t)c->nc * 9, nt = (size_t)c->nc * 3, nx = (size_t)c->np * 3;
+  const size_t total = nr + nt + nx;
+  double* tmp = nullptr;
+  CUDA_TRY(ctx, cudaMallocAsync((void**)&tmp, sizeof(double) * total, ctx->stream));
+  launch_export_state(c->d_desc, c->h, ctx->mixed, R ? tmp : nullptr, T ? tmp + nr : nullptr,
+                      X && nx ? tmp + nr + nt : nullptr, ctx->stream);
+  note_direct(ctx);
+  if (ptr_kind == BA_PTR_DEVICE) {
+    if (R) CUDA_TRY(ctx, cudaMemcpyAsync(R, tmp, sizeof(double) * nr, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (T) CUDA_TRY(ctx, cudaMemcpyAsync(T, tmp + nr, sizeof(double) * nt, cudaMemcpyDeviceToDevice, ctx->stream));
+    if (X && nx)
+      CUDA_TRY(ctx, cudaMemcpyAsync(X, tmp + nr + nt, sizeof(double) * nx, cudaMemcpyDeviceToDevice, ctx->stream));
     CUDA_TRY(ctx, cudaFreeAsync(tmp, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return BA_OK;
   }
+  if (ctx->hstage_bytes < sizeof(double) * total) {
+    if (ctx->hstage) cudaFreeHost(ctx->hstage);
+    ctx->hstage = nullptr;
+    ctx->hstage_bytes = 0;
+    const size_t want = std::max(sizeof(double) * total, (size_t)1 << 20);
+    CUDA_TRY(ctx, cudaMallocHost((void**)&ctx->hstage, want));
+    ctx->hstage_bytes = want;
+  }
+  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hstage, tmp, sizeof(double) * total, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaFreeAsync(tmp, ctx->stream));
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (R) std::memcpy(R, ctx->hstage, sizeof(double) * nr);
+  if (T) std::memcpy(T, ctx->hstage + nr, sizeof(double) * nt);
+  if (X && nx) std::memcpy(X, ctx->hstage + nr + nt, sizeof(double) * nx);
   return BA_OK;
 }
 
@@ -1731,7 +1777,7 @@ BA_API ba_status ba_destroy_cluster(ba_ctx* ctx, ba_cluster_id id) {
   std::lock_guard<std::mutex> g(ctx->api_mu);
   Cluster* c = find_cluster(ctx, id);
   if (!c) return BA_ERR_NOT_FOUND;
-  if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in the serving queue");
+  if (c->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in service");
   // stream-ordered: the arena is released after the work already queued on
   // the context's stream; serving rounds that used it have completed
   drop_plans_with(ctx, id);
@@ -1765,6 +1811,8 @@ BA_API ba_status ba_shutdown(ba_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   cudaMemPoolDestroy(ctx->pool);
   cudaStreamDestroy(ctx->sched_stream);
+  cudaStreamDestroy(ctx->plan_stream);
+  if (ctx->hstage) cudaFreeHost(ctx->hstage);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return BA_OK;

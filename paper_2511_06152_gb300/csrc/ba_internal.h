@@ -138,6 +138,11 @@ struct DevCluster {
   void* camreal;           // FP64 path: double [nc][20]: R[9], T[3], intr[7], free flag
   float* camdf;            // mixed path: [2][nc][kCamDf] double-float cameras
 
+  // per point, from the current iteration's linearisation: M = L^-1 of the
+  // damped point block (m00 m10 m11 m20 m21 m22), q = M g_p, D_p, g_p, pad;
+  // Real [n_pts][16], written by the linearise+Schur kernel for the
+  // back-substitution
+  void* ptblk;
   const Tile* tiles;       // [n_tiles]
   const int* obs_cam;      // [no] point-major
   const int* obs_pt;       // [no] point-major, internal point index
@@ -273,7 +278,8 @@ void launch_iteration(const BatchView& bv, bool mixed, int refine_steps, cudaStr
 void launch_grad_norm(const BatchView& bv, bool mixed, double* out, cudaStream_t st,
                       const std::vector<BigRef>* big = nullptr);
 void launch_reproj(const DevCluster* dcl, const DevCluster& hcl, bool mixed, double* err_pm, cudaStream_t st);
-void launch_export_points(const DevCluster* dcl, const DevCluster& hcl, bool mixed, double* out, cudaStream_t st);
+void launch_export_state(const DevCluster* dcl, const DevCluster& hcl, bool mixed, double* R, double* T, double* X,
+                         cudaStream_t st);
 size_t factor_smem_bytes(int max_n);
 int chunk_obs(bool mixed);
 int chunk_tiles(bool mixed);

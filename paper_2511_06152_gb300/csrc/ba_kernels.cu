@@ -194,6 +194,16 @@ __global__ void k_camdf_all(BatchView bv) {
 
 // ------------------------------------------------------------------ per-tile linearisation
 
+__device__ __forceinline__ void ld4(const float* r, int at, float* o) {
+  const float4 v = *reinterpret_cast<const float4*>(r + at);
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* r, int at, double* o) {
+  const double2 a = *reinterpret_cast<const double2*>(r + at);
+  const double2 b = *reinterpret_cast<const double2*>(r + at + 2);
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+
 // What one lane knows after linearising its observation of a tile: the
 // whitened, robust-weighted Jacobians and residual, Z = Jc^T Jp L^-T, and
 // (broadcast from the point's first lane) L^-1 and q = L^-1 g_p of the damped
@@ -228,7 +238,10 @@ __device__ __forceinline__ ObsView global_view(const DevCluster& C, int cur) {
 
 // Linearise one tile (one warp).  The same arithmetic wherever it is called
 // (the back-substitution linearises again rather than storing the result).
-template <bool MIXED, bool WANT_Z = true>
+// PT_BUF: the point blocks' M, q, D_p and g_p are read from C.ptblk, where
+// the linearise+Schur kernel of the same iteration stored them (same values),
+// instead of being reduced and factored again.
+template <bool MIXED, bool WANT_Z = true, bool PT_BUF = false>
 __device__ __forceinline__ void linearize_tile(const DevCluster& C, LmState* lm, const Tile& tl, int lane,
                                                bool report_fail, TileLin<MIXED>& L, const ObsView& V) {
   using Real = typename RealOf<MIXED>::T;
@@ -297,61 +310,73 @@ __device__ __forceinline__ void linearize_tile(const DevCluster& C, LmState* lm,
       for (int i = 0; i < 12; ++i) L.Jc[i] = 0;
     }
   }
-  // point blocks by segmented reduction
-  Real v00 = Jp[0] * Jp[0] + Jp[3] * Jp[3];
-  Real v01 = Jp[0] * Jp[1] + Jp[3] * Jp[4];
-  Real v02 = Jp[0] * Jp[2] + Jp[3] * Jp[5];
-  Real v11 = Jp[1] * Jp[1] + Jp[4] * Jp[4];
-  Real v12 = Jp[1] * Jp[2] + Jp[4] * Jp[5];
-  Real v22 = Jp[2] * Jp[2] + Jp[5] * Jp[5];
-  Real g0 = -(Jp[0] * L.r0 + Jp[3] * L.r1);
-  Real g1 = -(Jp[1] * L.r0 + Jp[4] * L.r1);
-  Real g2 = -(Jp[2] * L.r0 + Jp[5] * L.r1);
-  v00 = seg_reduce(v00, lane, L.seg_start, L.seg_end, L.span);
-  v01 = seg_reduce(v01, lane, L.seg_start, L.seg_end, L.span);
-  v02 = seg_reduce(v02, lane, L.seg_start, L.seg_end, L.span);
-  v11 = seg_reduce(v11, lane, L.seg_start, L.seg_end, L.span);
-  v12 = seg_reduce(v12, lane, L.seg_start, L.seg_end, L.span);
-  v22 = seg_reduce(v22, lane, L.seg_start, L.seg_end, L.span);
-  g0 = seg_reduce(g0, lane, L.seg_start, L.seg_end, L.span);
-  g1 = seg_reduce(g1, lane, L.seg_start, L.seg_end, L.span);
-  g2 = seg_reduce(g2, lane, L.seg_start, L.seg_end, L.span);
-  // head: damp, factor V* = L L^T, M = L^-1, q = M g_p
-  Real m00 = 0, m10 = 0, m11 = 0, m20 = 0, m21 = 0, m22 = 0, q0 = 0, q1 = 0, q2 = 0;
-  L.d0 = L.d1 = L.d2 = 0;
-  L.g0 = g0; L.g1 = g1; L.g2 = g2;
-  if (L.head) {
-    const Real d0 = clamp_diag(v00), d1 = clamp_diag(v11), d2 = clamp_diag(v22);
-    const Real a00 = v00 + mu * d0, a11 = v11 + mu * d1, a22 = v22 + mu * d2;
-    // V* = L L^T with M = L^-1 from reciprocal square roots of the pivots
-    bool ok = a00 > Real(0);
-    m00 = rsqrt_any(ok ? a00 : Real(1));
-    const Real l10 = v01 * m00, l20 = v02 * m00;
-    const Real t11 = a11 - l10 * l10;
-    ok = ok && t11 > Real(0);
-    m11 = rsqrt_any(t11 > Real(0) ? t11 : Real(1));
-    const Real l21 = (v12 - l20 * l10) * m11;
-    const Real t22 = a22 - l20 * l20 - l21 * l21;
-    ok = ok && t22 > Real(0);
-    m22 = rsqrt_any(t22 > Real(0) ? t22 : Real(1));
-    if (!ok && report_fail) lm->pt_fail = 1;  // point block not positive definite: reject this step
-    m10 = -l10 * m00 * m11;
-    m21 = -l21 * m11 * m22;
-    m20 = -(l20 * m00 + l21 * m10) * m22;
-    q0 = m00 * g0;
-    q1 = m10 * g0 + m11 * g1;
-    q2 = m20 * g0 + m21 * g1 + m22 * g2;
-    L.d0 = d0; L.d1 = d1; L.d2 = d2;
+  if constexpr (PT_BUF) {
+    // every lane of a point reads its block (one address per point); an
+    // inactive lane reads point 0 and keeps P = 0 (its Jp is 0)
+    const Real* pb = reinterpret_cast<const Real*>(C.ptblk) + (size_t)(L.act ? L.j : 0) * 16;
+    Real w[16];
+    ld4(pb, 0, w); ld4(pb, 4, w + 4); ld4(pb, 8, w + 8); ld4(pb, 12, w + 12);
+    L.m00 = w[0]; L.m10 = w[1]; L.m11 = w[2]; L.m20 = w[3]; L.m21 = w[4]; L.m22 = w[5];
+    L.q0 = w[6]; L.q1 = w[7]; L.q2 = w[8];
+    L.d0 = w[9]; L.d1 = w[10]; L.d2 = w[11];
+    L.g0 = w[12]; L.g1 = w[13]; L.g2 = w[14];
+  } else {
+    // point blocks by segmented reduction
+    Real v00 = Jp[0] * Jp[0] + Jp[3] * Jp[3];
+    Real v01 = Jp[0] * Jp[1] + Jp[3] * Jp[4];
+    Real v02 = Jp[0] * Jp[2] + Jp[3] * Jp[5];
+    Real v11 = Jp[1] * Jp[1] + Jp[4] * Jp[4];
+    Real v12 = Jp[1] * Jp[2] + Jp[4] * Jp[5];
+    Real v22 = Jp[2] * Jp[2] + Jp[5] * Jp[5];
+    Real g0 = -(Jp[0] * L.r0 + Jp[3] * L.r1);
+    Real g1 = -(Jp[1] * L.r0 + Jp[4] * L.r1);
+    Real g2 = -(Jp[2] * L.r0 + Jp[5] * L.r1);
+    v00 = seg_reduce(v00, lane, L.seg_start, L.seg_end, L.span);
+    v01 = seg_reduce(v01, lane, L.seg_start, L.seg_end, L.span);
+    v02 = seg_reduce(v02, lane, L.seg_start, L.seg_end, L.span);
+    v11 = seg_reduce(v11, lane, L.seg_start, L.seg_end, L.span);
+    v12 = seg_reduce(v12, lane, L.seg_start, L.seg_end, L.span);
+    v22 = seg_reduce(v22, lane, L.seg_start, L.seg_end, L.span);
+    g0 = seg_reduce(g0, lane, L.seg_start, L.seg_end, L.span);
+    g1 = seg_reduce(g1, lane, L.seg_start, L.seg_end, L.span);
+    g2 = seg_reduce(g2, lane, L.seg_start, L.seg_end, L.span);
+    // head: damp, factor V* = L L^T, M = L^-1, q = M g_p
+    Real m00 = 0, m10 = 0, m11 = 0, m20 = 0, m21 = 0, m22 = 0, q0 = 0, q1 = 0, q2 = 0;
+    L.d0 = L.d1 = L.d2 = 0;
+    L.g0 = g0; L.g1 = g1; L.g2 = g2;
+    if (L.head) {
+      const Real d0 = clamp_diag(v00), d1 = clamp_diag(v11), d2 = clamp_diag(v22);
+      const Real a00 = v00 + mu * d0, a11 = v11 + mu * d1, a22 = v22 + mu * d2;
+      // V* = L L^T with M = L^-1 from reciprocal square roots of the pivots
+      bool ok = a00 > Real(0);
+      m00 = rsqrt_any(ok ? a00 : Real(1));
+      const Real l10 = v01 * m00, l20 = v02 * m00;
+      const Real t11 = a11 - l10 * l10;
+      ok = ok && t11 > Real(0);
+      m11 = rsqrt_any(t11 > Real(0) ? t11 : Real(1));
+      const Real l21 = (v12 - l20 * l10) * m11;
+      const Real t22 = a22 - l20 * l20 - l21 * l21;
+      ok = ok && t22 > Real(0);
+      m22 = rsqrt_any(t22 > Real(0) ? t22 : Real(1));
+      if (!ok && report_fail) lm->pt_fail = 1;  // point block not positive definite: reject this step
+      m10 = -l10 * m00 * m11;
+      m21 = -l21 * m11 * m22;
+      m20 = -(l20 * m00 + l21 * m10) * m22;
+      q0 = m00 * g0;
+      q1 = m10 * g0 + m11 * g1;
+      q2 = m20 * g0 + m21 * g1 + m22 * g2;
+      L.d0 = d0; L.d1 = d1; L.d2 = d2;
+    }
+    L.m00 = __shfl_sync(BA_FULL_MASK, m00, L.seg_start);
+    L.m10 = __shfl_sync(BA_FULL_MASK, m10, L.seg_start);
+    L.m11 = __shfl_sync(BA_FULL_MASK, m11, L.seg_start);
+    L.m20 = __shfl_sync(BA_FULL_MASK, m20, L.seg_start);
+    L.m21 = __shfl_sync(BA_FULL_MASK, m21, L.seg_start);
+    L.m22 = __shfl_sync(BA_FULL_MASK, m22, L.seg_start);
+    L.q0 = __shfl_sync(BA_FULL_MASK, q0, L.seg_start);
+    L.q1 = __shfl_sync(BA_FULL_MASK, q1, L.seg_start);
+    L.q2 = __shfl_sync(BA_FULL_MASK, q2, L.seg_start);
   }
-  L.m00 = __shfl_sync(BA_FULL_MASK, m00, L.seg_start);
-  L.m10 = __shfl_sync(BA_FULL_MASK, m10, L.seg_start);
-  L.m11 = __shfl_sync(BA_FULL_MASK, m11, L.seg_start);
-  L.m20 = __shfl_sync(BA_FULL_MASK, m20, L.seg_start);
-  L.m21 = __shfl_sync(BA_FULL_MASK, m21, L.seg_start);
-  L.m22 = __shfl_sync(BA_FULL_MASK, m22, L.seg_start);
-  L.q0 = __shfl_sync(BA_FULL_MASK, q0, L.seg_start);
-  L.q1 = __shfl_sync(BA_FULL_MASK, q1, L.seg_start);
-  L.q2 = __shfl_sync(BA_FULL_MASK, q2, L.seg_start);
   // P = Jp M^T (2x3), Z = Jc^T P (6x3)
   const Real P00 = Jp[0] * L.m00;
   const Real P01 = Jp[0] * L.m10 + Jp[1] * L.m11;
@@ -379,16 +404,6 @@ __device__ __forceinline__ void linearize_tile(const DevCluster& C, LmState* lm,
 // observation's share of the image block is Jc^T Jc - Z Z^T = Jc^T W Jc, of
 // the right-hand side Z q = Jc^T u, and of a pair block
 // Z_a Z_b^T = Jc_a^T (P_a P_b^T) Jc_b.
-__device__ __forceinline__ void ld4(const float* r, int at, float* o) {
-  const float4 v = *reinterpret_cast<const float4*>(r + at);
-  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-}
-__device__ __forceinline__ void ld4(const double* r, int at, double* o) {
-  const double2 a = *reinterpret_cast<const double2*>(r + at);
-  const double2 b = *reinterpret_cast<const double2*>(r + at + 2);
-  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
-}
-
 // Jc (12) and P (6)
 template <typename Real>
 __device__ __forceinline__ void ld_rec_jcp(const Real* r, Real Jc[12], Real P[6]) {
@@ -438,6 +453,24 @@ __device__ __forceinline__ void st_rec(typename RealOf<MIXED>::T* r, const TileL
     double2* o = reinterpret_cast<double2*>(r);
 #pragma unroll
     for (int i = 0; i < 14; ++i) o[i] = make_double2(v[2 * i], v[2 * i + 1]);
+  }
+}
+
+// The point's block for the back-substitution (head lane of the point).
+template <bool MIXED>
+__device__ __forceinline__ void st_ptblk(const DevCluster& C, const TileLin<MIXED>& L) {
+  using Real = typename RealOf<MIXED>::T;
+  const Real v[16] = {L.m00, L.m10, L.m11, L.m20, L.m21, L.m22, L.q0, L.q1,
+                      L.q2,  L.d0,  L.d1,  L.d2,  L.g0,  L.g1,  L.g2, Real(0)};
+  Real* pb = reinterpret_cast<Real*>(C.ptblk) + (size_t)L.j * 16;
+  if constexpr (MIXED) {
+    float4* o = reinterpret_cast<float4*>(pb);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) o[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  } else {
+    double2* o = reinterpret_cast<double2*>(pb);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) o[i] = make_double2(v[2 * i], v[2 * i + 1]);
   }
 }
 
@@ -697,6 +730,7 @@ __global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed
         TileLin<MIXED> L;
         linearize_tile<MIXED, false>(C, lm, tl, lane, true, L, V);
         if (L.act) st_rec<MIXED>(srec + (size_t)(L.o - ch.obs_begin) * kSrec, L);
+        if (L.head) st_ptblk<MIXED>(C, L);
         if (diag) {  // largest |g_p| of the tile, for the gradient norm
           double gm = L.head ? fmax(fabs((double)L.g0), fmax(fabs((double)L.g1), fabs((double)L.g2))) : 0.0;
 #pragma unroll
@@ -1324,7 +1358,7 @@ __global__ void __launch_bounds__(256) k_backsub_cost(BatchView bv) {
     const int local = g - bv.tile_pre[s];
     const Tile tl = C.tiles[local];
     TileLin<MIXED> L;
-    linearize_tile<MIXED, false>(C, lm, tl, lane, false, L, global_view(C, lm->cur));
+    linearize_tile<MIXED, false, true>(C, lm, tl, lane, false, L, global_view(C, lm->cur));
     const int cur = lm->cur;
     Real mu_r;
     if constexpr (MIXED) mu_r = lm->mu_f; else mu_r = lm->mu;
@@ -1685,10 +1719,22 @@ __global__ void k_reproj(const DevCluster* dcl, int mixed, double* err) {
   }
 }
 
-__global__ void k_export_points(const DevCluster* dcl, int mixed, double* out) {
+// The current state in the caller's layout, binary64: R [nc][9] and T [nc][3]
+// of the current buffer, X [np][3] in the caller's point order (any output
+// may be null).
+__global__ void k_export_state(const DevCluster* dcl, int mixed, double* R, double* T, double* out) {
   const DevCluster& C = *dcl;
   const int cur = C.lm->cur;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < C.n_pts; j += gridDim.x * blockDim.x) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 12 * C.n_cams; i += stride) {
+    if (i < 9 * C.n_cams) {
+      if (R) R[i] = C.R[(size_t)cur * C.n_cams * 9 + i];
+    } else if (T) {
+      T[i - 9 * C.n_cams] = C.T[(size_t)cur * C.n_cams * 3 + i - 9 * C.n_cams];
+    }
+  }
+  if (!out) return;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < C.n_pts; j += stride) {
     double X[3];
     point_f64(C, mixed, cur, j, X);
     const int u = C.pt_perm[j];  // caller's index
@@ -2015,8 +2061,10 @@ void launch_reproj(const DevCluster* dcl, const DevCluster& hcl, bool mixed, dou
   LAUNCH(KK_OTHER, st, k_reproj<<<grid_for(hcl.n_obs, 256, num_sms() * 8), 256, 0, st>>>(dcl, mixed, err_pm));
 }
 
-void launch_export_points(const DevCluster* dcl, const DevCluster& hcl, bool mixed, double* out, cudaStream_t st) {
-  LAUNCH(KK_OTHER, st, k_export_points<<<grid_for(hcl.n_pts, 256, num_sms() * 8), 256, 0, st>>>(dcl, mixed, out));
+void launch_export_state(const DevCluster* dcl, const DevCluster& hcl, bool mixed, double* R, double* T, double* X,
+                         cudaStream_t st) {
+  const int items = hcl.n_pts > 12 * hcl.n_cams ? hcl.n_pts : 12 * hcl.n_cams;
+  LAUNCH(KK_OTHER, st, k_export_state<<<grid_for(items, 256, num_sms() * 8), 256, 0, st>>>(dcl, mixed, R, T, X));
 }
 
 cudaError_t set_kernel_attributes(int max_n) {

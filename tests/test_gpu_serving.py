@@ -220,3 +220,34 @@ def test_transition_matches_oracle(precision):
         np.testing.assert_allclose(T2[k], T, rtol=0, atol=1e-9)
         blended += 1
     assert blended >= 1
+
+
+def test_creation_during_batch_solve_equals_sequential():
+    """A batch is solved on one thread while other clusters are created on
+    worker threads (the batch's device run holds no lock); both groups end in
+    the states of the same work done one call after another, and the batch's
+    clusters are in service until the solve returns."""
+    from concurrent.futures import ThreadPoolExecutor
+    import paper_2511_06152_gb300 as ba
+    group_a = [sg.tiny_cluster(7100 + i, 2, 8, 1500) for i in range(6)]
+    group_b = [sg.tiny_cluster(7200 + i, 2, 7, 1200) for i in range(6)]
+    with ba.Context(precision=ba.BA_MIXED) as ctx:
+        ida = [ctx.create_cluster(s) for s in group_a]
+        ctx.solve_batch(ida, 8)
+        ref_a = [ctx.get_state(c) for c in ida]
+        idb = [ctx.create_cluster(s) for s in group_b]
+        ctx.solve_batch(idb, 8)
+        ref_b = [ctx.get_state(c) for c in idb]
+    with ba.Context(precision=ba.BA_MIXED) as ctx, ThreadPoolExecutor(4) as ex:
+        ida = [ctx.create_cluster(s) for s in group_a]
+        solving = ex.submit(ctx.solve_batch, ida, 8)
+        idb = list(ex.map(ctx.create_cluster, group_b))
+        res = solving.result()
+        assert all(r["status"] == 0 for r in res)
+        ctx.solve_batch(idb, 8)
+        for cid, ref in zip(ida, ref_a):
+            for x, y in zip(ctx.get_state(cid), ref):
+                assert np.array_equal(x, y)
+        for cid, ref in zip(idb, ref_b):
+            for x, y in zip(ctx.get_state(cid), ref):
+                assert np.array_equal(x, y)
