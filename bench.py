@@ -378,20 +378,23 @@ def run_reference(args):
 #               image (21 entries of Jc^T Jc - Z Z^T at 10, -Jc^T r 24, Z q 36,
 #               diag 24) + 216 / pair entry (36 entries of Z_a Z_b^T at 6)
 #               + 45 / point (damping, 3x3 Cholesky, inverse, q)
-#   backsub     258 / observation (relinearisation) + 36 / free observation
-#               (Z^T dc) + 63 / observation (candidate residual and Huber cost)
-#               + 60 / point (linearisation head, M^T (q - s), update)
+#   backsub     236 / observation (relinearisation without the point-block
+#               terms: projection 54, Huber 4, Jacobians 91, P 24; candidate
+#               residual and Huber cost 63) + 36 / free observation (P^T Jc dc)
+#               + 30 / point (M^T (q - s), pred term, update; the point block
+#               itself is read, not recomputed)
 #   bytes (lin_schur): per observation image index 4 + point index 4 +
-#               observation 8 B; per point state 24 B; per free observation
-#               2 B (list); per pair entry 4 B; per chunk partial 156 / 144 B written
+#               observation 8 B; per point state 24 B read and its block
+#               64 B written; per free observation 2 B (list); per pair entry
+#               4 B; per chunk partial 156 / 144 B written
 FLOP_LIN = dict(obs=258, free_obs=294, pair=216, pt=45)
-FLOP_BACK = dict(obs=258 + 63, free_obs=36, pair=0, pt=60)
+FLOP_BACK = dict(obs=236, free_obs=36, pair=0, pt=30)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes (read + write) per observation of one k_lin_schur launch, from an
-# ncu capture of the current kernel on 32 clusters of the same mix (87.95 MB for
+# ncu capture of the current kernel on 32 clusters of the same mix (120.73 MB for
 # 2,452,644 observations); scaled to a launch by its observations.  Set to
 # None whenever the kernel changes until it is captured again.
-LIN_SCHUR_DRAM_BYTES_PER_OBS = (81.45792e6 + 6.495488e6) / 2452644
+LIN_SCHUR_DRAM_BYTES_PER_OBS = (81.478912e6 + 39.24992e6) / 2452644
 FP64_PEAK_TFLOPS = 1.25                               # nominal dense FP64
 
 
@@ -423,7 +426,7 @@ def kernel_work(kind, u, infos, refine):
 
 
 def lin_schur_bytes(u):
-    return u["obs"] * 16 + u["pt"] * 24 + u["free_obs"] * 2 + u["pair"] * 4 + u["cslots"] * 156 + u["pslots"] * 144
+    return u["obs"] * 16 + u["pt"] * (24 + 64) + u["free_obs"] * 2 + u["pair"] * 4 + u["cslots"] * 156 + u["pslots"] * 144
 
 
 def factor_flops(infos, refine):
@@ -650,8 +653,7 @@ def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flight
         t1 = time.perf_counter()
         ce.solve_batch(cids, iters)
         t2 = time.perf_counter()
-        for c in cids:
-            ce.get_state(c)
+        ce.get_state_batch(cids)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
         phases.append({"create_s": t1 - t0, "solve_batch_s": t2 - t1, "get_state_s": time.perf_counter() - t2})
@@ -665,7 +667,7 @@ def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flight
     out["e2e"] = {"value": tot * iters / statistics.median(times), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                   "d2h_bytes_per_step": int(d2h), "seconds_per_step": statistics.median(times),
                   "includes": "ba_create_cluster from host arrays (validation, presort, H2D) on "
-                              f"{n_thr} host threads, batched solve, ba_get_state to host",
+                              f"{n_thr} host threads, batched solve, ba_get_state_batch to host",
                   "steps": args.e2e_steps, "all_seconds": times,
                   "host_presort_ms_summed_over_clusters": presort_ms, "upload_ms_summed_over_clusters": upload_ms,
                   "phases_of_median_step": phases[sorted(range(len(times)), key=times.__getitem__)[len(times) // 2]]}

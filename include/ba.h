@@ -279,6 +279,15 @@ BA_API ba_status ba_poll(ba_ctx* ctx, ba_ticket t, ba_result* out);
  * BA_PTR_HOST, device pointers when BA_PTR_DEVICE; any may be NULL. */
 BA_API ba_status ba_get_state(ba_ctx* ctx, ba_cluster_id id, double* R, double* T, double* X, int32_t ptr_kind);
 
+/* The current states of n clusters at once, each as ba_get_state returns it
+ * (binary64, caller's point order), into host memory: R[i], T[i], X[i] are
+ * the host destinations of cluster ids[i] ([nc][9], [nc][3], [np][3]; an
+ * entry, or a whole array, may be NULL).  One device export per cluster into
+ * one block, one copy to the host, one wait.  BA_ERR_NOT_FOUND if an id is
+ * unknown (nothing is written then). */
+BA_API ba_status ba_get_state_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n, double* const* R,
+                                    double* const* T, double* const* X);
+
 /* Per-observation reprojection error norms |pi(...) - p| in pixels at the
  * current state, in the caller's observation order (host buffer [n_obs]). */
 BA_API ba_status ba_reprojection_errors(ba_ctx* ctx, ba_cluster_id id, double* err);

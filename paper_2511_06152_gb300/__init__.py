@@ -98,7 +98,8 @@ class ba_dsm(ctypes.Structure):
 
 
 EXPORTS = ["ba_init", "ba_create_cluster", "ba_linearize", "ba_solve_step", "ba_run", "ba_solve_batch", "ba_reset",
-           "ba_reset_batch", "ba_submit", "ba_poll", "ba_get_state", "ba_reprojection_errors", "ba_memory_in_use",
+           "ba_reset_batch", "ba_submit", "ba_poll", "ba_get_state", "ba_get_state_batch", "ba_reprojection_errors",
+           "ba_memory_in_use",
            "ba_launch_count", "ba_kernel_stats", "ba_cost_noalloc", "ba_warm_start", "ba_transition", "ba_footprints", "ba_footprint_overlaps", "ba_get_cluster_info", "ba_destroy_cluster", "ba_shutdown",
            "ba_status_string", "ba_last_error"]
 
@@ -138,6 +139,8 @@ def lib(build: bool = True):
             L.ba_submit.argtypes = [vp, u64, ctypes.POINTER(ba_solve_opts), ctypes.POINTER(u64)]
             L.ba_poll.argtypes = [vp, u64, ctypes.POINTER(ba_result)]
             L.ba_get_state.argtypes = [vp, u64, _dp, _dp, _dp, ctypes.c_int32]
+            _pp = ctypes.POINTER(ctypes.c_void_p)
+            L.ba_get_state_batch.argtypes = [vp, ctypes.POINTER(u64), ctypes.c_int32, _pp, _pp, _pp]
             L.ba_reprojection_errors.argtypes = [vp, u64, _dp]
             L.ba_memory_in_use.argtypes = [vp, ctypes.POINTER(u64)]
             L.ba_get_cluster_info.argtypes = [vp, u64, ctypes.POINTER(ba_cluster_info)]
@@ -313,6 +316,23 @@ class Context:
         R, T, X = np.zeros((nc, 9)), np.zeros((nc, 3)), np.zeros((max(npt, 1), 3))
         _check(self.L.ba_get_state(self.h, cid, _d(R), _d(T), _d(X), BA_PTR_HOST), self.h, "ba_get_state")
         return R, T, X[:npt]
+
+    def get_state_batch(self, cids):
+        """The current states of several clusters in one call: a list of
+        (R, T, X) as get_state returns them."""
+        cids = list(cids)
+        n = len(cids)
+        out = []
+        ptrs = [(ctypes.c_void_p * max(n, 1))() for _ in range(3)]
+        for i, cid in enumerate(cids):
+            nc, npt, _ = self.sizes[cid]
+            R, T, X = np.empty((nc, 9)), np.empty((nc, 3)), np.empty((max(npt, 1), 3))
+            for a, arr in zip(ptrs, (R, T, X)):
+                a[i] = arr.ctypes.data
+            out.append((R, T, X, npt))
+        ids = (ctypes.c_uint64 * max(n, 1))(*cids)
+        _check(self.L.ba_get_state_batch(self.h, ids, n, ptrs[0], ptrs[1], ptrs[2]), self.h, "ba_get_state_batch")
+        return [(R, T, X[:npt]) for R, T, X, npt in out]
 
     def reprojection_errors(self, cid):
         _, _, no = self.sizes[cid]

@@ -1737,6 +1737,49 @@ BA_API ba_status ba_get_state(ba_ctx* ctx, ba_cluster_id id, double* R, double* 
   return BA_OK;
 }
 
+BA_API ba_status ba_get_state_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n, double* const* R,
+                                    double* const* T, double* const* X) {
+  if (!ctx || (n > 0 && !ids) || n < 0) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  std::vector<Cluster*> cs(n);
+  std::vector<size_t> off((size_t)n + 1, 0);  // doubles before cluster i's [R | T | X] in the block
+  for (int i = 0; i < n; ++i) {
+    cs[i] = find_cluster(ctx, ids[i]);
+    if (!cs[i]) return BA_ERR_NOT_FOUND;
+    off[i + 1] = off[i] + (size_t)cs[i]->nc * 12 + (size_t)cs[i]->np * 3;
+  }
+  const size_t total = off[n];
+  if (total == 0) return BA_OK;
+  double* tmp = nullptr;
+  CUDA_TRY(ctx, cudaMallocAsync((void**)&tmp, sizeof(double) * total, ctx->stream));
+  for (int i = 0; i < n; ++i) {
+    const Cluster* c = cs[i];
+    double* b = tmp + off[i];
+    launch_export_state(c->d_desc, c->h, ctx->mixed, b, b + (size_t)c->nc * 9, c->np ? b + (size_t)c->nc * 12 : nullptr,
+                        ctx->stream);
+  }
+  note_direct(ctx);
+  if (ctx->hstage_bytes < sizeof(double) * total) {
+    if (ctx->hstage) cudaFreeHost(ctx->hstage);
+    ctx->hstage = nullptr;
+    ctx->hstage_bytes = 0;
+    CUDA_TRY(ctx, cudaMallocHost((void**)&ctx->hstage, sizeof(double) * total));
+    ctx->hstage_bytes = sizeof(double) * total;
+  }
+  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hstage, tmp, sizeof(double) * total, cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaFreeAsync(tmp, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < n; ++i) {
+    const Cluster* c = cs[i];
+    const double* b = ctx->hstage + off[i];
+    const size_t nr = (size_t)c->nc * 9, nt = (size_t)c->nc * 3, nx = (size_t)c->np * 3;
+    if (R && R[i]) std::memcpy(R[i], b, sizeof(double) * nr);
+    if (T && T[i]) std::memcpy(T[i], b + nr, sizeof(double) * nt);
+    if (X && X[i] && nx) std::memcpy(X[i], b + nr + nt, sizeof(double) * nx);
+  }
+  return BA_OK;
+}
+
 BA_API ba_status ba_reprojection_errors(ba_ctx* ctx, ba_cluster_id id, double* err) {
   if (!ctx || !err) return BA_ERR_INVALID;
   std::lock_guard<std::mutex> g(ctx->api_mu);

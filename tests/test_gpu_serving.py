@@ -251,3 +251,18 @@ def test_creation_during_batch_solve_equals_sequential():
         for cid, ref in zip(idb, ref_b):
             for x, y in zip(ctx.get_state(cid), ref):
                 assert np.array_equal(x, y)
+
+
+def test_get_state_batch_equals_get_state():
+    """One batched read-back returns, cluster by cluster, exactly what
+    get_state returns (R, T of the current buffer, X in the caller's order)."""
+    import paper_2511_06152_gb300 as ba
+    scenes = [sg.tiny_cluster(7300 + i, 2, 6 + i, 900 + 100 * i) for i in range(5)]
+    for prec in (ba.BA_MIXED, ba.BA_FP64):
+        with ba.Context(precision=prec) as ctx:
+            ids = [ctx.create_cluster(s) for s in scenes]
+            ctx.solve_batch(ids[:3], 4)  # some clusters moved, some still at their initial state
+            got = ctx.get_state_batch(ids)
+            for cid, (R, T, X) in zip(ids, got):
+                R1, T1, X1 = ctx.get_state(cid)
+                assert np.array_equal(R, R1) and np.array_equal(T, T1) and np.array_equal(X, X1)
