@@ -107,6 +107,10 @@ struct ba_ctx {
   int attr_max_n = 0;
   bool timing = false;
   std::mutex stats_mu;  // kernel statistics (API threads and the scheduler)
+  // pinned host staging buffers of cluster creation, reused across calls (one
+  // per concurrent creation; taken and returned under stage_mu)
+  std::mutex stage_mu;
+  std::vector<std::pair<char*, size_t>> stage_free;
   double kms[KK_COUNT] = {0};
   uint64_t klaunch[KK_COUNT] = {0};
   std::atomic<uint64_t> launches{0};
@@ -159,19 +163,38 @@ struct Layout {
   }
 };
 
+// A read-only input array of ba_create_cluster: the caller's host memory in
+// place, or a host copy of the caller's device memory.
 template <typename T>
-bool fetch(const T* src, size_t n, int kind, std::vector<T>& out) {
-  out.resize(n);
-  if (n == 0) return true;
+struct In {
+  const T* p = nullptr;
+  size_t n = 0;
+  std::vector<T> own;
+  const T& operator[](size_t i) const { return p[i]; }
+  const T* data() const { return p; }
+  size_t size() const { return n; }
+};
+
+template <typename T>
+bool fetch(const T* src, size_t n, int kind, In<T>& out) {
+  out.n = n;
+  if (n == 0) {
+    out.p = out.own.data();
+    return true;
+  }
   if (!src) return false;
-  if (kind == BA_PTR_DEVICE) return cudaMemcpy(out.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost) == cudaSuccess;
-  std::memcpy(out.data(), src, n * sizeof(T));
+  if (kind == BA_PTR_DEVICE) {
+    out.own.resize(n);
+    out.p = out.own.data();
+    return cudaMemcpy(out.own.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost) == cudaSuccess;
+  }
+  out.p = src;
   return true;
 }
 
-bool all_finite(const std::vector<double>& v) {
-  for (double x : v)
-    if (!std::isfinite(x)) return false;
+bool all_finite(const In<double>& v) {
+  for (size_t i = 0; i < v.n; ++i)
+    if (!std::isfinite(v.p[i])) return false;
   return true;
 }
 
@@ -448,9 +471,9 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   if (!(d->sigma_px > 0.0) || !(d->huber_delta_px > 0.0) || !(d->sigma_gnss_m >= 0.0) || !(d->sigma_imu_rad >= 0.0))
     return set_err(ctx, BA_ERR_INVALID, "sigma_px and huber_delta_px must be > 0, prior sigmas >= 0");
   const int kind = d->ptr_kind;
-  std::vector<double> intr, R, T, X, Rp, Tp, uv;
-  std::vector<int32_t> ocam, opt;
-  std::vector<uint8_t> fixed;
+  In<double> intr, R, T, X, Rp, Tp, uv;
+  In<int32_t> ocam, opt;
+  In<uint8_t> fixed;
   if (!fetch(d->intr, (size_t)nc * 7, kind, intr) || !fetch(d->R, (size_t)nc * 9, kind, R) ||
       !fetch(d->T, (size_t)nc * 3, kind, T) || !fetch(d->X, (size_t)np * 3, kind, X) ||
       !fetch(d->R_prior, (size_t)nc * 9, kind, Rp) || !fetch(d->T_prior, (size_t)nc * 3, kind, Tp) ||
@@ -460,7 +483,9 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   if (d->fixed) {
     if (!fetch(d->fixed, (size_t)nc, kind, fixed)) return set_err(ctx, BA_ERR_INVALID, "bad fixed array");
   } else {
-    fixed.assign(nc, 0);
+    fixed.own.assign(nc, 0);
+    fixed.p = fixed.own.data();
+    fixed.n = nc;
   }
   if (!all_finite(intr) || !all_finite(R) || !all_finite(T) || !all_finite(X) || !all_finite(Rp) ||
       !all_finite(Tp) || !all_finite(uv))
@@ -854,8 +879,33 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const size_t o_bx = Lo.add(big ? sizeof(double) * 4 * (size_t)n : 0);
   const size_t total = Lo.off;
 
-  std::unique_ptr<char[]> stage_buf(new char[static_bytes]);  // every byte used below is written
-  char* const stage_ptr = stage_buf.get();
+  // a pinned staging buffer of the context (every byte the kernels read is
+  // written below; alignment padding may keep an earlier cluster's bytes)
+  std::pair<char*, size_t> stage{nullptr, 0};
+  {
+    std::lock_guard<std::mutex> g(ctx->stage_mu);
+    if (!ctx->stage_free.empty()) {
+      stage = ctx->stage_free.back();
+      ctx->stage_free.pop_back();
+    }
+  }
+  if (stage.second < static_bytes) {
+    if (stage.first) cudaFreeHost(stage.first);
+    stage = {nullptr, 0};
+    const size_t want = (static_bytes + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
+    if (cudaMallocHost((void**)&stage.first, want) != cudaSuccess)
+      return set_err(ctx, BA_ERR_CUDA, "pinned staging buffer");
+    stage.second = want;
+  }
+  struct StageBack {  // returns the buffer to the context once the upload is done (or abandoned)
+    ba_ctx* ctx;
+    std::pair<char*, size_t> s;
+    ~StageBack() {
+      std::lock_guard<std::mutex> g(ctx->stage_mu);
+      ctx->stage_free.push_back(s);
+    }
+  } stage_back{ctx, stage};
+  char* const stage_ptr = stage.first;
   auto put = [&](size_t off, const void* src, size_t bytes) {
     if (bytes) std::memcpy(stage_ptr + off, src, bytes);
   };
@@ -864,27 +914,31 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   put(o_R + sizeof(double) * R.size(), R.data(), sizeof(double) * R.size());
   put(o_T, T.data(), sizeof(double) * T.size());
   put(o_T + sizeof(double) * T.size(), T.data(), sizeof(double) * T.size());
-  // points in internal order: binary64, or double-float (hi, lo) pairs in the mixed path
-  std::vector<double> Xrep((size_t)np * 3);
-  for (int i = 0; i < np; ++i)
-    for (int a = 0; a < 3; ++a) Xrep[3 * (size_t)i + a] = X[3 * (size_t)perm[i] + a];
-  if (mixed) {
-    float* xf = reinterpret_cast<float*>(Xrep.data());
-    for (size_t i = 0; i < Xrep.size(); ++i) {
-      const double v = Xrep[i];
-      const float hi = (float)v;
-      const float lo = (float)(v - (double)hi);
-      xf[2 * i] = hi;
-      xf[2 * i + 1] = lo;
-    }
+  // points in internal order: binary64, or double-float (hi, lo) pairs in the
+  // mixed path; written once, then copied to the second state buffer and the
+  // initial state
+  const size_t xbytes = sizeof(double) * (size_t)np * 3;
+  {
+    double* xs = reinterpret_cast<double*>(stage_ptr + o_X);
+    float* xf = reinterpret_cast<float*>(xs);
+    for (int i = 0; i < np; ++i)
+      for (int a = 0; a < 3; ++a) {
+        const double v = X[3 * (size_t)perm[i] + a];
+        if (mixed) {
+          const float hi = (float)v;
+          xf[2 * (3 * (size_t)i + a)] = hi;
+          xf[2 * (3 * (size_t)i + a) + 1] = (float)(v - (double)hi);
+        } else {
+          xs[3 * (size_t)i + a] = v;
+        }
+      }
   }
-  put(o_X, Xrep.data(), sizeof(double) * Xrep.size());
-  put(o_X + sizeof(double) * Xrep.size(), Xrep.data(), sizeof(double) * Xrep.size());
+  put(o_X + xbytes, stage_ptr + o_X, xbytes);
   put(o_Rp, Rp.data(), sizeof(double) * Rp.size());
   put(o_Tp, Tp.data(), sizeof(double) * Tp.size());
   put(o_Ri, R.data(), sizeof(double) * R.size());
   put(o_Ti, T.data(), sizeof(double) * T.size());
-  put(o_Xi, Xrep.data(), sizeof(double) * Xrep.size());
+  put(o_Xi, stage_ptr + o_X, xbytes);
   put(o_perm, perm.data(), sizeof(int) * perm.size());
   put(o_free, free_idx.data(), sizeof(int) * nc);
   put(o_cof, cam_of_free.data(), sizeof(int) * nf);
@@ -1856,6 +1910,7 @@ BA_API ba_status ba_shutdown(ba_ctx* ctx) {
   cudaStreamDestroy(ctx->sched_stream);
   cudaStreamDestroy(ctx->plan_stream);
   if (ctx->hstage) cudaFreeHost(ctx->hstage);
+  for (auto& b : ctx->stage_free) cudaFreeHost(b.first);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return BA_OK;
