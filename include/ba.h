@@ -282,9 +282,10 @@ BA_API ba_status ba_get_state(ba_ctx* ctx, ba_cluster_id id, double* R, double* 
 /* The current states of n clusters at once, each as ba_get_state returns it
  * (binary64, caller's point order), into host memory: R[i], T[i], X[i] are
  * the host destinations of cluster ids[i] ([nc][9], [nc][3], [np][3]; an
- * entry, or a whole array, may be NULL).  One device export per cluster into
- * one block, one copy to the host, one wait.  BA_ERR_NOT_FOUND if an id is
- * unknown (nothing is written then). */
+ * entry, or a whole array, may be NULL).  The clusters go in groups of at
+ * most 32 MiB of state: per group one device export per cluster into one
+ * block, one copy to the host through pinned memory the context keeps, one
+ * wait.  BA_ERR_NOT_FOUND if an id is unknown (nothing is written then). */
 BA_API ba_status ba_get_state_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n, double* const* R,
                                     double* const* T, double* const* X);
 

@@ -1796,40 +1796,52 @@ BA_API ba_status ba_get_state_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32
   if (!ctx || (n > 0 && !ids) || n < 0) return BA_ERR_INVALID;
   std::lock_guard<std::mutex> g(ctx->api_mu);
   std::vector<Cluster*> cs(n);
-  std::vector<size_t> off((size_t)n + 1, 0);  // doubles before cluster i's [R | T | X] in the block
   for (int i = 0; i < n; ++i) {
     cs[i] = find_cluster(ctx, ids[i]);
     if (!cs[i]) return BA_ERR_NOT_FOUND;
-    off[i + 1] = off[i] + (size_t)cs[i]->nc * 12 + (size_t)cs[i]->np * 3;
   }
-  const size_t total = off[n];
-  if (total == 0) return BA_OK;
-  double* tmp = nullptr;
-  CUDA_TRY(ctx, cudaMallocAsync((void**)&tmp, sizeof(double) * total, ctx->stream));
-  for (int i = 0; i < n; ++i) {
-    const Cluster* c = cs[i];
-    double* b = tmp + off[i];
-    launch_export_state(c->d_desc, c->h, ctx->mixed, b, b + (size_t)c->nc * 9, c->np ? b + (size_t)c->nc * 12 : nullptr,
-                        ctx->stream);
-  }
-  note_direct(ctx);
-  if (ctx->hstage_bytes < sizeof(double) * total) {
-    if (ctx->hstage) cudaFreeHost(ctx->hstage);
-    ctx->hstage = nullptr;
-    ctx->hstage_bytes = 0;
-    CUDA_TRY(ctx, cudaMallocHost((void**)&ctx->hstage, sizeof(double) * total));
-    ctx->hstage_bytes = sizeof(double) * total;
-  }
-  CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hstage, tmp, sizeof(double) * total, cudaMemcpyDeviceToHost, ctx->stream));
-  CUDA_TRY(ctx, cudaFreeAsync(tmp, ctx->stream));
-  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  for (int i = 0; i < n; ++i) {
-    const Cluster* c = cs[i];
-    const double* b = ctx->hstage + off[i];
-    const size_t nr = (size_t)c->nc * 9, nt = (size_t)c->nc * 3, nx = (size_t)c->np * 3;
-    if (R && R[i]) std::memcpy(R[i], b, sizeof(double) * nr);
-    if (T && T[i]) std::memcpy(T[i], b + nr, sizeof(double) * nt);
-    if (X && X[i] && nx) std::memcpy(X[i], b + nr + nt, sizeof(double) * nx);
+  // groups of clusters whose states fit the pinned staging (at most
+  // kStateStageBytes, or one cluster's state if that is larger): per group,
+  // one device export per cluster into one block, one copy, one wait
+  constexpr size_t kStateStageBytes = (size_t)32 << 20;
+  auto doubles_of = [&](int i) { return (size_t)cs[i]->nc * 12 + (size_t)cs[i]->np * 3; };
+  for (int i0 = 0; i0 < n;) {
+    size_t total = doubles_of(i0);
+    int i1 = i0 + 1;
+    while (i1 < n && sizeof(double) * (total + doubles_of(i1)) <= kStateStageBytes) total += doubles_of(i1++);
+    if (ctx->hstage_bytes < sizeof(double) * total) {
+      if (ctx->hstage) cudaFreeHost(ctx->hstage);
+      ctx->hstage = nullptr;
+      ctx->hstage_bytes = 0;
+      const size_t want = std::max(sizeof(double) * total, std::min(kStateStageBytes, (size_t)1 << 20));
+      CUDA_TRY(ctx, cudaMallocHost((void**)&ctx->hstage, want));
+      ctx->hstage_bytes = want;
+    }
+    double* tmp = nullptr;
+    CUDA_TRY(ctx, cudaMallocAsync((void**)&tmp, sizeof(double) * total, ctx->stream));
+    size_t off = 0;
+    for (int i = i0; i < i1; ++i) {
+      const Cluster* c = cs[i];
+      double* b = tmp + off;
+      launch_export_state(c->d_desc, c->h, ctx->mixed, b, b + (size_t)c->nc * 9,
+                          c->np ? b + (size_t)c->nc * 12 : nullptr, ctx->stream);
+      off += doubles_of(i);
+    }
+    note_direct(ctx);
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hstage, tmp, sizeof(double) * total, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaFreeAsync(tmp, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    off = 0;
+    for (int i = i0; i < i1; ++i) {
+      const Cluster* c = cs[i];
+      const double* b = ctx->hstage + off;
+      const size_t nr = (size_t)c->nc * 9, nt = (size_t)c->nc * 3, nx = (size_t)c->np * 3;
+      if (R && R[i]) std::memcpy(R[i], b, sizeof(double) * nr);
+      if (T && T[i]) std::memcpy(T[i], b + nr, sizeof(double) * nt);
+      if (X && X[i] && nx) std::memcpy(X[i], b + nr + nt, sizeof(double) * nx);
+      off += doubles_of(i);
+    }
+    i0 = i1;
   }
   return BA_OK;
 }

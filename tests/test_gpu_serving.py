@@ -266,3 +266,18 @@ def test_get_state_batch_equals_get_state():
             for cid, (R, T, X) in zip(ids, got):
                 R1, T1, X1 = ctx.get_state(cid)
                 assert np.array_equal(R, R1) and np.array_equal(T, T1) and np.array_equal(X, X1)
+
+
+def test_get_state_batch_in_groups_equals_get_state():
+    """Three clusters of 500,000 points (36 MB of state, more than one 32 MiB
+    group of the batched read-back) come back exactly as get_state returns
+    them."""
+    import paper_2511_06152_gb300 as ba
+    scenes = [sg.tiny_cluster(7400 + i, 2, 8, 500_000) for i in range(3)]
+    with ba.Context(precision=ba.BA_MIXED) as ctx:
+        ids = [ctx.create_cluster(s) for s in scenes]
+        ctx.solve_batch(ids, 2)
+        got = ctx.get_state_batch(ids)
+        for cid, (R, T, X) in zip(ids, got):
+            R1, T1, X1 = ctx.get_state(cid)
+            assert np.array_equal(R, R1) and np.array_equal(T, T1) and np.array_equal(X, X1)
