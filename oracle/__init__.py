@@ -17,6 +17,8 @@ Functions and the passages they follow:
   cost            Eq. 7 plus the prior terms, halved
   solve_damped    Levenberg-Marquardt step by the Schur complement
   lm_step/lm_run  LM with Nielsen's damping update
+  patch_transfer_poses   Eq. 3 (Sec. 3.1): patch centres through the poses
+  patch_transfer_planar  Eq. 4 (Sec. 3.1): planar footprint-based transfer
 """
 from __future__ import annotations
 
@@ -186,6 +188,39 @@ def transition(R_old, T_old, w_old, R_new, T_new, w_new):
     lib().orc_transition(_d(_f64(R_old, (9,))), _d(_f64(T_old, (3,))), ctypes.c_double(w_old),
                          _d(_f64(R_new, (9,))), _d(_f64(T_new, (3,))), ctypes.c_double(w_new), _d(R), _d(T))
     return R.reshape(3, 3), T
+
+
+def patch_transfer_poses(intr0, R0, T0, p0, lam, intrk, Rk, Tk, width=None, height=None):
+    """Eq. 3: patch centres p0 (n, 2) of image 0 moved to image k at the
+    nominal depth lam; returns (pk (n, 2), inside (n,) bool): inside = in
+    front of image k and, when width/height are given, within the frame."""
+    p0 = np.ascontiguousarray(np.asarray(p0, dtype=np.float64).reshape(-1, 2))
+    out = np.zeros_like(p0)
+    inside = np.zeros(len(p0), dtype=bool)
+    L = lib()
+    a = [_d(_f64(x, (s,))) for x, s in ((intr0, 7), (R0, 9), (T0, 3), (intrk, 7), (Rk, 9), (Tk, 3))]
+    for i in range(len(p0)):
+        row = np.zeros(2)
+        front = L.orc_patch_transfer_poses(a[0], a[1], a[2], _d(p0[i]), ctypes.c_double(lam), a[3], a[4], a[5], _d(row))
+        out[i] = row
+        ok = bool(front)
+        if ok and width is not None:
+            ok = 0.0 <= row[0] < width and 0.0 <= row[1] < height
+        inside[i] = ok
+    return out, inside
+
+
+def patch_transfer_planar(q0, c, theta, g0, gk):
+    """Eq. 4: patch centres q0 (n, 2) (ground plane) moved to image k."""
+    q0 = np.ascontiguousarray(np.asarray(q0, dtype=np.float64).reshape(-1, 2))
+    out = np.zeros_like(q0)
+    L = lib()
+    cc, a0, ak = _f64(c, (2,)), _f64(g0, (2,)), _f64(gk, (2,))
+    for i in range(len(q0)):
+        row = np.zeros(2)
+        L.orc_patch_transfer_planar(_d(q0[i]), _d(cc), ctypes.c_double(theta), _d(a0), _d(ak), _d(row))
+        out[i] = row
+    return out
 
 
 def project(intr, R, T, X):

@@ -768,3 +768,35 @@ double orc_quad_area(const double q[12]) {
   for (int i = 0; i < 4; ++i) { A[2 * i] = q[3 * i]; A[2 * i + 1] = q[3 * i + 1]; }
   return fabs(poly_area(A, 4));
 }
+
+/* ---- Patch transfer (Sec. 3.1, Eq. 3 and Eq. 4). ---- */
+
+/* Eq. 3, written as it reads: X = T_0 + lambda R_0 K_0^-1 [u v 1]^T, then
+ * pi(K_k R_k^T (X - T_k)) with pi(x, y, z) = (x / z, y / z).  K has no
+ * distortion term in Eq. 3, so none is applied. */
+int orc_patch_transfer_poses(const double intr0[7], const double R0[9], const double T0[3], const double p0[2],
+                             double lambda, const double intrk[7], const double Rk[9], const double Tk[3],
+                             double pk[2]) {
+  /* K_0^-1 p_bar: K = [f 0 cx; 0 f cy; 0 0 1] */
+  const double ray[3] = {(p0[0] - intr0[1]) / intr0[0], (p0[1] - intr0[2]) / intr0[0], 1.0};
+  double X[3], d[3], xc[3], h[3];
+  for (int i = 0; i < 3; ++i) X[i] = T0[i] + lambda * (R0[3 * i] * ray[0] + R0[3 * i + 1] * ray[1] + R0[3 * i + 2] * ray[2]);
+  for (int i = 0; i < 3; ++i) d[i] = X[i] - Tk[i];
+  for (int i = 0; i < 3; ++i) xc[i] = Rk[i] * d[0] + Rk[3 + i] * d[1] + Rk[6 + i] * d[2]; /* R_k^T (X - T_k) */
+  if (!(xc[2] > 0.0)) return 0;
+  h[0] = intrk[0] * xc[0] + intrk[1] * xc[2]; /* K_k x_c */
+  h[1] = intrk[0] * xc[1] + intrk[2] * xc[2];
+  h[2] = xc[2];
+  pk[0] = h[0] / h[2];
+  pk[1] = h[1] / h[2];
+  return 1;
+}
+
+/* Eq. 4 with R(theta) = [cos(theta) sin(-theta); sin(theta) cos(theta)]. */
+void orc_patch_transfer_planar(const double q0[2], const double c[2], double theta, const double g0[2],
+                               const double gk[2], double qk[2]) {
+  const double a = cos(theta), b = sin(theta);
+  const double dx = q0[0] - c[0], dy = q0[1] - c[1];
+  qk[0] = (a * dx - b * dy) + c[0] + gk[0] - g0[0];
+  qk[1] = (b * dx + a * dy) + c[1] + gk[1] - g0[1];
+}

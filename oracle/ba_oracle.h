@@ -80,4 +80,17 @@ double orc_quad_area(const double q[12]);
 void orc_transition(const double R_old[9], const double T_old[3], double w_old, const double R_new[9],
                     const double T_new[3], double w_new, double R_out[9], double T_out[3]);
 
+/* Patch transfer (Sec. 3.1).  Eq. 3: the centre p0 (pixels) of a patch of
+ * image 0 moved to image k through the poses, at depth lambda along image
+ * 0's optical axis; K is the pinhole part of intr (f, cx, cy).  Returns 1
+ * (and writes pk) when the point is in front of image k, else 0. */
+int orc_patch_transfer_poses(const double intr0[7], const double R0[9], const double T0[3], const double p0[2],
+                             double lambda, const double intrk[7], const double Rk[9], const double Tk[3],
+                             double pk[2]);
+/* Eq. 4: a patch centre q0 (ground plane) moved by the in-plane rotation
+ * theta about the patch-grid centre c and the image-centre displacement
+ * gk - g0. */
+void orc_patch_transfer_planar(const double q0[2], const double c[2], double theta, const double g0[2],
+                               const double gk[2], double qk[2]);
+
 #endif
