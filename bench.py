@@ -118,9 +118,51 @@ def formation_leg(ba, torch, stream, form):
             continue
         ratio = A[np.ix_(win, other)] / np.diag(A)[win][:, None]
         adds.append(int((ratio >= 0.3).any(axis=0).sum()))
-    return {"images": int(n), "dsm_nodes": int(dsm["h"].size), "footprints_ms": 1e3 * statistics.median(tf[1:]),
-            "overlap_pairs": int(n * n), "overlaps_ms": 1e3 * statistics.median(to[1:]),
-            "adjacent_strip_images_per_window": adds, "poses": "GNSS/IMU priors (the initial values)"}
+    out = {"images": int(n), "dsm_nodes": int(dsm["h"].size), "footprints_ms": 1e3 * statistics.median(tf[1:]),
+           "overlap_pairs": int(n * n), "overlaps_ms": 1e3 * statistics.median(to[1:]),
+           "adjacent_strip_images_per_window": adds, "poses": "GNSS/IMU priors (the initial values)"}
+    out["patch_transfer"] = patch_leg(ba, torch, stream, fl, dsm, q)
+    return out
+
+
+def patch_leg(ba, torch, stream, fl, dsm, q):
+    """Patch transfer (Sec. 3.1) from the flight's first image to its next 40
+    images: a 128 x 96 grid of patch centres, Eq. 3 at the nominal depth
+    (height above the mean DSM) and Eq. 4 with the footprints' centroids and
+    headings; through the C ABI with host arrays (copies included), median of
+    5 calls each."""
+    n_gu, n_gv, m = 128, 96, min(40, fl["n_cams"] - 1)
+    gu, gv = np.meshgrid((np.arange(n_gu) + 0.5) * sg.SENSOR_W / n_gu, (np.arange(n_gv) + 0.5) * sg.SENSOR_H / n_gv)
+    p0 = np.c_[gu.ravel(), gv.ravel()]
+    intr, R, T = np.asarray(fl["intr"]), np.asarray(fl["R_prior"]).reshape(-1, 9), np.asarray(fl["T_prior"]).reshape(-1, 3)
+    lam = float(T[0, 2] - np.mean(dsm["h"]))
+    # Eq. 4 inputs: ground positions of the patch grid (bilinear in image 0's
+    # footprint), the footprints' centroids and headings
+    c4 = q[:, :, :2]
+    a, b = gu.ravel() / sg.SENSOR_W, gv.ravel() / sg.SENSOR_H
+    q0 = ((1 - a) * (1 - b))[:, None] * c4[0, 0] + (a * (1 - b))[:, None] * c4[0, 1] + (a * b)[:, None] * c4[0, 2] + \
+        ((1 - a) * b)[:, None] * c4[0, 3]
+    cen = c4.mean(axis=1)
+    head = np.arctan2(c4[:, 1, 1] - c4[:, 0, 1], c4[:, 1, 0] - c4[:, 0, 0])
+    ks = np.arange(1, m + 1)
+    ctx = ba.Context(device=torch.cuda.current_device(), stream=stream.cuda_stream)
+    t3, t4 = [], []
+    for _ in range(6):
+        t0 = time.perf_counter()
+        _, inside = ctx.patch_transfer_poses(p0, intr[0], R[0], T[0], lam, intr[ks], R[ks], T[ks], sg.SENSOR_W,
+                                             sg.SENSOR_H)
+        t1 = time.perf_counter()
+        ctx.patch_transfer_planar(q0, q0.mean(axis=0), cen[0], head[ks] - head[0], cen[ks])
+        t2 = time.perf_counter()
+        t3.append(t1 - t0)
+        t4.append(t2 - t1)
+    ctx.close()
+    tr = len(p0) * m
+    return {"patches": int(len(p0)), "targets": int(m), "transfers": int(tr),
+            "eq3_ms": 1e3 * statistics.median(t3[1:]), "eq3_transfers_per_s": tr / statistics.median(t3[1:]),
+            "eq3_inside_fraction": float(inside.mean()),
+            "eq4_ms": 1e3 * statistics.median(t4[1:]), "eq4_transfers_per_s": tr / statistics.median(t4[1:]),
+            "nominal_depth_m": lam}
 
 
 def serving_flight(seed):

@@ -235,6 +235,31 @@ BA_API ba_status ba_footprints(ba_ctx* ctx, int32_t n, const double* intr, doubl
 BA_API ba_status ba_footprint_overlaps(ba_ctx* ctx, int32_t na, const double* qa, int32_t nb, const double* qb,
                                        double* area);
 
+/* Patch transfer through the poses (Sec. 3.1, Eq. 3): the centres p0[n][2]
+ * (pixels) of patches of image 0 (intrinsics intr0[7], pose R0[9] camera->
+ * world, T0[3]) moved to the m images of intr[m][7], R[m][9], T[m][3]: the
+ * point at depth lambda along image 0's optical axis through each centre,
+ * projected into image k with the pinhole part (f, cx, cy) of its
+ * intrinsics (Eq. 3 has no distortion term).  p[m][n][2] (host, output;
+ * target-major; NaN where the point is behind image k) and inside[m][n]
+ * (host, output, may be NULL): 1 where the transferred centre lies in
+ * [0, width) x [0, height), the patch-keyed correspondences.  Binary64.
+ * BA_ERR_INVALID for bad sizes, null pointers or a non-finite lambda. */
+BA_API ba_status ba_patch_transfer_poses(ba_ctx* ctx, int32_t n, const double* p0, const double* intr0,
+                                         const double* R0, const double* T0, double lambda, int32_t m,
+                                         const double* intr, const double* R, const double* T, double width,
+                                         double height, double* p, uint8_t* inside);
+
+/* Patch transfer by the footprints (Sec. 3.1, Eq. 4): patch centres
+ * q0[n][2] of image 0 in a ground frame, moved to each of m images by the
+ * in-plane rotation theta[k] (radians, R = [cos -sin; sin cos]) about the
+ * patch-grid centre c[2] and the displacement g[k] - g0 of the image centres
+ * (g[m][2], g0[2]): q[m][n][2] (host, output; target-major).  Binary64.
+ * BA_ERR_INVALID for bad sizes or null pointers. */
+BA_API ba_status ba_patch_transfer_planar(ba_ctx* ctx, int32_t n, const double* q0, const double* c,
+                                          const double* g0, int32_t m, const double* theta, const double* g,
+                                          double* q);
+
 /* Evaluate F and the gradient infinity norm at the current state. */
 BA_API ba_status ba_linearize(ba_ctx* ctx, ba_cluster_id id, ba_lin_info* out);
 

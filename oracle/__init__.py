@@ -202,7 +202,7 @@ def patch_transfer_poses(intr0, R0, T0, p0, lam, intrk, Rk, Tk, width=None, heig
     for i in range(len(p0)):
         row = np.zeros(2)
         front = L.orc_patch_transfer_poses(a[0], a[1], a[2], _d(p0[i]), ctypes.c_double(lam), a[3], a[4], a[5], _d(row))
-        out[i] = row
+        out[i] = row if front else np.nan
         ok = bool(front)
         if ok and width is not None:
             ok = 0.0 <= row[0] < width and 0.0 <= row[1] < height

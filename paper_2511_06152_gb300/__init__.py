@@ -100,7 +100,7 @@ class ba_dsm(ctypes.Structure):
 EXPORTS = ["ba_init", "ba_create_cluster", "ba_linearize", "ba_solve_step", "ba_run", "ba_solve_batch", "ba_reset",
            "ba_reset_batch", "ba_submit", "ba_poll", "ba_get_state", "ba_get_state_batch", "ba_reprojection_errors",
            "ba_memory_in_use",
-           "ba_launch_count", "ba_kernel_stats", "ba_cost_noalloc", "ba_warm_start", "ba_transition", "ba_footprints", "ba_footprint_overlaps", "ba_get_cluster_info", "ba_destroy_cluster", "ba_shutdown",
+           "ba_launch_count", "ba_kernel_stats", "ba_cost_noalloc", "ba_warm_start", "ba_transition", "ba_footprints", "ba_footprint_overlaps", "ba_patch_transfer_poses", "ba_patch_transfer_planar", "ba_get_cluster_info", "ba_destroy_cluster", "ba_shutdown",
            "ba_status_string", "ba_last_error"]
 
 _lib = None
@@ -136,6 +136,10 @@ def lib(build: bool = True):
             L.ba_footprints.argtypes = [vp, ctypes.c_int32, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp,
                                         ctypes.POINTER(ba_dsm), _dp]
             L.ba_footprint_overlaps.argtypes = [vp, ctypes.c_int32, _dp, ctypes.c_int32, _dp, _dp]
+            L.ba_patch_transfer_poses.argtypes = [vp, ctypes.c_int32, _dp, _dp, _dp, _dp, ctypes.c_double,
+                                                  ctypes.c_int32, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                                  _dp, ctypes.POINTER(ctypes.c_uint8)]
+            L.ba_patch_transfer_planar.argtypes = [vp, ctypes.c_int32, _dp, _dp, _dp, ctypes.c_int32, _dp, _dp, _dp]
             L.ba_submit.argtypes = [vp, u64, ctypes.POINTER(ba_solve_opts), ctypes.POINTER(u64)]
             L.ba_poll.argtypes = [vp, u64, ctypes.POINTER(ba_result)]
             L.ba_get_state.argtypes = [vp, u64, _dp, _dp, _dp, ctypes.c_int32]
@@ -350,6 +354,32 @@ class Context:
         dst) by their observation counts in both clusters."""
         m = np.ascontiguousarray(cam_map, dtype=np.int32)
         _check(self.L.ba_transition(self.h, dst, src, m.ctypes.data_as(_ip)), self.h, "ba_transition")
+
+    def patch_transfer_poses(self, p0, intr0, R0, T0, lam, intr, R, T, width, height):
+        """Eq. 3: patch centres p0 (n, 2) of image 0 moved to the m images of
+        intr (m, 7), R (m, 9), T (m, 3) at depth lam: (p (m, n, 2), inside
+        (m, n) bool)."""
+        p0 = _f64(p0, (-1, 2))
+        intr, R, T = _f64(intr, (-1, 7)), _f64(R, (-1, 9)), _f64(T, (-1, 3))
+        n, m = p0.shape[0], intr.shape[0]
+        p = np.zeros((m, n, 2))
+        inside = np.zeros((m, n), dtype=np.uint8)
+        _check(self.L.ba_patch_transfer_poses(self.h, n, _d(p0), _d(_f64(intr0, (7,))), _d(_f64(R0, (9,))),
+                                              _d(_f64(T0, (3,))), float(lam), m, _d(intr), _d(R), _d(T),
+                                              float(width), float(height), _d(p),
+                                              inside.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))),
+               self.h, "ba_patch_transfer_poses")
+        return p, inside.astype(bool)
+
+    def patch_transfer_planar(self, q0, c, g0, theta, g):
+        """Eq. 4: patch centres q0 (n, 2) moved to m images by theta (m,) and
+        the image centres g (m, 2) relative to g0: q (m, n, 2)."""
+        q0, theta, g = _f64(q0, (-1, 2)), _f64(theta, (-1,)), _f64(g, (-1, 2))
+        n, m = q0.shape[0], theta.shape[0]
+        q = np.zeros((m, n, 2))
+        _check(self.L.ba_patch_transfer_planar(self.h, n, _d(q0), _d(_f64(c, (2,))), _d(_f64(g0, (2,))), m,
+                                               _d(theta), _d(g), _d(q)), self.h, "ba_patch_transfer_planar")
+        return q
 
     def footprints(self, intr, width, height, R, T, dsm):
         """Ground quadrilaterals (n, 4, 3) of the images' corners on a DSM

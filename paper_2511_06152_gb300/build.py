@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libba_gb300.so")
-SOURCES = ["ba_kernels.cu", "ba_big.cu", "ba_footprint.cu", "ba_api.cu", "ba_noalloc.cu"]
+SOURCES = ["ba_kernels.cu", "ba_big.cu", "ba_footprint.cu", "ba_patch.cu", "ba_api.cu", "ba_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]

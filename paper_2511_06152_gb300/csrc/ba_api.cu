@@ -1524,6 +1524,78 @@ BA_API ba_status ba_footprints(ba_ctx* ctx, int32_t n, const double* intr, doubl
   return BA_OK;
 }
 
+BA_API ba_status ba_patch_transfer_poses(ba_ctx* ctx, int32_t n, const double* p0, const double* intr0,
+                                         const double* R0, const double* T0, double lambda, int32_t m,
+                                         const double* intr, const double* R, const double* T, double width,
+                                         double height, double* p, uint8_t* inside) {
+  if (!ctx || n < 0 || m < 0) return BA_ERR_INVALID;
+  if (n == 0 || m == 0) return BA_OK;
+  if (!p0 || !intr0 || !R0 || !T0 || !intr || !R || !T || !p || !std::isfinite(lambda) || !(width > 0.0) ||
+      !(height > 0.0) || !(intr0[0] != 0.0))
+    return set_err(ctx, BA_ERR_INVALID, "ba_patch_transfer_poses: null pointer, bad size or bad depth");
+  if ((int64_t)n * m > (int64_t)1 << 30) return set_err(ctx, BA_ERR_INVALID, "ba_patch_transfer_poses: too many");
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  const size_t np0 = 2 * (size_t)n, ncam = 19, nk = 19 * (size_t)m, nout = 2 * (size_t)n * m;
+  const size_t bytes = sizeof(double) * (np0 + ncam + nk + nout) + (inside ? (size_t)n * m : 0);
+  char* buf = nullptr;
+  CUDA_TRY(ctx, cudaMallocAsync((void**)&buf, bytes, ctx->stream));
+  // the double2 arrays (centres in and out) first, at even offsets of the
+  // allocation's 256-byte aligned start
+  double* d_p0 = (double*)buf;
+  double* d_out = d_p0 + np0;
+  double* d_c0 = d_out + nout;  // intr0 7, R0 9, T0 3
+  double* d_intr = d_c0 + ncam;
+  double* d_R = d_intr + 7 * (size_t)m;
+  double* d_T = d_R + 9 * (size_t)m;
+  uint8_t* d_in = inside ? (uint8_t*)(d_T + 3 * (size_t)m) : nullptr;
+  const cudaStream_t st = ctx->stream;
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_p0, p0, sizeof(double) * np0, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_c0, intr0, sizeof(double) * 7, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_c0 + 7, R0, sizeof(double) * 9, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_c0 + 16, T0, sizeof(double) * 3, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_intr, intr, sizeof(double) * 7 * m, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_R, R, sizeof(double) * 9 * m, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_T, T, sizeof(double) * 3 * m, cudaMemcpyHostToDevice, st));
+  launch_patch_poses(n, d_p0, d_c0, d_c0 + 7, d_c0 + 16, lambda, m, d_intr, d_R, d_T, width, height, d_out, d_in, st);
+  note_direct(ctx);
+  CUDA_TRY(ctx, cudaMemcpyAsync(p, d_out, sizeof(double) * nout, cudaMemcpyDeviceToHost, st));
+  if (inside) CUDA_TRY(ctx, cudaMemcpyAsync(inside, d_in, (size_t)n * m, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(ctx, cudaFreeAsync(buf, st));
+  CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  CUDA_TRY(ctx, cudaGetLastError());
+  return BA_OK;
+}
+
+BA_API ba_status ba_patch_transfer_planar(ba_ctx* ctx, int32_t n, const double* q0, const double* c,
+                                          const double* g0, int32_t m, const double* theta, const double* g,
+                                          double* q) {
+  if (!ctx || n < 0 || m < 0) return BA_ERR_INVALID;
+  if (n == 0 || m == 0) return BA_OK;
+  if (!q0 || !c || !g0 || !theta || !g || !q)
+    return set_err(ctx, BA_ERR_INVALID, "ba_patch_transfer_planar: null pointer");
+  if ((int64_t)n * m > (int64_t)1 << 30) return set_err(ctx, BA_ERR_INVALID, "ba_patch_transfer_planar: too many");
+  std::lock_guard<std::mutex> gl(ctx->api_mu);
+  const size_t nq = 2 * (size_t)n, nout = 2 * (size_t)n * m;
+  char* buf = nullptr;
+  CUDA_TRY(ctx, cudaMallocAsync((void**)&buf, sizeof(double) * (nq + 3 * (size_t)m + nout), ctx->stream));
+  // the double2 arrays (centres, displacements, output) first, at even offsets
+  double* d_q0 = (double*)buf;
+  double* d_g = d_q0 + nq;
+  double* d_out = d_g + 2 * (size_t)m;
+  double* d_th = d_out + nout;
+  const cudaStream_t st = ctx->stream;
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_q0, q0, sizeof(double) * nq, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_th, theta, sizeof(double) * m, cudaMemcpyHostToDevice, st));
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_g, g, sizeof(double) * 2 * m, cudaMemcpyHostToDevice, st));
+  launch_patch_planar(n, d_q0, c, g0, m, d_th, d_g, d_out, st);
+  note_direct(ctx);
+  CUDA_TRY(ctx, cudaMemcpyAsync(q, d_out, sizeof(double) * nout, cudaMemcpyDeviceToHost, st));
+  CUDA_TRY(ctx, cudaFreeAsync(buf, st));
+  CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  CUDA_TRY(ctx, cudaGetLastError());
+  return BA_OK;
+}
+
 BA_API ba_status ba_footprint_overlaps(ba_ctx* ctx, int32_t na, const double* qa, int32_t nb, const double* qb,
                                        double* area) {
   if (!ctx || na < 0 || nb < 0 || (na > 0 && nb > 0 && (!qa || !qb || !area))) return BA_ERR_INVALID;

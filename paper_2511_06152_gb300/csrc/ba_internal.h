@@ -280,6 +280,12 @@ void launch_grad_norm(const BatchView& bv, bool mixed, double* out, cudaStream_t
 void launch_reproj(const DevCluster* dcl, const DevCluster& hcl, bool mixed, double* err_pm, cudaStream_t st);
 void launch_export_state(const DevCluster* dcl, const DevCluster& hcl, bool mixed, double* R, double* T, double* X,
                          cudaStream_t st);
+void launch_patch_poses(int n, const double* p0, const double* intr0, const double* R0, const double* T0,
+                        double lambda, int m, const double* intr, const double* R, const double* T, double width,
+                        double height, double* p, uint8_t* inside, cudaStream_t st);
+// c, g0: host arrays of 2
+void launch_patch_planar(int n, const double* q0, const double* c, const double* g0, int m, const double* theta,
+                         const double* g, double* q, cudaStream_t st);
 size_t factor_smem_bytes(int max_n);
 int chunk_obs(bool mixed);
 int chunk_tiles(bool mixed);
