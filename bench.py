@@ -78,10 +78,12 @@ def make_workload(replica, n_clusters, n_flights=0, large=False):
     with ctx.Pool(n) as pool:
         big = pool.apply_async(sg.cluster_c5, (replica,)) if large else None  # ~1 min, alongside the rest
         form = pool.apply_async(formation_scene, (4000 + 100 * replica,)) if large else None
+        gseed = 4050 + 100 * replica  # the global-vs-local flight (serving density)
+        gfl = pool.apply_async(sg.flight, (gseed,)) if large else None
         scenes = sg.batch_c3(replica=replica, n_clusters=n_clusters, pool=pool)
         flights = pool.map(serving_flight, [4000 + 100 * replica + f for f in range(n_flights)]) if n_flights else []
         big = big.get() if big is not None else None
-        form = form.get() if form is not None else None
+        form = form.get() + ((gfl.get(), gseed),) if form is not None else None
     return scenes, flights, (big, form)
 
 
@@ -96,7 +98,7 @@ def formation_leg(ba, torch, stream, form):
     on the DSM and the overlap areas of every pair, through the C ABI (host
     arrays in and out, copies included), median of 5 calls each; and the
     adjacent-strip images a 30 % overlap ratio brings into each window."""
-    fl, dsm = form
+    fl, dsm = form[0], form[1]
     ctx = ba.Context(device=torch.cuda.current_device(), stream=stream.cuda_stream)
     tf, to = [], []
     for _ in range(6):
@@ -123,6 +125,61 @@ def formation_leg(ba, torch, stream, form):
            "adjacent_strip_images_per_window": adds, "poses": "GNSS/IMU priors (the initial values)"}
     out["patch_transfer"] = patch_leg(ba, torch, stream, fl, dsm, q)
     return out
+
+
+def _pose_errors(R, T, R_true, T_true):
+    """RMS camera-centre error (m) and RMS rotation error (degrees) against the truth."""
+    R, R_true = np.asarray(R).reshape(-1, 3, 3), np.asarray(R_true).reshape(-1, 3, 3)
+    c = np.einsum("kji,kjl->kil", R_true, R)  # R_true^T R
+    ang = np.degrees(np.arccos(np.clip((np.trace(c, axis1=1, axis2=2) - 1.0) / 2.0, -1.0, 1.0)))
+    return float(np.sqrt(np.mean(np.sum((np.asarray(T) - T_true) ** 2, axis=1)))), float(np.sqrt(np.mean(ang ** 2)))
+
+
+def global_vs_local_leg(ba, torch, stream, fl, seed):
+    """The accuracy gap between local and global BA on one synthetic flight
+    (3 strips x 40 images): global = the whole flight as one cluster, 15 LM
+    iterations; local = the sliding windows of the serving workload in order,
+    each warm-started from the previous one, 10 iterations, then the Eq. 8
+    transition; an image's local pose is the one of the last window that
+    holds it.  Mixed precision, the same kernels."""
+    n = fl["n_cams"]
+    ctx = ba.Context(device=torch.cuda.current_device(), precision=ba.BA_MIXED, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    cg = ctx.create_cluster(fl)
+    t1 = time.perf_counter()
+    ctx.run(cg, 15, trace=False)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    Rg, Tg, _ = ctx.get_state(cg)
+    ctx.destroy_cluster(cg)
+    R_loc, T_loc = np.zeros((n, 9)), np.zeros((n, 3))
+    prev, t_local, n_win = None, 0.0, 0
+    for (s, e, nf) in sg.window_plan(seed, n):
+        c, cams, pts = sg.window_cluster(fl, s, e, nf)
+        t3 = time.perf_counter()
+        cid = ctx.create_cluster(c)
+        maps = None
+        if prev is not None:
+            maps = sg.warm_maps(prev[1], prev[2], cams, pts)
+            ctx.warm_start(cid, prev[0], *maps)
+        ctx.run(cid, 10, trace=False)
+        if maps is not None:
+            ctx.transition(cid, prev[0], maps[0])
+        R, T, _ = ctx.get_state(cid)
+        t_local += time.perf_counter() - t3
+        R_loc[cams], T_loc[cams] = R, T
+        if prev is not None:
+            ctx.destroy_cluster(prev[0])
+        prev, n_win = (cid, cams, pts), n_win + 1
+    ctx.close()
+    eg, el, ep = (_pose_errors(Rg, Tg, fl["R_true"], fl["T_true"]),
+                  _pose_errors(R_loc, T_loc, fl["R_true"], fl["T_true"]),
+                  _pose_errors(fl["R_prior"], fl["T_prior"], fl["R_true"], fl["T_true"]))
+    return {"images": int(n), "observations": int(fl["n_obs"]), "windows": n_win,
+            "global": {"centre_rms_m": eg[0], "rotation_rms_deg": eg[1], "create_s": t1 - t0, "solve_s": t2 - t1},
+            "local": {"centre_rms_m": el[0], "rotation_rms_deg": el[1], "seconds_all_windows": t_local},
+            "priors": {"centre_rms_m": ep[0], "rotation_rms_deg": ep[1]},
+            "local_over_global_centre_error": el[0] / eg[0] if eg[0] > 0 else None}
 
 
 def patch_leg(ba, torch, stream, fl, dsm, q):
@@ -719,6 +776,8 @@ def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flight
     if form is not None:
         log("cluster formation leg")
         out["cluster_formation"] = formation_leg(ba, torch, stream, form)
+        log("global vs local leg")
+        out["global_vs_local"] = global_vs_local_leg(ba, torch, stream, *form[2])
     if large is not None:
         log("large block leg")
         out["large_block"] = large_block_leg(ba, torch, stream, large)
