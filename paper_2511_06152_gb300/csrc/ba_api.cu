@@ -610,14 +610,15 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   std::vector<unsigned int> pent;
   std::vector<int> pair_of((size_t)nf * nf, -1);  // (fa, fb) -> pair index
   std::vector<int2> pair_key;
-  std::vector<std::vector<int>> cam_slot_lists(nf), pair_slot_lists;
+  std::vector<int2> cam_slot_ent, pair_slot_ent;  // (free camera or pair, slot), in chunk order
   int n_cslots = 0, n_pslots = 0;
   {
     std::vector<std::vector<unsigned short>> per_cam(nf);
     std::vector<std::vector<unsigned int>> per_pair;  // indexed by local pair; inner vectors are reused
     int n_lp_used = 0;
     std::vector<int> local_pair_of((size_t)nf * nf, -1);
-    std::vector<int> lp_keys;
+    std::vector<int> lp_keys, corder, order, lanes;
+    std::vector<double> cost;
     size_t t = 0;
     while (t < tiles.size()) {
       Chunk ch{};
@@ -662,19 +663,19 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
       // jobs: the chunk's free cameras, then its camera pairs (both by
       // decreasing item count, ties by index / key)
       ch.job_begin = (int)jobs.size();
-      std::vector<int> corder;
+      corder.clear();
       for (int f = 0; f < nf; ++f)
         if (!per_cam[f].empty()) corder.push_back(f);
       std::stable_sort(corder.begin(), corder.end(),
                        [&](int x, int y) { return per_cam[x].size() > per_cam[y].size(); });
       for (int f : corder) {
         Job jb{n_cslots++, (int)cm_list.size(), (int)per_cam[f].size(), 0, 1};
-        cam_slot_lists[f].push_back(jb.slot);
+        cam_slot_ent.push_back(make_int2(f, jb.slot));
         cm_list.insert(cm_list.end(), per_cam[f].begin(), per_cam[f].end());
         jobs.push_back(jb);
       }
       ch.n_lc = (int)corder.size();
-      std::vector<int> order(lp_keys.size());
+      order.resize(lp_keys.size());
       for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
       std::sort(order.begin(), order.end(), [&](int x, int y) {
         if (per_pair[x].size() != per_pair[y].size()) return per_pair[x].size() > per_pair[y].size();
@@ -685,10 +686,9 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
         if (pair_of[key] < 0) {
           pair_of[key] = (int)pair_key.size();
           pair_key.push_back(make_int2(key / nf, key % nf));
-          pair_slot_lists.emplace_back();
         }
         Job jb{n_pslots++, (int)pent.size(), (int)per_pair[li].size(), 0, 1};
-        pair_slot_lists[pair_of[key]].push_back(jb.slot);
+        pair_slot_ent.push_back(make_int2(pair_of[key], jb.slot));
         pent.insert(pent.end(), per_pair[li].begin(), per_pair[li].end());
         jobs.push_back(jb);
         local_pair_of[key] = -1;
@@ -702,9 +702,9 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
       // run one lane per job (the kernel's fallback mode).
       const int nj = ch.n_lc + ch.n_lp;
       if (nj > 0 && nj <= kChunkThreads) {
-        std::vector<double> cost(nj);
+        cost.resize(nj);
         for (int q = 0; q < nj; ++q) cost[q] = jobs[ch.job_begin + q].count * (q < ch.n_lc ? 165.0 : 123.0);
-        std::vector<int> lanes(nj);
+        lanes.resize(nj);
         auto alloc = [&](double Q, bool align) {
           int nc = 0, np_ = 0;
           for (int q = 0; q < nj; ++q) {
@@ -749,19 +749,20 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   }
   // pairs in key order (the reduced system does not depend on this order, but a
   // fixed one keeps the tables reproducible)
-  std::vector<int> cam_slot_begin((size_t)nf + 1, 0), cam_slots;
-  for (int f = 0; f < nf; ++f) {
-    cam_slot_begin[f] = (int)cam_slots.size();
-    cam_slots.insert(cam_slots.end(), cam_slot_lists[f].begin(), cam_slot_lists[f].end());
-  }
-  cam_slot_begin[nf] = (int)cam_slots.size();
+  // slots grouped by camera / pair, each group in chunk order (stable counting sort)
+  auto group = [](const std::vector<int2>& ent, int n_groups, std::vector<int>& begin, std::vector<int>& out) {
+    begin.assign((size_t)n_groups + 1, 0);
+    for (const int2& e : ent) ++begin[e.x + 1];
+    for (int i = 0; i < n_groups; ++i) begin[i + 1] += begin[i];
+    out.resize(ent.size());
+    std::vector<int> pos(begin.begin(), begin.end() - 1);
+    for (const int2& e : ent) out[pos[e.x]++] = e.y;
+  };
+  std::vector<int> cam_slot_begin, cam_slots;
+  group(cam_slot_ent, nf, cam_slot_begin, cam_slots);
   const int n_pairs = (int)pair_key.size();
-  std::vector<int> pair_slot_begin((size_t)n_pairs + 1, 0), pair_slots;
-  for (int p = 0; p < n_pairs; ++p) {
-    pair_slot_begin[p] = (int)pair_slots.size();
-    pair_slots.insert(pair_slots.end(), pair_slot_lists[p].begin(), pair_slot_lists[p].end());
-  }
-  pair_slot_begin[n_pairs] = (int)pair_slots.size();
+  std::vector<int> pair_slot_begin, pair_slots;
+  group(pair_slot_ent, n_pairs, pair_slot_begin, pair_slots);
 
   // Elimination order of the reduced camera system: reverse Cuthill-McKee
   // (Cuthill & McKee 1969; George 1971) on the co-visibility graph of the
