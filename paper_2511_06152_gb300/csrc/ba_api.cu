@@ -109,6 +109,7 @@ struct ba_ctx {
   std::mutex stats_mu;  // kernel statistics (API threads and the scheduler)
   // pinned host staging buffers of cluster creation, reused across calls (one
   // per concurrent creation; taken and returned under stage_mu)
+  std::atomic<int> creating{0};  // cluster creations in flight (host presort threads)
   std::mutex stage_mu;
   std::vector<std::pair<char*, size_t>> stage_free;
   double kms[KK_COUNT] = {0};
@@ -465,6 +466,11 @@ BatchView one_view(const DevCluster* d_desc, int n_free) {
 
 ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const auto t_start = std::chrono::steady_clock::now();
+  struct InFlight {
+    std::atomic<int>& n;
+    explicit InFlight(std::atomic<int>& v) : n(v) { ++n; }
+    ~InFlight() { --n; }
+  } in_flight(ctx->creating);
   const int nc = d->n_cams, np = d->n_pts, no = d->n_obs;
   if (nc < 1 || np < 0 || no < 0) return set_err(ctx, BA_ERR_INVALID, "n_cams must be >= 1, n_pts and n_obs >= 0");
   if (d->ptr_kind != BA_PTR_HOST && d->ptr_kind != BA_PTR_DEVICE) return set_err(ctx, BA_ERR_INVALID, "bad ptr_kind");
@@ -604,148 +610,200 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   const bool mixed = ctx->mixed;
   const int ch_tiles = chunk_tiles(mixed);
   std::vector<Chunk> chunks;
+  for (size_t t = 0; t < tiles.size();) {
+    Chunk ch{};
+    ch.obs_begin = tiles[t].obs_begin;
+    ch.tile_begin = (int)t;
+    while (t < tiles.size() && ch.n_tiles < ch_tiles) {
+      ch.n_obs += tiles[t].n_obs;
+      ++t;
+      ++ch.n_tiles;
+    }
+    ch.pt_begin = ppt[ch.obs_begin];  // observations are sorted by internal point
+    ch.n_pts = ppt[ch.obs_begin + ch.n_obs - 1] - ch.pt_begin + 1;
+    chunks.push_back(ch);
+  }
+  const int n_chunks = (int)chunks.size();
+  // Per chunk, on its own: the jobs (its free cameras, then its co-visible
+  // camera pairs, each by decreasing item count, ties by index / key), their
+  // item lists (increasing point-major order), lanes and lane-to-job table.
+  struct ChunkJobs {
+    std::vector<int> cam;            // free camera of each image job
+    std::vector<int> key;            // fa * nf + fb of each pair job
+    std::vector<int> count;          // items of each job, image jobs first
+    std::vector<unsigned short> cm;  // the image jobs' items, job after job
+    std::vector<unsigned int> pe;    // the pair jobs' items, job after job
+    std::vector<short> lane_begin, n_lanes;
+    unsigned char lane_job[kChunkThreads];
+  };
+  struct Scratch {
+    std::vector<std::vector<unsigned short>> per_cam;
+    std::vector<std::vector<unsigned int>> per_pair;  // by local pair; inner vectors are reused
+    std::vector<int> local_pair_of, lp_keys, corder, order;
+    std::vector<double> cost;
+    std::vector<int> lanes;
+    explicit Scratch(int nf_) : per_cam(nf_), local_pair_of((size_t)nf_ * nf_, -1) {}
+  };
+  std::vector<ChunkJobs> cj(n_chunks);
+  auto build_chunk = [&](int c, Scratch& S) {
+    const Chunk& ch = chunks[c];
+    ChunkJobs& J = cj[c];
+    for (auto& v : S.per_cam) v.clear();
+    int n_lp_used = 0;
+    S.lp_keys.clear();
+    for (int p = ch.obs_begin; p < ch.obs_begin + ch.n_obs; ++p) {
+      const int f = free_idx[pcam[p]];
+      if (f >= 0) S.per_cam[f].push_back((unsigned short)(p - ch.obs_begin));
+    }
+    // pairs, point by point (observations of a point are sorted by camera)
+    for (int p = ch.obs_begin; p < ch.obs_begin + ch.n_obs;) {
+      int e = p;
+      while (e < ch.obs_begin + ch.n_obs && ppt[e] == ppt[p]) ++e;
+      for (int a = p; a < e; ++a) {
+        const int fa = free_idx[pcam[a]];
+        if (fa < 0) continue;
+        for (int b = a + 1; b < e; ++b) {
+          const int fb = free_idx[pcam[b]];
+          if (fb < 0) continue;
+          const size_t key = (size_t)fa * nf + fb;
+          if (S.local_pair_of[key] < 0) {
+            if (n_lp_used == (int)S.per_pair.size()) S.per_pair.emplace_back();
+            S.per_pair[n_lp_used].clear();
+            S.local_pair_of[key] = n_lp_used++;
+            S.lp_keys.push_back((int)key);
+          }
+          S.per_pair[S.local_pair_of[key]].push_back((unsigned)(a - ch.obs_begin) | ((unsigned)(b - ch.obs_begin) << 16));
+        }
+      }
+      p = e;
+    }
+    S.corder.clear();
+    for (int f = 0; f < nf; ++f)
+      if (!S.per_cam[f].empty()) S.corder.push_back(f);
+    std::stable_sort(S.corder.begin(), S.corder.end(),
+                     [&](int x, int y) { return S.per_cam[x].size() > S.per_cam[y].size(); });
+    for (int f : S.corder) {
+      J.cam.push_back(f);
+      J.count.push_back((int)S.per_cam[f].size());
+      J.cm.insert(J.cm.end(), S.per_cam[f].begin(), S.per_cam[f].end());
+    }
+    S.order.resize(S.lp_keys.size());
+    for (size_t i = 0; i < S.order.size(); ++i) S.order[i] = (int)i;
+    std::sort(S.order.begin(), S.order.end(), [&](int x, int y) {
+      if (S.per_pair[x].size() != S.per_pair[y].size()) return S.per_pair[x].size() > S.per_pair[y].size();
+      return S.lp_keys[x] < S.lp_keys[y];
+    });
+    for (int li : S.order) {
+      const int key = S.lp_keys[li];
+      J.key.push_back(key);
+      J.count.push_back((int)S.per_pair[li].size());
+      J.pe.insert(J.pe.end(), S.per_pair[li].begin(), S.per_pair[li].end());
+      S.local_pair_of[key] = -1;
+    }
+    // Lanes per job: every lane of every job gets about the same work, a
+    // quantum Q of instructions (camera item ~165, pair item ~123), the
+    // smallest Q whose lanes fit the CTA; the pair jobs start on a warp
+    // boundary so that no warp runs both loop bodies.  A job has at least
+    // one lane and at most one per item; chunks with more jobs than threads
+    // run one lane per job (the kernel's fallback mode).
+    const int n_lc = (int)J.cam.size(), n_lp = (int)J.key.size(), nj = n_lc + n_lp;
+    J.lane_begin.assign(nj, 0);
+    J.n_lanes.assign(nj, 1);
+    std::memset(J.lane_job, 0, sizeof(J.lane_job));
+    if (nj > 0 && nj <= kChunkThreads) {
+      S.cost.resize(nj);
+      for (int q = 0; q < nj; ++q) S.cost[q] = J.count[q] * (q < n_lc ? 165.0 : 123.0);
+      S.lanes.resize(nj);
+      auto alloc = [&](double Q, bool align) {
+        int nc = 0, np_ = 0;
+        for (int q = 0; q < nj; ++q) {
+          const int cnt = J.count[q];
+          int l = (int)std::ceil(S.cost[q] / Q);
+          l = std::max(1, std::min(l, std::max(1, cnt)));
+          S.lanes[q] = l;
+          (q < n_lc ? nc : np_) += l;
+        }
+        return (align && n_lp > 0 ? (nc + 31) / 32 * 32 : nc) + np_;
+      };
+      bool align = alloc(1e300, true) <= kChunkThreads;  // one lane each must fit
+      double lo = 0.0, hi = 1.0;
+      for (int q = 0; q < nj; ++q) hi = std::max(hi, S.cost[q]);
+      for (int it = 0; it < 24; ++it) {  // smallest quantum that fits (to 2^-24 of the largest cost)
+        const double mid = 0.5 * (lo + hi);
+        if (mid > 0.0 && alloc(mid, align) <= kChunkThreads) hi = mid; else lo = mid;
+      }
+      alloc(hi, align);
+      int lb = 0;
+      for (int q = 0; q < nj; ++q) {
+        if (align && q == n_lc && q > 0) lb = (lb + 31) / 32 * 32;
+        J.lane_begin[q] = (short)lb;
+        J.n_lanes[q] = (short)S.lanes[q];
+        lb += S.lanes[q];
+      }
+      // lane t runs the last job whose lane run starts at or before t
+      int q = 0;
+      for (int t2 = 0; t2 < kChunkThreads; ++t2) {
+        while (q + 1 < nj && J.lane_begin[q + 1] <= t2) ++q;
+        J.lane_job[t2] = (unsigned char)q;
+      }
+    }
+  };
+  {
+    // the chunks on a few threads when few creations share the host (the
+    // result does not depend on the split); one thread otherwise
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    const int busy = std::max(1, ctx->creating.load());
+    const int n_thr = n_chunks >= 32 ? std::max(1, std::min(4, hw / busy)) : 1;
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+      Scratch S(nf);
+      for (int c; (c = next.fetch_add(1)) < n_chunks;) build_chunk(c, S);
+    };
+    std::vector<std::thread> th;
+    try {  // helpers beside the calling thread; if one cannot start, the others finish the chunks
+      for (int i = 1; i < n_thr; ++i) th.emplace_back(worker);
+    } catch (...) {
+    }
+    worker();
+    for (auto& x : th) x.join();
+  }
+  // merge, in chunk order: partial-sum slots, item offsets, pair indices
   std::vector<Job> jobs;
   std::vector<unsigned short> cm_list;
-  std::vector<unsigned char> lane_job;  // per chunk: the job of each lane (kChunkThreads bytes)
+  std::vector<unsigned char> lane_job((size_t)n_chunks * kChunkThreads);  // per chunk: the job of each lane
   std::vector<unsigned int> pent;
   std::vector<int> pair_of((size_t)nf * nf, -1);  // (fa, fb) -> pair index
   std::vector<int2> pair_key;
   std::vector<int2> cam_slot_ent, pair_slot_ent;  // (free camera or pair, slot), in chunk order
   int n_cslots = 0, n_pslots = 0;
-  {
-    std::vector<std::vector<unsigned short>> per_cam(nf);
-    std::vector<std::vector<unsigned int>> per_pair;  // indexed by local pair; inner vectors are reused
-    int n_lp_used = 0;
-    std::vector<int> local_pair_of((size_t)nf * nf, -1);
-    std::vector<int> lp_keys, corder, order, lanes;
-    std::vector<double> cost;
-    size_t t = 0;
-    while (t < tiles.size()) {
-      Chunk ch{};
-      ch.obs_begin = tiles[t].obs_begin;
-      ch.tile_begin = (int)t;
-      while (t < tiles.size() && ch.n_tiles < ch_tiles) {
-        ch.n_obs += tiles[t].n_obs;
-        ++t;
-        ++ch.n_tiles;
-      }
-      ch.pt_begin = ppt[ch.obs_begin];  // observations are sorted by internal point
-      ch.n_pts = ppt[ch.obs_begin + ch.n_obs - 1] - ch.pt_begin + 1;
-      for (auto& v : per_cam) v.clear();
-      for (int i = 0; i < n_lp_used; ++i) per_pair[i].clear();
-      n_lp_used = 0;
-      lp_keys.clear();
-      for (int p = ch.obs_begin; p < ch.obs_begin + ch.n_obs; ++p) {
-        const int f = free_idx[pcam[p]];
-        if (f >= 0) per_cam[f].push_back((unsigned short)(p - ch.obs_begin));
-      }
-      // pairs, point by point (observations of a point are sorted by camera)
-      for (int p = ch.obs_begin; p < ch.obs_begin + ch.n_obs;) {
-        int e = p;
-        while (e < ch.obs_begin + ch.n_obs && ppt[e] == ppt[p]) ++e;
-        for (int a = p; a < e; ++a) {
-          const int fa = free_idx[pcam[a]];
-          if (fa < 0) continue;
-          for (int b = a + 1; b < e; ++b) {
-            const int fb = free_idx[pcam[b]];
-            if (fb < 0) continue;
-            const size_t key = (size_t)fa * nf + fb;
-            if (local_pair_of[key] < 0) {
-              if (n_lp_used == (int)per_pair.size()) per_pair.emplace_back();
-              local_pair_of[key] = n_lp_used++;
-              lp_keys.push_back((int)key);
-            }
-            per_pair[local_pair_of[key]].push_back((unsigned)(a - ch.obs_begin) | ((unsigned)(b - ch.obs_begin) << 16));
-          }
-        }
-        p = e;
-      }
-      // jobs: the chunk's free cameras, then its camera pairs (both by
-      // decreasing item count, ties by index / key)
-      ch.job_begin = (int)jobs.size();
-      corder.clear();
-      for (int f = 0; f < nf; ++f)
-        if (!per_cam[f].empty()) corder.push_back(f);
-      std::stable_sort(corder.begin(), corder.end(),
-                       [&](int x, int y) { return per_cam[x].size() > per_cam[y].size(); });
-      for (int f : corder) {
-        Job jb{n_cslots++, (int)cm_list.size(), (int)per_cam[f].size(), 0, 1};
-        cam_slot_ent.push_back(make_int2(f, jb.slot));
-        cm_list.insert(cm_list.end(), per_cam[f].begin(), per_cam[f].end());
-        jobs.push_back(jb);
-      }
-      ch.n_lc = (int)corder.size();
-      order.resize(lp_keys.size());
-      for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-      std::sort(order.begin(), order.end(), [&](int x, int y) {
-        if (per_pair[x].size() != per_pair[y].size()) return per_pair[x].size() > per_pair[y].size();
-        return lp_keys[x] < lp_keys[y];
-      });
-      for (int li : order) {
-        const int key = lp_keys[li];
-        if (pair_of[key] < 0) {
-          pair_of[key] = (int)pair_key.size();
-          pair_key.push_back(make_int2(key / nf, key % nf));
-        }
-        Job jb{n_pslots++, (int)pent.size(), (int)per_pair[li].size(), 0, 1};
-        pair_slot_ent.push_back(make_int2(pair_of[key], jb.slot));
-        pent.insert(pent.end(), per_pair[li].begin(), per_pair[li].end());
-        jobs.push_back(jb);
-        local_pair_of[key] = -1;
-      }
-      ch.n_lp = (int)order.size();
-      // Lanes per job: every lane of every job gets about the same work, a
-      // quantum Q of instructions (camera item ~165, pair item ~123), the
-      // smallest Q whose lanes fit the CTA; the pair jobs start on a warp
-      // boundary so that no warp runs both loop bodies.  A job has at least
-      // one lane and at most one per item; chunks with more jobs than threads
-      // run one lane per job (the kernel's fallback mode).
-      const int nj = ch.n_lc + ch.n_lp;
-      if (nj > 0 && nj <= kChunkThreads) {
-        cost.resize(nj);
-        for (int q = 0; q < nj; ++q) cost[q] = jobs[ch.job_begin + q].count * (q < ch.n_lc ? 165.0 : 123.0);
-        lanes.resize(nj);
-        auto alloc = [&](double Q, bool align) {
-          int nc = 0, np_ = 0;
-          for (int q = 0; q < nj; ++q) {
-            const int cnt = jobs[ch.job_begin + q].count;
-            int l = (int)std::ceil(cost[q] / Q);
-            l = std::max(1, std::min(l, std::max(1, cnt)));
-            lanes[q] = l;
-            (q < ch.n_lc ? nc : np_) += l;
-          }
-          return (align && ch.n_lp > 0 ? (nc + 31) / 32 * 32 : nc) + np_;
-        };
-        bool align = alloc(1e300, true) <= kChunkThreads;  // one lane each must fit
-        double lo = 0.0, hi = 1.0;
-        for (int q = 0; q < nj; ++q) hi = std::max(hi, cost[q]);
-        for (int it = 0; it < 24; ++it) {  // smallest quantum that fits (to 2^-24 of the largest cost)
-          const double mid = 0.5 * (lo + hi);
-          if (mid > 0.0 && alloc(mid, align) <= kChunkThreads) hi = mid; else lo = mid;
-        }
-        alloc(hi, align);
-        int lb = 0;
-        for (int q = 0; q < nj; ++q) {
-          if (align && q == ch.n_lc && q > 0) lb = (lb + 31) / 32 * 32;
-          Job& jb = jobs[ch.job_begin + q];
-          jb.lane_begin = (short)lb;
-          jb.n_lanes = (short)lanes[q];
-          lb += lanes[q];
-        }
-      }
-      {  // lane t runs the last job whose lane run starts at or before t
-        const size_t base = lane_job.size();
-        lane_job.resize(base + kChunkThreads, 0);
-        if (nj > 0 && nj <= kChunkThreads) {
-          int q = 0;
-          for (int t2 = 0; t2 < kChunkThreads; ++t2) {
-            while (q + 1 < nj && jobs[ch.job_begin + q + 1].lane_begin <= t2) ++q;
-            lane_job[base + t2] = (unsigned char)q;
-          }
-        }
-      }
-      chunks.push_back(ch);
+  for (int c = 0; c < n_chunks; ++c) {
+    Chunk& ch = chunks[c];
+    const ChunkJobs& J = cj[c];
+    ch.job_begin = (int)jobs.size();
+    ch.n_lc = (int)J.cam.size();
+    ch.n_lp = (int)J.key.size();
+    size_t off = 0;
+    for (int q = 0; q < ch.n_lc; ++q) {
+      Job jb{n_cslots++, (int)cm_list.size(), J.count[q], J.lane_begin[q], J.n_lanes[q]};
+      cam_slot_ent.push_back(make_int2(J.cam[q], jb.slot));
+      cm_list.insert(cm_list.end(), J.cm.begin() + off, J.cm.begin() + off + J.count[q]);
+      off += J.count[q];
+      jobs.push_back(jb);
     }
+    off = 0;
+    for (int i = 0; i < ch.n_lp; ++i) {
+      const int q = ch.n_lc + i, key = J.key[i];
+      if (pair_of[key] < 0) {
+        pair_of[key] = (int)pair_key.size();
+        pair_key.push_back(make_int2(key / nf, key % nf));
+      }
+      Job jb{n_pslots++, (int)pent.size(), J.count[q], J.lane_begin[q], J.n_lanes[q]};
+      pair_slot_ent.push_back(make_int2(pair_of[key], jb.slot));
+      pent.insert(pent.end(), J.pe.begin() + off, J.pe.begin() + off + J.count[q]);
+      off += J.count[q];
+      jobs.push_back(jb);
+    }
+    std::memcpy(lane_job.data() + (size_t)c * kChunkThreads, J.lane_job, kChunkThreads);
   }
   // pairs in key order (the reduced system does not depend on this order, but a
   // fixed one keeps the tables reproducible)
