@@ -637,68 +637,94 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
     unsigned char lane_job[kChunkThreads];
   };
   struct Scratch {
-    std::vector<std::vector<unsigned short>> per_cam;
-    std::vector<std::vector<unsigned int>> per_pair;  // by local pair; inner vectors are reused
-    std::vector<int> local_pair_of, lp_keys, corder, order;
+    std::vector<int> cam_cnt, cam_off;  // by free camera
+    std::vector<int> local_pair_of;     // fa * nf + fb -> local pair, -1 between chunks
+    std::vector<int> pf;                // free camera of each observation of the chunk, or -1
+    std::vector<int> lp_keys, lp_cnt, lp_off, order;
+    std::vector<int> item_lp;           // local pair of each pair item, in point-major order
+    std::vector<unsigned int> item_val;
     std::vector<double> cost;
     std::vector<int> lanes;
-    explicit Scratch(int nf_) : per_cam(nf_), local_pair_of((size_t)nf_ * nf_, -1) {}
+    std::vector<int2> runs;
+    std::vector<int> l_lo, l_hi, l_mid;
+    explicit Scratch(int nf_) : cam_cnt(nf_, 0), cam_off(nf_), local_pair_of((size_t)nf_ * nf_, -1) {}
   };
   std::vector<ChunkJobs> cj(n_chunks);
   auto build_chunk = [&](int c, Scratch& S) {
     const Chunk& ch = chunks[c];
     ChunkJobs& J = cj[c];
-    for (auto& v : S.per_cam) v.clear();
-    int n_lp_used = 0;
-    S.lp_keys.clear();
-    for (int p = ch.obs_begin; p < ch.obs_begin + ch.n_obs; ++p) {
-      const int f = free_idx[pcam[p]];
-      if (f >= 0) S.per_cam[f].push_back((unsigned short)(p - ch.obs_begin));
+    const int o0 = ch.obs_begin, o1 = ch.obs_begin + ch.n_obs;
+    S.pf.resize(ch.n_obs);  // free camera of each of the chunk's observations, or -1
+    int* const pf = S.pf.data();
+    for (int p = o0; p < o1; ++p) pf[p - o0] = free_idx[pcam[p]];
+    // image jobs: items counted, jobs ordered, then each item placed at its
+    // job's next position (a stable counting sort: point-major order kept)
+    for (int i = 0; i < ch.n_obs; ++i) {
+      const int f = pf[i];
+      if (f >= 0 && S.cam_cnt[f]++ == 0) J.cam.push_back(f);
     }
-    // pairs, point by point (observations of a point are sorted by camera)
-    for (int p = ch.obs_begin; p < ch.obs_begin + ch.n_obs;) {
-      int e = p;
-      while (e < ch.obs_begin + ch.n_obs && ppt[e] == ppt[p]) ++e;
-      for (int a = p; a < e; ++a) {
-        const int fa = free_idx[pcam[a]];
+    std::sort(J.cam.begin(), J.cam.end(), [&](int x, int y) {
+      return S.cam_cnt[x] != S.cam_cnt[y] ? S.cam_cnt[x] > S.cam_cnt[y] : x < y;
+    });
+    {
+      int off = 0;
+      for (int f : J.cam) {
+        J.count.push_back(S.cam_cnt[f]);
+        S.cam_off[f] = off;
+        off += S.cam_cnt[f];
+      }
+      J.cm.resize(off);
+      for (int i = 0; i < ch.n_obs; ++i)
+        if (pf[i] >= 0) J.cm[S.cam_off[pf[i]]++] = (unsigned short)i;
+      for (int f : J.cam) S.cam_cnt[f] = 0;
+    }
+    // pair jobs, the same way; pairs point by point (observations of a point
+    // are sorted by camera), local pairs numbered by first appearance
+    S.lp_keys.clear();
+    S.lp_cnt.clear();
+    S.item_lp.clear();
+    S.item_val.clear();
+    for (int j = ch.pt_begin; j < ch.pt_begin + ch.n_pts; ++j) {
+      const int s0 = pt_start[j] - o0, e0 = pt_start[j + 1] - o0;
+      for (int a = s0; a < e0; ++a) {
+        const int fa = pf[a];
         if (fa < 0) continue;
-        for (int b = a + 1; b < e; ++b) {
-          const int fb = free_idx[pcam[b]];
+        int* const row = S.local_pair_of.data() + (size_t)fa * nf;
+        for (int b = a + 1; b < e0; ++b) {
+          const int fb = pf[b];
           if (fb < 0) continue;
-          const size_t key = (size_t)fa * nf + fb;
-          if (S.local_pair_of[key] < 0) {
-            if (n_lp_used == (int)S.per_pair.size()) S.per_pair.emplace_back();
-            S.per_pair[n_lp_used].clear();
-            S.local_pair_of[key] = n_lp_used++;
-            S.lp_keys.push_back((int)key);
+          int lp = row[fb];
+          if (lp < 0) {
+            lp = row[fb] = (int)S.lp_keys.size();
+            S.lp_keys.push_back(fa * nf + fb);
+            S.lp_cnt.push_back(0);
           }
-          S.per_pair[S.local_pair_of[key]].push_back((unsigned)(a - ch.obs_begin) | ((unsigned)(b - ch.obs_begin) << 16));
+          ++S.lp_cnt[lp];
+          S.item_lp.push_back(lp);
+          S.item_val.push_back((unsigned)a | ((unsigned)b << 16));
         }
       }
-      p = e;
     }
-    S.corder.clear();
-    for (int f = 0; f < nf; ++f)
-      if (!S.per_cam[f].empty()) S.corder.push_back(f);
-    std::stable_sort(S.corder.begin(), S.corder.end(),
-                     [&](int x, int y) { return S.per_cam[x].size() > S.per_cam[y].size(); });
-    for (int f : S.corder) {
-      J.cam.push_back(f);
-      J.count.push_back((int)S.per_cam[f].size());
-      J.cm.insert(J.cm.end(), S.per_cam[f].begin(), S.per_cam[f].end());
-    }
-    S.order.resize(S.lp_keys.size());
-    for (size_t i = 0; i < S.order.size(); ++i) S.order[i] = (int)i;
+    const int n_lp_used = (int)S.lp_keys.size();
+    S.order.resize(n_lp_used);
+    for (int i = 0; i < n_lp_used; ++i) S.order[i] = i;
     std::sort(S.order.begin(), S.order.end(), [&](int x, int y) {
-      if (S.per_pair[x].size() != S.per_pair[y].size()) return S.per_pair[x].size() > S.per_pair[y].size();
+      if (S.lp_cnt[x] != S.lp_cnt[y]) return S.lp_cnt[x] > S.lp_cnt[y];
       return S.lp_keys[x] < S.lp_keys[y];
     });
-    for (int li : S.order) {
-      const int key = S.lp_keys[li];
-      J.key.push_back(key);
-      J.count.push_back((int)S.per_pair[li].size());
-      J.pe.insert(J.pe.end(), S.per_pair[li].begin(), S.per_pair[li].end());
-      S.local_pair_of[key] = -1;
+    {
+      S.lp_off.resize(n_lp_used);
+      int off = 0;
+      for (int li : S.order) {
+        const int key = S.lp_keys[li];
+        J.key.push_back(key);
+        J.count.push_back(S.lp_cnt[li]);
+        S.lp_off[li] = off;
+        off += S.lp_cnt[li];
+        S.local_pair_of[key] = -1;
+      }
+      J.pe.resize(off);
+      for (size_t i = 0; i < S.item_lp.size(); ++i) J.pe[S.lp_off[S.item_lp[i]]++] = S.item_val[i];
     }
     // Lanes per job: every lane of every job gets about the same work, a
     // quantum Q of instructions (camera item ~165, pair item ~123), the
@@ -725,12 +751,71 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
         }
         return (align && n_lp > 0 ? (nc + 31) / 32 * 32 : nc) + np_;
       };
+      // alloc(Q, align) <= kChunkThreads.  Jobs of one kind are sorted by
+      // count, so equal jobs are runs that get equal lanes: one term per run,
+      // stopping as soon as the partial count exceeds the CTA.
+      S.runs.clear();  // (first job, jobs) of each run; the camera runs first
+      int n_cam_runs = 0;
+      for (int q = 0; q < nj; ++q) {
+        if (q == 0 || q == n_lc || J.count[q] != J.count[q - 1]) {
+          S.runs.push_back(make_int2(q, 0));
+          if (q < n_lc) ++n_cam_runs;
+        }
+        ++S.runs.back().y;
+      }
+      // Lanes never grow with Q (a correctly rounded division is monotone):
+      // a run's lanes at lo (or its cap, while lo = 0) and at hi bound them at
+      // every Q between, and a run whose bounds agree needs no division.
+      const int nr = (int)S.runs.size();
+      S.l_lo.resize(nr);
+      S.l_hi.resize(nr);
+      S.l_mid.resize(nr);
+      auto lanes_at = [&](int r, double Q) {
+        const int q = S.runs[r].x;
+        return std::max(1, std::min((int)std::ceil(S.cost[q] / Q), std::max(1, J.count[q])));
+      };
+      int evaluated = 0;  // runs whose l_mid the last fits() call set
+      auto fits = [&](double Q, bool align) {
+        int nc = 0, r = 0;
+        for (; r < n_cam_runs; ++r) {
+          const int l = S.l_lo[r] == S.l_hi[r] ? S.l_lo[r] : lanes_at(r, Q);
+          S.l_mid[r] = l;
+          nc += S.runs[r].y * l;
+          if (nc > kChunkThreads) {
+            evaluated = r + 1;
+            return false;
+          }
+        }
+        int tot = align && n_lp > 0 ? (nc + 31) / 32 * 32 : nc;
+        for (; r < nr; ++r) {
+          const int l = S.l_lo[r] == S.l_hi[r] ? S.l_lo[r] : lanes_at(r, Q);
+          S.l_mid[r] = l;
+          tot += S.runs[r].y * l;
+          if (tot > kChunkThreads) {
+            evaluated = r + 1;
+            return false;
+          }
+        }
+        evaluated = nr;
+        return tot <= kChunkThreads;
+      };
       bool align = alloc(1e300, true) <= kChunkThreads;  // one lane each must fit
       double lo = 0.0, hi = 1.0;
       for (int q = 0; q < nj; ++q) hi = std::max(hi, S.cost[q]);
+      for (int r = 0; r < nr; ++r) {
+        S.l_lo[r] = std::max(1, J.count[S.runs[r].x]);
+        S.l_hi[r] = lanes_at(r, hi);
+      }
       for (int it = 0; it < 24; ++it) {  // smallest quantum that fits (to 2^-24 of the largest cost)
         const double mid = 0.5 * (lo + hi);
-        if (mid > 0.0 && alloc(mid, align) <= kChunkThreads) hi = mid; else lo = mid;
+        if (mid > 0.0 && fits(mid, align)) {
+          hi = mid;
+          for (int r = 0; r < evaluated; ++r) S.l_hi[r] = S.l_mid[r];
+        } else {
+          lo = mid;
+          if (mid > 0.0)
+            for (int r = 0; r < evaluated; ++r) S.l_lo[r] = S.l_mid[r];
+        }
       }
       alloc(hi, align);
       int lb = 0;
@@ -776,33 +861,47 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
   std::vector<int2> pair_key;
   std::vector<int2> cam_slot_ent, pair_slot_ent;  // (free camera or pair, slot), in chunk order
   int n_cslots = 0, n_pslots = 0;
+  {
+    size_t n_lc = 0, n_lp = 0, n_cm = 0, n_pe = 0;
+    for (const ChunkJobs& J : cj) {
+      n_lc += J.cam.size();
+      n_lp += J.key.size();
+      n_cm += J.cm.size();
+      n_pe += J.pe.size();
+    }
+    jobs.reserve(n_lc + n_lp);
+    cam_slot_ent.reserve(n_lc);
+    pair_slot_ent.reserve(n_lp);
+    cm_list.reserve(n_cm);
+    pent.reserve(n_pe);
+  }
   for (int c = 0; c < n_chunks; ++c) {
     Chunk& ch = chunks[c];
     const ChunkJobs& J = cj[c];
     ch.job_begin = (int)jobs.size();
     ch.n_lc = (int)J.cam.size();
     ch.n_lp = (int)J.key.size();
-    size_t off = 0;
+    int off = (int)cm_list.size();  // the chunk's item lists are its jobs' lists, job after job
     for (int q = 0; q < ch.n_lc; ++q) {
-      Job jb{n_cslots++, (int)cm_list.size(), J.count[q], J.lane_begin[q], J.n_lanes[q]};
+      Job jb{n_cslots++, off, J.count[q], J.lane_begin[q], J.n_lanes[q]};
       cam_slot_ent.push_back(make_int2(J.cam[q], jb.slot));
-      cm_list.insert(cm_list.end(), J.cm.begin() + off, J.cm.begin() + off + J.count[q]);
       off += J.count[q];
       jobs.push_back(jb);
     }
-    off = 0;
+    cm_list.insert(cm_list.end(), J.cm.begin(), J.cm.end());
+    off = (int)pent.size();
     for (int i = 0; i < ch.n_lp; ++i) {
       const int q = ch.n_lc + i, key = J.key[i];
       if (pair_of[key] < 0) {
         pair_of[key] = (int)pair_key.size();
         pair_key.push_back(make_int2(key / nf, key % nf));
       }
-      Job jb{n_pslots++, (int)pent.size(), J.count[q], J.lane_begin[q], J.n_lanes[q]};
+      Job jb{n_pslots++, off, J.count[q], J.lane_begin[q], J.n_lanes[q]};
       pair_slot_ent.push_back(make_int2(pair_of[key], jb.slot));
-      pent.insert(pent.end(), J.pe.begin() + off, J.pe.begin() + off + J.count[q]);
       off += J.count[q];
       jobs.push_back(jb);
     }
+    pent.insert(pent.end(), J.pe.begin(), J.pe.end());
     std::memcpy(lane_job.data() + (size_t)c * kChunkThreads, J.lane_job, kChunkThreads);
   }
   // pairs in key order (the reduced system does not depend on this order, but a
