@@ -10,7 +10,8 @@ CUDA-graph launch, starting from the clusters' initial GNSS/IMU state.
 Metric: observations/s = sum(n_obs) * iterations / time, plus LM
 iterations/s, against the plain per-cluster FP64 GPU path and the FP64 CPU
 oracle.  Data are synthetic (seeded generator); every rank solves its own
-replica of the batch (weak scaling, no collective on the data path).
+replica of the batch (weak scaling, no collective on the data path; the
+time is the slowest rank's, the observations those of all replicas).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -67,6 +68,21 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def over_ranks(ms, units, world, dist=None, device="cpu"):
+    """Whole-job figures of a weak-scaling step over `world` ranks: the slowest
+    rank's time (ms) and the units all ranks processed (each rank's replica
+    has its own cluster sizes).  `dist` is torch.distributed with a process
+    group initialised; one rank returns its own figures."""
+    if world == 1:
+        return float(ms), int(units)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    n = torch.tensor([int(units)], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(n.item())
 
 
 def make_workload(replica, n_clusters, n_flights=0, large=False):
@@ -610,13 +626,10 @@ def main():
     ms = e0.elapsed_time(e1)
     launches = ctx.launch_count() - launches0
     kst = ctx.kernel_stats(reset=True)
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
+    # slowest rank's time; observations of every rank's own replica
+    t_max, obs_all = over_ranks(ms, total_obs, world, torch.distributed if world > 1 else None, "cuda")
     ms_per_step = t_max / args.steps
-    value = world * total_obs * iters * args.steps / (t_max * 1e-3)  # every rank solves an equal-shaped replica
+    value = obs_all * iters * args.steps / (t_max * 1e-3)
     lm_iters_per_s = world * len(ids) * iters * args.steps / (t_max * 1e-3)
 
     # dominant kernel and its roofline
@@ -652,7 +665,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "global_batch": args.clusters * world, "observations": total_obs * world,
+            "config": {"workload": WORKLOAD, "global_batch": args.clusters * world, "observations": obs_all,
                        "iters": iters, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (no flush)"},
             "lm_iters_per_s": lm_iters_per_s, "clocks": ck, "gpu_launches": launches, "roofline": roof,
