@@ -224,6 +224,49 @@ void free_probe(Probe* pr) {
 
 void note_direct(ba_ctx* ctx) { ctx->launches += take_direct_launches(); }
 
+// Host copies (pinned staging -> caller arrays) on up to max_threads threads,
+// each taking one contiguous share of the bytes of the list taken as one
+// sequence; small totals stay on the calling thread.
+struct HostCopy {
+  void* dst;
+  const void* src;
+  size_t bytes;
+};
+void copy_out(const std::vector<HostCopy>& items, int max_threads) {
+  size_t total = 0;
+  for (const HostCopy& c : items) total += c.bytes;
+  constexpr size_t kPerThread = (size_t)4 << 20;  // below this a thread does not pay for itself
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int n_thr = (int)std::max<size_t>(1, std::min<size_t>({(size_t)max_threads, (size_t)hw, total / kPerThread}));
+  auto part = [&](size_t b0, size_t b1) {  // bytes [b0, b1) of the sequence
+    size_t at = 0;
+    for (const HostCopy& c : items) {
+      const size_t lo = std::max(b0, at), hi = std::min(b1, at + c.bytes);
+      if (lo < hi) std::memcpy((char*)c.dst + (lo - at), (const char*)c.src + (lo - at), hi - lo);
+      at += c.bytes;
+      if (at >= b1) break;
+    }
+  };
+  std::vector<std::thread> th;
+  size_t started = 0;  // bytes handed to helper threads
+  if (n_thr > 1) {
+    const size_t share = (total + n_thr - 1) / n_thr;
+    try {
+      for (int t = 1; t < n_thr; ++t) {
+        const size_t b0 = std::min(total, (size_t)t * share), b1 = std::min(total, b0 + share);
+        th.emplace_back(part, b0, b1);
+        started = b1;
+      }
+    } catch (...) {  // a helper that cannot start leaves its share to this thread
+    }
+    part(0, std::min(total, share));
+    if (started < total) part(std::max(share, started), total);
+  } else {
+    part(0, total);
+  }
+  for (auto& x : th) x.join();
+}
+
 // Device memory of clusters and plans comes from the context's own pool,
 // stream-ordered: a free is queued behind the work already on its stream and
 // never waits for the device, so retiring a cluster does not stall a serving
@@ -2062,15 +2105,17 @@ BA_API ba_status ba_get_state_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32
     CUDA_TRY(ctx, cudaFreeAsync(tmp, ctx->stream));
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     off = 0;
+    std::vector<HostCopy> out;
     for (int i = i0; i < i1; ++i) {
       const Cluster* c = cs[i];
       const double* b = ctx->hstage + off;
       const size_t nr = (size_t)c->nc * 9, nt = (size_t)c->nc * 3, nx = (size_t)c->np * 3;
-      if (R && R[i]) std::memcpy(R[i], b, sizeof(double) * nr);
-      if (T && T[i]) std::memcpy(T[i], b + nr, sizeof(double) * nt);
-      if (X && X[i] && nx) std::memcpy(X[i], b + nr + nt, sizeof(double) * nx);
+      if (R && R[i]) out.push_back(HostCopy{R[i], b, sizeof(double) * nr});
+      if (T && T[i]) out.push_back(HostCopy{T[i], b + nr, sizeof(double) * nt});
+      if (X && X[i] && nx) out.push_back(HostCopy{X[i], b + nr + nt, sizeof(double) * nx});
       off += doubles_of(i);
     }
+    copy_out(out, 8);
     i0 = i1;
   }
   return BA_OK;
