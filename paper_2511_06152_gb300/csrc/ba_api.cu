@@ -459,8 +459,6 @@ ba_status run_and_collect(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, in
   ba_status st = get_plan(ctx, ids, &p);
   if (st != BA_OK) return st;
   const int n = (int)ids.size();
-  int before_iter = 0;
-  (void)before_iter;
   st = run_plan(ctx, p, iters);
   if (st != BA_OK) return st;
   StepRec* dtrace = nullptr;

@@ -943,7 +943,6 @@ __device__ void chol_blocked(double* A, int n, double* inv_diag, double* colbuf,
       }
       __syncthreads();
       const double inv = inv_diag[j];
-      const int w = k1 - j - 1;  // the panel's remaining columns j+1 .. k1-1
       for (int i = j + 1 + tid; i < n; i += bs) {
         if (efirst[i] > j) continue;  // L(i, j) = 0
         const double l = A[pk(i, j)] * inv;
@@ -951,7 +950,6 @@ __device__ void chol_blocked(double* A, int n, double* inv_diag, double* colbuf,
         const int cmax = min(i, k1 - 1);
         for (int c = j + 1; c <= cmax; ++c) A[pk(i, c)] -= l * colbuf[c];
       }
-      (void)w;
       __syncthreads();
     }
     if (*fail) return;
