@@ -151,18 +151,22 @@ typedef struct {
 } ba_step_info;
 
 typedef struct {
-  int32_t max_iters; /* LM iterations (accepted and rejected both count) */
+  int32_t max_iters; /* LM iterations at most (accepted and rejected both count) */
   int32_t reserved;
+  double ftol;       /* 0: run max_iters.  > 0: the cluster also stops after an accepted
+                        step, other than its first iteration, that lowered F by no more
+                        than ftol * F (F before that step).  Finite and >= 0. */
 } ba_solve_opts;
 
 typedef struct {
   int32_t status;     /* BA_OK, or the last step's error */
-  int32_t iters;      /* iterations run */
-  int32_t accepted;   /* accepted steps */
+  int32_t iters;      /* iterations run by this call (or ticket) */
+  int32_t accepted;   /* accepted steps: all of the cluster's, since its creation or reset */
   int32_t reserved;
-  double initial_cost;
+  double initial_cost; /* F before the first iteration: ba_solve_batch with a trace that holds
+                          every iteration; 0 otherwise (ba_poll included) */
   double final_cost;
-  double latency_ms;  /* submit -> completion seen by the scheduler */
+  double latency_ms;  /* submit -> completion seen by the scheduler (ba_poll) */
 } ba_result;
 
 /* Create a context on cfg->device.  *out receives the handle. */

@@ -70,7 +70,7 @@ class ba_step_info(ctypes.Structure):
 
 
 class ba_solve_opts(ctypes.Structure):
-    _fields_ = [("max_iters", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+    _fields_ = [("max_iters", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ftol", ctypes.c_double)]
 
 
 class ba_result(ctypes.Structure):
@@ -301,9 +301,9 @@ class Context:
         _check(self.L.ba_kernel_stats(self.h, _d(ms), cnt, n, int(reset)), self.h, "ba_kernel_stats")
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_KINDS)}
 
-    def submit(self, cid, iters):
+    def submit(self, cid, iters, ftol=0.0):
         t = ctypes.c_uint64()
-        _check(self.L.ba_submit(self.h, cid, ctypes.byref(ba_solve_opts(iters, 0)), ctypes.byref(t)), self.h,
+        _check(self.L.ba_submit(self.h, cid, ctypes.byref(ba_solve_opts(iters, 0, ftol)), ctypes.byref(t)), self.h,
                "ba_submit")
         return t.value
 

@@ -63,6 +63,10 @@ struct Plan {
 struct Ticket {
   ba_cluster_id id = 0;
   int iters = 0;
+  double ftol = 0.0;   // relative cost decrease that ends the solve (0: off)
+  int rounds = 0;      // scheduler rounds run = LM iterations run
+  double F_last = 0.0; // cost after the last round
+  int acc_last = -1;   // accepted steps after the last round (-1: before the first)
   int done = 0;
   ba_result res{};
   std::chrono::steady_clock::time_point t_submit;
@@ -1524,11 +1528,22 @@ void scheduler_loop(ba_ctx* ctx) {
       const auto now = std::chrono::steady_clock::now();
       for (int s = 0; s < T.n; ++s) {
         if (!T.occ[s]) continue;
-        if (st == BA_OK && T.lm[s].active) continue;
         Ticket& tk = ctx->tickets[T.occ_ticket[s]];
+        const LmState& L = T.lm[s];
+        bool finish = st != BA_OK || !L.active;
+        if (st == BA_OK) {  // one round = one LM iteration of every occupied slot
+          ++tk.rounds;
+          // converged: an accepted step (not the first) lowered F by at most ftol * F
+          if (!finish && tk.ftol > 0.0 && tk.acc_last >= 0 && L.n_accepted > tk.acc_last &&
+              tk.F_last - L.F <= tk.ftol * tk.F_last)
+            finish = true;
+          tk.F_last = L.F;
+          tk.acc_last = L.n_accepted;
+        }
+        if (!finish) continue;
         tk.done = 1;
         tk.res.status = st != BA_OK ? st : T.lm[s].status;
-        tk.res.iters = tk.iters;
+        tk.res.iters = tk.rounds;
         tk.res.final_cost = T.lm[s].F;
         tk.res.accepted = T.lm[s].n_accepted;
         tk.res.latency_ms = std::chrono::duration<double, std::milli>(now - tk.t_submit).count();
@@ -1973,6 +1988,7 @@ BA_API ba_status ba_kernel_stats(ba_ctx* ctx, double* ms, uint64_t* launches, in
 
 BA_API ba_status ba_submit(ba_ctx* ctx, ba_cluster_id id, const ba_solve_opts* opts, ba_ticket* out) {
   if (!ctx || !opts || !out || opts->max_iters <= 0) return BA_ERR_INVALID;
+  if (!(opts->ftol >= 0.0) || !std::isfinite(opts->ftol)) return set_err(ctx, BA_ERR_INVALID, "ftol must be finite and >= 0");
   cudaEvent_t ready = nullptr;
   {
     std::lock_guard<std::mutex> g(ctx->api_mu);
@@ -2001,6 +2017,7 @@ BA_API ba_status ba_submit(ba_ctx* ctx, ba_cluster_id id, const ba_solve_opts* o
   Ticket tk;
   tk.id = id;
   tk.iters = opts->max_iters;
+  tk.ftol = opts->ftol;
   tk.t_submit = std::chrono::steady_clock::now();
   tk.ready = ready;
   ctx->tickets[t] = tk;

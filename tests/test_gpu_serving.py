@@ -106,6 +106,39 @@ def test_serving_rejects_double_submit_and_reports_latency():
             ctx.poll(t)  # a ticket is consumed by the poll that returns it
 
 
+def test_serving_ftol_stops_at_the_first_small_accepted_step():
+    """ba_solve_opts.ftol: the ticket ends after the first accepted step, other
+    than the first iteration, whose decrease F_before - F_after is at most
+    ftol * F_before; the served state equals ba_run for that many iterations
+    on the same cluster, bit for bit."""
+    import paper_2511_06152_gb300 as ba
+    wins = _flight(9104)
+    ftol, cap = 1e-3, 100
+    with ba.Context(precision=ba.BA_MIXED, n_slots=4) as ctx:
+        c0 = _create(ctx, wins, 0, None)
+        t = ctx.submit(c0, cap, ftol=ftol)
+        r = None
+        for _ in range(20000):
+            r = ctx.poll(t)
+            if r is not None:
+                break
+            time.sleep(0.001)
+        assert r is not None and r["status"] == 0
+        assert 2 <= r["iters"] < cap
+        served = ctx.get_state(c0)
+        c1 = _create(ctx, wins, 0, None)
+        tr = ctx.run(c1, r["iters"])
+        for a, b in zip(served, ctx.get_state(c1)):
+            assert np.array_equal(a, b)
+        small = [i for i in range(1, len(tr))
+                 if tr[i]["accepted"] and tr[i]["F_before"] - tr[i]["F_after"] <= ftol * tr[i]["F_before"]]
+        assert small and small[0] == r["iters"] - 1
+        with pytest.raises(ba.BAError):
+            ctx.submit(c1, 5, ftol=-1.0)
+        with pytest.raises(ba.BAError):
+            ctx.submit(c1, 5, ftol=float("nan"))
+
+
 def test_warm_start_after_create_equals_warm_create():
     """ba_warm_start on an existing cluster gives the same state and result as
     creating the cluster with warm_from."""
