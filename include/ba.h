@@ -180,6 +180,35 @@ BA_API ba_status ba_init(ba_ctx** out, const ba_config* cfg);
  * exceed the context's budget. */
 BA_API ba_status ba_create_cluster(ba_ctx* ctx, const ba_cluster_desc* d, ba_cluster_id* out);
 
+/* Sizes and self-check of the presorted tables (ba_presort_host). */
+typedef struct {
+  int32_t n_free, n_tiles, n_chunks, n_pairs; /* free images, tiles, chunks, co-visible free pairs */
+  int32_t n_cam_jobs, n_pair_jobs;            /* image and pair reduction jobs over all chunks */
+  int32_t max_lanes;                          /* most lanes one chunk's jobs use (<= 256) */
+  int32_t fallback_chunks;                    /* chunks with more jobs than threads (one lane per job) */
+  int32_t tiles_per_chunk;                    /* of this precision */
+  int32_t checks_failed;                      /* 0 when every table invariant holds */
+  int64_t n_free_obs, n_pair_entries;         /* observations of free images; co-visible observation pairs */
+  uint64_t digest;                            /* FNV-1a of the tables' bytes */
+  char message[128];                          /* first failed check, or why the call failed */
+} ba_presort_info;
+
+/* Host only: the presort ba_create_cluster runs (validation, point order,
+ * point-major order, tiles, chunks, reduction jobs and their lanes, pair
+ * table, elimination order and envelope) on a cluster in host memory
+ * (d->ptr_kind = BA_PTR_HOST; warm-start fields ignored), for the tables of
+ * `precision`, with no context and no device: nothing is uploaded.  The
+ * tables are then checked against what the observations alone imply, rebuilt
+ * by brute force: every observation once in point-major order, tiles of whole
+ * points, each chunk's image and pair jobs holding exactly the observations
+ * and co-visible observation pairs of its points in order, counts
+ * non-increasing, lanes inside the CTA, the envelope holding every pair.
+ * threads > 0 builds the chunk tables on exactly that many threads (the
+ * tables must not depend on it; compare digests), 0 lets the library choose.
+ * Fails like ba_create_cluster on invalid input (BA_ERR_INVALID, reason in
+ * out->message); a failed table check is reported in out->checks_failed. */
+BA_API ba_status ba_presort_host(const ba_cluster_desc* d, int32_t precision, int32_t threads, ba_presort_info* out);
+
 /* Warm start an existing cluster from a live one (the cluster transition of
  * Sec. 3.2: a new window reuses the optimised overlap images and their
  * points).  cam_map[dst n_cams] / pt_map[dst n_pts] (host arrays) give, for

@@ -92,6 +92,19 @@ class ba_cluster_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class ba_presort_info(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in ("n_free", "n_tiles", "n_chunks", "n_pairs", "n_cam_jobs",
+                                             "n_pair_jobs", "max_lanes", "fallback_chunks", "tiles_per_chunk",
+                                             "checks_failed")] + \
+               [("n_free_obs", ctypes.c_int64), ("n_pair_entries", ctypes.c_int64), ("digest", ctypes.c_uint64),
+                ("message", ctypes.c_char * 128)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["message"] = self.message.decode()
+        return d
+
+
 class ba_dsm(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("x0", ctypes.c_double), ("y0", ctypes.c_double),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("h", ctypes.POINTER(ctypes.c_double))]
@@ -100,7 +113,7 @@ class ba_dsm(ctypes.Structure):
 EXPORTS = ["ba_init", "ba_create_cluster", "ba_linearize", "ba_solve_step", "ba_run", "ba_solve_batch", "ba_reset",
            "ba_reset_batch", "ba_submit", "ba_poll", "ba_get_state", "ba_get_state_batch", "ba_reprojection_errors",
            "ba_memory_in_use",
-           "ba_launch_count", "ba_kernel_stats", "ba_cost_noalloc", "ba_warm_start", "ba_transition", "ba_footprints", "ba_footprint_overlaps", "ba_patch_transfer_poses", "ba_patch_transfer_planar", "ba_get_cluster_info", "ba_destroy_cluster", "ba_shutdown",
+           "ba_launch_count", "ba_kernel_stats", "ba_cost_noalloc", "ba_warm_start", "ba_transition", "ba_footprints", "ba_footprint_overlaps", "ba_patch_transfer_poses", "ba_patch_transfer_planar", "ba_get_cluster_info", "ba_presort_host", "ba_destroy_cluster", "ba_shutdown",
            "ba_status_string", "ba_last_error"]
 
 _lib = None
@@ -148,6 +161,8 @@ def lib(build: bool = True):
             L.ba_reprojection_errors.argtypes = [vp, u64, _dp]
             L.ba_memory_in_use.argtypes = [vp, ctypes.POINTER(u64)]
             L.ba_get_cluster_info.argtypes = [vp, u64, ctypes.POINTER(ba_cluster_info)]
+            L.ba_presort_host.argtypes = [ctypes.POINTER(ba_cluster_desc), ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.POINTER(ba_presort_info)]
             L.ba_destroy_cluster.argtypes = [vp, u64]
             L.ba_shutdown.argtypes = [vp]
             L.ba_status_string.argtypes = [ctypes.c_int32]
@@ -208,6 +223,18 @@ def make_desc(scene, keep):
     d.mu0 = float(scene.get("mu0", 1e-4))
     d.warm_from = 0
     return d
+
+
+def presort_host(scene, precision=BA_MIXED, threads=0):
+    """ba_presort_host: the creation presort of a host-array scene on the host
+    alone (no GPU), its table sizes and the result of the tables' self-check."""
+    keep = []
+    d = make_desc(scene, keep)
+    out = ba_presort_info()
+    st = lib().ba_presort_host(ctypes.byref(d), precision, threads, ctypes.byref(out))
+    if st != BA_OK:
+        raise BAError(st, f"ba_presort_host: {lib().ba_status_string(st).decode()} {out.message.decode()}".strip())
+    return out.as_dict()
 
 
 class Context:

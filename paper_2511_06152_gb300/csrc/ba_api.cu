@@ -499,6 +499,300 @@ ba_status run_and_collect(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, in
 
 // ------------------------------------------------------------------ cluster creation
 
+// ------------------------------------------------------------------ presort self-check
+
+// ba_presort_host runs build_cluster with a probe: the chunk tables on a
+// given number of threads, and instead of the upload a check of the tables.
+struct PresortProbe {
+  int threads = 0;  // > 0: the chunk tables on exactly this many threads
+  ba_presort_info* out = nullptr;
+};
+
+// The presorted tables of one cluster, as build_cluster holds them before
+// staging.
+struct PresortView {
+  int nc, np, no, nf, tiles_per_chunk, obs_per_chunk;
+  const int32_t* ocam;
+  const int32_t* opt;
+  const std::vector<int>& free_idx;
+  const std::vector<int>& perm;
+  const std::vector<int>& inv;
+  const std::vector<int>& pm;
+  const std::vector<int>& pt_start;
+  const std::vector<int>& pcam;
+  const std::vector<int>& ppt;
+  const std::vector<Tile>& tiles;
+  const std::vector<Chunk>& chunks;
+  const std::vector<Job>& jobs;
+  const std::vector<unsigned short>& cm_list;
+  const std::vector<unsigned char>& lane_job;
+  const std::vector<unsigned int>& pent;
+  const std::vector<int2>& pair_key;
+  const std::vector<int>& cam_slot_begin;
+  const std::vector<int>& cam_slots;
+  const std::vector<int>& pair_slot_begin;
+  const std::vector<int>& pair_slots;
+  const std::vector<int>& fpos;
+  const std::vector<int>& env_first;
+};
+
+// Checks every table against what the observations alone imply, the
+// expected contents rebuilt here by brute force (not by the presort's own
+// steps), and reports the sizes and an FNV-1a digest of the tables.  A
+// failed check counts in checks_failed; message names the first.
+void check_presort(const PresortView& V, ba_presort_info* o) {
+  int failed = 0;
+  auto fail = [&](const char* what) {
+    if (failed++ == 0) std::snprintf(o->message, sizeof(o->message), "%s", what);
+  };
+  const int no = V.no, np = V.np, nf = V.nf;
+  // caller <-> internal point order, point-major order (points ascending,
+  // cameras strictly ascending within a point)
+  {
+    bool ok = (int)V.perm.size() == np && (int)V.inv.size() == np;
+    for (int j = 0; ok && j < np; ++j) ok = V.perm[j] >= 0 && V.perm[j] < np && V.inv[V.perm[j]] == j;
+    if (!ok) fail("point order: perm and inv are not inverse permutations");
+  }
+  {
+    std::vector<char> seen(no, 0);
+    bool ok = (int)V.pm.size() == no;
+    for (int p = 0; ok && p < no; ++p) {
+      const int i = V.pm[p];
+      if (i < 0 || i >= no || seen[i]) {
+        ok = false;
+        break;
+      }
+      seen[i] = 1;
+      ok = V.pcam[p] == V.ocam[i] && V.ppt[p] == V.inv[V.opt[i]] &&
+           (p == 0 || V.ppt[p] > V.ppt[p - 1] || (V.ppt[p] == V.ppt[p - 1] && V.pcam[p] > V.pcam[p - 1]));
+    }
+    if (!ok) fail("point-major order");
+    std::vector<int> cnt(np + 1, 0);
+    for (int i = 0; i < no; ++i) ++cnt[V.inv[V.opt[i]] + 1];
+    for (int j = 0; j < np; ++j) cnt[j + 1] += cnt[j];
+    if (V.pt_start != cnt) fail("point starts");
+  }
+  // tiles: consecutive runs of whole points, 1..32 observations, covering all
+  {
+    int at = 0;
+    bool ok = true;
+    for (const Tile& t : V.tiles) {
+      ok = ok && t.obs_begin == at && t.n_obs >= 1 && t.n_obs <= 32 &&
+           (at == 0 || V.ppt[at] != V.ppt[at - 1]);
+      at += t.n_obs;
+    }
+    if (!ok || at != no) fail("tiles");
+  }
+  // chunks: consecutive tiles; jobs consecutive, image jobs first
+  {
+    int tt = 0, jb = 0;
+    bool ok = true;
+    for (const Chunk& ch : V.chunks) {
+      int n_obs = 0;
+      for (int t = ch.tile_begin; t < ch.tile_begin + ch.n_tiles && t < (int)V.tiles.size(); ++t)
+        n_obs += V.tiles[t].n_obs;
+      ok = ok && ch.tile_begin == tt && ch.n_tiles >= 1 && ch.n_tiles <= V.tiles_per_chunk &&
+           tt + ch.n_tiles <= (int)V.tiles.size() && ch.obs_begin == V.tiles[tt].obs_begin && ch.n_obs == n_obs &&
+           ch.n_obs <= V.obs_per_chunk && ch.pt_begin == V.ppt[ch.obs_begin] &&
+           ch.n_pts == V.ppt[ch.obs_begin + ch.n_obs - 1] - ch.pt_begin + 1 && ch.job_begin == jb &&
+           ch.n_lc >= 0 && ch.n_lp >= 0;
+      if (!ok) break;
+      tt += ch.n_tiles;
+      jb += ch.n_lc + ch.n_lp;
+    }
+    if (!ok || tt != (int)V.tiles.size() || jb != (int)V.jobs.size()) {
+      fail("chunks");
+      o->checks_failed = failed;
+      return;  // the job checks below walk the chunks
+    }
+  }
+  // slot -> free camera and slot -> pair, from the grouped slot lists
+  const int n_pairs = (int)V.pair_key.size();
+  int n_cslots = 0, n_pslots = 0;
+  for (const Chunk& ch : V.chunks) {
+    n_cslots += ch.n_lc;
+    n_pslots += ch.n_lp;
+  }
+  std::vector<int> slot_cam(n_cslots, -1), slot_pair(n_pslots, -1);
+  {
+    bool ok = (int)V.cam_slot_begin.size() == nf + 1 && V.cam_slot_begin[0] == 0 &&
+              V.cam_slot_begin[nf] == n_cslots && (int)V.cam_slots.size() == n_cslots;
+    for (int f = 0; ok && f < nf; ++f)
+      for (int k = V.cam_slot_begin[f]; ok && k < V.cam_slot_begin[f + 1]; ++k) {
+        const int sl = V.cam_slots[k];
+        ok = sl >= 0 && sl < n_cslots && slot_cam[sl] < 0 && (k == V.cam_slot_begin[f] || sl > V.cam_slots[k - 1]);
+        if (ok) slot_cam[sl] = f;
+      }
+    ok = ok && (int)V.pair_slot_begin.size() == n_pairs + 1 && V.pair_slot_begin[0] == 0 &&
+         V.pair_slot_begin[n_pairs] == n_pslots && (int)V.pair_slots.size() == n_pslots;
+    for (int q = 0; ok && q < n_pairs; ++q)
+      for (int k = V.pair_slot_begin[q]; ok && k < V.pair_slot_begin[q + 1]; ++k) {
+        const int sl = V.pair_slots[k];
+        ok = sl >= 0 && sl < n_pslots && slot_pair[sl] < 0 && (k == V.pair_slot_begin[q] || sl > V.pair_slots[k - 1]);
+        if (ok) slot_pair[sl] = q;
+      }
+    if (!ok) {
+      fail("slot groups");
+      o->checks_failed = failed;
+      return;
+    }
+  }
+  // jobs: per chunk, one image job per free camera observed in it and one
+  // pair job per co-visible free pair, with exactly the items the
+  // observations imply, counts non-increasing (ties by camera / key), slots
+  // in job order; pairs numbered by first appearance
+  {
+    bool ok = true;
+    int cs = 0, ps = 0;
+    std::vector<char> pair_seen(n_pairs, 0);
+    int next_pair = 0;
+    for (size_t c = 0; ok && c < V.chunks.size(); ++c) {
+      const Chunk& ch = V.chunks[c];
+      std::map<int, std::vector<unsigned>> want_cam, want_pair;
+      for (int j = ch.pt_begin; j < ch.pt_begin + ch.n_pts; ++j)
+        for (int a = V.pt_start[j]; a < V.pt_start[j + 1]; ++a) {
+          const int fa = V.free_idx[V.pcam[a]];
+          if (fa < 0) continue;
+          want_cam[fa].push_back((unsigned)(a - ch.obs_begin));
+          for (int b = a + 1; b < V.pt_start[j + 1]; ++b) {
+            const int fb = V.free_idx[V.pcam[b]];
+            if (fb >= 0)
+              want_pair[fa * nf + fb].push_back((unsigned)(a - ch.obs_begin) | ((unsigned)(b - ch.obs_begin) << 16));
+          }
+        }
+      for (auto& kv : want_cam)  // items of a camera, ascending
+        std::sort(kv.second.begin(), kv.second.end());
+      ok = ch.n_lc == (int)want_cam.size() && ch.n_lp == (int)want_pair.size();
+      for (int q = 0; ok && q < ch.n_lc; ++q) {
+        const Job& jb = V.jobs[ch.job_begin + q];
+        ok = jb.slot == cs++;
+        if (!ok) break;
+        const int f = slot_cam[jb.slot];
+        auto it = want_cam.find(f);
+        ok = it != want_cam.end() && jb.count == (int)it->second.size() && jb.item_begin >= 0 &&
+             jb.item_begin + (size_t)jb.count <= V.cm_list.size();
+        for (int k = 0; ok && k < jb.count; ++k) ok = V.cm_list[jb.item_begin + k] == it->second[k];
+        if (ok && q > 0) {
+          const Job& pv = V.jobs[ch.job_begin + q - 1];
+          ok = pv.count > jb.count || (pv.count == jb.count && slot_cam[pv.slot] < f);
+        }
+      }
+      for (int q = 0; ok && q < ch.n_lp; ++q) {
+        const Job& jb = V.jobs[ch.job_begin + ch.n_lc + q];
+        ok = jb.slot == ps++;
+        if (!ok) break;
+        const int pi = slot_pair[jb.slot];
+        const int key = V.pair_key[pi].x * nf + V.pair_key[pi].y;
+        if (!pair_seen[pi]) {  // first appearance: the next pair index
+          ok = pi == next_pair++;
+          pair_seen[pi] = 1;
+        }
+        auto it = want_pair.find(key);
+        ok = ok && V.pair_key[pi].x < V.pair_key[pi].y && it != want_pair.end() &&
+             jb.count == (int)it->second.size() && jb.item_begin >= 0 &&
+             jb.item_begin + (size_t)jb.count <= V.pent.size();
+        for (int k = 0; ok && k < jb.count; ++k) ok = V.pent[jb.item_begin + k] == it->second[k];
+        if (ok && q > 0) {
+          const Job& pv = V.jobs[ch.job_begin + ch.n_lc + q - 1];
+          const int pkey = V.pair_key[slot_pair[pv.slot]].x * nf + V.pair_key[slot_pair[pv.slot]].y;
+          ok = pv.count > jb.count || (pv.count == jb.count && pkey < key);
+        }
+      }
+    }
+    if (ok) ok = next_pair == n_pairs;
+    size_t cm_total = 0, pe_total = 0;
+    for (const Chunk& ch : V.chunks) {
+      for (int q = 0; q < ch.n_lc; ++q) cm_total += V.jobs[ch.job_begin + q].count;
+      for (int q = 0; q < ch.n_lp; ++q) pe_total += V.jobs[ch.job_begin + ch.n_lc + q].count;
+    }
+    if (ok) ok = cm_total == V.cm_list.size() && pe_total == V.pent.size();
+    if (!ok) fail("jobs and their items");
+  }
+  // lanes: a run of at least one lane (at most one per item) per job, runs in
+  // job order within the CTA; lane t runs the last job whose run starts at or
+  // before t; chunks with more jobs than threads: one lane per job
+  int max_lanes = 0, fallback = 0;
+  {
+    bool ok = V.lane_job.size() == V.chunks.size() * (size_t)kChunkThreads;
+    for (size_t c = 0; ok && c < V.chunks.size(); ++c) {
+      const Chunk& ch = V.chunks[c];
+      const int nj = ch.n_lc + ch.n_lp;
+      const unsigned char* row = V.lane_job.data() + c * kChunkThreads;
+      if (nj == 0 || nj > kChunkThreads) {
+        fallback += nj > kChunkThreads;
+        for (int q = 0; ok && q < nj; ++q)
+          ok = V.jobs[ch.job_begin + q].lane_begin == 0 && V.jobs[ch.job_begin + q].n_lanes == 1;
+        for (int t = 0; ok && t < kChunkThreads; ++t) ok = row[t] == 0;
+        continue;
+      }
+      int end = 0;
+      for (int q = 0; ok && q < nj; ++q) {
+        const Job& jb = V.jobs[ch.job_begin + q];
+        ok = jb.n_lanes >= 1 && jb.n_lanes <= std::max(1, jb.count) && jb.lane_begin >= end &&
+             (q > 0 || jb.lane_begin == 0);
+        end = jb.lane_begin + jb.n_lanes;
+      }
+      ok = ok && end <= kChunkThreads;
+      max_lanes = std::max(max_lanes, end);
+      for (int t = 0, q = 0; ok && t < kChunkThreads; ++t) {
+        while (q + 1 < nj && V.jobs[ch.job_begin + q + 1].lane_begin <= t) ++q;
+        ok = row[t] == q;
+      }
+    }
+    if (!ok) fail("lanes");
+  }
+  // elimination order: a permutation whose envelope holds every co-visible pair
+  {
+    bool ok = (int)V.fpos.size() == nf && (int)V.env_first.size() == nf;
+    std::vector<char> seen(nf, 0);
+    for (int f = 0; ok && f < nf; ++f) {
+      ok = V.fpos[f] >= 0 && V.fpos[f] < nf && !seen[V.fpos[f]];
+      if (ok) seen[V.fpos[f]] = 1;
+    }
+    for (int p = 0; ok && p < nf; ++p) ok = V.env_first[p] >= 0 && V.env_first[p] <= p && (p == 0 || V.env_first[p] >= V.env_first[p - 1]);
+    for (const int2& k : V.pair_key) {
+      if (!ok) break;
+      const int a = V.fpos[k.x], b = V.fpos[k.y];
+      ok = V.env_first[std::max(a, b)] <= std::min(a, b);
+    }
+    if (!ok) fail("elimination order and envelope");
+  }
+  // sizes and digest
+  unsigned long long h = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t bytes) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < bytes; ++i) {
+      h ^= b[i];
+      h *= 1099511628211ull;
+    }
+  };
+  mix(V.pm.data(), sizeof(int) * V.pm.size());
+  mix(V.tiles.data(), sizeof(Tile) * V.tiles.size());
+  mix(V.chunks.data(), sizeof(Chunk) * V.chunks.size());
+  mix(V.jobs.data(), sizeof(Job) * V.jobs.size());
+  mix(V.cm_list.data(), sizeof(unsigned short) * V.cm_list.size());
+  mix(V.lane_job.data(), V.lane_job.size());
+  mix(V.pent.data(), sizeof(unsigned int) * V.pent.size());
+  mix(V.pair_key.data(), sizeof(int2) * V.pair_key.size());
+  mix(V.cam_slots.data(), sizeof(int) * V.cam_slots.size());
+  mix(V.pair_slots.data(), sizeof(int) * V.pair_slots.size());
+  mix(V.fpos.data(), sizeof(int) * V.fpos.size());
+  mix(V.env_first.data(), sizeof(int) * V.env_first.size());
+  o->n_free = nf;
+  o->n_tiles = (int32_t)V.tiles.size();
+  o->n_chunks = (int32_t)V.chunks.size();
+  o->n_pairs = n_pairs;
+  o->n_cam_jobs = n_cslots;
+  o->n_pair_jobs = n_pslots;
+  o->max_lanes = max_lanes;
+  o->fallback_chunks = fallback;
+  o->tiles_per_chunk = V.tiles_per_chunk;
+  o->checks_failed = failed;
+  o->n_free_obs = (int64_t)V.cm_list.size();
+  o->n_pair_entries = (int64_t)V.pent.size();
+  o->digest = h;
+}
+
 // A one-cluster view for the kernels that only walk the descriptor table
 // (camera records, warm start): no prefix sums, no device allocation.
 BatchView one_view(const DevCluster* d_desc, int n_free) {
@@ -509,7 +803,7 @@ BatchView one_view(const DevCluster* d_desc, int n_free) {
   return bv;
 }
 
-ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
+ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const PresortProbe* probe = nullptr) {
   const auto t_start = std::chrono::steady_clock::now();
   struct InFlight {
     std::atomic<int>& n;
@@ -883,7 +1177,8 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
     // result does not depend on the split); one thread otherwise
     const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
     const int busy = std::max(1, ctx->creating.load());
-    const int n_thr = n_chunks >= 32 ? std::max(1, std::min(4, hw / busy)) : 1;
+    const int n_thr = probe && probe->threads > 0 ? probe->threads
+                                                  : (n_chunks >= 32 ? std::max(1, std::min(4, hw / busy)) : 1);
     std::atomic<int> next{0};
     auto worker = [&]() {
       Scratch S(nf);
@@ -1022,6 +1317,14 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c) {
       while (i < nblk && 6 * env_first[(kBigNB * i) / 6] <= last_col) ++i;
       big_below[k] = i - (k + 1);
     }
+  }
+
+  if (probe) {  // ba_presort_host: the tables are checked instead of staged
+    check_presort(PresortView{nc, np, no, nf, ch_tiles, chunk_obs(mixed), ocam.data(), opt.data(), free_idx, perm, inv,
+                              pm, pt_start, pcam, ppt, tiles, chunks, jobs, cm_list, lane_job, pent, pair_key,
+                              cam_slot_begin, cam_slots, pair_slot_begin, pair_slots, fpos, env_first},
+                  probe->out);
+    return BA_OK;
   }
 
   // arena layout: static (uploaded) part first
@@ -1984,6 +2287,28 @@ BA_API ba_status ba_kernel_stats(ba_ctx* ctx, double* ms, uint64_t* launches, in
       ctx->klaunch[i] = 0;
     }
   return BA_OK;
+}
+
+BA_API ba_status ba_presort_host(const ba_cluster_desc* d, int32_t precision, int32_t threads, ba_presort_info* out) {
+  if (!out) return BA_ERR_INVALID;
+  std::memset(out, 0, sizeof(*out));
+  auto reject = [&](const char* why) {
+    std::snprintf(out->message, sizeof(out->message), "%s", why);
+    return BA_ERR_INVALID;
+  };
+  if (!d) return reject("null cluster description");
+  if (precision != BA_FP64 && precision != BA_MIXED) return reject("precision must be BA_FP64 or BA_MIXED");
+  if (d->ptr_kind != BA_PTR_HOST) return reject("ba_presort_host reads host arrays only");
+  if (threads < 0 || threads > 64) return reject("threads must be 0 (the library's choice) to 64");
+  ba_ctx ctx;  // host bookkeeping only: no device, stream or pool is touched
+  ctx.mixed = precision == BA_MIXED;
+  Cluster c;
+  PresortProbe probe;
+  probe.threads = threads;
+  probe.out = out;
+  const ba_status st = build_cluster(&ctx, d, &c, &probe);
+  if (st != BA_OK) std::snprintf(out->message, sizeof(out->message), "%s", t_last_error.c_str());
+  return st;
 }
 
 BA_API ba_status ba_submit(ba_ctx* ctx, ba_cluster_id id, const ba_solve_opts* opts, ba_ticket* out) {

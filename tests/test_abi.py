@@ -45,7 +45,7 @@ def test_status_strings_and_init_without_gpu():
 
 
 STRUCTS = ["ba_config", "ba_cluster_desc", "ba_lin_info", "ba_step_info", "ba_solve_opts", "ba_result",
-           "ba_cluster_info", "ba_dsm"]
+           "ba_cluster_info", "ba_dsm", "ba_presort_info"]
 
 
 def test_struct_layouts_match_header(tmp_path):
