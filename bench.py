@@ -45,7 +45,7 @@ WORKLOAD = ("batched local BA: 256 clusters, 8-32 images in 2-3 strips, 5k-60k p
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--clusters", type=int, default=256)
@@ -375,13 +375,17 @@ def serving_leg(args, ba, stream, flights):
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms, started before the
+    warm-up so that it is sampling when the timed region opens; stop(t0, t1)
+    summarises the samples taken inside [t0, t1] (time.time() seconds, by
+    nvidia-smi's own timestamp, else by arrival)."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,timestamp")
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
-        self.rows = []
+        self.rows = []  # (sample time, fields)
         self.proc = None
 
     def start(self):
@@ -393,22 +397,37 @@ class ClockSampler:
         except (OSError, ValueError):
             self.proc = None
 
+    @staticmethod
+    def sample_time(parts, arrival):
+        try:
+            import datetime
+            return datetime.datetime.strptime(parts[9], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except (IndexError, ValueError):
+            return arrival
+
     def _read(self):
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 9:
-                self.rows.append(parts)
+                self.rows.append((self.sample_time(parts, time.time()), parts))
 
-    def stop(self):
+    def stop(self, t0=None, t1=None):
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+        return self.summarize(self.rows, t0, t1)
+
+    @staticmethod
+    def summarize(rows, t0=None, t1=None):
+        inside = [r for t, r in rows if t0 is None or t0 <= t <= t1]
+        window = "timed region" if inside else "all samples (none inside the timed region)"
+        use = inside or [r for _, r in rows]
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        for r in use:
             try:
                 sm.append(float(r[1]))
                 mx.append(float(r[2]))
@@ -418,7 +437,7 @@ class ClockSampler:
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "window": window}
 
 
 # ---------------------------------------------------------------- CPU oracle leg
@@ -607,14 +626,15 @@ def main():
         ctx.reset_batch(ids)
         return ctx.solve_batch(ids, iters)
 
+    clocks = ClockSampler(local)
+    clocks.start()  # sampling by the time the timed region opens
     for _ in range(args.warmup):
         res = step()
     ctx.kernel_stats(reset=True)
     log(f"timing {args.steps} steps")
     launches0 = ctx.launch_count()
-    clocks = ClockSampler(local)
     barrier()
-    clocks.start()
+    t_on = time.time()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
@@ -622,7 +642,7 @@ def main():
     e1.record(stream)
     e1.synchronize()
     barrier()
-    ck = clocks.stop()
+    ck = clocks.stop(t_on, time.time())
     ms = e0.elapsed_time(e1)
     launches = ctx.launch_count() - launches0
     kst = ctx.kernel_stats(reset=True)
