@@ -499,6 +499,31 @@ ba_status run_and_collect(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, in
 
 // ------------------------------------------------------------------ cluster creation
 
+// f(begin, end) over [0, n) in n_thr contiguous ranges, the first on the
+// calling thread; a helper that cannot start leaves its range to the calling
+// thread.  f must write disjoint outputs per range.
+template <class F>
+void par_ranges(int n_thr, size_t n, const F& f) {
+  if (n_thr <= 1 || n < 2) {
+    f((size_t)0, n);
+    return;
+  }
+  const size_t share = (n + n_thr - 1) / n_thr;
+  std::vector<std::thread> th;
+  size_t started = std::min(n, share);  // [0, share) is the calling thread's
+  try {
+    for (int t = 1; t < n_thr && started < n; ++t) {
+      const size_t b0 = started, b1 = std::min(n, b0 + share);
+      th.emplace_back([&f, b0, b1] { f(b0, b1); });
+      started = b1;
+    }
+  } catch (...) {
+  }
+  f((size_t)0, std::min(n, share));
+  if (started < n) f(started, n);
+  for (auto& x : th) x.join();
+}
+
 // ------------------------------------------------------------------ presort self-check
 
 // ba_presort_host runs build_cluster with a probe: the chunk tables on a
@@ -838,6 +863,14 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
   for (int i = 0; i < no; ++i)
     if (ocam[i] < 0 || ocam[i] >= nc || opt[i] < 0 || opt[i] >= np)
       return set_err(ctx, BA_ERR_INVALID, "observation index out of range");
+  // threads for the staging gathers: a few when few creations share the host
+  // (hardware threads / creations in flight, at most 4), none for small
+  // clusters (a thread start costs tens of microseconds); no result depends
+  // on the split
+  const int hw_threads = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int par = probe && probe->threads > 0 ? probe->threads
+                                              : std::max(1, std::min(4, hw_threads / std::max(1, ctx->creating.load())));
+  auto par_for = [&](size_t n, const auto& f) { par_ranges(n >= ((size_t)1 << 16) ? par : 1, n, f); };
 
   // free cameras, in camera order
   std::vector<int> free_idx(nc, -1), cam_of_free;
@@ -1427,17 +1460,19 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
   {
     double* xs = reinterpret_cast<double*>(stage_ptr + o_X);
     float* xf = reinterpret_cast<float*>(xs);
-    for (int i = 0; i < np; ++i)
-      for (int a = 0; a < 3; ++a) {
-        const double v = X[3 * (size_t)perm[i] + a];
-        if (mixed) {
-          const float hi = (float)v;
-          xf[2 * (3 * (size_t)i + a)] = hi;
-          xf[2 * (3 * (size_t)i + a) + 1] = (float)(v - (double)hi);
-        } else {
-          xs[3 * (size_t)i + a] = v;
+    par_for((size_t)np, [&](size_t b, size_t e) {
+      for (size_t i = b; i < e; ++i)
+        for (int a = 0; a < 3; ++a) {
+          const double v = X[3 * (size_t)perm[i] + a];
+          if (mixed) {
+            const float hi = (float)v;
+            xf[2 * (3 * i + a)] = hi;
+            xf[2 * (3 * i + a) + 1] = (float)(v - (double)hi);
+          } else {
+            xs[3 * i + a] = v;
+          }
         }
-      }
+    });
   }
   put(o_X + xbytes, stage_ptr + o_X, xbytes);
   put(o_Rp, Rp.data(), sizeof(double) * Rp.size());
@@ -1462,18 +1497,20 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
     double* su = (double*)(stage_ptr + o_uv);
     float2* chi = mixed ? (float2*)(stage_ptr + o_chi) : nullptr;
     float2* clo = mixed ? (float2*)(stage_ptr + o_clo) : nullptr;
-    for (int p = 0; p < no; ++p) {
-      const int i = pm[p];
-      su[2 * p] = uv[2 * i];
-      su[2 * p + 1] = uv[2 * i + 1];
-      if (chi) {  // observation relative to the principal point, double-float
-        const double cu = uv[2 * i] - intr[7 * (size_t)ocam[i] + 1];
-        const double cv = uv[2 * i + 1] - intr[7 * (size_t)ocam[i] + 2];
-        const float hu = (float)cu, hv = (float)cv;
-        chi[p] = make_float2(hu, hv);
-        clo[p] = make_float2((float)(cu - (double)hu), (float)(cv - (double)hv));
+    par_for((size_t)no, [&](size_t b, size_t e) {
+      for (size_t p = b; p < e; ++p) {
+        const size_t i = (size_t)pm[p];
+        su[2 * p] = uv[2 * i];
+        su[2 * p + 1] = uv[2 * i + 1];
+        if (chi) {  // observation relative to the principal point, double-float
+          const double cu = uv[2 * i] - intr[7 * (size_t)ocam[i] + 1];
+          const double cv = uv[2 * i + 1] - intr[7 * (size_t)ocam[i] + 2];
+          const float hu = (float)cu, hv = (float)cv;
+          chi[p] = make_float2(hu, hv);
+          clo[p] = make_float2((float)(cu - (double)hu), (float)(cv - (double)hv));
+        }
       }
-    }
+    });
   }
   put(o_chunks, chunks.data(), sizeof(Chunk) * chunks.size());
   put(o_jobs, jobs.data(), sizeof(Job) * jobs.size());
