@@ -108,6 +108,7 @@ def _check(sc, precisions=(ba.BA_MIXED, ba.BA_FP64)):
 
 @pytest.mark.parametrize("seed,strips,per_strip,n_points,fixed", [
     (1, 1, 3, 12, None), (2, 2, 5, 400, None), (3, 3, 6, 2500, (0, 1)), (4, 2, 12, 6000, (0, 5, 11)),
+    (7, 4, 12, 8000, (0, 1)),  # 46 free images: the global-memory solver's tables
 ])
 def test_presort_tables_generated_clusters(seed, strips, per_strip, n_points, fixed):
     sc = sg.tiny_cluster(seed, strips, per_strip, n_points, fixed=fixed)
