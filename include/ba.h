@@ -293,14 +293,31 @@ BA_API ba_status ba_patch_transfer_planar(ba_ctx* ctx, int32_t n, const double* 
                                           const double* g0, int32_t m, const double* theta, const double* g,
                                           double* q);
 
-/* Evaluate F and the gradient infinity norm at the current state. */
+/* The robust cost F(x) of Eq. 7 at the current state (Huber on each
+ * squared pixel residual over sigma_px^2, halved, plus half the squared
+ * whitened GNSS/IMU prior residuals of the free images) and the infinity norm
+ * of its gradient over the free images' 6-vectors and the points' 3-vectors,
+ * from one linearisation (Sec. 3.2).  out (host, caller-owned) must not be
+ * NULL.  Blocking.  BA_ERR_NOT_FOUND for an unknown id, BA_ERR_INVALID for a
+ * NULL out or a cluster in service. */
 BA_API ba_status ba_linearize(ba_ctx* ctx, ba_cluster_id id, ba_lin_info* out);
 
-/* One LM iteration on one cluster (blocking); out may be NULL. */
+/* One Levenberg-Marquardt iteration of the local BA of Sec. 3.2 (Eq. 7) on
+ * one cluster: linearise, eliminate the points (Schur complement), damp,
+ * factor and solve the reduced camera system in binary64 with one refinement
+ * step, back-substitute the points, evaluate F at the candidate, accept or
+ * reject it and update the damping.  Blocking; *out (host, may be NULL)
+ * receives the step record.  A reduced or point system that is not positive
+ * definite is a rejected step with status BA_ERR_NOT_PD in the record, not a
+ * failed call.  BA_ERR_NOT_FOUND for an unknown id, BA_ERR_INVALID for a
+ * cluster in service. */
 BA_API ba_status ba_solve_step(ba_ctx* ctx, ba_cluster_id id, ba_step_info* out);
 
-/* iters LM iterations on one cluster in one device-side sequence (no host
- * round trip between iterations); trace[iters] may be NULL. */
+/* iters (>= 0) iterations of ba_solve_step on one cluster in one device-side
+ * sequence (one CUDA-graph launch, no host round trip between iterations).
+ * trace (host, caller-owned, may be NULL) receives [iters] step records; the
+ * device keeps the last 256, so for iters > 256 the earlier records are
+ * zero.  Blocking.  Errors as ba_solve_step; BA_ERR_INVALID for iters < 0. */
 BA_API ba_status ba_run(ba_ctx* ctx, ba_cluster_id id, int32_t iters, ba_step_info* trace);
 
 /* iters LM iterations on n clusters at once: every kernel of an iteration is
@@ -316,25 +333,40 @@ BA_API ba_status ba_run(ba_ctx* ctx, ba_cluster_id id, int32_t iters, ba_step_in
 BA_API ba_status ba_solve_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n, int32_t iters,
                          ba_result* results, ba_step_info* trace);
 
-/* Restore a cluster's initial state (the one given at create) and damping. */
+/* Restore a cluster's initial state (the one given at create, or the one a
+ * warm start wrote), its damping and LM counters.  Enqueued on the context's
+ * stream.  BA_ERR_NOT_FOUND for an unknown id, BA_ERR_INVALID for a cluster
+ * in service. */
 BA_API ba_status ba_reset(ba_ctx* ctx, ba_cluster_id id);
 
 /* ba_reset on n clusters in one launch (enqueued on the context's stream;
  * returns without waiting). */
 BA_API ba_status ba_reset_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n);
 
-/* Queue a cluster for the serving scheduler (non-blocking).  The scheduler
- * admits queued clusters into free slots between LM iterations, so work
- * submitted while others run joins the running batch.  *out receives a
- * ticket for ba_poll. */
+/* Queue a cluster for the serving scheduler (non-blocking): the sliding
+ * clusters of Sec. 3.2 solved as they arrive.  The scheduler admits queued
+ * clusters into free slots between LM iterations, so work submitted while
+ * others run joins the running batch; each iteration is the arithmetic of
+ * ba_solve_step.  Work the caller queued on the context's stream before the
+ * call (creation, warm start, reset) is ordered before the cluster's first
+ * iteration.  The cluster is in service until its ticket completes.  *out
+ * receives a ticket for ba_poll.  BA_ERR_NOT_FOUND for an unknown id;
+ * BA_ERR_INVALID for NULL opts or out, max_iters <= 0, a negative or
+ * non-finite ftol, a cluster of more than 32 free images, or a cluster
+ * already submitted. */
 BA_API ba_status ba_submit(ba_ctx* ctx, ba_cluster_id id, const ba_solve_opts* opts, ba_ticket* out);
 
 /* BA_PENDING while the ticket's cluster is queued or running; BA_OK with
- * *out filled once it has finished.  Thread-safe. */
+ * *out (host, may be NULL) filled once it has finished, which consumes the
+ * ticket.  BA_ERR_NOT_FOUND for an unknown or consumed ticket.  Thread-safe. */
 BA_API ba_status ba_poll(ba_ctx* ctx, ba_ticket t, ba_result* out);
 
-/* Copy the current state out.  Pointers are host pointers when ptr_kind is
- * BA_PTR_HOST, device pointers when BA_PTR_DEVICE; any may be NULL. */
+/* Copy the current state out in binary64 (double-float states rounded):
+ * R[n_cams][9] (row-major, camera->world), T[n_cams][3], X[n_pts][3] in the
+ * caller's camera and point order.  Caller-owned buffers: host pointers when
+ * ptr_kind is BA_PTR_HOST, device pointers when BA_PTR_DEVICE; any may be
+ * NULL.  Blocking (ordered behind the work on the context's stream).
+ * BA_ERR_NOT_FOUND for an unknown id. */
 BA_API ba_status ba_get_state(ba_ctx* ctx, ba_cluster_id id, double* R, double* T, double* X, int32_t ptr_kind);
 
 /* The current states of n clusters at once, each as ba_get_state returns it
@@ -347,8 +379,10 @@ BA_API ba_status ba_get_state(ba_ctx* ctx, ba_cluster_id id, double* R, double* 
 BA_API ba_status ba_get_state_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n, double* const* R,
                                     double* const* T, double* const* X);
 
-/* Per-observation reprojection error norms |pi(...) - p| in pixels at the
- * current state, in the caller's observation order (host buffer [n_obs]). */
+/* Per-observation reprojection error norms |pi(K R^T (X - T)) - p| in pixels
+ * (the model of Eq. 5, the residual of Eq. 6) at the current state, in the
+ * caller's observation order, into err[n_obs] (host, caller-owned).
+ * BA_ERR_INVALID for a NULL err, BA_ERR_NOT_FOUND for an unknown id. */
 BA_API ba_status ba_reprojection_errors(ba_ctx* ctx, ba_cluster_id id, double* err);
 
 /* Sizes of a cluster's presorted tables: the units the kernels of one LM
