@@ -409,7 +409,8 @@ typedef struct ba_cluster_info {
  * id.  Reads host-side records only: no device work. */
 BA_API ba_status ba_get_cluster_info(ba_ctx* ctx, ba_cluster_id id, ba_cluster_info* out);
 
-/* Device memory the context holds now, in bytes. */
+/* Device memory the context holds now, in bytes (clusters, plans, serving
+ * slots; the budget of ba_config.hbm_budget_bytes counts the same). */
 BA_API ba_status ba_memory_in_use(ba_ctx* ctx, uint64_t* bytes);
 
 /* Kernels this context has launched so far (kernel nodes of graph launches
@@ -444,12 +445,24 @@ BA_API ba_status ba_kernel_stats(ba_ctx* ctx, double* ms, uint64_t* launches, in
  * cudaMalloc, cudaFree or other allocating routine is called. */
 BA_API ba_status ba_cost_noalloc(const ba_cluster_desc* d, void* stream, double* F_out);
 
+/* Free a cluster: its device arena is released stream-ordered (after the
+ * work already queued on the context's stream), without waiting; batch plans
+ * that hold it are dropped.  BA_ERR_NOT_FOUND for an unknown id,
+ * BA_ERR_INVALID for a cluster in service. */
 BA_API ba_status ba_destroy_cluster(ba_ctx* ctx, ba_cluster_id id);
+
+/* Stop the serving scheduler once every submitted cluster has finished, wait
+ * for the device, free every cluster, plan and buffer of the context and the
+ * context itself.  Results not yet polled are dropped.  ctx is invalid
+ * afterwards. */
 BA_API ba_status ba_shutdown(ba_ctx* ctx);
+
+/* Static text of a status code (never NULL). */
 BA_API const char* ba_status_string(ba_status s);
 
-/* Human-readable reason of the last error returned on this context (valid
- * until the next call on the context). */
+/* Human-readable reason of the last error a call on the calling thread
+ * returned (thread-local: the API is called from several threads, the
+ * scheduler among them); valid until that thread's next failing call. */
 BA_API const char* ba_last_error(ba_ctx* ctx);
 
 #ifdef __cplusplus
