@@ -480,7 +480,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    scenes = make_workload(0, args.clusters)
+    scenes, _, _ = make_workload(0, args.clusters)
     total_obs = sum(s["n_obs"] for s in scenes)
     vals = []
     per_step = max(2.0, 120.0 / max(1, args.steps + args.warmup))

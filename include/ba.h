@@ -96,6 +96,13 @@ typedef struct {
 } ba_config;
 
 #define BA_FLAG_KERNEL_TIMING 1 /* bracket every kernel with CUDA events (also inside graphs) */
+/* Failure injection, for tests of the failure handling only: in mixed
+ * precision, the linearise+Schur kernel waits for each CTA's first staged
+ * chunk on a barrier that nothing completes, gives up after 1 ms, and takes
+ * the path of an expired copy wait (the copies it issued are waited for, the
+ * clusters of its chunks get BA_ERR_TIMEOUT in their step status and the
+ * step is rejected; nothing faults or hangs).  No effect in BA_FP64. */
+#define BA_FLAG_INJECT_COPY_TIMEOUT 2
 
 /* Kernel kinds reported by ba_kernel_stats, in this order. */
 #define BA_KERNEL_LIN_SCHUR 0      /* per chunk: residuals, Jacobians, point blocks, Schur partial sums */
@@ -169,15 +176,33 @@ typedef struct {
   double latency_ms;  /* submit -> completion seen by the scheduler (ba_poll) */
 } ba_result;
 
-/* Create a context on cfg->device.  *out receives the handle. */
+/* Create a context on cfg->device: the device-side home of the clusters a
+ * flight produces one after another (Sec. 3.2: BA runs on each cluster C_l
+ * as it fills, on the same platform, in real time; Sec. 1, Eq. 1 gives the
+ * per-image time budget it serves).  cfg (host, caller-owned, read during the
+ * call only): device ordinal, stream, device-memory budget, precision,
+ * serving slots, refinement passes, flags.  *out (host) receives the handle,
+ * which the caller releases with ba_shutdown.  BA_ERR_INVALID for a NULL
+ * argument or an unknown precision; BA_ERR_CUDA when the device cannot be
+ * used (no GPU, or a runtime call failed). */
 BA_API ba_status ba_init(ba_ctx** out, const ba_config* cfg);
 
 /* Copy a cluster to the device and presort its observation index
- * (point-major and camera-major orders, camera-pair table).  Fails with
- * BA_ERR_INVALID on indices out of range, repeated (camera, point) pairs,
- * more than BA_MAX_TRACK observations of one point, non-finite input, or
- * no free camera; with BA_ERR_BUDGET when the device memory it needs would
- * exceed the context's budget. */
+ * (point-major and camera-major orders, camera-pair table).  The cluster is
+ * the unit of the paper's local BA (Sec. 3.2): M images C_l = {I_k1 .. I_kM},
+ * including images of adjacent strips, each with its GNSS/IMU pose as the
+ * initial value (R, T) and as the prior (R_prior, T_prior); the tracks of
+ * the points matched inside the cluster (obs_cam, obs_pt, obs_uv: the
+ * observations p_kj of Eq. 5 and Eq. 6); and the overlap images carried over
+ * from the previous cluster, the first half of which are held fixed
+ * (`fixed`).  d (host, caller-owned) and the arrays it points to (host or
+ * device memory by d->ptr_kind) are read during the call only.  *out (host)
+ * receives the id; the cluster lives until ba_destroy_cluster or
+ * ba_shutdown.  Fails with BA_ERR_INVALID on indices out of range, repeated
+ * (camera, point) pairs, more than BA_MAX_TRACK observations of one point,
+ * non-finite input, or no free camera; with BA_ERR_BUDGET when the device
+ * memory it needs would exceed the context's budget (retry once other
+ * clusters are freed); BA_ERR_CUDA when an upload fails. */
 BA_API ba_status ba_create_cluster(ba_ctx* ctx, const ba_cluster_desc* d, ba_cluster_id* out);
 
 /* Sizes and self-check of the presorted tables (ba_presort_host). */
@@ -362,8 +387,11 @@ BA_API ba_status ba_submit(ba_ctx* ctx, ba_cluster_id id, const ba_solve_opts* o
 BA_API ba_status ba_poll(ba_ctx* ctx, ba_ticket t, ba_result* out);
 
 /* Copy the current state out in binary64 (double-float states rounded):
- * R[n_cams][9] (row-major, camera->world), T[n_cams][3], X[n_pts][3] in the
- * caller's camera and point order.  Caller-owned buffers: host pointers when
+ * the refined exterior orientations (R_k, T_k) of the cluster's images and
+ * the refined points X_j, the unknowns of Eq. 7 (Sec. 3.2) that the cluster
+ * transition hands on to the next cluster.  R[n_cams][9] (row-major,
+ * camera->world), T[n_cams][3], X[n_pts][3] in the caller's camera and point
+ * order.  Caller-owned buffers: host pointers when
  * ptr_kind is BA_PTR_HOST, device pointers when BA_PTR_DEVICE; any may be
  * NULL.  Blocking (ordered behind the work on the context's stream).
  * BA_ERR_NOT_FOUND for an unknown id. */
@@ -445,9 +473,11 @@ BA_API ba_status ba_kernel_stats(ba_ctx* ctx, double* ms, uint64_t* launches, in
  * cudaMalloc, cudaFree or other allocating routine is called. */
 BA_API ba_status ba_cost_noalloc(const ba_cluster_desc* d, void* stream, double* F_out);
 
-/* Free a cluster: its device arena is released stream-ordered (after the
- * work already queued on the context's stream), without waiting; batch plans
- * that hold it are dropped.  BA_ERR_NOT_FOUND for an unknown id,
+/* Free a cluster: the end of a sliding cluster's life (Sec. 3.2: once the
+ * next cluster has taken over its overlap images, its state is no longer
+ * needed).  Its device arena is released stream-ordered (after the work
+ * already queued on the context's stream), without waiting; batch plans that
+ * hold it are dropped.  BA_ERR_NOT_FOUND for an unknown id,
  * BA_ERR_INVALID for a cluster in service. */
 BA_API ba_status ba_destroy_cluster(ba_ctx* ctx, ba_cluster_id id);
 

@@ -31,6 +31,7 @@ BA_MIXED = 1
 BA_PTR_HOST = 0
 BA_PTR_DEVICE = 1
 BA_FLAG_KERNEL_TIMING = 1
+BA_FLAG_INJECT_COPY_TIMEOUT = 2  # failure injection for tests: the staged-copy wait expires
 KERNEL_KINDS = ["lin_schur", "partial_reduce", "factor", "backsub_cost", "lm_update", "cost_tiles", "cost_init",
                 "other"]
 

@@ -110,6 +110,7 @@ struct ba_ctx {
   std::map<std::vector<ba_cluster_id>, Plan*> plans;
   int attr_max_n = 0;
   bool timing = false;
+  int inject = 0;  // failure-injection bits for the kernels (BA_FLAG_INJECT_*)
   std::mutex stats_mu;  // kernel statistics (API threads and the scheduler)
   // pinned host staging buffers of cluster creation, reused across calls (one
   // per concurrent creation; taken and returned under stage_mu)
@@ -380,6 +381,7 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
   p->bv.total_chunks = pre[(n + 1) + n];
   p->bv.total_items = pre[2 * (n + 1) + n];
   p->bv.max_n = max_n;
+  p->bv.inject = ctx->inject;
   p->lm_out = (LmState*)(p->dbuf + o_lm);
   p->gnorm = (double*)(p->dbuf + o_gn);
   ctx->plans[ids] = p;
@@ -1745,6 +1747,7 @@ ba_status slots_setup(ba_ctx* ctx) {
   bv.n = n;
   bv.total_tiles = bv.total_chunks = bv.total_items = 1 << 30;  // the graph uses the largest grids
   bv.max_n = 6 * kMaxFreeSmall;
+  bv.inject = ctx->inject;
   T.dirty = true;
   return BA_OK;
 }
@@ -1937,6 +1940,7 @@ BA_API ba_status ba_init(ba_ctx** out, const ba_config* cfg) {
   ctx->n_slots = cfg->n_slots > 0 ? cfg->n_slots : 64;
   ctx->refine = cfg->refine_steps >= 0 ? cfg->refine_steps : 1;
   ctx->timing = (cfg->flags & BA_FLAG_KERNEL_TIMING) != 0;
+  ctx->inject = (cfg->flags & BA_FLAG_INJECT_COPY_TIMEOUT) ? kInjectCopyTimeout : 0;
   if (cfg->stream) {
     ctx->stream = (cudaStream_t)cfg->stream;
   } else {

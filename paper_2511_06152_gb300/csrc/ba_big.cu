@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(256) k_big_diag(const DevCluster* dcl, int k) 
       const double d = L[j][j];
       if (!(d > 0.0)) *C.bflag = 1;
       const double dd = d > 0.0 ? d : 1.0;
-      const double inv = rsqrt(dd);
+      const double inv = pivot_rsqrt(dd);
       L[j][j] = dd * inv;
       C.bx[3 * n + r0 + j] = inv;
       s_inv = inv;

@@ -13,6 +13,17 @@ namespace bagpu {
 
 __device__ __forceinline__ float rsqrt_any(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_any(double x) { return rsqrt(x); }
+
+// 1 / sqrt(d) of a Cholesky pivot d > 0.  A pivot can be positive but tiny
+// (a block whose only term is mu * D with a tiny damping mu, down to
+// subnormal values): the reciprocal square root is taken of d scaled by an
+// even power of two into the normal range, and the result is scaled back.
+__device__ __forceinline__ double pivot_rsqrt(double d) {
+  return d < 0x1p-960 ? rsqrt(d * 0x1p960) * 0x1p480 : rsqrt(d);
+}
+__device__ __forceinline__ float pivot_rsqrt(float d) {
+  return d < 0x1p-100f ? rsqrtf(d * 0x1p100f) * 0x1p50f : rsqrtf(d);
+}
 __device__ __forceinline__ float recip_any(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip_any(double x) { return 1.0 / x; }
 

@@ -188,8 +188,13 @@ struct BatchView {
   int n;
   int total_tiles, total_chunks, total_items;
   int max_n;             // largest 6 * n_free in the batch
-  int pad;
+  int inject;            // failure injection for tests (kInject* bits); 0 in normal use
 };
+
+// kInjectCopyTimeout: the mixed linearise+Schur kernel waits for its first
+// staged chunk on a barrier that nothing completes, with a 1 ms limit, so
+// that its bounded-wait failure path runs (BA_FLAG_INJECT_COPY_TIMEOUT).
+constexpr int kInjectCopyTimeout = 1;
 
 // Kernel kinds, for launch counting and per-kernel timing.
 enum KernelKind {

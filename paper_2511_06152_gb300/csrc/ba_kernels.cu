@@ -349,15 +349,15 @@ __device__ __forceinline__ void linearize_tile(const DevCluster& C, LmState* lm,
       const Real a00 = v00 + mu * d0, a11 = v11 + mu * d1, a22 = v22 + mu * d2;
       // V* = L L^T with M = L^-1 from reciprocal square roots of the pivots
       bool ok = a00 > Real(0);
-      m00 = rsqrt_any(ok ? a00 : Real(1));
+      m00 = pivot_rsqrt(ok ? a00 : Real(1));
       const Real l10 = v01 * m00, l20 = v02 * m00;
       const Real t11 = a11 - l10 * l10;
       ok = ok && t11 > Real(0);
-      m11 = rsqrt_any(t11 > Real(0) ? t11 : Real(1));
+      m11 = pivot_rsqrt(t11 > Real(0) ? t11 : Real(1));
       const Real l21 = (v12 - l20 * l10) * m11;
       const Real t22 = a22 - l20 * l20 - l21 * l21;
       ok = ok && t22 > Real(0);
-      m22 = rsqrt_any(t22 > Real(0) ? t22 : Real(1));
+      m22 = pivot_rsqrt(t22 > Real(0) ? t22 : Real(1));
       if (!ok && report_fail) lm->pt_fail = 1;  // point block not positive definite: reject this step
       m10 = -l10 * m00 * m11;
       m21 = -l21 * m11 * m22;
@@ -575,6 +575,7 @@ constexpr uint32_t kStageLaneBytes = kChunkThreads;  // one byte per lane
 constexpr uint32_t kTableBytes = kHeadBytes + kStageTileBytes + kStageJobBytes + kStageLaneBytes;
 constexpr uint32_t kStageBytes = 2 * kStageIdxBytes + kStageChiBytes + kStageXBytes + 2 * kTableBytes;
 constexpr uint64_t kCopyWaitNs = 200000000ull;  // give up on a staged copy after 200 ms
+constexpr uint64_t kInjectWaitNs = 1000000ull;  // the injected wait's limit (kInjectCopyTimeout)
 static_assert(kTableBytes % 16 == 0 && kStageTileBytes % 16 == 0 && kStageJobBytes % 16 == 0, "16-byte staging");
 
 struct Stage {
@@ -585,6 +586,7 @@ struct Stage {
   char* tab;  // two table buffers of kTableBytes
   uint64_t* bar;
   int* ok;
+  uint64_t* never;  // failure injection: a barrier no copy or thread completes
   __device__ ChunkHead* head(int b) const { return reinterpret_cast<ChunkHead*>(tab + b * kTableBytes); }
   __device__ char* tiles(int b) const { return tab + b * kTableBytes + kHeadBytes; }
   __device__ char* jobs(int b) const { return tab + b * kTableBytes + kHeadBytes + kStageTileBytes; }
@@ -676,8 +678,10 @@ __global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed
     S.tab = st + 2 * kStageIdxBytes + kStageChiBytes + kStageXBytes;
     S.bar = reinterpret_cast<uint64_t*>(st + kStageBytes);
     S.ok = reinterpret_cast<int*>(st + kStageBytes + 8);
+    S.never = reinterpret_cast<uint64_t*>(st + kStageBytes + 16);
     if (threadIdx.x == 0) {
       mbar_init(S.bar, 1);
+      mbar_init(S.never, 1);
       fence_barrier_init();
     }
     __syncthreads();
@@ -693,7 +697,11 @@ __global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed
     }
     ObsView V{};
     if constexpr (MIXED) {
-      if (threadIdx.x == 0) *S.ok = mbar_wait_bounded(S.bar, phase, kCopyWaitNs) ? 1 : 0;
+      if (threadIdx.x == 0) {
+        const bool ok = (bv.inject & kInjectCopyTimeout) ? mbar_wait_bounded(S.never, 0u, kInjectWaitNs)
+                                                         : mbar_wait_bounded(S.bar, phase, kCopyWaitNs);
+        *S.ok = ok ? 1 : 0;
+      }
       __syncthreads();
       phase ^= 1u;
       if (!*S.ok) {
@@ -933,7 +941,7 @@ __device__ void chol_blocked(double* A, int n, double* inv_diag, double* colbuf,
         if (lane == 0) {
           const double d = A[pk(j, j)];
           if (!(d > 0.0)) *fail = 1;
-          inv = rsqrt(d > 0.0 ? d : 1.0);  // one reciprocal square root per pivot
+          inv = pivot_rsqrt(d > 0.0 ? d : 1.0);  // one reciprocal square root per pivot
           const double r = (d > 0.0 ? d : 1.0) * inv;
           A[pk(j, j)] = r;
           inv_diag[j] = inv;
@@ -1023,7 +1031,7 @@ __device__ void chol_panel_p(double* A, int n, int k1, int k2, double* inv_diag,
       if (tid == 0) {
         const double d = A[pk(j, j)];
         if (!(d > 0.0)) *fail = 1;
-        inv = rsqrt(d > 0.0 ? d : 1.0);
+        inv = pivot_rsqrt(d > 0.0 ? d : 1.0);
         A[pk(j, j)] = (d > 0.0 ? d : 1.0) * inv;
         inv_diag[j] = inv;
       }
@@ -2003,8 +2011,8 @@ int chunk_tiles(bool mixed) { return mixed ? kChunkTilesMixed : kChunkTilesF64; 
 
 static size_t chunk_smem_bytes(bool mixed) {
   // records (later overlaid by the lane partials); mixed path: the chunk
-  // staging, its barrier and a flag
-  return chunk_records_bytes(mixed) + (mixed ? (size_t)kStageBytes + 16 : 0);
+  // staging, its barrier, a flag and the failure-injection barrier
+  return chunk_records_bytes(mixed) + (mixed ? (size_t)kStageBytes + 24 : 0);
 }
 
 template <bool MIXED>

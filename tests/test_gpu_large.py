@@ -14,7 +14,7 @@ import pytest
 
 import oracle as O
 import scenegen as sg
-from helpers import rms_inliers, state_rel_err
+from helpers import fp64_step_parity, rms_inliers
 
 pytestmark = pytest.mark.gpu
 
@@ -28,33 +28,19 @@ def ba():
     return m
 
 
-def _step_parity(ba, scene, iters):
-    P, S = O.Problem(scene), O.State(scene)
-    with ba.Context(precision=ba.BA_FP64) as ctx:
-        cid = ctx.create_cluster(scene)
-        assert ctx.cluster_info(cid)["n_free"] > 32
-        for it in range(iters):
-            io = O.lm_step(P, S)
-            ig = ctx.solve_step(cid)
-            R, T, X = ctx.get_state(cid)
-            assert ig["F_before"] == pytest.approx(io["F"], rel=TOL_STEP)
-            if abs(io["F"] - io["F_new"]) <= 1e-10 * abs(io["F"]) or abs(io["gain"]) < 1e-8:
-                break  # converged to rounding level: the decision is not determined in binary64
-            assert ig["accepted"] == io["accepted"], (it, ig, io)
-            assert ig["F_after"] == pytest.approx(io["F_new"], rel=TOL_STEP)
-            assert ig["mu"] == pytest.approx(io["mu"], rel=1e-9)
-            e = state_rel_err(R, T, X, S.R, S.T, S.X)
-            assert e < TOL_STEP, (it, e)
+def _step_parity(ba, scene, iters, min_steps):
+    n = fp64_step_parity(ba, O, scene, iters, TOL_STEP, min_free=33)
+    assert n >= min_steps, (n, min_steps)
 
 
 def test_fp64_step_parity_40_images(ba):
     """4 strips x 10 images, two of them fixed, priors on: n = 228."""
-    _step_parity(ba, sg.tiny_cluster(5151, 4, 10, 3000, fixed=(0, 11)), 8)
+    _step_parity(ba, sg.tiny_cluster(5151, 4, 10, 3000, fixed=(0, 11)), 8, min_steps=8)
 
 
 def test_fp64_step_parity_large_block(ba):
     """10 strips x 40 images (n = 2400), 300,000 points, two steps."""
-    _step_parity(ba, sg.cluster_c5(n_points=300_000), 2)
+    _step_parity(ba, sg.cluster_c5(n_points=300_000), 2, min_steps=2)
 
 
 def test_mixed_against_oracle_48_images(ba):

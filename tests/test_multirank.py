@@ -76,3 +76,23 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_reference_arm_prints_its_line_on_rank_zero():
+    """The reference arm (the FP64 oracle timed on the host cores) on rank 0
+    of a one-rank job prints one JSON line with the value, the cores it used
+    and an end-to-end figure without device copies."""
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0", CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--clusters", "2",
+                        "--steps", "1", "--warmup", "0", "--iters", "2"], env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.strip().splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    o = json.loads(lines[0])
+    assert o["impl"] == "reference" and o["value"] > 0 and o["unit"] == "obs/s"
+    assert o["cpu_baseline"]["kind"] == "oracle" and o["cpu_baseline"]["cores"] >= 1
+    assert o["cpu_baseline"]["value"] == o["value"]
+    assert o["e2e"]["value"] == o["value"]
+    assert o["e2e"]["h2d_bytes_per_step"] == 0 and o["e2e"]["d2h_bytes_per_step"] == 0
+    assert o["config"]["global_batch"] == 2 and o["steps"] == 1 and o["warmup"] == 0

@@ -5,9 +5,11 @@ flight software that reserves its memory at start-up, or a process whose
 device memory belongs to another allocator) evaluate the robust cost F(x)
 through ba_cost_noalloc, whose scratch is a fixed array inside the library.
 This test calls it through the C ABI with device arrays and checks it
-against the cost that ba_linearize reports for the same cluster, on two
-calls in a row (a large problem, then a smaller one, so that the second call
-reuses scratch the first call left behind).
+against the cost that ba_linearize reports for the same cluster and against
+the CPU oracle's cost at the same state, on two calls in a row (a large
+problem, then a smaller one, so that the second call reuses scratch the
+first call left behind); an observation whose point index is out of range
+must give NaN, not a fault.
 
 It lives in a file of its own, collected last, and passes both alone in a
 fresh process and after the other tests.
@@ -17,6 +19,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle as O
 import scenegen as sg
 
 pytestmark = pytest.mark.gpu
@@ -63,14 +66,15 @@ def test_cost_noalloc_matches_linearize_on_two_calls():
     import paper_2511_06152_gb300 as ba
     L = ba.lib()
     scenes = [sg.cluster_c2(fixed=(3,)), sg.cluster_c1()]  # ~230k then ~7k observations
-    refs = []
+    refs, orcs = [], []
     with ba.Context(precision=ba.BA_FP64) as ctx:
         for s in scenes:
             refs.append(ctx.linearize(ctx.create_cluster(s))["cost"])
+            orcs.append(O.cost(O.Problem(s), s["R0"], s["T0"], s["X0"]))
     stream = torch.cuda.Stream()
     out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
     keep = []
-    for s, ref in zip(scenes, refs):
+    for s, ref, orc in zip(scenes, refs, orcs):
         d = _device_desc(ba, torch, s, keep)
         torch.cuda.synchronize()
         st = L.ba_cost_noalloc(ctypes.byref(d), ctypes.c_void_p(stream.cuda_stream),
@@ -79,6 +83,28 @@ def test_cost_noalloc_matches_linearize_on_two_calls():
         stream.synchronize()
         got = float(out.item())
         assert got == pytest.approx(ref, rel=TOL), (got, ref)
+        assert got == pytest.approx(orc, rel=TOL), (got, orc)
+
+
+def test_cost_noalloc_out_of_range_index_gives_nan():
+    """Indices are not checked on the host; the kernel skips the bad
+    observation's reads and the cost comes out NaN."""
+    torch = pytest.importorskip("torch")
+    import paper_2511_06152_gb300 as ba
+    L = ba.lib()
+    s = sg.cluster_c1()
+    s = dict(s, obs_pt=np.array(s["obs_pt"], dtype=np.int32).copy())
+    s["obs_pt"][len(s["obs_pt"]) // 2] = int(s["n_pts"])  # one past the last point
+    keep = []
+    d = _device_desc(ba, torch, s, keep)
+    out = torch.zeros((1,), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    st = L.ba_cost_noalloc(ctypes.byref(d), ctypes.c_void_p(stream.cuda_stream),
+                           ctypes.cast(out.data_ptr(), ctypes.POINTER(ctypes.c_double)))
+    assert st == ba.BA_OK
+    stream.synchronize()
+    assert np.isnan(float(out.item()))
 
 
 def test_cost_noalloc_rejects_sizes_beyond_its_scratch():
