@@ -103,6 +103,13 @@ typedef struct {
  * clusters of its chunks get BA_ERR_TIMEOUT in their step status and the
  * step is rejected; nothing faults or hangs).  No effect in BA_FP64. */
 #define BA_FLAG_INJECT_COPY_TIMEOUT 2
+/* Reduced camera systems of more than 32 free images are factored on the
+ * tensor cores by default: the factor kept as double-float (binary32 pairs),
+ * its dense products computed exactly from 8-bit digit matrices on the bf16
+ * tensor cores (Ozaki's error-free splitting), the solution refined against
+ * S in binary64.  This flag selects the binary64 CUDA-core factorisation
+ * instead (same envelope, same refinement), for comparisons. */
+#define BA_FLAG_BIG_FP64_FACTOR 4
 
 /* Kernel kinds reported by ba_kernel_stats, in this order. */
 #define BA_KERNEL_LIN_SCHUR 0      /* per chunk: residuals, Jacobians, point blocks, Schur partial sums */
@@ -239,7 +246,9 @@ BA_API ba_status ba_presort_host(const ba_cluster_desc* d, int32_t precision, in
  * points).  cam_map[dst n_cams] / pt_map[dst n_pts] (host arrays) give, for
  * each camera / point of dst, its index in src or -1.  The current state of
  * the mapped cameras and points of src is copied on the device into dst
- * (also into the state ba_reset restores).  Neither cluster may be queued or
+ * (also into the state ba_reset restores), and so is src's damping state:
+ * dst starts from src's current mu and nu (the LM state stays resident on
+ * the device from one window to the next), which ba_reset also restores.  Neither cluster may be queued or
  * running in the serving scheduler.  Enqueued on the context's stream; this
  * split from ba_create_cluster lets a caller presort a window while the
  * previous one is still being solved. */
@@ -359,7 +368,8 @@ BA_API ba_status ba_solve_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n
                          ba_result* results, ba_step_info* trace);
 
 /* Restore a cluster's initial state (the one given at create, or the one a
- * warm start wrote), its damping and LM counters.  Enqueued on the context's
+ * warm start wrote), its initial damping (mu0 and nu = 2 from create, or the
+ * mu and nu a warm start carried over) and clear its LM counters.  Enqueued on the context's
  * stream.  BA_ERR_NOT_FOUND for an unknown id, BA_ERR_INVALID for a cluster
  * in service. */
 BA_API ba_status ba_reset(ba_ctx* ctx, ba_cluster_id id);

@@ -111,6 +111,7 @@ struct ba_ctx {
   int attr_max_n = 0;
   bool timing = false;
   int inject = 0;  // failure-injection bits for the kernels (BA_FLAG_INJECT_*)
+  bool big_fp64 = false;  // global-memory solver: binary64 CUDA-core factor instead of the tensor-core one
   std::mutex stats_mu;  // kernel statistics (API threads and the scheduler)
   // pinned host staging buffers of cluster creation, reused across calls (one
   // per concurrent creation; taken and returned under stage_mu)
@@ -329,7 +330,7 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
   for (int i = 0; i < n; ++i) {
     Cluster* c = find_cluster(ctx, ids[i]);
     if (c->nf > kMaxFreeSmall)
-      p->big.push_back(BigRef{c->d_desc, 6 * c->nf, c->nf, c->h.n_pairs, c->h.S, c->h.F, c->big_below});
+      p->big.push_back(BigRef{c->d_desc, 6 * c->nf, c->nf, c->h.n_pairs, c->h.S, c->h.F, c->big_below, !ctx->big_fp64});
   }
   pre.push_back(pre[n]);  // totals, read by the kernels
   pre.push_back(pre[(n + 1) + n]);
@@ -1418,6 +1419,10 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
   const size_t o_desc = Lo.add(sizeof(DevCluster));
   const size_t o_F = Lo.add(big ? sizeof(double) * (size_t)n * n : 0);
   const size_t o_bx = Lo.add(big ? sizeof(double) * 4 * (size_t)n : 0);
+  const int dig_rows = big ? big_dig_rows(n) : 0;
+  const size_t o_dig = Lo.add(big ? (size_t)kSlicesHost * dig_rows * 32 * sizeof(uint16_t) : 0);
+  const size_t o_dexp = Lo.add(big ? sizeof(int) * (size_t)dig_rows : 0);
+  const size_t o_linv = Lo.add(big ? sizeof(float) * 2 * kBigNB * kBigNB * (size_t)((n + kBigNB - 1) / kBigNB) : 0);
   const size_t total = Lo.off;
 
   // a pinned staging buffer of the context (every byte the kernels read is
@@ -1530,6 +1535,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
     lm.mu = lm.mu0;
     lm.mu_f = (float)lm.mu0;
     lm.nu = 2.0;
+    lm.nu0 = 2.0;
     put(o_lm, &lm, sizeof(lm));
   }
   if (big) {
@@ -1602,6 +1608,10 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
   h.F = big ? (double*)(arena + o_F) : nullptr;
   h.bx = big ? (double*)(arena + o_bx) : nullptr;
   h.bflag = big ? (int*)(arena + o_bflag) : nullptr;
+  h.dig = big ? (unsigned short*)(arena + o_dig) : nullptr;
+  h.dexp = big ? (int*)(arena + o_dexp) : nullptr;
+  h.linv = big ? (float*)(arena + o_linv) : nullptr;
+  h.dig_groups = dig_rows / 8;
   h.camreal = mixed ? nullptr : arena + o_camreal;
   h.camdf = mixed ? (float*)(arena + o_camdf) : nullptr;
   h.tiles = (const Tile*)(arena + o_tiles);
@@ -1683,14 +1693,17 @@ ba_status warm_copy(ba_ctx* ctx, Cluster* c, Cluster* src, const int32_t* cam_ma
     const int mu_ = pt_map[ju];
     if (mu_ >= 0 && mu_ < src->np) pairs.push_back(make_int2(c->pt_inv[ju], src->pt_inv[mu_]));
   }
-  if (pairs.empty()) return BA_OK;
+  // the kernel also carries the damping (mu, nu) over, so it runs even when
+  // no camera or point is shared
   int2* dp = nullptr;
-  CUDA_TRY(ctx, cudaMallocAsync((void**)&dp, sizeof(int2) * pairs.size(), ctx->stream));
-  CUDA_TRY(ctx, cudaMemcpyAsync(dp, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice, ctx->stream));
-  launch_warm_copy(c->d_desc, src->d_desc, dp, n_cam_pairs, dp + n_cam_pairs, (int)pairs.size() - n_cam_pairs,
-                   ctx->stream);
+  if (!pairs.empty()) {
+    CUDA_TRY(ctx, cudaMallocAsync((void**)&dp, sizeof(int2) * pairs.size(), ctx->stream));
+    CUDA_TRY(ctx, cudaMemcpyAsync(dp, pairs.data(), sizeof(int2) * pairs.size(), cudaMemcpyHostToDevice, ctx->stream));
+  }
+  launch_warm_copy(c->d_desc, src->d_desc, dp, n_cam_pairs, dp ? dp + n_cam_pairs : nullptr,
+                   (int)pairs.size() - n_cam_pairs, ctx->stream);
   note_direct(ctx);
-  CUDA_TRY(ctx, cudaFreeAsync(dp, ctx->stream));
+  if (dp) CUDA_TRY(ctx, cudaFreeAsync(dp, ctx->stream));
   return BA_OK;
 }
 
@@ -1941,6 +1954,7 @@ BA_API ba_status ba_init(ba_ctx** out, const ba_config* cfg) {
   ctx->refine = cfg->refine_steps >= 0 ? cfg->refine_steps : 1;
   ctx->timing = (cfg->flags & BA_FLAG_KERNEL_TIMING) != 0;
   ctx->inject = (cfg->flags & BA_FLAG_INJECT_COPY_TIMEOUT) ? kInjectCopyTimeout : 0;
+  ctx->big_fp64 = (cfg->flags & BA_FLAG_BIG_FP64_FACTOR) != 0;
   if (cfg->stream) {
     ctx->stream = (cudaStream_t)cfg->stream;
   } else {

@@ -1,20 +1,39 @@
 // Reduced camera systems larger than one CTA's shared memory holds (more than
 // kMaxFreeSmall free images, n = 6 n_free > 192; the 400-image large block
-// has n = 2400), solved in binary64 in global memory.  Same system, order and
-// algorithm as the shared-memory solver of ba_kernels.cu: S assembled in the
-// reverse Cuthill-McKee elimination order, Cholesky restricted to the
-// envelope of S (no fill outside it), a solve, one refinement step against S.
+// has n = 2400), solved in global memory.  Same system and elimination order
+// as the shared-memory solver of ba_kernels.cu: S assembled in binary64 in
+// the reverse Cuthill-McKee order, Cholesky restricted to the envelope of S
+// (no fill outside it), a solve, refinement steps against S in binary64.
 //
 //   k_big_prior   per free image: priors, damping D, g_c, rhs, diagonal block
 //   k_big_pairs   off-diagonal blocks of S from the co-visible pairs' sums
-//   (F = S)
+//
+// Factorisation on the tensor cores (default).  GB300 runs binary64 at about
+// 1/59 of its binary32 rate, so the factor is kept as double-float (binary32
+// pairs, ~48 bits) and its dense products run on the tcgen05 tensor cores as
+// exact products of 8-bit digit matrices (ba_tc.cuh):
+//   k_big_split      S -> F (lower triangle, double-float, zeros outside the envelope)
 //   per block column k of kBigNB columns (right-looking):
+//     k_big_panel      every CTA factors the diagonal block and inverts it
+//                      (double-float); CTA 0 stores both, CTA b stores the
+//                      panel L_ik = A_ik L_kk^-T of row block k + b and its
+//                      Ozaki digits
+//     k_big_update_tc  A_ij -= L_ik L_jk^T on 128 x 32 tiles inside the
+//                      envelope: digit products on the tensor cores,
+//                      double-float subtraction
+//   k_big_solve_df   forward and backward substitution (one CTA, double-float,
+//                    the inverted diagonal blocks and the panels)
+//   k_big_resid      t = rhs - S x in binary64
+//   k_big_finish     dc, candidate poses, pred and prior terms, status
+//
+// Binary64 factorisation on the CUDA cores (BA_FLAG_BIG_FP64_FACTOR):
+//   (F = S)
+//   per block column k:
 //     k_big_diag    factor the diagonal block (one CTA)
 //     k_big_trsm    L_ik = A_ik L_kk^-T for the row blocks inside the envelope
 //     k_big_update  A_ij -= L_ik L_jk^T for the tiles inside the envelope
 //   k_big_solve   forward and backward substitution (one CTA)
-//   k_big_resid   t = rhs - S x
-//   k_big_finish  dc, candidate poses, pred and prior terms, status
+//   k_big_resid, k_big_finish
 //
 // The envelope is non-decreasing: row r's first nonzero column is
 // ef(r) = 6 env_first[r / 6]; the rows of a column block that can be nonzero
@@ -22,9 +41,12 @@
 // column the host passes in (it fixes the grid sizes).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "ba_camera.cuh"
 #include "ba_device.cuh"
 #include "ba_internal.h"
+#include "ba_tc.cuh"
 
 namespace bagpu {
 
@@ -342,6 +364,449 @@ __global__ void __launch_bounds__(512) k_big_finish(const DevCluster* dcl) {
   }
 }
 
+// ------------------------------------------------------------------ tensor-core factorisation
+
+__device__ __forceinline__ float* df_hi(const DevCluster& C) { return reinterpret_cast<float*>(C.F); }
+__device__ __forceinline__ float* df_lo(const DevCluster& C) {
+  const int n = 6 * C.n_free;
+  return reinterpret_cast<float*>(C.F) + (size_t)n * n;
+}
+
+// F = S on the lower triangle as double-float (entries outside the envelope
+// are zero in S and become zero here), one CTA per row.
+__global__ void __launch_bounds__(256) k_big_split(const DevCluster* dcl) {
+  const DevCluster& C = *dcl;
+  const int n = 6 * C.n_free;
+  float* Fh = df_hi(C);
+  float* Fl = df_lo(C);
+  for (int r = blockIdx.x; r < n; r += gridDim.x) {
+    const double* srow = C.S + (size_t)r * n;
+    for (int c = threadIdx.x; c <= r; c += blockDim.x) {
+      const double v = srow[c];
+      float h = 0.0f, l = 0.0f;
+      if (v != 0.0) {
+        h = __double2float_rn(v);
+        l = __double2float_rn(v - (double)h);
+      }
+      Fh[(size_t)r * n + c] = h;
+      Fl[(size_t)r * n + c] = l;
+    }
+  }
+}
+
+constexpr int kPanelThreads = 1024;
+constexpr int kPanelW = 4;  // columns a warp factors between two block-wide barriers
+constexpr int kPld = kBigNB + 1;  // padded leading dimension of the shared blocks
+
+// Block column k: the diagonal block factored and inverted by every CTA
+// (double-float; rows past n padded with the identity), then CTA 0 stores
+// the factor and the inverse, CTA b (1 <= b <= m) the panel of row block
+// k + b, L_ik = A_ik (L_kk^-1)^T, and its Ozaki digits and row scales.
+//
+// The factor and its inverse come out of one right-looking sweep: W starts
+// as the identity and receives the same row operations as the matrix, so
+// that row j of W, scaled by 1 / L(j, j) once the column j is final, is row
+// j of L^-1 (forward substitution of L X = I, one row at a time).  Columns
+// go in blocks of kPanelW: one warp factors a block (the pivots' reciprocal
+// square roots, the block's columns of L, its rows of X) with warp-level
+// synchronisation only, then the whole CTA applies the block's rank-kPanelW
+// update below it: two block-wide barriers per block.
+__global__ void __launch_bounds__(kPanelThreads) k_big_panel(const DevCluster* dcl, int k) {
+  const DevCluster& C = *dcl;
+  const int n = 6 * C.n_free, r0 = kBigNB * k, nb = min(kBigNB, n - r0);
+  float* Fh = df_hi(C);
+  float* Fl = df_lo(C);
+  __shared__ float Lh[kBigNB][kPld], Ll[kBigNB][kPld];  // factor
+  __shared__ float Wh[kBigNB][kPld], Wl[kBigNB][kPld];  // identity -> inverse of the factor
+  __shared__ float Ph[kBigNB][kPld], Pl[kBigNB][kPld];  // A_ik
+  const int tid = threadIdx.x;
+  const int b = blockIdx.x;
+  const int ri = r0 + kBigNB * b, nr = b == 0 ? nb : min(kBigNB, n - ri);
+  for (int idx = tid; idx < kBigNB * kBigNB; idx += kPanelThreads) {
+    const int r = idx >> 5, c = idx & 31;
+    float h = 0.0f, l = 0.0f;
+    if (r < nb && c < nb) {
+      if (c <= r) {
+        h = Fh[(size_t)(r0 + r) * n + r0 + c];
+        l = Fl[(size_t)(r0 + r) * n + r0 + c];
+      }
+    } else if (r == c) {
+      h = 1.0f;
+    }
+    Lh[r][c] = h;
+    Ll[r][c] = l;
+    Wh[r][c] = r == c ? 1.0f : 0.0f;
+    Wl[r][c] = 0.0f;
+    if (b > 0) {
+      float ph = 0.0f, pl = 0.0f;
+      if (r < nr && c < nb) {
+        ph = Fh[(size_t)(ri + r) * n + r0 + c];
+        pl = Fl[(size_t)(ri + r) * n + r0 + c];
+      }
+      Ph[r][c] = ph;
+      Pl[r][c] = pl;
+    }
+  }
+  __shared__ float Dh[kBigNB], Dl[kBigNB];  // L(j, j), kept apart until the sweep ends
+  __syncthreads();
+  bool fail = false;
+  // blocks of kPanelW columns: warp 0 factors the block's columns (lane =
+  // row, warp-level synchronisation only) and finishes the block's rows of
+  // X; then every thread applies the block's rank-kPanelW update to the rows
+  // below it (entry (tr, tc) of the trailing matrix, or of W left of it)
+  const int tr = tid >> 5, tc = tid & 31, lane = tid & 31;
+  for (int jb = 0; jb < kBigNB; jb += kPanelW) {
+    const int je = jb + kPanelW - 1;  // last column of the block
+    if (tid < 32) {
+      for (int j = jb; j <= je; ++j) {
+        dfl d{Lh[j][j], Ll[j][j]};
+        if (!(d.hi > 0.0f)) {
+          fail = true;
+          d = dfl{1.0f, 0.0f};
+        }
+        const dfl iv = df_rsqrt(d);
+        if (lane > j) {
+          const dfl v = df_mul(dfl{Lh[lane][j], Ll[lane][j]}, iv);
+          Lh[lane][j] = v.hi;
+          Ll[lane][j] = v.lo;
+        } else {
+          if (lane == j) {
+            const dfl sq = df_mul(d, iv);
+            Dh[j] = sq.hi;
+            Dl[j] = sq.lo;
+          }
+          const dfl x = df_mul(dfl{Wh[j][lane], Wl[j][lane]}, iv);  // row j of X
+          Wh[j][lane] = x.hi;
+          Wl[j][lane] = x.lo;
+        }
+        __syncwarp();
+        if (lane > j) {  // the block's later columns, rows below j
+          const dfl lr{Lh[lane][j], Ll[lane][j]};
+          for (int c = j + 1; c <= je && c <= lane; ++c) {
+            const dfl a = df_fms(dfl{Lh[lane][c], Ll[lane][c]}, lr, dfl{Lh[c][j], Ll[c][j]});
+            Lh[lane][c] = a.hi;
+            Ll[lane][c] = a.lo;
+          }
+        }
+        if (lane <= j) {  // the block's later rows of W, column lane
+          const dfl xj{Wh[j][lane], Wl[j][lane]};
+          for (int r = j + 1; r <= je; ++r) {
+            const dfl a = df_fms(dfl{Wh[r][lane], Wl[r][lane]}, dfl{Lh[r][j], Ll[r][j]}, xj);
+            Wh[r][lane] = a.hi;
+            Wl[r][lane] = a.lo;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    if (tr > je && tc <= tr) {
+      if (tc <= je) {  // W(tr, tc) -= sum_j L(tr, j) X(j, tc) over the block's columns
+        dfl a{Wh[tr][tc], Wl[tr][tc]};
+#pragma unroll
+        for (int i = 0; i < kPanelW; ++i) {
+          const int j = jb + i;
+          if (j >= tc) a = df_fms(a, dfl{Lh[tr][j], Ll[tr][j]}, dfl{Wh[j][tc], Wl[j][tc]});
+        }
+        Wh[tr][tc] = a.hi;
+        Wl[tr][tc] = a.lo;
+      } else {  // L(tr, tc) -= sum_j L(tr, j) L(tc, j)
+        dfl a{Lh[tr][tc], Ll[tr][tc]};
+#pragma unroll
+        for (int i = 0; i < kPanelW; ++i) a = df_fms(a, dfl{Lh[tr][jb + i], Ll[tr][jb + i]}, dfl{Lh[tc][jb + i], Ll[tc][jb + i]});
+        Lh[tr][tc] = a.hi;
+        Ll[tr][tc] = a.lo;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid < kBigNB) {
+    Lh[tid][tid] = Dh[tid];
+    Ll[tid][tid] = Dl[tid];
+  }
+  __syncthreads();
+  if (b == 0) {
+    if (tid == 0 && fail) *C.bflag = 1;
+    float* lv = C.linv + (size_t)k * 2 * kBigNB * kBigNB;
+    for (int idx = tid; idx < kBigNB * kBigNB; idx += kPanelThreads) {
+      const int r = idx >> 5, c = idx & 31;
+      lv[idx] = Wh[r][c];
+      lv[kBigNB * kBigNB + idx] = Wl[r][c];
+      if (r < nb && c <= r) {
+        Fh[(size_t)(r0 + r) * n + r0 + c] = Lh[r][c];
+        Fl[(size_t)(r0 + r) * n + r0 + c] = Ll[r][c];
+      }
+    }
+    return;
+  }
+  // the panel: L_ik(r, c) = sum_{q <= c} A_ik(r, q) X(c, q), thread (r, c)
+  const int r = tid >> 5, c = tid & 31;
+  Dot2 acc;
+  for (int q = 0; q <= c; ++q) acc.add(dfl{Ph[r][q], Pl[r][q]}, dfl{Wh[c][q], Wl[c][q]});
+  const dfl out = acc.get();
+  int E = df_exp_bound(out.hi);
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) E = max(E, __shfl_xor_sync(BA_FULL_MASK, E, off));
+  const int row = ri + r;  // < big_dig_rows(n): ri < n and rows of a block column are padded to kBigNB
+  const size_t slice = (size_t)C.dig_groups * (kGroupBytes / 2);  // uint16 per digit matrix
+  const bool live = r < nr && c < nb;
+  if (live) {
+    Fh[(size_t)row * n + r0 + c] = out.hi;
+    Fl[(size_t)row * n + r0 + c] = out.lo;
+  }
+  uint16_t dg[kSlices];
+  df_digits(live ? out : dfl{0.0f, 0.0f}, E, dg);
+  const size_t off = canon_off(row, c) / 2;
+#pragma unroll
+  for (int t = 0; t < kSlices; ++t) C.dig[(size_t)t * slice + off] = dg[t];
+  if (c == 0) C.dexp[row] = E;
+}
+
+constexpr int kUpdThreads = 512;  // 16 warps: 4 per tensor-memory lane quarter, 8 columns each
+constexpr int kUpdM = 128, kUpdN = 32;
+constexpr uint32_t kUpdA = kUpdM / 8 * kGroupBytes;  // bytes of one digit matrix of the 128-row operand
+constexpr uint32_t kUpdB = kUpdN / 8 * kGroupBytes;  // of the 32-row operand
+constexpr uint32_t kUpdTmemCols = 256;               // kDiags accumulators of kUpdN columns
+constexpr size_t kUpdOperandBytes = (size_t)kSlices * (kUpdA + kUpdB);
+// Dynamic shared memory requested per CTA: more than a third of the SM's
+// 228 KB, so that at most two CTAs share an SM and their tensor-memory
+// allocations (2 x 256 of the 512 columns) always succeed at once.
+constexpr size_t kUpdSmem = 96 * 1024;
+static_assert(kUpdOperandBytes + 256 <= kUpdSmem && 3 * kUpdSmem > 228 * 1024, "update kernel shared memory");
+static_assert(kDiags * kUpdN <= (int)kUpdTmemCols, "accumulators fit the allocation");
+constexpr uint64_t kTcWaitNs = 200000000ull;  // give up on a copy or the products after 200 ms
+
+// Block column k, m row blocks below it: tile (column block jb, row group
+// rg) holds rows [R0 + 128 rg, + 128) x columns [R0 + 32 jb, + 32) of the
+// trailing matrix, R0 = 32 (k + 1).  A_ij -= L_ik L_jk^T by the digit
+// products on the tensor cores (accumulators in tensor memory), combined
+// per entry in double-float and subtracted from the factor.
+__global__ void __launch_bounds__(kUpdThreads, 1) k_big_update_tc(const DevCluster* dcl, int k, int m) {
+  const DevCluster& C = *dcl;
+  const int n = 6 * C.n_free;
+  const int R0 = kBigNB * (k + 1), band_end = min(n, R0 + kBigNB * m);
+  const int jb = blockIdx.x, rg = blockIdx.y;
+  const int rA = R0 + kUpdM * rg, cB = R0 + kUpdN * jb;
+  if (rA >= band_end || rA + kUpdM - 1 < cB) return;  // past the band, or above the diagonal
+  extern __shared__ __align__(1024) unsigned char smu[];
+  unsigned char* sa = smu;
+  unsigned char* sb = smu + (size_t)kSlices * kUpdA;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smu + kUpdOperandBytes);  // [0] copies, [1] products
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(bars + 2);
+  int* s_ok = reinterpret_cast<int*>(s_tmem + 1);
+  int* s_ecol = s_ok + 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) tmem_alloc(s_tmem, kUpdTmemCols);
+  if (tid < kUpdN) s_ecol[tid] = C.dexp[cB + tid];
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  const size_t slice_bytes = (size_t)C.dig_groups * kGroupBytes;
+  const unsigned char* dig = reinterpret_cast<const unsigned char*>(C.dig);
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&bars[0], (uint32_t)kUpdOperandBytes);
+    for (int t = 0; t < kSlices; ++t) {
+      bulk_copy_g2s(sa + (size_t)t * kUpdA, dig + t * slice_bytes + (size_t)(rA / 8) * kGroupBytes, kUpdA, &bars[0]);
+      bulk_copy_g2s(sb + (size_t)t * kUpdB, dig + t * slice_bytes + (size_t)(cB / 8) * kGroupBytes, kUpdB, &bars[0]);
+    }
+    int ok = mbar_wait_bounded(&bars[0], 0, kTcWaitNs) ? 1 : 0;
+    if (ok) {
+      issue_digit_products<kUpdM, kUpdN>(tmem, smem_u32(sa), kUpdA, smem_u32(sb), kUpdB);
+      mma_commit(&bars[1]);
+      ok = mbar_wait_bounded(&bars[1], 0, kTcWaitNs) ? 1 : 0;
+      if (!ok) mbar_wait_bounded(&bars[1], 0, kTcWaitNs);  // the products still running, once more
+    } else {
+      mbar_wait_bounded(&bars[0], 0, kTcWaitNs);  // the copies in flight, once more
+    }
+    *s_ok = ok;
+    if (!ok) C.lm->dev_error = kDevErrTimeout;
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (*s_ok) {
+    // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (rows) and columns
+    // 8 (w / 4) .. + 7 of every accumulator
+    const int quarter = warp & 3, cb = 8 * (warp >> 2);
+    const int row = rA + 32 * quarter + lane;
+    const bool live = row < band_end;
+    const int er = live ? C.dexp[row] : 0;
+    float* Fh = df_hi(C);
+    float* Fl = df_lo(C);
+    const size_t o0 = (size_t)row * n + cB + cb;
+    const int ncol = live ? min(8, row - (cB + cb) + 1) : 0;  // columns on or left of the diagonal
+    float fh[8], fl[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      fh[i] = i < ncol ? Fh[o0 + i] : 0.0f;
+      fl[i] = i < ncol ? Fl[o0 + i] : 0.0f;
+    }
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    float acc[kDiags][8];
+#pragma unroll
+    for (int c = 0; c < kDiags; ++c) tmem_ld8(lane_base + (uint32_t)(c * kUpdN + cb), acc[c]);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      float a[kDiags];
+#pragma unroll
+      for (int c = 0; c < kDiags; ++c) a[c] = acc[c][i];
+      const dfl v = df_ldexp(combine_diags(a), er + s_ecol[cb + i]);
+      const dfl f = df_sub(dfl{fh[i], fl[i]}, v);
+      if (i < ncol) {
+        Fh[o0 + i] = f.hi;
+        Fl[o0 + i] = f.lo;
+      }
+    }
+  }
+  (void)lane;
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, kUpdTmemCols);
+}
+
+// Dot2 partial sums of a warp (or of aligned groups of `width` lanes)
+// merged by a butterfly: every lane ends with the group's total.
+__device__ __forceinline__ Dot2 warp_merge(Dot2 d, int width) {
+  for (int off = 1; off < width; off <<= 1)
+    d.merge(__shfl_xor_sync(BA_FULL_MASK, d.s, off), __shfl_xor_sync(BA_FULL_MASK, d.c, off));
+  return d;
+}
+
+size_t big_solve_df_smem(int n) { return sizeof(float) * (2 * (size_t)n + 2 * kBigNB); }
+
+constexpr int kSolveChunk = 12;  // entries a lane loads before it sums them
+
+// Solve S y = v with the double-float factor (one CTA of 1024 threads; v in
+// shared memory).  Both sweeps read, per block k of 32 rows, the rows' own
+// entries left of the diagonal block, L(r0 + r, lo .. r0), lo = the block's
+// first envelope column (contiguous in memory: coalesced across a warp), and
+// the inverted diagonal block X = L_kk^-1 (loaded one block ahead).
+//   forward  (k ascending):  u = v_k - L(k, lo .. r0) v(lo .. r0); v_k = X u
+//   backward (k descending): x_k = X^T v_k; v(lo .. r0) -= L(k, lo .. r0)^T x_k
+// Every dot product is compensated (Dot2); each lane issues its loads in
+// groups of kSolveChunk before it sums them.  x = S^-1 rhs (mode 0) or
+// x += S^-1 t (mode 1), binary64 in and out.
+__global__ void __launch_bounds__(1024) k_big_solve_df(const DevCluster* dcl, int mode) {
+  const DevCluster& C = *dcl;
+  extern __shared__ float sv[];
+  const int n = 6 * C.n_free, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  float* vh = sv;
+  float* vl = sv + n;
+  float* yh = sv + 2 * n;
+  float* yl = yh + kBigNB;
+  const float* Fh = df_hi(C);
+  const float* Fl = df_lo(C);
+  const double* src = mode == 0 ? C.rhs : C.bx + 2 * n;
+  for (int i = tid; i < n; i += blockDim.x) {
+    const dfl v = df_from_d(src[i]);
+    vh[i] = v.hi;
+    vl[i] = v.lo;
+  }
+  const int nblk = (n + kBigNB - 1) / kBigNB;
+  const size_t xs = 2 * kBigNB * kBigNB;
+  // this thread's entry of X: (wid, lane) in the forward sweep, (lane, wid) in the backward one
+  float xh = C.linv[wid * kBigNB + lane], xl = C.linv[kBigNB * kBigNB + wid * kBigNB + lane];
+  __syncthreads();
+  for (int k = 0; k < nblk; ++k) {  // L y = v
+    const int r0 = kBigNB * k, nb = min(kBigNB, n - r0), lo = ef_row(C, r0);
+    const float cxh = xh, cxl = xl;
+    if (k + 1 < nblk) {
+      xh = C.linv[(k + 1) * xs + wid * kBigNB + lane];
+      xl = C.linv[(k + 1) * xs + kBigNB * kBigNB + wid * kBigNB + lane];
+    }
+    if (wid < nb) {  // warp r: u_r = v_r - sum_j L(r0 + r, j) v_j
+      const size_t ro = (size_t)(r0 + wid) * n;
+      Dot2 acc;
+      for (int base = lo; base < r0; base += 32 * kSolveChunk) {
+        float ah[kSolveChunk], al[kSolveChunk];
+#pragma unroll
+        for (int i = 0; i < kSolveChunk; ++i) {
+          const int j = base + lane + 32 * i;
+          ah[i] = j < r0 ? Fh[ro + j] : 0.0f;
+          al[i] = j < r0 ? Fl[ro + j] : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < kSolveChunk; ++i) {
+          const int j = base + lane + 32 * i;
+          if (j < r0) acc.add(dfl{ah[i], al[i]}, dfl{vh[j], vl[j]});
+        }
+      }
+      acc = warp_merge(acc, 32);
+      if (lane == 0) {
+        const dfl u = df_sub(dfl{vh[r0 + wid], vl[r0 + wid]}, acc.get());
+        yh[wid] = u.hi;
+        yl[wid] = u.lo;
+      }
+    }
+    __syncthreads();
+    {  // warp r: v_r = sum_q X(r, q) u_q
+      Dot2 acc;
+      if (lane < nb) acc.add(dfl{cxh, cxl}, dfl{yh[lane], yl[lane]});
+      acc = warp_merge(acc, 32);
+      if (lane == 0 && wid < nb) {
+        const dfl y = acc.get();
+        vh[r0 + wid] = y.hi;
+        vl[r0 + wid] = y.lo;
+      }
+    }
+    __syncthreads();
+  }
+  xh = C.linv[(nblk - 1) * xs + lane * kBigNB + wid];
+  xl = C.linv[(nblk - 1) * xs + kBigNB * kBigNB + lane * kBigNB + wid];
+  for (int k = nblk - 1; k >= 0; --k) {  // L^T x = y
+    const int r0 = kBigNB * k, nb = min(kBigNB, n - r0), lo = ef_row(C, r0);
+    {  // warp r: x_r = sum_q X(q, r) y_q
+      Dot2 acc;
+      if (lane < nb) acc.add(dfl{xh, xl}, dfl{vh[r0 + lane], vl[r0 + lane]});
+      acc = warp_merge(acc, 32);
+      if (lane == 0) {
+        const dfl x = acc.get();
+        yh[wid] = x.hi;
+        yl[wid] = x.lo;
+      }
+    }
+    if (k > 0) {
+      xh = C.linv[(k - 1) * xs + lane * kBigNB + wid];
+      xl = C.linv[(k - 1) * xs + kBigNB * kBigNB + lane * kBigNB + wid];
+    }
+    __syncthreads();
+    if (tid < nb) {
+      vh[r0 + tid] = yh[tid];
+      vl[r0 + tid] = yl[tid];
+    }
+    for (int j = lo + tid; j < r0; j += blockDim.x) {  // v_j -= sum_r L(r0 + r, j) x_r
+      Dot2 acc;
+      for (int q0 = 0; q0 < nb; q0 += kSolveChunk) {
+        float ah[kSolveChunk], al[kSolveChunk];
+#pragma unroll
+        for (int i = 0; i < kSolveChunk; ++i) {
+          const size_t o = (size_t)(r0 + q0 + i) * n + j;
+          ah[i] = q0 + i < nb ? Fh[o] : 0.0f;
+          al[i] = q0 + i < nb ? Fl[o] : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < kSolveChunk; ++i)
+          if (q0 + i < nb) acc.add(dfl{ah[i], al[i]}, dfl{yh[q0 + i], yl[q0 + i]});
+      }
+      const dfl v = df_sub(dfl{vh[j], vl[j]}, acc.get());
+      vh[j] = v.hi;
+      vl[j] = v.lo;
+    }
+    __syncthreads();
+  }
+  double* x = C.bx + n;
+  for (int i = tid; i < n; i += blockDim.x) {
+    const double v = (double)vh[i] + (double)vl[i];
+    x[i] = mode == 0 ? v : x[i] + v;
+  }
+}
+
 }  // namespace
 
 static int grid_for_big(int items, int per_block) {
@@ -358,21 +823,39 @@ void launch_big_solve(const BigRef& b, bool mixed, int refine_steps, int assembl
   LAUNCH(KK_FACTOR, st, k_big_prior<<<(b.nf + 63) / 64, 64, 0, st>>>(b.d));
   LAUNCH(KK_FACTOR, st, k_big_pairs<<<grid_for_big(b.n_pairs * 36, 256), 256, 0, st>>>(b.d));
   if (assemble_only) return;
-  cudaMemcpyAsync(b.F, b.S, nn * sizeof(double), cudaMemcpyDeviceToDevice, st);
   const int nblk = (n + kBigNB - 1) / kBigNB;
-  for (int k = 0; k < nblk; ++k) {
-    LAUNCH(KK_FACTOR, st, k_big_diag<<<1, 256, 0, st>>>(b.d, k));
-    const int m = b.below[k];
-    if (m > 0) {
-      LAUNCH(KK_FACTOR, st, k_big_trsm<<<m, 256, 0, st>>>(b.d, k));
-      LAUNCH(KK_FACTOR, st, k_big_update<<<m * (m + 1), 256, 0, st>>>(b.d, k));
+  if (b.tc) {
+    LAUNCH(KK_FACTOR, st, k_big_split<<<std::min(n, num_sms() * 8), 256, 0, st>>>(b.d));
+    for (int k = 0; k < nblk; ++k) {
+      const int m = b.below[k];
+      LAUNCH(KK_FACTOR, st, k_big_panel<<<1 + m, kPanelThreads, 0, st>>>(b.d, k));
+      if (m > 0) {
+        const dim3 grid(m, (kBigNB * m + kUpdM - 1) / kUpdM);
+        LAUNCH(KK_FACTOR, st, k_big_update_tc<<<grid, kUpdThreads, kUpdSmem, st>>>(b.d, k, m));
+      }
     }
-  }
-  const size_t sm = big_solve_smem(n);
-  LAUNCH(KK_FACTOR, st, k_big_solve<<<1, 1024, sm, st>>>(b.d, 0));
-  for (int it = 0; it < refine_steps; ++it) {
-    LAUNCH(KK_FACTOR, st, k_big_resid<<<grid_for_big(n * 32, 256), 256, 0, st>>>(b.d));
-    LAUNCH(KK_FACTOR, st, k_big_solve<<<1, 1024, sm, st>>>(b.d, 1));
+    const size_t sm = big_solve_df_smem(n);
+    LAUNCH(KK_FACTOR, st, k_big_solve_df<<<1, 1024, sm, st>>>(b.d, 0));
+    for (int it = 0; it < refine_steps; ++it) {
+      LAUNCH(KK_FACTOR, st, k_big_resid<<<grid_for_big(n * 32, 256), 256, 0, st>>>(b.d));
+      LAUNCH(KK_FACTOR, st, k_big_solve_df<<<1, 1024, sm, st>>>(b.d, 1));
+    }
+  } else {
+    cudaMemcpyAsync(b.F, b.S, nn * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    for (int k = 0; k < nblk; ++k) {
+      LAUNCH(KK_FACTOR, st, k_big_diag<<<1, 256, 0, st>>>(b.d, k));
+      const int m = b.below[k];
+      if (m > 0) {
+        LAUNCH(KK_FACTOR, st, k_big_trsm<<<m, 256, 0, st>>>(b.d, k));
+        LAUNCH(KK_FACTOR, st, k_big_update<<<m * (m + 1), 256, 0, st>>>(b.d, k));
+      }
+    }
+    const size_t sm = big_solve_smem(n);
+    LAUNCH(KK_FACTOR, st, k_big_solve<<<1, 1024, sm, st>>>(b.d, 0));
+    for (int it = 0; it < refine_steps; ++it) {
+      LAUNCH(KK_FACTOR, st, k_big_resid<<<grid_for_big(n * 32, 256), 256, 0, st>>>(b.d));
+      LAUNCH(KK_FACTOR, st, k_big_solve<<<1, 1024, sm, st>>>(b.d, 1));
+    }
   }
   if (mixed) LAUNCH(KK_FACTOR, st, k_big_finish<true><<<1, 512, 0, st>>>(b.d));
   else LAUNCH(KK_FACTOR, st, k_big_finish<false><<<1, 512, 0, st>>>(b.d));
@@ -380,7 +863,14 @@ void launch_big_solve(const BigRef& b, bool mixed, int refine_steps, int assembl
 
 cudaError_t set_big_attributes(int max_n) {
   const int smem = (int)big_solve_smem(max_n);
-  return cudaFuncSetAttribute(k_big_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem > 48 * 1024 ? smem : 48 * 1024);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_big_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem > 48 * 1024 ? smem : 48 * 1024);
+  if (e != cudaSuccess) return e;
+  const int smem_df = (int)big_solve_df_smem(max_n);
+  e = cudaFuncSetAttribute(k_big_solve_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           smem_df > 48 * 1024 ? smem_df : 48 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_big_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpdSmem);
 }
 
 }  // namespace bagpu

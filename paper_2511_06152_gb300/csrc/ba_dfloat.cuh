@@ -117,6 +117,52 @@ __device__ __forceinline__ dfl df_sqrt(dfl a) {
   return fast_two_sum(s, c);
 }
 
+// a - x y, the low-order terms added without their own TwoSum (as in
+// df_add_fast): the error stays near 2^-47 of max(|a|, |x y|), which is what
+// the backward-error analysis of a Cholesky update asks for.
+__device__ __forceinline__ dfl df_fms(dfl a, dfl x, dfl y) {
+  dfl p = two_prod(x.hi, y.hi);
+  p.lo = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo));
+  dfl s = two_sum(a.hi, -p.hi);
+  s.lo = __fadd_rn(s.lo, __fsub_rn(a.lo, p.lo));
+  return fast_two_sum(s.hi, s.lo);
+}
+
+// Compensated dot product of double-float vectors (Ogita, Rump and Oishi,
+// SIAM J. Sci. Comput. 26(6), 2005, "Accurate sum and dot product",
+// algorithm Dot2, with the low words' cross terms folded into the error
+// term): the result is as accurate as if the sum had been formed in twice
+// the working precision and then rounded to a double-float.
+struct Dot2 {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(dfl x, dfl y) {
+    const dfl p = two_prod(x.hi, y.hi);
+    const float e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, p.lo));
+    const dfl t = two_sum(s, p.hi);
+    s = t.hi;
+    c = __fadd_rn(c, __fadd_rn(t.lo, e));
+  }
+  // merge another partial sum (the reduction trees of a dot product)
+  __device__ __forceinline__ void merge(float s2, float c2) {
+    const dfl t = two_sum(s, s2);
+    s = t.hi;
+    c = __fadd_rn(c, __fadd_rn(t.lo, c2));
+  }
+  __device__ __forceinline__ dfl get() const { return fast_two_sum(s, c); }
+};
+
+// 1 / sqrt(d) for d > 0: the binary32 approximation, one binary32 Newton
+// step r + r/2 (1 - d r^2), then one in double-float (error about 2^-48).
+__device__ __forceinline__ dfl df_rsqrt(dfl d) {
+  float r = d.hi < 0x1p-100f ? rsqrtf(d.hi * 0x1p100f) * 0x1p50f : rsqrtf(d.hi);
+  const float t = __fmul_rn(d.hi, r);
+  const float e = __fmaf_rn(-t, r, 1.0f);
+  r = __fmaf_rn(__fmul_rn(0.5f, r), e, r);
+  const dfl p = df_mul(d, two_prod(r, r));  // d r^2, near 1
+  const float e2 = __fsub_rn(__fsub_rn(1.0f, p.hi), p.lo);
+  return fast_two_sum(r, __fmul_rn(__fmul_rn(0.5f, r), e2));
+}
+
 __device__ __forceinline__ float df_to_f(dfl a) { return __fadd_rn(a.hi, a.lo); }
 __device__ __forceinline__ double df_to_d(dfl a) { return (double)a.hi + (double)a.lo; }
 

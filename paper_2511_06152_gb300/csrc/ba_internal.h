@@ -36,6 +36,7 @@ constexpr int kMaxTrack = 32;
 constexpr int kMaxFreeSmall = 32;  // free cameras the single-CTA factor handles (n <= 192)
 constexpr int kMaxFree = 1024;     // free cameras of one cluster (larger systems: the global-memory solver)
 constexpr int kBigNB = 32;         // block size of the global-memory factorisation
+constexpr int kSlicesHost = 6;     // Ozaki digits per double-float entry (kSlices of ba_tc.cuh)
 constexpr double kDiagMin = 1e-6;
 constexpr double kDiagMax = 1e32;
 constexpr double kMinDepth = 1e-6;
@@ -82,8 +83,8 @@ struct LmState {
   double F_new;      // cost at the candidate
   double pred_cam;   // camera part of d^T (mu D d + g)
   double prior_new;  // prior cost at the candidate
-  double mu0;
-  double pad0;
+  double mu0;        // damping a reset restores (mu0 at create, or the warm start's)
+  double nu0;        // nu a reset restores (2 at create, or the warm start's)
   int cur;           // which of the double-buffered states is current
   int status;        // status of the last factorisation
   int iter;          // iterations run
@@ -135,6 +136,15 @@ struct DevCluster {
   double* F;               // [n][n] Cholesky factor (lower), elimination order
   double* bx;              // [4][n]: right-hand side / work, solution, correction, 1 / L(j, j)
   int* bflag;              // nonzero: a pivot was not positive
+  // tensor-core factorisation of the global-memory solver: F holds the factor
+  // as double-float (binary32 high words [n][n], then low words [n][n]);
+  // dig: Ozaki digits of the current panel's rows, [kSlices][dig_groups]
+  // groups of 8 rows x 32 columns in the canonical shared-memory layout
+  // (512 bytes each); dexp: each row's power-of-two scale; linv: the inverse
+  // of each 32 x 32 diagonal block of the factor, [nblk][hi, lo][32][32]
+  unsigned short* dig;
+  int* dexp;
+  float* linv;
   void* camreal;           // FP64 path: double [nc][20]: R[9], T[3], intr[7], free flag
   float* camdf;            // mixed path: [2][nc][kCamDf] double-float cameras
 
@@ -175,7 +185,7 @@ struct DevCluster {
   LmState* lm;
   StepRec* trace;   // [trace_cap]
   int trace_cap;
-  int pad;
+  int dig_groups;   // groups of 8 rows in dig (rows of the factor rounded up to 32, plus 128)
 };
 
 struct BatchView {
@@ -247,8 +257,12 @@ struct BigRef {
   double* S;               // device [n][n]
   double* F;               // device [n][n]
   std::vector<int> below;  // per block column of kBigNB: row blocks below it inside the envelope
+  bool tc = true;          // tensor-core double-float factor (else the binary64 CUDA-core one)
 };
 void launch_big_solve(const BigRef& b, bool mixed, int refine_steps, int assemble_only, cudaStream_t st);
+// rows of the digit buffer of a system of order n: n rounded up to kBigNB, plus
+// one 128-row tile, so that every tile the update kernel copies lies inside
+__host__ __device__ constexpr int big_dig_rows(int n) { return (n + kBigNB - 1) / kBigNB * kBigNB + 128; }
 cudaError_t set_big_attributes(int max_n);
 
 // Kernel launchers (ba_kernels.cu).  All run on `st`.

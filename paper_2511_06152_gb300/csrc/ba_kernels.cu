@@ -1166,7 +1166,9 @@ __device__ void chol_solve_blocked(const double* A, const double* inv_diag, cons
     }
     __syncthreads();
   }
-  for (int i = tid; i < n; i += bs) b[i] *= inv_diag[i] * inv_diag[i];  // w = D^-2 z
+  // w = D^-2 z, one factor 1 / L(i, i) at a time: the square of the
+  // reciprocal of a tiny (even subnormal) pivot would overflow
+  for (int i = tid; i < n; i += bs) b[i] = (b[i] * inv_diag[i]) * inv_diag[i];
   __syncthreads();
   const int nb = (n + kSolveNB - 1) / kSolveNB;
   for (int blk = nb - 1; blk >= 0; --blk) {  // Lu^T x = w
@@ -1823,6 +1825,13 @@ __global__ void k_warm_copy(const DevCluster* dst, const DevCluster* src, const 
                             const int2* pts, int n_pts) {
   const int scur = src->lm->cur;
   const int stride = gridDim.x * blockDim.x;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // the damping state goes with the poses and points
+    LmState* dl = dst->lm;
+    const LmState* sl = src->lm;
+    dl->mu = dl->mu0 = sl->mu;
+    dl->mu_f = (float)sl->mu;
+    dl->nu = dl->nu0 = sl->nu;
+  }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_pts; i += stride) {
     const int2 p = pts[i];
     const double* sx = src->X + ((size_t)scur * src->n_pts + p.y) * 3;
@@ -1864,7 +1873,7 @@ __global__ void k_reset(BatchView bv) {
         LmState* lm = C.lm;
         lm->mu = lm->mu0;
         lm->mu_f = (float)lm->mu0;
-        lm->nu = 2.0;
+        lm->nu = lm->nu0;
         lm->F = 0.0;
         lm->F_new = 0.0;
         lm->cur = 0;

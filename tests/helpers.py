@@ -19,42 +19,52 @@ def rms_inliers(err, outlier):
     return float(np.sqrt(np.mean(np.asarray(err)[~np.asarray(outlier)] ** 2)))
 
 
-def fp64_step_parity(ba, O, scene, iters, tol=1e-10, min_free=None):
-    """Step the FP64 GPU path (through the C ABI) and the oracle side by side
-    from the same state and compare every step: F before, the status, the
-    accept/reject decision, F after, the damping and the state (relative
-    `tol`, scale 1 m).  A step the oracle rejects as not positive definite
-    must be rejected the same way, with the state unchanged.  Once the cost
-    has converged to rounding level (|F - F(x+d)| <= 1e-10 F, or |gain| <
-    1e-8) the decision is not determined in binary64 and the comparison
-    stops there.  Returns the number of steps compared."""
+def compare_steps(ctx, cid, O, P, S, iters, tol=1e-10):
+    """Step the FP64 GPU path (cluster cid of ctx, through the C ABI) and the
+    oracle (problem P, state S) side by side from the same state and compare
+    every step: F before, the status, the accept/reject decision, F after,
+    the damping and the state (relative `tol`, scale 1 m).  A step the oracle
+    rejects as not positive definite must be rejected the same way, with the
+    state unchanged.  Once the cost has converged to rounding level
+    (|F - F(x+d)| <= 1e-10 F, or |gain| < 1e-8) the decision is not
+    determined in binary64 and the comparison stops there.  Returns the
+    number of steps compared."""
     import pytest
+    compared = 0
+    before = ctx.get_state(cid)
+    for it in range(iters):
+        io = O.lm_step(P, S)
+        ig = ctx.solve_step(cid)
+        R, T, X = ctx.get_state(cid)
+        assert ig["F_before"] == pytest.approx(io["F"], rel=tol, abs=1e-300)
+        assert ig["mu_used"] == io["mu_used"], (it, ig, io)
+        assert ig["status"] == io["status"], (it, ig, io)
+        if io["status"] != 0:
+            assert ig["accepted"] == 0 and io["accepted"] == 0
+            assert ig["mu"] == io["mu"] and ig["nu"] == io["nu"], (it, ig, io)
+            for a, b in zip((R, T, X), before):  # a rejected step leaves the GPU's state as it was
+                assert np.array_equal(a, b)
+            compared += 1
+            continue
+        if abs(io["F"] - io["F_new"]) <= 1e-10 * abs(io["F"]) or abs(io["gain"]) < 1e-8:
+            break
+        assert ig["accepted"] == io["accepted"], (it, ig, io)
+        assert ig["F_after"] == pytest.approx(io["F_new"], rel=tol, abs=1e-12)
+        assert ig["mu"] == pytest.approx(io["mu"], rel=1e-9)
+        e = state_rel_err(R, T, X, S.R, S.T, S.X)
+        assert e < tol, (it, e)
+        before = (R, T, X)
+        compared += 1
+    return compared
+
+
+def fp64_step_parity(ba, O, scene, iters, tol=1e-10, min_free=None, flags=0):
+    """compare_steps on a fresh FP64 context (with `flags`) and cluster made
+    from `scene` (its initial damping scene["mu0"], default 1e-4).  Returns
+    the number of steps compared."""
     P, S = O.Problem(scene), O.State(scene, mu0=scene.get("mu0", 1e-4))
-    with ba.Context(precision=ba.BA_FP64) as ctx:
+    with ba.Context(precision=ba.BA_FP64, flags=flags) as ctx:
         cid = ctx.create_cluster(scene)
         if min_free is not None:
             assert ctx.cluster_info(cid)["n_free"] >= min_free
-        compared = 0
-        for it in range(iters):
-            before = (S.R.copy(), S.T.copy(), S.X.copy())
-            io = O.lm_step(P, S)
-            ig = ctx.solve_step(cid)
-            R, T, X = ctx.get_state(cid)
-            assert ig["F_before"] == pytest.approx(io["F"], rel=tol, abs=1e-300)
-            assert ig["status"] == io["status"], (it, ig, io)
-            if io["status"] != 0:
-                assert ig["accepted"] == 0 and io["accepted"] == 0
-                assert ig["mu"] == io["mu"] and ig["nu"] == io["nu"], (it, ig, io)
-                for a, b in zip((R, T, X), before):
-                    assert np.array_equal(np.asarray(a).reshape(np.shape(b)), b)
-                compared += 1
-                continue
-            if abs(io["F"] - io["F_new"]) <= 1e-10 * abs(io["F"]) or abs(io["gain"]) < 1e-8:
-                break
-            assert ig["accepted"] == io["accepted"], (it, ig, io)
-            assert ig["F_after"] == pytest.approx(io["F_new"], rel=tol, abs=1e-12)
-            assert ig["mu"] == pytest.approx(io["mu"], rel=1e-9)
-            e = state_rel_err(R, T, X, S.R, S.T, S.X)
-            assert e < tol, (it, e)
-            compared += 1
-        return compared
+        return compare_steps(ctx, cid, O, P, S, iters, tol)

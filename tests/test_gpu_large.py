@@ -28,14 +28,36 @@ def ba():
     return m
 
 
-def _step_parity(ba, scene, iters, min_steps):
-    n = fp64_step_parity(ba, O, scene, iters, TOL_STEP, min_free=33)
+def _step_parity(ba, scene, iters, min_steps, flags=0):
+    n = fp64_step_parity(ba, O, scene, iters, TOL_STEP, min_free=33, flags=flags)
     assert n >= min_steps, (n, min_steps)
 
 
-def test_fp64_step_parity_40_images(ba):
-    """4 strips x 10 images, two of them fixed, priors on: n = 228."""
-    _step_parity(ba, sg.tiny_cluster(5151, 4, 10, 3000, fixed=(0, 11)), 8, min_steps=8)
+@pytest.mark.parametrize("factor", ["tensor_core", "fp64_cuda_core"])
+def test_fp64_step_parity_40_images(ba, factor):
+    """4 strips x 10 images, two of them fixed, priors on: n = 228; the
+    tensor-core double-float factorisation (default) and the binary64
+    CUDA-core one."""
+    flags = ba.BA_FLAG_BIG_FP64_FACTOR if factor == "fp64_cuda_core" else 0
+    _step_parity(ba, sg.tiny_cluster(5151, 4, 10, 3000, fixed=(0, 11)), 8, min_steps=8, flags=flags)
+
+
+def test_tensor_core_and_fp64_factor_agree_on_the_large_block(ba):
+    """The 400-image block in mixed precision, 3 LM iterations with each
+    factorisation: the same decisions, F within 1e-12 relative, centres
+    within 1e-9 m."""
+    c = sg.cluster_c5(n_points=200_000)
+    out = []
+    for flags in (0, ba.BA_FLAG_BIG_FP64_FACTOR):
+        with ba.Context(precision=ba.BA_MIXED, flags=flags) as ctx:
+            cid = ctx.create_cluster(c)
+            tr = ctx.run(cid, 3)
+            out.append((tr, ctx.get_state(cid)))
+    (ta, sa), (tb, sb) = out
+    for x, y in zip(ta, tb):
+        assert x["status"] == y["status"] == 0 and x["accepted"] == y["accepted"]
+        assert x["F_after"] == pytest.approx(y["F_after"], rel=1e-12)
+    assert np.abs(sa[1] - sb[1]).max() < 1e-9
 
 
 def test_fp64_step_parity_large_block(ba):

@@ -9,10 +9,14 @@ flight at the same time.  Every window's final state must agree bit for bit.
 """
 import time
 
+import ctypes
+
 import numpy as np
 import pytest
 
+import oracle as O
 import scenegen as sg
+from helpers import compare_steps
 
 pytestmark = pytest.mark.gpu
 
@@ -314,3 +318,91 @@ def test_get_state_batch_in_groups_equals_get_state():
         for cid, (R, T, X) in zip(ids, got):
             R1, T1, X1 = ctx.get_state(cid)
             assert np.array_equal(R, R1) and np.array_equal(T, T1) and np.array_equal(X, X1)
+
+
+def test_warm_start_carries_the_damping_and_matches_the_oracle():
+    """The next window starts from the previous window's poses, points and
+    damping (mu, nu) on the device; the oracle, seeded with the same state
+    and damping, takes the same FP64 steps (relative 1e-10).  A reset
+    restores the warm-started state and damping."""
+    import paper_2511_06152_gb300 as ba
+    wins = _flight(9105)
+    (c0, cams0, pts0), (c1, cams1, pts1) = wins[0], wins[1]
+    cm, pm = sg.warm_maps(cams0, pts0, cams1, pts1)
+    with ba.Context(precision=ba.BA_FP64) as ctx:
+        a = ctx.create_cluster(c0)
+        tr = ctx.run(a, ITERS)
+        mu, nu = tr[-1]["mu"], tr[-1]["nu"]
+        assert mu != 1e-4  # the previous window moved its damping
+        Ra, Ta, Xa = ctx.get_state(a)
+        b = ctx.create_cluster(c1)
+        ctx.warm_start(b, a, cm, pm)
+        seed = dict(c1, R0=np.array(c1["R0"]).reshape(-1, 9).copy(), T0=np.array(c1["T0"]).copy(),
+                    X0=np.array(c1["X0"]).copy())
+        seed["R0"][cm >= 0] = Ra[cm[cm >= 0]]
+        seed["T0"][cm >= 0] = Ta[cm[cm >= 0]]
+        seed["X0"][pm >= 0] = Xa[pm[pm >= 0]]
+        for u, v in zip(ctx.get_state(b), (seed["R0"], seed["T0"], seed["X0"])):
+            assert np.array_equal(u, v)
+        P, S = O.Problem(seed), O.State(seed, mu0=mu)
+        S.nu = ctypes.c_double(nu)
+        first = ctx.solve_step(b)
+        assert first["mu_used"] == mu
+        ctx.reset(b)  # the warm-started state and damping come back
+        for u, v in zip(ctx.get_state(b), (seed["R0"], seed["T0"], seed["X0"])):
+            assert np.array_equal(u, v)
+        n = compare_steps(ctx, b, O, P, S, ITERS)
+        assert n >= 4, n
+
+
+def test_hbm_budget_admission_waits_for_memory_and_keeps_results():
+    """A context whose device-memory budget holds only some of the windows:
+    creating one more returns BA_ERR_BUDGET while the others hold memory,
+    succeeds once a finished window has been freed, and every window's result
+    equals the one computed without a budget."""
+    import paper_2511_06152_gb300 as ba
+    wins = _flight(9106)[:3]
+    ref = []
+    with ba.Context(precision=ba.BA_MIXED) as ctx:
+        for c, _, _ in wins:
+            cid = ctx.create_cluster(c)
+            ctx.run(cid, ITERS, trace=False)
+            ref.append(ctx.get_state(cid))
+        arena = [ctx.cluster_info(cid)["arena_bytes"] for cid in list(ctx.sizes)]
+    with ba.Context(precision=ba.BA_MIXED) as probe:  # memory of the first window and the serving slots
+        cid = probe.create_cluster(wins[0][0])
+        t = probe.submit(cid, ITERS)
+        while probe.poll(t) is None:
+            time.sleep(0.001)
+        base = probe.memory_in_use()
+    # room for windows 0 and 1 (and the slot table) but not for window 2 as
+    # well; once window 0 is freed, windows 1 and 2 fit
+    budget = base + arena[1] + arena[2] - min(arena[0], arena[2]) // 2
+    assert budget < base + arena[1] + arena[2] and budget - base + arena[0] >= arena[1] + arena[2]
+    with ba.Context(precision=ba.BA_MIXED, hbm_budget_bytes=budget) as ctx:
+        c0 = ctx.create_cluster(wins[0][0])
+        t0 = ctx.submit(c0, ITERS)
+        c1 = ctx.create_cluster(wins[1][0])
+        with pytest.raises(ba.BAError) as ei:
+            ctx.create_cluster(wins[2][0])
+        assert ei.value.status == ba.BA_ERR_BUDGET
+        t1 = ctx.submit(c1, ITERS)
+        got = {}
+        for cid, t in ((c0, t0), (c1, t1)):
+            r = None
+            while r is None:
+                r = ctx.poll(t)
+                time.sleep(0.001)
+            assert r["status"] == 0 and r["iters"] == ITERS
+            got[cid] = ctx.get_state(cid)
+        ctx.destroy_cluster(c0)  # a completion frees memory: the waiting window is admitted
+        c2 = ctx.create_cluster(wins[2][0])
+        t2 = ctx.submit(c2, ITERS)
+        r = None
+        while r is None:
+            r = ctx.poll(t2)
+            time.sleep(0.001)
+        got[c2] = ctx.get_state(c2)
+        for cid, rf in zip((c0, c1, c2), ref):
+            for u, v in zip(got[cid], rf):
+                assert np.array_equal(u, v)
