@@ -93,6 +93,8 @@ typedef struct {
   int32_t n_slots;           /* clusters the serving scheduler runs at once (ba_submit); 0 = 64 */
   int32_t refine_steps;      /* iterative-refinement passes after the Cholesky solve; <0 = default 1 */
   int32_t flags;             /* BA_FLAG_* */
+  const char* tune_table;    /* NULL, or the path of a tuning table (ba_tune_table_lookup): the
+                                entry for this GPU and precision, if any, is applied at ba_init */
 } ba_config;
 
 #define BA_FLAG_KERNEL_TIMING 1 /* bracket every kernel with CUDA events (also inside graphs) */
@@ -482,6 +484,62 @@ BA_API ba_status ba_kernel_stats(ba_ctx* ctx, double* ms, uint64_t* launches, in
  * device address; make that first call before any stream capture.  No
  * cudaMalloc, cudaFree or other allocating routine is called. */
 BA_API ba_status ba_cost_noalloc(const ba_cluster_desc* d, void* stream, double* F_out);
+
+/* ---- Autotuning of the launch shapes ----
+ *
+ * Launch and presort parameters of the LM iteration.  None changes what is
+ * computed; chunk_tiles and factor_nb change the order of some sums (every
+ * configuration is deterministic: alone = in a batch, bit for bit).
+ * Values: chunk_tiles 0 (the precision's maximum: 16 mixed, 8 FP64) or
+ * 4 .. that maximum; lin_ctas_per_sm and back_ctas_per_sm 1 .. 32;
+ * factor_nb 2 .. 32; factor_threads 256, 384 or 512; big_panel_w 1, 2, 4, 8,
+ * 16 or 32.  ms_default / ms_tuned: what ba_autotune measured (device time
+ * of one solve of its batch with the defaults and with the chosen values;
+ * 0 when not measured). */
+typedef struct {
+  int32_t chunk_tiles;      /* observations per linearise+Schur CTA, in tiles of up to 32 (whole points) */
+  int32_t lin_ctas_per_sm;  /* linearise+Schur grid: CTAs per SM before it strides */
+  int32_t back_ctas_per_sm; /* back-substitution grid: CTAs per SM before it strides */
+  int32_t factor_nb;        /* panel width of the shared-memory Cholesky (clusters of <= 32 free images) */
+  int32_t factor_threads;   /* threads of its CTA */
+  int32_t big_panel_w;      /* column-block width of the tensor-core solver's diagonal factorisation */
+  double ms_default;
+  double ms_tuned;
+} ba_tune;
+
+/* The context's current parameters (defaults, the tuning table's entry,
+ * ba_set_tune's or ba_autotune's choice). */
+BA_API ba_status ba_get_tune(ba_ctx* ctx, ba_tune* out);
+
+/* Set the parameters (t host, read during the call; ms fields ignored).
+ * chunk_tiles applies to clusters created afterwards, the rest to every
+ * later launch.  BA_ERR_INVALID for a value out of range, or while a
+ * cluster is in service (a batch on the device, or serving). */
+BA_API ba_status ba_set_tune(ba_ctx* ctx, const ba_tune* t);
+
+/* Choose the parameters by measurement: the n clusters of descs (host
+ * arrays, as for ba_create_cluster) are created in this context, solved
+ * iters LM iterations at a time as one batch (ba_solve_batch, from their
+ * initial state), and timed with CUDA events on the context's stream, the
+ * fastest of three solves per candidate; one parameter at a time, each over
+ * a few candidates around the current choice, in the order above (a
+ * coordinate descent from the defaults; big_panel_w only when a cluster has
+ * more than 32 free images).  The choice is kept in the context and written
+ * to *out with both timings; the tuning clusters are destroyed.  Blocking;
+ * takes seconds (chunk_tiles candidates re-create the clusters).
+ * BA_ERR_INVALID for bad arguments or while a cluster is in service; errors
+ * of cluster creation are returned as they come. */
+BA_API ba_status ba_autotune(ba_ctx* ctx, const ba_cluster_desc* descs, int32_t n, int32_t iters, ba_tune* out);
+
+/* Host only: the entry of a tuning table (a text file) for a GPU and a
+ * precision.  One entry per line, '#' starts a comment:
+ *   <gpu name, spaces as '_'> <SM count> <fp64|mixed> chunk_tiles=.. lin_ctas_per_sm=..
+ *   back_ctas_per_sm=.. factor_nb=.. factor_threads=.. big_panel_w=.. [ms_default=.. ms_tuned=..]
+ * Missing keys keep their defaults; the last matching line wins.
+ * BA_ERR_NOT_FOUND when the file has no such entry or cannot be read,
+ * BA_ERR_INVALID for a malformed matching entry or out-of-range values. */
+BA_API ba_status ba_tune_table_lookup(const char* path, const char* gpu_name, int32_t sm_count, int32_t precision,
+                                      ba_tune* out);
 
 /* Free a cluster: the end of a sliding cluster's life (Sec. 3.2: once the
  * next cluster has taken over its overlap images, its state is no longer

@@ -44,7 +44,46 @@ _u8p = ctypes.POINTER(ctypes.c_uint8)
 class ba_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("stream", ctypes.c_void_p), ("hbm_budget_bytes", ctypes.c_uint64),
                 ("precision", ctypes.c_int32), ("n_slots", ctypes.c_int32), ("refine_steps", ctypes.c_int32),
-                ("flags", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("tune_table", ctypes.c_char_p)]
+
+
+TUNE_KEYS = ("chunk_tiles", "lin_ctas_per_sm", "back_ctas_per_sm", "factor_nb", "factor_threads", "big_panel_w")
+# the committed tuning table that Context hands to ba_init (entries per GPU and precision)
+TUNE_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.txt")
+
+
+class ba_tune(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in TUNE_KEYS] + [("ms_default", ctypes.c_double),
+                                                           ("ms_tuned", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+    @classmethod
+    def from_dict(cls, d):
+        t = cls()
+        for k, _ in cls._fields_:
+            if k in d:
+                setattr(t, k, d[k])
+        return t
+
+
+def tune_table_line(gpu_name, sm_count, precision, tune):
+    """One line of the tuning table read by ba_tune_table_lookup (format in ba.h)."""
+    prec = "mixed" if precision == BA_MIXED else "fp64"
+    kv = " ".join(f"{k}={int(tune[k])}" for k in TUNE_KEYS)
+    ms = f" ms_default={tune.get('ms_default', 0.0):.4f} ms_tuned={tune.get('ms_tuned', 0.0):.4f}"
+    return f"{gpu_name.replace(' ', '_')} {int(sm_count)} {prec} {kv}{ms}"
+
+
+def tune_table_lookup(path, gpu_name, sm_count, precision):
+    """ba_tune_table_lookup (host only): the table's entry as a dict, or None."""
+    t = ba_tune()
+    st = lib().ba_tune_table_lookup(path.encode(), gpu_name.encode(), int(sm_count), int(precision), ctypes.byref(t))
+    if st == BA_ERR_NOT_FOUND:
+        return None
+    _check(st, None, "ba_tune_table_lookup")
+    return t.as_dict()
 
 
 class ba_cluster_desc(ctypes.Structure):
@@ -116,6 +155,7 @@ EXPORTS = ["ba_init", "ba_create_cluster", "ba_linearize", "ba_solve_step", "ba_
            "ba_reset_batch", "ba_submit", "ba_poll", "ba_get_state", "ba_get_state_batch", "ba_reprojection_errors",
            "ba_memory_in_use",
            "ba_launch_count", "ba_kernel_stats", "ba_cost_noalloc", "ba_warm_start", "ba_transition", "ba_footprints", "ba_footprint_overlaps", "ba_patch_transfer_poses", "ba_patch_transfer_planar", "ba_get_cluster_info", "ba_presort_host", "ba_destroy_cluster", "ba_shutdown",
+           "ba_get_tune", "ba_set_tune", "ba_autotune", "ba_tune_table_lookup",
            "ba_status_string", "ba_last_error"]
 
 _lib = None
@@ -165,6 +205,12 @@ def lib(build: bool = True):
             L.ba_get_cluster_info.argtypes = [vp, u64, ctypes.POINTER(ba_cluster_info)]
             L.ba_presort_host.argtypes = [ctypes.POINTER(ba_cluster_desc), ctypes.c_int32, ctypes.c_int32,
                                           ctypes.POINTER(ba_presort_info)]
+            L.ba_get_tune.argtypes = [vp, ctypes.POINTER(ba_tune)]
+            L.ba_set_tune.argtypes = [vp, ctypes.POINTER(ba_tune)]
+            L.ba_autotune.argtypes = [vp, ctypes.POINTER(ba_cluster_desc), ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.POINTER(ba_tune)]
+            L.ba_tune_table_lookup.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.POINTER(ba_tune)]
             L.ba_destroy_cluster.argtypes = [vp, u64]
             L.ba_shutdown.argtypes = [vp]
             L.ba_status_string.argtypes = [ctypes.c_int32]
@@ -243,10 +289,11 @@ class Context:
     """Owns one ba_ctx on one device and stream."""
 
     def __init__(self, device=0, precision=BA_FP64, stream=None, hbm_budget_bytes=0, n_slots=0, refine_steps=-1,
-                 flags=0):
+                 flags=0, tune_table=TUNE_TABLE):
         self.L = lib()
         cfg = ba_config(device=device, stream=stream, hbm_budget_bytes=hbm_budget_bytes, precision=precision,
-                        n_slots=n_slots, refine_steps=refine_steps, flags=flags)
+                        n_slots=n_slots, refine_steps=refine_steps, flags=flags,
+                        tune_table=tune_table.encode() if tune_table else None)
         h = ctypes.c_void_p()
         _check(self.L.ba_init(ctypes.byref(h), ctypes.byref(cfg)), None, "ba_init")
         self.h = h
@@ -288,6 +335,22 @@ class Context:
         out = ba_lin_info()
         _check(self.L.ba_linearize(self.h, cid, ctypes.byref(out)), self.h, "ba_linearize")
         return {"cost": out.cost, "grad_inf": out.grad_inf, "n_free": out.n_free}
+
+    def get_tune(self):
+        t = ba_tune()
+        _check(self.L.ba_get_tune(self.h, ctypes.byref(t)), self.h, "ba_get_tune")
+        return t.as_dict()
+
+    def set_tune(self, **kw):
+        t = ba_tune.from_dict(dict(self.get_tune(), **kw))
+        _check(self.L.ba_set_tune(self.h, ctypes.byref(t)), self.h, "ba_set_tune")
+
+    def autotune(self, scenes, iters):
+        keep = []
+        descs = (ba_cluster_desc * len(scenes))(*[make_desc(sc, keep) for sc in scenes])
+        t = ba_tune()
+        _check(self.L.ba_autotune(self.h, descs, len(scenes), int(iters), ctypes.byref(t)), self.h, "ba_autotune")
+        return t.as_dict()
 
     def solve_step(self, cid):
         out = ba_step_info()

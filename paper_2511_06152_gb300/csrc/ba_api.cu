@@ -3,12 +3,16 @@
 // with CUDA-graph replay, and the serving scheduler.
 #include <cuda_runtime.h>
 
+#include <fstream>
+#include <sstream>
+
 #include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -76,6 +80,7 @@ struct Ticket {
 // Serving slots (see scheduler_loop).
 struct SlotTable {
   int n = 0;
+  int tune_gen = -1;  // ctx->tune_gen the serving graph was captured with
   char* dbuf = nullptr;
   size_t bytes = 0;
   BatchView bv{};
@@ -112,6 +117,8 @@ struct ba_ctx {
   bool timing = false;
   int inject = 0;  // failure-injection bits for the kernels (BA_FLAG_INJECT_*)
   bool big_fp64 = false;  // global-memory solver: binary64 CUDA-core factor instead of the tensor-core one
+  TuneParams tune;        // launch and presort parameters (ba_set_tune, ba_autotune, the tuning table)
+  std::atomic<int> tune_gen{0};  // bumped by every change of tune: the serving graph is captured again
   std::mutex stats_mu;  // kernel statistics (API threads and the scheduler)
   // pinned host staging buffers of cluster creation, reused across calls (one
   // per concurrent creation; taken and returned under stage_mu)
@@ -281,6 +288,55 @@ cudaError_t pool_alloc(ba_ctx* ctx, void** p, size_t bytes, cudaStream_t st) {
   return cudaMallocFromPoolAsync(p, bytes, ctx->pool, st);
 }
 
+bool tune_in_range(const ba_tune& t, bool mixed, std::string* why) {
+  const int cmax = chunk_tiles(mixed);
+  auto bad = [&](const char* m) {
+    *why = m;
+    return false;
+  };
+  if (t.chunk_tiles != 0 && (t.chunk_tiles < 4 || t.chunk_tiles > cmax))
+    return bad("chunk_tiles must be 0 or 4 .. 16 (mixed) / 8 (FP64)");
+  if (t.lin_ctas_per_sm < 1 || t.lin_ctas_per_sm > 32) return bad("lin_ctas_per_sm must be 1 .. 32");
+  if (t.back_ctas_per_sm < 1 || t.back_ctas_per_sm > 32) return bad("back_ctas_per_sm must be 1 .. 32");
+  if (t.factor_nb < 2 || t.factor_nb > 32) return bad("factor_nb must be 2 .. 32");
+  if (t.factor_threads != 256 && t.factor_threads != 384 && t.factor_threads != 512)
+    return bad("factor_threads must be 256, 384 or 512");
+  if (t.big_panel_w < 1 || t.big_panel_w > 32 || (32 % t.big_panel_w) != 0)
+    return bad("big_panel_w must be 1, 2, 4, 8, 16 or 32");
+  return true;
+}
+
+TuneParams tune_from_abi(const ba_tune& t) {
+  TuneParams p;
+  p.chunk_tiles = t.chunk_tiles;
+  p.lin_ctas_per_sm = t.lin_ctas_per_sm;
+  p.back_ctas_per_sm = t.back_ctas_per_sm;
+  p.factor_nb = t.factor_nb;
+  p.factor_threads = t.factor_threads;
+  p.big_panel_w = t.big_panel_w;
+  return p;
+}
+
+ba_tune tune_to_abi(const TuneParams& p) {
+  ba_tune t{};
+  t.chunk_tiles = p.chunk_tiles;
+  t.lin_ctas_per_sm = p.lin_ctas_per_sm;
+  t.back_ctas_per_sm = p.back_ctas_per_sm;
+  t.factor_nb = p.factor_nb;
+  t.factor_threads = p.factor_threads;
+  t.big_panel_w = p.big_panel_w;
+  return t;
+}
+
+// the autotuned launch parameters into a batch view (grids and CTA shapes
+// are fixed when a plan's graph is captured)
+void apply_tune(const ba_ctx* ctx, BatchView& bv) {
+  bv.lin_ctas_per_sm = ctx->tune.lin_ctas_per_sm;
+  bv.back_ctas_per_sm = ctx->tune.back_ctas_per_sm;
+  bv.factor_nb = ctx->tune.factor_nb;
+  bv.factor_threads = ctx->tune.factor_threads;
+}
+
 void free_plan(ba_ctx* ctx, Plan* p) {
   for (auto& kv : p->graphs) {
     cudaGraphExecDestroy(kv.second.exec);  // an executing graph is freed when it completes
@@ -330,7 +386,8 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
   for (int i = 0; i < n; ++i) {
     Cluster* c = find_cluster(ctx, ids[i]);
     if (c->nf > kMaxFreeSmall)
-      p->big.push_back(BigRef{c->d_desc, 6 * c->nf, c->nf, c->h.n_pairs, c->h.S, c->h.F, c->big_below, !ctx->big_fp64});
+      p->big.push_back(BigRef{c->d_desc, 6 * c->nf, c->nf, c->h.n_pairs, c->h.S, c->h.F, c->big_below, !ctx->big_fp64,
+                              ctx->tune.big_panel_w});
   }
   pre.push_back(pre[n]);  // totals, read by the kernels
   pre.push_back(pre[(n + 1) + n]);
@@ -383,6 +440,7 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
   p->bv.total_items = pre[2 * (n + 1) + n];
   p->bv.max_n = max_n;
   p->bv.inject = ctx->inject;
+  apply_tune(ctx, p->bv);
   p->lm_out = (LmState*)(p->dbuf + o_lm);
   p->gnorm = (double*)(p->dbuf + o_gn);
   ctx->plans[ids] = p;
@@ -983,7 +1041,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
   // chunk the observation lists of its free cameras and the observation pairs
   // of its co-visible camera pairs (all in increasing point-major order)
   const bool mixed = ctx->mixed;
-  const int ch_tiles = chunk_tiles(mixed);
+  const int ch_tiles = ctx->tune.chunk_tiles > 0 ? ctx->tune.chunk_tiles : chunk_tiles(mixed);
   std::vector<Chunk> chunks;
   for (size_t t = 0; t < tiles.size();) {
     Chunk ch{};
@@ -1761,6 +1819,7 @@ ba_status slots_setup(ba_ctx* ctx) {
   bv.total_tiles = bv.total_chunks = bv.total_items = 1 << 30;  // the graph uses the largest grids
   bv.max_n = 6 * kMaxFreeSmall;
   bv.inject = ctx->inject;
+  apply_tune(ctx, bv);
   T.dirty = true;
   return BA_OK;
 }
@@ -1792,7 +1851,16 @@ ba_status slots_upload(ba_ctx* ctx) {
 // one round: arm -> F for newly armed slots -> one LM iteration -> gather
 ba_status slots_round(ba_ctx* ctx) {
   SlotTable& T = ctx->slots;
+  const int gen = ctx->tune_gen.load();
+  if (T.graph.exec && T.tune_gen != gen) {  // launch parameters changed since the capture
+    cudaGraphExecDestroy(T.graph.exec);
+    T.graph.exec = nullptr;
+    free_probe(T.graph.probe);
+    T.graph.probe = nullptr;
+  }
   if (!T.graph.exec) {
+    apply_tune(ctx, T.bv);
+    T.tune_gen = gen;
     cudaGraph_t graph = nullptr;
     note_direct(ctx);
     take_captured_launches();
@@ -1955,6 +2023,13 @@ BA_API ba_status ba_init(ba_ctx** out, const ba_config* cfg) {
   ctx->timing = (cfg->flags & BA_FLAG_KERNEL_TIMING) != 0;
   ctx->inject = (cfg->flags & BA_FLAG_INJECT_COPY_TIMEOUT) ? kInjectCopyTimeout : 0;
   ctx->big_fp64 = (cfg->flags & BA_FLAG_BIG_FP64_FACTOR) != 0;
+  if (cfg->tune_table) {  // this GPU's entry of the tuning table, if it has one
+    cudaDeviceProp prop{};
+    ba_tune t{};
+    if (cudaGetDeviceProperties(&prop, cfg->device) == cudaSuccess &&
+        ba_tune_table_lookup(cfg->tune_table, prop.name, prop.multiProcessorCount, cfg->precision, &t) == BA_OK)
+      ctx->tune = tune_from_abi(t);
+  }
   if (cfg->stream) {
     ctx->stream = (cudaStream_t)cfg->stream;
   } else {
@@ -2548,6 +2623,181 @@ BA_API ba_status ba_get_cluster_info(ba_ctx* ctx, ba_cluster_id id, ba_cluster_i
   Cluster* c = find_cluster(ctx, id);
   if (!c) return BA_ERR_NOT_FOUND;
   *out = c->info;
+  return BA_OK;
+}
+
+BA_API ba_status ba_get_tune(ba_ctx* ctx, ba_tune* out) {
+  if (!ctx || !out) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  *out = tune_to_abi(ctx->tune);
+  return BA_OK;
+}
+
+BA_API ba_status ba_set_tune(ba_ctx* ctx, const ba_tune* t) {
+  if (!ctx || !t) return BA_ERR_INVALID;
+  std::string why;
+  if (!tune_in_range(*t, ctx->mixed, &why)) return set_err(ctx, BA_ERR_INVALID, why);
+  std::lock_guard<std::mutex> g(ctx->api_mu);
+  for (auto& kv : ctx->clusters)
+    if (kv.second->in_service) return set_err(ctx, BA_ERR_INVALID, "a cluster is in service");
+  ctx->tune = tune_from_abi(*t);
+  // plans hold graphs captured with the old launch shapes: rebuilt on demand
+  for (auto& kv : ctx->plans) {
+    ctx->mem -= kv.second->dbuf_bytes;
+    free_plan(ctx, kv.second);
+  }
+  ctx->plans.clear();
+  ctx->tune_gen.fetch_add(1);  // and the serving graph is captured again before its next round
+  return BA_OK;
+}
+
+BA_API ba_status ba_autotune(ba_ctx* ctx, const ba_cluster_desc* descs, int32_t n, int32_t iters, ba_tune* out) {
+  if (!ctx || !descs || n <= 0 || iters <= 0 || !out) return BA_ERR_INVALID;
+  std::vector<ba_cluster_id> ids;
+  int created = -1;  // chunk_tiles the current tuning clusters were created with
+  bool has_big = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto destroy_all = [&]() {
+    for (ba_cluster_id id : ids) ba_destroy_cluster(ctx, id);
+    ids.clear();
+  };
+  auto finish = [&](ba_status st) {
+    destroy_all();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return st;
+  };
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return finish(set_err(ctx, BA_ERR_CUDA, "ba_autotune: event creation failed"));
+  // device time of one batch solve with t: the fastest of three after a warm-up
+  auto measure = [&](const TuneParams& t, double* ms) -> ba_status {
+    ba_tune bt = tune_to_abi(t);
+    ba_status st = ba_set_tune(ctx, &bt);
+    if (st != BA_OK) return st;
+    const int ct = t.chunk_tiles > 0 ? t.chunk_tiles : chunk_tiles(ctx->mixed);
+    if (ct != created) {
+      destroy_all();
+      for (int i = 0; i < n; ++i) {
+        ba_cluster_id id = 0;
+        st = ba_create_cluster(ctx, &descs[i], &id);
+        if (st != BA_OK) return st;
+        ids.push_back(id);
+        ba_cluster_info info{};
+        if (ba_get_cluster_info(ctx, id, &info) == BA_OK && info.n_free > kMaxFreeSmall) has_big = true;
+      }
+      created = ct;
+    }
+    double best = 1e300;
+    for (int rep = 0; rep < 4; ++rep) {
+      st = ba_reset_batch(ctx, ids.data(), n);
+      if (st != BA_OK) return st;
+      CUDA_TRY(ctx, cudaEventRecord(e0, ctx->stream));
+      st = ba_solve_batch(ctx, ids.data(), n, iters, nullptr, nullptr);
+      if (st != BA_OK) return st;
+      CUDA_TRY(ctx, cudaEventRecord(e1, ctx->stream));
+      CUDA_TRY(ctx, cudaEventSynchronize(e1));
+      float el = 0.f;
+      CUDA_TRY(ctx, cudaEventElapsedTime(&el, e0, e1));
+      if (rep > 0) best = std::min(best, (double)el);  // rep 0 captures the graphs
+    }
+    *ms = best;
+    return BA_OK;
+  };
+  TuneParams cur;  // the defaults
+  cur.chunk_tiles = chunk_tiles(ctx->mixed);
+  double cur_ms = 0.0;
+  ba_status st = measure(cur, &cur_ms);
+  if (st != BA_OK) return finish(st);
+  const double ms_default = cur_ms;
+  // one parameter at a time; a candidate replaces the current value only
+  // when it is faster by more than 1 % (timing noise keeps the default)
+  struct Knob {
+    int TuneParams::*field;
+    std::vector<int> cands;
+    bool big_only;
+  };
+  const bool mixed = ctx->mixed;
+  const std::vector<Knob> knobs = {
+      {&TuneParams::chunk_tiles, mixed ? std::vector<int>{12, 8} : std::vector<int>{6, 4}, false},
+      {&TuneParams::lin_ctas_per_sm, {4, 2}, false},
+      {&TuneParams::back_ctas_per_sm, {8, 4}, false},
+      {&TuneParams::factor_nb, {4, 16}, false},
+      {&TuneParams::factor_threads, {384, 256}, false},
+      {&TuneParams::big_panel_w, {2, 8}, true},
+  };
+  for (const Knob& k : knobs) {
+    if (k.big_only && !has_big) continue;
+    TuneParams best = cur;
+    double best_ms = cur_ms;
+    for (int v : k.cands) {
+      TuneParams t = cur;
+      t.*(k.field) = v;
+      double ms = 0.0;
+      st = measure(t, &ms);
+      if (st != BA_OK) return finish(st);
+      if (ms < best_ms * 0.99) {
+        best = t;
+        best_ms = ms;
+      }
+    }
+    cur = best;
+    cur_ms = best_ms;
+  }
+  ba_tune bt = tune_to_abi(cur);
+  st = ba_set_tune(ctx, &bt);
+  if (st != BA_OK) return finish(st);
+  bt.ms_default = ms_default;
+  bt.ms_tuned = cur_ms;
+  *out = bt;
+  return finish(BA_OK);
+}
+
+BA_API ba_status ba_tune_table_lookup(const char* path, const char* gpu_name, int32_t sm_count, int32_t precision,
+                                      ba_tune* out) {
+  if (!path || !gpu_name || !out || (precision != BA_FP64 && precision != BA_MIXED)) return BA_ERR_INVALID;
+  std::ifstream f(path);
+  if (!f) return BA_ERR_NOT_FOUND;
+  std::string want(gpu_name);
+  std::replace(want.begin(), want.end(), ' ', '_');
+  const std::string prec = precision == BA_MIXED ? "mixed" : "fp64";
+  bool found = false;
+  ba_tune result{};
+  std::string line;
+  while (std::getline(f, line)) {
+    const size_t hash = line.find('#');
+    if (hash != std::string::npos) line.resize(hash);
+    std::istringstream in(line);
+    std::string name, pr;
+    int sms = 0;
+    if (!(in >> name >> sms >> pr)) continue;
+    if (name != want || sms != sm_count || pr != prec) continue;
+    ba_tune t = tune_to_abi(TuneParams{});
+    std::string kv;
+    while (in >> kv) {
+      const size_t eq = kv.find('=');
+      if (eq == std::string::npos) return BA_ERR_INVALID;
+      const std::string key = kv.substr(0, eq), val = kv.substr(eq + 1);
+      char* end = nullptr;
+      const double v = std::strtod(val.c_str(), &end);
+      if (end == val.c_str() || *end != '\0') return BA_ERR_INVALID;
+      if (key == "chunk_tiles") t.chunk_tiles = (int)v;
+      else if (key == "lin_ctas_per_sm") t.lin_ctas_per_sm = (int)v;
+      else if (key == "back_ctas_per_sm") t.back_ctas_per_sm = (int)v;
+      else if (key == "factor_nb") t.factor_nb = (int)v;
+      else if (key == "factor_threads") t.factor_threads = (int)v;
+      else if (key == "big_panel_w") t.big_panel_w = (int)v;
+      else if (key == "ms_default") t.ms_default = v;
+      else if (key == "ms_tuned") t.ms_tuned = v;
+      else return BA_ERR_INVALID;
+    }
+    std::string why;
+    if (!tune_in_range(t, precision == BA_MIXED, &why)) return BA_ERR_INVALID;
+    result = t;
+    found = true;  // the last matching line wins
+  }
+  if (!found) return BA_ERR_NOT_FOUND;
+  *out = result;
   return BA_OK;
 }
 

@@ -395,7 +395,6 @@ __global__ void __launch_bounds__(256) k_big_split(const DevCluster* dcl) {
 }
 
 constexpr int kPanelThreads = 1024;
-constexpr int kPanelW = 4;  // columns a warp factors between two block-wide barriers
 constexpr int kPld = kBigNB + 1;  // padded leading dimension of the shared blocks
 
 // Block column k: the diagonal block factored and inverted by every CTA
@@ -407,11 +406,11 @@ constexpr int kPld = kBigNB + 1;  // padded leading dimension of the shared bloc
 // as the identity and receives the same row operations as the matrix, so
 // that row j of W, scaled by 1 / L(j, j) once the column j is final, is row
 // j of L^-1 (forward substitution of L X = I, one row at a time).  Columns
-// go in blocks of kPanelW: one warp factors a block (the pivots' reciprocal
-// square roots, the block's columns of L, its rows of X) with warp-level
-// synchronisation only, then the whole CTA applies the block's rank-kPanelW
-// update below it: two block-wide barriers per block.
-__global__ void __launch_bounds__(kPanelThreads) k_big_panel(const DevCluster* dcl, int k) {
+// go in blocks of pw (a divisor of 32): one warp factors a block (the
+// pivots' reciprocal square roots, the block's columns of L, its rows of X)
+// with warp-level synchronisation only, then the whole CTA applies the
+// block's rank-pw update below it: two block-wide barriers per block.
+__global__ void __launch_bounds__(kPanelThreads) k_big_panel(const DevCluster* dcl, int k, int pw) {
   const DevCluster& C = *dcl;
   const int n = 6 * C.n_free, r0 = kBigNB * k, nb = min(kBigNB, n - r0);
   float* Fh = df_hi(C);
@@ -450,13 +449,13 @@ __global__ void __launch_bounds__(kPanelThreads) k_big_panel(const DevCluster* d
   __shared__ float Dh[kBigNB], Dl[kBigNB];  // L(j, j), kept apart until the sweep ends
   __syncthreads();
   bool fail = false;
-  // blocks of kPanelW columns: warp 0 factors the block's columns (lane =
-  // row, warp-level synchronisation only) and finishes the block's rows of
-  // X; then every thread applies the block's rank-kPanelW update to the rows
-  // below it (entry (tr, tc) of the trailing matrix, or of W left of it)
+  // blocks of pw columns: warp 0 factors the block's columns (lane = row,
+  // warp-level synchronisation only) and finishes the block's rows of X;
+  // then every thread applies the block's rank-pw update to the rows below
+  // it (entry (tr, tc) of the trailing matrix, or of W left of it)
   const int tr = tid >> 5, tc = tid & 31, lane = tid & 31;
-  for (int jb = 0; jb < kBigNB; jb += kPanelW) {
-    const int je = jb + kPanelW - 1;  // last column of the block
+  for (int jb = 0; jb < kBigNB; jb += pw) {
+    const int je = jb + pw - 1;  // last column of the block
     if (tid < 32) {
       for (int j = jb; j <= je; ++j) {
         dfl d{Lh[j][j], Ll[j][j]};
@@ -503,8 +502,7 @@ __global__ void __launch_bounds__(kPanelThreads) k_big_panel(const DevCluster* d
     if (tr > je && tc <= tr) {
       if (tc <= je) {  // W(tr, tc) -= sum_j L(tr, j) X(j, tc) over the block's columns
         dfl a{Wh[tr][tc], Wl[tr][tc]};
-#pragma unroll
-        for (int i = 0; i < kPanelW; ++i) {
+        for (int i = 0; i < pw; ++i) {
           const int j = jb + i;
           if (j >= tc) a = df_fms(a, dfl{Lh[tr][j], Ll[tr][j]}, dfl{Wh[j][tc], Wl[j][tc]});
         }
@@ -512,8 +510,7 @@ __global__ void __launch_bounds__(kPanelThreads) k_big_panel(const DevCluster* d
         Wl[tr][tc] = a.lo;
       } else {  // L(tr, tc) -= sum_j L(tr, j) L(tc, j)
         dfl a{Lh[tr][tc], Ll[tr][tc]};
-#pragma unroll
-        for (int i = 0; i < kPanelW; ++i) a = df_fms(a, dfl{Lh[tr][jb + i], Ll[tr][jb + i]}, dfl{Lh[tc][jb + i], Ll[tc][jb + i]});
+        for (int i = 0; i < pw; ++i) a = df_fms(a, dfl{Lh[tr][jb + i], Ll[tr][jb + i]}, dfl{Lh[tc][jb + i], Ll[tc][jb + i]});
         Lh[tr][tc] = a.hi;
         Ll[tr][tc] = a.lo;
       }
@@ -828,7 +825,7 @@ void launch_big_solve(const BigRef& b, bool mixed, int refine_steps, int assembl
     LAUNCH(KK_FACTOR, st, k_big_split<<<std::min(n, num_sms() * 8), 256, 0, st>>>(b.d));
     for (int k = 0; k < nblk; ++k) {
       const int m = b.below[k];
-      LAUNCH(KK_FACTOR, st, k_big_panel<<<1 + m, kPanelThreads, 0, st>>>(b.d, k));
+      LAUNCH(KK_FACTOR, st, k_big_panel<<<1 + m, kPanelThreads, 0, st>>>(b.d, k, b.panel_w));
       if (m > 0) {
         const dim3 grid(m, (kBigNB * m + kUpdM - 1) / kUpdM);
         LAUNCH(KK_FACTOR, st, k_big_update_tc<<<grid, kUpdThreads, kUpdSmem, st>>>(b.d, k, m));

@@ -199,6 +199,21 @@ struct BatchView {
   int total_tiles, total_chunks, total_items;
   int max_n;             // largest 6 * n_free in the batch
   int inject;            // failure injection for tests (kInject* bits); 0 in normal use
+  // launch parameters the autotuner chooses (TuneParams)
+  int lin_ctas_per_sm;   // linearise+Schur grid: at most this many CTAs per SM (grid-stride beyond)
+  int back_ctas_per_sm;  // back-substitution grid: at most this many CTAs per SM
+  int factor_nb;         // panel width of the shared-memory Cholesky
+  int factor_threads;    // threads of the shared-memory factor CTA
+};
+
+// Launch and presort parameters chosen by the autotuner (ba_tune in ba.h).
+struct TuneParams {
+  int chunk_tiles = 0;       // tiles per linearise+Schur chunk (0: the precision's maximum)
+  int lin_ctas_per_sm = 8;
+  int back_ctas_per_sm = 16;
+  int factor_nb = 8;
+  int factor_threads = 512;
+  int big_panel_w = 4;       // columns of a block of the global-memory solver's panel factorisation
 };
 
 // kInjectCopyTimeout: the mixed linearise+Schur kernel waits for its first
@@ -258,6 +273,7 @@ struct BigRef {
   double* F;               // device [n][n]
   std::vector<int> below;  // per block column of kBigNB: row blocks below it inside the envelope
   bool tc = true;          // tensor-core double-float factor (else the binary64 CUDA-core one)
+  int panel_w = 4;         // column-block width of the panel factorisation (1, 2, 4, 8, 16 or 32)
 };
 void launch_big_solve(const BigRef& b, bool mixed, int refine_steps, int assemble_only, cudaStream_t st);
 // rows of the digit buffer of a system of order n: n rounded up to kBigNB, plus

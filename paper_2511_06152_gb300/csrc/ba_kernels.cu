@@ -913,14 +913,10 @@ size_t factor_smem_bytes(int max_n) {
 #endif
 constexpr int kFactorThreads = BA_FACTOR_THREADS;  // threads of the shared-memory factor CTA
 
-#ifndef BA_FACTOR_NB
-#define BA_FACTOR_NB 8
-#endif
-constexpr int kFactorNB = BA_FACTOR_NB;  // panel width of the blocked factorisation
 constexpr int kSolveNB = 32;   // diagonal block of the triangular solves (one warp)
 
 // Blocked right-looking Cholesky A = L L^T of the packed lower matrix in
-// shared memory, by the whole CTA.  Per column j of a panel of kFactorNB
+// shared memory, by the whole CTA.  Per column j of a panel of nb
 // columns: warp 0 takes the pivot (square root and its reciprocal, once) and
 // the scaled entries of the panel's own rows; then every thread scales its
 // rows of column j and updates the panel's remaining columns.  After the
@@ -930,10 +926,11 @@ constexpr int kSolveNB = 32;   // diagonal block of the triangular solves (one w
 // no fill outside the envelope, so every product with an entry left of it
 // is zero and is skipped (the sums are unchanged).
 // Sets *fail (shared) when a pivot is not positive.
-__device__ void chol_blocked(double* A, int n, double* inv_diag, double* colbuf, const int* efirst, int* fail) {
+__device__ void chol_blocked(double* A, int n, double* inv_diag, double* colbuf, const int* efirst, int* fail,
+                             int nb) {
   const int tid = threadIdx.x, bs = blockDim.x;
-  for (int k0 = 0; k0 < n; k0 += kFactorNB) {
-    const int k1 = min(k0 + kFactorNB, n);
+  for (int k0 = 0; k0 < n; k0 += nb) {
+    const int k1 = min(k0 + nb, n);
     for (int j = k0; j < k1; ++j) {
       if (tid < 32) {
         const int lane = tid;
@@ -1051,14 +1048,15 @@ __device__ void chol_panel_p(double* A, int n, int k1, int k2, double* inv_diag,
   }
 }
 
-__device__ void chol_lookahead(double* A, int n, double* inv_diag, double* colbuf, const int* efirst, int* fail) {
+__device__ void chol_lookahead(double* A, int n, double* inv_diag, double* colbuf, const int* efirst, int* fail,
+                               int nb) {
   const int tid = threadIdx.x;
   const bool gp = tid < 128;
-  if (gp) chol_panel_p(A, n, 0, min(kFactorNB, n), inv_diag, colbuf, efirst, fail);
+  if (gp) chol_panel_p(A, n, 0, min(nb, n), inv_diag, colbuf, efirst, fail);
   __syncthreads();
-  for (int k0 = 0; k0 < n; k0 += kFactorNB) {
+  for (int k0 = 0; k0 < n; k0 += nb) {
     if (*fail) return;
-    const int k1 = min(k0 + kFactorNB, n), k2 = min(k1 + kFactorNB, n);
+    const int k1 = min(k0 + nb, n), k2 = min(k1 + nb, n);
     if (gp) {
       if (k1 < n) {
         // the next panel's columns c in [k1, k2), rows i >= c, with panel p
@@ -1283,9 +1281,9 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_solve(BatchView bv, i
     for (int idx = tid; idx < n; idx += bs) efirst[idx] = 6 * C.env_first[idx / 6];
     __syncthreads();
 #ifdef BA_FACTOR_NO_LOOKAHEAD
-    if (!fail) chol_blocked(A, n, inv_diag, t, efirst, &fail);
+    if (!fail) chol_blocked(A, n, inv_diag, t, efirst, &fail, bv.factor_nb);
 #else
-    if (!fail) chol_lookahead(A, n, inv_diag, t, efirst, &fail);
+    if (!fail) chol_lookahead(A, n, inv_diag, t, efirst, &fail, bv.factor_nb);
 #endif
     __syncthreads();
     const int status = fail ? BA_STATUS_NOT_PD : 0;
@@ -2027,7 +2025,8 @@ static size_t chunk_smem_bytes(bool mixed) {
 template <bool MIXED>
 static void launch_lin_schur(const BatchView& bv, int diag, cudaStream_t st) {
   LAUNCH(KK_LIN_SCHUR, st,
-         k_lin_schur<MIXED><<<grid_for(bv.total_chunks, 1, num_sms() * 8), kChunkThreads, chunk_smem_bytes(MIXED),
+         k_lin_schur<MIXED><<<grid_for(bv.total_chunks, 1, num_sms() * bv.lin_ctas_per_sm), kChunkThreads,
+                              chunk_smem_bytes(MIXED),
                               st>>>(bv, diag));
 }
 
@@ -2043,10 +2042,11 @@ static void launch_iteration_t(const BatchView& bv, int refine_steps, cudaStream
   launch_lin_schur<MIXED>(bv, 0, st);
   launch_partial_reduce<MIXED>(bv, st);
   const size_t smem = factor_smem_bytes(bv.max_n);
-  LAUNCH(KK_FACTOR, st, k_factor_solve<MIXED><<<grid_for(bv.n, 1, 65535), kFactorThreads, smem, st>>>(bv, refine_steps, 0));
+  LAUNCH(KK_FACTOR, st,
+         k_factor_solve<MIXED><<<grid_for(bv.n, 1, 65535), bv.factor_threads, smem, st>>>(bv, refine_steps, 0));
   if (big)
     for (const BigRef& b : *big) launch_big_solve(b, MIXED, refine_steps, 0, st);
-  LAUNCH(KK_BACKSUB, st, k_backsub_cost<MIXED><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
+  LAUNCH(KK_BACKSUB, st, k_backsub_cost<MIXED><<<grid_for(bv.total_tiles, 8, sms * bv.back_ctas_per_sm), 256, 0, st>>>(bv));
   LAUNCH(KK_LM_UPDATE, st, k_lm_update<MIXED><<<grid_for(bv.n, 1, 65535), 1024, 0, st>>>(bv));
 }
 
@@ -2061,7 +2061,7 @@ static void launch_grad_norm_t(const BatchView& bv, double* out, cudaStream_t st
   launch_lin_schur<MIXED>(bv, 1, st);
   launch_partial_reduce<MIXED>(bv, st);
   LAUNCH(KK_FACTOR, st,
-         k_factor_solve<MIXED><<<grid_for(bv.n, 1, 65535), kFactorThreads, factor_smem_bytes(bv.max_n), st>>>(bv, 0, 1));
+         k_factor_solve<MIXED><<<grid_for(bv.n, 1, 65535), bv.factor_threads, factor_smem_bytes(bv.max_n), st>>>(bv, 0, 1));
   if (big)
     for (const BigRef& b : *big) launch_big_solve(b, MIXED, 0, 1, st);
   LAUNCH(KK_OTHER, st, k_grad_norm<<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv, out));
