@@ -555,6 +555,14 @@ BA_API ba_status ba_destroy_cluster(ba_ctx* ctx, ba_cluster_id id);
  * afterwards. */
 BA_API ba_status ba_shutdown(ba_ctx* ctx);
 
+/* Measure this GPU's binary32 fused multiply-add rate (the denominator of
+ * the roofline of the binary32-bound kernels): one launch of ctas_per_sm x
+ * SMs CTAs of 512 threads, each thread running 16 independent FMA chains
+ * for `iters` steps, timed with CUDA events on the context's stream after
+ * one warm-up launch.  *tflops = 2 x 16 x iters x threads / time; *ms = the
+ * launch's time.  Blocking.  BA_ERR_INVALID for NULL outputs or sizes < 1. */
+BA_API ba_status ba_probe_fp32_fma(ba_ctx* ctx, int32_t ctas_per_sm, int32_t iters, double* tflops, double* ms);
+
 /* Static text of a status code (never NULL). */
 BA_API const char* ba_status_string(ba_status s);
 

@@ -155,7 +155,7 @@ EXPORTS = ["ba_init", "ba_create_cluster", "ba_linearize", "ba_solve_step", "ba_
            "ba_reset_batch", "ba_submit", "ba_poll", "ba_get_state", "ba_get_state_batch", "ba_reprojection_errors",
            "ba_memory_in_use",
            "ba_launch_count", "ba_kernel_stats", "ba_cost_noalloc", "ba_warm_start", "ba_transition", "ba_footprints", "ba_footprint_overlaps", "ba_patch_transfer_poses", "ba_patch_transfer_planar", "ba_get_cluster_info", "ba_presort_host", "ba_destroy_cluster", "ba_shutdown",
-           "ba_get_tune", "ba_set_tune", "ba_autotune", "ba_tune_table_lookup",
+           "ba_get_tune", "ba_set_tune", "ba_autotune", "ba_tune_table_lookup", "ba_probe_fp32_fma",
            "ba_status_string", "ba_last_error"]
 
 _lib = None
@@ -211,6 +211,7 @@ def lib(build: bool = True):
                                       ctypes.POINTER(ba_tune)]
             L.ba_tune_table_lookup.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.POINTER(ba_tune)]
+            L.ba_probe_fp32_fma.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, _dp, _dp]
             L.ba_destroy_cluster.argtypes = [vp, u64]
             L.ba_shutdown.argtypes = [vp]
             L.ba_status_string.argtypes = [ctypes.c_int32]
@@ -335,6 +336,12 @@ class Context:
         out = ba_lin_info()
         _check(self.L.ba_linearize(self.h, cid, ctypes.byref(out)), self.h, "ba_linearize")
         return {"cost": out.cost, "grad_inf": out.grad_inf, "n_free": out.n_free}
+
+    def probe_fp32_fma(self, ctas_per_sm=4, iters=4096):
+        tf, ms = ctypes.c_double(), ctypes.c_double()
+        _check(self.L.ba_probe_fp32_fma(self.h, int(ctas_per_sm), int(iters), ctypes.byref(tf), ctypes.byref(ms)),
+               self.h, "ba_probe_fp32_fma")
+        return tf.value, ms.value
 
     def get_tune(self):
         t = ba_tune()

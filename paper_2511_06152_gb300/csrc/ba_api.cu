@@ -2801,6 +2801,32 @@ BA_API ba_status ba_tune_table_lookup(const char* path, const char* gpu_name, in
   return BA_OK;
 }
 
+BA_API ba_status ba_probe_fp32_fma(ba_ctx* ctx, int32_t ctas_per_sm, int32_t iters, double* tflops, double* ms) {
+  if (!ctx || !tflops || !ms || ctas_per_sm < 1 || iters < 1) return BA_ERR_INVALID;
+  CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  float* sink = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(ctx, cudaMallocAsync((void**)&sink, sizeof(float), ctx->stream));
+  CUDA_TRY(ctx, cudaEventCreate(&e0));
+  CUDA_TRY(ctx, cudaEventCreate(&e1));
+  const int ctas = ctas_per_sm * num_sms();
+  launch_fma_probe(ctas, iters, sink, ctx->stream);  // warm-up
+  cudaEventRecord(e0, ctx->stream);
+  launch_fma_probe(ctas, iters, sink, ctx->stream);
+  cudaEventRecord(e1, ctx->stream);
+  note_direct(ctx);
+  const cudaError_t e = cudaEventSynchronize(e1);
+  float el = 0.f;
+  if (e == cudaSuccess) cudaEventElapsedTime(&el, e0, e1);
+  cudaFreeAsync(sink, ctx->stream);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess || !(el > 0.f)) return set_err(ctx, BA_ERR_CUDA, "ba_probe_fp32_fma: timing failed");
+  *ms = el;
+  *tflops = 2.0 * 16.0 * (double)iters * 512.0 * (double)ctas / (el * 1e-3) / 1e12;
+  return BA_OK;
+}
+
 BA_API ba_status ba_destroy_cluster(ba_ctx* ctx, ba_cluster_id id) {
   if (!ctx) return BA_ERR_INVALID;
   std::lock_guard<std::mutex> g(ctx->api_mu);

@@ -322,6 +322,7 @@ void launch_patch_poses(int n, const double* p0, const double* intr0, const doub
 void launch_patch_planar(int n, const double* q0, const double* c, const double* g0, int m, const double* theta,
                          const double* g, double* q, cudaStream_t st);
 size_t factor_smem_bytes(int max_n);
+void launch_fma_probe(int ctas, int iters, float* sink, cudaStream_t st);
 int chunk_obs(bool mixed);
 int chunk_tiles(bool mixed);
 

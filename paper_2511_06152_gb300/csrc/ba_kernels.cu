@@ -2082,6 +2082,28 @@ void launch_export_state(const DevCluster* dcl, const DevCluster& hcl, bool mixe
   LAUNCH(KK_OTHER, st, k_export_state<<<grid_for(items, 256, num_sms() * 8), 256, 0, st>>>(dcl, mixed, R, T, X));
 }
 
+// binary32 FMA-rate probe: 16 independent chains per thread (enough to
+// cover the pipe's latency), the result stored only if it comes out as an
+// impossible value so that nothing is optimised away
+__global__ void __launch_bounds__(512) k_fma_probe(int iters, float seed, float* sink) {
+  float a[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = seed + (float)(threadIdx.x + i);
+  const float m = 0.999999f, c = 1e-7f;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = __fmaf_rn(a[i], m, c);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) s += a[i];
+  if (s == -1.0f) *sink = s;
+}
+
+void launch_fma_probe(int ctas, int iters, float* sink, cudaStream_t st) {
+  LAUNCH(KK_OTHER, st, k_fma_probe<<<ctas, 512, 0, st>>>(iters, 1.0f, sink));
+}
+
 cudaError_t set_kernel_attributes(int max_n) {
   const size_t smem = factor_smem_bytes(max_n);
   cudaError_t e = cudaFuncSetAttribute(k_factor_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
