@@ -373,7 +373,7 @@ def serving_leg(args, ba, stream, flights, rate=None, n_requests=None):
         ex.shutdown(wait=True, cancel_futures=True)
     kst = ctx.kernel_stats(reset=True)
     ctx.close()
-    rounds = max(1, kst["lm_update"][1])
+    rounds = max(1, kst["backsub_cost"][1])  # one back-substitution launch per round
     round_kernels = {k: v[0] / rounds for k, v in kst.items() if v[1]}
     lat = np.array(lat)
     pct = {k: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))} for k, v in parts.items() if v}

@@ -360,8 +360,13 @@ __global__ void __launch_bounds__(512) k_big_finish(const DevCluster* dcl) {
     lm->prior_new = s1;
     lm->status = lm->dev_error ? lm->dev_error : (fail ? BA_STATUS_NOT_PD : 0);
     lm->dev_error = 0;
+    lm->tiles_done = 0;  // the back-substitution counts its tiles from here
     *C.bflag = 0;
   }
+  __syncthreads();
+  // a cluster without observations has no back-substitution tile to count:
+  // its LM step is taken here
+  if (C.n_tiles == 0 && lm->active && tid < 32) lm_update_warp<MIXED>(C, tid);
 }
 
 // ------------------------------------------------------------------ tensor-core factorisation

@@ -301,4 +301,83 @@ __device__ __forceinline__ bool obs_linearize(const Real* Rm, Real dx, Real dy, 
   return true;
 }
 
+// The LM decision of one cluster, by one warp, once every tile of its
+// back-substitution is done: F(x + d) and pred from the tiles' partial sums
+// (in k_cost_init's summation order), the gain ratio,
+// accept or reject, Nielsen's update of mu and nu, the step record; on
+// acceptance in binary64 the camera records of the new state.
+template <bool MIXED>
+__device__ __forceinline__ void lm_update_warp(const DevCluster& C, int lane) {
+  LmState* lm = C.lm;
+  const bool ok = lm->status == 0;
+  double Fo = 0.0, pp = 0.0;
+  if (ok) {
+    // the order of k_cost_init's sum over a 256-thread CTA (thread t of warp
+    // t / 32 adds tiles t, t + 256, ... in turn; a warp tree; the 8 warps in
+    // order), so that F carried from one iteration to the next equals F
+    // evaluated afresh at the start of a solve, bit for bit
+    const double2* tp = reinterpret_cast<const double2*>(C.tilepart);
+    for (int w = 0; w < kCostInitThreads / 32; ++w) {
+      double a = 0.0, b = 0.0;
+      for (int i = 32 * w + lane; i < C.n_tiles; i += kCostInitThreads) {
+        const double2 v = tp[i];
+        a += v.x;
+        b += v.y;
+      }
+      Fo += warp_sum(a);
+      pp += warp_sum(b);
+    }
+  }
+  int accepted = 0, cur = 0;
+  if (lane == 0) {
+    const double F = lm->F;
+    const double Fn = ok ? Fo + lm->prior_new : F;
+    const double pred = ok ? 0.5 * (pp + lm->pred_cam) : 0.0;
+    const double gain = pred > 0.0 ? (F - Fn) / pred : 0.0;
+    accepted = ok && pred > 0.0 && gain > 0.0;
+    const double mu_used = lm->mu;
+    if (accepted) {
+      const double tt = 2.0 * gain - 1.0;
+      const double fct = 1.0 - tt * tt * tt;
+      lm->mu = mu_used * (fct > 1.0 / 3.0 ? fct : 1.0 / 3.0);
+      lm->nu = 2.0;
+      lm->cur ^= 1;
+      lm->F = Fn;
+      lm->n_accepted += 1;
+    } else {
+      lm->mu = mu_used * lm->nu;
+      lm->nu *= 2.0;
+    }
+    if (C.trace_cap > 0) {
+      StepRec& r = C.trace[lm->iter % C.trace_cap];
+      r.accepted = accepted;
+      r.status = lm->status;
+      r.F_before = F;
+      r.F_after = Fn;
+      r.predicted = pred;
+      r.gain = gain;
+      r.mu_used = mu_used;
+      r.mu = lm->mu;
+      r.nu = lm->nu;
+    }
+    lm->iter += 1;
+    if (lm->iter >= lm->iters_target) lm->active = 0;
+    lm->pt_fail = 0;
+    lm->mu_f = (float)lm->mu;
+    cur = lm->cur;
+  }
+  accepted = __shfl_sync(BA_FULL_MASK, accepted, 0);
+  cur = __shfl_sync(BA_FULL_MASK, cur, 0);
+  if (!MIXED && accepted) {  // refresh the binary64 camera records for the new state
+    double* cr = (double*)C.camreal;
+    for (int k = lane; k < C.n_cams; k += 32) {
+      const double* R = C.R + ((size_t)cur * C.n_cams + k) * 9;
+      const double* T = C.T + ((size_t)cur * C.n_cams + k) * 3;
+      double* o = cr + (size_t)kCamReal * k;
+      for (int i = 0; i < 9; ++i) o[i] = R[i];
+      for (int i = 0; i < 3; ++i) o[9 + i] = T[i];
+    }
+  }
+}
+
 }  // namespace bagpu

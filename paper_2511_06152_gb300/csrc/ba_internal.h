@@ -42,6 +42,7 @@ constexpr double kDiagMax = 1e32;
 constexpr double kMinDepth = 1e-6;
 constexpr int BA_STATUS_NOT_PD = -3;  // same value as BA_ERR_NOT_PD in ba.h
 constexpr int kTraceCap = 256;
+constexpr int kCostInitThreads = 256;  // threads of k_cost_init's CTA (its sums' order)
 // double-float camera record (floats): high words of R [0, 9), T.hi [9, 12),
 // T.lo [12, 15), f.hi 15, k1 k2 p1 p2 .hi [16, 20), free flag 20, pad; then
 // the low words of R [24, 33), f.lo 33, k1 k2 p1 p2 .lo [34, 38), pad to 40
@@ -95,6 +96,9 @@ struct LmState {
   float mu_f;        // mu rounded to binary32 (mixed-path kernels)
   int needs_init;    // F must be evaluated at the current state before the next iteration
   int dev_error;     // a kernel gave up on a bounded wait this iteration (kDevErrTimeout); rejects the step
+  int tiles_done;    // back-substitution tiles finished this iteration; the warp that finishes the last
+                     // one takes the cluster's LM decision (zeroed by the factor kernels)
+  int pad1;
 };
 
 constexpr int kDevErrTimeout = -4;  // = BA_ERR_TIMEOUT

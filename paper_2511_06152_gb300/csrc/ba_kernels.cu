@@ -17,11 +17,14 @@
 //   k_factor_solve   per cluster (FP64): assemble S = U* - W V*^-1 W^T and
 //                    rhs = g_c - W V*^-1 g_p with priors and damping, blocked
 //                    Cholesky in shared memory, solve, iterative refinement,
-//                    candidate camera poses.
+//                    candidate camera poses.  (Clusters of more than 32 free
+//                    images: the global-memory solver of ba_big.cu.)
 //   k_backsub_cost   per tile: linearise again (same arithmetic, same values),
 //                    dX = M^T (q - sum_k Z_k^T dc_k), candidate points, cost
-//                    at the candidate and the predicted reduction.
-//   k_lm_update      per cluster: gain ratio, accept/reject, Nielsen update.
+//                    at the candidate and the predicted reduction; the warp
+//                    that finishes a cluster's last tile takes its LM step:
+//                    gain ratio, accept/reject, Nielsen update.
+//   Four launches per LM iteration.
 //
 // Precision.  MIXED = false: every step in binary64.  MIXED = true: the
 // per-observation linearisation, the Schur reductions and the back-
@@ -30,8 +33,9 @@
 // per observation in double-float and summed in binary64; the reduced
 // camera system is assembled, factored and refined in binary64.
 //
-// Every sum runs in an order fixed by the cluster's presorted tables; there
-// are no atomics.
+// Every sum runs in an order fixed by the cluster's presorted tables; the
+// only atomic is the back-substitution's per-cluster tile counter, which
+// chooses the warp that takes the LM step and enters no sum.
 #include <cuda_runtime.h>
 #include <stdio.h>
 
@@ -851,11 +855,47 @@ struct AccD {
 template <typename Real> struct AccOf { using T = AccD; };
 template <> struct AccOf<float> { using T = AccF; };
 
-// Warp per free camera or camera pair of a cluster: sum its chunk partials in
-// chunk order (lane i owns element i and i + 32).
+// Item `it` of a cluster (a free camera, it < n_free, or a camera pair): sum
+// its chunk partials in chunk order, by one warp (lane i owns element i and
+// i + 32), into camsum / pairsum.
+template <typename Real>
+__device__ __forceinline__ void reduce_item_partials(const DevCluster& C, int it, int lane) {
+  using Acc = typename AccOf<Real>::T;
+  const bool cam = it < C.n_free;
+  const int key = cam ? it : it - C.n_free;
+  const int width = cam ? 39 : 36, stride = cam ? kCamPart : kPairPart;
+  const int* slots = cam ? C.cam_slots : C.pair_slots;
+  const int b = cam ? C.cam_slot_begin[key] : C.pair_slot_begin[key];
+  const int e = cam ? C.cam_slot_begin[key + 1] : C.pair_slot_begin[key + 1];
+  const Real* part = (const Real*)(cam ? C.campart : C.pairpart);
+  double* out = cam ? C.camsum + (size_t)kCamPart * key : C.pairsum + (size_t)kPairPart * key;
+  const bool two = lane + 32 < width;
+  Acc v0, v1;
+  int p = b;
+  for (; p + 4 <= e; p += 4) {  // four independent loads in flight, added in slot order
+    const Real* a0 = part + (size_t)stride * slots[p];
+    const Real* a1 = part + (size_t)stride * slots[p + 1];
+    const Real* a2 = part + (size_t)stride * slots[p + 2];
+    const Real* a3 = part + (size_t)stride * slots[p + 3];
+    const Real x0 = lane < width ? a0[lane] : Real(0), x1 = lane < width ? a1[lane] : Real(0);
+    const Real x2 = lane < width ? a2[lane] : Real(0), x3 = lane < width ? a3[lane] : Real(0);
+    const Real y0 = two ? a0[lane + 32] : Real(0), y1 = two ? a1[lane + 32] : Real(0);
+    const Real y2 = two ? a2[lane + 32] : Real(0), y3 = two ? a3[lane + 32] : Real(0);
+    v0.add(x0); v0.add(x1); v0.add(x2); v0.add(x3);
+    v1.add(y0); v1.add(y1); v1.add(y2); v1.add(y3);
+  }
+  for (; p < e; ++p) {
+    const Real* a0 = part + (size_t)stride * slots[p];
+    if (lane < width) v0.add(a0[lane]);
+    if (two) v1.add(a0[lane + 32]);
+  }
+  if (lane < width) out[lane] = v0.get();
+  if (two) out[lane + 32] = v1.get();
+}
+
+// Warp per free camera or camera pair of every cluster of the batch.
 template <typename Real>
 __global__ void __launch_bounds__(256) k_partial_reduce(BatchView bv) {
-  using Acc = typename AccOf<Real>::T;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -864,37 +904,7 @@ __global__ void __launch_bounds__(256) k_partial_reduce(BatchView bv) {
     const int s = find_slot(bv.item_pre, bv.n, g);
     const DevCluster& C = bv.cl[s];
     if (!C.lm->active) continue;
-    const int it = g - bv.item_pre[s];
-    const bool cam = it < C.n_free;
-    const int key = cam ? it : it - C.n_free;
-    const int width = cam ? 39 : 36, stride = cam ? kCamPart : kPairPart;
-    const int* slots = cam ? C.cam_slots : C.pair_slots;
-    const int b = cam ? C.cam_slot_begin[key] : C.pair_slot_begin[key];
-    const int e = cam ? C.cam_slot_begin[key + 1] : C.pair_slot_begin[key + 1];
-    const Real* part = (const Real*)(cam ? C.campart : C.pairpart);
-    double* out = cam ? C.camsum + (size_t)kCamPart * key : C.pairsum + (size_t)kPairPart * key;
-    const bool two = lane + 32 < width;
-    Acc v0, v1;
-    int p = b;
-    for (; p + 4 <= e; p += 4) {  // four independent loads in flight, added in slot order
-      const Real* a0 = part + (size_t)stride * slots[p];
-      const Real* a1 = part + (size_t)stride * slots[p + 1];
-      const Real* a2 = part + (size_t)stride * slots[p + 2];
-      const Real* a3 = part + (size_t)stride * slots[p + 3];
-      const Real x0 = lane < width ? a0[lane] : Real(0), x1 = lane < width ? a1[lane] : Real(0);
-      const Real x2 = lane < width ? a2[lane] : Real(0), x3 = lane < width ? a3[lane] : Real(0);
-      const Real y0 = two ? a0[lane + 32] : Real(0), y1 = two ? a1[lane + 32] : Real(0);
-      const Real y2 = two ? a2[lane + 32] : Real(0), y3 = two ? a3[lane + 32] : Real(0);
-      v0.add(x0); v0.add(x1); v0.add(x2); v0.add(x3);
-      v1.add(y0); v1.add(y1); v1.add(y2); v1.add(y3);
-    }
-    for (; p < e; ++p) {
-      const Real* a0 = part + (size_t)stride * slots[p];
-      if (lane < width) v0.add(a0[lane]);
-      if (two) v1.add(a0[lane + 32]);
-    }
-    if (lane < width) out[lane] = v0.get();
-    if (two) out[lane + 32] = v1.get();
+    reduce_item_partials<Real>(C, g - bv.item_pre[s], lane);
   }
 }
 
@@ -1218,6 +1228,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_solve(BatchView bv, i
     const double* Rc = C.R + (size_t)cur * nc * 9;
     const double* Tc = C.T + (size_t)cur * nc * 3;
 
+    if (tid == 0) lm->tiles_done = 0;  // the back-substitution counts its tiles from here
     // per-camera sums (k_partial_reduce)
     for (int idx = tid; idx < nf * 39; idx += bs) {
       const int f = idx / 39, e = idx - 39 * f;
@@ -1341,6 +1352,10 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_solve(BatchView bv, i
       lm->dev_error = 0;
     }
     __syncthreads();
+    // a cluster without observations has no back-substitution tile to count:
+    // its LM step is taken here
+    if (!assemble_only && C.n_tiles == 0 && tid < 32) lm_update_warp<MIXED>(C, tid);
+    __syncthreads();
   }
 }
 
@@ -1350,18 +1365,60 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_solve(BatchView bv, i
 // linearised again (the same arithmetic as in k_lin_schur) instead of reading
 // per-observation records back from memory.
 template <bool MIXED>
+__device__ void backsub_tile(const DevCluster& C, LmState* lm, int local, int lane);
+
+// add a warp's count of finished tiles to its cluster's total; the warp that
+// completes the total takes the cluster's LM decision
+template <bool MIXED>
+__device__ __forceinline__ void publish_tiles(const DevCluster& C, int count, int lane) {
+  int done = 0;
+  if (lane == 0) {
+    __threadfence();  // this warp's partial sums before the count
+    done = atomicAdd(&C.lm->tiles_done, count) + count;
+  }
+  done = __shfl_sync(BA_FULL_MASK, done, 0);
+  if (done == C.n_tiles) {
+    __threadfence();
+    lm_update_warp<MIXED>(C, lane);
+  }
+}
+
+template <bool MIXED>
 __global__ void __launch_bounds__(256) k_backsub_cost(BatchView bv) {
   using Real = typename RealOf<MIXED>::T;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   const int total = bv.tot[0];
-  for (int g = warp; g < total; g += nwarps) {
-    const int s = find_slot(bv.tile_pre, bv.n, g);
+  // each warp takes a contiguous run of tiles, so that its tiles mostly
+  // belong to one cluster: it counts them per cluster and publishes the
+  // count once per cluster it leaves (one fence and one atomic each); the
+  // warp whose count completes a cluster takes the cluster's LM decision,
+  // every other tile's partial sums being written by then
+  const int per = (total + nwarps - 1) / nwarps;
+  const int g0 = warp * per, g1 = min(total, g0 + per);
+  int s = g0 < g1 ? find_slot(bv.tile_pre, bv.n, g0) : 0;
+  int pending = 0;
+  for (int g = g0; g < g1; ++g) {
+    while (g >= bv.tile_pre[s + 1]) {  // the next cluster: publish the count of this one
+      if (pending) publish_tiles<MIXED>(bv.cl[s], pending, lane);
+      pending = 0;
+      ++s;
+    }
     const DevCluster& C = bv.cl[s];
     LmState* lm = C.lm;
-    if (!lm->active || lm->status != 0) continue;
-    const int local = g - bv.tile_pre[s];
+    if (!lm->active) continue;
+    if (lm->status == 0) backsub_tile<MIXED>(C, lm, g - bv.tile_pre[s], lane);
+    ++pending;
+  }
+  if (pending) publish_tiles<MIXED>(bv.cl[s], pending, lane);
+}
+
+// back-substitution and candidate cost of one tile (one warp)
+template <bool MIXED>
+__device__ void backsub_tile(const DevCluster& C, LmState* lm, int local, int lane) {
+  using Real = typename RealOf<MIXED>::T;
+  {
     const Tile tl = C.tiles[local];
     TileLin<MIXED> L;
     linearize_tile<MIXED, false, true>(C, lm, tl, lane, false, L, global_view(C, lm->cur));
@@ -1611,74 +1668,6 @@ __global__ void __launch_bounds__(256) k_cost_init(BatchView bv) {
 }
 
 // ------------------------------------------------------------------ K6
-
-template <bool MIXED>
-__global__ void __launch_bounds__(1024) k_lm_update(BatchView bv) {
-  __shared__ double red[64];
-  __shared__ int s_cur, s_act;
-  for (int s = blockIdx.x; s < bv.n; s += gridDim.x) {
-    const DevCluster& C = bv.cl[s];
-    LmState* lm = C.lm;
-    if (!lm->active) continue;
-    const bool ok = lm->status == 0;
-    double Fo = 0.0, pp = 0.0;
-    if (ok) {
-      const double2 t = block_sum_tiles2(C, red);
-      Fo = t.x;
-      pp = t.y;
-    }
-    if (threadIdx.x == 0) {
-      const double F = lm->F;
-      const double Fn = ok ? Fo + lm->prior_new : F;
-      const double pred = ok ? 0.5 * (pp + lm->pred_cam) : 0.0;
-      const double gain = pred > 0.0 ? (F - Fn) / pred : 0.0;
-      const int accepted = ok && pred > 0.0 && gain > 0.0;
-      const double mu_used = lm->mu;
-      if (accepted) {
-        const double tt = 2.0 * gain - 1.0;
-        const double fct = 1.0 - tt * tt * tt;
-        lm->mu = mu_used * (fct > 1.0 / 3.0 ? fct : 1.0 / 3.0);
-        lm->nu = 2.0;
-        lm->cur ^= 1;
-        lm->F = Fn;
-        lm->n_accepted += 1;
-      } else {
-        lm->mu = mu_used * lm->nu;
-        lm->nu *= 2.0;
-      }
-      if (C.trace_cap > 0) {
-        StepRec& r = C.trace[lm->iter % C.trace_cap];
-        r.accepted = accepted;
-        r.status = lm->status;
-        r.F_before = F;
-        r.F_after = Fn;
-        r.predicted = pred;
-        r.gain = gain;
-        r.mu_used = mu_used;
-        r.mu = lm->mu;
-        r.nu = lm->nu;
-      }
-      lm->iter += 1;
-      if (lm->iter >= lm->iters_target) lm->active = 0;
-      lm->pt_fail = 0;
-      lm->mu_f = (float)lm->mu;
-      s_cur = lm->cur;
-      s_act = accepted;
-    }
-    __syncthreads();
-    if (!MIXED && s_act) {  // refresh the binary64 camera records for the new state
-      double* cr = (double*)C.camreal;
-      for (int k = threadIdx.x; k < C.n_cams; k += blockDim.x) {
-        const double* R = C.R + ((size_t)s_cur * C.n_cams + k) * 9;
-        const double* T = C.T + ((size_t)s_cur * C.n_cams + k) * 3;
-        double* o = cr + (size_t)kCamReal * k;
-        for (int i = 0; i < 9; ++i) o[i] = R[i];
-        for (int i = 0; i < 3; ++i) o[9 + i] = T[i];
-      }
-    }
-    __syncthreads();
-  }
-}
 
 // ------------------------------------------------------------------ diagnostics
 
@@ -2005,7 +1994,7 @@ template <bool MIXED>
 static void launch_cost_init_t(const BatchView& bv, cudaStream_t st) {
   const int sms = num_sms();
   LAUNCH(KK_COST_TILES, st, k_cost_tiles<MIXED><<<grid_for(bv.total_tiles, 8, sms * 16), 256, 0, st>>>(bv));
-  LAUNCH(KK_COST_INIT, st, k_cost_init<<<grid_for(bv.n, 1, 65535), 256, 0, st>>>(bv));
+  LAUNCH(KK_COST_INIT, st, k_cost_init<<<grid_for(bv.n, 1, 65535), kCostInitThreads, 0, st>>>(bv));
 }
 
 void launch_cost_init(const BatchView& bv, bool mixed, cudaStream_t st) {
@@ -2030,6 +2019,7 @@ static void launch_lin_schur(const BatchView& bv, int diag, cudaStream_t st) {
                               st>>>(bv, diag));
 }
 
+
 template <bool MIXED>
 static void launch_partial_reduce(const BatchView& bv, cudaStream_t st) {
   using Real = typename RealOf<MIXED>::T;
@@ -2047,7 +2037,6 @@ static void launch_iteration_t(const BatchView& bv, int refine_steps, cudaStream
   if (big)
     for (const BigRef& b : *big) launch_big_solve(b, MIXED, refine_steps, 0, st);
   LAUNCH(KK_BACKSUB, st, k_backsub_cost<MIXED><<<grid_for(bv.total_tiles, 8, sms * bv.back_ctas_per_sm), 256, 0, st>>>(bv));
-  LAUNCH(KK_LM_UPDATE, st, k_lm_update<MIXED><<<grid_for(bv.n, 1, 65535), 1024, 0, st>>>(bv));
 }
 
 void launch_iteration(const BatchView& bv, bool mixed, int refine_steps, cudaStream_t st,

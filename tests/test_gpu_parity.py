@@ -286,3 +286,15 @@ def test_chunks_with_only_fixed_camera_observations(ba):
         rms = rms_inliers(ctx.reprojection_errors(cid), c["outlier"])
     assert abs(rms - ref_rms) < 1e-3
     assert sg.centre_error(T, S.T) < 1e-3
+
+
+def test_fp64_step_parity_cluster_without_observations(ba):
+    """Three free images with priors and no observation at all (no
+    back-substitution tile): the LM step is still taken every iteration and
+    matches the oracle (the poses move to the priors)."""
+    c = sg.tiny_cluster(808, 1, 3, 20)
+    c = {key: (v.copy() if isinstance(v, np.ndarray) else v) for key, v in c.items()}
+    c["T0"] = np.asarray(c["T0"]) + np.array([0.3, -0.2, 0.1])
+    c.update(n_pts=0, n_obs=0, X0=np.zeros((0, 3)), obs_cam=np.zeros(0, np.int32), obs_pt=np.zeros(0, np.int32),
+             obs_uv=np.zeros((0, 2)), outlier=np.zeros(0, bool))
+    assert _step_parity(ba, c, 4, min_steps=2) >= 2
