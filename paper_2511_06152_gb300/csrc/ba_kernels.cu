@@ -669,6 +669,10 @@ __global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed
   Real* lanepart = srec;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int total = bv.tot[1];
+  // a contiguous run of chunks per CTA: neighbouring chunks (Morton order of
+  // the points) share images and points in the caches
+  const int per = (total + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int g0 = (int)blockIdx.x * per, g1 = min(total, g0 + per);
   // mixed path: the next chunk's observations and points are copied into
   // shared memory by the copy engine while this chunk is reduced
   Stage S{};
@@ -689,10 +693,10 @@ __global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed
       fence_barrier_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0 && (int)blockIdx.x < total) stage_issue(bv, blockIdx.x, S, 0);
+    if (threadIdx.x == 0 && g0 < g1) stage_issue(bv, g0, S, 0);
   }
   int b = 0;  // table buffer of the current chunk (mixed path)
-  for (int g = blockIdx.x; g < total; g += gridDim.x, b ^= 1) {
+  for (int g = g0; g < g1; ++g, b ^= 1) {
     int s;
     Chunk ch;
     if constexpr (!MIXED) {
@@ -713,7 +717,7 @@ __global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed
         // this CTA has still to process (their steps are rejected), wait once
         // more for the copies in flight, and stop
         if (threadIdx.x == 0) {
-          for (int h = g; h < total; h += gridDim.x) {
+          for (int h = g; h < g1; ++h) {
             LmState* hl = bv.cl[find_slot(bv.chunk_pre, bv.n, h)].lm;
             hl->dev_error = kDevErrTimeout;
             hl->pt_fail = 1;
@@ -753,7 +757,7 @@ __global__ void __launch_bounds__(kChunkThreads, MIXED ? kLinSchurMinBlocksMixed
     }
     __syncthreads();
     if constexpr (MIXED) {  // staging is free: start the copies of this CTA's next chunk
-      if (threadIdx.x == 0 && g + (int)gridDim.x < total) stage_issue(bv, g + gridDim.x, S, b ^ 1);
+      if (threadIdx.x == 0 && g + 1 < g1) stage_issue(bv, g + 1, S, b ^ 1);
     }
     if (!active) continue;
     // 2. Schur reductions of the chunk.  Jobs: each free camera (sum of
