@@ -65,6 +65,9 @@ def parse():
                     help="further arrival rates (req/s) of the serving sweep, comma-separated ('' for none)")
     ap.add_argument("--sweep-requests", type=int, default=600, help="requests per rate of the serving sweep")
     ap.add_argument("--tune", action="store_true", help="run ba_autotune on the workload first and report its table line")
+    ap.add_argument("--large-only", type=int, default=0, metavar="POINTS",
+                    help="only the 400-image large block with this many points: --iters mixed LM iterations from "
+                         "the initial state, timed with CUDA events (a small case for profiling)")
     ap.add_argument("--tune-clusters", type=int, default=256, help="clusters of the workload ba_autotune times")
     ap.add_argument("--sweep-flights", type=int, default=32, help="flights of the serving sweep (the first "
                     "--serving-flights of them serve the main leg)")
@@ -547,7 +550,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x ma
 # ncu capture of the current kernel on 32 clusters of the same mix (120.73 MB for
 # 2,452,644 observations); scaled to a launch by its observations.  Set to
 # None whenever the kernel changes until it is captured again.
-LIN_SCHUR_DRAM_BYTES_PER_OBS = None
+LIN_SCHUR_DRAM_BYTES_PER_OBS = (81.5232e6 + 38.791936e6) / 2452644
 FP64_PEAK_TFLOPS = 1.25                               # nominal dense FP64
 TUNE_DEFAULTS = dict(chunk_tiles=0, lin_ctas_per_sm=8, back_ctas_per_sm=16, factor_nb=8, factor_threads=512,
                      big_panel_w=4)
@@ -609,6 +612,29 @@ def main():
         run_reference(args)
         return
     rank, world, local = dist_env()
+    if args.large_only:
+        c = sg.cluster_c5(n_points=args.large_only)
+        import torch
+        import paper_2511_06152_gb300 as ba
+        torch.cuda.set_device(local)
+        stream = torch.cuda.Stream()
+        with ba.Context(device=local, precision=ba.BA_MIXED, stream=stream.cuda_stream,
+                        flags=ba.BA_FLAG_KERNEL_TIMING) as cx:
+            cid = cx.create_cluster(c)
+            cx.run(cid, args.iters, trace=False)  # graph capture
+            cx.reset(cid)
+            cx.kernel_stats(reset=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tr = cx.run(cid, args.iters)
+            e1.record(stream)
+            e1.synchronize()
+            k = cx.kernel_stats(reset=True)
+        print(json.dumps({"large_block_points": args.large_only, "observations": int(c["n_obs"]), "iters": args.iters,
+                          "ms_per_iter": e0.elapsed_time(e1) / args.iters,
+                          "kernel_ms_per_iter": {a: v[0] / args.iters for a, v in k.items() if v[1]},
+                          "accepted": int(sum(x["accepted"] for x in tr))}), flush=True)
+        return
     if args.serving_only:
         import multiprocessing as mp
         with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
