@@ -962,62 +962,74 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
       v = (v | (v << 1)) & 0x55555555u;
       return v;
     };
-    // stable LSD radix sort of the codes, 8 bits per pass, starting from the
-    // caller's order (so ties stay in caller order)
-    std::vector<uint32_t> code(np), code2(np);
-    std::vector<int> idx(np), idx2(np);
+    // stable LSD radix sort of the codes, 11 bits per pass (three passes,
+    // histograms of all three digits in one sweep), on packed (code, caller
+    // index) keys, starting from the caller's order (so ties stay in caller
+    // order)
+    std::vector<uint64_t> key(np), key2(np);
+    uint32_t hist[3][2049] = {{0}};
     for (int j = 0; j < np; ++j) {
       const uint32_t qx = (uint32_t)((X[3 * (size_t)j] - xmin) * sx), qy = (uint32_t)((X[3 * (size_t)j + 1] - ymin) * sy);
-      code[j] = spread(qx) | (spread(qy) << 1);
-      idx[j] = j;
+      const uint32_t code = spread(qx) | (spread(qy) << 1);
+      key[j] = ((uint64_t)code << 32) | (uint32_t)j;
+      ++hist[0][(code & 2047u) + 1];
+      ++hist[1][((code >> 11) & 2047u) + 1];
+      ++hist[2][(code >> 22) + 1];
     }
-    for (int shift = 0; shift < 32; shift += 8) {
-      int cnt[257] = {0};
-      for (int j = 0; j < np; ++j) ++cnt[((code[j] >> shift) & 255u) + 1];
-      for (int b = 0; b < 256; ++b) cnt[b + 1] += cnt[b];
+    for (int d = 0; d < 3; ++d) {
+      uint32_t* c = hist[d];
+      for (int b = 0; b < 2048; ++b) c[b + 1] += c[b];
+      const int shift = 32 + 11 * d;
       for (int j = 0; j < np; ++j) {
-        const int dst = cnt[(code[j] >> shift) & 255u]++;
-        code2[dst] = code[j];
-        idx2[dst] = idx[j];
+        const uint64_t k = key[j];
+        key2[c[(k >> shift) & 2047u]++] = k;
       }
-      code.swap(code2);
-      idx.swap(idx2);
+      key.swap(key2);
     }
     for (int i = 0; i < np; ++i) {
-      perm[i] = idx[i];
-      inv[idx[i]] = i;
+      const int j = (int)(uint32_t)key[i];
+      perm[i] = j;
+      inv[j] = i;
     }
   }
 
-  // point-major order: counting sort by internal point, then by camera within a point
-  std::vector<int> cnt((size_t)np + 1, 0), pm(no);
-  for (int i = 0; i < no; ++i) cnt[inv[opt[i]] + 1]++;
-  for (int j = 0; j < np; ++j) cnt[j + 1] += cnt[j];
-  std::vector<int> pt_start(cnt);
+  // point-major order: counting sort by internal point, then by camera within
+  // a point; the camera and internal point of each point-major observation
+  // are written in the same scatter
+  std::vector<int> cnt((size_t)np + 1, 0), pm(no), pcam(no), ppt(no);
   {
+    std::vector<int> okey(no);  // internal point of each observation
+    for (int i = 0; i < no; ++i) {
+      const int j = inv[opt[i]];
+      okey[i] = j;
+      cnt[j + 1]++;
+    }
+    for (int j = 0; j < np; ++j) cnt[j + 1] += cnt[j];
     std::vector<int> pos(cnt.begin(), cnt.end() - 1);
-    for (int i = 0; i < no; ++i) pm[pos[inv[opt[i]]]++] = i;
+    for (int i = 0; i < no; ++i) {
+      const int j = okey[i], q = pos[j]++;
+      pm[q] = i;
+      pcam[q] = ocam[i];
+      ppt[q] = j;
+    }
   }
+  std::vector<int> pt_start(cnt);
   for (int j = 0; j < np; ++j) {
     const int s = pt_start[j], e = pt_start[j + 1];
     if (e - s > kMaxTrack) return set_err(ctx, BA_ERR_INVALID, "a point has more than 32 observations");
-    for (int a = s + 1; a < e; ++a) {
-      const int v = pm[a];
+    for (int a = s + 1; a < e; ++a) {  // insertion sort by camera (stable), carrying the observation
+      const int v = pm[a], vc = pcam[a];
       int b = a - 1;
-      while (b >= s && ocam[pm[b]] > ocam[v]) {
+      while (b >= s && pcam[b] > vc) {
         pm[b + 1] = pm[b];
+        pcam[b + 1] = pcam[b];
         --b;
       }
       pm[b + 1] = v;
+      pcam[b + 1] = vc;
     }
     for (int a = s + 1; a < e; ++a)
-      if (ocam[pm[a]] == ocam[pm[a - 1]]) return set_err(ctx, BA_ERR_INVALID, "repeated (camera, point) observation");
-  }
-  // camera of each point-major observation, and its point
-  std::vector<int> pcam(no), ppt(no);
-  for (int p = 0; p < no; ++p) {
-    pcam[p] = ocam[pm[p]];
-    ppt[p] = inv[opt[pm[p]]];
+      if (pcam[a] == pcam[a - 1]) return set_err(ctx, BA_ERR_INVALID, "repeated (camera, point) observation");
   }
 
   // tiles: runs of whole points with at most 32 observations
