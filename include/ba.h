@@ -91,7 +91,10 @@ typedef struct {
   uint64_t hbm_budget_bytes; /* device memory the context may hold; 0 = unlimited */
   int32_t precision;         /* BA_FP64 or BA_MIXED */
   int32_t n_slots;           /* clusters the serving scheduler runs at once (ba_submit); 0 = 64 */
-  int32_t refine_steps;      /* iterative-refinement passes after the Cholesky solve; <0 = default 1 */
+  int32_t refine_steps;      /* iterative-refinement passes against the binary64 S after the Cholesky
+                                solve; <0 = the default: 1 in BA_FP64, 0 in BA_MIXED (whose system
+                                carries binary32 rounding from the per-observation terms, far above
+                                the double-float factor's) */
   int32_t flags;             /* BA_FLAG_* */
   const char* tune_table;    /* NULL, or the path of a tuning table (ba_tune_table_lookup): the
                                 entry for this GPU and precision, if any, is applied at ba_init */
@@ -109,9 +112,17 @@ typedef struct {
  * tensor cores by default: the factor kept as double-float (binary32 pairs),
  * its dense products computed exactly from 8-bit digit matrices on the bf16
  * tensor cores (Ozaki's error-free splitting), the solution refined against
- * S in binary64.  This flag selects the binary64 CUDA-core factorisation
- * instead (same envelope, same refinement), for comparisons. */
+ * S in binary64 by the configured refinement passes.  This flag selects the
+ * binary64 CUDA-core factorisation instead (same envelope, same refinement),
+ * for comparisons. */
 #define BA_FLAG_BIG_FP64_FACTOR 4
+/* Reduced camera systems of up to 32 free images are factored in shared
+ * memory by one CTA: in binary64 in BA_FP64, in double-float on the binary32
+ * pipe in BA_MIXED (the system equilibrated by powers of two), then the
+ * configured refinement passes against the binary64 S.  This flag selects
+ * the double-float factorisation in BA_FP64 too, for comparisons (no effect
+ * in BA_MIXED). */
+#define BA_FLAG_SMALL_DF_FACTOR 8
 
 /* Kernel kinds reported by ba_kernel_stats, in this order. */
 #define BA_KERNEL_LIN_SCHUR 0      /* per chunk: residuals, Jacobians, point blocks, Schur partial sums */
@@ -340,9 +351,10 @@ BA_API ba_status ba_linearize(ba_ctx* ctx, ba_cluster_id id, ba_lin_info* out);
 
 /* One Levenberg-Marquardt iteration of the local BA of Sec. 3.2 (Eq. 7) on
  * one cluster: linearise, eliminate the points (Schur complement), damp,
- * factor and solve the reduced camera system in binary64 with one refinement
- * step, back-substitute the points, evaluate F at the candidate, accept or
- * reject it and update the damping.  Blocking; *out (host, may be NULL)
+ * factor and solve the reduced camera system (BA_FP64: binary64 with one
+ * refinement pass; BA_MIXED: double-float), back-substitute the points,
+ * evaluate F at the candidate, accept or reject it and update the damping.
+ * Blocking; *out (host, may be NULL)
  * receives the step record.  A reduced or point system that is not positive
  * definite is a rejected step with status BA_ERR_NOT_PD in the record, not a
  * failed call.  BA_ERR_NOT_FOUND for an unknown id, BA_ERR_INVALID for a

@@ -33,6 +33,7 @@ BA_PTR_DEVICE = 1
 BA_FLAG_KERNEL_TIMING = 1
 BA_FLAG_INJECT_COPY_TIMEOUT = 2  # failure injection for tests: the staged-copy wait expires
 BA_FLAG_BIG_FP64_FACTOR = 4      # large reduced systems: binary64 CUDA-core factor instead of the tensor cores
+BA_FLAG_SMALL_DF_FACTOR = 8      # BA_FP64: small reduced systems factored in double-float, as in BA_MIXED
 KERNEL_KINDS = ["lin_schur", "partial_reduce", "factor", "backsub_cost", "lm_update", "cost_tiles", "cost_init",
                 "other"]
 

@@ -117,6 +117,7 @@ struct ba_ctx {
   bool timing = false;
   int inject = 0;  // failure-injection bits for the kernels (BA_FLAG_INJECT_*)
   bool big_fp64 = false;  // global-memory solver: binary64 CUDA-core factor instead of the tensor-core one
+  bool small_df = false;  // BA_FP64: shared-memory factor in double-float (as in the mixed path)
   TuneParams tune;        // launch and presort parameters (ba_set_tune, ba_autotune, the tuning table)
   std::atomic<int> tune_gen{0};  // bumped by every change of tune: the serving graph is captured again
   std::mutex stats_mu;  // kernel statistics (API threads and the scheduler)
@@ -335,6 +336,7 @@ void apply_tune(const ba_ctx* ctx, BatchView& bv) {
   bv.back_ctas_per_sm = ctx->tune.back_ctas_per_sm;
   bv.factor_nb = ctx->tune.factor_nb;
   bv.factor_threads = ctx->tune.factor_threads;
+  bv.factor_df = ctx->mixed || ctx->small_df;
 }
 
 void free_plan(ba_ctx* ctx, Plan* p) {
@@ -2031,10 +2033,14 @@ BA_API ba_status ba_init(ba_ctx** out, const ba_config* cfg) {
   ctx->budget = cfg->hbm_budget_bytes;
   ctx->mixed = cfg->precision == BA_MIXED;
   ctx->n_slots = cfg->n_slots > 0 ? cfg->n_slots : 64;
-  ctx->refine = cfg->refine_steps >= 0 ? cfg->refine_steps : 1;
+  // mixed: the double-float factor's rounding lies far below the binary32
+  // rounding of the per-observation terms the system is built from, so a
+  // binary64 refinement pass would not change the step beyond that
+  ctx->refine = cfg->refine_steps >= 0 ? cfg->refine_steps : (ctx->mixed ? 0 : 1);
   ctx->timing = (cfg->flags & BA_FLAG_KERNEL_TIMING) != 0;
   ctx->inject = (cfg->flags & BA_FLAG_INJECT_COPY_TIMEOUT) ? kInjectCopyTimeout : 0;
   ctx->big_fp64 = (cfg->flags & BA_FLAG_BIG_FP64_FACTOR) != 0;
+  ctx->small_df = (cfg->flags & BA_FLAG_SMALL_DF_FACTOR) != 0;
   if (cfg->tune_table) {  // this GPU's entry of the tuning table, if it has one
     cudaDeviceProp prop{};
     ba_tune t{};

@@ -173,4 +173,31 @@ __device__ __forceinline__ dfl df_from_d(double v) {
   return dfl{hi, lo};
 }
 
+// v 2^e as a double-word (binary64 v, integer e): the same value as
+// df_from_d(ldexp(v, e)), formed with integer operations when v 2^e is a
+// normal binary64 number with a binary32-normal low word (|v 2^e| within about
+// 2^-73 .. 2^127), which spares the binary64 pipe; the conversion itself
+// otherwise.  hi = v 2^e rounded to 24 bits (to nearest, ties to even, on the
+// integer significand), lo = the exact remainder rounded to 24 bits.
+__device__ __forceinline__ dfl df_from_d_pow2(double v, int e) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  if ((b << 1) == 0ull) return dfl{0.0f, 0.0f};  // +-0
+  const int ex = (int)((b >> 52) & 0x7ffull), E = ex + e;
+  if (ex == 0 || ex == 0x7ff || E < 950 || E > 1150) return df_from_d(ldexp(v, e));
+  const unsigned long long m = (b & 0xfffffffffffffull) | 0x10000000000000ull;  // 53-bit significand
+  unsigned int q = (unsigned int)(m >> 29);
+  const unsigned int rem = (unsigned int)(m & 0x1fffffffull);
+  if (rem > 0x10000000u || (rem == 0x10000000u && (q & 1u))) ++q;  // q <= 2^24
+  const int r = (int)((long long)m - ((long long)q << 29));         // |r| <= 2^28
+  const float ph = __int_as_float((E - 1023 - 23 + 127) << 23);    // 2^(E - 1046), normal for E in range
+  const float pl = __int_as_float((E - 1023 - 52 + 127) << 23);    // 2^(E - 1075)
+  float hi = __uint2float_rn(q) * ph;  // exact
+  float lo = __int2float_rn(r) * pl;   // r rounded to 24 bits, scaled exactly
+  if (b >> 63) {
+    hi = -hi;
+    lo = -lo;
+  }
+  return dfl{hi, lo};
+}
+
 }  // namespace bagpu

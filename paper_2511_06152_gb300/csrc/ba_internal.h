@@ -208,6 +208,7 @@ struct BatchView {
   int back_ctas_per_sm;  // back-substitution grid: at most this many CTAs per SM
   int factor_nb;         // panel width of the shared-memory Cholesky
   int factor_threads;    // threads of the shared-memory factor CTA
+  int factor_df;         // 1: the shared-memory factor in double-float (mixed path, or BA_FLAG_SMALL_DF_FACTOR)
 };
 
 // Launch and presort parameters chosen by the autotuner (ba_tune in ba.h).

@@ -1207,6 +1207,238 @@ __device__ void chol_solve_blocked(const double* A, const double* inv_diag, cons
   }
 }
 
+// ---- the same factorisation and solves in double-float (mixed path)
+//
+// The binary64 pipe of GB300 runs at 1/59 of the binary32 rate, and it bounds
+// the binary64 factor of the largest clusters (about 2 DFMA per clock per
+// SM).  The mixed path therefore factors an equilibrated copy of the system
+// in double-float on the binary32 pipe: A' = E A E with E = diag(2^e_i)
+// (powers of two, exact), e_i chosen so that A'(i, i) lies in [1/2, 4); the
+// diagonal near 1 keeps every entry of the factor well inside the binary32
+// exponent range whatever the scale of A.  A x = b is solved as A' y = E b,
+// x = E y; the iterative refinement against the binary64 S (unchanged)
+// removes the factor's rounding (double-float, about 2^-47 relative per
+// operation).  Same blocking, look-ahead and envelope skipping as the binary64
+// functions above; a pivot that is not positive sets *fail.
+
+// A (binary64, packed lower, envelope entries) -> A' = E A E as double-float
+// in the same bytes; escale[i] = e_i.  Entries left of a row's envelope are
+// zero in both representations.
+__device__ void chol_to_scaled_df(double* A, int n, const int* efirst, int* escale) {
+  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = bs >> 5;
+  for (int i = tid; i < n; i += bs) {
+    const double d = A[pk(i, i)];
+    escale[i] = (d > 0.0 && d < INFINITY) ? -(ilogb(d) / 2) : 0;
+  }
+  __syncthreads();
+  dfl* Af = reinterpret_cast<dfl*>(A);
+  for (int i = wid; i < n; i += nw) {
+    const int ei = escale[i];
+    for (int j = efirst[i] + lane; j <= i; j += 32) Af[pk(i, j)] = df_from_d_pow2(A[pk(i, j)], ei + escale[j]);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ dfl shfl_df(dfl v, int src) {
+  return dfl{__shfl_sync(BA_FULL_MASK, v.hi, src), __shfl_sync(BA_FULL_MASK, v.lo, src)};
+}
+
+// factor columns [k1, k2) (already updated by every earlier panel), group P only
+__device__ void chol_panel_p_df(dfl* A, int n, int k1, int k2, dfl* inv_diag, dfl* colbuf, const int* efirst,
+                                int* fail) {
+  const int tid = threadIdx.x;
+  for (int j = k1; j < k2; ++j) {
+    if (tid < 32) {
+      dfl inv{0.0f, 0.0f};
+      if (tid == 0) {
+        dfl d = A[pk(j, j)];
+        if (!(d.hi > 0.0f)) {
+          *fail = 1;
+          d = dfl{1.0f, 0.0f};
+        }
+        inv = df_rsqrt(d);
+        A[pk(j, j)] = df_mul(d, inv);
+        inv_diag[j] = inv;
+      }
+      inv = shfl_df(inv, 0);
+      if (j + 1 + tid < k2) colbuf[j + 1 + tid] = df_mul(A[pk(j + 1 + tid, j)], inv);
+    }
+    bar_group_p();
+    const dfl inv = inv_diag[j];
+    for (int i = j + 1 + tid; i < n; i += 128) {
+      if (efirst[i] > j) continue;  // L(i, j) = 0
+      const dfl l = df_mul(A[pk(i, j)], inv);
+      A[pk(i, j)] = l;
+      const int cmax = min(i, k2 - 1);
+      for (int c = j + 1; c <= cmax; ++c) A[pk(i, c)] = df_fms(A[pk(i, c)], l, colbuf[c]);
+    }
+    bar_group_p();
+  }
+}
+
+__device__ void chol_lookahead_df(dfl* A, int n, dfl* inv_diag, dfl* colbuf, const int* efirst, int* fail, int nb) {
+  const int tid = threadIdx.x;
+  const bool gp = tid < 128;
+  if (gp) chol_panel_p_df(A, n, 0, min(nb, n), inv_diag, colbuf, efirst, fail);
+  __syncthreads();
+  for (int k0 = 0; k0 < n; k0 += nb) {
+    if (*fail) return;
+    const int k1 = min(k0 + nb, n), k2 = min(k1 + nb, n);
+    if (gp) {
+      if (k1 < n) {
+        const int w = k2 - k1;
+        for (int u = tid; u < (n - k1) * w; u += 128) {
+          const int i = k1 + u / w, c = k1 + u % w;
+          if (c > i) continue;
+          const int qlo = max(k0, max(efirst[i], efirst[c]));
+          if (qlo >= k1) continue;
+          Dot2 s;
+          for (int q = qlo; q < k1; ++q) s.add(A[pk(i, q)], A[pk(c, q)]);
+          A[pk(i, c)] = df_sub(A[pk(i, c)], s.get());
+        }
+        bar_group_p();
+        chol_panel_p_df(A, n, k1, k2, inv_diag, colbuf, efirst, fail);
+      }
+    } else if (k2 < n) {
+      const int tt = tid - 128, nt_thr = blockDim.x - 128;
+      const int m = n - k2;
+      const int nt = (m + 3) >> 2;
+      const int ntiles = nt * (nt + 1) / 2;
+      for (int t = tt; t < ntiles; t += nt_thr) {
+        int bi = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+        while (bi * (bi + 1) / 2 > t) --bi;
+        const int bc = t - bi * (bi + 1) / 2;
+        const int i0 = k2 + 4 * bi, c0 = k2 + 4 * bc;
+        int fi = n, fc = n;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          if (i0 + a < n) fi = min(fi, efirst[i0 + a]);
+          if (c0 + a < n) fc = min(fc, efirst[c0 + a]);
+        }
+        const int qlo = max(k0, max(fi, fc));
+        if (qlo >= k1) continue;
+        Dot2 acc[4][4];
+        for (int q = qlo; q < k1; ++q) {
+          dfl li[4], lc[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            li[a] = i0 + a < n ? A[pk(i0 + a, q)] : dfl{0.0f, 0.0f};
+            lc[a] = c0 + a < n ? A[pk(c0 + a, q)] : dfl{0.0f, 0.0f};
+          }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b].add(li[a], lc[b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int i = i0 + a, c = c0 + b;
+            if (i < n && c <= i) A[pk(i, c)] = df_sub(A[pk(i, c)], acc[a][b].get());
+          }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ void chol_unit_scale_df(dfl* A, const dfl* inv_diag, const int* efirst, int n) {
+  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = bs >> 5;
+  (void)bs;
+  for (int i = wid; i < n; i += nw)
+    for (int j = efirst[i] + lane; j < i; j += 32) A[pk(i, j)] = df_mul(A[pk(i, j)], inv_diag[j]);
+}
+
+// S' y = b in place with S' = Lu D^2 Lu^T (double-float), the sweeps of
+// chol_solve_blocked with compensated (Dot2) row sums
+__device__ void chol_solve_df(const dfl* A, const dfl* inv_diag, const int* efirst, dfl* b, int n) {
+  const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  for (int k0 = 0; k0 < n; k0 += kSolveNB) {  // Lu z = b
+    const int k1 = min(k0 + kSolveNB, n);
+    if (wid == 0) {
+      const int i = k0 + lane;
+      dfl v = i < k1 ? b[i] : dfl{0.0f, 0.0f};
+      for (int j = k0; j < k1 - 1; ++j) {
+        const dfl z = shfl_df(v, j - k0);
+        if (i > j && i < k1 && efirst[i] <= j) v = df_fms(v, A[pk(i, j)], z);
+      }
+      if (i < k1) b[i] = v;
+    }
+    __syncthreads();
+    for (int i = k1 + tid; i < n; i += bs) {
+      const int q0 = max(k0, efirst[i]);
+      if (q0 >= k1) continue;
+      Dot2 s0, s1, s2, s3;  // four interleaved sums, merged in a fixed order
+      int q = q0;
+      for (; q + 3 < k1; q += 4) {
+        s0.add(A[pk(i, q)], b[q]);
+        s1.add(A[pk(i, q + 1)], b[q + 1]);
+        s2.add(A[pk(i, q + 2)], b[q + 2]);
+        s3.add(A[pk(i, q + 3)], b[q + 3]);
+      }
+      for (; q < k1; ++q) s0.add(A[pk(i, q)], b[q]);
+      s0.merge(s1.s, s1.c);
+      s2.merge(s3.s, s3.c);
+      s0.merge(s2.s, s2.c);
+      b[i] = df_sub(b[i], s0.get());
+    }
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += bs) b[i] = df_mul(df_mul(b[i], inv_diag[i]), inv_diag[i]);  // D^-2
+  __syncthreads();
+  const int nb = (n + kSolveNB - 1) / kSolveNB;
+  for (int blk = nb - 1; blk >= 0; --blk) {  // Lu^T x = w
+    const int k0 = blk * kSolveNB, k1 = min(k0 + kSolveNB, n);
+    if (wid == 0) {
+      const int i = k0 + lane;
+      dfl v = i < k1 ? b[i] : dfl{0.0f, 0.0f};
+      for (int j = k1 - 1; j > k0; --j) {
+        const dfl xj = shfl_df(v, j - k0);
+        if (i < j && i >= k0 && efirst[j] <= i) v = df_fms(v, A[pk(j, i)], xj);
+      }
+      if (i < k1) b[i] = v;
+    }
+    __syncthreads();
+    int lo = k0;
+    for (int q = k0; q < k1; ++q) lo = min(lo, efirst[q]);
+    for (int i = lo + tid; i < k0; i += bs) {
+      // the block's rows whose envelope reaches column i are a prefix
+      // [k0, qe) of it (the envelope is monotone)
+      int qe = k0;
+      while (qe < k1 && efirst[qe] <= i) ++qe;
+      if (qe == k0) continue;
+      Dot2 s0, s1, s2, s3;
+      int q = k0;
+      for (; q + 3 < qe; q += 4) {
+        s0.add(A[pk(q, i)], b[q]);
+        s1.add(A[pk(q + 1, i)], b[q + 1]);
+        s2.add(A[pk(q + 2, i)], b[q + 2]);
+        s3.add(A[pk(q + 3, i)], b[q + 3]);
+      }
+      for (; q < qe; ++q) s0.add(A[pk(q, i)], b[q]);
+      s0.merge(s1.s, s1.c);
+      s2.merge(s3.s, s3.c);
+      s0.merge(s2.s, s2.c);
+      b[i] = df_sub(b[i], s0.get());
+    }
+    __syncthreads();
+  }
+}
+
+// A x = v for the binary64 vector v (in place): scaled into double-float in
+// the same bytes, solved, scaled back
+__device__ void solve_scaled_df(const dfl* A, const dfl* inv_diag, const int* efirst, const int* escale, double* v,
+                                int n) {
+  dfl* vf = reinterpret_cast<dfl*>(v);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) vf[i] = df_from_d_pow2(v[i], escale[i]);
+  __syncthreads();
+  chol_solve_df(A, inv_diag, efirst, vf, n);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = ldexp(df_to_d(vf[i]), escale[i]);
+  __syncthreads();
+}
+
 template <bool MIXED>
 __global__ void __launch_bounds__(kFactorThreads) k_factor_solve(BatchView bv, int refine_steps, int assemble_only) {
   using Real = typename RealOf<MIXED>::T;
@@ -1295,17 +1527,34 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_solve(BatchView bv, i
     int* efirst = reinterpret_cast<int*>(inv_diag + n);  // [n]: first column of each row's envelope
     for (int idx = tid; idx < n; idx += bs) efirst[idx] = 6 * C.env_first[idx / 6];
     __syncthreads();
+    // double-float factor of the equilibrated system (escale: its exponents):
+    // the mixed path, and the binary64 path under BA_FLAG_SMALL_DF_FACTOR
+    const bool use_df = MIXED || bv.factor_df;
+    int* escale = efirst + n;
+    dfl* Af = reinterpret_cast<dfl*>(A);
+    dfl* inv_f = reinterpret_cast<dfl*>(inv_diag);
+    if (use_df) {
+      chol_to_scaled_df(A, n, efirst, escale);
+      if (!fail) chol_lookahead_df(Af, n, inv_f, reinterpret_cast<dfl*>(t), efirst, &fail, bv.factor_nb);
+    } else {
 #ifdef BA_FACTOR_NO_LOOKAHEAD
-    if (!fail) chol_blocked(A, n, inv_diag, t, efirst, &fail, bv.factor_nb);
+      if (!fail) chol_blocked(A, n, inv_diag, t, efirst, &fail, bv.factor_nb);
 #else
-    if (!fail) chol_lookahead(A, n, inv_diag, t, efirst, &fail, bv.factor_nb);
+      if (!fail) chol_lookahead(A, n, inv_diag, t, efirst, &fail, bv.factor_nb);
 #endif
+    }
     __syncthreads();
     const int status = fail ? BA_STATUS_NOT_PD : 0;
     if (!fail) {
-      chol_unit_scale(A, inv_diag, efirst, n);
-      __syncthreads();
-      chol_solve_blocked(A, inv_diag, efirst, b, n);
+      if (use_df) {
+        chol_unit_scale_df(Af, inv_f, efirst, n);
+        __syncthreads();
+        solve_scaled_df(Af, inv_f, efirst, escale, b, n);
+      } else {
+        chol_unit_scale(A, inv_diag, efirst, n);
+        __syncthreads();
+        chol_solve_blocked(A, inv_diag, efirst, b, n);
+      }
       for (int idx = tid; idx < n; idx += bs) x[idx] = b[idx];
       __syncthreads();
       // iterative refinement against the FP64 system kept in global memory
@@ -1319,7 +1568,8 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_solve(BatchView bv, i
           if (lane == 0) t[r] = C.rhs[r] - acc;
         }
         __syncthreads();
-        chol_solve_blocked(A, inv_diag, efirst, t, n);
+        if (use_df) solve_scaled_df(Af, inv_f, efirst, escale, t, n);
+        else chol_solve_blocked(A, inv_diag, efirst, t, n);
         for (int idx = tid; idx < n; idx += bs) x[idx] += t[idx];
         __syncthreads();
       }

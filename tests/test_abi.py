@@ -75,3 +75,21 @@ def test_struct_layouts_match_header(tmp_path):
         assert int(out[name]) == ctypes.sizeof(st), name
         for f, _ in st._fields_:
             assert int(out[f"{name}.{f}"]) == getattr(st, f).offset, (name, f)
+
+
+def test_binding_constants_match_the_header():
+    """Every BA_FLAG_*, BA_PTR_*, BA_FP64 / BA_MIXED and BA_ERR_* value the
+    binding defines equals the header's."""
+    import paper_2511_06152_gb300 as ba
+    with open(os.path.join(ROOT, "include", "ba.h")) as f:
+        src = f.read()
+    defines = {k: int(v) for k, v in re.findall(r"#define\s+(BA_\w+)\s+(-?\d+)\b", src)}
+    enums = {k: int(v) for k, v in re.findall(r"\b(BA_\w+)\s*=\s*(-?\d+)\s*[,}]", src)}
+    values = {**defines, **enums}
+    checked = 0
+    for name, v in values.items():
+        if hasattr(ba, name):
+            assert getattr(ba, name) == v, name
+            checked += 1
+    assert "BA_FLAG_SMALL_DF_FACTOR" in values and ba.BA_FLAG_SMALL_DF_FACTOR == values["BA_FLAG_SMALL_DF_FACTOR"]
+    assert checked >= 8

@@ -42,22 +42,27 @@ def test_fp64_step_parity_40_images(ba, factor):
     _step_parity(ba, sg.tiny_cluster(5151, 4, 10, 3000, fixed=(0, 11)), 8, min_steps=8, flags=flags)
 
 
-def test_tensor_core_and_fp64_factor_agree_on_the_large_block(ba):
+@pytest.mark.parametrize("refine,f_rel,centre_m", [(1, 1e-12, 1e-9), (-1, 1e-10, 1e-6)])
+def test_tensor_core_and_fp64_factor_agree_on_the_large_block(ba, refine, f_rel, centre_m):
     """The 400-image block in mixed precision, 3 LM iterations with each
-    factorisation: the same decisions, F within 1e-12 relative, centres
-    within 1e-9 m."""
+    factorisation: the same decisions; with one binary64 refinement pass F
+    within 1e-12 relative and centres within 1e-9 m (the refinement removes
+    the factor's rounding), with the mixed path's default (no refinement
+    pass) within 1e-10 and 1e-6 m (the double-float factor's rounding,
+    about 2^-47 times the condition of this n = 2400 system, whose weakest
+    directions move the centres by a few 1e-7 m)."""
     c = sg.cluster_c5(n_points=200_000)
     out = []
     for flags in (0, ba.BA_FLAG_BIG_FP64_FACTOR):
-        with ba.Context(precision=ba.BA_MIXED, flags=flags) as ctx:
+        with ba.Context(precision=ba.BA_MIXED, flags=flags, refine_steps=refine) as ctx:
             cid = ctx.create_cluster(c)
             tr = ctx.run(cid, 3)
             out.append((tr, ctx.get_state(cid)))
     (ta, sa), (tb, sb) = out
     for x, y in zip(ta, tb):
         assert x["status"] == y["status"] == 0 and x["accepted"] == y["accepted"]
-        assert x["F_after"] == pytest.approx(y["F_after"], rel=1e-12)
-    assert np.abs(sa[1] - sb[1]).max() < 1e-9
+        assert x["F_after"] == pytest.approx(y["F_after"], rel=f_rel)
+    assert np.abs(sa[1] - sb[1]).max() < centre_m
 
 
 def test_fp64_step_parity_large_block(ba):
