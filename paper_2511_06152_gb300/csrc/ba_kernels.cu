@@ -917,8 +917,11 @@ __global__ void __launch_bounds__(256) k_partial_reduce(BatchView bv) {
 __device__ __forceinline__ int pk(int i, int j) { return (i * (i + 1)) / 2 + j; }  // packed lower, j <= i
 
 size_t factor_smem_bytes(int max_n) {
+  // packed A, per-camera sums and priors, x, b, t, inv_diag, the envelope and
+  // scale exponents (ints), the double-float solves' block inverses
   const int nf = max_n / 6;
-  const size_t doubles = (size_t)max_n * (max_n + 1) / 2 + (size_t)nf * 40 + (size_t)nf * 42 + 5 * (size_t)max_n + 64;
+  const size_t doubles = (size_t)max_n * (max_n + 1) / 2 + (size_t)nf * 40 + (size_t)nf * 42 + 5 * (size_t)max_n +
+                         (size_t)((max_n + 31) / 32) * (32 * 33 / 2) + 64;
   return doubles * sizeof(double);
 }
 
@@ -1351,19 +1354,63 @@ __device__ void chol_unit_scale_df(dfl* A, const dfl* inv_diag, const int* efirs
     for (int j = efirst[i] + lane; j < i; j += 32) A[pk(i, j)] = df_mul(A[pk(i, j)], inv_diag[j]);
 }
 
-// S' y = b in place with S' = Lu D^2 Lu^T (double-float), the sweeps of
-// chol_solve_blocked with compensated (Dot2) row sums
-__device__ void chol_solve_df(const dfl* A, const dfl* inv_diag, const int* efirst, dfl* b, int n) {
+// Inverses of the unit-lower diagonal blocks of kSolveNB rows of Lu, packed
+// lower (entry (r, c) of a block at r (r + 1) / 2 + c, the unit diagonal
+// stored), one warp per block, lane = column c:
+// X(c, c) = 1, X(r, c) = -sum_{q=c}^{r-1} Lu(r, q) X(q, c) for r > c.
+// The solves then apply each block as a product instead of a sequential
+// substitution.
+constexpr int kSolveTri = kSolveNB * (kSolveNB + 1) / 2;
+__device__ void chol_block_inverses_df(const dfl* A, const int* efirst, dfl* binv, int n) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nb = (n + kSolveNB - 1) / kSolveNB;
+  for (int blk = wid; blk < nb; blk += nw) {
+    const int k0 = blk * kSolveNB, m = min(kSolveNB, n - k0);
+    dfl* X = binv + (size_t)blk * kSolveTri;
+    const int c = lane;
+    if (c >= m) continue;
+    X[c * (c + 1) / 2 + c] = dfl{1.0f, 0.0f};
+    for (int r = c + 1; r < m; ++r) {
+      const int qs = max(c, efirst[k0 + r] - k0);  // Lu(r, q) = 0 left of the envelope
+      const dfl* Lr = A + pk(k0 + r, k0);
+      Dot2 s0, s1;
+      int q = qs;
+      for (; q + 1 < r; q += 2) {
+        s0.add(Lr[q], X[q * (q + 1) / 2 + c]);
+        s1.add(Lr[q + 1], X[(q + 1) * (q + 2) / 2 + c]);
+      }
+      for (; q < r; ++q) s0.add(Lr[q], X[q * (q + 1) / 2 + c]);
+      s0.merge(s1.s, s1.c);
+      X[r * (r + 1) / 2 + c] = df_neg(s0.get());
+    }
+  }
+}
+
+// S' y = b in place with S' = Lu D^2 Lu^T (double-float): the sweeps of
+// chol_solve_blocked, each diagonal block applied through its inverse (warp
+// 0, lane = row), the rest of the vector updated thread per row, all sums
+// compensated (Dot2)
+__device__ void chol_solve_df(const dfl* A, const dfl* inv_diag, const int* efirst, const dfl* binv, dfl* b, int n) {
   const int tid = threadIdx.x, bs = blockDim.x, lane = tid & 31, wid = tid >> 5;
   for (int k0 = 0; k0 < n; k0 += kSolveNB) {  // Lu z = b
     const int k1 = min(k0 + kSolveNB, n);
     if (wid == 0) {
-      const int i = k0 + lane;
-      dfl v = i < k1 ? b[i] : dfl{0.0f, 0.0f};
-      for (int j = k0; j < k1 - 1; ++j) {
-        const dfl z = shfl_df(v, j - k0);
-        if (i > j && i < k1 && efirst[i] <= j) v = df_fms(v, A[pk(i, j)], z);
+      const dfl* X = binv + (size_t)(k0 / kSolveNB) * kSolveTri;
+      const int r = lane, i = k0 + r;
+      dfl v{0.0f, 0.0f};
+      if (i < k1) {  // z_r = sum_{q <= r} X(r, q) b_q
+        const dfl* Xr = X + r * (r + 1) / 2;
+        Dot2 s0, s1;
+        int q = 0;
+        for (; q + 1 <= r; q += 2) {
+          s0.add(Xr[q], b[k0 + q]);
+          s1.add(Xr[q + 1], b[k0 + q + 1]);
+        }
+        for (; q <= r; ++q) s0.add(Xr[q], b[k0 + q]);
+        s0.merge(s1.s, s1.c);
+        v = s0.get();
       }
+      __syncwarp();
       if (i < k1) b[i] = v;
     }
     __syncthreads();
@@ -1390,14 +1437,23 @@ __device__ void chol_solve_df(const dfl* A, const dfl* inv_diag, const int* efir
   __syncthreads();
   const int nb = (n + kSolveNB - 1) / kSolveNB;
   for (int blk = nb - 1; blk >= 0; --blk) {  // Lu^T x = w
-    const int k0 = blk * kSolveNB, k1 = min(k0 + kSolveNB, n);
+    const int k0 = blk * kSolveNB, k1 = min(k0 + kSolveNB, n), m = k1 - k0;
     if (wid == 0) {
-      const int i = k0 + lane;
-      dfl v = i < k1 ? b[i] : dfl{0.0f, 0.0f};
-      for (int j = k1 - 1; j > k0; --j) {
-        const dfl xj = shfl_df(v, j - k0);
-        if (i < j && i >= k0 && efirst[j] <= i) v = df_fms(v, A[pk(j, i)], xj);
+      const dfl* X = binv + (size_t)blk * kSolveTri;
+      const int r = lane, i = k0 + r;
+      dfl v{0.0f, 0.0f};
+      if (i < k1) {  // x_r = sum_{q >= r} X(q, r) w_q
+        Dot2 s0, s1;
+        int q = r;
+        for (; q + 1 < m; q += 2) {
+          s0.add(X[q * (q + 1) / 2 + r], b[k0 + q]);
+          s1.add(X[(q + 1) * (q + 2) / 2 + r], b[k0 + q + 1]);
+        }
+        for (; q < m; ++q) s0.add(X[q * (q + 1) / 2 + r], b[k0 + q]);
+        s0.merge(s1.s, s1.c);
+        v = s0.get();
       }
+      __syncwarp();
       if (i < k1) b[i] = v;
     }
     __syncthreads();
@@ -1429,12 +1485,12 @@ __device__ void chol_solve_df(const dfl* A, const dfl* inv_diag, const int* efir
 
 // A x = v for the binary64 vector v (in place): scaled into double-float in
 // the same bytes, solved, scaled back
-__device__ void solve_scaled_df(const dfl* A, const dfl* inv_diag, const int* efirst, const int* escale, double* v,
-                                int n) {
+__device__ void solve_scaled_df(const dfl* A, const dfl* inv_diag, const int* efirst, const int* escale,
+                                const dfl* binv, double* v, int n) {
   dfl* vf = reinterpret_cast<dfl*>(v);
   for (int i = threadIdx.x; i < n; i += blockDim.x) vf[i] = df_from_d_pow2(v[i], escale[i]);
   __syncthreads();
-  chol_solve_df(A, inv_diag, efirst, vf, n);
+  chol_solve_df(A, inv_diag, efirst, binv, vf, n);
   for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = ldexp(df_to_d(vf[i]), escale[i]);
   __syncthreads();
 }
@@ -1514,9 +1570,11 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_solve(BatchView bv, i
       else A[pk(6 * pa + i, 6 * pb + c)] = -v;
     }
     __syncthreads();
-    for (int idx = tid; idx < n * n; idx += bs) {
-      const int r = idx / n, c = idx - n * r;
-      C.S[idx] = r >= c ? A[pk(r, c)] : A[pk(c, r)];
+    if (assemble_only || refine_steps > 0) {  // S in binary64 for the refinement (only the refinement reads it)
+      for (int idx = tid; idx < n * n; idx += bs) {
+        const int r = idx / n, c = idx - n * r;
+        C.S[idx] = r >= c ? A[pk(r, c)] : A[pk(c, r)];
+      }
     }
     if (assemble_only) {
       __syncthreads();
@@ -1531,6 +1589,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_solve(BatchView bv, i
     // the mixed path, and the binary64 path under BA_FLAG_SMALL_DF_FACTOR
     const bool use_df = MIXED || bv.factor_df;
     int* escale = efirst + n;
+    dfl* binv = reinterpret_cast<dfl*>(inv_diag + 2 * n);  // inverses of the solves' diagonal blocks
     dfl* Af = reinterpret_cast<dfl*>(A);
     dfl* inv_f = reinterpret_cast<dfl*>(inv_diag);
     if (use_df) {
@@ -1549,7 +1608,9 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_solve(BatchView bv, i
       if (use_df) {
         chol_unit_scale_df(Af, inv_f, efirst, n);
         __syncthreads();
-        solve_scaled_df(Af, inv_f, efirst, escale, b, n);
+        chol_block_inverses_df(Af, efirst, binv, n);
+        __syncthreads();
+        solve_scaled_df(Af, inv_f, efirst, escale, binv, b, n);
       } else {
         chol_unit_scale(A, inv_diag, efirst, n);
         __syncthreads();
@@ -1568,7 +1629,7 @@ __global__ void __launch_bounds__(kFactorThreads) k_factor_solve(BatchView bv, i
           if (lane == 0) t[r] = C.rhs[r] - acc;
         }
         __syncthreads();
-        if (use_df) solve_scaled_df(Af, inv_f, efirst, escale, t, n);
+        if (use_df) solve_scaled_df(Af, inv_f, efirst, escale, binv, t, n);
         else chol_solve_blocked(A, inv_diag, efirst, t, n);
         for (int idx = tid; idx < n; idx += bs) x[idx] += t[idx];
         __syncthreads();
