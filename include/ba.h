@@ -427,7 +427,10 @@ BA_API ba_status ba_get_state(ba_ctx* ctx, ba_cluster_id id, double* R, double* 
  * entry, or a whole array, may be NULL).  The clusters go in groups of at
  * most 32 MiB of state: per group one device export per cluster into one
  * block, one copy to the host through pinned memory the context keeps, one
- * wait.  BA_ERR_NOT_FOUND if an id is unknown (nothing is written then). */
+ * wait.  The clusters are in service during the call, which does not hold
+ * the context's lock meanwhile (other threads may create or solve other
+ * clusters).  BA_ERR_NOT_FOUND if an id is unknown, BA_ERR_INVALID if one is
+ * in service (nothing is written then). */
 BA_API ba_status ba_get_state_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n, double* const* R,
                                     double* const* T, double* const* X);
 

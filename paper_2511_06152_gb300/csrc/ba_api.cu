@@ -144,6 +144,7 @@ struct ba_ctx {
   cudaStream_t sched_stream = nullptr;  // the scheduler's rounds
   cudaStream_t plan_stream = nullptr;   // plan tables (allocated and uploaded without waiting for the solves)
   double* hstage = nullptr;             // pinned host staging of ba_get_state (grown on demand)
+  std::mutex hstage_mu;                 // the staging's user (ba_get_state_batch runs without api_mu)
   size_t hstage_bytes = 0;
   SlotTable slots;
 };
@@ -534,6 +535,24 @@ ba_status run_and_collect(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, in
     CUDA_TRY(ctx, cudaMallocAsync((void**)&dtrace, sizeof(StepRec) * (size_t)n * tcap, ctx->stream));
   }
   launch_gather(p->bv, tcap, p->lm_out, dtrace, ctx->stream);
+  // The copies of the results go to pageable host memory, which makes them
+  // wait for the whole batch on the host: with lk they are issued only after
+  // the lock has been released, so that other threads (cluster creation)
+  // are not held up for the duration of the solve.
+  struct Relock {
+    std::unique_lock<std::mutex>* lk;
+    ~Relock() {
+      if (lk && !lk->owns_lock()) lk->lock();
+    }
+  } relock{lk};
+  if (lk) {
+    // the waiting thread sleeps instead of spinning: the host threads stay
+    // free for cluster creation meanwhile
+    if (!p->done) CUDA_TRY(ctx, cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming | cudaEventBlockingSync));
+    CUDA_TRY(ctx, cudaEventRecord(p->done, ctx->stream));
+    lk->unlock();
+    CUDA_TRY(ctx, cudaEventSynchronize(p->done));
+  }
   if (lm) {
     lm->resize(n);
     CUDA_TRY(ctx, cudaMemcpyAsync(lm->data(), p->lm_out, sizeof(LmState) * n, cudaMemcpyDeviceToHost, ctx->stream));
@@ -544,16 +563,8 @@ ba_status run_and_collect(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, in
                                   ctx->stream));
     CUDA_TRY(ctx, cudaFreeAsync(dtrace, ctx->stream));
   }
-  if (lk) {
-    if (!p->done) CUDA_TRY(ctx, cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
-    CUDA_TRY(ctx, cudaEventRecord(p->done, ctx->stream));
-    lk->unlock();
-    const cudaError_t e = cudaEventSynchronize(p->done);
-    lk->lock();
-    CUDA_TRY(ctx, e);
-  } else {
-    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  }
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (lk) lk->lock();
   CUDA_TRY(ctx, cudaGetLastError());
   note_direct(ctx);
   collect_timing(ctx, p);
@@ -889,6 +900,23 @@ BatchView one_view(const DevCluster* d_desc, int n_free) {
   bv.n = 1;
   bv.max_n = 6 * n_free;
   return bv;
+}
+
+// Host copy of the mixed path's camera record (write_camdf's layout and
+// values: hi = the binary64 value rounded to binary32, lo = the remainder
+// rounded to binary32)
+void host_camdf(float* o, const double* R, const double* T, const double* intr, bool is_free) {
+  auto split = [](double v, float* hi, float* lo) {
+    *hi = (float)v;
+    *lo = (float)(v - (double)*hi);
+  };
+  for (int i = 0; i < 9; ++i) split(R[i], &o[i], &o[24 + i]);
+  for (int i = 0; i < 3; ++i) split(T[i], &o[9 + i], &o[12 + i]);
+  split(intr[0], &o[15], &o[33]);
+  for (int i = 0; i < 4; ++i) split(intr[3 + i], &o[16 + i], &o[34 + i]);
+  o[20] = is_free ? 1.0f : 0.0f;
+  for (int i = 21; i < 24; ++i) o[i] = 0.0f;
+  for (int i = 38; i < kCamDf; ++i) o[i] = 0.0f;
 }
 
 ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const PresortProbe* probe = nullptr) {
@@ -1472,9 +1500,9 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
   const size_t o_ps = Lo.add(sizeof(int) * pair_slots.size());
   const size_t o_lm = Lo.add(sizeof(LmState));
   const size_t o_bflag = Lo.add(big ? sizeof(int) : 0);  // zero from the staging
-  const size_t static_bytes = Lo.off;
   const size_t o_camreal = Lo.add(mixed ? 0 : sizeof(double) * kCamReal * nc);
   const size_t o_camdf = Lo.add(mixed ? sizeof(float) * 2 * kCamDf * nc : 0);
+  const size_t static_bytes = Lo.off;
   const size_t o_cpart = Lo.add(rs * kCamPart * (size_t)n_cslots);
   const size_t o_ppart = Lo.add(rs * kPairPart * (size_t)n_pslots);
   const size_t o_csum = Lo.add(sizeof(double) * kCamPart * (size_t)nf);
@@ -1498,18 +1526,24 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
   const size_t total = Lo.off;
 
   // a pinned staging buffer of the context (every byte the kernels read is
-  // written below; alignment padding may keep an earlier cluster's bytes)
+  // written below; alignment padding may keep an earlier cluster's bytes):
+  // the smallest free one that holds this cluster, else a new one.  Buffers
+  // are only freed at shutdown: freeing pinned memory waits for the device,
+  // which would stall a creation behind a batch that is being solved.
   std::pair<char*, size_t> stage{nullptr, 0};
   {
     std::lock_guard<std::mutex> g(ctx->stage_mu);
-    if (!ctx->stage_free.empty()) {
-      stage = ctx->stage_free.back();
-      ctx->stage_free.pop_back();
+    int best = -1;
+    for (int i = 0; i < (int)ctx->stage_free.size(); ++i)
+      if (ctx->stage_free[i].second >= static_bytes &&
+          (best < 0 || ctx->stage_free[i].second < ctx->stage_free[best].second))
+        best = i;
+    if (best >= 0) {
+      stage = ctx->stage_free[best];
+      ctx->stage_free.erase(ctx->stage_free.begin() + best);
     }
   }
-  if (stage.second < static_bytes) {
-    if (stage.first) cudaFreeHost(stage.first);
-    stage = {nullptr, 0};
+  if (!stage.first) {
     const size_t want = (static_bytes + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
     if (cudaMallocHost((void**)&stage.first, want) != cudaSuccess)
       return set_err(ctx, BA_ERR_CUDA, "pinned staging buffer");
@@ -1613,6 +1647,24 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
   if (big) {
     const int zero = 0;
     put(o_bflag, &zero, sizeof(int));
+  }
+  // the camera records the kernels read, formed here rather than by a kernel
+  // at creation (a kernel would wait for SMs behind any batch being solved):
+  // the same values as write_camdf / k_camreal, both state buffers equal
+  if (mixed) {
+    float* o = reinterpret_cast<float*>(stage_ptr + o_camdf);
+    for (int k = 0; k < nc; ++k) host_camdf(o + (size_t)k * kCamDf, &R[9 * (size_t)k], &T[3 * (size_t)k], &intr[7 * (size_t)k],
+                                            free_idx[k] >= 0);
+    std::memcpy(o + (size_t)nc * kCamDf, o, sizeof(float) * kCamDf * nc);
+  } else {
+    double* o = reinterpret_cast<double*>(stage_ptr + o_camreal);
+    for (int k = 0; k < nc; ++k) {
+      double* r = o + (size_t)kCamReal * k;
+      for (int i = 0; i < 9; ++i) r[i] = R[9 * (size_t)k + i];
+      for (int i = 0; i < 3; ++i) r[9 + i] = T[3 * (size_t)k + i];
+      for (int i = 0; i < 7; ++i) r[12 + i] = intr[7 * (size_t)k + i];
+      r[19] = free_idx[k] >= 0 ? 1.0 : 0.0;
+    }
   }
 
   const auto t_staged = std::chrono::steady_clock::now();
@@ -1719,11 +1771,6 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
   h.trace_cap = kTraceCap;
   c->d_desc = (DevCluster*)(arena + o_desc);
   e = cudaMemcpyAsync(c->d_desc, &h, sizeof(DevCluster), cudaMemcpyHostToDevice, up);
-  if (e == cudaSuccess) {
-    launch_camreal(one_view(c->d_desc, nf), mixed, up);
-    note_direct(ctx);
-    e = cudaGetLastError();
-  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(up);
   if (e != cudaSuccess) return fail("cluster upload: ", e);
   cudaStreamDestroy(up);
@@ -2514,6 +2561,7 @@ BA_API ba_status ba_poll(ba_ctx* ctx, ba_ticket t, ba_result* out) {
 BA_API ba_status ba_get_state(ba_ctx* ctx, ba_cluster_id id, double* R, double* T, double* X, int32_t ptr_kind) {
   if (!ctx) return BA_ERR_INVALID;
   std::lock_guard<std::mutex> g(ctx->api_mu);
+  std::lock_guard<std::mutex> hs(ctx->hstage_mu);
   Cluster* c = find_cluster(ctx, id);
   if (!c) return BA_ERR_NOT_FOUND;
   // one kernel writes the requested parts of the current state into one
@@ -2555,12 +2603,27 @@ BA_API ba_status ba_get_state(ba_ctx* ctx, ba_cluster_id id, double* R, double* 
 BA_API ba_status ba_get_state_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n, double* const* R,
                                     double* const* T, double* const* X) {
   if (!ctx || (n > 0 && !ids) || n < 0) return BA_ERR_INVALID;
-  std::lock_guard<std::mutex> g(ctx->api_mu);
+  std::unique_lock<std::mutex> g(ctx->api_mu);
   std::vector<Cluster*> cs(n);
   for (int i = 0; i < n; ++i) {
     cs[i] = find_cluster(ctx, ids[i]);
     if (!cs[i]) return BA_ERR_NOT_FOUND;
+    if (cs[i]->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in service");
   }
+  // the batch's clusters are in service while the device exports them and the
+  // host copies them out, without the context's lock (other threads may create
+  // or solve other clusters meanwhile)
+  for (Cluster* c : cs) c->in_service = 1;
+  struct Release {
+    ba_ctx* ctx;
+    std::vector<Cluster*>& cs;
+    ~Release() {
+      std::lock_guard<std::mutex> l(ctx->api_mu);
+      for (Cluster* c : cs) c->in_service = 0;
+    }
+  } release{ctx, cs};
+  g.unlock();
+  std::lock_guard<std::mutex> hs(ctx->hstage_mu);
   // groups of clusters whose states fit the pinned staging (at most
   // kStateStageBytes, or one cluster's state if that is larger): per group,
   // one device export per cluster into one block, one copy, one wait
