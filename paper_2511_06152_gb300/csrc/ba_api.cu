@@ -208,10 +208,16 @@ bool fetch(const T* src, size_t n, int kind, In<T>& out) {
   return true;
 }
 
+// every value finite: no exponent field of all ones (a branch-free pass the
+// compiler vectorises)
 bool all_finite(const In<double>& v) {
-  for (size_t i = 0; i < v.n; ++i)
-    if (!std::isfinite(v.p[i])) return false;
-  return true;
+  uint64_t bad = 0;
+  for (size_t i = 0; i < v.n; ++i) {
+    uint64_t x;
+    std::memcpy(&x, v.p + i, sizeof(x));
+    bad |= (uint64_t)(((x >> 52) & 0x7ffu) == 0x7ffu);
+  }
+  return bad == 0;
 }
 
 Cluster* find_cluster(ba_ctx* ctx, ba_cluster_id id) {
@@ -951,9 +957,12 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
   if (!all_finite(intr) || !all_finite(R) || !all_finite(T) || !all_finite(X) || !all_finite(Rp) ||
       !all_finite(Tp) || !all_finite(uv))
     return set_err(ctx, BA_ERR_INVALID, "non-finite value in the input");
-  for (int i = 0; i < no; ++i)
-    if (ocam[i] < 0 || ocam[i] >= nc || opt[i] < 0 || opt[i] >= np)
-      return set_err(ctx, BA_ERR_INVALID, "observation index out of range");
+  {
+    unsigned bad = 0;  // one branch-free pass over both index arrays
+    for (int i = 0; i < no; ++i)
+      bad |= (unsigned)((uint32_t)ocam[i] >= (uint32_t)nc) | (unsigned)((uint32_t)opt[i] >= (uint32_t)np);
+    if (bad) return set_err(ctx, BA_ERR_INVALID, "observation index out of range");
+  }
   // threads for the staging gathers: a few when few creations share the host
   // (hardware threads / creations in flight, at most 4), none for small
   // clusters (a thread start costs tens of microseconds); no result depends
