@@ -83,6 +83,9 @@ struct SlotTable {
   int tune_gen = -1;  // ctx->tune_gen the serving graph was captured with
   char* dbuf = nullptr;
   size_t bytes = 0;
+  char* hbuf = nullptr;  // pinned host mirror of dbuf's layout: the table goes up, the LM states come
+                         // back, in copies that do not stage through the driver
+  size_t o_lm = 0;       // offset of the LM states (everything before it is the uploaded table)
   BatchView bv{};
   DevCluster* d_desc = nullptr;
   int* d_pre = nullptr;
@@ -1862,8 +1865,11 @@ ba_status slots_setup(ba_ctx* ctx) {
   const size_t o_lm = L.add(sizeof(LmState) * n);
   const size_t o_dummy = L.add(sizeof(LmState));
   T.bytes = L.off;
+  T.o_lm = o_lm;
   CUDA_TRY(ctx, cudaMalloc((void**)&T.dbuf, T.bytes));
   CUDA_TRY(ctx, cudaMemset(T.dbuf, 0, T.bytes));
+  CUDA_TRY(ctx, cudaMallocHost((void**)&T.hbuf, T.bytes));
+  std::memset(T.hbuf, 0, T.bytes);
   ctx->mem += T.bytes;
   T.n = n;
   T.d_desc = (DevCluster*)(T.dbuf + o_desc);
@@ -1910,10 +1916,15 @@ ba_status slots_upload(ba_ctx* ctx) {
   pre[3 * (n + 1) + 2] = pre[2 * (n + 1) + n];
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int b) { return T.descs[a].n_free > T.descs[b].n_free; });
-  CUDA_TRY(ctx, cudaMemcpyAsync(T.d_desc, T.descs.data(), sizeof(DevCluster) * n, cudaMemcpyHostToDevice, ctx->sched_stream));
-  CUDA_TRY(ctx, cudaMemcpyAsync(T.d_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, ctx->sched_stream));
-  CUDA_TRY(ctx, cudaMemcpyAsync(T.d_order, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->sched_stream));
-  CUDA_TRY(ctx, cudaMemcpyAsync(T.d_arm, T.arm.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->sched_stream));
+  // the whole table through the pinned mirror in one copy (the previous
+  // round's copies have completed: every round ends with a stream sync)
+  char* const h = T.hbuf;
+  auto at = [&](const void* dev) { return h + ((const char*)dev - T.dbuf); };
+  std::memcpy(at(T.d_desc), T.descs.data(), sizeof(DevCluster) * n);
+  std::memcpy(at(T.d_pre), pre.data(), sizeof(int) * pre.size());
+  std::memcpy(at(T.d_order), order.data(), sizeof(int) * n);
+  std::memcpy(at(T.d_arm), T.arm.data(), sizeof(int) * n);
+  CUDA_TRY(ctx, cudaMemcpyAsync(T.dbuf, h, T.o_lm, cudaMemcpyHostToDevice, ctx->sched_stream));
   T.dirty = false;
   return BA_OK;
 }
@@ -1957,9 +1968,11 @@ ba_status slots_round(ba_ctx* ctx) {
   }
   CUDA_TRY(ctx, cudaGraphLaunch(T.graph.exec, ctx->sched_stream));
   ctx->launches += T.graph.kernels;
-  CUDA_TRY(ctx, cudaMemcpyAsync(T.lm.data(), T.d_lm, sizeof(LmState) * T.n, cudaMemcpyDeviceToHost, ctx->sched_stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(T.hbuf + T.o_lm, T.d_lm, sizeof(LmState) * T.n, cudaMemcpyDeviceToHost,
+                                ctx->sched_stream));
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->sched_stream));
   CUDA_TRY(ctx, cudaGetLastError());
+  std::memcpy(T.lm.data(), T.hbuf + T.o_lm, sizeof(LmState) * T.n);
   if (ctx->timing && T.graph.probe) fold_probe(ctx, T.graph.probe);
   bool armed = false;
   for (int s = 0; s < T.n; ++s)
@@ -2948,6 +2961,7 @@ BA_API ba_status ba_shutdown(ba_ctx* ctx) {
   if (ctx->slots.graph.exec) cudaGraphExecDestroy(ctx->slots.graph.exec);
   free_probe(ctx->slots.graph.probe);
   if (ctx->slots.dbuf) cudaFree(ctx->slots.dbuf);
+  if (ctx->slots.hbuf) cudaFreeHost(ctx->slots.hbuf);
   for (auto& kv : ctx->plans) free_plan(ctx, kv.second);
   for (auto& kv : ctx->clusters) {
     cudaFreeAsync(kv.second->arena, ctx->stream);
