@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--serving-rate", type=float, default=200.0, help="requests/s, Poisson, all flights")
     ap.add_argument("--serving-iters", type=int, default=10)
     ap.add_argument("--serving-only", action="store_true", help="run only the serving leg")
+    ap.add_argument("--serving-no-kernel-timing", action="store_true",
+                    help="serving-only: no per-kernel CUDA events in the rounds")
     ap.add_argument("--no-large", action="store_true", help="skip the 400-image large-block leg")
     ap.add_argument("--serving-timeout", type=float, default=120.0, help="seconds before the serving leg gives up")
     ap.add_argument("--serving-requests", type=int, default=2000, help="requests of the serving leg (flights replayed)")
@@ -274,13 +276,14 @@ def torch_device():
     return torch.cuda.current_device()
 
 
-def serving_leg(args, ba, stream, flights, rate=None, n_requests=None):
+def serving_leg(args, ba, stream, flights, rate=None, n_requests=None, timing=True):
     """Poisson arrivals of sliding-window requests from several flights; each
     window warm-starts on the device from the flight's previous window and is
     submitted to the continuous-batching scheduler.  A flight's windows are
     replayed in order (from its first window, without warm start) until the
     leg has n_requests requests.  Latency = completion - arrival (host
-    clock)."""
+    clock).  timing: per-kernel CUDA events inside the serving graph, for the
+    per-round kernel breakdown (they lengthen every round a little)."""
     import time as _t
     from concurrent.futures import ThreadPoolExecutor
     rate = args.serving_rate if rate is None else rate
@@ -297,7 +300,7 @@ def serving_leg(args, ba, stream, flights, rate=None, n_requests=None):
     arrivals = [np.cumsum(rng.exponential(1.0 / rate_f, len(w))) for w in flights]
     ctx = ba.Context(device=torch_device(), precision=ba.BA_MIXED,
                      stream=stream.cuda_stream, n_slots=64, hbm_budget_bytes=16 << 30,
-                     flags=ba.BA_FLAG_KERNEL_TIMING)
+                     flags=ba.BA_FLAG_KERNEL_TIMING if timing else 0)
     iters = args.serving_iters
     deadline = _t.perf_counter() + args.serving_timeout
     stop = threading.Event()
@@ -375,10 +378,10 @@ def serving_leg(args, ba, stream, flights, rate=None, n_requests=None):
     finally:
         stop.set()
         ex.shutdown(wait=True, cancel_futures=True)
-    kst = ctx.kernel_stats(reset=True)
+    kst = ctx.kernel_stats(reset=True) if timing else None
     ctx.close()
-    rounds = max(1, kst["backsub_cost"][1])  # one back-substitution launch per round
-    round_kernels = {k: v[0] / rounds for k, v in kst.items() if v[1]}
+    rounds = max(1, kst["backsub_cost"][1]) if timing else None  # one back-substitution launch per round
+    round_kernels = {k: v[0] / rounds for k, v in kst.items() if v[1]} if timing else None
     lat = np.array(lat)
     pct = {k: {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99))} for k, v in parts.items() if v}
     return {"requests": int(len(lat)), "flights": len(flights), "arrival_rate_req_s": rate, "replays": reps,
@@ -647,7 +650,8 @@ def main():
         torch.cuda.set_device(local)
         stream = torch.cuda.Stream()
         log("serving leg")
-        print(json.dumps({"serving": serving_leg(args, ba, stream, flights)}), flush=True)
+        print(json.dumps({"serving": serving_leg(args, ba, stream, flights,
+                                                 timing=not args.serving_no_kernel_timing)}), flush=True)
         return
     n_fl = 0 if (args.no_extras or rank != 0 or world != 1) else max(args.serving_flights, args.sweep_flights)
     log(f"generating {args.clusters} clusters and {n_fl} serving flights")
@@ -1082,7 +1086,8 @@ def extras(args, ba, torch, scenes, ids, ctx, stream, iters, value_mixed, flight
         for r in sweep:
             log(f"serving sweep: {args.sweep_requests} requests at {r} req/s")
             try:
-                sv = serving_leg(args, ba, stream, flights, rate=r, n_requests=args.sweep_requests)  # every flight
+                sv = serving_leg(args, ba, stream, flights, rate=r, n_requests=args.sweep_requests,
+                                 timing=False)  # every flight; no kernel events in the rounds
                 points.append({k: sv[k] for k in ("arrival_rate_req_s", "requests", "flights", "p50_ms", "p99_ms",
                                                   "throughput_req_s", "obs_per_s", "max_in_flight")})
             except RuntimeError as e:  # the leg's own time limit: the rate is beyond capacity
