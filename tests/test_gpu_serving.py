@@ -406,3 +406,55 @@ def test_hbm_budget_admission_waits_for_memory_and_keeps_results():
         for cid, rf in zip((c0, c1, c2), ref):
             for u, v in zip(got[cid], rf):
                 assert np.array_equal(u, v)
+
+
+def test_streamed_batches_equal_sequential():
+    """Batches streamed as a caller feeding windows continuously runs them:
+    batch k+1 is created on worker threads while batch k is solved and read
+    back on another thread (neither holds the context's lock while the device
+    works); every state equals that of the same calls made one after another."""
+    from concurrent.futures import ThreadPoolExecutor
+    import paper_2511_06152_gb300 as ba
+    groups = [[sg.tiny_cluster(7400 + 10 * g + i, 2, 6 + i % 3, 1000 + 200 * i) for i in range(5)] for g in range(3)]
+    with ba.Context(precision=ba.BA_MIXED) as ctx:
+        ref = []
+        for grp in groups:
+            ids = [ctx.create_cluster(s) for s in grp]
+            ctx.solve_batch(ids, 6)
+            ref.append(ctx.get_state_batch(ids))
+    with ba.Context(precision=ba.BA_MIXED) as ctx, ThreadPoolExecutor(4) as pool, ThreadPoolExecutor(1) as solver:
+        def solve_read(ids):
+            ctx.solve_batch(ids, 6)
+            return ctx.get_state_batch(ids)
+        cur = list(pool.map(ctx.create_cluster, groups[0]))
+        got = []
+        for k in range(len(groups)):
+            fut = solver.submit(solve_read, cur)
+            nxt = list(pool.map(ctx.create_cluster, groups[k + 1])) if k + 1 < len(groups) else None
+            got.append(fut.result())
+            cur = nxt
+    for g_ref, g_got in zip(ref, got):
+        for a, b in zip(g_ref, g_got):
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y)
+
+
+def test_get_state_batch_refuses_a_cluster_in_service():
+    """ba_get_state_batch runs without the context's lock and keeps its
+    clusters in service meanwhile, so it refuses one that the serving
+    scheduler is running (nothing is written) and still reads the others."""
+    import paper_2511_06152_gb300 as ba
+    sa, sb = sg.tiny_cluster(7501, 2, 8, 2000), sg.tiny_cluster(7502, 2, 6, 800)
+    with ba.Context(precision=ba.BA_MIXED) as ctx:
+        a, b = ctx.create_cluster(sa), ctx.create_cluster(sb)
+        before = ctx.get_state_batch([b])[0]
+        t = ctx.submit(a, 400)  # hundreds of rounds: still running when the read comes
+        with pytest.raises(ba.BAError) as e:
+            ctx.get_state_batch([b, a])
+        assert e.value.status == ba.BA_ERR_INVALID
+        for x, y in zip(ctx.get_state_batch([b])[0], before):
+            assert np.array_equal(x, y)
+        while ctx.poll(t) is None:
+            time.sleep(0.002)
+        R, T, X = ctx.get_state_batch([a])[0]
+        assert np.all(np.isfinite(R)) and np.all(np.isfinite(T)) and np.all(np.isfinite(X))
