@@ -67,10 +67,7 @@ struct Plan {
 struct Ticket {
   ba_cluster_id id = 0;
   int iters = 0;
-  double ftol = 0.0;   // relative cost decrease that ends the solve (0: off)
-  int rounds = 0;      // scheduler rounds run = LM iterations run
-  double F_last = 0.0; // cost after the last round
-  int acc_last = -1;   // accepted steps after the last round (-1: before the first)
+  double ftol = 0.0;   // relative cost decrease that ends the solve (0: off; tested on the device)
   int done = 0;
   ba_result res{};
   std::chrono::steady_clock::time_point t_submit;
@@ -83,18 +80,26 @@ struct SlotTable {
   int tune_gen = -1;  // ctx->tune_gen the serving graph was captured with
   char* dbuf = nullptr;
   size_t bytes = 0;
-  char* hbuf = nullptr;  // pinned host mirror of dbuf's layout: the table goes up, the LM states come
-                         // back, in copies that do not stage through the driver
+  char* hbuf = nullptr;  // two pinned host mirrors of dbuf's layout, one per round parity: the table
+                         // goes up, the LM states come back, in copies that do not stage through the
+                         // driver, while the other parity's round may still be in flight
   size_t o_lm = 0;       // offset of the LM states (everything before it is the uploaded table)
+  cudaEvent_t done[2] = {nullptr, nullptr};  // end of the round of each parity
+  cudaEvent_t tail = nullptr;  // end of the last round launched: a completed ticket orders the
+                               // context's stream after it (the cluster may still be read, inert,
+                               // by a round in flight)
   BatchView bv{};
   DevCluster* d_desc = nullptr;
   int* d_pre = nullptr;
   int* d_order = nullptr;
   int* d_arm = nullptr;
+  double* d_ftol = nullptr;
   LmState* d_lm = nullptr;
   DevCluster empty{};
   std::vector<DevCluster> descs;
   std::vector<int> arm;
+  std::vector<double> ftol;
+  std::vector<long long> first_round;  // per slot: the round its cluster first ran in
   std::vector<ba_cluster_id> occ;
   std::vector<ba_ticket> occ_ticket;
   std::vector<LmState> lm;
@@ -146,8 +151,11 @@ struct ba_ctx {
   bool sched_started = false;
   cudaStream_t sched_stream = nullptr;  // the scheduler's rounds
   cudaStream_t plan_stream = nullptr;   // plan tables (allocated and uploaded without waiting for the solves)
+  cudaStream_t copy_stream = nullptr;   // result copies issued without the API lock: never the caller's
+                                        // stream, which another thread may be capturing into a graph
   double* hstage = nullptr;             // pinned host staging of ba_get_state (grown on demand)
-  std::mutex hstage_mu;                 // the staging's user (ba_get_state_batch runs without api_mu)
+  std::mutex hstage_mu;                 // the staging's user (taken before api_mu)
+  cudaEvent_t state_done = nullptr;     // end of a ba_get_state_batch group's copy
   size_t hstage_bytes = 0;
   SlotTable slots;
 };
@@ -544,35 +552,34 @@ ba_status run_and_collect(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, in
     CUDA_TRY(ctx, cudaMallocAsync((void**)&dtrace, sizeof(StepRec) * (size_t)n * tcap, ctx->stream));
   }
   launch_gather(p->bv, tcap, p->lm_out, dtrace, ctx->stream);
-  // The copies of the results go to pageable host memory, which makes them
-  // wait for the whole batch on the host: with lk they are issued only after
-  // the lock has been released, so that other threads (cluster creation)
-  // are not held up for the duration of the solve.
+  // The results go to pageable host memory, a copy that waits on the host
+  // for the whole batch.  It is issued on the context's copy stream behind
+  // the batch's event, and with lk after the lock has been released: other
+  // threads (cluster creation) are not held up for the duration of the
+  // solve, and nothing lands on the context's stream without the lock.
   struct Relock {
     std::unique_lock<std::mutex>* lk;
     ~Relock() {
       if (lk && !lk->owns_lock()) lk->lock();
     }
   } relock{lk};
-  if (lk) {
-    // the waiting thread sleeps instead of spinning: the host threads stay
-    // free for cluster creation meanwhile
-    if (!p->done) CUDA_TRY(ctx, cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming | cudaEventBlockingSync));
-    CUDA_TRY(ctx, cudaEventRecord(p->done, ctx->stream));
-    lk->unlock();
-    CUDA_TRY(ctx, cudaEventSynchronize(p->done));
-  }
+  // the waiting thread sleeps instead of spinning: the host threads stay
+  // free for cluster creation meanwhile
+  if (!p->done) CUDA_TRY(ctx, cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming | cudaEventBlockingSync));
+  CUDA_TRY(ctx, cudaEventRecord(p->done, ctx->stream));
+  if (lk) lk->unlock();
+  const cudaStream_t cs = ctx->copy_stream;
+  CUDA_TRY(ctx, cudaEventSynchronize(p->done));
   if (lm) {
     lm->resize(n);
-    CUDA_TRY(ctx, cudaMemcpyAsync(lm->data(), p->lm_out, sizeof(LmState) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaMemcpyAsync(lm->data(), p->lm_out, sizeof(LmState) * n, cudaMemcpyDeviceToHost, cs));
   }
   if (trace && dtrace) {
     trace->assign((size_t)n * tcap, StepRec{});
-    CUDA_TRY(ctx, cudaMemcpyAsync(trace->data(), dtrace, sizeof(StepRec) * (size_t)n * tcap, cudaMemcpyDeviceToHost,
-                                  ctx->stream));
-    CUDA_TRY(ctx, cudaFreeAsync(dtrace, ctx->stream));
+    CUDA_TRY(ctx, cudaMemcpyAsync(trace->data(), dtrace, sizeof(StepRec) * (size_t)n * tcap, cudaMemcpyDeviceToHost, cs));
+    CUDA_TRY(ctx, cudaFreeAsync(dtrace, cs));
   }
-  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(cs));
   if (lk) lk->lock();
   CUDA_TRY(ctx, cudaGetLastError());
   note_direct(ctx);
@@ -1846,7 +1853,8 @@ ba_status warm_copy(ba_ctx* ctx, Cluster* c, Cluster* src, const int32_t* cam_ma
 // runs one LM iteration for every slot, reading the table as data.  Every
 // round the scheduler (1) admits queued clusters into free slots and uploads
 // the table if it changed, (2) launches the graph, (3) reads back the slots'
-// LM state and retires the clusters that reached their iteration count.
+// LM states of the round before (rounds are pipelined one deep; see
+// scheduler_loop) and retires the clusters that stopped on the device.
 // Requests that arrive while others run join at the next round.  A cluster's
 // iterations are exactly those of ba_run: every reduction is per cluster and
 // fixed-order, so results do not depend on which clusters share a round.
@@ -1862,25 +1870,31 @@ ba_status slots_setup(ba_ctx* ctx) {
   const size_t o_pre = L.add(sizeof(int) * (3 * (size_t)(n + 1) + 3));
   const size_t o_ord = L.add(sizeof(int) * n);
   const size_t o_arm = L.add(sizeof(int) * n);
+  const size_t o_ftol = L.add(sizeof(double) * n);
   const size_t o_lm = L.add(sizeof(LmState) * n);
   const size_t o_dummy = L.add(sizeof(LmState));
   T.bytes = L.off;
   T.o_lm = o_lm;
   CUDA_TRY(ctx, cudaMalloc((void**)&T.dbuf, T.bytes));
   CUDA_TRY(ctx, cudaMemset(T.dbuf, 0, T.bytes));
-  CUDA_TRY(ctx, cudaMallocHost((void**)&T.hbuf, T.bytes));
-  std::memset(T.hbuf, 0, T.bytes);
+  CUDA_TRY(ctx, cudaMallocHost((void**)&T.hbuf, 2 * T.bytes));
+  std::memset(T.hbuf, 0, 2 * T.bytes);
+  for (auto& ev : T.done) CUDA_TRY(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  CUDA_TRY(ctx, cudaEventCreateWithFlags(&T.tail, cudaEventDisableTiming));
   ctx->mem += T.bytes;
   T.n = n;
   T.d_desc = (DevCluster*)(T.dbuf + o_desc);
   T.d_pre = (int*)(T.dbuf + o_pre);
   T.d_order = (int*)(T.dbuf + o_ord);
   T.d_arm = (int*)(T.dbuf + o_arm);
+  T.d_ftol = (double*)(T.dbuf + o_ftol);
   T.d_lm = (LmState*)(T.dbuf + o_lm);
   T.empty = DevCluster{};
   T.empty.lm = (LmState*)(T.dbuf + o_dummy);  // zeroed: inactive, nothing to evaluate
   T.descs.assign(n, T.empty);
   T.arm.assign(n, 0);
+  T.ftol.assign(n, 0.0);
+  T.first_round.assign(n, -1);
   T.occ.assign(n, 0);
   T.occ_ticket.assign(n, 0);
   T.lm.assign(n, LmState{});
@@ -1900,7 +1914,7 @@ ba_status slots_setup(ba_ctx* ctx) {
   return BA_OK;
 }
 
-ba_status slots_upload(ba_ctx* ctx) {
+ba_status slots_upload(ba_ctx* ctx, int parity) {
   SlotTable& T = ctx->slots;
   const int n = T.n;
   std::vector<int> pre(3 * (size_t)(n + 1) + 3, 0), order(n);
@@ -1916,25 +1930,30 @@ ba_status slots_upload(ba_ctx* ctx) {
   pre[3 * (n + 1) + 2] = pre[2 * (n + 1) + n];
   std::stable_sort(order.begin(), order.end(),
                    [&](int a, int b) { return T.descs[a].n_free > T.descs[b].n_free; });
-  // the whole table through the pinned mirror in one copy (the previous
-  // round's copies have completed: every round ends with a stream sync)
-  char* const h = T.hbuf;
+  // the whole table through this parity's pinned mirror in one copy (the
+  // mirror's last copy, two rounds ago, has completed: that round has been
+  // collected)
+  char* const h = T.hbuf + parity * T.bytes;
   auto at = [&](const void* dev) { return h + ((const char*)dev - T.dbuf); };
   std::memcpy(at(T.d_desc), T.descs.data(), sizeof(DevCluster) * n);
   std::memcpy(at(T.d_pre), pre.data(), sizeof(int) * pre.size());
   std::memcpy(at(T.d_order), order.data(), sizeof(int) * n);
   std::memcpy(at(T.d_arm), T.arm.data(), sizeof(int) * n);
+  std::memcpy(at(T.d_ftol), T.ftol.data(), sizeof(double) * n);
   CUDA_TRY(ctx, cudaMemcpyAsync(T.dbuf, h, T.o_lm, cudaMemcpyHostToDevice, ctx->sched_stream));
   T.dirty = false;
   return BA_OK;
 }
 
-// one round: arm -> F for newly armed slots -> one LM iteration -> gather
-ba_status slots_round(ba_ctx* ctx) {
+// Launch one round on the scheduler's stream: arm -> F for newly armed slots
+// -> one LM iteration -> gather; then the LM states go back to this parity's
+// pinned mirror and the parity's event is recorded.  Nothing here waits for
+// the device.
+ba_status slots_launch(ba_ctx* ctx, int parity) {
   SlotTable& T = ctx->slots;
   const int gen = ctx->tune_gen.load();
   if (T.graph.exec && T.tune_gen != gen) {  // launch parameters changed since the capture
-    cudaGraphExecDestroy(T.graph.exec);
+    cudaGraphExecDestroy(T.graph.exec);      // freed once a launch of it in flight completes
     T.graph.exec = nullptr;
     free_probe(T.graph.probe);
     T.graph.probe = nullptr;
@@ -1950,7 +1969,7 @@ ba_status slots_round(ba_ctx* ctx) {
       set_probe(T.graph.probe);
     }
     CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->sched_stream, cudaStreamCaptureModeThreadLocal));
-    launch_arm_slots(T.bv, T.d_arm, ctx->sched_stream);
+    launch_arm_slots(T.bv, T.d_arm, T.d_ftol, ctx->sched_stream);
     launch_cost_init(T.bv, ctx->mixed, ctx->sched_stream);
     launch_iteration(T.bv, ctx->mixed, ctx->refine, ctx->sched_stream);
     launch_gather(T.bv, 0, T.d_lm, nullptr, ctx->sched_stream);
@@ -1963,17 +1982,16 @@ ba_status slots_round(ba_ctx* ctx) {
     if (e != cudaSuccess) return set_err(ctx, BA_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   }
   if (T.dirty) {
-    ba_status st = slots_upload(ctx);
+    ba_status st = slots_upload(ctx, parity);
     if (st != BA_OK) return st;
   }
   CUDA_TRY(ctx, cudaGraphLaunch(T.graph.exec, ctx->sched_stream));
   ctx->launches += T.graph.kernels;
-  CUDA_TRY(ctx, cudaMemcpyAsync(T.hbuf + T.o_lm, T.d_lm, sizeof(LmState) * T.n, cudaMemcpyDeviceToHost,
-                                ctx->sched_stream));
-  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->sched_stream));
-  CUDA_TRY(ctx, cudaGetLastError());
-  std::memcpy(T.lm.data(), T.hbuf + T.o_lm, sizeof(LmState) * T.n);
-  if (ctx->timing && T.graph.probe) fold_probe(ctx, T.graph.probe);
+  CUDA_TRY(ctx, cudaMemcpyAsync(T.hbuf + parity * T.bytes + T.o_lm, T.d_lm, sizeof(LmState) * T.n,
+                                cudaMemcpyDeviceToHost, ctx->sched_stream));
+  CUDA_TRY(ctx, cudaEventRecord(T.done[parity], ctx->sched_stream));
+  CUDA_TRY(ctx, cudaEventRecord(T.tail, ctx->sched_stream));
+  // the slots armed for this round are not armed again by the next one
   bool armed = false;
   for (int s = 0; s < T.n; ++s)
     if (T.arm[s]) {
@@ -1984,17 +2002,54 @@ ba_status slots_round(ba_ctx* ctx) {
   return BA_OK;
 }
 
+// Wait for the round of this parity and take its LM states.
+ba_status slots_collect(ba_ctx* ctx, int parity) {
+  SlotTable& T = ctx->slots;
+  CUDA_TRY(ctx, cudaEventSynchronize(T.done[parity]));
+  CUDA_TRY(ctx, cudaGetLastError());
+  if (ctx->timing && T.graph.probe) fold_probe(ctx, T.graph.probe);
+  std::memcpy(T.lm.data(), T.hbuf + parity * T.bytes + T.o_lm, sizeof(LmState) * T.n);
+  return BA_OK;
+}
+
+// The scheduler thread.  Rounds are pipelined one deep: round r is launched
+// before the results of round r - 1 are read, so the host's work between
+// rounds (reading the states, retiring and admitting clusters, the table
+// upload) overlaps the device's next round.  A cluster whose state shows it
+// finished (its iteration count reached, converged on the device, or an
+// error) leaves the table for the next launch and its ticket completes at
+// once, although it may still sit, inert (inactive), in the round already in
+// flight, which reads its LM state: ba_poll therefore orders the context's
+// stream after the last round launched before it hands a result back, so
+// that nothing the caller then queues on the cluster (freeing it, a reset, a
+// warm start) overtakes that round.  With per-kernel timing the rounds run
+// one at a time (a graph's event probes are read after each round).
 void scheduler_loop(ba_ctx* ctx) {
   SlotTable& T = ctx->slots;
   cudaSetDevice(ctx->device);
-  int running = 0;
+  int occupied = 0;          // slots holding a cluster
+  long long launched = 0;    // rounds launched
+  long long collected = 0;   // rounds read
   std::vector<cudaEvent_t> admitted;
+  auto finish_ticket = [&](int s, const std::chrono::steady_clock::time_point& now) {
+    Ticket& tk = ctx->tickets[T.occ_ticket[s]];
+    tk.done = 1;
+    tk.res.latency_ms = std::chrono::duration<double, std::milli>(now - tk.t_submit).count();
+    {
+      std::lock_guard<std::mutex> g(ctx->api_mu);
+      Cluster* c = find_cluster(ctx, T.occ[s]);
+      if (c) c->in_service = 0;
+    }
+    T.occ[s] = 0;
+    T.first_round[s] = -1;
+    --occupied;
+  };
   for (;;) {
     admitted.clear();
     {
       std::unique_lock<std::mutex> lk(ctx->sv_mu);
-      ctx->sv_cv.wait(lk, [&] { return ctx->sched_stop || !ctx->queue.empty() || running > 0; });
-      if (ctx->sched_stop && running == 0) return;
+      ctx->sv_cv.wait(lk, [&] { return ctx->sched_stop || !ctx->queue.empty() || occupied > 0 || launched > collected; });
+      if (ctx->sched_stop && occupied == 0 && launched == collected) return;
       for (int s = 0; s < T.n && !ctx->queue.empty(); ++s) {
         if (T.occ[s]) continue;
         const ba_ticket t = ctx->queue.front();
@@ -2014,13 +2069,15 @@ void scheduler_loop(ba_ctx* ctx) {
         T.occ_ticket[s] = t;
         T.descs[s] = c->h;
         T.arm[s] = tk.iters;
+        T.ftol[s] = tk.ftol;
+        T.first_round[s] = launched;  // it runs from the next round on
         T.dirty = true;
-        ++running;
+        ++occupied;
         admitted.push_back(tk.ready);
         tk.ready = nullptr;
       }
     }
-    // The round runs without the API lock: the clusters in the slots are
+    // The rounds run without the API lock: the clusters in the slots are
     // marked in service, which every call that writes or frees a cluster
     // refuses.  Work the caller queued on the context's stream before
     // submitting (creation, warm start, reset) is ordered before the round.
@@ -2029,40 +2086,50 @@ void scheduler_loop(ba_ctx* ctx) {
       if (cudaStreamWaitEvent(ctx->sched_stream, ev, 0) != cudaSuccess) st = BA_ERR_CUDA;
       cudaEventDestroy(ev);
     }
-    if (st == BA_OK) st = slots_round(ctx);
+    // launch the next round while one may still be in flight (the mirrors
+    // of its parity are free: the round two back has been read)
+    if (st == BA_OK && occupied > 0) {
+      st = slots_launch(ctx, (int)(launched & 1));
+      if (st == BA_OK) ++launched;
+    }
+    // read the older round in flight: always when two are, otherwise when no
+    // further round follows it, or right away with per-kernel timing
+    long long reading = -1;
+    const long long pending = launched - collected;
+    if (st == BA_OK && (pending >= 2 || (pending == 1 && (occupied == 0 || ctx->timing)))) {
+      reading = collected;
+      st = slots_collect(ctx, (int)(reading & 1));
+      collected = reading + 1;
+    }
+    if (st != BA_OK) {  // let whatever was queued end before the clusters are handed back
+      cudaStreamSynchronize(ctx->sched_stream);
+      collected = launched;
+    }
     {
       std::lock_guard<std::mutex> lk(ctx->sv_mu);
       const auto now = std::chrono::steady_clock::now();
       for (int s = 0; s < T.n; ++s) {
         if (!T.occ[s]) continue;
-        Ticket& tk = ctx->tickets[T.occ_ticket[s]];
+        if (st != BA_OK) {  // the round failed: every occupied slot ends with the error
+          ctx->tickets[T.occ_ticket[s]].res.status = st;
+          T.descs[s] = T.empty;
+          T.dirty = true;
+          finish_ticket(s, now);
+          continue;
+        }
+        if (reading < 0 || T.first_round[s] > reading) continue;  // not in the round read
         const LmState& L = T.lm[s];
-        bool finish = st != BA_OK || !L.active;
-        if (st == BA_OK) {  // one round = one LM iteration of every occupied slot
-          ++tk.rounds;
-          // converged: an accepted step (not the first) lowered F by at most ftol * F
-          if (!finish && tk.ftol > 0.0 && tk.acc_last >= 0 && L.n_accepted > tk.acc_last &&
-              tk.F_last - L.F <= tk.ftol * tk.F_last)
-            finish = true;
-          tk.F_last = L.F;
-          tk.acc_last = L.n_accepted;
-        }
-        if (!finish) continue;
-        tk.done = 1;
-        tk.res.status = st != BA_OK ? st : T.lm[s].status;
-        tk.res.iters = tk.rounds;
-        tk.res.final_cost = T.lm[s].F;
-        tk.res.accepted = T.lm[s].n_accepted;
-        tk.res.latency_ms = std::chrono::duration<double, std::milli>(now - tk.t_submit).count();
-        {
-          std::lock_guard<std::mutex> g(ctx->api_mu);
-          Cluster* c = find_cluster(ctx, T.occ[s]);
-          if (c) c->in_service = 0;
-        }
-        T.occ[s] = 0;
+        if (L.active) continue;
+        // finished in the round read: its result; out of the table from the
+        // next launch on
+        Ticket& tk = ctx->tickets[T.occ_ticket[s]];
+        tk.res.status = L.status;
+        tk.res.iters = L.iter - L.iter0;
+        tk.res.final_cost = L.F;
+        tk.res.accepted = L.n_accepted;
         T.descs[s] = T.empty;
         T.dirty = true;
-        --running;
+        finish_ticket(s, now);
       }
       ctx->sv_cv.notify_all();
     }
@@ -2133,11 +2200,13 @@ BA_API ba_status ba_init(ba_ctx** out, const ba_config* cfg) {
   const uint64_t keep = UINT64_MAX;
   if (cudaStreamCreateWithFlags(&ctx->sched_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->plan_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess ||
       cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, (void*)&keep) != cudaSuccess) {
     if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     if (ctx->sched_stream) cudaStreamDestroy(ctx->sched_stream);
     if (ctx->plan_stream) cudaStreamDestroy(ctx->plan_stream);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return BA_ERR_CUDA;
@@ -2571,10 +2640,28 @@ BA_API ba_status ba_submit(ba_ctx* ctx, ba_cluster_id id, const ba_solve_opts* o
 
 BA_API ba_status ba_poll(ba_ctx* ctx, ba_ticket t, ba_result* out) {
   if (!ctx) return BA_ERR_INVALID;
+  {
+    std::lock_guard<std::mutex> lk(ctx->sv_mu);
+    auto it = ctx->tickets.find(t);
+    if (it == ctx->tickets.end()) return BA_ERR_NOT_FOUND;
+    if (!it->second.done) return BA_PENDING;
+  }
+  // The cluster may still be read (inert) by the serving round in flight:
+  // whatever the caller queues on it from now on waits for that round (under
+  // the API lock, so that the wait cannot land in another thread's capture of
+  // the context's stream).
+  cudaError_t e = cudaSuccess;
+  {
+    std::lock_guard<std::mutex> g(ctx->api_mu);
+    if (ctx->slots.tail) e = cudaStreamWaitEvent(ctx->stream, ctx->slots.tail, 0);
+  }
   std::lock_guard<std::mutex> lk(ctx->sv_mu);
   auto it = ctx->tickets.find(t);
   if (it == ctx->tickets.end()) return BA_ERR_NOT_FOUND;
-  if (!it->second.done) return BA_PENDING;
+  if (e != cudaSuccess) {
+    ctx->tickets.erase(it);
+    return set_err(ctx, BA_ERR_CUDA, std::string("ordering after the serving round: ") + cudaGetErrorString(e));
+  }
   if (out) *out = it->second.res;
   ctx->tickets.erase(it);
   return BA_OK;
@@ -2582,8 +2669,8 @@ BA_API ba_status ba_poll(ba_ctx* ctx, ba_ticket t, ba_result* out) {
 
 BA_API ba_status ba_get_state(ba_ctx* ctx, ba_cluster_id id, double* R, double* T, double* X, int32_t ptr_kind) {
   if (!ctx) return BA_ERR_INVALID;
-  std::lock_guard<std::mutex> g(ctx->api_mu);
   std::lock_guard<std::mutex> hs(ctx->hstage_mu);
+  std::lock_guard<std::mutex> g(ctx->api_mu);
   Cluster* c = find_cluster(ctx, id);
   if (!c) return BA_ERR_NOT_FOUND;
   // one kernel writes the requested parts of the current state into one
@@ -2625,6 +2712,7 @@ BA_API ba_status ba_get_state(ba_ctx* ctx, ba_cluster_id id, double* R, double* 
 BA_API ba_status ba_get_state_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32_t n, double* const* R,
                                     double* const* T, double* const* X) {
   if (!ctx || (n > 0 && !ids) || n < 0) return BA_ERR_INVALID;
+  std::lock_guard<std::mutex> hs(ctx->hstage_mu);  // (taken before the API lock, as in ba_get_state)
   std::unique_lock<std::mutex> g(ctx->api_mu);
   std::vector<Cluster*> cs(n);
   for (int i = 0; i < n; ++i) {
@@ -2632,20 +2720,21 @@ BA_API ba_status ba_get_state_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32
     if (!cs[i]) return BA_ERR_NOT_FOUND;
     if (cs[i]->in_service) return set_err(ctx, BA_ERR_INVALID, "cluster is in service");
   }
-  // the batch's clusters are in service while the device exports them and the
-  // host copies them out, without the context's lock (other threads may create
-  // or solve other clusters meanwhile)
+  // The batch's clusters are in service for the call.  Each group's work is
+  // queued on the context's stream under the lock; the wait for it and the
+  // host copies run without the lock (other threads may create or solve
+  // other clusters meanwhile).
   for (Cluster* c : cs) c->in_service = 1;
   struct Release {
     ba_ctx* ctx;
     std::vector<Cluster*>& cs;
+    std::unique_lock<std::mutex>& g;
     ~Release() {
-      std::lock_guard<std::mutex> l(ctx->api_mu);
+      if (!g.owns_lock()) g.lock();
       for (Cluster* c : cs) c->in_service = 0;
     }
-  } release{ctx, cs};
-  g.unlock();
-  std::lock_guard<std::mutex> hs(ctx->hstage_mu);
+  } release{ctx, cs, g};
+  if (!ctx->state_done) CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->state_done, cudaEventDisableTiming | cudaEventBlockingSync));
   // groups of clusters whose states fit the pinned staging (at most
   // kStateStageBytes, or one cluster's state if that is larger): per group,
   // one device export per cluster into one block, one copy, one wait
@@ -2655,6 +2744,7 @@ BA_API ba_status ba_get_state_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32
     size_t total = doubles_of(i0);
     int i1 = i0 + 1;
     while (i1 < n && sizeof(double) * (total + doubles_of(i1)) <= kStateStageBytes) total += doubles_of(i1++);
+    if (!g.owns_lock()) g.lock();
     if (ctx->hstage_bytes < sizeof(double) * total) {
       if (ctx->hstage) cudaFreeHost(ctx->hstage);
       ctx->hstage = nullptr;
@@ -2676,7 +2766,9 @@ BA_API ba_status ba_get_state_batch(ba_ctx* ctx, const ba_cluster_id* ids, int32
     note_direct(ctx);
     CUDA_TRY(ctx, cudaMemcpyAsync(ctx->hstage, tmp, sizeof(double) * total, cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_TRY(ctx, cudaFreeAsync(tmp, ctx->stream));
-    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    CUDA_TRY(ctx, cudaEventRecord(ctx->state_done, ctx->stream));
+    g.unlock();
+    CUDA_TRY(ctx, cudaEventSynchronize(ctx->state_done));
     off = 0;
     std::vector<HostCopy> out;
     for (int i = i0; i < i1; ++i) {
@@ -2941,6 +3033,9 @@ BA_API ba_status ba_destroy_cluster(ba_ctx* ctx, ba_cluster_id id) {
   drop_plans_with(ctx, id);
   ctx->clusters.erase(id);
   ctx->mem -= c->arena_bytes;
+  // a serving round in flight may still read the cluster (inert, after its
+  // ticket completed): the memory goes back once that round has ended
+  if (ctx->slots.tail) CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, ctx->slots.tail, 0));
   CUDA_TRY(ctx, cudaFreeAsync(c->arena, ctx->stream));
   delete c;
   return BA_OK;
@@ -2962,6 +3057,9 @@ BA_API ba_status ba_shutdown(ba_ctx* ctx) {
   free_probe(ctx->slots.graph.probe);
   if (ctx->slots.dbuf) cudaFree(ctx->slots.dbuf);
   if (ctx->slots.hbuf) cudaFreeHost(ctx->slots.hbuf);
+  for (auto& ev : ctx->slots.done)
+    if (ev) cudaEventDestroy(ev);
+  if (ctx->slots.tail) cudaEventDestroy(ctx->slots.tail);
   for (auto& kv : ctx->plans) free_plan(ctx, kv.second);
   for (auto& kv : ctx->clusters) {
     cudaFreeAsync(kv.second->arena, ctx->stream);
@@ -2971,7 +3069,9 @@ BA_API ba_status ba_shutdown(ba_ctx* ctx) {
   cudaMemPoolDestroy(ctx->pool);
   cudaStreamDestroy(ctx->sched_stream);
   cudaStreamDestroy(ctx->plan_stream);
+  cudaStreamDestroy(ctx->copy_stream);
   if (ctx->hstage) cudaFreeHost(ctx->hstage);
+  if (ctx->state_done) cudaEventDestroy(ctx->state_done);
   for (auto& b : ctx->stage_free) cudaFreeHost(b.first);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;

@@ -362,6 +362,9 @@ __device__ __forceinline__ void lm_update_warp(const DevCluster& C, int lane) {
     }
     lm->iter += 1;
     if (lm->iter >= lm->iters_target) lm->active = 0;
+    // converged (serving): an accepted step, not the first since arming, that
+    // lowered F by at most ftol * F
+    if (lm->ftol > 0.0 && accepted && lm->iter - lm->iter0 >= 2 && F - Fn <= lm->ftol * F) lm->active = 0;
     lm->pt_fail = 0;
     lm->mu_f = (float)lm->mu;
     cur = lm->cur;

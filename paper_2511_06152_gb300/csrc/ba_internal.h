@@ -98,7 +98,9 @@ struct LmState {
   int dev_error;     // a kernel gave up on a bounded wait this iteration (kDevErrTimeout); rejects the step
   int tiles_done;    // back-substitution tiles finished this iteration; the warp that finishes the last
                      // one takes the cluster's LM decision (zeroed by the factor kernels)
-  int pad1;
+  int iter0;         // iter when the cluster was last armed
+  double ftol;       // serving: an accepted step after the first that lowers F by at most ftol * F
+                     // ends the solve (0: off)
 };
 
 constexpr int kDevErrTimeout = -4;  // = BA_ERR_TIMEOUT
@@ -289,7 +291,7 @@ cudaError_t set_big_attributes(int max_n);
 // Kernel launchers (ba_kernels.cu).  All run on `st`.
 cudaError_t set_kernel_attributes(int max_n);
 void launch_arm(const BatchView& bv, int iters, cudaStream_t st);
-void launch_arm_slots(const BatchView& bv, const int* arm, cudaStream_t st);
+void launch_arm_slots(const BatchView& bv, const int* arm, const double* ftol, cudaStream_t st);
 // DSM raster on the device (heights h[iy * nx + ix] at (x0 + ix dx, y0 + iy dy)),
 // with its height range
 struct DsmView {

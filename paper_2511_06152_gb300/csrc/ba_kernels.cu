@@ -2069,12 +2069,15 @@ __global__ void k_arm(BatchView bv, int iters) {
     }
     lm->needs_init = 1;
     lm->pt_fail = 0;
+    lm->iter0 = lm->iter;
+    lm->ftol = 0.0;
   }
 }
 
 // Serving slots: arm[s] > 0 starts arm[s] more iterations for slot s (and asks
-// for F at its state first); 0 leaves the slot as it is.
-__global__ void k_arm_slots(BatchView bv, const int* arm) {
+// for F at its state first), ending early on convergence when ftol[s] > 0; 0
+// leaves the slot as it is.
+__global__ void k_arm_slots(BatchView bv, const int* arm, const double* ftol) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < bv.n; s += gridDim.x * blockDim.x) {
     const int a = arm[s];
     if (a <= 0) continue;
@@ -2083,6 +2086,8 @@ __global__ void k_arm_slots(BatchView bv, const int* arm) {
     lm->active = 1;
     lm->needs_init = 1;
     lm->pt_fail = 0;
+    lm->iter0 = lm->iter;
+    lm->ftol = ftol[s];
   }
 }
 
@@ -2275,8 +2280,8 @@ void launch_arm(const BatchView& bv, int iters, cudaStream_t st) {
   LAUNCH(KK_OTHER, st, k_arm<<<(bv.n + 127) / 128, 128, 0, st>>>(bv, iters));
 }
 
-void launch_arm_slots(const BatchView& bv, const int* arm, cudaStream_t st) {
-  LAUNCH(KK_OTHER, st, k_arm_slots<<<(bv.n + 127) / 128, 128, 0, st>>>(bv, arm));
+void launch_arm_slots(const BatchView& bv, const int* arm, const double* ftol, cudaStream_t st) {
+  LAUNCH(KK_OTHER, st, k_arm_slots<<<(bv.n + 127) / 128, 128, 0, st>>>(bv, arm, ftol));
 }
 
 void launch_warm_copy(const DevCluster* dst, const DevCluster* src, const int2* cams, int n_cams, const int2* pts,
