@@ -551,10 +551,10 @@ FLOP_LIN = dict(obs=258, free_obs=294, pair=216, pt=45)
 FLOP_BACK = dict(obs=236, free_obs=36, pair=0, pt=30)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes (read + write) per observation of one k_lin_schur launch, from an
-# ncu capture of the current kernel on 32 clusters of the same mix (120.73 MB for
+# ncu capture of the current kernel on 32 clusters of the same mix (120.82 MB for
 # 2,452,644 observations); scaled to a launch by its observations.  Set to
 # None whenever the kernel changes until it is captured again.
-LIN_SCHUR_DRAM_BYTES_PER_OBS = (81.5232e6 + 38.791936e6) / 2452644
+LIN_SCHUR_DRAM_BYTES_PER_OBS = (81.449216e6 + 39.365888e6) / 2452644
 FP64_PEAK_TFLOPS = 1.25                               # nominal dense FP64
 TUNE_DEFAULTS = dict(chunk_tiles=0, lin_ctas_per_sm=8, back_ctas_per_sm=16, factor_nb=8, factor_threads=512,
                      big_panel_w=4)

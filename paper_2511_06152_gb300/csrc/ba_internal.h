@@ -20,7 +20,7 @@
 
 namespace bagpu {
 
-constexpr int kSrec = 28;         // per-observation shared record: Jc[12], P[6], r[2], u[2], W[3], pad
+constexpr int kSrec = 28;         // per-observation shared record: Jc[12], r[2], u[2], W[3], pad, P[6], pad
 #ifndef BA_LIN_SCHUR_MIN_BLOCKS
 #define BA_LIN_SCHUR_MIN_BLOCKS 2
 #endif

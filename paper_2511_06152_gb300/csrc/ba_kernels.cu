@@ -403,11 +403,12 @@ __device__ __forceinline__ void linearize_tile(const DevCluster& C, LmState* lm,
 // ------------------------------------------------------------------ K1: linearise + Schur reductions, one CTA per chunk
 
 // Shared record of one observation, kSrec = 28 Real, 16-byte aligned:
-// Jc [0, 12), P [12, 18) (P = Jp M^T, 2x3), r [18, 20), u = P q [20, 22),
-// W = I - P P^T as (w00, w01, w11) [22, 25), pad.  Since Z = Jc^T P, the
-// observation's share of the image block is Jc^T Jc - Z Z^T = Jc^T W Jc, of
-// the right-hand side Z q = Jc^T u, and of a pair block
-// Z_a Z_b^T = Jc_a^T (P_a P_b^T) Jc_b.
+// Jc [0, 12), r [12, 14), u = P q [14, 16), W = I - P P^T as
+// (w00, w01, w11) [16, 19), pad, P [20, 26) (P = Jp M^T, 2x3), pad.  Since
+// Z = Jc^T P, the observation's share of the image block is
+// Jc^T Jc - Z Z^T = Jc^T W Jc, of the right-hand side Z q = Jc^T u, and of a
+// pair block Z_a Z_b^T = Jc_a^T (P_a P_b^T) Jc_b.  An image job reads the
+// first five 16-byte groups, a pair job groups 0-2, 5 and 6.
 // Jc (12) and P (6)
 template <typename Real>
 __device__ __forceinline__ void ld_rec_jcp(const Real* r, Real Jc[12], Real P[6]) {
@@ -415,8 +416,8 @@ __device__ __forceinline__ void ld_rec_jcp(const Real* r, Real Jc[12], Real P[6]
   ld4(r, 4, Jc + 4);
   ld4(r, 8, Jc + 8);
   Real t[4];
-  ld4(r, 12, P);
-  ld4(r, 16, t);
+  ld4(r, 20, P);
+  ld4(r, 24, t);
   P[4] = t[0];
   P[5] = t[1];
 }
@@ -426,17 +427,16 @@ __device__ __forceinline__ void ld_rec_cam(const Real* r, Real Jc[12], Real rr[2
   ld4(r, 0, Jc);
   ld4(r, 4, Jc + 4);
   ld4(r, 8, Jc + 8);
-  Real a[4], b[4], c[4];
-  ld4(r, 16, a);
-  ld4(r, 20, b);
-  ld4(r, 24, c);
-  rr[0] = a[2]; rr[1] = a[3];
-  u[0] = b[0]; u[1] = b[1];
-  w[0] = b[2]; w[1] = b[3]; w[2] = c[0];
+  Real a[4], b[4];
+  ld4(r, 12, a);
+  ld4(r, 16, b);
+  rr[0] = a[0]; rr[1] = a[1];
+  u[0] = a[2]; u[1] = a[3];
+  w[0] = b[0]; w[1] = b[1]; w[2] = b[2];
 }
 
-// Store one observation's record (vector stores): Jc, P, r, u = P q and
-// W = I - P P^T.
+// Store one observation's record (vector stores): Jc, r, u = P q,
+// W = I - P P^T and P.
 template <bool MIXED>
 __device__ __forceinline__ void st_rec(typename RealOf<MIXED>::T* r, const TileLin<MIXED>& L) {
   using Real = typename RealOf<MIXED>::T;
@@ -447,8 +447,8 @@ __device__ __forceinline__ void st_rec(typename RealOf<MIXED>::T* r, const TileL
   const Real w01 = -(P[0] * P[3] + P[1] * P[4] + P[2] * P[5]);
   const Real w11 = Real(1) - (P[3] * P[3] + P[4] * P[4] + P[5] * P[5]);
   const Real v[28] = {L.Jc[0], L.Jc[1], L.Jc[2], L.Jc[3], L.Jc[4], L.Jc[5], L.Jc[6], L.Jc[7], L.Jc[8], L.Jc[9],
-                      L.Jc[10], L.Jc[11], P[0], P[1], P[2], P[3], P[4], P[5], L.r0, L.r1, u0, u1, w00, w01,
-                      w11, Real(0), Real(0), Real(0)};
+                      L.Jc[10], L.Jc[11], L.r0, L.r1, u0, u1, w00, w01, w11, Real(0),
+                      P[0], P[1], P[2], P[3], P[4], P[5], Real(0), Real(0)};
   if constexpr (MIXED) {
     float4* o = reinterpret_cast<float4*>(r);
 #pragma unroll
@@ -534,13 +534,30 @@ __device__ __forceinline__ void job_sums(const DevCluster& C, const Job& J, bool
   }
 }
 
+// One job's partial sums as 16-byte stores (the rows are 16-byte aligned:
+// kCamPart and kPairPart are multiples of 16 bytes); a camera row's last
+// group carries a zero in its pad word.
+static_assert(kCamPart % 4 == 0 && kPairPart % 4 == 0, "partial rows of 16-byte groups");
+__device__ __forceinline__ void store_job_row(float* out, bool cam, const float acc[39]) {
+  float4* o = reinterpret_cast<float4*>(out);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) o[i] = make_float4(acc[4 * i], acc[4 * i + 1], acc[4 * i + 2], acc[4 * i + 3]);
+  if (cam) o[9] = make_float4(acc[36], acc[37], acc[38], 0.f);
+}
+__device__ __forceinline__ void store_job_row(double* out, bool cam, const double acc[39]) {
+  double2* o = reinterpret_cast<double2*>(out);
+#pragma unroll
+  for (int i = 0; i < 18; ++i) o[i] = make_double2(acc[2 * i], acc[2 * i + 1]);
+  if (cam) {
+    o[18] = make_double2(acc[36], acc[37]);
+    o[19] = make_double2(acc[38], 0.0);
+  }
+}
+
 template <typename Real>
 __device__ __forceinline__ void store_job(const DevCluster& C, const Job& J, bool cam, const Real acc[39]) {
   Real* out = cam ? (Real*)C.campart + (size_t)kCamPart * J.slot : (Real*)C.pairpart + (size_t)kPairPart * J.slot;
-  const int width = cam ? 39 : 36;
-#pragma unroll
-  for (int i = 0; i < 39; ++i)
-    if (i < width) out[i] = acc[i];
+  store_job_row(out, cam, acc);
 }
 
 // bytes of the per-observation records (and, overlaid, the lane partials)
