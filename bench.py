@@ -6,7 +6,8 @@ double-float Cholesky of the equilibrated reduced system, back-substitution,
 double-float cost, accept/reject) of a
 batch of 256 independent, uneven local-BA clusters (8-32 images in 2-3
 strips, 5k-60k points, tracks 2 + Geometric(0.5)), all clusters in one
-CUDA-graph launch, starting from the clusters' initial GNSS/IMU state.
+CUDA-graph launch (four concurrent launch chains over parts of the batch),
+starting from the clusters' initial GNSS/IMU state.
 
 Metric: observations/s = sum(n_obs) * iterations / time, plus LM
 iterations/s, against the plain per-cluster FP64 GPU path and the FP64 CPU
@@ -557,7 +558,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x ma
 LIN_SCHUR_DRAM_BYTES_PER_OBS = (81.449216e6 + 39.365888e6) / 2452644
 FP64_PEAK_TFLOPS = 1.25                               # nominal dense FP64
 TUNE_DEFAULTS = dict(chunk_tiles=0, lin_ctas_per_sm=8, back_ctas_per_sm=16, factor_nb=8, factor_threads=512,
-                     big_panel_w=4)
+                     big_panel_w=4, batch_chains=4)
 
 
 def units(infos):
@@ -714,6 +715,23 @@ def main():
     ms = e0.elapsed_time(e1)
     launches = ctx.launch_count() - launches0
     kst = ctx.kernel_stats(reset=True)
+    # Per-kernel times (breakdown and roofline): in the timed steps the
+    # batch's iterations run as concurrent launch chains whose kernels share
+    # the GPU, so a launch's duration is not one kernel's; two more steps with
+    # the iterations as one chain time each kernel alone on the GPU.
+    chains = ctx.get_tune()["batch_chains"]
+    kernel_timing = "timed steps (one launch chain)"
+    if chains > 1:
+        ctx.set_tune(batch_chains=1)
+        step()  # captures the one-chain graph
+        ctx.kernel_stats(reset=True)
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        kst = ctx.kernel_stats(reset=True)
+        ctx.set_tune(batch_chains=chains)
+        kernel_timing = (f"2 steps after the timed region with the iterations as one launch chain (the timed steps "
+                         f"ran {chains} concurrent chains)")
     # slowest rank's time; observations of every rank's own replica
     t_max, obs_all = over_ranks(ms, total_obs, world, torch.distributed if world > 1 else None, "cuda")
     ms_per_step = t_max / args.steps
@@ -771,7 +789,7 @@ def main():
                        "iters": iters, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (no flush)"},
             "lm_iters_per_s": lm_iters_per_s, "clocks": ck, "gpu_launches": launches, "roofline": roof,
-            "kernels": kernels,
+            "kernels": kernels, "kernel_timing": kernel_timing,
             "fp32_fma_peak": {"tflops": fp32_peak, "runs": fp32_runs, "clocks": fp32_ck,
                               "derived_tflops_at_2070_mhz": FP32_PEAK_TFLOPS}}
     tune_now = ctx.get_tune()

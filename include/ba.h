@@ -368,9 +368,11 @@ BA_API ba_status ba_solve_step(ba_ctx* ctx, ba_cluster_id id, ba_step_info* out)
  * zero.  Blocking.  Errors as ba_solve_step; BA_ERR_INVALID for iters < 0. */
 BA_API ba_status ba_run(ba_ctx* ctx, ba_cluster_id id, int32_t iters, ba_step_info* trace);
 
-/* iters LM iterations on n clusters at once: every kernel of an iteration is
- * one launch over all clusters, and the whole sequence is one CUDA-graph
- * launch.  Each cluster's result equals its ba_run result bit for bit.
+/* iters LM iterations on n clusters at once: the clusters are dealt to
+ * batch_chains (ba_tune) concurrent launch chains, every kernel of an
+ * iteration is one launch over a chain's clusters, and the whole sequence is
+ * one CUDA-graph launch.  Each cluster's result equals its ba_run result bit
+ * for bit, for any number of chains.
  * results[n] may be NULL; trace may be NULL or [n][iters].  While the device
  * runs the batch the context stays open to other threads (creating, reading
  * or solving other clusters); the batch's own clusters are in service until
@@ -508,7 +510,7 @@ BA_API ba_status ba_cost_noalloc(const ba_cluster_desc* d, void* stream, double*
  * Values: chunk_tiles 0 (the precision's maximum: 16 mixed, 8 FP64) or
  * 4 .. that maximum; lin_ctas_per_sm and back_ctas_per_sm 1 .. 32;
  * factor_nb 2 .. 32; factor_threads 256, 384 or 512; big_panel_w 1, 2, 4, 8,
- * 16 or 32.  ms_default / ms_tuned: what ba_autotune measured (device time
+ * 16 or 32; batch_chains 1 .. 8.  ms_default / ms_tuned: what ba_autotune measured (device time
  * of one solve of its batch with the defaults and with the chosen values;
  * 0 when not measured). */
 typedef struct {
@@ -518,6 +520,8 @@ typedef struct {
   int32_t factor_nb;        /* panel width of the shared-memory Cholesky (clusters of <= 32 free images) */
   int32_t factor_threads;   /* threads of its CTA */
   int32_t big_panel_w;      /* column-block width of the tensor-core solver's diagonal factorisation */
+  int32_t batch_chains;     /* a batch's LM iterations as this many concurrent launch chains over disjoint
+                               parts of the batch (clusters dealt by decreasing size); 1: one chain */
   double ms_default;
   double ms_tuned;
 } ba_tune;
@@ -549,7 +553,8 @@ BA_API ba_status ba_autotune(ba_ctx* ctx, const ba_cluster_desc* descs, int32_t 
 /* Host only: the entry of a tuning table (a text file) for a GPU and a
  * precision.  One entry per line, '#' starts a comment:
  *   <gpu name, spaces as '_'> <SM count> <fp64|mixed> chunk_tiles=.. lin_ctas_per_sm=..
- *   back_ctas_per_sm=.. factor_nb=.. factor_threads=.. big_panel_w=.. [ms_default=.. ms_tuned=..]
+ *   back_ctas_per_sm=.. factor_nb=.. factor_threads=.. big_panel_w=.. batch_chains=..
+ *   [ms_default=.. ms_tuned=..]
  * Missing keys keep their defaults; the last matching line wins.
  * BA_ERR_NOT_FOUND when the file has no such entry or cannot be read,
  * BA_ERR_INVALID for a malformed matching entry or out-of-range values. */

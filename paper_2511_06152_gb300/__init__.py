@@ -48,7 +48,8 @@ class ba_config(ctypes.Structure):
                 ("flags", ctypes.c_int32), ("tune_table", ctypes.c_char_p)]
 
 
-TUNE_KEYS = ("chunk_tiles", "lin_ctas_per_sm", "back_ctas_per_sm", "factor_nb", "factor_threads", "big_panel_w")
+TUNE_KEYS = ("chunk_tiles", "lin_ctas_per_sm", "back_ctas_per_sm", "factor_nb", "factor_threads", "big_panel_w",
+             "batch_chains")
 # the committed tuning table that Context hands to ba_init (entries per GPU and precision)
 TUNE_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.txt")
 

@@ -51,11 +51,20 @@ struct GraphRec {
   Probe* probe = nullptr;          // event pairs captured with the graph (timing mode)
 };
 
+// One of a batch's concurrent iteration chains: a view of part of the
+// batch (its own descriptor copies, prefix sums and factor order) and the
+// part's clusters that go to the global-memory solver.
+struct Chain {
+  BatchView bv{};
+  std::vector<BigRef> big;
+};
+
 struct Plan {
   std::vector<ba_cluster_id> ids;
   char* dbuf = nullptr;
   size_t dbuf_bytes = 0;
   BatchView bv{};
+  std::vector<Chain> chains;     // the LM iterations' launches, one stream each (empty: one chain, bv)
   LmState* lm_out = nullptr;     // device [n]
   double* gnorm = nullptr;       // device [n]
   std::map<int, GraphRec> graphs;
@@ -158,6 +167,12 @@ struct ba_ctx {
   cudaEvent_t state_done = nullptr;     // end of a ba_get_state_batch group's copy
   size_t hstage_bytes = 0;
   SlotTable slots;
+  // forked streams of a batch graph's concurrent chains (capture only: no
+  // work is ever issued to them outside a capture), with the fork and join
+  // events; created on first use
+  std::vector<cudaStream_t> chain_streams;
+  std::vector<cudaEvent_t> chain_join;
+  cudaEvent_t chain_fork = nullptr;
 };
 
 namespace {
@@ -322,6 +337,7 @@ bool tune_in_range(const ba_tune& t, bool mixed, std::string* why) {
     return bad("factor_threads must be 256, 384 or 512");
   if (t.big_panel_w < 1 || t.big_panel_w > 32 || (32 % t.big_panel_w) != 0)
     return bad("big_panel_w must be 1, 2, 4, 8, 16 or 32");
+  if (t.batch_chains < 1 || t.batch_chains > kMaxBatchChains) return bad("batch_chains must be 1 .. 8");
   return true;
 }
 
@@ -333,6 +349,7 @@ TuneParams tune_from_abi(const ba_tune& t) {
   p.factor_nb = t.factor_nb;
   p.factor_threads = t.factor_threads;
   p.big_panel_w = t.big_panel_w;
+  p.batch_chains = t.batch_chains;
   return p;
 }
 
@@ -344,6 +361,7 @@ ba_tune tune_to_abi(const TuneParams& p) {
   t.factor_nb = p.factor_nb;
   t.factor_threads = p.factor_threads;
   t.big_panel_w = p.big_panel_w;
+  t.batch_chains = p.batch_chains;
   return t;
 }
 
@@ -403,11 +421,13 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
   if (st != BA_OK) return st;
   Plan* p = new Plan();
   p->ids = ids;
+  auto big_ref = [&](const Cluster* c) {
+    return BigRef{c->d_desc, 6 * c->nf, c->nf, c->h.n_pairs, c->h.S, c->h.F, c->big_below, !ctx->big_fp64,
+                  ctx->tune.big_panel_w};
+  };
   for (int i = 0; i < n; ++i) {
     Cluster* c = find_cluster(ctx, ids[i]);
-    if (c->nf > kMaxFreeSmall)
-      p->big.push_back(BigRef{c->d_desc, 6 * c->nf, c->nf, c->h.n_pairs, c->h.S, c->h.F, c->big_below, !ctx->big_fp64,
-                              ctx->tune.big_panel_w});
+    if (c->nf > kMaxFreeSmall) p->big.push_back(big_ref(c));
   }
   pre.push_back(pre[n]);  // totals, read by the kernels
   pre.push_back(pre[(n + 1) + n]);
@@ -421,6 +441,46 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
   std::vector<int> order(n);  // factor kernel: largest reduced systems first
   for (int i = 0; i < n; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return descs[a].n_free > descs[b].n_free; });
+  // The LM iterations run as tune.batch_chains concurrent chains of launches over
+  // disjoint parts of the batch, so that one chain's kernels fill the SMs
+  // another chain's kernels leave idle (the factor's largest systems, the
+  // grids' last waves, the gaps between launches).  Clusters are dealt to
+  // the chains in order of decreasing reduced-system size; a chain lists its
+  // clusters in batch order.  Every cluster's arithmetic is its own, so the
+  // results do not depend on the split.
+  struct ChainHost {
+    std::vector<int> mem;  // batch indices
+    std::vector<DevCluster> descs;
+    std::vector<int> pre, ord;
+    size_t o_desc = 0, o_pre = 0, o_ord = 0;
+    int max_n = 6;
+  };
+  const int n_chains = std::min(n, ctx->tune.batch_chains);
+  std::vector<ChainHost> chh(n_chains > 1 ? n_chains : 0);
+  for (int r = 0; r < n && n_chains > 1; ++r) chh[r % n_chains].mem.push_back(order[r]);
+  for (ChainHost& h : chh) {
+    std::sort(h.mem.begin(), h.mem.end());
+    const int m = (int)h.mem.size();
+    h.pre.assign(3 * (size_t)(m + 1), 0);
+    for (int i = 0; i < m; ++i) {
+      const DevCluster& d = descs[h.mem[i]];
+      h.descs.push_back(d);
+      h.pre[i + 1] = h.pre[i] + d.n_tiles;
+      h.pre[(m + 1) + i + 1] = h.pre[(m + 1) + i] + d.n_chunks;
+      h.pre[2 * (m + 1) + i + 1] = h.pre[2 * (m + 1) + i] + d.n_free + d.n_pairs;
+      if (find_cluster(ctx, ids[h.mem[i]])->nf <= kMaxFreeSmall) h.max_n = std::max(h.max_n, 6 * d.n_free);
+    }
+    h.pre.push_back(h.pre[m]);
+    h.pre.push_back(h.pre[(m + 1) + m]);
+    h.pre.push_back(h.pre[2 * (m + 1) + m]);
+    h.ord.resize(m);
+    for (int i = 0; i < m; ++i) h.ord[i] = i;
+    std::stable_sort(h.ord.begin(), h.ord.end(),
+                     [&](int a, int b) { return h.descs[a].n_free > h.descs[b].n_free; });
+    h.o_desc = L.add(sizeof(DevCluster) * m);
+    h.o_pre = L.add(sizeof(int) * h.pre.size());
+    h.o_ord = L.add(sizeof(int) * m);
+  }
   p->dbuf_bytes = L.off;
   if (ctx->budget && ctx->mem + p->dbuf_bytes > ctx->budget) {
     delete p;
@@ -441,6 +501,15 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
     e = cudaMemcpyAsync(p->dbuf + o_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, ps);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(p->dbuf + o_ord, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ps);
+  for (const ChainHost& h : chh) {
+    const size_t m = h.mem.size();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->dbuf + h.o_desc, h.descs.data(), sizeof(DevCluster) * m, cudaMemcpyHostToDevice, ps);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->dbuf + h.o_pre, h.pre.data(), sizeof(int) * h.pre.size(), cudaMemcpyHostToDevice, ps);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->dbuf + h.o_ord, h.ord.data(), sizeof(int) * m, cudaMemcpyHostToDevice, ps);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(ps);
   if (e != cudaSuccess) {
     ctx->mem -= p->dbuf_bytes;
@@ -461,6 +530,29 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
   p->bv.max_n = max_n;
   p->bv.inject = ctx->inject;
   apply_tune(ctx, p->bv);
+  for (const ChainHost& h : chh) {
+    const int m = (int)h.mem.size();
+    Chain c;
+    const int* cpre = (const int*)(p->dbuf + h.o_pre);
+    c.bv.cl = (const DevCluster*)(p->dbuf + h.o_desc);
+    c.bv.tile_pre = cpre;
+    c.bv.chunk_pre = cpre + (m + 1);
+    c.bv.item_pre = cpre + 2 * (m + 1);
+    c.bv.factor_order = (const int*)(p->dbuf + h.o_ord);
+    c.bv.tot = cpre + 3 * (m + 1);
+    c.bv.n = m;
+    c.bv.total_tiles = h.pre[m];
+    c.bv.total_chunks = h.pre[(m + 1) + m];
+    c.bv.total_items = h.pre[2 * (m + 1) + m];
+    c.bv.max_n = h.max_n;
+    c.bv.inject = ctx->inject;
+    apply_tune(ctx, c.bv);
+    for (int i : h.mem) {
+      const Cluster* cc = find_cluster(ctx, ids[i]);
+      if (cc->nf > kMaxFreeSmall) c.big.push_back(big_ref(cc));
+    }
+    p->chains.push_back(std::move(c));
+  }
   p->lm_out = (LmState*)(p->dbuf + o_lm);
   p->gnorm = (double*)(p->dbuf + o_gn);
   ctx->plans[ids] = p;
@@ -468,13 +560,56 @@ ba_status get_plan(ba_ctx* ctx, const std::vector<ba_cluster_id>& ids, Plan** ou
   return BA_OK;
 }
 
+// Streams and events for forking k - 1 chains off the context's stream
+// inside a capture (created once, kept until shutdown).
+ba_status ensure_chain_streams(ba_ctx* ctx, int k) {
+  if (!ctx->chain_fork) CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->chain_fork, cudaEventDisableTiming));
+  while ((int)ctx->chain_streams.size() < k - 1) {
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ce = nullptr;
+    CUDA_TRY(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const cudaError_t e = cudaEventCreateWithFlags(&ce, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cs);
+      return set_err(ctx, BA_ERR_CUDA, std::string("chain event: ") + cudaGetErrorString(e));
+    }
+    ctx->chain_streams.push_back(cs);
+    ctx->chain_join.push_back(ce);
+  }
+  return BA_OK;
+}
+
+// Inside a capture on the context's stream: the plan's chains, chain 0 on
+// the context's stream and chain c on chain_streams[c - 1], forked after
+// what the stream holds and joined back into it.
+cudaError_t capture_chains(ba_ctx* ctx, Plan* p, int iters) {
+  const int k = (int)p->chains.size();
+  cudaError_t e = cudaEventRecord(ctx->chain_fork, ctx->stream);
+  for (int c = 1; c < k && e == cudaSuccess; ++c) e = cudaStreamWaitEvent(ctx->chain_streams[c - 1], ctx->chain_fork, 0);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < iters; ++i)
+    for (int c = 0; c < k; ++c)
+      launch_iteration(p->chains[c].bv, ctx->mixed, ctx->refine, c == 0 ? ctx->stream : ctx->chain_streams[c - 1],
+                       &p->chains[c].big);
+  for (int c = 1; c < k && e == cudaSuccess; ++c) {
+    e = cudaEventRecord(ctx->chain_join[c - 1], ctx->chain_streams[c - 1]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->chain_join[c - 1], 0);
+  }
+  return e;
+}
+
 // iters LM iterations on the plan's clusters as one graph launch:
-// arm -> cost at the current state -> iters x (K1..K6).
+// arm -> cost at the current state -> iters x (K1..K6), the iterations as
+// the plan's concurrent chains when it has more than one.
 ba_status run_plan(ba_ctx* ctx, Plan* p, int iters) {
   auto it = p->graphs.find(iters);
   if (it == p->graphs.end()) {
     GraphRec g;
     cudaGraph_t graph = nullptr;
+    if (!p->chains.empty()) {
+      const ba_status cst = ensure_chain_streams(ctx, (int)p->chains.size());
+      if (cst != BA_OK) return cst;
+    }
     note_direct(ctx);
     take_captured_launches();
     if (ctx->timing) {
@@ -484,8 +619,18 @@ ba_status run_plan(ba_ctx* ctx, Plan* p, int iters) {
     CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     launch_arm(p->bv, iters, ctx->stream);
     launch_cost_init(p->bv, ctx->mixed, ctx->stream);
-    for (int i = 0; i < iters; ++i) launch_iteration(p->bv, ctx->mixed, ctx->refine, ctx->stream, &p->big);
+    cudaError_t ec = cudaSuccess;
+    if (p->chains.empty()) {
+      for (int i = 0; i < iters; ++i) launch_iteration(p->bv, ctx->mixed, ctx->refine, ctx->stream, &p->big);
+    } else {
+      ec = capture_chains(ctx, p, iters);
+    }
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (e == cudaSuccess && ec != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      graph = nullptr;
+      e = ec;
+    }
     set_probe(nullptr);
     g.kernels = take_captured_launches();
     if (e != cudaSuccess) {
@@ -2920,6 +3065,7 @@ BA_API ba_status ba_autotune(ba_ctx* ctx, const ba_cluster_desc* descs, int32_t 
       {&TuneParams::factor_nb, {4, 16}, false},
       {&TuneParams::factor_threads, {384, 256}, false},
       {&TuneParams::big_panel_w, {2, 8}, true},
+      {&TuneParams::batch_chains, {2, 8}, false},
   };
   for (const Knob& k : knobs) {
     if (k.big_only && !has_big) continue;
@@ -2982,6 +3128,7 @@ BA_API ba_status ba_tune_table_lookup(const char* path, const char* gpu_name, in
       else if (key == "factor_nb") t.factor_nb = (int)v;
       else if (key == "factor_threads") t.factor_threads = (int)v;
       else if (key == "big_panel_w") t.big_panel_w = (int)v;
+      else if (key == "batch_chains") t.batch_chains = (int)v;
       else if (key == "ms_default") t.ms_default = v;
       else if (key == "ms_tuned") t.ms_tuned = v;
       else return BA_ERR_INVALID;
@@ -3070,6 +3217,9 @@ BA_API ba_status ba_shutdown(ba_ctx* ctx) {
   cudaStreamDestroy(ctx->sched_stream);
   cudaStreamDestroy(ctx->plan_stream);
   cudaStreamDestroy(ctx->copy_stream);
+  for (cudaStream_t cs : ctx->chain_streams) cudaStreamDestroy(cs);
+  for (cudaEvent_t ce : ctx->chain_join) cudaEventDestroy(ce);
+  if (ctx->chain_fork) cudaEventDestroy(ctx->chain_fork);
   if (ctx->hstage) cudaFreeHost(ctx->hstage);
   if (ctx->state_done) cudaEventDestroy(ctx->state_done);
   for (auto& b : ctx->stage_free) cudaFreeHost(b.first);

@@ -34,6 +34,7 @@ constexpr int kChunkObsF64 = 32 * kChunkTilesF64;
 constexpr int kChunkThreads = 256;
 constexpr int kMaxTrack = 32;
 constexpr int kMaxFreeSmall = 32;  // free cameras the single-CTA factor handles (n <= 192)
+constexpr int kMaxBatchChains = 8;  // concurrent launch chains of a batch's LM iterations, at most
 constexpr int kMaxFree = 1024;     // free cameras of one cluster (larger systems: the global-memory solver)
 constexpr int kBigNB = 32;         // block size of the global-memory factorisation
 constexpr int kSlicesHost = 6;     // Ozaki digits per double-float entry (kSlices of ba_tc.cuh)
@@ -221,6 +222,7 @@ struct TuneParams {
   int factor_nb = 8;
   int factor_threads = 512;
   int big_panel_w = 4;       // columns of a block of the global-memory solver's panel factorisation
+  int batch_chains = 4;      // concurrent launch chains of a batch's LM iterations
 };
 
 // kInjectCopyTimeout: the mixed linearise+Schur kernel waits for its first

@@ -9,7 +9,7 @@ import pytest
 import paper_2511_06152_gb300 as ba
 
 DEFAULTS = dict(chunk_tiles=0, lin_ctas_per_sm=8, back_ctas_per_sm=16, factor_nb=8, factor_threads=512,
-                big_panel_w=4)
+                big_panel_w=4, batch_chains=4)
 
 
 def _write(tmp_path, lines):
@@ -20,7 +20,7 @@ def _write(tmp_path, lines):
 
 def test_formatted_line_round_trips(tmp_path):
     t = dict(chunk_tiles=12, lin_ctas_per_sm=4, back_ctas_per_sm=8, factor_nb=16, factor_threads=384, big_panel_w=2,
-             ms_default=71.5, ms_tuned=68.25)
+             batch_chains=3, ms_default=71.5, ms_tuned=68.25)
     path = _write(tmp_path, ["# header", ba.tune_table_line("NVIDIA GB300", 152, ba.BA_MIXED, t)])
     got = ba.tune_table_lookup(path, "NVIDIA GB300", 152, ba.BA_MIXED)
     assert got == t
@@ -39,7 +39,8 @@ def test_other_gpus_and_precisions_are_ignored_and_the_last_line_wins(tmp_path):
 
 
 @pytest.mark.parametrize("entry", ["chunk_tiles=3", "chunk_tiles=17", "factor_threads=300", "big_panel_w=3",
-                                   "lin_ctas_per_sm=0", "factor_nb=64", "unknown_key=1", "chunk_tiles", "factor_nb=x"])
+                                   "lin_ctas_per_sm=0", "factor_nb=64", "batch_chains=0", "batch_chains=9",
+                                   "unknown_key=1", "chunk_tiles", "factor_nb=x"])
 def test_bad_entries_are_rejected(tmp_path, entry):
     path = _write(tmp_path, [f"NVIDIA_GB300 152 mixed {entry}"])
     with pytest.raises(ba.BAError) as ei:
