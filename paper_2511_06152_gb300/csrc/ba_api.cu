@@ -1188,8 +1188,10 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
   }
 
   // point-major order: counting sort by internal point, then by camera within
-  // a point; the camera and internal point of each point-major observation
-  // are written in the same scatter
+  // a point.  The scatter writes one packed word per observation (camera in
+  // the high half, observation index in the low half), so the per-point sort
+  // by camera moves single words and, with ties in observation order, is the
+  // stable sort by camera; the point of each entry follows from the counts.
   std::vector<int> cnt((size_t)np + 1, 0), pm(no), pcam(no), ppt(no);
   {
     std::vector<int> okey(no);  // internal point of each observation
@@ -1200,31 +1202,30 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
     }
     for (int j = 0; j < np; ++j) cnt[j + 1] += cnt[j];
     std::vector<int> pos(cnt.begin(), cnt.end() - 1);
-    for (int i = 0; i < no; ++i) {
-      const int j = okey[i], q = pos[j]++;
-      pm[q] = i;
-      pcam[q] = ocam[i];
-      ppt[q] = j;
+    std::vector<uint64_t> ent(no);
+    for (int i = 0; i < no; ++i) ent[pos[okey[i]]++] = ((uint64_t)(uint32_t)ocam[i] << 32) | (uint32_t)i;
+    for (int j = 0; j < np; ++j) {
+      const int s = cnt[j], e = cnt[j + 1];
+      if (e - s > kMaxTrack) return set_err(ctx, BA_ERR_INVALID, "a point has more than 32 observations");
+      for (int a = s + 1; a < e; ++a) {  // insertion sort of the point's words
+        const uint64_t v = ent[a];
+        int b = a - 1;
+        while (b >= s && ent[b] > v) {
+          ent[b + 1] = ent[b];
+          --b;
+        }
+        ent[b + 1] = v;
+      }
+      for (int q = s; q < e; ++q) {
+        pm[q] = (int)(uint32_t)ent[q];
+        pcam[q] = (int)(ent[q] >> 32);
+        ppt[q] = j;
+      }
+      for (int a = s + 1; a < e; ++a)
+        if (pcam[a] == pcam[a - 1]) return set_err(ctx, BA_ERR_INVALID, "repeated (camera, point) observation");
     }
   }
   std::vector<int> pt_start(cnt);
-  for (int j = 0; j < np; ++j) {
-    const int s = pt_start[j], e = pt_start[j + 1];
-    if (e - s > kMaxTrack) return set_err(ctx, BA_ERR_INVALID, "a point has more than 32 observations");
-    for (int a = s + 1; a < e; ++a) {  // insertion sort by camera (stable), carrying the observation
-      const int v = pm[a], vc = pcam[a];
-      int b = a - 1;
-      while (b >= s && pcam[b] > vc) {
-        pm[b + 1] = pm[b];
-        pcam[b + 1] = pcam[b];
-        --b;
-      }
-      pm[b + 1] = v;
-      pcam[b + 1] = vc;
-    }
-    for (int a = s + 1; a < e; ++a)
-      if (pcam[a] == pcam[a - 1]) return set_err(ctx, BA_ERR_INVALID, "repeated (camera, point) observation");
-  }
 
   // tiles: runs of whole points with at most 32 observations
   std::vector<Tile> tiles;
@@ -1280,7 +1281,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
     std::vector<int> local_pair_of;     // fa * nf + fb -> local pair, -1 between chunks
     std::vector<int> pf;                // free camera of each observation of the chunk, or -1
     std::vector<int> lp_keys, lp_cnt, lp_off, order;
-    std::vector<int> item_lp;           // local pair of each pair item, in point-major order
+    std::vector<int> item_lp;           // local pair of each pair item, in point-major order (grown, not cleared)
     std::vector<unsigned int> item_val;
     std::vector<double> cost;
     std::vector<int> lanes;
@@ -1321,8 +1322,18 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
     // are sorted by camera), local pairs numbered by first appearance
     S.lp_keys.clear();
     S.lp_cnt.clear();
-    S.item_lp.clear();
-    S.item_val.clear();
+    size_t max_items = 0;  // k (k - 1) / 2 per point of k observations
+    for (int j = ch.pt_begin; j < ch.pt_begin + ch.n_pts; ++j) {
+      const size_t k = (size_t)(pt_start[j + 1] - pt_start[j]);
+      max_items += k > 1 ? k * (k - 1) / 2 : 0;
+    }
+    if (S.item_lp.size() < max_items) {
+      S.item_lp.resize(max_items);
+      S.item_val.resize(max_items);
+    }
+    int* const item_lp = S.item_lp.data();
+    unsigned int* const item_val = S.item_val.data();
+    size_t n_items = 0;
     for (int j = ch.pt_begin; j < ch.pt_begin + ch.n_pts; ++j) {
       const int s0 = pt_start[j] - o0, e0 = pt_start[j + 1] - o0;
       for (int a = s0; a < e0; ++a) {
@@ -1339,8 +1350,9 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
             S.lp_cnt.push_back(0);
           }
           ++S.lp_cnt[lp];
-          S.item_lp.push_back(lp);
-          S.item_val.push_back((unsigned)a | ((unsigned)b << 16));
+          item_lp[n_items] = lp;
+          item_val[n_items] = (unsigned)a | ((unsigned)b << 16);
+          ++n_items;
         }
       }
     }
@@ -1363,7 +1375,7 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
         S.local_pair_of[key] = -1;
       }
       J.pe.resize(off);
-      for (size_t i = 0; i < S.item_lp.size(); ++i) J.pe[S.lp_off[S.item_lp[i]]++] = S.item_val[i];
+      for (size_t i = 0; i < n_items; ++i) J.pe[S.lp_off[item_lp[i]]++] = item_val[i];
     }
     // Lanes per job: every lane of every job gets about the same work, a
     // quantum Q of instructions (camera item ~165, pair item ~123), the
