@@ -1297,6 +1297,9 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
     S.pf.resize(ch.n_obs);  // free camera of each of the chunk's observations, or -1
     int* const pf = S.pf.data();
     for (int p = o0; p < o1; ++p) pf[p - o0] = free_idx[pcam[p]];
+    J.cam.reserve(nf);
+    J.count.reserve(nf + 64);
+    J.key.reserve(64);
     // image jobs: items counted, jobs ordered, then each item placed at its
     // job's next position (a stable counting sort: point-major order kept)
     for (int i = 0; i < ch.n_obs; ++i) {
@@ -1450,7 +1453,8 @@ ba_status build_cluster(ba_ctx* ctx, const ba_cluster_desc* d, Cluster* c, const
         evaluated = nr;
         return tot <= kChunkThreads;
       };
-      bool align = alloc(1e300, true) <= kChunkThreads;  // one lane each must fit
+      // one lane each must fit (alloc at an unbounded quantum, in closed form)
+      bool align = (n_lp > 0 ? (n_lc + 31) / 32 * 32 : n_lc) + n_lp <= kChunkThreads;
       double lo = 0.0, hi = 1.0;
       for (int q = 0; q < nj; ++q) hi = std::max(hi, S.cost[q]);
       for (int r = 0; r < nr; ++r) {
